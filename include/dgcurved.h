@@ -1,0 +1,172 @@
+/*
+ * dgcurved.h -- C ABI of libdgcurved.so, a GB300 (sm_103a) implementation of
+ * the right-hand side and Runge-Kutta stage update of the curved-element
+ * discontinuous Galerkin method for the 2D Euler equations of Siebenborn,
+ * Schulz & Schmidt, "A curved-element unstructured discontinuous Galerkin
+ * method on GPUs for the Euler equations" (arXiv 1208.4772).
+ *
+ * Conventions (all calls)
+ *   - Every function returns an int status: DG_OK (0) or a negative DG_E*
+ *     code.  No C++ exception crosses the ABI.  dg_last_error(ctx) returns a
+ *     NUL-terminated description of the last failure on that context (valid
+ *     until the next call on the same context; ctx may be NULL for calls
+ *     that take none).
+ *   - Reference triangle T: vertices (-1,-1), (1,-1), (-1,1).  Elements are
+ *     counter-clockwise; face f joins local vertices f and (f+1) mod 3.  On a
+ *     shared face the neighbour runs the edge the other way, so face point g
+ *     meets the neighbour's point N_g - 1 - g.
+ *   - N is the polynomial degree, 2 <= N <= 6; N_p = (N+1)(N+2)/2.
+ *   - Canonical host state layout: double U[K][4][N_p], variables
+ *     (rho, rho u, rho v, E), nodes in the order of dg_reference_nodes.  The
+ *     device layout is private to the library.
+ *   - Pointers passed in are only read during the call (the library copies
+ *     what it keeps); pointers passed out are caller-owned buffers of the
+ *     stated size.  All calls on one context are issued on its stream and
+ *     are not thread-safe with respect to each other.
+ *   - Calls that read results back (dg_get_state, dg_eval_rhs, dg_residual)
+ *     synchronise the context's stream; dg_step and dg_batch_step only
+ *     enqueue work (use dg_sync to wait).
+ */
+#ifndef DGCURVED_H
+#define DGCURVED_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum dg_status {
+    DG_OK = 0,
+    DG_EINVAL = -1,      /* bad argument, malformed mesh, non-positive Jacobian */
+    DG_ENOMEM = -2,      /* device or host allocation failed, or budget exceeded */
+    DG_ECUDA = -3,       /* a CUDA runtime call failed */
+    DG_ENONFINITE = -4,  /* a residual norm came back NaN or Inf */
+    DG_ETIMEOUT = -5,    /* dg_sync gave up waiting */
+    DG_EBUSY = -6,       /* work is still in flight where none may be */
+    DG_ENOTFOUND = -7    /* unknown mesh handle */
+};
+
+/* Arithmetic of the operator products.  DG_FP32: FP32 state, FP32 FMA
+ * products.  DG_FP64_DEBUG: every device quantity in FP64 (slow; used to
+ * check the kernels' logic against the FP64 oracle to round-off).
+ * DG_TF32 and DG_BF16X3: FP32 state, operator products on the tensor
+ * cores (TF32 inputs, or each FP32 operand split into three BF16 parts),
+ * FP32 accumulate. */
+enum dg_prec { DG_FP32 = 0, DG_TF32 = 1, DG_BF16X3 = 2, DG_FP64_DEBUG = 3 };
+
+/* Face codes of the bc array.  Periodic faces are interior faces whose
+ * neighbour is the periodic image. */
+enum dg_bc { DG_BC_INTERIOR = 0, DG_BC_WALL = 1, DG_BC_FARFIELD = 2 };
+
+typedef struct dg_ctx dg_ctx;   /* opaque: device, stream, meshes, graphs */
+typedef int32_t dg_mesh;        /* mesh handle within one context */
+
+/* Physical and numerical parameters of one mesh (paper Sec. 2 and Sec. 5).
+ *   gamma      adiabatic index
+ *   flux       0 = local Lax-Friedrichs (Sec. 2 approximate Riemann solver)
+ *   av_on      1 = Persson-Peraire artificial viscosity (Sec. 2)
+ *   kappa, eps0, s0   sensor ramp parameters; s0 = NaN -> log10(1/N^4)
+ *   u_inf      conserved farfield state used by DG_BC_FARFIELD faces
+ *   prec       enum dg_prec
+ *   cub_q      points per direction of the volume rule and points per edge
+ *              of the face rule; 0 -> ceil((3N+1)/2) (exact to degree 3N) */
+typedef struct {
+    double gamma;
+    int32_t flux;
+    int32_t av_on;
+    double kappa, eps0, s0;
+    double u_inf[4];
+    int32_t prec;
+    int32_t cub_q;
+} dg_params;
+
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to
+ * issue work on, or NULL for a stream owned by the context.  *out is set on
+ * success.  Errors: DG_EINVAL (out NULL, bad device), DG_ECUDA. */
+int dg_create(dg_ctx** out, int device, void* cuda_stream);
+
+/* Free every mesh, graph and buffer of ctx, then ctx itself.  NULL is a no-op. */
+int dg_destroy(dg_ctx* ctx);
+
+/* Collocation nodes of degree N on T (paper Sec. 2: nodes after Warburton
+ * 2006, the warp & blend construction, blending parameter 0), written as
+ * rs_out[N_p][2] (caller-owned).  The order is j (the s index) outer, i
+ * inner, starting at (-1,-1).  Host-only; needs no GPU.  Errors: DG_EINVAL. */
+int dg_reference_nodes(int N, double* rs_out);
+
+/* Sizes for degree N with cub_q points per direction (0 = default):
+ * out4 = {N_p, N_q, N_g, q}.  Host-only. */
+int dg_sizes(int N, int cub_q, int32_t* out4);
+
+/* Upload one mesh (paper Sec. 4 flowchart: "setup operators and transfer to
+ * GPU").  K elements of degree N:
+ *   EToE[K][3]   neighbour element across each face (self on boundary faces)
+ *   EToF[K][3]   the neighbour's face index (0..2)
+ *   bc[K][3]     enum dg_bc per face
+ *   node_xy[K][N_p][2]  collocation-node coordinates (FP64), curved
+ *                elements by isoparametric node displacement (paper Sec. 3)
+ *   p            parameters (copied)
+ * The library builds the reference operators, computes the geometric
+ * factors in FP64 (J = |det D Psi|, r_x, ..., face normals and sJ, and the
+ * mass matrix with its Cholesky-based inverse for curved elements, paper
+ * Sec. 2 eqs. stiffness, mass, face_mass), classifies each element as affine
+ * or curved, and copies everything to the device.  The state is set to 0.
+ * Errors: DG_EINVAL (bad sizes or connectivity, J <= 0 at a cubature node,
+ * unsupported N or prec), DG_ENOMEM, DG_ECUDA. */
+int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int8_t* EToF,
+                   const int8_t* bc, const double* node_xy, const dg_params* p, dg_mesh* out);
+
+/* Release a mesh and its device memory. */
+int dg_mesh_free(dg_ctx* ctx, dg_mesh m);
+
+/* Device bytes held by mesh m (state buffers, geometry, operators, scratch). */
+int dg_mesh_bytes(dg_ctx* ctx, dg_mesh m, int64_t* out);
+
+/* Set / read the state U^n from / to host memory, canonical layout
+ * double[K][4][N_p].  The device holds it in the precision of p->prec. */
+int dg_set_state(dg_ctx* ctx, dg_mesh m, const double* U);
+int dg_get_state(dg_ctx* ctx, dg_mesh m, double* U_out);
+
+/* Device-resident variants: U is a device pointer to float[K][4][N_p] in
+ * canonical order (FP32 precision modes only).  Asynchronous on the
+ * context's stream.  Errors: DG_EINVAL for DG_FP64_DEBUG meshes. */
+int dg_set_state_device(dg_ctx* ctx, dg_mesh m, const float* U_dev);
+int dg_get_state_device(dg_ctx* ctx, dg_mesh m, float* U_dev_out);
+
+/* Right-hand side L(U^n) of the semi-discrete system (paper Sec. 2, eq.
+ * semidiscrete; with the artificial-viscosity terms when av_on) written to
+ * rhs_out[K][4][N_p] (host, FP64, canonical layout). */
+int dg_eval_rhs(dg_ctx* ctx, dg_mesh m, double* rhs_out);
+
+/* Advance U^n by nsteps SSP-RK3 steps of size dt (three right-hand-side
+ * evaluations with the stage combination fused into each; a fixed step
+ * replayed from a captured CUDA graph).  Asynchronous. */
+int dg_step(dg_ctx* ctx, dg_mesh m, double dt, int nsteps);
+
+/* Residual norms of L(U^n) per variable, accumulated in FP64 on the device
+ * (paper Sec. 5 checks the residual norm): out_linf[v] = max |L|,
+ * out_l2[v] = sqrt(sum L^2) over all nodal values.  Returns DG_ENONFINITE
+ * (with the norms still written) if any norm is NaN or Inf. */
+int dg_residual(dg_ctx* ctx, dg_mesh m, double out_linf[4], double out_l2[4]);
+
+/* Advance n meshes (any mix of N and K) by nsteps SSP-RK3 steps each, with
+ * per-mesh step sizes dts[n], using one persistent launch per RK stage that
+ * walks a work list over all n meshes, replayed from a captured CUDA graph.
+ * All meshes must share one precision mode and have av_on = 0.
+ * Asynchronous. */
+int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* ms, const double* dts, int nsteps);
+
+/* Wait for the context's stream, polling at most timeout_s seconds
+ * (<= 0: wait without limit).  DG_ETIMEOUT if work is still in flight then;
+ * the work itself is not cancelled. */
+int dg_sync(dg_ctx* ctx, double timeout_s);
+
+/* Description of the last failure on ctx (or of the last failure of a call
+ * without a context when ctx is NULL). */
+const char* dg_last_error(dg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGCURVED_H */

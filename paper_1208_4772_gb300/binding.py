@@ -1,0 +1,194 @@
+"""ctypes binding of libdgcurved.so (include/dgcurved.h), same names as the
+C ABI.  Argument marshalling only: every step of the computation runs in the
+library.  Loading fails loudly when the library is missing; there is no
+fallback.
+"""
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdgcurved.so")
+
+DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENONFINITE, DG_ETIMEOUT, DG_EBUSY, DG_ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7
+DG_FP32, DG_TF32, DG_BF16X3, DG_FP64_DEBUG = 0, 1, 2, 3
+DG_BC_INTERIOR, DG_BC_WALL, DG_BC_FARFIELD = 0, 1, 2
+PREC = {"fp32": DG_FP32, "tf32": DG_TF32, "bf16x3": DG_BF16X3, "fp64": DG_FP64_DEBUG}
+
+
+class DgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("dgcurved status %d: %s" % (status, msg))
+        self.status = status
+
+
+class dg_params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("flux", C.c_int32), ("av_on", C.c_int32),
+                ("kappa", C.c_double), ("eps0", C.c_double), ("s0", C.c_double),
+                ("u_inf", C.c_double * 4), ("prec", C.c_int32), ("cub_q", C.c_int32)]
+
+
+def make_params(gamma=1.4, av_on=False, kappa=4.0, eps0=0.3, s0=None, u_inf=(1.0, 0.0, 0.0, 2.5),
+                prec="fp32", cub_q=0):
+    p = dg_params()
+    p.gamma = gamma
+    p.flux = 0
+    p.av_on = int(bool(av_on))
+    p.kappa, p.eps0 = kappa, eps0
+    p.s0 = math.nan if s0 is None else float(s0)
+    for i in range(4):
+        p.u_inf[i] = float(u_inf[i])
+    p.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    p.cub_q = cub_q
+    return p
+
+
+_lib = None
+
+
+def load():
+    """Load the library (build it first with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libdgcurved.so not built at %s: run __graft_entry__.build()" % LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, I64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+    dp = C.POINTER(C.c_double)
+    sig = {
+        "dg_create": (I, [C.POINTER(P), I, P]),
+        "dg_destroy": (I, [P]),
+        "dg_reference_nodes": (I, [I, dp]),
+        "dg_sizes": (I, [I, I, C.POINTER(C.c_int32)]),
+        "dg_mesh_upload": (I, [P, I, I64, P, P, P, dp, C.POINTER(dg_params), C.POINTER(C.c_int32)]),
+        "dg_mesh_free": (I, [P, C.c_int32]),
+        "dg_mesh_bytes": (I, [P, C.c_int32, C.POINTER(I64)]),
+        "dg_set_state": (I, [P, C.c_int32, dp]),
+        "dg_get_state": (I, [P, C.c_int32, dp]),
+        "dg_set_state_device": (I, [P, C.c_int32, P]),
+        "dg_get_state_device": (I, [P, C.c_int32, P]),
+        "dg_eval_rhs": (I, [P, C.c_int32, dp]),
+        "dg_step": (I, [P, C.c_int32, D, I]),
+        "dg_residual": (I, [P, C.c_int32, dp, dp]),
+        "dg_batch_step": (I, [P, I, C.POINTER(C.c_int32), dp, I]),
+        "dg_sync": (I, [P, D]),
+        "dg_last_error": (C.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+def _check(status, ctx=None):
+    if status != DG_OK:
+        msg = load().dg_last_error(ctx)
+        raise DgError(status, msg.decode() if msg else "")
+    return status
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# --------------------------------------------------------------------- calls
+def dg_create(device=0, stream=None):
+    ctx = C.c_void_p()
+    _check(load().dg_create(C.byref(ctx), device, stream), None)
+    return ctx
+
+
+def dg_destroy(ctx):
+    return _check(load().dg_destroy(ctx), None)
+
+
+def dg_reference_nodes(N):
+    np_ = (N + 1) * (N + 2) // 2
+    out = np.zeros((np_, 2))
+    _check(load().dg_reference_nodes(N, _dptr(out)), None)
+    return out[:, 0].copy(), out[:, 1].copy()
+
+
+def dg_sizes(N, cub_q=0):
+    out = (C.c_int32 * 4)()
+    _check(load().dg_sizes(N, cub_q, out), None)
+    return tuple(out)
+
+
+def dg_mesh_upload(ctx, N, EToE, EToF, bc, node_xy, params):
+    EToE = np.ascontiguousarray(EToE, dtype=np.int32)
+    EToF = np.ascontiguousarray(EToF, dtype=np.int8)
+    bc = np.ascontiguousarray(bc, dtype=np.int8)
+    node_xy = np.ascontiguousarray(node_xy, dtype=np.float64)
+    K = EToE.shape[0]
+    h = C.c_int32()
+    _check(load().dg_mesh_upload(ctx, N, K, EToE.ctypes.data, EToF.ctypes.data, bc.ctypes.data,
+                                 _dptr(node_xy), C.byref(params), C.byref(h)), ctx)
+    return h.value
+
+
+def dg_mesh_free(ctx, m):
+    return _check(load().dg_mesh_free(ctx, m), ctx)
+
+
+def dg_mesh_bytes(ctx, m):
+    out = C.c_int64()
+    _check(load().dg_mesh_bytes(ctx, m, C.byref(out)), ctx)
+    return out.value
+
+
+def dg_set_state(ctx, m, U):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    return _check(load().dg_set_state(ctx, m, _dptr(U)), ctx)
+
+
+def dg_get_state(ctx, m, K, Np):
+    out = np.zeros((K, 4, Np))
+    _check(load().dg_get_state(ctx, m, _dptr(out)), ctx)
+    return out
+
+
+def dg_set_state_device(ctx, m, dev_ptr):
+    return _check(load().dg_set_state_device(ctx, m, C.c_void_p(dev_ptr)), ctx)
+
+
+def dg_get_state_device(ctx, m, dev_ptr):
+    return _check(load().dg_get_state_device(ctx, m, C.c_void_p(dev_ptr)), ctx)
+
+
+def dg_eval_rhs(ctx, m, K, Np):
+    out = np.zeros((K, 4, Np))
+    _check(load().dg_eval_rhs(ctx, m, _dptr(out)), ctx)
+    return out
+
+
+def dg_step(ctx, m, dt, nsteps):
+    return _check(load().dg_step(ctx, m, float(dt), int(nsteps)), ctx)
+
+
+def dg_residual(ctx, m, allow_nonfinite=False):
+    linf = np.zeros(4)
+    l2 = np.zeros(4)
+    st = load().dg_residual(ctx, m, _dptr(linf), _dptr(l2))
+    if not (allow_nonfinite and st == DG_ENONFINITE):
+        _check(st, ctx)
+    return linf, l2
+
+
+def dg_batch_step(ctx, meshes, dts, nsteps):
+    ms = (C.c_int32 * len(meshes))(*meshes)
+    d = np.ascontiguousarray(dts, dtype=np.float64)
+    return _check(load().dg_batch_step(ctx, len(meshes), ms, _dptr(d), int(nsteps)), ctx)
+
+
+def dg_sync(ctx, timeout_s=0.0):
+    return _check(load().dg_sync(ctx, float(timeout_s)), ctx)
+
+
+def dg_last_error(ctx=None):
+    msg = load().dg_last_error(ctx)
+    return msg.decode() if msg else ""

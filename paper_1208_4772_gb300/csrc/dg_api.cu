@@ -1,0 +1,806 @@
+// Host side of libdgcurved.so: the C ABI of include/dgcurved.h.
+//
+// Set-up (paper Sec. 4 flowchart: "setup operators and transfer to GPU"):
+// reference operators per degree (refops.cpp), per-element geometric
+// factors computed in FP64 from the collocation-node coordinates, elements
+// reordered affine-first, everything copied to the device once.  The time
+// loop enqueues the stage kernels (kernels.cuh) and replays a captured CUDA
+// graph per (mesh, dt).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "dg_device.h"
+#include "dgcurved.h"
+#include "refops.h"
+#include "dg_internal.h"
+#include "dg_batch.h"
+
+using namespace dgc;
+
+namespace {
+
+thread_local std::string g_err;  // errors of calls without a context
+
+int fail(dg_ctx* ctx, int code, const std::string& msg) {
+    if (ctx)
+        ctx->err = msg;
+    else
+        g_err = msg;
+    return code;
+}
+
+#define CUDA_OK(ctx, call)                                                                  \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) return fail((ctx), DG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+bool supported_degree(int N) { return N >= 2 && N <= 6; }
+
+template <typename Real>
+int dispatch_prepare(int N) {
+    switch (N) {
+        case 2: return prepare_kernels<2, Real>();
+        case 3: return prepare_kernels<3, Real>();
+        case 4: return prepare_kernels<4, Real>();
+        case 5: return prepare_kernels<5, Real>();
+        case 6: return prepare_kernels<6, Real>();
+    }
+    return (int)cudaErrorInvalidValue;
+}
+template <typename Real>
+int dispatch_stage(int N, const StageArgs<Real>& a, int av, cudaStream_t st) {
+    switch (N) {
+        case 2: return launch_stage<2, Real>(a, av, st);
+        case 3: return launch_stage<3, Real>(a, av, st);
+        case 4: return launch_stage<4, Real>(a, av, st);
+        case 5: return launch_stage<5, Real>(a, av, st);
+        case 6: return launch_stage<6, Real>(a, av, st);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+template <typename Real>
+int dispatch_sensor(int N, const StageArgs<Real>& a, Real* out, cudaStream_t st) {
+    switch (N) {
+        case 2: return launch_sensor<2, Real>(a, out, st);
+        case 3: return launch_sensor<3, Real>(a, out, st);
+        case 4: return launch_sensor<4, Real>(a, out, st);
+        case 5: return launch_sensor<5, Real>(a, out, st);
+        case 6: return launch_sensor<6, Real>(a, out, st);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+template <typename Real>
+int dispatch_grad(int N, const StageArgs<Real>& a, Real* out, cudaStream_t st) {
+    switch (N) {
+        case 2: return launch_grad<2, Real>(a, out, st);
+        case 3: return launch_grad<3, Real>(a, out, st);
+        case 4: return launch_grad<4, Real>(a, out, st);
+        case 5: return launch_grad<5, Real>(a, out, st);
+        case 6: return launch_grad<6, Real>(a, out, st);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+// Packed operator table (layout of ops_layout) in FP64.
+std::vector<double> pack_ops(const RefOps& R) {
+    const int NP = R.Np, NQ = R.Nq, NF = R.Nf;
+    const OpsLayout L = ops_layout(R.N);
+    std::vector<double> o(L.total, 0.0);
+    for (int j = 0; j < NP; ++j)
+        for (int q = 0; q < NQ; ++q) {
+            o[L.icub + j * NQ + q] = R.Icub[(size_t)q * NP + j];
+            o[L.itopt + j * NQ + q] = R.Itop[(size_t)q * NP + j];
+        }
+    for (int q = 0; q < NQ; ++q)
+        for (int i = 0; i < NP; ++i) {
+            o[L.mrt + q * NP + i] = R.MrW[(size_t)i * NQ + q];
+            o[L.mst + q * NP + i] = R.MsW[(size_t)i * NQ + q];
+            o[L.drt + q * NP + i] = R.DrW[(size_t)i * NQ + q];
+            o[L.dst + q * NP + i] = R.DsW[(size_t)i * NQ + q];
+        }
+    for (int j = 0; j < NP; ++j)
+        for (int fg = 0; fg < NF; ++fg) o[L.igt + j * NF + fg] = R.Ig[(size_t)fg * NP + j];
+    for (int fg = 0; fg < NF; ++fg)
+        for (int i = 0; i < NP; ++i) {
+            o[L.mlt + fg * NP + i] = R.MLift[(size_t)i * NF + fg];
+            o[L.lt + fg * NP + i] = R.Lift[(size_t)i * NF + fg];
+        }
+    for (int j = 0; j < NP; ++j)
+        for (int i = 0; i < NP; ++i) {
+            o[L.qrt + j * NP + i] = R.Qr[(size_t)i * NP + j];
+            o[L.qst + j * NP + i] = R.Qs[(size_t)i * NP + j];
+            o[L.vinvt + j * NP + i] = R.Vinv[(size_t)i * NP + j];
+        }
+    for (int q = 0; q < NQ; ++q) o[L.w + q] = R.wq[q];
+    return o;
+}
+
+const RefOps* get_refops(int N, std::string& err) {
+    static std::mutex mu;
+    static std::map<int, std::unique_ptr<RefOps>> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(N);
+    if (it != cache.end()) return it->second.get();
+    auto R = std::make_unique<RefOps>();
+    if (!build_refops(N, 0, *R, err)) return nullptr;
+    const RefOps* p = R.get();
+    cache[N] = std::move(R);
+    return p;
+}
+
+template <typename Real>
+std::vector<Real> to_real(const std::vector<double>& v) {
+    return std::vector<Real>(v.begin(), v.end());
+}
+
+int alloc(dg_ctx* ctx, MeshData& m, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return DG_OK;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ctx, DG_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    m.bytes += bytes;
+    m.allocs.push_back(*p);
+    return DG_OK;
+}
+
+void free_mesh(MeshData* m) {
+    if (!m) return;
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    if (m->graph) cudaGraphDestroy(m->graph);
+    for (void* p : m->allocs) cudaFree(p);
+    delete m;
+}
+
+void reset_batch(dg_ctx* ctx) {
+    if (ctx->batch_gexec) cudaGraphExecDestroy(ctx->batch_gexec);
+    if (ctx->batch_graph) cudaGraphDestroy(ctx->batch_graph);
+    ctx->batch_gexec = nullptr;
+    ctx->batch_graph = nullptr;
+    for (void* b : ctx->batch_bufs) cudaFree(b);
+    ctx->batch_bufs.clear();
+    ctx->batch_key_meshes.clear();
+    ctx->batch_key_dts.clear();
+}
+
+MeshData* find(dg_ctx* ctx, dg_mesh h) {
+    auto it = ctx->meshes.find(h);
+    return it == ctx->meshes.end() ? nullptr : it->second;
+}
+
+template <typename Real>
+StageArgs<Real> make_args(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b,
+                          double dt, int rhs_only) {
+    StageArgs<Real> s{};
+    s.Us = (const Real*)Us;
+    s.Un = (const Real*)Un;
+    s.Uout = (Real*)out;
+    s.a = (Real)a;
+    s.b = (Real)b;
+    s.dt = (Real)dt;
+    s.rhs_only = rhs_only;
+    s.conn = m.conn;
+    s.geoA = (const Real*)m.geoA;
+    s.geoC = (const Real*)m.geoC;
+    s.ops = (const Real*)m.ops;
+    s.eps = (const Real*)m.eps;
+    s.q = (const Real*)m.q;
+    s.K = m.K;
+    s.Kaff = m.Kaff;
+    s.gamma = (Real)m.p.gamma;
+    for (int v = 0; v < 4; ++v) s.uinf[v] = (Real)m.p.u_inf[v];
+    s.s0 = m.s0;
+    s.kappa = m.p.kappa;
+    s.eps0 = m.p.eps0;
+    return s;
+}
+
+template <typename Real>
+int enqueue_stage_t(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
+                    int rhs_only, cudaStream_t st) {
+    StageArgs<Real> s = make_args<Real>(m, Us, Un, out, a, b, dt, rhs_only);
+    int e;
+    if (m.p.av_on) {
+        if ((e = dispatch_sensor<Real>(m.N, s, (Real*)m.eps, st))) return e;
+        if ((e = dispatch_grad<Real>(m.N, s, (Real*)m.q, st))) return e;
+    }
+    return dispatch_stage<Real>(m.N, s, m.p.av_on, st);
+}
+
+}  // namespace
+
+namespace dgc {
+
+int enqueue_stage(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
+                  int rhs_only, cudaStream_t st) {
+    if (m.prec == DG_FP64_DEBUG) return enqueue_stage_t<double>(m, Us, Un, out, a, b, dt, rhs_only, st);
+    return enqueue_stage_t<float>(m, Us, Un, out, a, b, dt, rhs_only, st);
+}
+
+// One SSP-RK3 step: U0 -> U1 -> U2 -> U0 (stage 3 writes U^n in place; each
+// thread reads U^n only for the value it overwrites).
+int enqueue_step(const MeshData& m, double dt, cudaStream_t st) {
+    int e;
+    if ((e = enqueue_stage(m, m.U[0], nullptr, m.U[1], 0.0, 1.0, dt, 0, st))) return e;
+    if ((e = enqueue_stage(m, m.U[1], m.U[0], m.U[2], 0.75, 0.25, dt, 0, st))) return e;
+    return enqueue_stage(m, m.U[2], m.U[0], m.U[0], 1.0 / 3.0, 2.0 / 3.0, dt, 0, st);
+}
+
+}  // namespace dgc
+
+
+template <typename Real>
+static int build_batch(dg_ctx* ctx, const std::vector<MeshData*>& ms, const double* dts) {
+    const int n = (int)ms.size();
+    std::vector<BatchItem> items;
+    for (int i = 0; i < n; ++i) {
+        const MeshData& m = *ms[i];
+        const int E = batch_tile_e(m.N, (int)m.rsize);
+        for (long long e0 = 0; e0 < m.Kaff; e0 += E)
+            items.push_back(BatchItem{i, m.N, e0, (int)std::min<long long>(E, m.Kaff - e0), 0});
+        for (long long e0 = m.Kaff; e0 < m.K; e0 += E)
+            items.push_back(BatchItem{i, m.N, e0, (int)std::min<long long>(E, m.K - e0), 1});
+    }
+    // largest work first: curved tiles, then by degree
+    std::stable_sort(items.begin(), items.end(), [&](const BatchItem& a, const BatchItem& b) {
+        const double ca = (double)a.ne * np_of(a.N) * nq_of(a.N) * (a.curved ? 2.0 : 1.0);
+        const double cb = (double)b.ne * np_of(b.N) * nq_of(b.N) * (b.curved ? 2.0 : 1.0);
+        return ca > cb;
+    });
+    std::vector<StageArgs<Real>> args(3 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const MeshData& m = *ms[i];
+        args[i] = make_args<Real>(m, m.U[0], nullptr, m.U[1], 0.0, 1.0, dts[i], 0);
+        args[n + i] = make_args<Real>(m, m.U[1], m.U[0], m.U[2], 0.75, 0.25, dts[i], 0);
+        args[2 * n + i] = make_args<Real>(m, m.U[2], m.U[0], m.U[0], 1.0 / 3.0, 2.0 / 3.0, dts[i], 0);
+    }
+    void *dargs = nullptr, *ditems = nullptr, *dcnt = nullptr;
+    if (cudaMalloc(&dargs, args.size() * sizeof(StageArgs<Real>)) != cudaSuccess ||
+        cudaMalloc(&ditems, items.size() * sizeof(BatchItem)) != cudaSuccess ||
+        cudaMalloc(&dcnt, 4 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (dargs) cudaFree(dargs);
+        if (ditems) cudaFree(ditems);
+        return fail(ctx, DG_ENOMEM, "batch work-list allocation failed");
+    }
+    ctx->batch_bufs = {dargs, ditems, dcnt};
+    CUDA_OK(ctx, cudaMemcpy(dargs, args.data(), args.size() * sizeof(StageArgs<Real>), cudaMemcpyHostToDevice));
+    CUDA_OK(ctx, cudaMemcpy(ditems, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
+    const int grid = batch_grid<Real>(ctx->device, 0);
+    if (grid <= 0) return fail(ctx, DG_ECUDA, "batch kernel occupancy query failed");
+    CUDA_OK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    int e = (int)cudaMemsetAsync(dcnt, 0, 4 * sizeof(int), ctx->stream);
+    const size_t as = sizeof(StageArgs<Real>);
+    for (int st = 0; st < 3 && !e; ++st)
+        e = launch_batch_stage<Real>((const char*)dargs + (size_t)st * n * as, (const BatchItem*)ditems,
+                                     (int)items.size(), (int*)dcnt + st, grid, ctx->stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+    if (e || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(ctx, DG_ECUDA, "graph capture of the batched step failed");
+    }
+    ctx->batch_graph = g;
+    CUDA_OK(ctx, cudaGraphInstantiate(&ctx->batch_gexec, g, 0));
+    return DG_OK;
+}
+
+extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* hs, const double* dts, int nsteps) {
+    if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    if (n <= 0 || !hs || !dts || nsteps < 0) return fail(ctx, DG_EINVAL, "bad argument");
+    std::vector<MeshData*> ms(n);
+    for (int i = 0; i < n; ++i) {
+        ms[i] = find(ctx, hs[i]);
+        if (!ms[i]) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle in batch");
+        if (ms[i]->p.av_on) return fail(ctx, DG_EINVAL, "batched path runs meshes without artificial viscosity");
+        if (ms[i]->rsize != ms[0]->rsize) return fail(ctx, DG_EINVAL, "batch mixes precision modes");
+        if (!std::isfinite(dts[i])) return fail(ctx, DG_EINVAL, "bad dt");
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return fail(ctx, DG_EINVAL, "mesh listed twice in batch");
+    }
+    if (nsteps == 0) return DG_OK;
+    cudaSetDevice(ctx->device);
+    const std::vector<int> key(hs, hs + n);
+    const std::vector<double> kdt(dts, dts + n);
+    if (!ctx->batch_gexec || key != ctx->batch_key_meshes || kdt != ctx->batch_key_dts) {
+        CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
+        reset_batch(ctx);
+        const int e = (ms[0]->rsize == 8) ? build_batch<double>(ctx, ms, dts) : build_batch<float>(ctx, ms, dts);
+        if (e) {
+            reset_batch(ctx);
+            return e;
+        }
+        ctx->batch_key_meshes = key;
+        ctx->batch_key_dts = kdt;
+    }
+    for (int s = 0; s < nsteps; ++s) CUDA_OK(ctx, cudaGraphLaunch(ctx->batch_gexec, ctx->stream));
+    return DG_OK;
+}
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int dg_create(dg_ctx** out, int device, void* cuda_stream) {
+    if (!out) return fail(nullptr, DG_EINVAL, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return fail(nullptr, DG_EINVAL, "no such CUDA device: " + std::to_string(device));
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return fail(nullptr, DG_ECUDA, "cudaSetDevice failed");
+    auto* c = new dg_ctx();
+    c->device = device;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+        c->own_stream = false;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return fail(nullptr, DG_ECUDA, "cudaStreamCreate failed");
+        }
+        c->own_stream = true;
+    }
+    *out = c;
+    return DG_OK;
+}
+
+int dg_destroy(dg_ctx* ctx) {
+    if (!ctx) return DG_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& kv : ctx->meshes) free_mesh(kv.second);
+    ctx->meshes.clear();
+    for (auto& kv : ctx->ops) cudaFree(kv.second);
+    reset_batch(ctx);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return DG_OK;
+}
+
+int dg_reference_nodes(int N, double* rs_out) {
+    if (!rs_out) return fail(nullptr, DG_EINVAL, "rs_out is NULL");
+    if (N < 1 || N > 8) return fail(nullptr, DG_EINVAL, "N out of range");
+    std::string err;
+    const RefOps* R = get_refops(N, err);
+    if (!R) return fail(nullptr, DG_EINVAL, err);
+    for (int i = 0; i < R->Np; ++i) {
+        rs_out[2 * i] = R->r[i];
+        rs_out[2 * i + 1] = R->s[i];
+    }
+    return DG_OK;
+}
+
+int dg_sizes(int N, int cub_q, int32_t* out4) {
+    if (!out4 || N < 1 || N > 8 || cub_q < 0) return fail(nullptr, DG_EINVAL, "bad argument");
+    const int q = cub_q ? cub_q : default_q(N);
+    out4[0] = n_modes(N);
+    out4[1] = q * q;
+    out4[2] = q;
+    out4[3] = q;
+    return DG_OK;
+}
+
+int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int8_t* EToF, const int8_t* bc,
+                   const double* node_xy, const dg_params* p, dg_mesh* out) {
+    if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    if (!EToE || !EToF || !bc || !node_xy || !p || !out) return fail(ctx, DG_EINVAL, "NULL argument");
+    if (!supported_degree(N)) return fail(ctx, DG_EINVAL, "device path supports 2 <= N <= 6");
+    if (K <= 0 || K > (int64_t)1 << 31) return fail(ctx, DG_EINVAL, "K out of range");
+    if (p->cub_q != 0 && p->cub_q != default_q(N))
+        return fail(ctx, DG_EINVAL, "device path uses cub_q = ceil((3N+1)/2) only");
+    if (p->prec != DG_FP32 && p->prec != DG_FP64_DEBUG && p->prec != DG_TF32 && p->prec != DG_BF16X3)
+        return fail(ctx, DG_EINVAL, "unknown precision mode");
+    if (p->flux != 0) return fail(ctx, DG_EINVAL, "only the local Lax-Friedrichs flux (0) is built");
+    if (!(p->gamma > 1.0)) return fail(ctx, DG_EINVAL, "gamma must exceed 1");
+    std::string err;
+    const RefOps* R = get_refops(N, err);
+    if (!R) return fail(ctx, DG_EINVAL, err);
+    const int NP = R->Np, NQ = R->Nq, NF = R->Nf, NG = R->Ng;
+
+    // connectivity checks
+    for (int64_t k = 0; k < K; ++k)
+        for (int f = 0; f < 3; ++f) {
+            const int64_t nb = EToE[3 * k + f];
+            const int fn = EToF[3 * k + f], b = bc[3 * k + f];
+            if (b < 0 || b > 2) return fail(ctx, DG_EINVAL, "bad bc code at element " + std::to_string(k));
+            if (b == DG_BC_INTERIOR) {
+                if (nb < 0 || nb >= K || fn < 0 || fn > 2)
+                    return fail(ctx, DG_EINVAL, "bad neighbour at element " + std::to_string(k));
+                if (EToE[3 * nb + fn] != k || EToF[3 * nb + fn] != f)
+                    return fail(ctx, DG_EINVAL, "non-reciprocal connectivity at element " + std::to_string(k));
+            }
+        }
+
+    // classify: affine if the nodes are the affine image of the three vertex nodes
+    const int iv1 = N, iv2 = NP - 1;
+    std::vector<char> curved(K, 0);
+    for (int64_t k = 0; k < K; ++k) {
+        const double* X = node_xy + (size_t)k * NP * 2;
+        const double x0 = X[0], y0 = X[1], x1 = X[2 * iv1], y1 = X[2 * iv1 + 1], x2 = X[2 * iv2], y2 = X[2 * iv2 + 1];
+        const double diam = std::fabs(x1 - x0) + std::fabs(y1 - y0) + std::fabs(x2 - x0) + std::fabs(y2 - y0);
+        double dev = 0.0;
+        for (int i = 0; i < NP; ++i) {
+            const double l1 = -(R->r[i] + R->s[i]) / 2, l2 = (1 + R->r[i]) / 2, l3 = (1 + R->s[i]) / 2;
+            dev = std::max(dev, std::fabs(X[2 * i] - (l1 * x0 + l2 * x1 + l3 * x2)));
+            dev = std::max(dev, std::fabs(X[2 * i + 1] - (l1 * y0 + l2 * y1 + l3 * y2)));
+        }
+        if (!(dev <= 1e-12 * diam)) curved[k] = 1;
+    }
+    auto* m = new MeshData();
+    m->N = N; m->Np = NP; m->Nq = NQ; m->Ng = NG; m->Nf = NF;
+    m->K = K;
+    m->p = *p;
+    m->prec = p->prec;
+    m->rsize = (p->prec == DG_FP64_DEBUG) ? 8 : 4;
+    m->s0 = std::isnan(p->s0) ? std::log10(1.0 / std::pow((double)N, 4)) : p->s0;
+    m->perm.reserve(K);
+    for (int64_t k = 0; k < K; ++k)
+        if (!curved[k]) m->perm.push_back(k);
+    m->Kaff = (long long)m->perm.size();
+    for (int64_t k = 0; k < K; ++k)
+        if (curved[k]) m->perm.push_back(k);
+    m->Kc = K - m->Kaff;
+    std::vector<long long> iperm(K);
+    for (int64_t d = 0; d < K; ++d) iperm[m->perm[d]] = d;
+
+    // connectivity in device order
+    std::vector<int4> conn(K);
+    for (int64_t d = 0; d < K; ++d) {
+        const int64_t k = m->perm[d];
+        int nb[3], code = 0;
+        for (int f = 0; f < 3; ++f) {
+            const int b = bc[3 * k + f];
+            nb[f] = (b == DG_BC_INTERIOR) ? (int)iperm[EToE[3 * k + f]] : (int)d;
+            const int fn = (b == DG_BC_INTERIOR) ? EToF[3 * k + f] : f;
+            code |= (fn | (b << 2)) << (4 * f);
+        }
+        conn[d] = make_int4(nb[0], nb[1], nb[2], code);
+    }
+
+    // geometry (FP64)
+    std::vector<double> geoA((size_t)m->Kaff * 4);
+    for (long long d = 0; d < m->Kaff; ++d) {
+        const double* X = node_xy + (size_t)m->perm[d] * NP * 2;
+        const double xr = 0.5 * (X[2 * iv1] - X[0]), xs = 0.5 * (X[2 * iv2] - X[0]);
+        const double yr = 0.5 * (X[2 * iv1 + 1] - X[1]), ys = 0.5 * (X[2 * iv2 + 1] - X[1]);
+        if (!(xr * ys - xs * yr > 0.0)) {
+            free_mesh(m);
+            return fail(ctx, DG_EINVAL, "non-positive Jacobian at element " + std::to_string(m->perm[d]));
+        }
+        geoA[4 * d] = xr; geoA[4 * d + 1] = xs; geoA[4 * d + 2] = yr; geoA[4 * d + 3] = ys;
+    }
+    const int CS = curved_stride(N);
+    std::vector<double> geoC((size_t)m->Kc * CS);
+    {
+        std::vector<double> M((size_t)NP * NP), Mi((size_t)NP * NP);
+        const double drdt[3] = {1.0, -1.0, 0.0}, dsdt[3] = {0.0, 1.0, -1.0};
+        for (long long c = 0; c < m->Kc; ++c) {
+            const long long k = m->perm[m->Kaff + c];
+            const double* X = node_xy + (size_t)k * NP * 2;
+            double* g = geoC.data() + (size_t)c * CS;
+            std::vector<double> J(NQ);
+            for (int q = 0; q < NQ; ++q) {
+                double xr = 0, xs = 0, yr = 0, ys = 0;
+                for (int j = 0; j < NP; ++j) {
+                    xr += R->Dr[(size_t)q * NP + j] * X[2 * j];
+                    xs += R->Ds[(size_t)q * NP + j] * X[2 * j];
+                    yr += R->Dr[(size_t)q * NP + j] * X[2 * j + 1];
+                    ys += R->Ds[(size_t)q * NP + j] * X[2 * j + 1];
+                }
+                J[q] = xr * ys - xs * yr;
+                if (!(J[q] > 0.0)) {
+                    free_mesh(m);
+                    return fail(ctx, DG_EINVAL, "non-positive Jacobian at a cubature node of element " +
+                                                    std::to_string(k));
+                }
+                g[q] = ys; g[NQ + q] = -xs; g[2 * NQ + q] = -yr; g[3 * NQ + q] = xr; g[4 * NQ + q] = J[q];
+            }
+            for (int fg = 0; fg < NF; ++fg) {
+                const int f = fg / NG;
+                double xr = 0, xs = 0, yr = 0, ys = 0;
+                for (int j = 0; j < NP; ++j) {
+                    xr += R->Drg[(size_t)fg * NP + j] * X[2 * j];
+                    xs += R->Dsg[(size_t)fg * NP + j] * X[2 * j];
+                    yr += R->Drg[(size_t)fg * NP + j] * X[2 * j + 1];
+                    ys += R->Dsg[(size_t)fg * NP + j] * X[2 * j + 1];
+                }
+                const double xt = xr * drdt[f] + xs * dsdt[f], yt = yr * drdt[f] + ys * dsdt[f];
+                const double sJ = std::sqrt(xt * xt + yt * yt);
+                g[5 * NQ + fg] = yt / sJ;
+                g[5 * NQ + NF + fg] = -xt / sJ;
+                g[5 * NQ + 2 * NF + fg] = sJ;
+            }
+            for (int i = 0; i < NP; ++i)
+                for (int j = 0; j < NP; ++j) {
+                    double v = 0;
+                    for (int q = 0; q < NQ; ++q)
+                        v += R->Icub[(size_t)q * NP + i] * R->wq[q] * J[q] * R->Icub[(size_t)q * NP + j];
+                    M[(size_t)i * NP + j] = v;
+                }
+            if (!spd_inverse(M.data(), Mi.data(), NP)) {
+                free_mesh(m);
+                return fail(ctx, DG_EINVAL, "curved mass matrix not SPD at element " + std::to_string(k));
+            }
+            for (int j = 0; j < NP; ++j)
+                for (int i = 0; i < NP; ++i) g[5 * NQ + 3 * NF + j * NP + i] = Mi[(size_t)i * NP + j];
+        }
+    }
+
+    // device buffers
+    cudaSetDevice(ctx->device);
+    const size_t rs = m->rsize, nstate = (size_t)K * 4 * NP;
+    int e;
+    for (int b = 0; b < 3; ++b)
+        if ((e = alloc(ctx, *m, &m->U[b], nstate * rs))) { free_mesh(m); return e; }
+    if ((e = alloc(ctx, *m, &m->rhs, nstate * rs))) { free_mesh(m); return e; }
+    if ((e = alloc(ctx, *m, (void**)&m->conn, (size_t)K * sizeof(int4)))) { free_mesh(m); return e; }
+    if ((e = alloc(ctx, *m, &m->geoA, geoA.size() * rs))) { free_mesh(m); return e; }
+    if ((e = alloc(ctx, *m, &m->geoC, geoC.size() * rs))) { free_mesh(m); return e; }
+    if ((e = alloc(ctx, *m, (void**)&m->dperm, (size_t)K * sizeof(long long)))) { free_mesh(m); return e; }
+    if ((e = alloc(ctx, *m, (void**)&m->diperm, (size_t)K * sizeof(long long)))) { free_mesh(m); return e; }
+    if ((e = alloc(ctx, *m, (void**)&m->red, (size_t)(residual_blocks() * 8 + 8) * sizeof(double)))) {
+        free_mesh(m);
+        return e;
+    }
+    if (p->av_on) {
+        if ((e = alloc(ctx, *m, &m->eps, (size_t)K * rs))) { free_mesh(m); return e; }
+        if ((e = alloc(ctx, *m, &m->q, (size_t)K * 8 * NP * rs))) { free_mesh(m); return e; }
+    }
+    // operators (shared per context, degree and precision)
+    const int okey = N * 16 + (m->rsize == 8 ? 1 : 0);
+    auto oit = ctx->ops.find(okey);
+    if (oit == ctx->ops.end()) {
+        const std::vector<double> packed = pack_ops(*R);
+        void* d = nullptr;
+        if (cudaMalloc(&d, packed.size() * rs) != cudaSuccess) {
+            cudaGetLastError();
+            free_mesh(m);
+            return fail(ctx, DG_ENOMEM, "operator table allocation failed");
+        }
+        cudaError_t ce;
+        if (rs == 8)
+            ce = cudaMemcpy(d, packed.data(), packed.size() * 8, cudaMemcpyHostToDevice);
+        else {
+            const auto f = to_real<float>(packed);
+            ce = cudaMemcpy(d, f.data(), f.size() * 4, cudaMemcpyHostToDevice);
+        }
+        if (ce != cudaSuccess) {
+            cudaFree(d);
+            free_mesh(m);
+            return fail(ctx, DG_ECUDA, "operator table copy failed");
+        }
+        ctx->ops[okey] = d;
+        const int pe = (rs == 8) ? dispatch_prepare<double>(N) : dispatch_prepare<float>(N);
+        if (pe) {
+            free_mesh(m);
+            return fail(ctx, DG_ECUDA, std::string("kernel attribute set-up failed: ") +
+                                           cudaGetErrorString((cudaError_t)pe));
+        }
+        oit = ctx->ops.find(okey);
+    }
+    m->ops = oit->second;
+
+    auto upload = [&](void* dst, const std::vector<double>& src) -> cudaError_t {
+        if (src.empty()) return cudaSuccess;
+        if (rs == 8) return cudaMemcpy(dst, src.data(), src.size() * 8, cudaMemcpyHostToDevice);
+        const auto f = to_real<float>(src);
+        return cudaMemcpy(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice);
+    };
+    if (upload(m->geoA, geoA) != cudaSuccess || upload(m->geoC, geoC) != cudaSuccess ||
+        cudaMemcpy(m->conn, conn.data(), (size_t)K * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->dperm, m->perm.data(), (size_t)K * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->diperm, iperm.data(), (size_t)K * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(m->U[0], 0, nstate * rs) != cudaSuccess) {
+        free_mesh(m);
+        return fail(ctx, DG_ECUDA, "mesh upload copy failed");
+    }
+    if (p->av_on && (cudaMemset(m->eps, 0, (size_t)K * rs) != cudaSuccess ||
+                     cudaMemset(m->q, 0, (size_t)K * 8 * NP * rs) != cudaSuccess)) {
+        free_mesh(m);
+        return fail(ctx, DG_ECUDA, "mesh upload memset failed");
+    }
+    const dg_mesh h = ctx->next_id++;
+    ctx->meshes[h] = m;
+    *out = h;
+    return DG_OK;
+}
+
+int dg_mesh_free(dg_ctx* ctx, dg_mesh h) {
+    if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_mesh(m);
+    ctx->meshes.erase(h);
+    reset_batch(ctx);
+    return DG_OK;
+}
+
+int dg_mesh_bytes(dg_ctx* ctx, dg_mesh h, int64_t* out) {
+    if (!ctx || !out) return fail(ctx, DG_EINVAL, "NULL argument");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    *out = (int64_t)m->bytes;
+    return DG_OK;
+}
+
+// host FP64 canonical <-> device order in the mesh precision
+static int put_host(dg_ctx* ctx, MeshData* m, const double* U, void* dst) {
+    const size_t row = 4 * (size_t)m->Np, n = (size_t)m->K * row;
+    cudaError_t ce;
+    if (m->rsize == 8) {
+        std::vector<double> buf(n);
+        for (long long d = 0; d < m->K; ++d) std::memcpy(&buf[d * row], U + m->perm[d] * row, row * 8);
+        ce = cudaMemcpyAsync(dst, buf.data(), n * 8, cudaMemcpyHostToDevice, ctx->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+    } else {
+        std::vector<float> buf(n);
+        for (long long d = 0; d < m->K; ++d)
+            for (size_t i = 0; i < row; ++i) buf[d * row + i] = (float)U[m->perm[d] * row + i];
+        ce = cudaMemcpyAsync(dst, buf.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+    }
+    if (ce != cudaSuccess) return fail(ctx, DG_ECUDA, std::string("state upload: ") + cudaGetErrorString(ce));
+    return DG_OK;
+}
+
+static int get_host(dg_ctx* ctx, MeshData* m, const void* src, double* U) {
+    const size_t row = 4 * (size_t)m->Np, n = (size_t)m->K * row;
+    cudaError_t ce;
+    if (m->rsize == 8) {
+        std::vector<double> buf(n);
+        ce = cudaMemcpyAsync(buf.data(), src, n * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+        if (ce == cudaSuccess)
+            for (long long d = 0; d < m->K; ++d) std::memcpy(U + m->perm[d] * row, &buf[d * row], row * 8);
+    } else {
+        std::vector<float> buf(n);
+        ce = cudaMemcpyAsync(buf.data(), src, n * 4, cudaMemcpyDeviceToHost, ctx->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+        if (ce == cudaSuccess)
+            for (long long d = 0; d < m->K; ++d)
+                for (size_t i = 0; i < row; ++i) U[m->perm[d] * row + i] = buf[d * row + i];
+    }
+    if (ce != cudaSuccess) return fail(ctx, DG_ECUDA, std::string("state download: ") + cudaGetErrorString(ce));
+    return DG_OK;
+}
+
+int dg_set_state(dg_ctx* ctx, dg_mesh h, const double* U) {
+    if (!ctx || !U) return fail(ctx, DG_EINVAL, "NULL argument");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    cudaSetDevice(ctx->device);
+    return put_host(ctx, m, U, m->U[0]);
+}
+
+int dg_get_state(dg_ctx* ctx, dg_mesh h, double* U_out) {
+    if (!ctx || !U_out) return fail(ctx, DG_EINVAL, "NULL argument");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    cudaSetDevice(ctx->device);
+    return get_host(ctx, m, m->U[0], U_out);
+}
+
+int dg_set_state_device(dg_ctx* ctx, dg_mesh h, const float* U_dev) {
+    if (!ctx || !U_dev) return fail(ctx, DG_EINVAL, "NULL argument");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    if (m->rsize != 4) return fail(ctx, DG_EINVAL, "device state I/O needs an FP32 precision mode");
+    cudaSetDevice(ctx->device);
+    // device row d <- canonical row perm[d]
+    int e = launch_permute<float>(U_dev, (float*)m->U[0], m->dperm, m->K, 4 * m->Np, ctx->stream);
+    if (e) return fail(ctx, DG_ECUDA, cudaGetErrorString((cudaError_t)e));
+    return DG_OK;
+}
+
+int dg_get_state_device(dg_ctx* ctx, dg_mesh h, float* U_dev_out) {
+    if (!ctx || !U_dev_out) return fail(ctx, DG_EINVAL, "NULL argument");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    if (m->rsize != 4) return fail(ctx, DG_EINVAL, "device state I/O needs an FP32 precision mode");
+    cudaSetDevice(ctx->device);
+    // canonical row k <- device row iperm[k]
+    int e = launch_permute<float>((const float*)m->U[0], U_dev_out, m->diperm, m->K, 4 * m->Np, ctx->stream);
+    if (e) return fail(ctx, DG_ECUDA, cudaGetErrorString((cudaError_t)e));
+    return DG_OK;
+}
+
+int dg_eval_rhs(dg_ctx* ctx, dg_mesh h, double* rhs_out) {
+    if (!ctx || !rhs_out) return fail(ctx, DG_EINVAL, "NULL argument");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    cudaSetDevice(ctx->device);
+    int e = enqueue_stage(*m, m->U[0], nullptr, m->rhs, 0.0, 0.0, 0.0, 1, ctx->stream);
+    if (e) return fail(ctx, DG_ECUDA, std::string("stage launch: ") + cudaGetErrorString((cudaError_t)e));
+    return get_host(ctx, m, m->rhs, rhs_out);
+}
+
+int dg_step(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
+    if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    if (nsteps < 0 || !std::isfinite(dt)) return fail(ctx, DG_EINVAL, "bad dt or nsteps");
+    if (nsteps == 0) return DG_OK;
+    cudaSetDevice(ctx->device);
+    if (!m->gexec || m->gdt != dt) {
+        if (m->gexec) { cudaGraphExecDestroy(m->gexec); m->gexec = nullptr; }
+        if (m->graph) { cudaGraphDestroy(m->graph); m->graph = nullptr; }
+        CUDA_OK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        const int e = enqueue_step(*m, dt, ctx->stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+        if (e || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(ctx, DG_ECUDA, "graph capture of the RK step failed");
+        }
+        m->graph = g;
+        CUDA_OK(ctx, cudaGraphInstantiate(&m->gexec, g, 0));
+        m->gdt = dt;
+    }
+    for (int s = 0; s < nsteps; ++s) CUDA_OK(ctx, cudaGraphLaunch(m->gexec, ctx->stream));
+    return DG_OK;
+}
+
+int dg_residual(dg_ctx* ctx, dg_mesh h, double out_linf[4], double out_l2[4]) {
+    if (!ctx || !out_linf || !out_l2) return fail(ctx, DG_EINVAL, "NULL argument");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    cudaSetDevice(ctx->device);
+    int e = enqueue_stage(*m, m->U[0], nullptr, m->rhs, 0.0, 0.0, 0.0, 1, ctx->stream);
+    if (e) return fail(ctx, DG_ECUDA, "stage launch failed");
+    double* out8 = m->red + residual_blocks() * 8;
+    if (m->rsize == 8)
+        e = launch_residual<double>((const double*)m->rhs, 0, m->K, m->Np, m->red, out8, ctx->stream);
+    else
+        e = launch_residual<float>((const float*)m->rhs, 0, m->K, m->Np, m->red, out8, ctx->stream);
+    if (e) return fail(ctx, DG_ECUDA, "residual launch failed");
+    double h8[8];
+    CUDA_OK(ctx, cudaMemcpyAsync(h8, out8, sizeof(h8), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
+    bool finite = true;
+    for (int v = 0; v < 4; ++v) {
+        out_linf[v] = h8[v];
+        out_l2[v] = h8[4 + v];
+        finite = finite && std::isfinite(h8[v]) && std::isfinite(h8[4 + v]);
+    }
+    return finite ? DG_OK : fail(ctx, DG_ENONFINITE, "non-finite residual norm");
+}
+
+int dg_sync(dg_ctx* ctx, double timeout_s) {
+    if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    cudaSetDevice(ctx->device);
+    if (timeout_s <= 0) {
+        CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
+        return DG_OK;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    while (true) {
+        const cudaError_t q = cudaStreamQuery(ctx->stream);
+        if (q == cudaSuccess) return DG_OK;
+        if (q != cudaErrorNotReady) return fail(ctx, DG_ECUDA, cudaGetErrorString(q));
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_s) return fail(ctx, DG_ETIMEOUT, "work still in flight after the timeout");
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+}
+
+const char* dg_last_error(dg_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,21 @@
+// Work list of the persistent batched stage kernel.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace dgc {
+
+struct BatchItem {
+    int mesh;        // index into the per-stage argument array
+    int N;           // degree of that mesh
+    long long e0;    // first element (device order)
+    int ne;          // elements in the tile
+    int curved;      // tile of curved elements
+};
+
+int batch_tile_e(int N, int rsize);
+template <typename Real> int batch_grid(int device, int ctas_per_sm);
+template <typename Real>
+int launch_batch_stage(const void* args, const BatchItem* items, int nitems, int* counter, int grid,
+                       cudaStream_t st);
+
+}  // namespace dgc

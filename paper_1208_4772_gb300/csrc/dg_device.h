@@ -1,0 +1,92 @@
+// Device-side data layout and kernel launch interface shared by the host
+// library (dg_api.cpp) and the per-degree kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dgc {
+
+constexpr int THREADS = 256;
+
+__host__ __device__ constexpr int np_of(int N) { return (N + 1) * (N + 2) / 2; }
+__host__ __device__ constexpr int q_of(int N) { return (3 * N + 2) / 2; }
+__host__ __device__ constexpr int nq_of(int N) { return q_of(N) * q_of(N); }
+__host__ __device__ constexpr int ng_of(int N) { return q_of(N); }
+__host__ __device__ constexpr int nf_of(int N) { return 3 * q_of(N); }
+
+// Packed operator table of degree N (offsets in elements of the real type).
+// All tables are stored transposed so that the thread index runs along the
+// contiguous dimension in the kernels.
+struct OpsLayout {
+    int icub, mrt, mst, drt, dst, igt, mlt, lt, qrt, qst, vinvt, itopt, w, total;
+};
+__host__ __device__ constexpr OpsLayout ops_layout(int N) {
+    const int NP = np_of(N), NQ = nq_of(N), NF = nf_of(N);
+    OpsLayout o{};
+    o.icub = 0;                    // IcubT [NP][NQ]
+    o.mrt = o.icub + NP * NQ;      // (Mref^-1 D_r^T W)^T [NQ][NP]
+    o.mst = o.mrt + NQ * NP;
+    o.drt = o.mst + NQ * NP;       // (D_r^T W)^T [NQ][NP]
+    o.dst = o.drt + NQ * NP;
+    o.igt = o.dst + NQ * NP;       // I_g^T [NP][NF]
+    o.mlt = o.igt + NP * NF;       // (Mref^-1 Lift)^T [NF][NP]
+    o.lt = o.mlt + NF * NP;        // Lift^T [NF][NP]
+    o.qrt = o.lt + NF * NP;        // (Mref^-1 D_r^T W I_cub)^T [NP][NP]
+    o.qst = o.qrt + NP * NP;
+    o.vinvt = o.qst + NP * NP;     // (V^-1)^T [NP][NP]
+    o.itopt = o.vinvt + NP * NP;   // Itop^T [NP][NQ]
+    o.w = o.itopt + NP * NQ;       // cubature weights [NQ]
+    o.total = o.w + NQ;
+    return o;
+}
+
+// Curved-element geometry record (per element, stride curved_stride):
+//   [c * NQ + qn]          c = 0..4: J r_x, J r_y, J s_x, J s_y, J at cubature nodes
+//   [5 NQ + c * NF + fg]   c = 0..2: n_x, n_y, sJ at face points
+//   [5 NQ + 3 NF + j NP + i]  (M_k^-1)^T
+__host__ __device__ constexpr int curved_stride(int N) {
+    return 5 * nq_of(N) + 3 * nf_of(N) + np_of(N) * np_of(N);
+}
+
+// Connectivity word per element: int4 {nb0, nb1, nb2, code}, with
+// code bits [4f, 4f+1] = neighbour face of face f, [4f+2, 4f+3] = bc of face f.
+__host__ __device__ constexpr int code_face(int code, int f) { return (code >> (4 * f)) & 3; }
+__host__ __device__ constexpr int code_bc(int code, int f) { return (code >> (4 * f + 2)) & 3; }
+
+template <typename Real>
+struct StageArgs {
+    const Real* Us;     // stage input [K][4][NP] (device order)
+    const Real* Un;     // U^n (read when a != 0)
+    Real* Uout;         // output
+    Real a, b, dt;      // Uout = a Un + b (Us + dt L(Us));  rhs_only: Uout = L(Us)
+    int rhs_only;
+    const int4* conn;   // [K]
+    const Real* geoA;   // [K_aff][4]: x_r, x_s, y_r, y_s
+    const Real* geoC;   // [Kc][curved_stride]
+    const Real* ops;    // packed operator table
+    const Real* eps;    // [K] viscosity (AV)
+    const Real* q;      // [K][2][4][NP] sqrt(eps) grad U (AV)
+    long long K, Kaff;
+    Real gamma;
+    Real uinf[4];
+    // sensor parameters (AV)
+    double s0, kappa, eps0;
+};
+
+// Per-degree launchers (kernels_n<N>.cu).  Return cudaError_t as int.
+template <int N, typename Real> int launch_stage(const StageArgs<Real>& a, int av, cudaStream_t st);
+template <int N, typename Real> int launch_sensor(const StageArgs<Real>& a, Real* eps_out, cudaStream_t st);
+template <int N, typename Real> int launch_grad(const StageArgs<Real>& a, Real* q_out, cudaStream_t st);
+// Set the dynamic shared-memory limits of the degree-N kernels (call once
+// per device before the first launch or stream capture).
+template <int N, typename Real> int prepare_kernels();
+
+// Generic kernels (kernels_common.cu)
+template <typename Real>
+int launch_residual(const Real* L, long long n_per_var_block, long long K, int NP, double* partial,
+                    double* out8, cudaStream_t st);
+template <typename Real>
+int launch_permute(const Real* src, Real* dst, const long long* map, long long K, int rowlen, cudaStream_t st);
+int residual_blocks();
+
+}  // namespace dgc

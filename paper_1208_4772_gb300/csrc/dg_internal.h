@@ -1,0 +1,59 @@
+// Host-side structures of the library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "dgcurved.h"
+
+namespace dgc {
+
+struct MeshData {
+    int N = 0, Np = 0, Nq = 0, Ng = 0, Nf = 0;
+    long long K = 0, Kaff = 0, Kc = 0;
+    dg_params p{};
+    int prec = 0;
+    size_t rsize = 4;             // bytes of the device real type
+    double s0 = 0.0;              // sensor offset actually used
+    std::vector<long long> perm;  // device element d is caller element perm[d]
+    void* U[3] = {nullptr, nullptr, nullptr};  // U^n, stage buffers
+    void* rhs = nullptr;          // L(U) scratch
+    void* eps = nullptr;          // [K] viscosity (AV)
+    void* q = nullptr;            // [K][2][4][Np] (AV)
+    void* geoA = nullptr;         // [Kaff][4]
+    void* geoC = nullptr;         // [Kc][curved_stride]
+    void* ops = nullptr;          // shared operator table (owned by the context)
+    int4* conn = nullptr;         // [K]
+    long long* dperm = nullptr;   // device copy of perm
+    long long* diperm = nullptr;  // inverse permutation
+    double* red = nullptr;        // residual partials + 8 results
+    size_t bytes = 0;
+    std::vector<void*> allocs;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    double gdt = 0.0;
+};
+
+int enqueue_stage(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
+                  int rhs_only, cudaStream_t st);
+int enqueue_step(const MeshData& m, double dt, cudaStream_t st);
+
+}  // namespace dgc
+
+struct dg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::map<int, dgc::MeshData*> meshes;
+    int next_id = 1;
+    std::map<int, void*> ops;         // operator tables by (N, precision)
+    std::vector<void*> batch_bufs;    // work lists of the batched path
+    // batched-step graph cache
+    std::vector<int> batch_key_meshes;
+    std::vector<double> batch_key_dts;
+    cudaGraph_t batch_graph = nullptr;
+    cudaGraphExec_t batch_gexec = nullptr;
+    std::string err;
+};

@@ -1,0 +1,117 @@
+// Degree-independent kernels: FP64 residual reduction and element
+// permutation between the caller's order and the device order.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "dg_device.h"
+
+namespace dgc {
+
+namespace {
+
+constexpr int RED_THREADS = 256;
+
+// Per-variable max |L| and sum L^2 of L[K][4][NP] in FP64.  Each block
+// writes 8 partials; the order of accumulation is fixed by the launch shape,
+// so the result is deterministic.
+template <typename Real>
+__global__ void __launch_bounds__(RED_THREADS) residual_partial(const Real* L, long long total, int NP,
+                                                                 double* partial) {
+    double mx[4] = {0, 0, 0, 0}, ss[4] = {0, 0, 0, 0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += stride) {
+        const int v = (int)((n / NP) & 3);
+        const double x = (double)L[n];
+        const double ax = fabs(x);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            if (w == v) {
+                mx[w] = (ax > mx[w] || ax != ax) ? ax : mx[w];
+                ss[w] += x * x;
+            }
+        }
+    }
+    __shared__ double sm[8][RED_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        double a = mx[w], b = ss[w];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ao = __shfl_xor_sync(0xffffffffu, a, o);
+            a = (ao > a || ao != ao) ? ao : a;
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) {
+            sm[w][warp] = a;
+            sm[4 + w][warp] = b;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int w = threadIdx.x;
+        double acc = 0.0;
+        for (int i = 0; i < RED_THREADS / 32; ++i) {
+            const double x = sm[w][i];
+            if (w < 4)
+                acc = (x > acc || x != x) ? x : acc;
+            else
+                acc += x;
+        }
+        partial[(long long)blockIdx.x * 8 + w] = acc;
+    }
+}
+
+__global__ void residual_final(const double* partial, int nblocks, double* out8) {
+    if (threadIdx.x < 8) {
+        const int w = threadIdx.x;
+        double acc = 0.0;
+        for (int b = 0; b < nblocks; ++b) {
+            const double x = partial[(long long)b * 8 + w];
+            if (w < 4)
+                acc = (x > acc || x != x) ? x : acc;
+            else
+                acc += x;
+        }
+        out8[w] = (w < 4) ? acc : sqrt(acc);
+    }
+}
+
+template <typename Real>
+__global__ void permute_rows(const Real* src, Real* dst, const long long* map, long long K, int rowlen) {
+    const long long total = K * rowlen;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += stride) {
+        const long long row = n / rowlen;
+        const int c = (int)(n - row * rowlen);
+        dst[n] = src[map[row] * rowlen + c];
+    }
+}
+
+}  // namespace
+
+int residual_blocks() { return 304; }
+
+template <typename Real>
+int launch_residual(const Real* L, long long /*unused*/, long long K, int NP, double* partial, double* out8,
+                    cudaStream_t st) {
+    const int nb = residual_blocks();
+    residual_partial<Real><<<nb, RED_THREADS, 0, st>>>(L, K * 4 * NP, NP, partial);
+    residual_final<<<1, 32, 0, st>>>(partial, nb, out8);
+    return (int)cudaGetLastError();
+}
+
+template <typename Real>
+int launch_permute(const Real* src, Real* dst, const long long* map, long long K, int rowlen, cudaStream_t st) {
+    if (K == 0) return 0;
+    const long long total = K * rowlen;
+    const unsigned grid = (unsigned)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
+    permute_rows<Real><<<grid, 256, 0, st>>>(src, dst, map, K, rowlen);
+    return (int)cudaGetLastError();
+}
+
+template int launch_residual<float>(const float*, long long, long long, int, double*, double*, cudaStream_t);
+template int launch_residual<double>(const double*, long long, long long, int, double*, double*, cudaStream_t);
+template int launch_permute<float>(const float*, float*, const long long*, long long, int, cudaStream_t);
+template int launch_permute<double>(const double*, double*, const long long*, long long, int, cudaStream_t);
+
+}  // namespace dgc

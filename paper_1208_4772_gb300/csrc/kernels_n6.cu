@@ -1,0 +1,15 @@
+// Degree-6 instantiations of the CUDA-core stage, sensor and gradient kernels.
+#include "kernels.cuh"
+
+namespace dgc {
+template int launch_stage<6, float>(const StageArgs<float>&, int, cudaStream_t);
+template int launch_stage<6, double>(const StageArgs<double>&, int, cudaStream_t);
+template int launch_sensor<6, float>(const StageArgs<float>&, float*, cudaStream_t);
+template int launch_sensor<6, double>(const StageArgs<double>&, double*, cudaStream_t);
+template int launch_grad<6, float>(const StageArgs<float>&, float*, cudaStream_t);
+template int launch_grad<6, double>(const StageArgs<double>&, double*, cudaStream_t);
+}  // namespace dgc
+namespace dgc {
+template int prepare_kernels<6, float>();
+template int prepare_kernels<6, double>();
+}  // namespace dgc

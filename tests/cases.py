@@ -1,0 +1,44 @@
+"""Shared seeded test cases: a mesh, its node coordinates on the library's
+reference nodes, parameters, and a perturbed state.  Inputs only."""
+import numpy as np
+
+from paper_1208_4772_gb300.inputs import curving, meshes, states
+
+
+def rel_l2_per_var(a, b):
+    """||a - b|| / ||b|| per conserved variable (arrays [K, 4, Np])."""
+    return np.linalg.norm((a - b).transpose(1, 0, 2).reshape(4, -1), axis=1) / \
+        np.linalg.norm(b.transpose(1, 0, 2).reshape(4, -1), axis=1)
+
+
+def make_case(kind, N, r, s, seed=0, av=False, size="small", perturb=0.02):
+    """Returns dict(mesh, xy, curved, u_inf, U, av, name)."""
+    rng = np.random.default_rng(seed)
+    if kind == "vortex":
+        n = {"tiny": 3, "small": 6, "config": 16}.get(size, size) if isinstance(size, str) else size
+        m = meshes.periodic_square(n, length=10.0, seed=1000 + seed)
+        xy = meshes.straight_nodes(m.verts, r, s)
+        curved = np.zeros(m.K, bool)
+        ui = states.freestream(0.5, 45.0)
+        U = states.vortex_state(xy, period=(10.0, 10.0))
+    elif kind in ("naca", "cyl"):
+        if kind == "naca":
+            nt, nr = {"tiny": (12, 2), "small": (40, 5), "config": (300, 100)}[size]
+            m = meshes.naca_omesh(n_t=nt, n_r=nr, seed=1001 + seed)
+            ui = states.freestream(0.8, 1.25)
+        else:
+            nt, nr = {"tiny": (12, 2), "small": (32, 5), "config": (500, 250)}[size]
+            m = meshes.cylinder_channel(n_t=nt, n_r=nr, seed=1002 + seed)
+            ui = states.freestream(0.38, 0.0)
+        xy, curved = curving.curve_mesh(m, N, r, s)
+        x = xy[..., 0]
+        y = xy[..., 1]
+        U = states.uniform_state(m.K, len(r), ui)
+        # smooth perturbation plus a little noise so that every term is exercised
+        U[:, 0] *= 1.0 + perturb * np.sin(1.3 * x) * np.cos(0.7 * y)
+        U[:, 3] *= 1.0 + perturb * np.cos(0.9 * x + 0.4 * y)
+        U[:, 1] += perturb * np.sin(y)
+        U *= 1.0 + 0.1 * perturb * rng.standard_normal(U.shape)
+    else:
+        raise ValueError(kind)
+    return dict(mesh=m, xy=xy, curved=curved, u_inf=ui, U=U, av=av, name=kind, N=N)

@@ -1,0 +1,73 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, exports
+every function include/dgcurved.h declares, its own reference nodes equal
+the oracle's, and calls fail with status codes rather than crashing."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+from oracle.operators import ReferenceElement
+from oracle.quadrature import default_q
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    __graft_entry__.build()
+    from paper_1208_4772_gb300 import binding
+    binding.load()
+    return binding
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "dgcurved.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(B):
+    lib = B.load()
+    names = declared_functions()
+    assert len(names) >= 17
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_names_match_abi(B):
+    for n in declared_functions():
+        assert callable(getattr(B, n)), n
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6])
+def test_reference_nodes_match_oracle(B, N):
+    r, s = B.dg_reference_nodes(N)
+    ref = ReferenceElement(N)
+    assert np.abs(r - ref.r).max() < 1e-14
+    assert np.abs(s - ref.s).max() < 1e-14
+    Np, Nq, Ng, q = B.dg_sizes(N)
+    assert (Np, Nq, Ng, q) == (ref.Np, ref.Nq, ref.Ng, default_q(N))
+
+
+def test_errors_are_status_codes(B):
+    with pytest.raises(B.DgError) as e:
+        B.dg_reference_nodes(0)
+    assert e.value.status == B.DG_EINVAL
+    with pytest.raises(B.DgError):
+        B.dg_sizes(9)
+    # no GPU here, or a bad device index on a GPU machine: EINVAL, not a crash
+    with pytest.raises(B.DgError) as e:
+        B.dg_create(10_000)
+    assert e.value.status == B.DG_EINVAL
+    assert "device" in B.dg_last_error(None)
+    lib = B.load()
+    assert lib.dg_destroy(None) == 0
+    assert lib.dg_sync(None, 0.0) == B.DG_EINVAL
+
+
+def test_params_struct_layout(B):
+    import ctypes
+    assert ctypes.sizeof(B.dg_params) == 80
+    assert B.dg_params.u_inf.offset == 40 and B.dg_params.prec.offset == 72
