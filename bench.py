@@ -1,0 +1,411 @@
+#!/usr/bin/env python3
+"""Benchmark of the curved-element RKDG hot path on GB300.
+
+Metric: RK-stage DOF-updates/s = K * N_p * 4 * (RK stages) / device time.
+Default workload: transonic flow past a NACA 0012 profile (Mach 0.8, angle
+of attack 1.25 deg) on a seeded O-mesh of 60,000 triangles in a radius-20
+farfield, wall elements curved to degree N = 4 by the linear-elasticity
+set-up, Persson-Peraire artificial viscosity on, FP32 state, SSP-RK3.
+
+One "step" = one SSP-RK3 step = 3 right-hand-side evaluations with the stage
+update fused in (sensor, gradient and stage kernels per stage), replayed from
+the library's captured CUDA graph.  Each timed step is bracketed by CUDA
+events on the library's stream; L2 is flushed (512 MiB memset) before every
+timed step, outside the events.  Per-kernel device times come from event
+nodes inside the step graph, read after every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (launched by torch.distributed.run) every rank runs an
+independent replica of the workload (the method is not sharded here);
+value = all ranks' DOF-updates / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RK-stage DOF-updates/s"
+UNIT = "DOF-updates/s"
+
+WORKLOADS = {
+    "naca0012_m0.8_n4_av": dict(kind="naca", N=4, n_t=300, n_r=100, mach=0.8, aoa=1.25, av=True,
+                                describe="NACA 0012, Mach 0.8, AoA 1.25 deg, 60k curved-wall triangles, "
+                                         "N=4, artificial viscosity on"),
+    "cylinder_m0.38_n6": dict(kind="cyl", N=6, n_t=500, n_r=250, mach=0.38, aoa=0.0, av=False,
+                              describe="cylinder in a channel, Mach 0.38, 250k triangles, N=6"),
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="naca0012_m0.8_n4_av", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="fp32")
+    ap.add_argument("--compare-prec", default="", help="also time this precision (e.g. fp32)")
+    ap.add_argument("--flush-mb", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", default="", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-budget-s", type=float, default=20.0, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ workload
+def make_workload(name, r, s):
+    """Seeded mesh, curved nodes, initial state and time step (inputs only)."""
+    from paper_1208_4772_gb300.inputs import curving, meshes, states
+    w = WORKLOADS[name]
+    if w["kind"] == "naca":
+        mesh = meshes.naca_omesh(n_t=w["n_t"], n_r=w["n_r"], seed=1001)
+    else:
+        mesh = meshes.cylinder_channel(n_t=w["n_t"], n_r=w["n_r"], seed=1002)
+    xy, curved = curving.curve_mesh(mesh, w["N"], r, s)
+    ui = states.freestream(w["mach"], w["aoa"])
+    U0 = states.uniform_state(mesh.K, len(r), ui)
+    dt = states.time_step(mesh.verts, U0, w["N"], cfl=0.3, eps0=0.3 if w["av"] else None)
+    return dict(mesh=mesh, xy=xy, curved=curved, u_inf=ui, U0=U0, dt=dt, **w)
+
+
+def stage_kernel_bytes(K, Kc, N, av):
+    """Algorithmic HBM bytes of one stage-kernel launch, averaged over the
+    three SSP-RK3 stages: read U_s, read U^n (stages 2 and 3), write U_out
+    (4 N_p FP32 each), affine geometry 16 B + connectivity 16 B per element,
+    curved elements' factor record, and with viscosity q (8 N_p FP32) and
+    eps (4 B).  Neighbour traces are L2 hits and count 0."""
+    q = (3 * N + 2) // 2
+    Np, Nq, Nf = (N + 1) * (N + 2) // 2, q * q, 3 * q
+    state = 4 * Np * 4
+    b = K * (state * (1 + 2.0 / 3.0 + 1) + 16) + (K - Kc) * 16 + Kc * (5 * Nq + 3 * Nf + Np * Np) * 4
+    if av:
+        b += K * (8 * Np * 4 + 4)
+    return b
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-i", str(self.device), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_sample(name, budget_s):
+    """Time the FP64 oracle on the workload (fresh single-thread process)."""
+    import numpy as np
+    from oracle.dg import Oracle
+    from oracle.operators import ReferenceElement
+    ref = ReferenceElement(WORKLOADS[name]["N"])
+    wl = make_workload(name, ref.r, ref.s)
+    m = wl["mesh"]
+    o = Oracle(wl["N"], m.EToE, m.EToF, m.bc, wl["xy"], u_inf=wl["u_inf"], av=wl["av"])
+    o.geometry(None)
+    U = wl["U0"]
+    t0 = time.perf_counter()
+    U = o.ssp_rk3_step(U, wl["dt"])
+    full = time.perf_counter() - t0
+    steps = 1
+    while time.perf_counter() - t0 + full < budget_s:
+        U = o.ssp_rk3_step(U, wl["dt"])
+        steps += 1
+    el = time.perf_counter() - t0
+    dof = m.K * ref.Np * 4
+    return {"value": dof * 3 * steps / el, "seconds": el,
+            "sample": "%d full SSP-RK3 step(s) (%d RHS evaluations) of the whole %d-element mesh, "
+                      "oracle geometry set-up excluded" % (steps, 3 * steps, m.K)}
+
+
+def run_cpu_baseline(name, budget_s):
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", name,
+                        "--cpu-budget-s", str(budget_s)], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"error": r.stderr[-500:]}
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": out["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": out["sample"]}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"          # before numpy loads: the oracle runs on one core
+    import numpy as np
+    from oracle.dg import Oracle
+    from oracle.operators import ReferenceElement
+    wl_def = WORKLOADS[args.workload]
+    ref = ReferenceElement(wl_def["N"])
+    wl = make_workload(args.workload, ref.r, ref.s)
+    m = wl["mesh"]
+    o = Oracle(wl["N"], m.EToE, m.EToF, m.bc, wl["xy"], u_inf=wl["u_inf"], av=wl["av"])
+    # each step: one SSP-RK3 step (3 RHS evaluations) on a fixed sample of
+    # elements, sized so that warm-up + timed steps take about 150 s
+    t0 = time.perf_counter()
+    probe = np.arange(0, m.K, max(1, m.K // 256))
+    o.rhs(wl["U0"], probe)
+    per_elt = (time.perf_counter() - t0) / len(probe)
+    per_step = 150.0 / max(1, args.steps + args.warmup)
+    S = int(max(16, min(m.K, per_step / (3 * per_elt))))
+    idx = np.linspace(0, m.K - 1, S).astype(np.int64)
+    U = wl["U0"].copy()
+
+    def step():
+        Us = U
+        for a, b in ((0.0, 1.0), (0.75, 0.25), (1 / 3, 2 / 3)):
+            L = o.rhs(Us, idx)
+            Us = Us.copy()
+            Us[idx] = a * U[idx] + b * (Us[idx] + wl["dt"] * L)
+        return Us
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = S * ref.Np * 4 * 3 * args.steps / el
+    sample = "%d of %d elements per SSP-RK3 step (3 RHS evaluations on the sample)" % (S, m.K)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(args, wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(args, wl):
+    m = wl["mesh"]
+    Np = (wl["N"] + 1) * (wl["N"] + 2) // 2
+    return {"workload": args.workload, "describe": wl["describe"], "K": int(m.K), "N": wl["N"], "Np": Np,
+            "curved_elements": int(wl["curved"].sum()), "artificial_viscosity": bool(wl["av"]),
+            "state_precision": "fp32" if args.prec != "fp64" else "fp64", "products": args.prec,
+            "time_integrator": "SSP-RK3", "dt": wl["dt"], "dof_per_stage": int(m.K * Np * 4),
+            "l2": "flushed before every timed step (%d MiB memset, outside the step events)" % args.flush_mb,
+            "parallelism": "replicas (one independent solve per GPU)"}
+
+
+# ------------------------------------------------------------------ our arm
+def timed_steps(B, ctx, h, dt, steps, stream, flush, torch):
+    """Time `steps` single-step graph replays; returns (step_ms list, summed
+    per-kind kernel ms, kernel launches)."""
+    import numpy as np
+    kt = np.zeros(3)
+    launches = 0
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        B.dg_step(ctx, h, dt, 1)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+        t = B.dg_kernel_times(ctx, h)
+        kt += t[:3]
+        launches += int(t[3])
+    return times, kt, launches
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    from paper_1208_4772_gb300 import binding as B
+    B.load()
+    N = WORKLOADS[args.workload]["N"]
+    r, s = B.dg_reference_nodes(N)
+    wl = make_workload(args.workload, r, s)
+    m = wl["mesh"]
+    Np = len(r)
+    dof_stage = m.K * Np * 4
+    stream = torch.cuda.current_stream()
+    ctx = B.dg_create(local, stream.cuda_stream)
+    flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device="cuda")
+
+    def upload(prec):
+        p = B.make_params(u_inf=wl["u_inf"], av_on=wl["av"], prec=prec)
+        h = B.dg_mesh_upload(ctx, N, m.EToE, m.EToF, m.bc, wl["xy"], p)
+        B.dg_set_state(ctx, h, wl["U0"])
+        B.dg_set_profiling(ctx, h, 1)
+        return h
+
+    h = upload(args.prec)
+    for _ in range(args.warmup):
+        flush.zero_()
+        B.dg_step(ctx, h, wl["dt"], 1)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times, kt, launches = timed_steps(B, ctx, h, wl["dt"], args.steps, stream, flush, torch)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = float(sum(times))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * dof_stage * 3 * args.steps / (total_ms / 1e3)
+    linf, l2 = B.dg_residual(ctx, h, allow_nonfinite=True)
+
+    # roofline of the dominant kernel (the fused stage kernel)
+    stage_launch_ms = kt[2] / (3 * args.steps)
+    kinds = ["sensor", "gradient", "stage"]
+    dom = int(np.argmax(kt))
+    bytes_launch = stage_kernel_bytes(m.K, int(wl["curved"].sum()), N, wl["av"])
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = 6800.0, "fallback"
+    if os.path.exists(peaks_path):
+        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+    achieved = bytes_launch / (stage_launch_ms * 1e-3) / 1e9
+    roofline = {"kernel": "stage_kernel (N=%d, AV %s)" % (N, "on" if wl["av"] else "off"), "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_src, "traffic": None,
+                "bytes_per_launch": bytes_launch, "avg_launch_ms": stage_launch_ms,
+                "dominant_kind_by_time": kinds[dom]}
+
+    extra = {}
+    if args.compare_prec and args.compare_prec != args.prec:
+        h2 = upload(args.compare_prec)
+        for _ in range(args.warmup):
+            flush.zero_()
+            B.dg_step(ctx, h2, wl["dt"], 1)
+        n2 = min(args.steps, 500)
+        t2, kt2, _ = timed_steps(B, ctx, h2, wl["dt"], n2, stream, flush, torch)
+        extra["compare"] = {"products": args.compare_prec,
+                            "value": world * dof_stage * 3 * n2 / (sum(t2) / 1e3),
+                            "ms_per_step": sum(t2) / n2}
+        B.dg_mesh_free(ctx, h2)
+
+    e2e = None
+    if not args.no_e2e:
+        B.dg_set_profiling(ctx, h, 0)
+        B.dg_step(ctx, h, wl["dt"], 1)     # capture the plain graph outside the timing
+        torch.cuda.synchronize()
+        U_host = np.ascontiguousarray(wl["U0"])
+        t0 = time.perf_counter()
+        B.dg_set_state(ctx, h, U_host)
+        B.dg_step(ctx, h, wl["dt"], args.steps)
+        U_out = B.dg_get_state(ctx, h, m.K, Np)
+        el = time.perf_counter() - t0
+        nbytes = U_host.nbytes
+        e2e = {"value": dof_stage * 3 * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": U_out.nbytes / args.steps,
+               "how": "dg_set_state(host FP64) + dg_step(%d) + dg_get_state(host FP64), wall clock" % args.steps}
+    B.dg_destroy(ctx)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(args.workload, args.cpu_budget_s)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec != "fp64" else "f64",
+                "data": "synthetic", "config": config_of(args, wl), "roofline": roofline,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches * world),
+                "clocks": clk,
+                "kernel_ms_per_step": {k: float(kt[i] / args.steps) for i, k in enumerate(kinds)},
+                "residual_linf": [float(x) for x in linf], **extra}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.cpu_sample:
+        print(json.dumps(cpu_sample(args.cpu_sample, args.cpu_budget_s)))
+        return 0
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

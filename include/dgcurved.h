@@ -157,6 +157,16 @@ int dg_residual(dg_ctx* ctx, dg_mesh m, double out_linf[4], double out_l2[4]);
  * Asynchronous. */
 int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* ms, const double* dts, int nsteps);
 
+/* Kernel timing for profiling (paper Sec. 4 reports run times of the time
+ * loop).  dg_set_profiling(ctx, m, 1) puts CUDA event-record nodes around
+ * every kernel of the step graph of mesh m (the graph is re-captured);
+ * after a dg_step has completed, dg_kernel_times writes the device time in
+ * milliseconds of the last step's kernels, summed per kind:
+ * out_ms[0] sensor, [1] gradient, [2] stage, [3] kernels launched per step.
+ * Errors: DG_EINVAL if profiling is off. */
+int dg_set_profiling(dg_ctx* ctx, dg_mesh m, int on);
+int dg_kernel_times(dg_ctx* ctx, dg_mesh m, double out_ms[4]);
+
 /* Wait for the context's stream, polling at most timeout_s seconds
  * (<= 0: wait without limit).  DG_ETIMEOUT if work is still in flight then;
  * the work itself is not cancelled. */

@@ -75,6 +75,8 @@ def load():
         "dg_residual": (I, [P, C.c_int32, dp, dp]),
         "dg_batch_step": (I, [P, I, C.POINTER(C.c_int32), dp, I]),
         "dg_sync": (I, [P, D]),
+        "dg_set_profiling": (I, [P, C.c_int32, I]),
+        "dg_kernel_times": (I, [P, C.c_int32, dp]),
         "dg_last_error": (C.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -187,6 +189,17 @@ def dg_batch_step(ctx, meshes, dts, nsteps):
 
 def dg_sync(ctx, timeout_s=0.0):
     return _check(load().dg_sync(ctx, float(timeout_s)), ctx)
+
+
+def dg_set_profiling(ctx, m, on):
+    return _check(load().dg_set_profiling(ctx, m, int(on)), ctx)
+
+
+def dg_kernel_times(ctx, m):
+    """(sensor_ms, gradient_ms, stage_ms, kernels_per_step) of the last step."""
+    out = np.zeros(4)
+    _check(load().dg_kernel_times(ctx, m, _dptr(out)), ctx)
+    return out
 
 
 def dg_last_error(ctx=None):

@@ -159,6 +159,7 @@ int alloc(dg_ctx* ctx, MeshData& m, void** p, size_t bytes) {
 
 void free_mesh(MeshData* m) {
     if (!m) return;
+    for (cudaEvent_t e : m->prof_ev) cudaEventDestroy(e);
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
     if (m->graph) cudaGraphDestroy(m->graph);
     for (void* p : m->allocs) cudaFree(p);
@@ -208,15 +209,39 @@ StageArgs<Real> make_args(const MeshData& m, const void* Us, const void* Un, voi
     return s;
 }
 
+// Event pair around one kernel when the mesh is being profiled.
+struct ProfScope {
+    const MeshData& m;
+    cudaStream_t st;
+    int idx = -1;
+    ProfScope(const MeshData& m_, cudaStream_t s, int kind) : m(m_), st(s) {
+        if (m.profiling && m.prof_next * 2 + 1 < (int)m.prof_ev.size()) {
+            idx = m.prof_next++;
+            const_cast<MeshData&>(m).prof_kind[idx] = kind;
+            cudaEventRecord(m.prof_ev[2 * idx], st);
+        }
+    }
+    ~ProfScope() {
+        if (idx >= 0) cudaEventRecord(m.prof_ev[2 * idx + 1], st);
+    }
+};
+
 template <typename Real>
 int enqueue_stage_t(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
                     int rhs_only, cudaStream_t st) {
     StageArgs<Real> s = make_args<Real>(m, Us, Un, out, a, b, dt, rhs_only);
     int e;
     if (m.p.av_on) {
-        if ((e = dispatch_sensor<Real>(m.N, s, (Real*)m.eps, st))) return e;
-        if ((e = dispatch_grad<Real>(m.N, s, (Real*)m.q, st))) return e;
+        {
+            ProfScope ps(m, st, 0);
+            if ((e = dispatch_sensor<Real>(m.N, s, (Real*)m.eps, st))) return e;
+        }
+        {
+            ProfScope ps(m, st, 1);
+            if ((e = dispatch_grad<Real>(m.N, s, (Real*)m.q, st))) return e;
+        }
     }
+    ProfScope ps(m, st, 2);
     return dispatch_stage<Real>(m.N, s, m.p.av_on, st);
 }
 
@@ -743,7 +768,10 @@ int dg_step(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
         if (m->gexec) { cudaGraphExecDestroy(m->gexec); m->gexec = nullptr; }
         if (m->graph) { cudaGraphDestroy(m->graph); m->graph = nullptr; }
         CUDA_OK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        m->prof_next = 0;
         const int e = enqueue_step(*m, dt, ctx->stream);
+        m->prof_count = m->prof_next;
+        m->prof_next = 1 << 30;   // no event records outside the profiled step graph
         cudaGraph_t g = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
         if (e || ce != cudaSuccess) {
@@ -799,6 +827,41 @@ int dg_sync(dg_ctx* ctx, double timeout_s) {
         if (el > timeout_s) return fail(ctx, DG_ETIMEOUT, "work still in flight after the timeout");
         std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
+}
+
+int dg_set_profiling(dg_ctx* ctx, dg_mesh h, int on) {
+    if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    cudaSetDevice(ctx->device);
+    CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (on && m->prof_ev.empty()) {
+        const int pairs = 9;  // up to three kernels per stage, three stages
+        m->prof_ev.resize(2 * pairs);
+        m->prof_kind.assign(pairs, -1);
+        for (auto& e : m->prof_ev) CUDA_OK(ctx, cudaEventCreate(&e));
+    }
+    m->profiling = on != 0;
+    m->prof_next = 1 << 30;
+    m->prof_count = 0;
+    if (m->gexec) { cudaGraphExecDestroy(m->gexec); m->gexec = nullptr; }
+    if (m->graph) { cudaGraphDestroy(m->graph); m->graph = nullptr; }
+    return DG_OK;
+}
+
+int dg_kernel_times(dg_ctx* ctx, dg_mesh h, double out_ms[4]) {
+    if (!ctx || !out_ms) return fail(ctx, DG_EINVAL, "NULL argument");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    if (!m->profiling || m->prof_count == 0) return fail(ctx, DG_EINVAL, "profiling is off or no step has run");
+    out_ms[0] = out_ms[1] = out_ms[2] = 0.0;
+    for (int i = 0; i < m->prof_count; ++i) {
+        float ms = 0.0f;
+        CUDA_OK(ctx, cudaEventElapsedTime(&ms, m->prof_ev[2 * i], m->prof_ev[2 * i + 1]));
+        if (m->prof_kind[i] >= 0 && m->prof_kind[i] < 3) out_ms[m->prof_kind[i]] += ms;
+    }
+    out_ms[3] = m->prof_count;
+    return DG_OK;
 }
 
 const char* dg_last_error(dg_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }

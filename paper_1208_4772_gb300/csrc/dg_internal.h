@@ -34,6 +34,12 @@ struct MeshData {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     double gdt = 0.0;
+    // profiling: event pairs around each kernel of one step, with its kind
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_kind;
+    mutable int prof_next = 1 << 30;
+    int prof_count = 0;
 };
 
 int enqueue_stage(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,

@@ -217,12 +217,20 @@ def naca_omesh(n_t=300, n_r=100, radius=20.0, ratio=1.06, jitter=0.1, seed=1001,
     radius about (0.5, 0); 2 n_t n_r triangles."""
     rng = np.random.default_rng(seed)
     curve = NacaCurve(tau)
-    # sigma_i = cos(pi i / n_t): clustered at both edges, counter-clockwise
-    sg = np.cos(np.pi * np.arange(n_t) / n_t)
+    # sigma uniform from 1 to -1 (counter-clockwise); x = sigma^2 clusters
+    # points at the leading edge and keeps the trailing-edge cells regular
+    sg = 1.0 - 2.0 * np.arange(n_t) / n_t
     surf = curve.point(sg)
-    ang = np.arctan2(surf[:, 1], surf[:, 0] - 0.5)
-    ang[0] = 0.0
-    outer = np.stack([0.5 + radius * np.cos(ang), radius * np.sin(ang)], axis=-1)
+    # grid lines leave the wall along its outward normal (the bisector at the
+    # trailing-edge corner) and end on the farfield circle about (0.5, 0)
+    tang = -curve.dpoint(sg)                  # traversal direction (sigma decreasing)
+    nrm = np.stack([tang[:, 1], -tang[:, 0]], axis=-1)
+    nrm[0] = (1.0, 0.0)
+    nrm /= np.linalg.norm(nrm, axis=-1, keepdims=True)
+    rel = surf - np.array([0.5, 0.0])
+    b = np.sum(rel * nrm, axis=-1)
+    t = -b + np.sqrt(b * b - (np.sum(rel * rel, axis=-1) - radius ** 2))
+    outer = surf + t[:, None] * nrm
     # the parameter of surface vertex i, with the wrap to sigma = -1 at i = n_t
     param = np.concatenate([sg, [-1.0]])
     return _omesh("naca0012", surf, outer, n_r, ratio, jitter, rng, curve, wall_param=param)
