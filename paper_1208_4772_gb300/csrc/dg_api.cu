@@ -218,11 +218,11 @@ struct ProfScope {
         if (m.profiling && m.prof_next * 2 + 1 < (int)m.prof_ev.size()) {
             idx = m.prof_next++;
             const_cast<MeshData&>(m).prof_kind[idx] = kind;
-            cudaEventRecord(m.prof_ev[2 * idx], st);
+            cudaEventRecordWithFlags(m.prof_ev[2 * idx], st, cudaEventRecordExternal);
         }
     }
     ~ProfScope() {
-        if (idx >= 0) cudaEventRecord(m.prof_ev[2 * idx + 1], st);
+        if (idx >= 0) cudaEventRecordWithFlags(m.prof_ev[2 * idx + 1], st, cudaEventRecordExternal);
     }
 };
 
