@@ -297,7 +297,11 @@ def run_ours(args):
     m = wl["mesh"]
     Np = len(r)
     dof_stage = m.K * Np * 4
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library, the L2 flush and the timing events all
+    # run on it (the legacy default stream has handle 0, which the C ABI
+    # reads as "no stream given")
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
     ctx = B.dg_create(local, stream.cuda_stream)
     flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device="cuda")
 
