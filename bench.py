@@ -21,6 +21,7 @@ independent replica of the workload (the method is not sharded here);
 value = all ranks' DOF-updates / max-over-ranks time.
 """
 import argparse
+import faulthandler
 import json
 import os
 import statistics
@@ -402,6 +403,7 @@ def run_ours(args):
 
 
 def main():
+    faulthandler.enable()
     args = parse_args()
     if args.cpu_sample:
         print(json.dumps(cpu_sample(args.cpu_sample, args.cpu_budget_s)))

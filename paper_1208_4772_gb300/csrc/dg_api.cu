@@ -92,6 +92,39 @@ int dispatch_grad(int N, const StageArgs<Real>& a, Real* out, cudaStream_t st) {
     return (int)cudaErrorInvalidValue;
 }
 
+int dispatch_stage_tc(int N, const StageArgs<float>& a, int av, int prec, const unsigned char* ops, int* err,
+                      cudaStream_t st) {
+    switch (N) {
+        case 2: return launch_stage_tc<2>(a, av, prec, ops, err, st);
+        case 3: return launch_stage_tc<3>(a, av, prec, ops, err, st);
+        case 4: return launch_stage_tc<4>(a, av, prec, ops, err, st);
+        case 5: return launch_stage_tc<5>(a, av, prec, ops, err, st);
+        case 6: return launch_stage_tc<6>(a, av, prec, ops, err, st);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+int dispatch_prepare_tc(int N) {
+    switch (N) {
+        case 2: return prepare_tc<2>();
+        case 3: return prepare_tc<3>();
+        case 4: return prepare_tc<4>();
+        case 5: return prepare_tc<5>();
+        case 6: return prepare_tc<6>();
+    }
+    return (int)cudaErrorInvalidValue;
+}
+std::vector<uint8_t> dispatch_pack_tc(int N, const RefOps& R, int prec) {
+    switch (N) {
+        case 2: return pack_ops_tc<2>(R, prec);
+        case 3: return pack_ops_tc<3>(R, prec);
+        case 4: return pack_ops_tc<4>(R, prec);
+        case 5: return pack_ops_tc<5>(R, prec);
+        case 6: return pack_ops_tc<6>(R, prec);
+    }
+    return {};
+}
+bool tensor_prec(int prec) { return prec == DG_TF32 || prec == DG_BF16X3; }
+
 // Packed operator table (layout of ops_layout) in FP64.
 std::vector<double> pack_ops(const RefOps& R) {
     const int NP = R.Np, NQ = R.Nq, NF = R.Nf;
@@ -177,6 +210,17 @@ void reset_batch(dg_ctx* ctx) {
     ctx->batch_key_dts.clear();
 }
 
+// Error words written by kernels whose bounded waits ran out.
+int check_device_errors(dg_ctx* ctx) {
+    for (auto& kv : ctx->meshes) {
+        int w = 0;
+        if (kv.second->err && cudaMemcpy(&w, kv.second->err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess &&
+            w != 0)
+            return fail(ctx, DG_ETIMEOUT, "a device-side wait ran out (error word " + std::to_string(w) + ")");
+    }
+    return DG_OK;
+}
+
 MeshData* find(dg_ctx* ctx, dg_mesh h) {
     auto it = ctx->meshes.find(h);
     return it == ctx->meshes.end() ? nullptr : it->second;
@@ -215,7 +259,7 @@ struct ProfScope {
     cudaStream_t st;
     int idx = -1;
     ProfScope(const MeshData& m_, cudaStream_t s, int kind) : m(m_), st(s) {
-        if (m.profiling && m.prof_next * 2 + 1 < (int)m.prof_ev.size()) {
+        if (m.prof_capturing && m.prof_next >= 0 && (size_t)m.prof_next < m.prof_kind.size()) {
             idx = m.prof_next++;
             const_cast<MeshData&>(m).prof_kind[idx] = kind;
             cudaEventRecordWithFlags(m.prof_ev[2 * idx], st, cudaEventRecordExternal);
@@ -242,6 +286,11 @@ int enqueue_stage_t(const MeshData& m, const void* Us, const void* Un, void* out
         }
     }
     ProfScope ps(m, st, 2);
+    if constexpr (sizeof(Real) == 4) {
+        if (tensor_prec(m.prec))
+            return dispatch_stage_tc(m.N, s, m.p.av_on, m.prec == DG_TF32 ? 1 : 2,
+                                     (const unsigned char*)m.ops_tc, m.err, st);
+    }
     return dispatch_stage<Real>(m.N, s, m.p.av_on, st);
 }
 
@@ -331,7 +380,9 @@ extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* hs, const double
         ms[i] = find(ctx, hs[i]);
         if (!ms[i]) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle in batch");
         if (ms[i]->p.av_on) return fail(ctx, DG_EINVAL, "batched path runs meshes without artificial viscosity");
-        if (ms[i]->rsize != ms[0]->rsize) return fail(ctx, DG_EINVAL, "batch mixes precision modes");
+        if (ms[i]->prec != ms[0]->prec) return fail(ctx, DG_EINVAL, "batch mixes precision modes");
+        if (tensor_prec(ms[i]->prec))
+            return fail(ctx, DG_EINVAL, "batched path runs DG_FP32 or DG_FP64_DEBUG meshes");
         if (!std::isfinite(dts[i])) return fail(ctx, DG_EINVAL, "bad dt");
         for (int j = 0; j < i; ++j)
             if (hs[j] == hs[i]) return fail(ctx, DG_EINVAL, "mesh listed twice in batch");
@@ -583,6 +634,34 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
         free_mesh(m);
         return e;
     }
+    if ((e = alloc(ctx, *m, (void**)&m->err, 16))) { free_mesh(m); return e; }
+    if (cudaMemset(m->err, 0, 16) != cudaSuccess) { free_mesh(m); return fail(ctx, DG_ECUDA, "memset failed"); }
+    if (tensor_prec(p->prec)) {
+        const int tkey = N * 16 + 4 + p->prec;
+        auto tit = ctx->ops.find(tkey);
+        if (tit == ctx->ops.end()) {
+            const std::vector<uint8_t> packed = dispatch_pack_tc(N, *R, p->prec == DG_TF32 ? 1 : 2);
+            void* d = nullptr;
+            if (cudaMalloc(&d, packed.size()) != cudaSuccess) {
+                cudaGetLastError();
+                free_mesh(m);
+                return fail(ctx, DG_ENOMEM, "tensor-core operator table allocation failed");
+            }
+            if (cudaMemcpy(d, packed.data(), packed.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+                cudaFree(d);
+                free_mesh(m);
+                return fail(ctx, DG_ECUDA, "tensor-core operator table copy failed");
+            }
+            ctx->ops[tkey] = d;
+            const int pe = dispatch_prepare_tc(N);
+            if (pe) {
+                free_mesh(m);
+                return fail(ctx, DG_ECUDA, "tensor-core kernel attribute set-up failed");
+            }
+            tit = ctx->ops.find(tkey);
+        }
+        m->ops_tc = tit->second;
+    }
     if (p->av_on) {
         if ((e = alloc(ctx, *m, &m->eps, (size_t)K * rs))) { free_mesh(m); return e; }
         if ((e = alloc(ctx, *m, &m->q, (size_t)K * 8 * NP * rs))) { free_mesh(m); return e; }
@@ -769,9 +848,10 @@ int dg_step(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
         if (m->graph) { cudaGraphDestroy(m->graph); m->graph = nullptr; }
         CUDA_OK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
         m->prof_next = 0;
+        m->prof_capturing = m->profiling;
         const int e = enqueue_step(*m, dt, ctx->stream);
-        m->prof_count = m->prof_next;
-        m->prof_next = 1 << 30;   // no event records outside the profiled step graph
+        m->prof_capturing = false;   // no event records outside the profiled step graph
+        m->prof_count = m->profiling ? m->prof_next : 0;
         cudaGraph_t g = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
         if (e || ce != cudaSuccess) {
@@ -816,12 +896,12 @@ int dg_sync(dg_ctx* ctx, double timeout_s) {
     cudaSetDevice(ctx->device);
     if (timeout_s <= 0) {
         CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
-        return DG_OK;
+        return check_device_errors(ctx);
     }
     const auto t0 = std::chrono::steady_clock::now();
     while (true) {
         const cudaError_t q = cudaStreamQuery(ctx->stream);
-        if (q == cudaSuccess) return DG_OK;
+        if (q == cudaSuccess) return check_device_errors(ctx);
         if (q != cudaErrorNotReady) return fail(ctx, DG_ECUDA, cudaGetErrorString(q));
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (el > timeout_s) return fail(ctx, DG_ETIMEOUT, "work still in flight after the timeout");
@@ -842,7 +922,8 @@ int dg_set_profiling(dg_ctx* ctx, dg_mesh h, int on) {
         for (auto& e : m->prof_ev) CUDA_OK(ctx, cudaEventCreate(&e));
     }
     m->profiling = on != 0;
-    m->prof_next = 1 << 30;
+    m->prof_capturing = false;
+    m->prof_next = 0;
     m->prof_count = 0;
     if (m->gexec) { cudaGraphExecDestroy(m->gexec); m->gexec = nullptr; }
     if (m->graph) { cudaGraphDestroy(m->graph); m->graph = nullptr; }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace dgc {
 
 constexpr int THREADS = 256;
@@ -80,6 +82,14 @@ template <int N, typename Real> int launch_grad(const StageArgs<Real>& a, Real* 
 // Set the dynamic shared-memory limits of the degree-N kernels (call once
 // per device before the first launch or stream capture).
 template <int N, typename Real> int prepare_kernels();
+
+// Tensor-core stage kernel (tc_kernels.cuh): prec 1 = TF32, 2 = BF16 x3.
+template <int N>
+int launch_stage_tc(const StageArgs<float>& a, int av, int prec, const unsigned char* ops_tc, int* err,
+                    cudaStream_t st);
+template <int N> int prepare_tc();
+struct RefOps;
+template <int N> std::vector<uint8_t> pack_ops_tc(const RefOps& R, int prec);
 
 // Generic kernels (kernels_common.cu)
 template <typename Real>

@@ -25,6 +25,8 @@ struct MeshData {
     void* geoA = nullptr;         // [Kaff][4]
     void* geoC = nullptr;         // [Kc][curved_stride]
     void* ops = nullptr;          // shared operator table (owned by the context)
+    void* ops_tc = nullptr;       // tensor-core operator table (owned by the context)
+    int* err = nullptr;           // device error word (bounded waits that ran out)
     int4* conn = nullptr;         // [K]
     long long* dperm = nullptr;   // device copy of perm
     long long* diperm = nullptr;  // inverse permutation
@@ -38,7 +40,8 @@ struct MeshData {
     bool profiling = false;
     std::vector<cudaEvent_t> prof_ev;
     std::vector<int> prof_kind;
-    mutable int prof_next = 1 << 30;
+    mutable int prof_next = 0;    // next event pair while capturing
+    bool prof_capturing = false;  // true only while a profiled step is being captured
     int prof_count = 0;
 };
 

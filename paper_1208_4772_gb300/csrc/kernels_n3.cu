@@ -1,5 +1,6 @@
-// Degree-3 instantiations of the CUDA-core stage, sensor and gradient kernels.
+// Degree-3 instantiations of the CUDA-core and tensor-core kernels.
 #include "kernels.cuh"
+#include "tc_kernels.cuh"
 
 namespace dgc {
 template int launch_stage<3, float>(const StageArgs<float>&, int, cudaStream_t);
@@ -12,4 +13,9 @@ template int launch_grad<3, double>(const StageArgs<double>&, double*, cudaStrea
 namespace dgc {
 template int prepare_kernels<3, float>();
 template int prepare_kernels<3, double>();
+}  // namespace dgc
+namespace dgc {
+template int launch_stage_tc<3>(const StageArgs<float>&, int, int, const unsigned char*, int*, cudaStream_t);
+template int prepare_tc<3>();
+template std::vector<uint8_t> pack_ops_tc<3>(const RefOps&, int);
 }  // namespace dgc

@@ -1,0 +1,633 @@
+// Tensor-core (tcgen05) stage kernel: the right-hand side and SSP-RK stage
+// of one tile of 32 affine elements, with the element-local operator
+// products on the fifth-generation tensor cores (TF32, or BF16 split into a
+// high and a low part with three products), FP32 accumulate in TMEM.
+//
+// Rows of both products are the 128 (element, variable) pairs of the tile:
+//   G1: D1[(e,v), p] = sum_j dU[(e,v), j] B1[p, j]
+//       B1 rows: I_cub (cubature points p < NQ), I_g (face points at FOFF+fg);
+//       dU = U - mean_e(U): the element mean is added back exactly
+//       (rows of I_cub and I_g sum to 1), so the low-precision products only
+//       see the deviation.
+//   G2: D2[(e,v), i] = sum_k A2[(e,v), k] B2[i, k], K in chunks of 32:
+//       face chunks    A2 = (F*.n - F(Ubar).n) sJ          B2 = -Mref^-1 Lift
+//       cubature chunks A2 = J(r_x dF + r_y dG), J(s_x dF + s_y dG), dF = F - F(Ubar)
+//                                                         B2 = Mref^-1 D_r^T W, Mref^-1 D_s^T W
+//       viscous chunks A2 = sqrt(eps) (J r_x q_x + J r_y q_y), ... at nodes
+//                                                         B2 = -Mref^-1 D^T W I_cub
+//   Subtracting the element-constant flux F(Ubar) changes nothing in exact
+//   arithmetic (free-stream preservation: the volume and face terms of a
+//   constant flux cancel on an affine element) and removes the cancellation
+//   that would otherwise amplify the products' rounding.
+//   L = D2 / J; U_out = a U^n + b (U_s + dt L).
+// Each A2 chunk is written by the 256 threads from registers while the
+// tensor core works on the previous chunk (two smem buffers, one mbarrier
+// each).  Curved tiles run the CUDA-core tile body in the same launch.
+#pragma once
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <vector>
+
+#include "kernels.cuh"
+#include "refops.h"
+#include "tc_ptx.cuh"
+
+namespace dgc {
+
+constexpr int PREC_TF32 = 1, PREC_BF16X3 = 2;
+
+template <int N>
+struct TcDims {
+    static constexpr int NP = np_of(N), NQ = nq_of(N), NG = ng_of(N), NF = nf_of(N);
+    static constexpr int NPK = (NP + 15) / 16 * 16;        // K of G1
+    static constexpr int FOFF = (NQ + 15) / 16 * 16;       // first face column of D1
+    static constexpr int N1 = (FOFF + NF + 15) / 16 * 16;  // columns of D1
+    static constexpr int NFP = (NF + 15) / 16 * 16;        // columns of each q-trace block
+    static constexpr int N2 = (NP + 15) / 16 * 16;         // columns of D2
+    static constexpr int CF = (NF + 31) / 32;              // face chunks
+    static constexpr int CQ = (NQ + 15) / 16;              // cubature chunks
+    static constexpr int CA = (NP + 15) / 16;              // viscous chunks
+    static constexpr int NCH = CF + CQ + CA;               // chunks in the operator table
+    static constexpr int E = 32;
+    static constexpr int NFS = NF + 1;                     // row stride of the trace exchange
+    static constexpr int TMEM_COLS = (N1 + 2 * NFP + N2) <= 128 ? 128 : 256;
+};
+
+// Operator table of the tensor-core path (bytes; built by the host).
+template <int N>
+struct TcLayout {
+    using D = TcDims<N>;
+    static constexpr int B1 = 0;                                   // [N1 rows][NPK]
+    static constexpr int B1_BYTES = D::N1 * D::NPK * 4;
+    static constexpr int B1Q = B1 + B1_BYTES;                      // [NFP rows][NPK]  I_g
+    static constexpr int B1Q_BYTES = D::NFP * D::NPK * 4;
+    static constexpr int B2 = B1Q + B1Q_BYTES;                     // NCH x [N2 rows][32]
+    static constexpr int B2_CHUNK = D::N2 * 32 * 4;
+    static constexpr int IGF = B2 + D::NCH * B2_CHUNK;             // I_g fp32 [NF][NP]
+    static constexpr int TOTAL = IGF + D::NF * D::NP * 4;
+};
+
+template <int N, bool AV>
+struct TcSmem {
+    using D = TcDims<N>;
+    using L = TcLayout<N>;
+    static constexpr int NCHU = D::CF + D::CQ + (AV ? D::CA : 0);  // chunks used
+    static constexpr int sB1 = 0;
+    static constexpr int sB1Q = sB1 + L::B1_BYTES;
+    static constexpr int sB2 = sB1Q + (AV ? L::B1Q_BYTES : 0);
+    static constexpr int sIGF = sB2 + NCHU * L::B2_CHUNK;
+    static constexpr int sA1 = (sIGF + D::NF * D::NP * 4 + 127) / 128 * 128;  // [128][NPK]
+    static constexpr int A1_BYTES = 128 * D::NPK * 4;
+    static constexpr int sA2 = sA1 + A1_BYTES * (AV ? 3 : 1);               // 2 x [128][32]
+    static constexpr int A2_BYTES = 128 * 32 * 4;
+    static constexpr int sTR = sA2 + 2 * A2_BYTES;                           // [128][NFS] floats
+    static constexpr int TR_BYTES = 128 * D::NFS * 4;
+    static constexpr int sMEAN = sTR + TR_BYTES * (AV ? 3 : 1);              // [128] floats
+    static constexpr int sGEO = sMEAN + 128 * 4;                             // [E][16]
+    static constexpr int sSE = sGEO + D::E * 16 * 4;                         // [E] sqrt(eps)
+    static constexpr int sNB = sSE + D::E * 4;                               // [E] int4
+    static constexpr int sBAR = sNB + D::E * 16;                             // 4 mbarriers
+    static constexpr int sTMEM = sBAR + 4 * 8;
+    static constexpr int TOTAL = sTMEM + 16;
+};
+
+template <int N, bool AV>
+constexpr size_t tc_smem_bytes() {
+    const size_t a = TcSmem<N, AV>::TOTAL;
+    const size_t b = Tile<N, float>::smem_stage(AV);
+    return a > b ? a : b;
+}
+
+// Writes 8 consecutive K values (k0 multiple of 8) of one row of an A
+// operand with row_k K values.  TF32: rounded fp32; BF16X3: high part in the
+// first half of the buffer, low part (x - high) in the second half.
+template <int PREC>
+__device__ __forceinline__ void store8(unsigned char* A, int row, int k0, int row_k, const float x[8]) {
+    if constexpr (PREC == PREC_TF32) {
+        const uint32_t rb = row_k * 4;
+        float4 lo = make_float4(tc::to_tf32(x[0]), tc::to_tf32(x[1]), tc::to_tf32(x[2]), tc::to_tf32(x[3]));
+        float4 hi = make_float4(tc::to_tf32(x[4]), tc::to_tf32(x[5]), tc::to_tf32(x[6]), tc::to_tf32(x[7]));
+        *reinterpret_cast<float4*>(A + tc::cm_offset(row, k0 * 4, rb)) = lo;
+        *reinterpret_cast<float4*>(A + tc::cm_offset(row, k0 * 4 + 16, rb)) = hi;
+    } else {
+        const uint32_t rb = row_k * 2;
+        const int half = 128 * row_k * 2;
+        __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            h[i] = __float2bfloat16_rn(x[i]);
+            l[i] = __float2bfloat16_rn(x[i] - __bfloat162float(h[i]));
+        }
+        *reinterpret_cast<uint4*>(A + tc::cm_offset(row, k0 * 2, rb)) = *reinterpret_cast<const uint4*>(h);
+        *reinterpret_cast<uint4*>(A + half + tc::cm_offset(row, k0 * 2, rb)) = *reinterpret_cast<const uint4*>(l);
+    }
+}
+
+// Issue the products D += A x B^T over K = row_k values (A: 128 rows, B: n
+// rows, both in the core-matrix layout with row_k values per row).
+template <int PREC>
+__device__ __forceinline__ void issue_mma(uint32_t d_tmem, const unsigned char* A, const unsigned char* B, int n,
+                                          int row_k, bool accumulate) {
+    if constexpr (PREC == PREC_TF32) {
+        const uint32_t rb = row_k * 4;
+        const uint32_t idesc = tc::instr_desc(2, 128, n);
+        const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(B);
+        for (int ks = 0; ks < row_k / 8; ++ks)
+            tc::mma_tf32(d_tmem, tc::smem_desc(a0 + ks * 256, rb), tc::smem_desc(b0 + ks * 256, rb), idesc,
+                         (accumulate || ks > 0) ? 1u : 0u);
+    } else {
+        const uint32_t rb = row_k * 2;
+        const uint32_t idesc = tc::instr_desc(1, 128, n);
+        const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(B);
+        const uint32_t ah = a0, al = a0 + 128 * rb, bh = b0, bl = b0 + n * rb;
+        for (int ks = 0; ks < row_k / 16; ++ks) {
+            const uint32_t o = ks * 256;
+            tc::mma_bf16(d_tmem, tc::smem_desc(ah + o, rb), tc::smem_desc(bh + o, rb), idesc,
+                         (accumulate || ks > 0) ? 1u : 0u);
+            tc::mma_bf16(d_tmem, tc::smem_desc(ah + o, rb), tc::smem_desc(bl + o, rb), idesc, 1u);
+            tc::mma_bf16(d_tmem, tc::smem_desc(al + o, rb), tc::smem_desc(bh + o, rb), idesc, 1u);
+        }
+    }
+}
+
+template <int N, bool AV, int PREC>
+__device__ void stage_tile_tc(const StageArgs<float>& p, long long e0, int ne, const unsigned char* ops_tc,
+                              unsigned char* smem, int* err) {
+    using D = TcDims<N>;
+    using S = TcSmem<N, AV>;
+    using L = TcLayout<N>;
+    constexpr int NP = D::NP, NQ = D::NQ, NG = D::NG, NF = D::NF, NPK = D::NPK, FOFF = D::FOFF;
+    constexpr int N1 = D::N1, NFP = D::NFP, N2 = D::N2, NFS = D::NFS;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = (warp & 3) * 32 + lane;     // TMEM lane = (element, variable) row
+    const int half = warp >> 2;                 // which half of the columns
+    const int e = row >> 2, v = row & 3;
+    const unsigned quad_mask = 0xffffffffu;
+    const int qbase = lane & ~3;
+
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::sBAR);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S::sTMEM);
+    float* sMean = reinterpret_cast<float*>(smem + S::sMEAN);
+    float* sGeo = reinterpret_cast<float*>(smem + S::sGEO);
+    float* sSe = reinterpret_cast<float*>(smem + S::sSE);
+    int4* sNb = reinterpret_cast<int4*>(smem + S::sNB);
+    float* sTr = reinterpret_cast<float*>(smem + S::sTR);
+    const float* sIgF = reinterpret_cast<const float*>(smem + S::sIGF);
+
+    // ---------------- operators, mbarriers, TMEM
+    {
+        const int4* src = reinterpret_cast<const int4*>(ops_tc);
+        int4* dst = reinterpret_cast<int4*>(smem);
+        for (int i = tid; i < L::B1_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+        if constexpr (AV)
+            for (int i = tid; i < L::B1Q_BYTES / 16; i += blockDim.x)
+                dst[S::sB1Q / 16 + i] = src[L::B1Q / 16 + i];
+        for (int i = tid; i < S::NCHU * L::B2_CHUNK / 16; i += blockDim.x) dst[S::sB2 / 16 + i] = src[L::B2 / 16 + i];
+        for (int i = tid; i < NF * NP * 4 / 16; i += blockDim.x) dst[S::sIGF / 16 + i] = src[L::IGF / 16 + i];
+        if ((NF * NP) % 4)
+            for (int i = (NF * NP) / 4 * 4 + tid; i < NF * NP; i += blockDim.x)
+                reinterpret_cast<float*>(smem + S::sIGF)[i] = reinterpret_cast<const float*>(ops_tc + L::IGF)[i];
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 4; ++b) tc::mbar_init(&bars[b], 1);
+        tc::mbar_fence_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tmem_slot, D::TMEM_COLS);
+
+    // ---------------- state tile: deviations from the element mean into A1
+    const long long k = e0 + e;
+    const bool live = e < ne;
+    unsigned char* A1 = smem + S::sA1;
+    if (half == 0) {
+        float u[NP];
+        float mean = 0.f;
+        if (live) {
+            const float* src = p.Us + (k * 4 + v) * NP;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                u[j] = src[j];
+                mean += u[j];
+            }
+            mean *= (1.0f / NP);
+        } else {
+            mean = (v == 0) ? 1.f : (v == 3) ? 2.5f : 0.f;   // a valid state for padding rows
+#pragma unroll
+            for (int j = 0; j < NP; ++j) u[j] = mean;
+        }
+        sMean[row] = mean;
+#pragma unroll
+        for (int j0 = 0; j0 < NPK; j0 += 8) {
+            float x[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = (j0 + i < NP) ? u[j0 + i] - mean : 0.f;
+            store8<PREC>(A1, row, j0, NPK, x);
+        }
+    } else if constexpr (AV) {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            unsigned char* Aq = A1 + (1 + m) * S::A1_BYTES;
+            const float* src = p.q + ((k * 2 + m) * 4 + v) * NP;
+#pragma unroll
+            for (int j0 = 0; j0 < NPK; j0 += 8) {
+                float x[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) x[i] = (live && j0 + i < NP) ? src[j0 + i] : 0.f;
+                store8<PREC>(Aq, row, j0, NPK, x);
+            }
+        }
+    }
+    if (tid < D::E) {
+        if (tid < ne) {
+            affine_geometry(p.geoA + (e0 + tid) * 4, sGeo + tid * 16);
+            sNb[tid] = p.conn[e0 + tid];
+            sSe[tid] = AV ? sqrtf(p.eps[e0 + tid]) : 0.f;
+        } else {
+            for (int i = 0; i < 16; ++i) sGeo[tid * 16 + i] = (i == 4 || i == 7 || i == 10 || i == 13) ? 1.f : 0.f;
+            sNb[tid] = make_int4(0, 0, 0, 0xAAA);   // farfield on all faces
+            sSe[tid] = 0.f;
+        }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t tD1 = tmem, tD1q = tmem + N1, tD2 = tmem + N1 + (AV ? 2 * NFP : 0);
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+
+    // ---------------- G1
+    if (tid == 0) {
+        issue_mma<PREC>(tD1, A1, smem + S::sB1, N1, NPK, false);
+        if constexpr (AV) {
+            issue_mma<PREC>(tD1q, A1 + S::A1_BYTES, smem + S::sB1Q, NFP, NPK, false);
+            issue_mma<PREC>(tD1q + NFP, A1 + 2 * S::A1_BYTES, smem + S::sB1Q, NFP, NPK, false);
+        }
+        tc::mma_commit(&bars[2]);
+    }
+    // flux of the element-mean state while the products run
+    const float* g = sGeo + e * 16;
+    const float jrx = g[0], jry = g[1], jsx = g[2], jsy = g[3], invJ = g[4];
+    float Ub[4], Fb[4], Gb[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) Ub[w] = sMean[e * 4 + w];
+    euler_flux(Ub, p.gamma, Fb, Gb);
+    const float fbar = Fb[v], gbar = Gb[v];
+    const float mean_v = Ub[v];
+    const float se = sSe[e];
+    if (!tc::mbar_wait(&bars[2], 0)) atomicOr(err, 1);
+    tc::fence_after_sync();
+
+    // ---------------- own traces to shared memory for the exchange
+    {
+        // half 0: U traces; half 1: q traces (AV) -- each row NF values
+        if (half == 0) {
+#pragma unroll
+            for (int c0 = 0; c0 < NF; c0 += 8) {
+                float x[8];
+                tc::tmem_ld8(tD1 + lane_base + FOFF + c0, x);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (c0 + i < NF) sTr[row * NFS + c0 + i] = x[i] + mean_v;
+            }
+        } else if constexpr (AV) {
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int c0 = 0; c0 < NF; c0 += 8) {
+                    float x[8];
+                    tc::tmem_ld8(tD1q + m * NFP + lane_base + c0, x);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (c0 + i < NF) sTr[(1 + m) * 128 * NFS + row * NFS + c0 + i] = x[i];
+                }
+        }
+    }
+    __syncthreads();
+
+    // ---------------- chunk pipeline for G2
+    int chunk = 0;
+    auto begin_chunk = [&](int c) -> unsigned char* {
+        const int buf = c & 1;
+        if (c >= 2 && !tc::mbar_wait(&bars[buf], ((c - 2) >> 1) & 1)) atomicOr(err, 2);
+        return smem + S::sA2 + buf * S::A2_BYTES;
+    };
+    auto end_chunk = [&](int c) {
+        tc::fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            issue_mma<PREC>(tD2, smem + S::sA2 + (c & 1) * S::A2_BYTES, smem + S::sB2 + c * TcLayout<N>::B2_CHUNK,
+                            N2, 32, c > 0);
+            tc::mma_commit(&bars[c & 1]);
+        }
+    };
+
+    // face chunks: (F*.n - visc - F(Ubar).n) sJ, face points split between halves
+    const int4 nbw = sNb[e];
+    const int ncode = nbw.w;
+#pragma unroll 1
+    for (int cf = 0; cf < D::CF; ++cf, ++chunk) {
+        unsigned char* A2 = begin_chunk(chunk);
+#pragma unroll 1
+        for (int s0 = half * 16; s0 < half * 16 + 16; s0 += 8) {
+            float out[8];
+#pragma unroll 1
+            for (int i = 0; i < 8; ++i) {
+                const int fg = cf * 32 + s0 + i;
+                float val = 0.f;
+                if (fg < NF) {
+                    const int f = fg / NG, gg = fg - f * NG;
+                    const int bc = code_bc(ncode, f);
+                    const int nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
+                    const int fgn = code_face(ncode, f) * NG + (NG - 1 - gg);
+                    const float nx = g[5 + 3 * f], ny = g[6 + 3 * f], sJ = g[7 + 3 * f];
+                    float Um[4], Up[4];
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) Um[w] = sTr[(e * 4 + w) * NFS + fg];
+                    const long long nbl = (long long)nb - e0;
+                    const bool in_tile = (bc == 0) && nbl >= 0 && nbl < ne;
+                    if (bc != 0) {
+                        ghost_state(Um, bc, nx, ny, p.uinf, Up);
+                    } else if (in_tile) {
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) Up[w] = sTr[((int)nbl * 4 + w) * NFS + fgn];
+                    } else {
+                        const float* un = p.Us + (long long)nb * 4 * NP;
+                        const float* ig = sIgF + fgn * NP;
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) {
+                            float a = 0.f;
+#pragma unroll
+                            for (int j = 0; j < NP; ++j) a += ig[j] * __ldg(un + w * NP + j);
+                            Up[w] = a;
+                        }
+                    }
+                    float Fn[4];
+                    llf_flux(Um, Up, nx, ny, p.gamma, Fn);
+                    float fv = Fn[v];
+                    if constexpr (AV) {
+                        const float qmx = sTr[128 * NFS + row * NFS + fg];
+                        const float qmy = sTr[2 * 128 * NFS + row * NFS + fg];
+                        float qpx = qmx, qpy = qmy, sep = se;
+                        if (bc == 0) {
+                            sep = sqrtf(__ldg(p.eps + nb));
+                            if (in_tile) {
+                                qpx = sTr[128 * NFS + ((int)nbl * 4 + v) * NFS + fgn];
+                                qpy = sTr[2 * 128 * NFS + ((int)nbl * 4 + v) * NFS + fgn];
+                            } else {
+                                const float* qn = p.q + (long long)nb * 8 * NP;
+                                const float* ig = sIgF + fgn * NP;
+                                float ax = 0.f, ay = 0.f;
+#pragma unroll
+                                for (int j = 0; j < NP; ++j) {
+                                    ax += ig[j] * __ldg(qn + v * NP + j);
+                                    ay += ig[j] * __ldg(qn + (4 + v) * NP + j);
+                                }
+                                qpx = ax;
+                                qpy = ay;
+                            }
+                        }
+                        fv -= 0.5f * (se * (qmx * nx + qmy * ny) + sep * (qpx * nx + qpy * ny));
+                    }
+                    val = (fv - (fbar * nx + gbar * ny)) * sJ;
+                }
+                out[i] = val;
+            }
+            store8<PREC>(A2, row, s0, 32, out);
+        }
+        end_chunk(chunk);
+    }
+
+    // cubature chunks: contravariant flux deviations
+#pragma unroll 1
+    for (int cq = 0; cq < D::CQ; ++cq, ++chunk) {
+        unsigned char* A2 = begin_chunk(chunk);
+        const int q0 = cq * 16 + half * 8;
+        float x[8];
+        tc::tmem_ld8(tD1 + lane_base + q0, x);
+        tc::tmem_ld_wait();
+        float fo[8], go[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float mine = x[i] + mean_v;
+            float Uc[4];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) Uc[w] = __shfl_sync(quad_mask, mine, qbase + w);
+            const float ir = 1.f / Uc[0];
+            const float uu = Uc[1] * ir, vv = Uc[2] * ir;
+            const float pr = (p.gamma - 1.f) * (Uc[3] - 0.5f * (Uc[1] * uu + Uc[2] * vv));
+            float F, G;
+            // F_v, G_v of the 2D Euler flux for this thread's variable
+            if (v == 0) { F = Uc[1]; G = Uc[2]; }
+            else if (v == 1) { F = Uc[1] * uu + pr; G = Uc[1] * vv; }
+            else if (v == 2) { F = Uc[2] * uu; G = Uc[2] * vv + pr; }
+            else { F = uu * (Uc[3] + pr); G = vv * (Uc[3] + pr); }
+            const float dF = F - fbar, dG = G - gbar;
+            const bool ok = (q0 + i) < NQ;
+            fo[i] = ok ? jrx * dF + jry * dG : 0.f;
+            go[i] = ok ? jsx * dF + jsy * dG : 0.f;
+        }
+        store8<PREC>(A2, row, half * 8, 32, fo);
+        store8<PREC>(A2, row, 16 + half * 8, 32, go);
+        end_chunk(chunk);
+    }
+
+    // viscous chunks: sqrt(eps) (J r_x q_x + J r_y q_y), sqrt(eps) (J s_x q_x + J s_y q_y)
+    if constexpr (AV) {
+#pragma unroll 1
+        for (int ca = 0; ca < D::CA; ++ca, ++chunk) {
+            unsigned char* A2 = begin_chunk(chunk);
+            const int j0 = ca * 16 + half * 8;
+            float ar[8], as[8];
+            const float* qx = p.q + ((k * 2 + 0) * 4 + v) * NP;
+            const float* qy = p.q + ((k * 2 + 1) * 4 + v) * NP;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int j = j0 + i;
+                const float a = (live && j < NP) ? qx[j] : 0.f;
+                const float b = (live && j < NP) ? qy[j] : 0.f;
+                ar[i] = se * (jrx * a + jry * b);
+                as[i] = se * (jsx * a + jsy * b);
+            }
+            store8<PREC>(A2, row, half * 8, 32, ar);
+            store8<PREC>(A2, row, 16 + half * 8, 32, as);
+            end_chunk(chunk);
+        }
+    }
+
+    // ---------------- epilogue: L = D2 / J, stage combination
+    {
+        const int last = chunk - 1;
+        if (!tc::mbar_wait(&bars[last & 1], (last >> 1) & 1)) atomicOr(err, 4);
+        tc::fence_after_sync();
+        constexpr int per_half = N2 / 2;
+#pragma unroll
+        for (int c0 = 0; c0 < per_half; c0 += 8) {
+            float x[8];
+            const int i0 = half * per_half + c0;
+            tc::tmem_ld8(tD2 + lane_base + i0, x);
+            tc::tmem_ld_wait();
+            if (live) {
+                const long long base = (k * 4 + v) * NP;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int ii = i0 + i;
+                    if (ii < NP) {
+                        const float Lv = x[i] * invJ;
+                        p.Uout[base + ii] = p.rhs_only ? Lv
+                                                       : (p.a != 0.f ? p.a * p.Un[base + ii] : 0.f) +
+                                                             p.b * (p.Us[base + ii] + p.dt * Lv);
+                    }
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tmem, D::TMEM_COLS);
+}
+
+// Grid: affine tiles of 32 elements on the tensor cores, then curved tiles
+// on the CUDA-core body.
+template <int N, bool AV, int PREC>
+__global__ void __launch_bounds__(THREADS, 1) stage_kernel_tc(StageArgs<float> p, const unsigned char* ops_tc, int* err) {
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
+    const long long nAff = (p.Kaff + ET - 1) / ET;
+    if ((long long)blockIdx.x < nAff) {
+        const long long e0 = (long long)blockIdx.x * ET;
+        stage_tile_tc<N, AV, PREC>(p, e0, (int)min((long long)ET, p.Kaff - e0), ops_tc, smem_tc, err);
+    } else {
+        TileRange t;
+        t.curved = true;
+        t.e0 = p.Kaff + ((long long)blockIdx.x - nAff) * EC;
+        t.ne = (int)min((long long)EC, p.K - t.e0);
+        if (t.ne > 0) stage_tile<N, float, AV>(p, t, smem_tc);
+    }
+}
+
+template <int N, bool AV, int PREC>
+int launch_stage_tc_t(const StageArgs<float>& a, const unsigned char* ops_tc, int* err, cudaStream_t st) {
+    constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
+    const unsigned grid = (unsigned)((a.Kaff + ET - 1) / ET + (a.K - a.Kaff + EC - 1) / EC);
+    if (grid == 0) return 0;
+    stage_kernel_tc<N, AV, PREC><<<grid, THREADS, tc_smem_bytes<N, AV>(), st>>>(a, ops_tc, err);
+    return (int)cudaGetLastError();
+}
+
+template <int N>
+int launch_stage_tc(const StageArgs<float>& a, int av, int prec, const unsigned char* ops_tc, int* err,
+                    cudaStream_t st) {
+    if (prec == PREC_TF32)
+        return av ? launch_stage_tc_t<N, true, PREC_TF32>(a, ops_tc, err, st)
+                  : launch_stage_tc_t<N, false, PREC_TF32>(a, ops_tc, err, st);
+    return av ? launch_stage_tc_t<N, true, PREC_BF16X3>(a, ops_tc, err, st)
+              : launch_stage_tc_t<N, false, PREC_BF16X3>(a, ops_tc, err, st);
+}
+
+template <int N>
+int prepare_tc() {
+    int e = 0;
+    e |= (int)cudaFuncSetAttribute(stage_kernel_tc<N, false, PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)tc_smem_bytes<N, false>());
+    e |= (int)cudaFuncSetAttribute(stage_kernel_tc<N, true, PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)tc_smem_bytes<N, true>());
+    e |= (int)cudaFuncSetAttribute(stage_kernel_tc<N, false, PREC_BF16X3>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<N, false>());
+    e |= (int)cudaFuncSetAttribute(stage_kernel_tc<N, true, PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)tc_smem_bytes<N, true>());
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// host: operator table of the tensor-core path
+// ---------------------------------------------------------------------------
+inline uint32_t host_tf32_bits(double x) {
+    float f = (float)x;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x1000u;          // round to nearest, ties away from zero, at 10 mantissa bits
+    u &= ~0x1FFFu;
+    return u;
+}
+inline uint16_t host_bf16_bits(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);   // round to nearest even
+    return (uint16_t)(u >> 16);
+}
+inline float host_bf16_value(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Write an operand matrix M[rows][K] (value(row, k)) into the core-matrix
+// layout: TF32 (4-byte, rounded) or BF16 high block followed by low block.
+template <typename F>
+inline void pack_operand(std::vector<uint8_t>& out, size_t off, int rows, int K, int prec, F value) {
+    if (prec == PREC_TF32) {
+        for (int r = 0; r < rows; ++r)
+            for (int k = 0; k < K; ++k) {
+                const uint32_t b = host_tf32_bits(value(r, k));
+                std::memcpy(&out[off + tc::cm_offset(r, k * 4, K * 4)], &b, 4);
+            }
+    } else {
+        const size_t lo = (size_t)rows * K * 2;
+        for (int r = 0; r < rows; ++r)
+            for (int k = 0; k < K; ++k) {
+                const float x = (float)value(r, k);
+                const uint16_t h = host_bf16_bits(x);
+                const uint16_t l = host_bf16_bits(x - host_bf16_value(h));
+                std::memcpy(&out[off + tc::cm_offset(r, k * 2, K * 2)], &h, 2);
+                std::memcpy(&out[off + lo + tc::cm_offset(r, k * 2, K * 2)], &l, 2);
+            }
+    }
+}
+
+template <int N>
+std::vector<uint8_t> pack_ops_tc(const RefOps& R, int prec) {
+    using D = TcDims<N>;
+    using L = TcLayout<N>;
+    constexpr int NP = D::NP, NQ = D::NQ, NF = D::NF;
+    std::vector<uint8_t> out(L::TOTAL, 0);
+    auto Icub = [&](int q, int j) { return R.Icub[(size_t)q * NP + j]; };
+    auto Ig = [&](int fg, int j) { return R.Ig[(size_t)fg * NP + j]; };
+    pack_operand(out, L::B1, D::N1, D::NPK, prec, [&](int r, int k) -> double {
+        if (k >= NP) return 0.0;
+        if (r < NQ) return Icub(r, k);
+        if (r >= D::FOFF && r < D::FOFF + NF) return Ig(r - D::FOFF, k);
+        return 0.0;
+    });
+    pack_operand(out, L::B1Q, D::NFP, D::NPK, prec,
+                 [&](int r, int k) -> double { return (r < NF && k < NP) ? Ig(r, k) : 0.0; });
+    for (int c = 0; c < D::NCH; ++c) {
+        pack_operand(out, L::B2 + (size_t)c * L::B2_CHUNK, D::N2, 32, prec, [&](int i, int s) -> double {
+            if (i >= NP) return 0.0;
+            if (c < D::CF) {
+                const int fg = c * 32 + s;
+                return fg < NF ? -R.MLift[(size_t)i * NF + fg] : 0.0;
+            }
+            if (c < D::CF + D::CQ) {
+                const int q = (c - D::CF) * 16 + (s & 15);
+                if (q >= NQ) return 0.0;
+                return s < 16 ? R.MrW[(size_t)i * NQ + q] : R.MsW[(size_t)i * NQ + q];
+            }
+            const int j = (c - D::CF - D::CQ) * 16 + (s & 15);
+            if (j >= NP) return 0.0;
+            return s < 16 ? -R.Qr[(size_t)i * NP + j] : -R.Qs[(size_t)i * NP + j];
+        });
+    }
+    for (int fg = 0; fg < NF; ++fg)
+        for (int j = 0; j < NP; ++j) {
+            const float f = (float)Ig(fg, j);
+            std::memcpy(&out[L::IGF + ((size_t)fg * NP + j) * 4], &f, 4);
+        }
+    return out;
+}
+
+}  // namespace dgc

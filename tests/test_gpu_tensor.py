@@ -1,0 +1,144 @@
+"""Tensor-core (tcgen05) path, DG_TF32 and DG_BF16X3, against the FP64
+oracle and against the FP32 CUDA-core path.
+
+Tolerances (from the arithmetic of the products):
+  * BF16 x3: each operand is split into a BF16 high and low part and three
+    products are summed; the dropped low x low term and the BF16 rounding of
+    the low parts leave ~2^-16 relative error per product, applied to the
+    deviation from the element-mean state -> right-hand side within 1e-5 of
+    the volume-term norm (as the FP32 path), states after 100 steps within
+    1e-5 relative L2.
+  * TF32: 10-bit mantissa (2^-11 relative per operand), again on the
+    deviations only -> right-hand side within 2e-3 of the volume-term norm,
+    states after 100 vortex steps within 1e-4 relative L2.
+"""
+import numpy as np
+import pytest
+
+import __graft_entry__
+from oracle.dg import Oracle
+from paper_1208_4772_gb300.inputs import meshes, states
+from cases import make_case, rel_l2_per_var
+
+pytestmark = pytest.mark.gpu
+
+RHS_TOL = {"tf32": 2e-3, "bf16x3": 1e-5}
+STEP_TOL = {"tf32": 1e-4, "bf16x3": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def B():
+    __graft_entry__.build()
+    from paper_1208_4772_gb300 import binding
+    binding.load()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.dg_create(0)
+    yield c
+    B.dg_destroy(c)
+
+
+def upload(B, ctx, case, prec, U=None):
+    m = case["mesh"]
+    p = B.make_params(u_inf=case["u_inf"], av_on=case["av"], prec=prec)
+    h = B.dg_mesh_upload(ctx, case["N"], m.EToE, m.EToF, m.bc, case["xy"], p)
+    B.dg_set_state(ctx, h, case["U"] if U is None else U)
+    return h
+
+
+def oracle_of(case):
+    m = case["mesh"]
+    return Oracle(case["N"], m.EToE, m.EToF, m.bc, case["xy"], u_inf=case["u_inf"], av=case["av"])
+
+
+def term_scale(o, U):
+    _, vol, _ = o.rhs(U, parts=True)
+    V = np.einsum('kij,kvj->kvi', o.geometry(None).Minv, vol)
+    return np.linalg.norm(V.transpose(1, 0, 2).reshape(4, -1), axis=1)
+
+
+def rel_err(L, Lo, scale):
+    return np.linalg.norm((L - Lo).transpose(1, 0, 2).reshape(4, -1), axis=1) / scale
+
+
+CASES = [("vortex", N, False) for N in (2, 3, 4, 5, 6)] + \
+        [("naca", 4, False), ("naca", 4, True), ("cyl", 6, False), ("cyl", 3, True), ("vortex", 5, True)]
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+@pytest.mark.parametrize("kind,N,av", CASES)
+def test_tc_rhs_matches_oracle(B, ctx, kind, N, av, prec):
+    r, s = B.dg_reference_nodes(N)
+    case = make_case(kind, N, r, s, av=av)
+    case["U"] = case["U"].astype(np.float32).astype(np.float64)
+    h = upload(B, ctx, case, prec)
+    L = B.dg_eval_rhs(ctx, h, case["mesh"].K, len(r))
+    B.dg_mesh_free(ctx, h)
+    o = oracle_of(case)
+    Lo = o.rhs(case["U"])
+    err = rel_err(L, Lo, term_scale(o, case["U"]))
+    tol = RHS_TOL[prec] * (10 if av else 1)
+    assert np.all(err <= tol), err
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_tc_vortex_100_steps(B, ctx, prec):
+    N = 2
+    r, s = B.dg_reference_nodes(N)
+    m = meshes.periodic_square(16, length=10.0, jitter=0.1, seed=1000)
+    xy = meshes.straight_nodes(m.verts, r, s)
+    U0 = states.vortex_state(xy, period=(10.0, 10.0))
+    dt = states.time_step(m.verts, U0, N, cfl=0.3)
+    o = Oracle(N, m.EToE, m.EToF, m.bc, xy)
+    Uo = U0.copy()
+    for _ in range(100):
+        Uo = o.ssp_rk3_step(Uo, dt)
+    case = dict(mesh=m, xy=xy, u_inf=states.freestream(0.5), U=U0, av=False, N=N)
+    h = upload(B, ctx, case, prec)
+    B.dg_step(ctx, h, dt, 100)
+    Ug = B.dg_get_state(ctx, h, m.K, len(r))
+    B.dg_mesh_free(ctx, h)
+    err = rel_l2_per_var(Ug, Uo)
+    assert np.all(err <= STEP_TOL[prec]), err
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_tc_ragged_and_mixed_tiles(B, ctx, prec):
+    """K below one tile, K not a multiple of 32, and a mesh whose curved
+    tiles run the CUDA-core body inside the tensor-core launch."""
+    for kind, N, size in (("vortex", 3, 3), ("vortex", 4, 5), ("naca", 2, "tiny"), ("cyl", 4, "small")):
+        r, s = B.dg_reference_nodes(N)
+        case = make_case(kind, N, r, s, size=size)
+        case["U"] = case["U"].astype(np.float32).astype(np.float64)
+        h = upload(B, ctx, case, prec)
+        L = B.dg_eval_rhs(ctx, h, case["mesh"].K, len(r))
+        B.dg_mesh_free(ctx, h)
+        o = oracle_of(case)
+        err = rel_err(L, o.rhs(case["U"]), term_scale(o, case["U"]))
+        assert np.all(err <= RHS_TOL[prec]), (kind, N, size, err)
+
+
+def test_profiling_times_and_later_calls(B, ctx):
+    """Kernel timing nodes in the step graph; calls made afterwards outside
+    the graph (residual, state reads) are unaffected."""
+    N = 4
+    r, s = B.dg_reference_nodes(N)
+    case = make_case("naca", N, r, s, av=True)
+    h = upload(B, ctx, case, "tf32")
+    B.dg_set_profiling(ctx, h, 1)
+    dt = 0.1 * states.time_step(case["mesh"].verts, case["U"], N, eps0=0.3)
+    B.dg_step(ctx, h, dt, 2)
+    B.dg_sync(ctx, 30.0)
+    t = B.dg_kernel_times(ctx, h)
+    assert t[3] == 9 and np.all(t[:3] > 0)
+    B.dg_residual(ctx, h)
+    B.dg_eval_rhs(ctx, h, case["mesh"].K, len(r))
+    B.dg_set_profiling(ctx, h, 0)
+    B.dg_step(ctx, h, dt, 1)
+    B.dg_sync(ctx, 30.0)
+    with pytest.raises(B.DgError):
+        B.dg_kernel_times(ctx, h)
+    B.dg_mesh_free(ctx, h)
