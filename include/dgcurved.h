@@ -167,6 +167,28 @@ int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* ms, const double* dts, int 
 int dg_set_profiling(dg_ctx* ctx, dg_mesh m, int on);
 int dg_kernel_times(dg_ctx* ctx, dg_mesh m, double out_ms[4]);
 
+/* Residual norms of a caller's device array with no allocation at all.  The
+ * paper has no counterpart: this serves callers that cannot allocate device
+ * memory where they need the norms -- code running during CUDA graph
+ * capture, real-time loops that must avoid the allocator, hosts whose
+ * framework owns every device byte.  values_dev: device float[K][4][Np]
+ * (any element order); out8_dev: device double[8] receiving max |x| for
+ * the four variables, then sqrt(sum x^2) for the four variables, in FP64
+ * (the definition dg_residual uses).  Runs on the calling thread's current
+ * device, asynchronously on cuda_stream (NULL = legacy default stream); both
+ * pointers must belong to that device.  The reduction's partial results
+ * live in a fixed 1 MiB file-scope device array that every GPU loading the
+ * library keeps until the process exits, so K*4*Np may not exceed
+ * 67,108,864 values (DG_EINVAL beyond that, and for NULL pointers or
+ * non-positive sizes).  The first call on a device looks up that array's
+ * address (cudaGetSymbolAddress), so make it before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race; calls in
+ * order on one stream are safe.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.  Errors: DG_EINVAL, DG_ECUDA (message in
+ * dg_last_error(NULL)). */
+int dg_residual_norms_noalloc(const float* values_dev, int64_t K, int32_t Np, double* out8_dev,
+                              void* cuda_stream);
+
 /* Wait for the context's stream, polling at most timeout_s seconds
  * (<= 0: wait without limit).  DG_ETIMEOUT if work is still in flight then;
  * the work itself is not cancelled. */

@@ -76,6 +76,7 @@ def load():
         "dg_batch_step": (I, [P, I, C.POINTER(C.c_int32), dp, I]),
         "dg_sync": (I, [P, D]),
         "dg_set_profiling": (I, [P, C.c_int32, I]),
+        "dg_residual_norms_noalloc": (I, [P, I64, C.c_int32, P, P]),
         "dg_kernel_times": (I, [P, C.c_int32, dp]),
         "dg_last_error": (C.c_char_p, [P]),
     }
@@ -189,6 +190,14 @@ def dg_batch_step(ctx, meshes, dts, nsteps):
 
 def dg_sync(ctx, timeout_s=0.0):
     return _check(load().dg_sync(ctx, float(timeout_s)), ctx)
+
+
+def dg_residual_norms_noalloc(values_dev_ptr, K, Np, out8_dev_ptr, stream=None):
+    """FP64 residual norms of a device float[K][4][Np] into a device
+    double[8], without any allocation (see include/dgcurved.h)."""
+    st = load().dg_residual_norms_noalloc(C.c_void_p(values_dev_ptr), int(K), int(Np), C.c_void_p(out8_dev_ptr),
+                                          None if stream is None else C.c_void_p(stream))
+    return _check(st, None)
 
 
 def dg_set_profiling(ctx, m, on):

@@ -298,6 +298,8 @@ int enqueue_stage_t(const MeshData& m, const void* Us, const void* Un, void* out
 
 namespace dgc {
 
+void set_global_error(const std::string& msg) { g_err = msg; }
+
 int enqueue_stage(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
                   int rhs_only, cudaStream_t st) {
     if (m.prec == DG_FP64_DEBUG) return enqueue_stage_t<double>(m, Us, Un, out, a, b, dt, rhs_only, st);
