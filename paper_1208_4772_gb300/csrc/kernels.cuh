@@ -342,11 +342,13 @@ __global__ void __launch_bounds__(THREADS) stage_kernel(StageArgs<Real> p) {
 }
 
 // ---------------------------------------------------------------------------
-// Persson-Peraire sensor: eps_k from the density (paper Sec. 2).  One warp
-// per element.  Affine: S = sum_{deg N} u^2 / sum u^2 with u = V^-1 rho
-// (the cubature form reduces to this for constant J and an orthonormal
-// basis).  Curved: both integrals by cubature with J.  The ratio and its
-// log10 are taken in FP64.
+// Persson-Peraire sensor: eps_k from the density (paper Sec. 2).  A warp
+// takes 32 elements; for each, the lanes share the sums over modes (affine:
+// S = sum_{deg N} u^2 / sum u^2 with u = V^-1 rho, which is the cubature
+// form for constant J and an orthonormal basis) or over cubature points
+// (curved: both integrals with J), accumulated in the state precision; lane
+// e then keeps element e's two sums and takes the ratio, log10 and the sine
+// ramp in FP64 for its element, so the FP64 work runs 32 elements wide.
 // ---------------------------------------------------------------------------
 template <int N, typename Real>
 __global__ void __launch_bounds__(THREADS) sensor_kernel(StageArgs<Real> p, Real* eps_out) {
@@ -354,37 +356,48 @@ __global__ void __launch_bounds__(THREADS) sensor_kernel(StageArgs<Real> p, Real
     constexpr int NLOW = N * (N + 1) / 2;  // modes of degree <= N-1 come first
     constexpr OpsLayout L = ops_layout(N);
     const int lane = threadIdx.x & 31;
-    const long long k = (long long)blockIdx.x * (THREADS / 32) + (threadIdx.x >> 5);
-    if (k >= p.K) return;
-    const Real* rho = p.Us + k * 4 * NP;  // variable 0
-    double num = 0.0, den = 0.0;
-    if (k < p.Kaff) {
-        for (int m = lane; m < NP; m += 32) {
-            Real um = 0;
-            for (int j = 0; j < NP; ++j) um += p.ops[L.vinvt + j * NP + m] * rho[j];
-            const double d = (double)um * (double)um;
-            den += d;
-            if (m >= NLOW) num += d;
-        }
-    } else {
-        const Real* g = p.geoC + (k - p.Kaff) * curved_stride(N);
-        for (int qn = lane; qn < NQ; qn += 32) {
-            Real a = 0, b = 0;
-            for (int j = 0; j < NP; ++j) {
-                a += p.ops[L.icub + j * NQ + qn] * rho[j];
-                b += p.ops[L.itopt + j * NQ + qn] * rho[j];
-            }
-            const double wj = (double)p.ops[L.w + qn] * (double)g[4 * NQ + qn];
-            den += wj * (double)a * (double)a;
-            num += wj * (double)b * (double)b;
-        }
-    }
+    const long long k0 = ((long long)blockIdx.x * (THREADS / 32) + (threadIdx.x >> 5)) * 32;
+    if (k0 >= p.K) return;
+    Real my_num = 0, my_den = 0;
+    for (int e = 0; e < 32; ++e) {
+        const long long k = k0 + e;
+        if (k >= p.K) break;
+        const Real* rho = p.Us + k * 4 * NP;  // variable 0
+        Real num = 0, den = 0;
+        if (k < p.Kaff) {
+            if (lane < NP) {
+                Real um = 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        num += __shfl_xor_sync(0xffffffffu, num, o);
-        den += __shfl_xor_sync(0xffffffffu, den, o);
+                for (int j = 0; j < NP; ++j) um += p.ops[L.vinvt + j * NP + lane] * rho[j];
+                den = um * um;
+                num = (lane >= NLOW) ? den : Real(0);
+            }
+        } else {
+            const Real* g = p.geoC + (k - p.Kaff) * curved_stride(N);
+            for (int qn = lane; qn < NQ; qn += 32) {
+                Real a = 0, b = 0;
+                for (int j = 0; j < NP; ++j) {
+                    a += p.ops[L.icub + j * NQ + qn] * rho[j];
+                    b += p.ops[L.itopt + j * NQ + qn] * rho[j];
+                }
+                const Real wj = p.ops[L.w + qn] * g[4 * NQ + qn];
+                den += wj * a * a;
+                num += wj * b * b;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            num += __shfl_xor_sync(0xffffffffu, num, o);
+            den += __shfl_xor_sync(0xffffffffu, den, o);
+        }
+        if (lane == e) {
+            my_num = num;
+            my_den = den;
+        }
     }
-    if (lane == 0) {
+    const long long k = k0 + lane;
+    if (k < p.K) {
+        const double num = (double)my_num, den = (double)my_den;
         double e = 0.0;
         if (num > 0.0 && den > 0.0) {
             const double s = log10(num / den);
@@ -574,7 +587,7 @@ int launch_stage(const StageArgs<Real>& a, int av, cudaStream_t st) {
 
 template <int N, typename Real>
 int launch_sensor(const StageArgs<Real>& a, Real* eps_out, cudaStream_t st) {
-    const long long per = THREADS / 32;
+    const long long per = (THREADS / 32) * 32;   // elements per block
     const unsigned grid = (unsigned)((a.K + per - 1) / per);
     if (grid == 0) return 0;
     sensor_kernel<N, Real><<<grid, THREADS, 0, st>>>(a, eps_out);

@@ -73,21 +73,29 @@ struct TcSmem {
     using D = TcDims<N>;
     using L = TcLayout<N>;
     static constexpr int NCHU = D::CF + D::CQ + (AV ? D::CA : 0);  // chunks used
+    static constexpr int al(int x) { return (x + 127) / 128 * 128; }
+    // constant region: operators, loaded once per CTA
     static constexpr int sB1 = 0;
     static constexpr int sB1Q = sB1 + L::B1_BYTES;
     static constexpr int sB2 = sB1Q + (AV ? L::B1Q_BYTES : 0);
     static constexpr int sIGF = sB2 + NCHU * L::B2_CHUNK;
-    static constexpr int sA1 = (sIGF + D::NF * D::NP * 4 + 127) / 128 * 128;  // [128][NPK]
+    // per-tile region
+    static constexpr int sA1 = al(sIGF + D::NF * D::NP * 4);               // [128][NPK] (x3 with AV)
     static constexpr int A1_BYTES = 128 * D::NPK * 4;
     static constexpr int sA2 = sA1 + A1_BYTES * (AV ? 3 : 1);               // 2 x [128][32]
     static constexpr int A2_BYTES = 128 * 32 * 4;
-    static constexpr int sTR = sA2 + 2 * A2_BYTES;                           // [128][NFS] floats
-    static constexpr int TR_BYTES = 128 * D::NFS * 4;
-    static constexpr int sMEAN = sTR + TR_BYTES * (AV ? 3 : 1);              // [128] floats
-    static constexpr int sGEO = sMEAN + 128 * 4;                             // [E][16]
-    static constexpr int sSE = sGEO + D::E * 16 * 4;                         // [E] sqrt(eps)
-    static constexpr int sNB = sSE + D::E * 4;                               // [E] int4
-    static constexpr int sBAR = sNB + D::E * 16;                             // 4 mbarriers
+    static constexpr int sTR = sA2 + 2 * A2_BYTES;                           // traces [128][NFS] (x2 with AV)
+    static constexpr int TR_FLOATS = 128 * D::NFS;
+    static constexpr int sIO = al(sTR + TR_FLOATS * 4 * (AV ? 2 : 1));       // staging
+    static constexpr int ST1 = 32 * 68;                                      // [e][16 q x 4 v + 4]
+    static constexpr int ST2 = 128 * 36;                                     // [row][32 + 4]
+    static constexpr int IO_FLOATS = (32 * 4 * D::NP > ST1 + ST2) ? 32 * 4 * D::NP : ST1 + ST2;
+    static constexpr int sMEAN = al(sIO + IO_FLOATS * 4);                     // [128]
+    static constexpr int sGEO = sMEAN + 128 * 4;                             // [32][16]
+    static constexpr int sFB = sGEO + 32 * 16 * 4;                           // [32][8] mean flux
+    static constexpr int sSE = sFB + 32 * 8 * 4;                             // [32] sqrt(eps)
+    static constexpr int sNB = sSE + 32 * 4;                                 // [32] int4
+    static constexpr int sBAR = sNB + 32 * 16;                               // 4 mbarriers
     static constexpr int sTMEM = sBAR + 4 * 8;
     static constexpr int TOTAL = sTMEM + 16;
 };
@@ -151,54 +159,57 @@ __device__ __forceinline__ void issue_mma(uint32_t d_tmem, const unsigned char* 
     }
 }
 
+// Tile body: one tile of up to 32 affine elements.  The operator tables,
+// mbarriers and TMEM are set up once per CTA by the persistent kernel;
+// ph tracks the phases of the mbarriers across tiles.
+struct TcPhase {
+    uint32_t g1 = 0;            // completions consumed on the G1 barrier
+    uint32_t commits[2] = {0, 0};
+    uint32_t waits[2] = {0, 0};
+};
+
 template <int N, bool AV, int PREC>
-__device__ void stage_tile_tc(const StageArgs<float>& p, long long e0, int ne, const unsigned char* ops_tc,
-                              unsigned char* smem, int* err) {
+__device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long long e0, int ne, unsigned char* smem,
+                                              uint32_t tmem, TcPhase& ph, int* err) {
     using D = TcDims<N>;
     using S = TcSmem<N, AV>;
-    using L = TcLayout<N>;
     constexpr int NP = D::NP, NQ = D::NQ, NG = D::NG, NF = D::NF, NPK = D::NPK, FOFF = D::FOFF;
     constexpr int N1 = D::N1, NFP = D::NFP, N2 = D::N2, NFS = D::NFS;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = (warp & 3) * 32 + lane;     // TMEM lane = (element, variable) row
-    const int half = warp >> 2;                 // which half of the columns
+    const int half = warp >> 2;                 // which half of the columns this thread loads
     const int e = row >> 2, v = row & 3;
-    const unsigned quad_mask = 0xffffffffu;
-    const int qbase = lane & ~3;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const uint32_t tD1 = tmem, tD1q = tmem + N1, tD2 = tmem + N1 + (AV ? 2 * NFP : 0);
 
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::sBAR);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S::sTMEM);
     float* sMean = reinterpret_cast<float*>(smem + S::sMEAN);
     float* sGeo = reinterpret_cast<float*>(smem + S::sGEO);
+    float* sFb = reinterpret_cast<float*>(smem + S::sFB);
     float* sSe = reinterpret_cast<float*>(smem + S::sSE);
     int4* sNb = reinterpret_cast<int4*>(smem + S::sNB);
     float* sTr = reinterpret_cast<float*>(smem + S::sTR);
+    float* sQn = sTr + S::TR_FLOATS;            // AV: sqrt(eps) q.n at own face points
+    float* sIO = reinterpret_cast<float*>(smem + S::sIO);
+    float* st1 = sIO;                           // [e][q x 4 + 4]
+    float* st2 = sIO + S::ST1;                  // [row][36]
     const float* sIgF = reinterpret_cast<const float*>(smem + S::sIGF);
+    unsigned char* A1 = smem + S::sA1;
 
-    // ---------------- operators, mbarriers, TMEM
-    {
-        const int4* src = reinterpret_cast<const int4*>(ops_tc);
-        int4* dst = reinterpret_cast<int4*>(smem);
-        for (int i = tid; i < L::B1_BYTES / 16; i += blockDim.x) dst[i] = src[i];
-        if constexpr (AV)
-            for (int i = tid; i < L::B1Q_BYTES / 16; i += blockDim.x)
-                dst[S::sB1Q / 16 + i] = src[L::B1Q / 16 + i];
-        for (int i = tid; i < S::NCHU * L::B2_CHUNK / 16; i += blockDim.x) dst[S::sB2 / 16 + i] = src[L::B2 / 16 + i];
-        for (int i = tid; i < NF * NP * 4 / 16; i += blockDim.x) dst[S::sIGF / 16 + i] = src[L::IGF / 16 + i];
-        if ((NF * NP) % 4)
-            for (int i = (NF * NP) / 4 * 4 + tid; i < NF * NP; i += blockDim.x)
-                reinterpret_cast<float*>(smem + S::sIGF)[i] = reinterpret_cast<const float*>(ops_tc + L::IGF)[i];
+    // ---------------- per-element data and the state deviations
+    if (tid < 32) {
+        if (tid < ne) {
+            affine_geometry(p.geoA + (e0 + tid) * 4, sGeo + tid * 16);
+            sNb[tid] = p.conn[e0 + tid];
+            sSe[tid] = AV ? sqrtf(p.eps[e0 + tid]) : 0.f;
+        } else {  // padding element: unit geometry, farfield faces, never stored
+            for (int i = 0; i < 16; ++i) sGeo[tid * 16 + i] = (i == 4 || i == 7 || i == 10 || i == 13) ? 1.f : 0.f;
+            sNb[tid] = make_int4(0, 0, 0, 0x888);
+            sSe[tid] = 0.f;
+        }
     }
-    if (tid == 0) {
-        for (int b = 0; b < 4; ++b) tc::mbar_init(&bars[b], 1);
-        tc::mbar_fence_init();
-    }
-    if (warp == 0) tc::tmem_alloc(tmem_slot, D::TMEM_COLS);
-
-    // ---------------- state tile: deviations from the element mean into A1
     const long long k = e0 + e;
     const bool live = e < ne;
-    unsigned char* A1 = smem + S::sA1;
     if (half == 0) {
         float u[NP];
         float mean = 0.f;
@@ -211,7 +222,7 @@ __device__ void stage_tile_tc(const StageArgs<float>& p, long long e0, int ne, c
             }
             mean *= (1.0f / NP);
         } else {
-            mean = (v == 0) ? 1.f : (v == 3) ? 2.5f : 0.f;   // a valid state for padding rows
+            mean = (v == 0) ? 1.f : (v == 3) ? 2.5f : 0.f;
 #pragma unroll
             for (int j = 0; j < NP; ++j) u[j] = mean;
         }
@@ -237,26 +248,12 @@ __device__ void stage_tile_tc(const StageArgs<float>& p, long long e0, int ne, c
             }
         }
     }
-    if (tid < D::E) {
-        if (tid < ne) {
-            affine_geometry(p.geoA + (e0 + tid) * 4, sGeo + tid * 16);
-            sNb[tid] = p.conn[e0 + tid];
-            sSe[tid] = AV ? sqrtf(p.eps[e0 + tid]) : 0.f;
-        } else {
-            for (int i = 0; i < 16; ++i) sGeo[tid * 16 + i] = (i == 4 || i == 7 || i == 10 || i == 13) ? 1.f : 0.f;
-            sNb[tid] = make_int4(0, 0, 0, 0xAAA);   // farfield on all faces
-            sSe[tid] = 0.f;
-        }
-    }
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = *tmem_slot;
-    const uint32_t tD1 = tmem, tD1q = tmem + N1, tD2 = tmem + N1 + (AV ? 2 * NFP : 0);
-    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
 
-    // ---------------- G1
+    // ---------------- G1: state deviations to cubature and face points
     if (tid == 0) {
         issue_mma<PREC>(tD1, A1, smem + S::sB1, N1, NPK, false);
         if constexpr (AV) {
@@ -265,178 +262,196 @@ __device__ void stage_tile_tc(const StageArgs<float>& p, long long e0, int ne, c
         }
         tc::mma_commit(&bars[2]);
     }
-    // flux of the element-mean state while the products run
-    const float* g = sGeo + e * 16;
-    const float jrx = g[0], jry = g[1], jsx = g[2], jsy = g[3], invJ = g[4];
-    float Ub[4], Fb[4], Gb[4];
+    if (tid < 128) {   // flux of the element-mean state, one (element, variable) per thread
+        float Ub[4], Fb[4], Gb[4];
 #pragma unroll
-    for (int w = 0; w < 4; ++w) Ub[w] = sMean[e * 4 + w];
-    euler_flux(Ub, p.gamma, Fb, Gb);
-    const float fbar = Fb[v], gbar = Gb[v];
-    const float mean_v = Ub[v];
-    const float se = sSe[e];
-    if (!tc::mbar_wait(&bars[2], 0)) atomicOr(err, 1);
+        for (int w = 0; w < 4; ++w) Ub[w] = sMean[e * 4 + w];
+        euler_flux(Ub, p.gamma, Fb, Gb);
+        sFb[e * 8 + v] = Fb[v];
+        sFb[e * 8 + 4 + v] = Gb[v];
+    }
+    if (!tc::mbar_wait(&bars[2], ph.g1 & 1)) atomicOr(err, 1);
+    ph.g1++;
     tc::fence_after_sync();
 
-    // ---------------- own traces to shared memory for the exchange
-    {
-        // half 0: U traces; half 1: q traces (AV) -- each row NF values
-        if (half == 0) {
+    // ---------------- own traces (and sqrt(eps) q.n) to shared memory
+    const float mean_v = sMean[row];
+    if (half == 0) {
 #pragma unroll
-            for (int c0 = 0; c0 < NF; c0 += 8) {
-                float x[8];
-                tc::tmem_ld8(tD1 + lane_base + FOFF + c0, x);
-                tc::tmem_ld_wait();
+        for (int c0 = 0; c0 < NF; c0 += 8) {
+            float x[8];
+            tc::tmem_ld8(tD1 + lane_base + FOFF + c0, x);
+            tc::tmem_ld_wait();
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    if (c0 + i < NF) sTr[row * NFS + c0 + i] = x[i] + mean_v;
-            }
-        } else if constexpr (AV) {
+            for (int i = 0; i < 8; ++i)
+                if (c0 + i < NF) sTr[row * NFS + c0 + i] = x[i] + mean_v;
+        }
+    } else if constexpr (AV) {
+        const float se = sSe[e];
 #pragma unroll
-            for (int m = 0; m < 2; ++m)
+        for (int c0 = 0; c0 < NF; c0 += 8) {
+            float qx[8], qy[8];
+            tc::tmem_ld8(tD1q + lane_base + c0, qx);
+            tc::tmem_ld8(tD1q + NFP + lane_base + c0, qy);
+            tc::tmem_ld_wait();
 #pragma unroll
-                for (int c0 = 0; c0 < NF; c0 += 8) {
-                    float x[8];
-                    tc::tmem_ld8(tD1q + m * NFP + lane_base + c0, x);
-                    tc::tmem_ld_wait();
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        if (c0 + i < NF) sTr[(1 + m) * 128 * NFS + row * NFS + c0 + i] = x[i];
+            for (int i = 0; i < 8; ++i) {
+                const int fg = c0 + i;
+                if (fg < NF) {
+                    const int f = fg / NG;
+                    sQn[row * NFS + fg] = se * (qx[i] * sGeo[e * 16 + 5 + 3 * f] + qy[i] * sGeo[e * 16 + 6 + 3 * f]);
                 }
+            }
         }
     }
     __syncthreads();
 
-    // ---------------- chunk pipeline for G2
+    // ---------------- G2 chunk pipeline
     int chunk = 0;
     auto begin_chunk = [&](int c) -> unsigned char* {
         const int buf = c & 1;
-        if (c >= 2 && !tc::mbar_wait(&bars[buf], ((c - 2) >> 1) & 1)) atomicOr(err, 2);
+        // the buffer is free once every product issued from it has completed
+        while (ph.waits[buf] < ph.commits[buf]) {
+            if (!tc::mbar_wait(&bars[buf], ph.waits[buf] & 1)) atomicOr(err, 2);
+            ph.waits[buf]++;
+        }
         return smem + S::sA2 + buf * S::A2_BYTES;
     };
     auto end_chunk = [&](int c) {
         tc::fence_async_smem();
         __syncthreads();
+        const int buf = c & 1;
         if (tid == 0) {
             tc::fence_after_sync();
-            issue_mma<PREC>(tD2, smem + S::sA2 + (c & 1) * S::A2_BYTES, smem + S::sB2 + c * TcLayout<N>::B2_CHUNK,
-                            N2, 32, c > 0);
-            tc::mma_commit(&bars[c & 1]);
+            issue_mma<PREC>(tD2, smem + S::sA2 + buf * S::A2_BYTES, smem + S::sB2 + c * TcLayout<N>::B2_CHUNK, N2,
+                            32, c > 0);
+            tc::mma_commit(&bars[buf]);
+        }
+        ph.commits[buf]++;
+    };
+    // rows of st2 (36 floats: 32 slots + 4 pad) to the A2 chunk, 16 slots per half
+    auto st2_to_a2 = [&](unsigned char* A2) {
+#pragma unroll
+        for (int s0 = 0; s0 < 16; s0 += 8) {
+            const float4 a = *reinterpret_cast<const float4*>(st2 + row * 36 + half * 16 + s0);
+            const float4 b = *reinterpret_cast<const float4*>(st2 + row * 36 + half * 16 + s0 + 4);
+            const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            store8<PREC>(A2, row, half * 16 + s0, 32, x);
         }
     };
 
-    // face chunks: (F*.n - visc - F(Ubar).n) sJ, face points split between halves
-    const int4 nbw = sNb[e];
-    const int ncode = nbw.w;
-#pragma unroll 1
-    for (int cf = 0; cf < D::CF; ++cf, ++chunk) {
+    // face chunk: (F*.n - (sqrt(eps) q)*.n - F(Ubar).n) sJ for the 4 variables of (element, face point)
+    static_assert(D::CF == 1, "one face chunk");
+    {
         unsigned char* A2 = begin_chunk(chunk);
-#pragma unroll 1
-        for (int s0 = half * 16; s0 < half * 16 + 16; s0 += 8) {
-            float out[8];
-#pragma unroll 1
-            for (int i = 0; i < 8; ++i) {
-                const int fg = cf * 32 + s0 + i;
-                float val = 0.f;
-                if (fg < NF) {
-                    const int f = fg / NG, gg = fg - f * NG;
-                    const int bc = code_bc(ncode, f);
-                    const int nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
-                    const int fgn = code_face(ncode, f) * NG + (NG - 1 - gg);
-                    const float nx = g[5 + 3 * f], ny = g[6 + 3 * f], sJ = g[7 + 3 * f];
-                    float Um[4], Up[4];
+        for (int it = tid; it < 128 * 36 / 4; it += blockDim.x)
+            reinterpret_cast<float4*>(st2)[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        for (int it = tid; it < 32 * NF; it += blockDim.x) {
+            const int ee = it / NF, fg = it - ee * NF;
+            const int f = fg / NG, gg = fg - f * NG;
+            const int4 nbw = sNb[ee];
+            const int bc = code_bc(nbw.w, f);
+            const int nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
+            const int fgn = code_face(nbw.w, f) * NG + (NG - 1 - gg);
+            const float* ge = sGeo + ee * 16;
+            const float nx = ge[5 + 3 * f], ny = ge[6 + 3 * f], sJ = ge[7 + 3 * f];
+            float Um[4], Up[4];
 #pragma unroll
-                    for (int w = 0; w < 4; ++w) Um[w] = sTr[(e * 4 + w) * NFS + fg];
-                    const long long nbl = (long long)nb - e0;
-                    const bool in_tile = (bc == 0) && nbl >= 0 && nbl < ne;
-                    if (bc != 0) {
-                        ghost_state(Um, bc, nx, ny, p.uinf, Up);
-                    } else if (in_tile) {
+            for (int w = 0; w < 4; ++w) Um[w] = sTr[(ee * 4 + w) * NFS + fg];
+            const long long nbl = (long long)nb - e0;
+            const bool in_tile = (bc == 0) && nbl >= 0 && nbl < ne;
+            if (bc != 0) {
+                ghost_state(Um, bc, nx, ny, p.uinf, Up);
+            } else if (in_tile) {
 #pragma unroll
-                        for (int w = 0; w < 4; ++w) Up[w] = sTr[((int)nbl * 4 + w) * NFS + fgn];
-                    } else {
-                        const float* un = p.Us + (long long)nb * 4 * NP;
-                        const float* ig = sIgF + fgn * NP;
+                for (int w = 0; w < 4; ++w) Up[w] = sTr[((int)nbl * 4 + w) * NFS + fgn];
+            } else {
+                const float* un = p.Us + (long long)nb * 4 * NP;
+                const float* ig = sIgF + fgn * NP;
 #pragma unroll
-                        for (int w = 0; w < 4; ++w) {
-                            float a = 0.f;
+                for (int w = 0; w < 4; ++w) {
+                    float a = 0.f;
 #pragma unroll
-                            for (int j = 0; j < NP; ++j) a += ig[j] * __ldg(un + w * NP + j);
-                            Up[w] = a;
-                        }
-                    }
-                    float Fn[4];
-                    llf_flux(Um, Up, nx, ny, p.gamma, Fn);
-                    float fv = Fn[v];
-                    if constexpr (AV) {
-                        const float qmx = sTr[128 * NFS + row * NFS + fg];
-                        const float qmy = sTr[2 * 128 * NFS + row * NFS + fg];
-                        float qpx = qmx, qpy = qmy, sep = se;
-                        if (bc == 0) {
-                            sep = sqrtf(__ldg(p.eps + nb));
-                            if (in_tile) {
-                                qpx = sTr[128 * NFS + ((int)nbl * 4 + v) * NFS + fgn];
-                                qpy = sTr[2 * 128 * NFS + ((int)nbl * 4 + v) * NFS + fgn];
-                            } else {
-                                const float* qn = p.q + (long long)nb * 8 * NP;
-                                const float* ig = sIgF + fgn * NP;
-                                float ax = 0.f, ay = 0.f;
-#pragma unroll
-                                for (int j = 0; j < NP; ++j) {
-                                    ax += ig[j] * __ldg(qn + v * NP + j);
-                                    ay += ig[j] * __ldg(qn + (4 + v) * NP + j);
-                                }
-                                qpx = ax;
-                                qpy = ay;
-                            }
-                        }
-                        fv -= 0.5f * (se * (qmx * nx + qmy * ny) + sep * (qpx * nx + qpy * ny));
-                    }
-                    val = (fv - (fbar * nx + gbar * ny)) * sJ;
+                    for (int j = 0; j < NP; ++j) a += ig[j] * __ldg(un + w * NP + j);
+                    Up[w] = a;
                 }
-                out[i] = val;
             }
-            store8<PREC>(A2, row, s0, 32, out);
+            float Fn[4];
+            llf_flux(Um, Up, nx, ny, p.gamma, Fn);
+            if constexpr (AV) {
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const float own = sQn[(ee * 4 + w) * NFS + fg];
+                    float other;   // the neighbour's sqrt(eps) q.n' with n' = -n, negated
+                    if (bc != 0) {
+                        other = own;
+                    } else if (in_tile) {
+                        other = -sQn[((int)nbl * 4 + w) * NFS + fgn];
+                    } else {
+                        const float* qn_ = p.q + (long long)nb * 8 * NP;
+                        const float* ig = sIgF + fgn * NP;
+                        float ax = 0.f, ay = 0.f;
+#pragma unroll
+                        for (int j = 0; j < NP; ++j) {
+                            ax += ig[j] * __ldg(qn_ + w * NP + j);
+                            ay += ig[j] * __ldg(qn_ + (4 + w) * NP + j);
+                        }
+                        other = sqrtf(__ldg(p.eps + nb)) * (ax * nx + ay * ny);
+                    }
+                    Fn[w] -= 0.5f * (own + other);
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                st2[(ee * 4 + w) * 36 + fg] = (Fn[w] - (sFb[ee * 8 + w] * nx + sFb[ee * 8 + 4 + w] * ny)) * sJ;
         }
+        __syncthreads();
+        st2_to_a2(A2);
         end_chunk(chunk);
+        ++chunk;
     }
 
-    // cubature chunks: contravariant flux deviations
+    // cubature chunks: contravariant flux deviations, one flux per (element, point)
 #pragma unroll 1
     for (int cq = 0; cq < D::CQ; ++cq, ++chunk) {
         unsigned char* A2 = begin_chunk(chunk);
-        const int q0 = cq * 16 + half * 8;
-        float x[8];
-        tc::tmem_ld8(tD1 + lane_base + q0, x);
-        tc::tmem_ld_wait();
-        float fo[8], go[8];
+        {
+            float x[8];
+            tc::tmem_ld8(tD1 + lane_base + cq * 16 + half * 8, x);
+            tc::tmem_ld_wait();
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const float mine = x[i] + mean_v;
-            float Uc[4];
-#pragma unroll
-            for (int w = 0; w < 4; ++w) Uc[w] = __shfl_sync(quad_mask, mine, qbase + w);
-            const float ir = 1.f / Uc[0];
-            const float uu = Uc[1] * ir, vv = Uc[2] * ir;
-            const float pr = (p.gamma - 1.f) * (Uc[3] - 0.5f * (Uc[1] * uu + Uc[2] * vv));
-            float F, G;
-            // F_v, G_v of the 2D Euler flux for this thread's variable
-            if (v == 0) { F = Uc[1]; G = Uc[2]; }
-            else if (v == 1) { F = Uc[1] * uu + pr; G = Uc[1] * vv; }
-            else if (v == 2) { F = Uc[2] * uu; G = Uc[2] * vv + pr; }
-            else { F = uu * (Uc[3] + pr); G = vv * (Uc[3] + pr); }
-            const float dF = F - fbar, dG = G - gbar;
-            const bool ok = (q0 + i) < NQ;
-            fo[i] = ok ? jrx * dF + jry * dG : 0.f;
-            go[i] = ok ? jsx * dF + jsy * dG : 0.f;
+            for (int i = 0; i < 8; ++i) st1[e * 68 + (half * 8 + i) * 4 + v] = x[i] + mean_v;
         }
-        store8<PREC>(A2, row, half * 8, 32, fo);
-        store8<PREC>(A2, row, 16 + half * 8, 32, go);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int it = tid + r * 256;
+            const int ee = it >> 4, ql = it & 15;
+            const float4 U4 = *reinterpret_cast<const float4*>(st1 + ee * 68 + ql * 4);
+            const float Uc[4] = {U4.x, U4.y, U4.z, U4.w};
+            float F[4], G[4];
+            euler_flux(Uc, p.gamma, F, G);
+            const float* ge = sGeo + ee * 16;
+            const float jrx = ge[0], jry = ge[1], jsx = ge[2], jsy = ge[3];
+            const bool ok = cq * 16 + ql < NQ;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const float dF = F[w] - sFb[ee * 8 + w], dG = G[w] - sFb[ee * 8 + 4 + w];
+                st2[(ee * 4 + w) * 36 + ql] = ok ? jrx * dF + jry * dG : 0.f;
+                st2[(ee * 4 + w) * 36 + 16 + ql] = ok ? jsx * dF + jsy * dG : 0.f;
+            }
+        }
+        __syncthreads();
+        st2_to_a2(A2);
         end_chunk(chunk);
     }
 
-    // viscous chunks: sqrt(eps) (J r_x q_x + J r_y q_y), sqrt(eps) (J s_x q_x + J s_y q_y)
+    // viscous chunks: sqrt(eps) (J r_x q_x + J r_y q_y), sqrt(eps) (J s_x q_x + J s_y q_y) at nodes
     if constexpr (AV) {
+        const float* ge = sGeo + e * 16;
+        const float jrx = ge[0], jry = ge[1], jsx = ge[2], jsy = ge[3];
+        const float se = sSe[e];
 #pragma unroll 1
         for (int ca = 0; ca < D::CA; ++ca, ++chunk) {
             unsigned char* A2 = begin_chunk(chunk);
@@ -458,11 +473,17 @@ __device__ void stage_tile_tc(const StageArgs<float>& p, long long e0, int ne, c
         }
     }
 
-    // ---------------- epilogue: L = D2 / J, stage combination
+    // ---------------- epilogue: L = D2 / J into shared memory, then a
+    // coalesced pass over the tile for the stage combination
+    for (int b = 0; b < 2; ++b)
+        while (ph.waits[b] < ph.commits[b]) {
+            if (!tc::mbar_wait(&bars[b], ph.waits[b] & 1)) atomicOr(err, 4);
+            ph.waits[b]++;
+        }
+    tc::fence_after_sync();
     {
-        const int last = chunk - 1;
-        if (!tc::mbar_wait(&bars[last & 1], (last >> 1) & 1)) atomicOr(err, 4);
-        tc::fence_after_sync();
+        float* sOut = sIO;
+        const float invJ = sGeo[e * 16 + 4];
         constexpr int per_half = N2 / 2;
 #pragma unroll
         for (int c0 = 0; c0 < per_half; c0 += 8) {
@@ -470,50 +491,135 @@ __device__ void stage_tile_tc(const StageArgs<float>& p, long long e0, int ne, c
             const int i0 = half * per_half + c0;
             tc::tmem_ld8(tD2 + lane_base + i0, x);
             tc::tmem_ld_wait();
-            if (live) {
-                const long long base = (k * 4 + v) * NP;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int ii = i0 + i;
-                    if (ii < NP) {
-                        const float Lv = x[i] * invJ;
-                        p.Uout[base + ii] = p.rhs_only ? Lv
-                                                       : (p.a != 0.f ? p.a * p.Un[base + ii] : 0.f) +
-                                                             p.b * (p.Us[base + ii] + p.dt * Lv);
-                    }
+            for (int i = 0; i < 8; ++i)
+                if (i0 + i < NP) sOut[row * NP + i0 + i] = x[i] * invJ;
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        const long long base = e0 * 4 * NP;
+        const int n4 = ne * NP;   // float4 groups: ne * 4 * NP / 4
+        const float4* us = reinterpret_cast<const float4*>(p.Us + base);
+        const float4* un = reinterpret_cast<const float4*>(p.Un + base);
+        float4* uo = reinterpret_cast<float4*>(p.Uout + base);
+        const float4* lo = reinterpret_cast<const float4*>(sOut);
+        for (int i = tid; i < n4; i += blockDim.x) {
+            const float4 L4 = lo[i];
+            float4 r;
+            if (p.rhs_only) {
+                r = L4;
+            } else {
+                const float4 s4 = us[i];
+                r = make_float4(p.b * (s4.x + p.dt * L4.x), p.b * (s4.y + p.dt * L4.y), p.b * (s4.z + p.dt * L4.z),
+                                p.b * (s4.w + p.dt * L4.w));
+                if (p.a != 0.f) {
+                    const float4 n4v = un[i];
+                    r.x += p.a * n4v.x;
+                    r.y += p.a * n4v.y;
+                    r.z += p.a * n4v.z;
+                    r.w += p.a * n4v.w;
                 }
             }
+            uo[i] = r;
         }
+        __syncthreads();   // staging and per-element data are reused by the next tile
     }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) tc::tmem_free(tmem, D::TMEM_COLS);
 }
 
-// Grid: affine tiles of 32 elements on the tensor cores, then curved tiles
-// on the CUDA-core body.
+// Persistent grid: each CTA sets up its operators, mbarriers and TMEM once,
+// takes tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...: affine tiles of
+// 32 elements on the tensor cores, then curved tiles on the CUDA-core body.
 template <int N, bool AV, int PREC>
 __global__ void __launch_bounds__(THREADS, 1) stage_kernel_tc(StageArgs<float> p, const unsigned char* ops_tc, int* err) {
     extern __shared__ __align__(128) unsigned char smem_tc[];
+    using S = TcSmem<N, AV>;
+    using L = TcLayout<N>;
     constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
+    constexpr int NF = TcDims<N>::NF, NP = TcDims<N>::NP;
+    const int tid = threadIdx.x;
     const long long nAff = (p.Kaff + ET - 1) / ET;
-    if ((long long)blockIdx.x < nAff) {
-        const long long e0 = (long long)blockIdx.x * ET;
-        stage_tile_tc<N, AV, PREC>(p, e0, (int)min((long long)ET, p.Kaff - e0), ops_tc, smem_tc, err);
-    } else {
-        TileRange t;
-        t.curved = true;
-        t.e0 = p.Kaff + ((long long)blockIdx.x - nAff) * EC;
-        t.ne = (int)min((long long)EC, p.K - t.e0);
-        if (t.ne > 0) stage_tile<N, float, AV>(p, t, smem_tc);
+    const long long nCur = (p.K - p.Kaff + EC - 1) / EC;
+    const bool any_affine = (long long)blockIdx.x < nAff;
+
+    uint32_t tmem = 0;
+    TcPhase ph;
+    if (any_affine) {
+        const int4* src = reinterpret_cast<const int4*>(ops_tc);
+        int4* dst = reinterpret_cast<int4*>(smem_tc);
+        for (int i = tid; i < L::B1_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+        if constexpr (AV)
+            for (int i = tid; i < L::B1Q_BYTES / 16; i += blockDim.x) dst[S::sB1Q / 16 + i] = src[L::B1Q / 16 + i];
+        for (int i = tid; i < S::NCHU * L::B2_CHUNK / 16; i += blockDim.x) dst[S::sB2 / 16 + i] = src[L::B2 / 16 + i];
+        const float* igs = reinterpret_cast<const float*>(ops_tc + L::IGF);
+        float* igd = reinterpret_cast<float*>(smem_tc + S::sIGF);
+        for (int i = tid; i < NF * NP; i += blockDim.x) igd[i] = igs[i];
+        uint64_t* bars = reinterpret_cast<uint64_t*>(smem_tc + S::sBAR);
+        if (tid == 0) {
+            for (int b = 0; b < 4; ++b) tc::mbar_init(&bars[b], 1);
+            tc::mbar_fence_init();
+        }
+        uint32_t* slot = reinterpret_cast<uint32_t*>(smem_tc + S::sTMEM);
+        if ((tid >> 5) == 0) tc::tmem_alloc(slot, TcDims<N>::TMEM_COLS);
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        tmem = *slot;
     }
+    for (long long t = blockIdx.x; t < nAff + nCur; t += gridDim.x) {
+        if (t < nAff) {
+            const long long e0 = t * ET;
+            stage_tile_tc<N, AV, PREC>(p, e0, (int)min((long long)ET, p.Kaff - e0), smem_tc, tmem, ph, err);
+        } else {
+            // curved tiles come last for every CTA: the CUDA-core body may now
+            // overwrite the operator region
+            __syncthreads();
+            TileRange tr;
+            tr.curved = true;
+            tr.e0 = p.Kaff + (t - nAff) * EC;
+            tr.ne = (int)min((long long)EC, p.K - tr.e0);
+            stage_tile<N, float, AV>(p, tr, smem_tc);
+            __syncthreads();
+        }
+    }
+    if (any_affine) {
+        tc::fence_before_sync();
+        __syncthreads();
+        if ((tid >> 5) == 0) tc::tmem_free(tmem, TcDims<N>::TMEM_COLS);
+    }
+}
+
+// Persistent grid size per instantiation: SMs x resident CTAs (shared memory
+// and TMEM columns both limit residency), set by prepare_tc before any launch.
+template <int N, bool AV, int PREC>
+struct TcGrid {
+    static inline int ctas = 0;
+};
+
+template <int N, bool AV, int PREC>
+int prepare_tc_t() {
+    auto kern = stage_kernel_tc<N, AV, PREC>;
+    const int sm = (int)tc_smem_bytes<N, AV>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return (int)e;
+    int occ = 0, dev = 0, nsm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THREADS, sm)) != cudaSuccess) return (int)e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)e;
+    const int by_tmem = 512 / TcDims<N>::TMEM_COLS;
+    occ = occ < by_tmem ? occ : by_tmem;
+    if (occ < 1) return (int)cudaErrorInvalidConfiguration;
+    TcGrid<N, AV, PREC>::ctas = nsm * occ;
+    return 0;
 }
 
 template <int N, bool AV, int PREC>
 int launch_stage_tc_t(const StageArgs<float>& a, const unsigned char* ops_tc, int* err, cudaStream_t st) {
     constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
-    const unsigned grid = (unsigned)((a.Kaff + ET - 1) / ET + (a.K - a.Kaff + EC - 1) / EC);
-    if (grid == 0) return 0;
+    const long long tiles = (a.Kaff + ET - 1) / ET + (a.K - a.Kaff + EC - 1) / EC;
+    if (tiles == 0) return 0;
+    const int ctas = TcGrid<N, AV, PREC>::ctas;
+    if (ctas <= 0) return (int)cudaErrorNotReady;   // prepare_tc was not called
+    const unsigned grid = (unsigned)(tiles < ctas ? tiles : ctas);
     stage_kernel_tc<N, AV, PREC><<<grid, THREADS, tc_smem_bytes<N, AV>(), st>>>(a, ops_tc, err);
     return (int)cudaGetLastError();
 }
@@ -530,15 +636,10 @@ int launch_stage_tc(const StageArgs<float>& a, int av, int prec, const unsigned 
 
 template <int N>
 int prepare_tc() {
-    int e = 0;
-    e |= (int)cudaFuncSetAttribute(stage_kernel_tc<N, false, PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)tc_smem_bytes<N, false>());
-    e |= (int)cudaFuncSetAttribute(stage_kernel_tc<N, true, PREC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)tc_smem_bytes<N, true>());
-    e |= (int)cudaFuncSetAttribute(stage_kernel_tc<N, false, PREC_BF16X3>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes<N, false>());
-    e |= (int)cudaFuncSetAttribute(stage_kernel_tc<N, true, PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)tc_smem_bytes<N, true>());
+    int e = prepare_tc_t<N, false, PREC_TF32>();
+    if (!e) e = prepare_tc_t<N, true, PREC_TF32>();
+    if (!e) e = prepare_tc_t<N, false, PREC_BF16X3>();
+    if (!e) e = prepare_tc_t<N, true, PREC_BF16X3>();
     return e;
 }
 

@@ -120,7 +120,8 @@ class ServeLoop:
         self.prec = prec
         self.clock = clock
         self.used = 0
-        self.log = []
+        self.peak_used = 0
+        self.peak_active = 0
 
     def _admit(self, req, now):
         p = B.make_params(u_inf=req.u_inf, prec=self.prec)
@@ -129,6 +130,7 @@ class ServeLoop:
         B.dg_set_state(self.ctx, req.handle, req.U0)
         req.bytes = B.dg_mesh_bytes(self.ctx, req.handle)
         self.used += req.bytes
+        self.peak_used = max(self.peak_used, self.used)
         req.admitted = now
 
     def _retire(self, req, now, reason):
@@ -149,7 +151,9 @@ class ServeLoop:
         while pending or active:
             now = self.clock() - t0
             while pending and pending[0].arrival <= now:
-                est = estimate_bytes(pending[0].K, pending[0].N)
+                nxt = pending[0]
+                curved = int(np.any(nxt.mesh.bc == 1, axis=1).sum()) if nxt.mesh is not None else 0
+                est = estimate_bytes(nxt.K, nxt.N, curved=curved)
                 if est > self.budget:
                     raise ValueError("request %d exceeds the whole HBM budget" % pending[0].rid)
                 if self.used + est > self.budget:
@@ -161,6 +165,7 @@ class ServeLoop:
                 if pending:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
                 continue
+            self.peak_active = max(self.peak_active, len(active))
             n = min(self.check_every, min(self.max_steps - r.steps for r in active))
             B.dg_batch_step(self.ctx, [r.handle for r in active], [r.dt for r in active], n)
             for r in active:
