@@ -342,72 +342,68 @@ __global__ void __launch_bounds__(THREADS) stage_kernel(StageArgs<Real> p) {
 }
 
 // ---------------------------------------------------------------------------
-// Persson-Peraire sensor: eps_k from the density (paper Sec. 2).  A warp
-// takes 32 elements; for each, the lanes share the sums over modes (affine:
-// S = sum_{deg N} u^2 / sum u^2 with u = V^-1 rho, which is the cubature
-// form for constant J and an orthonormal basis) or over cubature points
-// (curved: both integrals with J), accumulated in the state precision; lane
-// e then keeps element e's two sums and takes the ratio, log10 and the sine
-// ramp in FP64 for its element, so the FP64 work runs 32 elements wide.
+// Persson-Peraire sensor: eps_k from the density (paper Sec. 2), one thread
+// per element.  The block stages the densities of its 128 elements in shared
+// memory with coalesced loads; V^-1 (affine) or I_cub and I_top (curved)
+// are read as broadcasts.  Affine: S = sum_{deg N} u^2 / sum u^2 with
+// u = V^-1 rho (the cubature form for constant J and an orthonormal basis);
+// curved: both integrals by cubature with J.  Sums in the state precision,
+// ratio, log10 and the sine ramp in FP64.
 // ---------------------------------------------------------------------------
+constexpr int SENSOR_THREADS = 128;
+
 template <int N, typename Real>
-__global__ void __launch_bounds__(THREADS) sensor_kernel(StageArgs<Real> p, Real* eps_out) {
+__global__ void __launch_bounds__(SENSOR_THREADS) sensor_kernel(StageArgs<Real> p, Real* eps_out) {
     constexpr int NP = np_of(N), NQ = nq_of(N);
     constexpr int NLOW = N * (N + 1) / 2;  // modes of degree <= N-1 come first
     constexpr OpsLayout L = ops_layout(N);
-    const int lane = threadIdx.x & 31;
-    const long long k0 = ((long long)blockIdx.x * (THREADS / 32) + (threadIdx.x >> 5)) * 32;
-    if (k0 >= p.K) return;
-    Real my_num = 0, my_den = 0;
-    for (int e = 0; e < 32; ++e) {
-        const long long k = k0 + e;
-        if (k >= p.K) break;
-        const Real* rho = p.Us + k * 4 * NP;  // variable 0
-        Real num = 0, den = 0;
-        if (k < p.Kaff) {
-            if (lane < NP) {
-                Real um = 0;
+    __shared__ Real sRho[SENSOR_THREADS * (NP + 1)];
+    __shared__ Real sV[NP * NP];
+    const long long k0 = (long long)blockIdx.x * SENSOR_THREADS;
+    const int nb = (int)min((long long)SENSOR_THREADS, p.K - k0);
+    for (int i = threadIdx.x; i < NP * NP; i += SENSOR_THREADS) sV[i] = p.ops[L.vinvt + i];
+    for (int i = threadIdx.x; i < nb * NP; i += SENSOR_THREADS) {
+        const int e = i / NP, j = i - e * NP;
+        sRho[e * (NP + 1) + j] = p.Us[(k0 + e) * 4 * NP + j];
+    }
+    __syncthreads();
+    const int e = threadIdx.x;
+    if (e >= nb) return;
+    const long long k = k0 + e;
+    const Real* rho = sRho + e * (NP + 1);
+    Real num = 0, den = 0;
+    if (k < p.Kaff) {
+#pragma unroll 1
+        for (int m = 0; m < NP; ++m) {
+            Real um = 0;
 #pragma unroll
-                for (int j = 0; j < NP; ++j) um += p.ops[L.vinvt + j * NP + lane] * rho[j];
-                den = um * um;
-                num = (lane >= NLOW) ? den : Real(0);
-            }
-        } else {
-            const Real* g = p.geoC + (k - p.Kaff) * curved_stride(N);
-            for (int qn = lane; qn < NQ; qn += 32) {
-                Real a = 0, b = 0;
-                for (int j = 0; j < NP; ++j) {
-                    a += p.ops[L.icub + j * NQ + qn] * rho[j];
-                    b += p.ops[L.itopt + j * NQ + qn] * rho[j];
-                }
-                const Real wj = p.ops[L.w + qn] * g[4 * NQ + qn];
-                den += wj * a * a;
-                num += wj * b * b;
-            }
+            for (int j = 0; j < NP; ++j) um += sV[j * NP + m] * rho[j];
+            den += um * um;
+            if (m >= NLOW) num += um * um;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            num += __shfl_xor_sync(0xffffffffu, num, o);
-            den += __shfl_xor_sync(0xffffffffu, den, o);
-        }
-        if (lane == e) {
-            my_num = num;
-            my_den = den;
+    } else {
+        const Real* g = p.geoC + (k - p.Kaff) * curved_stride(N);
+        for (int qn = 0; qn < NQ; ++qn) {
+            Real a = 0, b = 0;
+            for (int j = 0; j < NP; ++j) {
+                a += p.ops[L.icub + j * NQ + qn] * rho[j];
+                b += p.ops[L.itopt + j * NQ + qn] * rho[j];
+            }
+            const Real wj = p.ops[L.w + qn] * g[4 * NQ + qn];
+            den += wj * a * a;
+            num += wj * b * b;
         }
     }
-    const long long k = k0 + lane;
-    if (k < p.K) {
-        const double num = (double)my_num, den = (double)my_den;
-        double e = 0.0;
-        if (num > 0.0 && den > 0.0) {
-            const double s = log10(num / den);
-            if (s > p.s0 + p.kappa)
-                e = p.eps0;
-            else if (s >= p.s0 - p.kappa)
-                e = 0.5 * p.eps0 * (1.0 + sin(M_PI * (s - p.s0) / (2.0 * p.kappa)));
-        }
-        eps_out[k] = (Real)e;
+    double eps = 0.0;
+    const double dn = (double)num, dd = (double)den;
+    if (dn > 0.0 && dd > 0.0) {
+        const double s = log10(dn / dd);
+        if (s > p.s0 + p.kappa)
+            eps = p.eps0;
+        else if (s >= p.s0 - p.kappa)
+            eps = 0.5 * p.eps0 * (1.0 + sin(M_PI * (s - p.s0) / (2.0 * p.kappa)));
     }
+    eps_out[k] = (Real)eps;
 }
 
 // ---------------------------------------------------------------------------
@@ -587,10 +583,9 @@ int launch_stage(const StageArgs<Real>& a, int av, cudaStream_t st) {
 
 template <int N, typename Real>
 int launch_sensor(const StageArgs<Real>& a, Real* eps_out, cudaStream_t st) {
-    const long long per = (THREADS / 32) * 32;   // elements per block
-    const unsigned grid = (unsigned)((a.K + per - 1) / per);
+    const unsigned grid = (unsigned)((a.K + SENSOR_THREADS - 1) / SENSOR_THREADS);
     if (grid == 0) return 0;
-    sensor_kernel<N, Real><<<grid, THREADS, 0, st>>>(a, eps_out);
+    sensor_kernel<N, Real><<<grid, SENSOR_THREADS, 0, st>>>(a, eps_out);
     return (int)cudaGetLastError();
 }
 
