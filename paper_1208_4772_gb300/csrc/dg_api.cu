@@ -172,6 +172,59 @@ const RefOps* get_refops(int N, std::string& err) {
     return p;
 }
 
+// Device order of a set of elements: consecutive patches of `tile`
+// elements grown breadth-first across interior faces, each new patch seeded
+// from the frontier the previous one left, so that most face neighbours of
+// a tile lie in the same tile and consecutive tiles are adjacent in space.
+void compact_order(const std::vector<long long>& elems, const int32_t* EToE, const int8_t* bc, int64_t K, int tile,
+                   std::vector<long long>& out) {
+    std::vector<char> member(K, 0), placed(K, 0), queued(K, 0);
+    for (long long e : elems) member[e] = 1;
+    std::vector<long long> queue, frontier;
+    size_t scan = 0, done = 0;
+    auto next_seed = [&]() -> long long {
+        while (!frontier.empty()) {
+            const long long c = frontier.back();
+            frontier.pop_back();
+            if (!placed[c]) return c;
+        }
+        while (scan < elems.size() && placed[elems[scan]]) ++scan;
+        return scan < elems.size() ? elems[scan] : -1;
+    };
+    while (done < elems.size()) {
+        int count = 0;
+        queue.clear();
+        size_t head = 0;
+        while (count < tile && done < elems.size()) {
+            if (head == queue.size()) {
+                const long long seed = next_seed();
+                if (seed < 0) break;
+                queue.push_back(seed);
+                queued[seed] = 1;
+            }
+            const long long e = queue[head++];
+            if (placed[e]) continue;
+            placed[e] = 1;
+            out.push_back(e);
+            ++done;
+            ++count;
+            for (int f = 0; f < 3; ++f) {
+                if (bc[3 * e + f] != DG_BC_INTERIOR) continue;
+                const long long nb = EToE[3 * e + f];
+                if (member[nb] && !placed[nb] && !queued[nb]) {
+                    queued[nb] = 1;
+                    queue.push_back(nb);
+                }
+            }
+        }
+        // discovered but not placed: seeds for the next patch
+        for (size_t i = head; i < queue.size(); ++i) {
+            queued[queue[i]] = 0;
+            if (!placed[queue[i]]) frontier.push_back(queue[i]);
+        }
+    }
+}
+
 template <typename Real>
 std::vector<Real> to_real(const std::vector<double>& v) {
     return std::vector<Real>(v.begin(), v.end());
@@ -250,6 +303,8 @@ StageArgs<Real> make_args(const MeshData& m, const void* Us, const void* Un, voi
     s.s0 = m.s0;
     s.kappa = m.p.kappa;
     s.eps0 = m.p.eps0;
+    s.S_lo = std::pow(10.0, m.s0 - m.p.kappa);
+    s.S_hi = std::pow(10.0, m.s0 + m.p.kappa);
     return s;
 }
 
@@ -522,14 +577,19 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
     }
     auto* m = new MeshData();
     m->N = N; m->Np = NP; m->Nq = NQ; m->Ng = NG; m->Nf = NF;
+    m->perm.reserve(K);
     m->K = K;
     m->p = *p;
     m->prec = p->prec;
     m->rsize = (p->prec == DG_FP64_DEBUG) ? 8 : 4;
     m->s0 = std::isnan(p->s0) ? std::log10(1.0 / std::pow((double)N, 4)) : p->s0;
-    m->perm.reserve(K);
-    for (int64_t k = 0; k < K; ++k)
-        if (!curved[k]) m->perm.push_back(k);
+    {
+        std::vector<long long> affine;
+        affine.reserve(K);
+        for (int64_t k = 0; k < K; ++k)
+            if (!curved[k]) affine.push_back(k);
+        compact_order(affine, EToE, bc, K, 32, m->perm);
+    }
     m->Kaff = (long long)m->perm.size();
     for (int64_t k = 0; k < K; ++k)
         if (curved[k]) m->perm.push_back(k);

@@ -71,8 +71,9 @@ struct StageArgs {
     long long K, Kaff;
     Real gamma;
     Real uinf[4];
-    // sensor parameters (AV)
+    // sensor parameters (AV); ramp band of S = 10^(s0 -+ kappa), set on the host
     double s0, kappa, eps0;
+    double S_lo, S_hi;
 };
 
 // Per-degree launchers (kernels_n<N>.cu).  Return cudaError_t as int.

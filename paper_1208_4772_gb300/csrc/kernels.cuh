@@ -394,14 +394,21 @@ __global__ void __launch_bounds__(SENSOR_THREADS) sensor_kernel(StageArgs<Real> 
             num += wj * b * b;
         }
     }
+    // s = log10(num/den) is needed only inside the ramp band: outside it the
+    // two comparisons (in FP64, without a division) decide, which keeps the
+    // FP64 transcendentals off the elements where eps is 0 or eps0
     double eps = 0.0;
     const double dn = (double)num, dd = (double)den;
-    if (dn > 0.0 && dd > 0.0) {
-        const double s = log10(dn / dd);
-        if (s > p.s0 + p.kappa)
+    if (dn > 0.0 && dd > 0.0 && dn >= p.S_lo * dd) {
+        if (dn > p.S_hi * dd) {
             eps = p.eps0;
-        else if (s >= p.s0 - p.kappa)
-            eps = 0.5 * p.eps0 * (1.0 + sin(M_PI * (s - p.s0) / (2.0 * p.kappa)));
+        } else {
+            const double s = log10(dn / dd);
+            if (s > p.s0 + p.kappa)
+                eps = p.eps0;
+            else if (s >= p.s0 - p.kappa)
+                eps = 0.5 * p.eps0 * (1.0 + sin(M_PI * (s - p.s0) / (2.0 * p.kappa)));
+        }
     }
     eps_out[k] = (Real)eps;
 }

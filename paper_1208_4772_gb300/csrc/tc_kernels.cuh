@@ -68,29 +68,44 @@ struct TcLayout {
     static constexpr int TOTAL = IGF + D::NF * D::NP * 4;
 };
 
+// Shared-memory carve-up of the tensor-core kernel.  Regions whose
+// lifetimes do not overlap share storage: the out-of-tile neighbour traces
+// reuse the G1 operand region once G1 has completed, the cubature transpose
+// stage reuses the trace region once the face fluxes are done, and the
+// epilogue reuses the G2 staging rows.  One or two A2 buffers: two when the
+// CTA then still fits twice on an SM (or cannot fit twice anyway).
 template <int N, bool AV>
 struct TcSmem {
     using D = TcDims<N>;
     using L = TcLayout<N>;
     static constexpr int NCHU = D::CF + D::CQ + (AV ? D::CA : 0);  // chunks used
     static constexpr int al(int x) { return (x + 127) / 128 * 128; }
+    static constexpr int mx(int a, int b) { return a > b ? a : b; }
     // constant region: operators, loaded once per CTA
     static constexpr int sB1 = 0;
     static constexpr int sB1Q = sB1 + L::B1_BYTES;
     static constexpr int sB2 = sB1Q + (AV ? L::B1Q_BYTES : 0);
     static constexpr int sIGF = sB2 + NCHU * L::B2_CHUNK;
     // per-tile region
-    static constexpr int sA1 = al(sIGF + D::NF * D::NP * 4);               // [128][NPK] (x3 with AV)
     static constexpr int A1_BYTES = 128 * D::NPK * 4;
-    static constexpr int sA2 = sA1 + A1_BYTES * (AV ? 3 : 1);               // 2 x [128][32]
+    static constexpr int NBV_C = AV ? 8 : 4;                                  // values per face point
+    static constexpr int NBV_BYTES = 32 * D::NF * NBV_C * 4;
+    static constexpr int sA1 = al(sIGF + D::NF * D::NP * 4);                  // G1 operands, then neighbour traces
+    static constexpr int A1_REGION = al(mx(A1_BYTES * (AV ? 3 : 1), NBV_BYTES));
     static constexpr int A2_BYTES = 128 * 32 * 4;
-    static constexpr int sTR = sA2 + 2 * A2_BYTES;                           // traces [128][NFS] (x2 with AV)
     static constexpr int TR_FLOATS = 128 * D::NFS;
-    static constexpr int sIO = al(sTR + TR_FLOATS * 4 * (AV ? 2 : 1));       // staging
     static constexpr int ST1 = 32 * 68;                                      // [e][16 q x 4 v + 4]
     static constexpr int ST2 = 128 * 36;                                     // [row][32 + 4]
-    static constexpr int IO_FLOATS = (32 * 4 * D::NP > ST1 + ST2) ? 32 * 4 * D::NP : ST1 + ST2;
-    static constexpr int sMEAN = al(sIO + IO_FLOATS * 4);                     // [128]
+    static constexpr int TR_REGION = al(mx(TR_FLOATS * 4 * (AV ? 2 : 1), ST1 * 4));
+    static constexpr int IO_REGION = al(mx(ST2 * 4, 32 * 4 * D::NP * 4));
+    static constexpr int SMALL = 128 * 4 + 32 * 16 * 4 + 32 * 8 * 4 + 32 * 4 + 32 * 16 + 4 * 8 + 16;
+    static constexpr int total_for(int nbuf) { return sA1 + A1_REGION + nbuf * A2_BYTES + TR_REGION + IO_REGION + SMALL; }
+    static constexpr int TWO_PER_SM = 113 * 1024;
+    static constexpr int NBUF = (total_for(2) <= TWO_PER_SM || total_for(1) > TWO_PER_SM) ? 2 : 1;
+    static constexpr int sA2 = sA1 + A1_REGION;
+    static constexpr int sTR = sA2 + NBUF * A2_BYTES;
+    static constexpr int sIO = sTR + TR_REGION;
+    static constexpr int sMEAN = sIO + IO_REGION;                            // [128]
     static constexpr int sGEO = sMEAN + 128 * 4;                             // [32][16]
     static constexpr int sFB = sGEO + 32 * 16 * 4;                           // [32][8] mean flux
     static constexpr int sSE = sFB + 32 * 8 * 4;                             // [32] sqrt(eps)
@@ -98,13 +113,12 @@ struct TcSmem {
     static constexpr int sBAR = sNB + 32 * 16;                               // 4 mbarriers
     static constexpr int sTMEM = sBAR + 4 * 8;
     static constexpr int TOTAL = sTMEM + 16;
+    static_assert(TOTAL <= 232448, "tensor-core tile exceeds the shared-memory limit");
 };
 
 template <int N, bool AV>
 constexpr size_t tc_smem_bytes() {
-    const size_t a = TcSmem<N, AV>::TOTAL;
-    const size_t b = Tile<N, float>::smem_stage(AV);
-    return a > b ? a : b;
+    return TcSmem<N, AV>::TOTAL;
 }
 
 // Writes 8 consecutive K values (k0 multiple of 8) of one row of an A
@@ -191,8 +205,8 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     float* sTr = reinterpret_cast<float*>(smem + S::sTR);
     float* sQn = sTr + S::TR_FLOATS;            // AV: sqrt(eps) q.n at own face points
     float* sIO = reinterpret_cast<float*>(smem + S::sIO);
-    float* st1 = sIO;                           // [e][q x 4 + 4]
-    float* st2 = sIO + S::ST1;                  // [row][36]
+    float* st1 = sTr;                           // [e][q x 4 + 4], after the face fluxes
+    float* st2 = sIO;                           // [row][36]
     const float* sIgF = reinterpret_cast<const float*>(smem + S::sIGF);
     unsigned char* A1 = smem + S::sA1;
 
@@ -273,6 +287,44 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     if (!tc::mbar_wait(&bars[2], ph.g1 & 1)) atomicOr(err, 1);
     ph.g1++;
     tc::fence_after_sync();
+    // out-of-tile neighbours' traces at the reversed face points, from their
+    // states in L2, into the G1 operand region (G1 has completed)
+    float* sNbv = reinterpret_cast<float*>(smem + S::sA1);
+    for (int it = tid; it < 32 * NF; it += blockDim.x) {
+        const int ee = it / NF, fg = it - ee * NF;
+        const int f = fg / NG, gg = fg - f * NG;
+        const int4 nbw = sNb[ee];
+        const int nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
+        const long long nbl = (long long)nb - e0;
+        if (ee >= ne || code_bc(nbw.w, f) != 0 || (nbl >= 0 && nbl < ne)) continue;
+        const int fgn = code_face(nbw.w, f) * NG + (NG - 1 - gg);
+        const float* ig = sIgF + fgn * NP;
+        const float* un = p.Us + (long long)nb * 4 * NP;
+        float* dst = sNbv + (ee * NF + fg) * S::NBV_C;
+#pragma unroll 1
+        for (int w = 0; w < 4; ++w) {
+            float a = 0.f;
+#pragma unroll 5
+            for (int j = 0; j < NP; ++j) a += ig[j] * __ldg(un + w * NP + j);
+            dst[w] = a;
+        }
+        if constexpr (AV) {
+            const float* ge = sGeo + ee * 16;
+            const float nx = ge[5 + 3 * f], ny = ge[6 + 3 * f];
+            const float sen = sqrtf(__ldg(p.eps + nb));
+            const float* qn_ = p.q + (long long)nb * 8 * NP;
+#pragma unroll 1
+            for (int w = 0; w < 4; ++w) {
+                float ax = 0.f, ay = 0.f;
+#pragma unroll 5
+                for (int j = 0; j < NP; ++j) {
+                    ax += ig[j] * __ldg(qn_ + w * NP + j);
+                    ay += ig[j] * __ldg(qn_ + (4 + w) * NP + j);
+                }
+                dst[4 + w] = sen * (ax * nx + ay * ny);
+            }
+        }
+    }
 
     // ---------------- own traces (and sqrt(eps) q.n) to shared memory
     const float mean_v = sMean[row];
@@ -309,7 +361,7 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     // ---------------- G2 chunk pipeline
     int chunk = 0;
     auto begin_chunk = [&](int c) -> unsigned char* {
-        const int buf = c & 1;
+        const int buf = c % S::NBUF;
         // the buffer is free once every product issued from it has completed
         while (ph.waits[buf] < ph.commits[buf]) {
             if (!tc::mbar_wait(&bars[buf], ph.waits[buf] & 1)) atomicOr(err, 2);
@@ -320,7 +372,7 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     auto end_chunk = [&](int c) {
         tc::fence_async_smem();
         __syncthreads();
-        const int buf = c & 1;
+        const int buf = c % S::NBUF;
         if (tid == 0) {
             tc::fence_after_sync();
             issue_mma<PREC>(tD2, smem + S::sA2 + buf * S::A2_BYTES, smem + S::sB2 + c * TcLayout<N>::B2_CHUNK, N2,
@@ -367,15 +419,8 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
 #pragma unroll
                 for (int w = 0; w < 4; ++w) Up[w] = sTr[((int)nbl * 4 + w) * NFS + fgn];
             } else {
-                const float* un = p.Us + (long long)nb * 4 * NP;
-                const float* ig = sIgF + fgn * NP;
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    float a = 0.f;
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) a += ig[j] * __ldg(un + w * NP + j);
-                    Up[w] = a;
-                }
+                for (int w = 0; w < 4; ++w) Up[w] = sNbv[(ee * NF + fg) * S::NBV_C + w];
             }
             float Fn[4];
             llf_flux(Um, Up, nx, ny, p.gamma, Fn);
@@ -389,15 +434,7 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
                     } else if (in_tile) {
                         other = -sQn[((int)nbl * 4 + w) * NFS + fgn];
                     } else {
-                        const float* qn_ = p.q + (long long)nb * 8 * NP;
-                        const float* ig = sIgF + fgn * NP;
-                        float ax = 0.f, ay = 0.f;
-#pragma unroll
-                        for (int j = 0; j < NP; ++j) {
-                            ax += ig[j] * __ldg(qn_ + w * NP + j);
-                            ay += ig[j] * __ldg(qn_ + (4 + w) * NP + j);
-                        }
-                        other = sqrtf(__ldg(p.eps + nb)) * (ax * nx + ay * ny);
+                        other = sNbv[(ee * NF + fg) * S::NBV_C + 4 + w];
                     }
                     Fn[w] -= 0.5f * (own + other);
                 }
@@ -526,19 +563,19 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     }
 }
 
-// Persistent grid: each CTA sets up its operators, mbarriers and TMEM once,
-// takes tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...: affine tiles of
-// 32 elements on the tensor cores, then curved tiles on the CUDA-core body.
+// Persistent grid: each CTA sets up its operators, mbarriers and TMEM once
+// and takes the affine tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (32 elements each) on the tensor cores.  Curved tiles run the CUDA-core
+// body in a second launch (stage_kernel_curved).
 template <int N, bool AV, int PREC>
 __global__ void __launch_bounds__(THREADS, 1) stage_kernel_tc(StageArgs<float> p, const unsigned char* ops_tc, int* err) {
     extern __shared__ __align__(128) unsigned char smem_tc[];
     using S = TcSmem<N, AV>;
     using L = TcLayout<N>;
-    constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
+    constexpr int ET = TcDims<N>::E;
     constexpr int NF = TcDims<N>::NF, NP = TcDims<N>::NP;
     const int tid = threadIdx.x;
     const long long nAff = (p.Kaff + ET - 1) / ET;
-    const long long nCur = (p.K - p.Kaff + EC - 1) / EC;
     const bool any_affine = (long long)blockIdx.x < nAff;
 
     uint32_t tmem = 0;
@@ -565,27 +602,27 @@ __global__ void __launch_bounds__(THREADS, 1) stage_kernel_tc(StageArgs<float> p
         tc::fence_after_sync();
         tmem = *slot;
     }
-    for (long long t = blockIdx.x; t < nAff + nCur; t += gridDim.x) {
-        if (t < nAff) {
-            const long long e0 = t * ET;
-            stage_tile_tc<N, AV, PREC>(p, e0, (int)min((long long)ET, p.Kaff - e0), smem_tc, tmem, ph, err);
-        } else {
-            // curved tiles come last for every CTA: the CUDA-core body may now
-            // overwrite the operator region
-            __syncthreads();
-            TileRange tr;
-            tr.curved = true;
-            tr.e0 = p.Kaff + (t - nAff) * EC;
-            tr.ne = (int)min((long long)EC, p.K - tr.e0);
-            stage_tile<N, float, AV>(p, tr, smem_tc);
-            __syncthreads();
-        }
+    for (long long t = blockIdx.x; t < nAff; t += gridDim.x) {
+        const long long e0 = t * ET;
+        stage_tile_tc<N, AV, PREC>(p, e0, (int)min((long long)ET, p.Kaff - e0), smem_tc, tmem, ph, err);
     }
     if (any_affine) {
         tc::fence_before_sync();
         __syncthreads();
         if ((tid >> 5) == 0) tc::tmem_free(tmem, TcDims<N>::TMEM_COLS);
     }
+}
+
+// Curved tiles only (CUDA-core body), after the tensor-core launch.
+template <int N, bool AV>
+__global__ void __launch_bounds__(THREADS) stage_kernel_curved(StageArgs<float> p) {
+    extern __shared__ __align__(16) unsigned char smem_cc[];
+    constexpr int EC = Tile<N, float>::E;
+    TileRange tr;
+    tr.curved = true;
+    tr.e0 = p.Kaff + (long long)blockIdx.x * EC;
+    tr.ne = (int)min((long long)EC, p.K - tr.e0);
+    if (tr.ne > 0) stage_tile<N, float, AV>(p, tr, smem_cc);
 }
 
 // Persistent grid size per instantiation: SMs x resident CTAs (shared memory
@@ -609,18 +646,24 @@ int prepare_tc_t() {
     occ = occ < by_tmem ? occ : by_tmem;
     if (occ < 1) return (int)cudaErrorInvalidConfiguration;
     TcGrid<N, AV, PREC>::ctas = nsm * occ;
-    return 0;
+    e = cudaFuncSetAttribute(stage_kernel_curved<N, AV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Tile<N, float>::smem_stage(AV));
+    return (int)e;
 }
 
 template <int N, bool AV, int PREC>
 int launch_stage_tc_t(const StageArgs<float>& a, const unsigned char* ops_tc, int* err, cudaStream_t st) {
     constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
-    const long long tiles = (a.Kaff + ET - 1) / ET + (a.K - a.Kaff + EC - 1) / EC;
-    if (tiles == 0) return 0;
-    const int ctas = TcGrid<N, AV, PREC>::ctas;
-    if (ctas <= 0) return (int)cudaErrorNotReady;   // prepare_tc was not called
-    const unsigned grid = (unsigned)(tiles < ctas ? tiles : ctas);
-    stage_kernel_tc<N, AV, PREC><<<grid, THREADS, tc_smem_bytes<N, AV>(), st>>>(a, ops_tc, err);
+    const long long tiles = (a.Kaff + ET - 1) / ET;
+    if (tiles > 0) {
+        const int ctas = TcGrid<N, AV, PREC>::ctas;
+        if (ctas <= 0) return (int)cudaErrorNotReady;   // prepare_tc was not called
+        const unsigned grid = (unsigned)(tiles < ctas ? tiles : ctas);
+        stage_kernel_tc<N, AV, PREC><<<grid, THREADS, tc_smem_bytes<N, AV>(), st>>>(a, ops_tc, err);
+    }
+    const long long ctiles = (a.K - a.Kaff + EC - 1) / EC;
+    if (ctiles > 0)
+        stage_kernel_curved<N, AV><<<(unsigned)ctiles, THREADS, Tile<N, float>::smem_stage(AV), st>>>(a);
     return (int)cudaGetLastError();
 }
 
