@@ -357,20 +357,21 @@ __global__ void __launch_bounds__(SENSOR_THREADS) sensor_kernel(StageArgs<Real> 
     constexpr int NP = np_of(N), NQ = nq_of(N);
     constexpr int NLOW = N * (N + 1) / 2;  // modes of degree <= N-1 come first
     constexpr OpsLayout L = ops_layout(N);
-    __shared__ Real sRho[SENSOR_THREADS * (NP + 1)];
+    constexpr int RS = NP | 1;   // odd row stride: conflict-free column reads
+    __shared__ Real sRho[SENSOR_THREADS * RS];
     __shared__ Real sV[NP * NP];
     const long long k0 = (long long)blockIdx.x * SENSOR_THREADS;
     const int nb = (int)min((long long)SENSOR_THREADS, p.K - k0);
     for (int i = threadIdx.x; i < NP * NP; i += SENSOR_THREADS) sV[i] = p.ops[L.vinvt + i];
     for (int i = threadIdx.x; i < nb * NP; i += SENSOR_THREADS) {
         const int e = i / NP, j = i - e * NP;
-        sRho[e * (NP + 1) + j] = p.Us[(k0 + e) * 4 * NP + j];
+        sRho[e * RS + j] = p.Us[(k0 + e) * 4 * NP + j];
     }
     __syncthreads();
     const int e = threadIdx.x;
     if (e >= nb) return;
     const long long k = k0 + e;
-    const Real* rho = sRho + e * (NP + 1);
+    const Real* rho = sRho + e * RS;
     Real num = 0, den = 0;
     if (k < p.Kaff) {
 #pragma unroll 1
