@@ -105,11 +105,22 @@ int dispatch_stage_tc(int N, const StageArgs<float>& a, int av, int prec, const 
 }
 int dispatch_prepare_tc(int N) {
     switch (N) {
-        case 2: return prepare_tc<2>();
-        case 3: return prepare_tc<3>();
-        case 4: return prepare_tc<4>();
-        case 5: return prepare_tc<5>();
-        case 6: return prepare_tc<6>();
+        case 2: { int e = prepare_tc<2>(); return e ? e : prepare_grad_tc<2>(); }
+        case 3: { int e = prepare_tc<3>(); return e ? e : prepare_grad_tc<3>(); }
+        case 4: { int e = prepare_tc<4>(); return e ? e : prepare_grad_tc<4>(); }
+        case 5: { int e = prepare_tc<5>(); return e ? e : prepare_grad_tc<5>(); }
+        case 6: { int e = prepare_tc<6>(); return e ? e : prepare_grad_tc<6>(); }
+    }
+    return (int)cudaErrorInvalidValue;
+}
+int dispatch_grad_tc(int N, const StageArgs<float>& a, float* q, int prec, const unsigned char* ops, int* err,
+                     cudaStream_t st) {
+    switch (N) {
+        case 2: return launch_grad_tc<2>(a, q, prec, ops, err, st);
+        case 3: return launch_grad_tc<3>(a, q, prec, ops, err, st);
+        case 4: return launch_grad_tc<4>(a, q, prec, ops, err, st);
+        case 5: return launch_grad_tc<5>(a, q, prec, ops, err, st);
+        case 6: return launch_grad_tc<6>(a, q, prec, ops, err, st);
     }
     return (int)cudaErrorInvalidValue;
 }
@@ -337,7 +348,17 @@ int enqueue_stage_t(const MeshData& m, const void* Us, const void* Un, void* out
         }
         {
             ProfScope ps(m, st, 1);
-            if ((e = dispatch_grad<Real>(m.N, s, (Real*)m.q, st))) return e;
+            if constexpr (sizeof(Real) == 4) {
+                if (tensor_prec(m.prec)) {
+                    if ((e = dispatch_grad_tc(m.N, s, (float*)m.q, m.prec == DG_TF32 ? 1 : 2,
+                                              (const unsigned char*)m.ops_tc, m.err, st)))
+                        return e;
+                } else if ((e = dispatch_grad<Real>(m.N, s, (Real*)m.q, st))) {
+                    return e;
+                }
+            } else if ((e = dispatch_grad<Real>(m.N, s, (Real*)m.q, st))) {
+                return e;
+            }
         }
     }
     ProfScope ps(m, st, 2);

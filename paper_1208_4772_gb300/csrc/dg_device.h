@@ -89,6 +89,10 @@ template <int N>
 int launch_stage_tc(const StageArgs<float>& a, int av, int prec, const unsigned char* ops_tc, int* err,
                     cudaStream_t st);
 template <int N> int prepare_tc();
+template <int N>
+int launch_grad_tc(const StageArgs<float>& a, float* q_out, int prec, const unsigned char* ops_tc, int* err,
+                   cudaStream_t st);
+template <int N> int prepare_grad_tc();
 struct RefOps;
 template <int N> std::vector<uint8_t> pack_ops_tc(const RefOps& R, int prec);
 

@@ -333,6 +333,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileR
     }
 }
 
+// Out-of-line copies of the CUDA-core tile bodies, called from the
+// persistent tensor-core kernels for curved tiles so that they do not add
+// to those kernels' register allocation.
+template <int N, typename Real, bool AV>
+__device__ __noinline__ void stage_tile_call(const StageArgs<Real>& p, const TileRange& t, unsigned char* smem) {
+    stage_tile<N, Real, AV>(p, t, smem);
+}
+
 template <int N, typename Real, bool AV>
 __global__ void __launch_bounds__(THREADS) stage_kernel(StageArgs<Real> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -423,11 +431,11 @@ __global__ void __launch_bounds__(SENSOR_THREADS) sensor_kernel(StageArgs<Real> 
 // cubature nodes with per-node factors and apply M_k^-1.
 // ---------------------------------------------------------------------------
 template <int N, typename Real>
-__global__ void __launch_bounds__(THREADS) grad_kernel(StageArgs<Real> p, Real* q_out) {
+__device__ __forceinline__ void grad_tile(const StageArgs<Real>& p, Real* q_out, const TileRange& t,
+                                          unsigned char* smem_raw) {
     using T = Tile<N, Real>;
     constexpr int NP = T::NP, NQ = T::NQ, NG = T::NG, NF = T::NF, E = T::E;
     constexpr OpsLayout L = ops_layout(N);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     Real* sIcubT = reinterpret_cast<Real*>(smem_raw);   // curved only
     Real* sXrT = sIcubT + NP * NQ;                      // DrT [NQ][NP] or QrT [NP][NP]
     Real* sXsT = sXrT + NQ * NP;
@@ -440,8 +448,6 @@ __global__ void __launch_bounds__(THREADS) grad_kernel(StageArgs<Real> p, Real* 
     Real* sR = sGeo + E * 16;          // [e][m][v][NP]
     Real* sEps = sR + E * 8 * NP;
 
-    const TileRange t = tile_range<E>(p.K, p.Kaff);
-    if (t.ne <= 0) return;
     const Real* ops = p.ops;
     if (t.curved) {
         copy_to_smem(sIcubT, ops + L.icub, NP * NQ);
@@ -566,6 +572,32 @@ __global__ void __launch_bounds__(THREADS) grad_kernel(StageArgs<Real> p, Real* 
             q_out[(t.e0 + e) * 8 * NP + mv * NP + i] = val;
         }
     }
+}
+
+template <int N, typename Real>
+__global__ void __launch_bounds__(THREADS) grad_kernel(StageArgs<Real> p, Real* q_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TileRange t = tile_range<Tile<N, Real>::E>(p.K, p.Kaff);
+    if (t.ne <= 0) return;
+    grad_tile<N, Real>(p, q_out, t, smem_raw);
+}
+
+template <int N, typename Real>
+__device__ __noinline__ void grad_tile_call(const StageArgs<Real>& p, Real* q_out, const TileRange& t,
+                                            unsigned char* smem) {
+    grad_tile<N, Real>(p, q_out, t, smem);
+}
+
+// Curved tiles only, after a tensor-core gradient launch over the affine ones.
+template <int N, typename Real>
+__global__ void __launch_bounds__(THREADS) grad_kernel_curved(StageArgs<Real> p, Real* q_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int E = Tile<N, Real>::E;
+    TileRange t;
+    t.curved = true;
+    t.e0 = p.Kaff + (long long)blockIdx.x * E;
+    t.ne = (int)min((long long)E, p.K - t.e0);
+    if (t.ne > 0) grad_tile<N, Real>(p, q_out, t, smem_raw);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,6 +1,7 @@
 // Degree-5 instantiations of the CUDA-core and tensor-core kernels.
 #include "kernels.cuh"
 #include "tc_kernels.cuh"
+#include "tc_grad.cuh"
 
 namespace dgc {
 template int launch_stage<5, float>(const StageArgs<float>&, int, cudaStream_t);
@@ -18,4 +19,8 @@ namespace dgc {
 template int launch_stage_tc<5>(const StageArgs<float>&, int, int, const unsigned char*, int*, cudaStream_t);
 template int prepare_tc<5>();
 template std::vector<uint8_t> pack_ops_tc<5>(const RefOps&, int);
+}  // namespace dgc
+namespace dgc {
+template int launch_grad_tc<5>(const StageArgs<float>&, float*, int, const unsigned char*, int*, cudaStream_t);
+template int prepare_grad_tc<5>();
 }  // namespace dgc

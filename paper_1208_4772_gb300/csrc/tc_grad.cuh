@@ -1,0 +1,393 @@
+// Tensor-core gradient kernel of the artificial viscosity: q = sqrt(eps)
+// grad U by the DG weak form with central fluxes (the BR1 q equation), for
+// tiles of 32 affine elements, products on tcgen05 with FP32 accumulate:
+//   G1: D1 = dU I_g^T (own traces), DQ = dU [Q_r; Q_s]^T with
+//       Q_r = Mref^-1 D_r^T W I_cub (node to node);
+//   GL: DLx = USx (-Mref^-1 Lift)^T, DLy = USy (-Mref^-1 Lift)^T with
+//       USm = n_m sJ ((sqrt(eps) U)* - sqrt(eps) Ubar) at the face points;
+//   q_m = (1/J) (-sqrt(eps) (J r_m Q_r dU + J s_m Q_s dU) - DLm).
+// dU is the state minus its element mean; the mean drops out exactly
+// because the discrete gradient of a constant vanishes.  Curved tiles run
+// the CUDA-core body in a second launch.
+#pragma once
+#include "tc_kernels.cuh"
+
+namespace dgc {
+
+template <int N>
+struct TgSmem {
+    using D = TcDims<N>;
+    using L = TcLayout<N>;
+    static constexpr int al(int x) { return (x + 127) / 128 * 128; }
+    static constexpr int mx(int a, int b) { return a > b ? a : b; }
+    static constexpr int sB1Q = 0;                                 // I_g rows
+    static constexpr int sBQ = sB1Q + L::B1Q_BYTES;                // Q_r; Q_s rows
+    static constexpr int sB2F = sBQ + L::BQ_BYTES;                 // -Mref^-1 Lift (face chunk)
+    static constexpr int sIGF = sB2F + L::B2_CHUNK;
+    static constexpr int A1_BYTES = 128 * D::NPK * 4;
+    static constexpr int NBV_C = 5;                                // U+ (4) and sqrt(eps+)
+    static constexpr int sA1 = al(sIGF + D::NF * D::NP * 4);       // G1 operand, then neighbour traces
+    static constexpr int A1_REGION = al(mx(A1_BYTES, 32 * D::NF * NBV_C * 4));
+    static constexpr int A2_BYTES = 128 * 32 * 4;
+    static constexpr int sA2 = sA1 + A1_REGION;                    // USx, USy operands
+    static constexpr int ST2 = 128 * 36;
+    static constexpr int sTR = sA2 + 2 * A2_BYTES;                 // [128][NFS] traces
+    static constexpr int sIO = al(sTR + 128 * D::NFS * 4);         // staging x, y; then q tile
+    static constexpr int IO_REGION = al(mx(2 * ST2 * 4, 32 * 8 * D::NP * 4));
+    static constexpr int sMEAN = sIO + IO_REGION;
+    static constexpr int sGEO = sMEAN + 128 * 4;
+    static constexpr int sSE = sGEO + 32 * 16 * 4;
+    static constexpr int sNB = sSE + 32 * 4;
+    static constexpr int sBAR = sNB + 32 * 16;
+    static constexpr int sTMEM = sBAR + 4 * 8;
+    static constexpr int sLIST = sTMEM + 16;                       // out-of-tile faces: n, then (e,f)
+    static constexpr int TOTAL = sLIST + 100 * 4;
+    static constexpr int TMEM_COLS = (D::NFP + 4 * D::N2) <= 128 ? 128 : 256;
+    static_assert(TOTAL <= 232448, "gradient tile exceeds the shared-memory limit");
+    static_assert(Tile<N, float>::smem_grad() <= (size_t)sMEAN, "curved tile would clobber the tile state");
+};
+
+template <int N, int PREC>
+__device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q_out, long long e0, int ne,
+                                             unsigned char* smem, uint32_t tmem, uint32_t& nwait, int* err) {
+    using D = TcDims<N>;
+    using S = TgSmem<N>;
+    constexpr int NP = D::NP, NG = D::NG, NF = D::NF, NPK = D::NPK, NFP = D::NFP, N2 = D::N2, NFS = D::NFS;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = (warp & 3) * 32 + lane;
+    const int half = warp >> 2;
+    const int e = row >> 2, v = row & 3;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const uint32_t tD1 = tmem, tDQ = tmem + NFP, tDLx = tDQ + 2 * N2, tDLy = tDLx + N2;
+
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::sBAR);
+    float* sMean = reinterpret_cast<float*>(smem + S::sMEAN);
+    float* sGeo = reinterpret_cast<float*>(smem + S::sGEO);
+    float* sSe = reinterpret_cast<float*>(smem + S::sSE);
+    int4* sNb = reinterpret_cast<int4*>(smem + S::sNB);
+    float* sTr = reinterpret_cast<float*>(smem + S::sTR);
+    float* stx = reinterpret_cast<float*>(smem + S::sIO);
+    float* sty = stx + S::ST2;
+    const float* sIgF = reinterpret_cast<const float*>(smem + S::sIGF);
+    unsigned char* A1 = smem + S::sA1;
+
+    int* sList = reinterpret_cast<int*>(smem + S::sLIST);
+    if (tid < 32) {
+        int nout = 0, fo[3] = {0, 0, 0};
+        if (tid < ne) {
+            affine_geometry(p.geoA + (e0 + tid) * 4, sGeo + tid * 16);
+            const int4 c = p.conn[e0 + tid];
+            sNb[tid] = c;
+            sSe[tid] = sqrtf(p.eps[e0 + tid]);
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const long long nbl = (long long)((f == 0) ? c.x : (f == 1) ? c.y : c.z) - e0;
+                if (code_bc(c.w, f) == 0 && (nbl < 0 || nbl >= ne)) fo[nout++] = f;
+            }
+        } else {
+            for (int i = 0; i < 16; ++i) sGeo[tid * 16 + i] = (i == 4 || i == 7 || i == 10 || i == 13) ? 1.f : 0.f;
+            sNb[tid] = make_int4(0, 0, 0, 0x888);
+            sSe[tid] = 0.f;
+        }
+        int incl = nout;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += y;
+        }
+        const int excl = incl - nout;
+        for (int i = 0; i < nout; ++i) sList[1 + excl + i] = tid * 3 + fo[i];
+        if (tid == 31) sList[0] = incl;
+    }
+    const long long k = e0 + e;
+    const bool live = e < ne;
+    if (half == 0) {
+        float u[NP];
+        float mean = 0.f;
+        if (live) {
+            const float* src = p.Us + (k * 4 + v) * NP;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                u[j] = src[j];
+                mean += u[j];
+            }
+            mean *= (1.0f / NP);
+        } else {
+            mean = (v == 0) ? 1.f : (v == 3) ? 2.5f : 0.f;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) u[j] = mean;
+        }
+        sMean[row] = mean;
+#pragma unroll
+        for (int j0 = 0; j0 < NPK; j0 += 8) {
+            float x[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = (j0 + i < NP) ? u[j0 + i] - mean : 0.f;
+            store8<PREC>(A1, row, j0, NPK, x);
+        }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+        issue_mma<PREC>(tD1, A1, smem + S::sB1Q, NFP, NPK, false);
+        issue_mma<PREC>(tDQ, A1, smem + S::sBQ, 2 * N2, NPK, false);
+        tc::mma_commit(&bars[0]);
+    }
+    if (!tc::mbar_wait(&bars[0], nwait & 1)) atomicOr(err, 8);
+    ++nwait;
+    tc::fence_after_sync();
+
+    // out-of-tile neighbours: trace at the reversed point and sqrt(eps)
+    float* sNbv = reinterpret_cast<float*>(smem + S::sA1);
+    const int nlist = sList[0];
+    for (int it = tid; it < nlist * NG; it += blockDim.x) {
+        const int entry = sList[1 + it / NG], gg = it % NG;
+        const int ee = entry / 3, f = entry - ee * 3, fg = f * NG + gg;
+        const int4 nbw = sNb[ee];
+        const int nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
+        const int fgn = code_face(nbw.w, f) * NG + (NG - 1 - gg);
+        const float* ig = sIgF + fgn * NP;
+        const float* un = p.Us + (long long)nb * 4 * NP;
+        float* dst = sNbv + (ee * NF + fg) * S::NBV_C;
+#pragma unroll 1
+        for (int w = 0; w < 4; ++w) {
+            float a = 0.f;
+#pragma unroll 5
+            for (int j = 0; j < NP; ++j) a += ig[j] * __ldg(un + w * NP + j);
+            dst[w] = a;
+        }
+        dst[4] = sqrtf(__ldg(p.eps + nb));
+    }
+    const float mean_v = sMean[row];
+    if (half == 0) {
+#pragma unroll
+        for (int c0 = 0; c0 < NF; c0 += 8) {
+            float x[8];
+            tc::tmem_ld8(tD1 + lane_base + c0, x);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (c0 + i < NF) sTr[row * NFS + c0 + i] = x[i] + mean_v;
+        }
+    }
+    for (int i = tid; i < 2 * S::ST2 / 4; i += blockDim.x)
+        reinterpret_cast<float4*>(stx)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+
+    // face points: n_m sJ ((sqrt(eps) U)* - sqrt(eps) Ubar) for the 4 variables
+    for (int it = tid; it < 32 * NF; it += blockDim.x) {
+        const int ee = it / NF, fg = it - ee * NF;
+        const int f = fg / NG, gg = fg - f * NG;
+        const int4 nbw = sNb[ee];
+        const int bc = code_bc(nbw.w, f);
+        const int nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
+        const int fgn = code_face(nbw.w, f) * NG + (NG - 1 - gg);
+        const float* ge = sGeo + ee * 16;
+        const float nx = ge[5 + 3 * f], ny = ge[6 + 3 * f], sJ = ge[7 + 3 * f];
+        const float se = sSe[ee];
+        float Um[4], Up[4], sep;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) Um[w] = sTr[(ee * 4 + w) * NFS + fg];
+        const long long nbl = (long long)nb - e0;
+        if (bc != 0) {
+            ghost_state(Um, bc, nx, ny, p.uinf, Up);
+            sep = se;
+        } else if (nbl >= 0 && nbl < ne) {
+#pragma unroll
+            for (int w = 0; w < 4; ++w) Up[w] = sTr[((int)nbl * 4 + w) * NFS + fgn];
+            sep = sSe[(int)nbl];
+        } else {
+            const float* src = sNbv + (ee * NF + fg) * S::NBV_C;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) Up[w] = src[w];
+            sep = src[4];
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const float st = (0.5f * (se * Um[w] + sep * Up[w]) - se * sMean[ee * 4 + w]) * sJ;
+            stx[(ee * 4 + w) * 36 + fg] = nx * st;
+            sty[(ee * 4 + w) * 36 + fg] = ny * st;
+        }
+    }
+    __syncthreads();
+    {
+        unsigned char* Ax = smem + S::sA2;
+        unsigned char* Ay = smem + S::sA2 + S::A2_BYTES;
+        const float* src = half == 0 ? stx : sty;
+        unsigned char* dst = half == 0 ? Ax : Ay;
+#pragma unroll
+        for (int s0 = 0; s0 < 32; s0 += 8) {
+            const float4 a = *reinterpret_cast<const float4*>(src + row * 36 + s0);
+            const float4 b = *reinterpret_cast<const float4*>(src + row * 36 + s0 + 4);
+            const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            store8<PREC>(dst, row, s0, 32, x);
+        }
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+        tc::fence_after_sync();
+        issue_mma<PREC>(tDLx, smem + S::sA2, smem + S::sB2F, N2, 32, false);
+        issue_mma<PREC>(tDLy, smem + S::sA2 + S::A2_BYTES, smem + S::sB2F, N2, 32, false);
+        tc::mma_commit(&bars[0]);
+    }
+    if (!tc::mbar_wait(&bars[0], nwait & 1)) atomicOr(err, 16);
+    ++nwait;
+    tc::fence_after_sync();
+
+    // epilogue: q_m for (element, variable) rows, then a coalesced store
+    {
+        float* sOut = stx;   // [e][2][4][NP]
+        const float* ge = sGeo + e * 16;
+        const float jrx = ge[0], jry = ge[1], jsx = ge[2], jsy = ge[3], invJ = ge[4];
+        const float se = sSe[e];
+        constexpr int per_half = N2 / 2;
+#pragma unroll
+        for (int c0 = 0; c0 < per_half; c0 += 8) {
+            const int i0 = half * per_half + c0;
+            float qr[8], qs[8], lx[8], ly[8];
+            tc::tmem_ld8(tDQ + lane_base + i0, qr);
+            tc::tmem_ld8(tDQ + N2 + lane_base + i0, qs);
+            tc::tmem_ld8(tDLx + lane_base + i0, lx);
+            tc::tmem_ld8(tDLy + lane_base + i0, ly);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i0 + i < NP) {
+                    sOut[(e * 8 + v) * NP + i0 + i] = invJ * (-se * (jrx * qr[i] + jsx * qs[i]) - lx[i]);
+                    sOut[(e * 8 + 4 + v) * NP + i0 + i] = invJ * (-se * (jry * qr[i] + jsy * qs[i]) - ly[i]);
+                }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        const int n4 = ne * 2 * NP;   // float4 groups: ne * 8 * NP / 4
+        float4* qo = reinterpret_cast<float4*>(q_out + e0 * 8 * NP);
+        const float4* so = reinterpret_cast<const float4*>(sOut);
+        for (int i = tid; i < n4; i += blockDim.x) qo[i] = so[i];
+        __syncthreads();
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void load_grad_operators(const unsigned char* ops_tc, unsigned char* smem) {
+    using S = TgSmem<N>;
+    using L = TcLayout<N>;
+    constexpr int NF = TcDims<N>::NF, NP = TcDims<N>::NP;
+    const int tid = threadIdx.x;
+    const int4* src = reinterpret_cast<const int4*>(ops_tc);
+    int4* dst = reinterpret_cast<int4*>(smem);
+    for (int i = tid; i < L::B1Q_BYTES / 16; i += blockDim.x) dst[S::sB1Q / 16 + i] = src[L::B1Q / 16 + i];
+    for (int i = tid; i < L::BQ_BYTES / 16; i += blockDim.x) dst[S::sBQ / 16 + i] = src[L::BQ / 16 + i];
+    for (int i = tid; i < L::B2_CHUNK / 16; i += blockDim.x) dst[S::sB2F / 16 + i] = src[L::B2 / 16 + i];
+    const float* igs = reinterpret_cast<const float*>(ops_tc + L::IGF);
+    float* igd = reinterpret_cast<float*>(smem + S::sIGF);
+    for (int i = tid; i < NF * NP; i += blockDim.x) igd[i] = igs[i];
+}
+
+// Persistent grid claiming tiles from an atomic counter: curved tiles first
+// (CUDA-core body), then affine tiles on the tensor cores.
+template <int N, int PREC>
+__global__ void __launch_bounds__(THREADS, 2) grad_kernel_tc(StageArgs<float> p, float* q_out,
+                                                             const unsigned char* ops_tc, int* err, int* counter) {
+    extern __shared__ __align__(128) unsigned char smem_g[];
+    using S = TgSmem<N>;
+    constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
+    const int tid = threadIdx.x;
+    const long long nAff = (p.Kaff + ET - 1) / ET;
+    const long long nCur = (p.K - p.Kaff + EC - 1) / EC;
+    __shared__ long long s_tile;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_g + S::sBAR);
+    if (tid == 0) {
+        for (int b = 0; b < 4; ++b) tc::mbar_init(&bars[b], 1);
+        tc::mbar_fence_init();
+    }
+    uint32_t* slot = reinterpret_cast<uint32_t*>(smem_g + S::sTMEM);
+    if ((tid >> 5) == 0) tc::tmem_alloc(slot, S::TMEM_COLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot;
+    uint32_t nwait = 0;
+    bool ops_loaded = false;
+    while (true) {
+        if (tid == 0) s_tile = atomicAdd(counter, 1);
+        __syncthreads();
+        const long long t = s_tile;
+        __syncthreads();
+        if (t >= nCur + nAff) break;
+        if (t < nCur) {
+            TileRange tr;
+            tr.curved = true;
+            tr.e0 = p.Kaff + t * EC;
+            tr.ne = (int)min((long long)EC, p.K - tr.e0);
+            grad_tile_call<N, float>(p, q_out, tr, smem_g);
+            ops_loaded = false;
+            __syncthreads();
+        } else {
+            if (!ops_loaded) {
+                load_grad_operators<N>(ops_tc, smem_g);
+                __syncthreads();
+                ops_loaded = true;
+            }
+            const long long e0 = (t - nCur) * ET;
+            grad_tile_tc<N, PREC>(p, q_out, e0, (int)min((long long)ET, p.Kaff - e0), smem_g, tmem, nwait, err);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if ((tid >> 5) == 0) tc::tmem_free(tmem, S::TMEM_COLS);
+}
+
+template <int N, int PREC>
+struct TgGrid {
+    static inline int ctas = 0;
+};
+
+template <int N, int PREC>
+int prepare_grad_tc_t() {
+    auto kern = grad_kernel_tc<N, PREC>;
+    const int sm = TgSmem<N>::TOTAL;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return (int)e;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
+        return (int)e;
+    int occ = 0, dev = 0, nsm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THREADS, sm)) != cudaSuccess) return (int)e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)e;
+    const int by_tmem = 512 / TgSmem<N>::TMEM_COLS;
+    occ = occ < by_tmem ? occ : by_tmem;
+    if (occ < 1) return (int)cudaErrorInvalidConfiguration;
+    TgGrid<N, PREC>::ctas = nsm * occ;
+    return 0;
+}
+
+template <int N>
+int prepare_grad_tc() {
+    int e = prepare_grad_tc_t<N, PREC_TF32>();
+    if (!e) e = prepare_grad_tc_t<N, PREC_BF16X3>();
+    return e;
+}
+
+// err[2]: tile counter of this launch (zeroed first).
+template <int N>
+int launch_grad_tc(const StageArgs<float>& a, float* q_out, int prec, const unsigned char* ops_tc, int* err,
+                   cudaStream_t st) {
+    constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
+    const long long tiles = (a.Kaff + ET - 1) / ET + (a.K - a.Kaff + EC - 1) / EC;
+    if (tiles == 0) return 0;
+    const int ctas = prec == PREC_TF32 ? TgGrid<N, PREC_TF32>::ctas : TgGrid<N, PREC_BF16X3>::ctas;
+    if (ctas <= 0) return (int)cudaErrorNotReady;
+    cudaError_t e = cudaMemsetAsync(err + 2, 0, sizeof(int), st);
+    if (e != cudaSuccess) return (int)e;
+    const unsigned grid = (unsigned)(tiles < ctas ? tiles : ctas);
+    if (prec == PREC_TF32)
+        grad_kernel_tc<N, PREC_TF32><<<grid, THREADS, TgSmem<N>::TOTAL, st>>>(a, q_out, ops_tc, err, err + 2);
+    else
+        grad_kernel_tc<N, PREC_BF16X3><<<grid, THREADS, TgSmem<N>::TOTAL, st>>>(a, q_out, ops_tc, err, err + 2);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace dgc

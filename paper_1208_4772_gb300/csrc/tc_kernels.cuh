@@ -65,7 +65,9 @@ struct TcLayout {
     static constexpr int B2 = B1Q + B1Q_BYTES;                     // NCH x [N2 rows][32]
     static constexpr int B2_CHUNK = D::N2 * 32 * 4;
     static constexpr int IGF = B2 + D::NCH * B2_CHUNK;             // I_g fp32 [NF][NP]
-    static constexpr int TOTAL = IGF + D::NF * D::NP * 4;
+    static constexpr int BQ = (IGF + D::NF * D::NP * 4 + 15) / 16 * 16;  // [2 N2 rows][NPK]: Q_r; Q_s
+    static constexpr int BQ_BYTES = 2 * D::N2 * D::NPK * 4;
+    static constexpr int TOTAL = BQ + BQ_BYTES;
 };
 
 // Shared-memory carve-up of the tensor-core kernel.  Regions whose
@@ -98,7 +100,7 @@ struct TcSmem {
     static constexpr int ST2 = 128 * 36;                                     // [row][32 + 4]
     static constexpr int TR_REGION = al(mx(TR_FLOATS * 4 * (AV ? 2 : 1), ST1 * 4));
     static constexpr int IO_REGION = al(mx(ST2 * 4, 32 * 4 * D::NP * 4));
-    static constexpr int SMALL = 128 * 4 + 32 * 16 * 4 + 32 * 8 * 4 + 32 * 4 + 32 * 16 + 4 * 8 + 16;
+    static constexpr int SMALL = 128 * 4 + 32 * 16 * 4 + 32 * 8 * 4 + 32 * 4 + 32 * 16 + 4 * 8 + 16 + 100 * 4;
     static constexpr int total_for(int nbuf) { return sA1 + A1_REGION + nbuf * A2_BYTES + TR_REGION + IO_REGION + SMALL; }
     static constexpr int TWO_PER_SM = 113 * 1024;
     static constexpr int NBUF = (total_for(2) <= TWO_PER_SM || total_for(1) > TWO_PER_SM) ? 2 : 1;
@@ -112,8 +114,11 @@ struct TcSmem {
     static constexpr int sNB = sSE + 32 * 4;                                 // [32] int4
     static constexpr int sBAR = sNB + 32 * 16;                               // 4 mbarriers
     static constexpr int sTMEM = sBAR + 4 * 8;
-    static constexpr int TOTAL = sTMEM + 16;
+    static constexpr int sLIST = sTMEM + 16;                                 // out-of-tile faces: n, then (e,f)
+    static constexpr int TOTAL = sLIST + 100 * 4;
     static_assert(TOTAL <= 232448, "tensor-core tile exceeds the shared-memory limit");
+    // a curved tile (CUDA-core body) may overwrite everything before sMEAN
+    static_assert(Tile<N, float>::smem_stage(AV) <= (size_t)sMEAN, "curved tile would clobber the tile state");
 };
 
 template <int N, bool AV>
@@ -211,16 +216,34 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     unsigned char* A1 = smem + S::sA1;
 
     // ---------------- per-element data and the state deviations
+    int* sList = reinterpret_cast<int*>(smem + S::sLIST);
     if (tid < 32) {
+        int nout = 0, fo[3] = {0, 0, 0};
         if (tid < ne) {
             affine_geometry(p.geoA + (e0 + tid) * 4, sGeo + tid * 16);
-            sNb[tid] = p.conn[e0 + tid];
+            const int4 c = p.conn[e0 + tid];
+            sNb[tid] = c;
             sSe[tid] = AV ? sqrtf(p.eps[e0 + tid]) : 0.f;
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const long long nbl = (long long)((f == 0) ? c.x : (f == 1) ? c.y : c.z) - e0;
+                if (code_bc(c.w, f) == 0 && (nbl < 0 || nbl >= ne)) fo[nout++] = f;
+            }
         } else {  // padding element: unit geometry, farfield faces, never stored
             for (int i = 0; i < 16; ++i) sGeo[tid * 16 + i] = (i == 4 || i == 7 || i == 10 || i == 13) ? 1.f : 0.f;
             sNb[tid] = make_int4(0, 0, 0, 0x888);
             sSe[tid] = 0.f;
         }
+        // the out-of-tile faces of the tile as a compact list (warp scan)
+        int incl = nout;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += y;
+        }
+        const int excl = incl - nout;
+        for (int i = 0; i < nout; ++i) sList[1 + excl + i] = tid * 3 + fo[i];
+        if (tid == 31) sList[0] = incl;
     }
     const long long k = e0 + e;
     const bool live = e < ne;
@@ -290,13 +313,12 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     // out-of-tile neighbours' traces at the reversed face points, from their
     // states in L2, into the G1 operand region (G1 has completed)
     float* sNbv = reinterpret_cast<float*>(smem + S::sA1);
-    for (int it = tid; it < 32 * NF; it += blockDim.x) {
-        const int ee = it / NF, fg = it - ee * NF;
-        const int f = fg / NG, gg = fg - f * NG;
+    const int nlist = sList[0];
+    for (int it = tid; it < nlist * NG; it += blockDim.x) {
+        const int entry = sList[1 + it / NG], gg = it % NG;
+        const int ee = entry / 3, f = entry - ee * 3, fg = f * NG + gg;
         const int4 nbw = sNb[ee];
         const int nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
-        const long long nbl = (long long)nb - e0;
-        if (ee >= ne || code_bc(nbw.w, f) != 0 || (nbl >= 0 && nbl < ne)) continue;
         const int fgn = code_face(nbw.w, f) * NG + (NG - 1 - gg);
         const float* ig = sIgF + fgn * NP;
         const float* un = p.Us + (long long)nb * 4 * NP;
@@ -461,24 +483,29 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
             for (int i = 0; i < 8; ++i) st1[e * 68 + (half * 8 + i) * 4 + v] = x[i] + mean_v;
         }
         __syncthreads();
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int it = tid + r * 256;
-            const int ee = it >> 4, ql = it & 15;
+        constexpr int LASTV = NQ - 16 * (D::CQ - 1);          // valid points in the last chunk
+        const int nvalid = (cq == D::CQ - 1) ? LASTV : 16;
+        for (int it = tid; it < 32 * nvalid; it += blockDim.x) {
+            const int ee = it / nvalid, ql = it - ee * nvalid;
             const float4 U4 = *reinterpret_cast<const float4*>(st1 + ee * 68 + ql * 4);
             const float Uc[4] = {U4.x, U4.y, U4.z, U4.w};
             float F[4], G[4];
             euler_flux(Uc, p.gamma, F, G);
             const float* ge = sGeo + ee * 16;
             const float jrx = ge[0], jry = ge[1], jsx = ge[2], jsy = ge[3];
-            const bool ok = cq * 16 + ql < NQ;
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 const float dF = F[w] - sFb[ee * 8 + w], dG = G[w] - sFb[ee * 8 + 4 + w];
-                st2[(ee * 4 + w) * 36 + ql] = ok ? jrx * dF + jry * dG : 0.f;
-                st2[(ee * 4 + w) * 36 + 16 + ql] = ok ? jsx * dF + jsy * dG : 0.f;
+                st2[(ee * 4 + w) * 36 + ql] = jrx * dF + jry * dG;
+                st2[(ee * 4 + w) * 36 + 16 + ql] = jsx * dF + jsy * dG;
             }
         }
+        if (nvalid < 16)   // padded points of the last chunk
+            for (int it = tid; it < 128 * (16 - nvalid); it += blockDim.x) {
+                const int r = it / (16 - nvalid), ql = nvalid + it % (16 - nvalid);
+                st2[r * 36 + ql] = 0.f;
+                st2[r * 36 + 16 + ql] = 0.f;
+            }
         __syncthreads();
         st2_to_a2(A2);
         end_chunk(chunk);
@@ -563,66 +590,80 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     }
 }
 
-// Persistent grid: each CTA sets up its operators, mbarriers and TMEM once
-// and takes the affine tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
-// (32 elements each) on the tensor cores.  Curved tiles run the CUDA-core
-// body in a second launch (stage_kernel_curved).
-template <int N, bool AV, int PREC>
-__global__ void __launch_bounds__(THREADS, 1) stage_kernel_tc(StageArgs<float> p, const unsigned char* ops_tc, int* err) {
-    extern __shared__ __align__(128) unsigned char smem_tc[];
+template <int N, bool AV>
+__device__ __forceinline__ void load_tc_operators(const unsigned char* ops_tc, unsigned char* smem) {
     using S = TcSmem<N, AV>;
     using L = TcLayout<N>;
-    constexpr int ET = TcDims<N>::E;
     constexpr int NF = TcDims<N>::NF, NP = TcDims<N>::NP;
     const int tid = threadIdx.x;
-    const long long nAff = (p.Kaff + ET - 1) / ET;
-    const bool any_affine = (long long)blockIdx.x < nAff;
-
-    uint32_t tmem = 0;
-    TcPhase ph;
-    if (any_affine) {
-        const int4* src = reinterpret_cast<const int4*>(ops_tc);
-        int4* dst = reinterpret_cast<int4*>(smem_tc);
-        for (int i = tid; i < L::B1_BYTES / 16; i += blockDim.x) dst[i] = src[i];
-        if constexpr (AV)
-            for (int i = tid; i < L::B1Q_BYTES / 16; i += blockDim.x) dst[S::sB1Q / 16 + i] = src[L::B1Q / 16 + i];
-        for (int i = tid; i < S::NCHU * L::B2_CHUNK / 16; i += blockDim.x) dst[S::sB2 / 16 + i] = src[L::B2 / 16 + i];
-        const float* igs = reinterpret_cast<const float*>(ops_tc + L::IGF);
-        float* igd = reinterpret_cast<float*>(smem_tc + S::sIGF);
-        for (int i = tid; i < NF * NP; i += blockDim.x) igd[i] = igs[i];
-        uint64_t* bars = reinterpret_cast<uint64_t*>(smem_tc + S::sBAR);
-        if (tid == 0) {
-            for (int b = 0; b < 4; ++b) tc::mbar_init(&bars[b], 1);
-            tc::mbar_fence_init();
-        }
-        uint32_t* slot = reinterpret_cast<uint32_t*>(smem_tc + S::sTMEM);
-        if ((tid >> 5) == 0) tc::tmem_alloc(slot, TcDims<N>::TMEM_COLS);
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        tmem = *slot;
-    }
-    for (long long t = blockIdx.x; t < nAff; t += gridDim.x) {
-        const long long e0 = t * ET;
-        stage_tile_tc<N, AV, PREC>(p, e0, (int)min((long long)ET, p.Kaff - e0), smem_tc, tmem, ph, err);
-    }
-    if (any_affine) {
-        tc::fence_before_sync();
-        __syncthreads();
-        if ((tid >> 5) == 0) tc::tmem_free(tmem, TcDims<N>::TMEM_COLS);
-    }
+    const int4* src = reinterpret_cast<const int4*>(ops_tc);
+    int4* dst = reinterpret_cast<int4*>(smem);
+    for (int i = tid; i < L::B1_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+    if constexpr (AV)
+        for (int i = tid; i < L::B1Q_BYTES / 16; i += blockDim.x) dst[S::sB1Q / 16 + i] = src[L::B1Q / 16 + i];
+    for (int i = tid; i < S::NCHU * L::B2_CHUNK / 16; i += blockDim.x) dst[S::sB2 / 16 + i] = src[L::B2 / 16 + i];
+    const float* igs = reinterpret_cast<const float*>(ops_tc + L::IGF);
+    float* igd = reinterpret_cast<float*>(smem + S::sIGF);
+    for (int i = tid; i < NF * NP; i += blockDim.x) igd[i] = igs[i];
 }
 
-// Curved tiles only (CUDA-core body), after the tensor-core launch.
-template <int N, bool AV>
-__global__ void __launch_bounds__(THREADS) stage_kernel_curved(StageArgs<float> p) {
-    extern __shared__ __align__(16) unsigned char smem_cc[];
-    constexpr int EC = Tile<N, float>::E;
-    TileRange tr;
-    tr.curved = true;
-    tr.e0 = p.Kaff + (long long)blockIdx.x * EC;
-    tr.ne = (int)min((long long)EC, p.K - tr.e0);
-    if (tr.ne > 0) stage_tile<N, float, AV>(p, tr, smem_cc);
+// Persistent grid (SMs x resident CTAs).  Each CTA sets up its mbarriers and
+// TMEM once and claims tiles from an atomic counter: first the curved tiles
+// (CUDA-core body, which overwrites the operator region, so the operators
+// are reloaded before the next tensor-core tile), then the affine tiles of
+// 32 elements on the tensor cores.  Handing the slow curved tiles out first
+// lets them overlap the affine work instead of forming a tail.
+template <int N, bool AV, int PREC>
+__global__ void __launch_bounds__(THREADS, 2) stage_kernel_tc(StageArgs<float> p, const unsigned char* ops_tc, int* err,
+                                                              int* counter) {
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    using S = TcSmem<N, AV>;
+    constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
+    const int tid = threadIdx.x;
+    const long long nAff = (p.Kaff + ET - 1) / ET;
+    const long long nCur = (p.K - p.Kaff + EC - 1) / EC;
+    __shared__ long long s_tile;
+
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_tc + S::sBAR);
+    if (tid == 0) {
+        for (int b = 0; b < 4; ++b) tc::mbar_init(&bars[b], 1);
+        tc::mbar_fence_init();
+    }
+    uint32_t* slot = reinterpret_cast<uint32_t*>(smem_tc + S::sTMEM);
+    if ((tid >> 5) == 0) tc::tmem_alloc(slot, TcDims<N>::TMEM_COLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot;
+    TcPhase ph;
+    bool ops_loaded = false;
+    while (true) {
+        if (tid == 0) s_tile = atomicAdd(counter, 1);
+        __syncthreads();
+        const long long t = s_tile;
+        __syncthreads();
+        if (t >= nCur + nAff) break;
+        if (t < nCur) {
+            TileRange tr;
+            tr.curved = true;
+            tr.e0 = p.Kaff + t * EC;
+            tr.ne = (int)min((long long)EC, p.K - tr.e0);
+            stage_tile_call<N, float, AV>(p, tr, smem_tc);
+            ops_loaded = false;
+            __syncthreads();
+        } else {
+            if (!ops_loaded) {
+                load_tc_operators<N, AV>(ops_tc, smem_tc);
+                __syncthreads();
+                ops_loaded = true;
+            }
+            const long long e0 = (t - nCur) * ET;
+            stage_tile_tc<N, AV, PREC>(p, e0, (int)min((long long)ET, p.Kaff - e0), smem_tc, tmem, ph, err);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if ((tid >> 5) == 0) tc::tmem_free(tmem, TcDims<N>::TMEM_COLS);
 }
 
 // Persistent grid size per instantiation: SMs x resident CTAs (shared memory
@@ -638,6 +679,8 @@ int prepare_tc_t() {
     const int sm = (int)tc_smem_bytes<N, AV>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return (int)e;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
+        return (int)e;
     int occ = 0, dev = 0, nsm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THREADS, sm)) != cudaSuccess) return (int)e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
@@ -646,24 +689,21 @@ int prepare_tc_t() {
     occ = occ < by_tmem ? occ : by_tmem;
     if (occ < 1) return (int)cudaErrorInvalidConfiguration;
     TcGrid<N, AV, PREC>::ctas = nsm * occ;
-    e = cudaFuncSetAttribute(stage_kernel_curved<N, AV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Tile<N, float>::smem_stage(AV));
-    return (int)e;
+    return 0;
 }
 
+// err[0]: error word; err[1]: tile counter of this launch (zeroed first).
 template <int N, bool AV, int PREC>
 int launch_stage_tc_t(const StageArgs<float>& a, const unsigned char* ops_tc, int* err, cudaStream_t st) {
     constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
-    const long long tiles = (a.Kaff + ET - 1) / ET;
-    if (tiles > 0) {
-        const int ctas = TcGrid<N, AV, PREC>::ctas;
-        if (ctas <= 0) return (int)cudaErrorNotReady;   // prepare_tc was not called
-        const unsigned grid = (unsigned)(tiles < ctas ? tiles : ctas);
-        stage_kernel_tc<N, AV, PREC><<<grid, THREADS, tc_smem_bytes<N, AV>(), st>>>(a, ops_tc, err);
-    }
-    const long long ctiles = (a.K - a.Kaff + EC - 1) / EC;
-    if (ctiles > 0)
-        stage_kernel_curved<N, AV><<<(unsigned)ctiles, THREADS, Tile<N, float>::smem_stage(AV), st>>>(a);
+    const long long tiles = (a.Kaff + ET - 1) / ET + (a.K - a.Kaff + EC - 1) / EC;
+    if (tiles == 0) return 0;
+    const int ctas = TcGrid<N, AV, PREC>::ctas;
+    if (ctas <= 0) return (int)cudaErrorNotReady;   // prepare_tc was not called
+    cudaError_t e = cudaMemsetAsync(err + 1, 0, sizeof(int), st);
+    if (e != cudaSuccess) return (int)e;
+    const unsigned grid = (unsigned)(tiles < ctas ? tiles : ctas);
+    stage_kernel_tc<N, AV, PREC><<<grid, THREADS, tc_smem_bytes<N, AV>(), st>>>(a, ops_tc, err, err + 1);
     return (int)cudaGetLastError();
 }
 
@@ -771,6 +811,12 @@ std::vector<uint8_t> pack_ops_tc(const RefOps& R, int prec) {
             const float f = (float)Ig(fg, j);
             std::memcpy(&out[L::IGF + ((size_t)fg * NP + j) * 4], &f, 4);
         }
+    pack_operand(out, L::BQ, 2 * D::N2, D::NPK, prec, [&](int r, int j) -> double {
+        if (j >= NP) return 0.0;
+        if (r < D::N2) return r < NP ? R.Qr[(size_t)r * NP + j] : 0.0;
+        const int i = r - D::N2;
+        return i < NP ? R.Qs[(size_t)i * NP + j] : 0.0;
+    });
     return out;
 }
 
