@@ -96,6 +96,32 @@ template <int N> int prepare_grad_tc();
 struct RefOps;
 template <int N> std::vector<uint8_t> pack_ops_tc(const RefOps& R, int prec);
 
+// Resident CTAs per SM of a kernel from its attributes and the device
+// limits (registers, shared memory incl. the per-block reservation, warps),
+// and the larger of that and the runtime's occupancy estimate.
+inline int resident_ctas(const void* kern, int threads, size_t dyn_smem) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return 0;
+    int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0, warps_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&warps_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    warps_sm /= 32;
+    const size_t per_block = dyn_smem + fa.sharedSizeBytes + (size_t)reserved;
+    int by_smem = per_block ? (int)(smem_sm / per_block) : 64;
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    int by_regs = regs_warp ? regs_sm / (regs_warp * ((threads + 31) / 32)) : 64;
+    int by_warps = warps_sm / ((threads + 31) / 32);
+    int manual = by_smem < by_regs ? by_smem : by_regs;
+    manual = manual < by_warps ? manual : by_warps;
+    int api = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&api, kern, threads, dyn_smem) != cudaSuccess) api = 0;
+    cudaGetLastError();
+    return api > manual ? api : manual;
+}
+
 // Generic kernels (kernels_common.cu)
 template <typename Real>
 int launch_residual(const Real* L, long long n_per_var_block, long long K, int NP, double* partial,

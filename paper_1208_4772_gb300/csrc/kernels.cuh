@@ -350,62 +350,25 @@ __global__ void __launch_bounds__(THREADS) stage_kernel(StageArgs<Real> p) {
 }
 
 // ---------------------------------------------------------------------------
-// Persson-Peraire sensor: eps_k from the density (paper Sec. 2), one thread
-// per element.  The block stages the densities of its 128 elements in shared
-// memory with coalesced loads; V^-1 (affine) or I_cub and I_top (curved)
-// are read as broadcasts.  Affine: S = sum_{deg N} u^2 / sum u^2 with
-// u = V^-1 rho (the cubature form for constant J and an orthonormal basis);
-// curved: both integrals by cubature with J.  Sums in the state precision,
-// ratio, log10 and the sine ramp in FP64.
+// Persson-Peraire sensor: eps_k from the density (paper Sec. 2).
+// Affine elements: one thread per element; the block stages the densities of
+// its 128 elements in shared memory with coalesced loads and reads V^-1 as
+// broadcasts.  S = sum_{deg N} u^2 / sum u^2 with u = V^-1 rho (the cubature
+// form for constant J and an orthonormal basis).
+// Curved elements: one warp per element, lanes over the cubature points,
+// both integrals by cubature with J, in blocks of their own at the front of
+// the grid so that they do not form a tail.
+// Sums in the state precision; ratio, log10 and the sine ramp in FP64.
 // ---------------------------------------------------------------------------
 constexpr int SENSOR_THREADS = 128;
+constexpr int SENSOR_CURVED_PER_BLOCK = SENSOR_THREADS / 32;
 
-template <int N, typename Real>
-__global__ void __launch_bounds__(SENSOR_THREADS) sensor_kernel(StageArgs<Real> p, Real* eps_out) {
-    constexpr int NP = np_of(N), NQ = nq_of(N);
-    constexpr int NLOW = N * (N + 1) / 2;  // modes of degree <= N-1 come first
-    constexpr OpsLayout L = ops_layout(N);
-    constexpr int RS = NP | 1;   // odd row stride: conflict-free column reads
-    __shared__ Real sRho[SENSOR_THREADS * RS];
-    __shared__ Real sV[NP * NP];
-    const long long k0 = (long long)blockIdx.x * SENSOR_THREADS;
-    const int nb = (int)min((long long)SENSOR_THREADS, p.K - k0);
-    for (int i = threadIdx.x; i < NP * NP; i += SENSOR_THREADS) sV[i] = p.ops[L.vinvt + i];
-    for (int i = threadIdx.x; i < nb * NP; i += SENSOR_THREADS) {
-        const int e = i / NP, j = i - e * NP;
-        sRho[e * RS + j] = p.Us[(k0 + e) * 4 * NP + j];
-    }
-    __syncthreads();
-    const int e = threadIdx.x;
-    if (e >= nb) return;
-    const long long k = k0 + e;
-    const Real* rho = sRho + e * RS;
-    Real num = 0, den = 0;
-    if (k < p.Kaff) {
-#pragma unroll 1
-        for (int m = 0; m < NP; ++m) {
-            Real um = 0;
-#pragma unroll
-            for (int j = 0; j < NP; ++j) um += sV[j * NP + m] * rho[j];
-            den += um * um;
-            if (m >= NLOW) num += um * um;
-        }
-    } else {
-        const Real* g = p.geoC + (k - p.Kaff) * curved_stride(N);
-        for (int qn = 0; qn < NQ; ++qn) {
-            Real a = 0, b = 0;
-            for (int j = 0; j < NP; ++j) {
-                a += p.ops[L.icub + j * NQ + qn] * rho[j];
-                b += p.ops[L.itopt + j * NQ + qn] * rho[j];
-            }
-            const Real wj = p.ops[L.w + qn] * g[4 * NQ + qn];
-            den += wj * a * a;
-            num += wj * b * b;
-        }
-    }
-    // s = log10(num/den) is needed only inside the ramp band: outside it the
-    // two comparisons (in FP64, without a division) decide, which keeps the
-    // FP64 transcendentals off the elements where eps is 0 or eps0
+// eps from the two sensor integrals.  s = log10(num/den) is needed only
+// inside the ramp band: outside it two comparisons (in FP64, without a
+// division) decide, which keeps the FP64 transcendentals off the elements
+// where eps is 0 or eps0.
+template <typename Real>
+__device__ __forceinline__ Real sensor_eps(const StageArgs<Real>& p, Real num, Real den) {
     double eps = 0.0;
     const double dn = (double)num, dd = (double)den;
     if (dn > 0.0 && dd > 0.0 && dn >= p.S_lo * dd) {
@@ -419,7 +382,65 @@ __global__ void __launch_bounds__(SENSOR_THREADS) sensor_kernel(StageArgs<Real> 
                 eps = 0.5 * p.eps0 * (1.0 + sin(M_PI * (s - p.s0) / (2.0 * p.kappa)));
         }
     }
-    eps_out[k] = (Real)eps;
+    return (Real)eps;
+}
+
+template <int N, typename Real>
+__global__ void __launch_bounds__(SENSOR_THREADS) sensor_kernel(StageArgs<Real> p, Real* eps_out, int ncb) {
+    constexpr int NP = np_of(N), NQ = nq_of(N);
+    constexpr int NLOW = N * (N + 1) / 2;  // modes of degree <= N-1 come first
+    constexpr OpsLayout L = ops_layout(N);
+    if ((int)blockIdx.x < ncb) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const long long k = p.Kaff + (long long)blockIdx.x * SENSOR_CURVED_PER_BLOCK + warp;
+        if (k >= p.K) return;
+        const Real* rho = p.Us + k * 4 * NP;
+        const Real* g = p.geoC + (k - p.Kaff) * curved_stride(N);
+        Real num = 0, den = 0;
+        for (int qn = lane; qn < NQ; qn += 32) {
+            Real a = 0, b = 0;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                const Real r = __ldg(rho + j);
+                a += __ldg(p.ops + L.icub + j * NQ + qn) * r;
+                b += __ldg(p.ops + L.itopt + j * NQ + qn) * r;
+            }
+            const Real wj = p.ops[L.w + qn] * g[4 * NQ + qn];
+            den += wj * a * a;
+            num += wj * b * b;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            num += __shfl_xor_sync(0xffffffffu, num, o);
+            den += __shfl_xor_sync(0xffffffffu, den, o);
+        }
+        if (lane == 0) eps_out[k] = sensor_eps(p, num, den);
+        return;
+    }
+    constexpr int RS = NP | 1;   // odd row stride: conflict-free column reads
+    __shared__ Real sRho[SENSOR_THREADS * RS];
+    __shared__ Real sV[NP * NP];
+    const long long k0 = (long long)(blockIdx.x - ncb) * SENSOR_THREADS;
+    const int nb = (int)min((long long)SENSOR_THREADS, p.Kaff - k0);
+    for (int i = threadIdx.x; i < NP * NP; i += SENSOR_THREADS) sV[i] = p.ops[L.vinvt + i];
+    for (int i = threadIdx.x; i < nb * NP; i += SENSOR_THREADS) {
+        const int e = i / NP, j = i - e * NP;
+        sRho[e * RS + j] = p.Us[(k0 + e) * 4 * NP + j];
+    }
+    __syncthreads();
+    const int e = threadIdx.x;
+    if (e >= nb) return;
+    const Real* rho = sRho + e * RS;
+    Real num = 0, den = 0;
+#pragma unroll 1
+    for (int m = 0; m < NP; ++m) {
+        Real um = 0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) um += sV[j * NP + m] * rho[j];
+        den += um * um;
+        if (m >= NLOW) num += um * um;
+    }
+    eps_out[k0 + e] = sensor_eps(p, num, den);
 }
 
 // ---------------------------------------------------------------------------
@@ -623,9 +644,11 @@ int launch_stage(const StageArgs<Real>& a, int av, cudaStream_t st) {
 
 template <int N, typename Real>
 int launch_sensor(const StageArgs<Real>& a, Real* eps_out, cudaStream_t st) {
-    const unsigned grid = (unsigned)((a.K + SENSOR_THREADS - 1) / SENSOR_THREADS);
+    const long long Kc = a.K - a.Kaff;
+    const int ncb = (int)((Kc + SENSOR_CURVED_PER_BLOCK - 1) / SENSOR_CURVED_PER_BLOCK);
+    const unsigned grid = (unsigned)(ncb + (a.Kaff + SENSOR_THREADS - 1) / SENSOR_THREADS);
     if (grid == 0) return 0;
-    sensor_kernel<N, Real><<<grid, SENSOR_THREADS, 0, st>>>(a, eps_out);
+    sensor_kernel<N, Real><<<grid, SENSOR_THREADS, 0, st>>>(a, eps_out, ncb);
     return (int)cudaGetLastError();
 }
 

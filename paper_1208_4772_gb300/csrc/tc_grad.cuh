@@ -10,6 +10,8 @@
 // because the discrete gradient of a constant vanishes.  Curved tiles run
 // the CUDA-core body in a second launch.
 #pragma once
+#include <cstdio>
+#include <cstdlib>
 #include "tc_kernels.cuh"
 
 namespace dgc {
@@ -353,13 +355,13 @@ int prepare_grad_tc_t() {
     if (e != cudaSuccess) return (int)e;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
         return (int)e;
-    int occ = 0, dev = 0, nsm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THREADS, sm)) != cudaSuccess) return (int)e;
+    int occ = resident_ctas((const void*)kern, THREADS, sm), dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)e;
     const int by_tmem = 512 / TgSmem<N>::TMEM_COLS;
     occ = occ < by_tmem ? occ : by_tmem;
     if (occ < 1) return (int)cudaErrorInvalidConfiguration;
+    if (getenv("DGC_VERBOSE")) fprintf(stderr, "dgcurved: %s N=%d: %d CTAs per SM\n", __func__, N, occ);
     TgGrid<N, PREC>::ctas = nsm * occ;
     return 0;
 }

@@ -24,6 +24,8 @@
 // tensor core works on the previous chunk (two smem buffers, one mbarrier
 // each).  Curved tiles run the CUDA-core tile body in the same launch.
 #pragma once
+#include <cstdio>
+#include <cstdlib>
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -50,7 +52,7 @@ struct TcDims {
     static constexpr int CA = (NP + 15) / 16;              // viscous chunks
     static constexpr int NCH = CF + CQ + CA;               // chunks in the operator table
     static constexpr int E = 32;
-    static constexpr int NFS = NF + 1;                     // row stride of the trace exchange
+    static constexpr int NFS = NF | 1;                     // odd row stride of the trace exchange
     static constexpr int TMEM_COLS = (N1 + 2 * NFP + N2) <= 128 ? 128 : 256;
 };
 
@@ -681,13 +683,13 @@ int prepare_tc_t() {
     if (e != cudaSuccess) return (int)e;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
         return (int)e;
-    int occ = 0, dev = 0, nsm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THREADS, sm)) != cudaSuccess) return (int)e;
+    int occ = resident_ctas((const void*)kern, THREADS, sm), dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)e;
     const int by_tmem = 512 / TcDims<N>::TMEM_COLS;
     occ = occ < by_tmem ? occ : by_tmem;
     if (occ < 1) return (int)cudaErrorInvalidConfiguration;
+    if (getenv("DGC_VERBOSE")) fprintf(stderr, "dgcurved: %s N=%d: %d CTAs per SM\n", __func__, N, occ);
     TcGrid<N, AV, PREC>::ctas = nsm * occ;
     return 0;
 }
