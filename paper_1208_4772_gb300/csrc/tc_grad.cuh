@@ -137,30 +137,51 @@ __device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q
         issue_mma<PREC>(tDQ, A1, smem + S::sBQ, 2 * N2, NPK, false);
         tc::mma_commit(&bars[0]);
     }
-    if (!tc::mbar_wait(&bars[0], nwait & 1)) atomicOr(err, 8);
-    ++nwait;
-    tc::fence_after_sync();
-
-    // out-of-tile neighbours: trace at the reversed point and sqrt(eps)
+    // out-of-tile neighbours: trace at the reversed point and sqrt(eps); one
+    // item per (face, variable, half of the face points), loads issued
+    // before the wait for G1 (the traces overwrite its operand region)
     float* sNbv = reinterpret_cast<float*>(smem + S::sA1);
-    const int nlist = sList[0];
-    for (int it = tid; it < nlist * NG; it += blockDim.x) {
-        const int entry = sList[1 + it / NG], gg = it % NG;
-        const int ee = entry / 3, f = entry - ee * 3, fg = f * NG + gg;
-        const int4 nbw = sNb[ee];
-        const int nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
-        const int fgn = code_face(nbw.w, f) * NG + (NG - 1 - gg);
-        const float* ig = sIgF + fgn * NP;
-        const float* un = p.Us + (long long)nb * 4 * NP;
-        float* dst = sNbv + (ee * NF + fg) * S::NBV_C;
+    {
+        constexpr int GH = (NG + 1) / 2;
+        const int nitems = sList[0] * 8;
+        float un[NP], sen = 0.f;
+        auto load_item = [&](int it) {
+            const int entry = sList[1 + (it >> 3)], w = it & 3;
+            const int ee = entry / 3, f = entry - ee * 3;
+            const int4 nbw = sNb[ee];
+            const long long nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
+            const float* src = p.Us + (nb * 4 + w) * NP;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) un[j] = __ldg(src + j);
+            sen = sqrtf(__ldg(p.eps + nb));
+        };
+        auto store_item = [&](int it) {
+            const int entry = sList[1 + (it >> 3)], w = it & 3, hp = (it >> 2) & 1;
+            const int ee = entry / 3, f = entry - ee * 3;
+            const int fn = code_face(sNb[ee].w, f);
+            const int g1 = hp ? NG : GH;
 #pragma unroll 1
-        for (int w = 0; w < 4; ++w) {
-            float a = 0.f;
-#pragma unroll 5
-            for (int j = 0; j < NP; ++j) a += ig[j] * __ldg(un + w * NP + j);
-            dst[w] = a;
+            for (int gg = hp * GH; gg < g1; ++gg) {
+                const float* ig = sIgF + (fn * NG + (NG - 1 - gg)) * NP;
+                float* dst = sNbv + (ee * NF + f * NG + gg) * S::NBV_C;
+                float a = 0.f;
+#pragma unroll
+                for (int j = 0; j < NP; ++j) a += ig[j] * un[j];
+                dst[w] = a;
+                if (w == 0) dst[4] = sen;
+            }
+        };
+        int it = tid;
+        const bool first = it < nitems;
+        if (first) load_item(it);
+        if (!tc::mbar_wait(&bars[0], nwait & 1)) atomicOr(err, 8);
+        ++nwait;
+        tc::fence_after_sync();
+        if (first) store_item(it);
+        for (it += blockDim.x; it < nitems; it += blockDim.x) {
+            load_item(it);
+            store_item(it);
         }
-        dst[4] = sqrtf(__ldg(p.eps + nb));
     }
     const float mean_v = sMean[row];
     if (half == 0) {

@@ -74,10 +74,11 @@ struct TcLayout {
 
 // Shared-memory carve-up of the tensor-core kernel.  Regions whose
 // lifetimes do not overlap share storage: the out-of-tile neighbour traces
-// reuse the G1 operand region once G1 has completed, the cubature transpose
-// stage reuses the trace region once the face fluxes are done, and the
-// epilogue reuses the G2 staging rows.  One or two A2 buffers: two when the
-// CTA then still fits twice on an SM (or cannot fit twice anyway).
+// reuse the G1 operand region once G1 has completed; the trace region holds
+// the own traces, then the face fluxes (in place), then the warp-private
+// transposes of the cubature chunks, then the epilogue rows.  Two A2
+// buffers, so that the tensor core works on one chunk while the next is
+// written.
 template <int N, bool AV>
 struct TcSmem {
     using D = TcDims<N>;
@@ -97,19 +98,13 @@ struct TcSmem {
     static constexpr int sA1 = al(sIGF + D::NF * D::NP * 4);                  // G1 operands, then neighbour traces
     static constexpr int A1_REGION = al(mx(A1_BYTES * (AV ? 3 : 1), NBV_BYTES));
     static constexpr int A2_BYTES = 128 * 32 * 4;
+    static constexpr int NBUF = 2;
     static constexpr int TR_FLOATS = 128 * D::NFS;
-    static constexpr int ST1 = 32 * 68;                                      // [e][16 q x 4 v + 4]
-    static constexpr int ST2 = 128 * 36;                                     // [row][32 + 4]
-    static constexpr int TR_REGION = al(mx(TR_FLOATS * 4 * (AV ? 2 : 1), ST1 * 4));
-    static constexpr int IO_REGION = al(mx(ST2 * 4, 32 * 4 * D::NP * 4));
-    static constexpr int SMALL = 128 * 4 + 32 * 16 * 4 + 32 * 8 * 4 + 32 * 4 + 32 * 16 + 4 * 8 + 16 + 100 * 4;
-    static constexpr int total_for(int nbuf) { return sA1 + A1_REGION + nbuf * A2_BYTES + TR_REGION + IO_REGION + SMALL; }
-    static constexpr int TWO_PER_SM = 113 * 1024;
-    static constexpr int NBUF = (total_for(2) <= TWO_PER_SM || total_for(1) > TWO_PER_SM) ? 2 : 1;
+    static constexpr int WST = 32 * 18;                                      // floats per warp: cubature transpose
+    static constexpr int TR_REGION = al(mx(mx(TR_FLOATS * 4 * (AV ? 2 : 1), 8 * WST * 4), 32 * 4 * D::NP * 4));
     static constexpr int sA2 = sA1 + A1_REGION;
     static constexpr int sTR = sA2 + NBUF * A2_BYTES;
-    static constexpr int sIO = sTR + TR_REGION;
-    static constexpr int sMEAN = sIO + IO_REGION;                            // [128]
+    static constexpr int sMEAN = sTR + TR_REGION;                            // [128]
     static constexpr int sGEO = sMEAN + 128 * 4;                             // [32][16]
     static constexpr int sFB = sGEO + 32 * 16 * 4;                           // [32][8] mean flux
     static constexpr int sSE = sFB + 32 * 8 * 4;                             // [32] sqrt(eps)
@@ -117,8 +112,10 @@ struct TcSmem {
     static constexpr int sBAR = sNB + 32 * 16;                               // 4 mbarriers
     static constexpr int sTMEM = sBAR + 4 * 8;
     static constexpr int sLIST = sTMEM + 16;                                 // out-of-tile faces: n, then (e,f)
-    static constexpr int TOTAL = sLIST + 100 * 4;
+    static constexpr int sFL = sLIST + 100 * 4;                              // faces owned by the tile: n, then (e,f)
+    static constexpr int TOTAL = sFL + 100 * 4;
     static_assert(TOTAL <= 232448, "tensor-core tile exceeds the shared-memory limit");
+    static_assert(D::CA <= NBUF, "viscous chunks are written at tile start, one per A2 buffer");
     // a curved tile (CUDA-core body) may overwrite everything before sMEAN
     static_assert(Tile<N, float>::smem_stage(AV) <= (size_t)sMEAN, "curved tile would clobber the tile state");
 };
@@ -195,7 +192,8 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     using D = TcDims<N>;
     using S = TcSmem<N, AV>;
     constexpr int NP = D::NP, NQ = D::NQ, NG = D::NG, NF = D::NF, NPK = D::NPK, FOFF = D::FOFF;
-    constexpr int N1 = D::N1, NFP = D::NFP, N2 = D::N2, NFS = D::NFS;
+    constexpr int N1 = D::N1, NFP = D::NFP, N2 = D::N2, NFS = D::NFS, CF = D::CF, CQ = D::CQ, CA = D::CA;
+    constexpr int B2C = TcLayout<N>::B2_CHUNK;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = (warp & 3) * 32 + lane;     // TMEM lane = (element, variable) row
     const int half = warp >> 2;                 // which half of the columns this thread loads
@@ -211,16 +209,28 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     int4* sNb = reinterpret_cast<int4*>(smem + S::sNB);
     float* sTr = reinterpret_cast<float*>(smem + S::sTR);
     float* sQn = sTr + S::TR_FLOATS;            // AV: sqrt(eps) q.n at own face points
-    float* sIO = reinterpret_cast<float*>(smem + S::sIO);
-    float* st1 = sTr;                           // [e][q x 4 + 4], after the face fluxes
-    float* st2 = sIO;                           // [row][36]
     const float* sIgF = reinterpret_cast<const float*>(smem + S::sIGF);
     unsigned char* A1 = smem + S::sA1;
-
-    // ---------------- per-element data and the state deviations
     int* sList = reinterpret_cast<int*>(smem + S::sLIST);
+    int* sFL = reinterpret_cast<int*>(smem + S::sFL);
+
+    // G2 runs as a sequence of K chunks; chunk number s uses A2 buffer s % 2.
+    auto a2_buf = [&](int s) { return smem + S::sA2 + (s & 1) * S::A2_BYTES; };
+    auto wait_buf = [&](int b) {   // every product issued from buffer b has completed
+        while (ph.waits[b] < ph.commits[b]) {
+            if (!tc::mbar_wait(&bars[b], ph.waits[b] & 1)) atomicOr(err, 2);
+            ph.waits[b]++;
+        }
+    };
+    auto issue_chunk = [&](int s, int op_chunk) {   // thread 0, after the operand is visible
+        issue_mma<PREC>(tD2, a2_buf(s), smem + S::sB2 + op_chunk * B2C, N2, 32, s > 0);
+        tc::mma_commit(&bars[s & 1]);
+    };
+    int seq = 0;
+
+    // ---------------- per-element data, the lists of faces, and the G1 operands
     if (tid < 32) {
-        int nout = 0, fo[3] = {0, 0, 0};
+        int nout = 0, nown = 0, fo[3] = {0, 0, 0}, fw[3] = {0, 0, 0};
         if (tid < ne) {
             affine_geometry(p.geoA + (e0 + tid) * 4, sGeo + tid * 16);
             const int4 c = p.conn[e0 + tid];
@@ -229,23 +239,33 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
                 const long long nbl = (long long)((f == 0) ? c.x : (f == 1) ? c.y : c.z) - e0;
-                if (code_bc(c.w, f) == 0 && (nbl < 0 || nbl >= ne)) fo[nout++] = f;
+                const bool bnd = code_bc(c.w, f) != 0;
+                const bool out = !bnd && (nbl < 0 || nbl >= ne);
+                if (out) fo[nout++] = f;
+                // each face point's flux is computed once: by the element itself
+                // on boundary and out-of-tile faces, by the lower-numbered
+                // element of an in-tile pair
+                if (bnd || out || nbl > tid) fw[nown++] = f;
             }
         } else {  // padding element: unit geometry, farfield faces, never stored
             for (int i = 0; i < 16; ++i) sGeo[tid * 16 + i] = (i == 4 || i == 7 || i == 10 || i == 13) ? 1.f : 0.f;
             sNb[tid] = make_int4(0, 0, 0, 0x888);
             sSe[tid] = 0.f;
         }
-        // the out-of-tile faces of the tile as a compact list (warp scan)
-        int incl = nout;
+        // both lists as compact arrays (one warp scan of the packed counts)
+        int incl = nout | (nown << 16);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, o);
             if (tid >= o) incl += y;
         }
-        const int excl = incl - nout;
-        for (int i = 0; i < nout; ++i) sList[1 + excl + i] = tid * 3 + fo[i];
-        if (tid == 31) sList[0] = incl;
+        const int excl_o = (incl & 0xffff) - nout, excl_w = (incl >> 16) - nown;
+        for (int i = 0; i < nout; ++i) sList[1 + excl_o + i] = tid * 3 + fo[i];
+        for (int i = 0; i < nown; ++i) sFL[1 + excl_w + i] = tid * 3 + fw[i];
+        if (tid == 31) {
+            sList[0] = incl & 0xffff;
+            sFL[0] = incl >> 16;
+        }
     }
     const long long k = e0 + e;
     const bool live = e < ne;
@@ -274,16 +294,49 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
             store8<PREC>(A1, row, j0, NPK, x);
         }
     } else if constexpr (AV) {
+        // q rows: the G1 operands for the q traces, and the viscous chunks
+        // sqrt(eps) (J r_x q_x + J r_y q_y), sqrt(eps) (J s_x q_x + J s_y q_y)
+        // at the nodes, written straight into the first A2 buffers
+        float qx[NP], qy[NP];
+        const float* src = p.q + (k * 8 + v) * NP;
 #pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            unsigned char* Aq = A1 + (1 + m) * S::A1_BYTES;
-            const float* src = p.q + ((k * 2 + m) * 4 + v) * NP;
+        for (int j = 0; j < NP; ++j) {
+            qx[j] = live ? src[j] : 0.f;
+            qy[j] = live ? src[4 * NP + j] : 0.f;
+        }
+        float g[16];
+        float se = 0.f;
+        if (live) {
+            affine_geometry(p.geoA + k * 4, g);
+            se = sqrtf(p.eps[k]);
+        } else {
+            g[0] = g[1] = g[2] = g[3] = 0.f;
+        }
 #pragma unroll
-            for (int j0 = 0; j0 < NPK; j0 += 8) {
-                float x[8];
+        for (int j0 = 0; j0 < NPK; j0 += 8) {
+            float x[8], y[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) x[i] = (live && j0 + i < NP) ? src[j0 + i] : 0.f;
-                store8<PREC>(Aq, row, j0, NPK, x);
+            for (int i = 0; i < 8; ++i) {
+                x[i] = (j0 + i < NP) ? qx[j0 + i] : 0.f;
+                y[i] = (j0 + i < NP) ? qy[j0 + i] : 0.f;
+            }
+            store8<PREC>(A1 + S::A1_BYTES, row, j0, NPK, x);
+            store8<PREC>(A1 + 2 * S::A1_BYTES, row, j0, NPK, y);
+        }
+#pragma unroll
+        for (int ca = 0; ca < CA; ++ca) {
+#pragma unroll
+            for (int k0 = 0; k0 < 16; k0 += 8) {
+                float ar[8], as[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int j = ca * 16 + k0 + i;
+                    const float a = (j < NP) ? qx[j] : 0.f, b = (j < NP) ? qy[j] : 0.f;
+                    ar[i] = se * (g[0] * a + g[1] * b);
+                    as[i] = se * (g[2] * a + g[3] * b);
+                }
+                store8<PREC>(a2_buf(ca), row, k0, 32, ar);
+                store8<PREC>(a2_buf(ca), row, 16 + k0, 32, as);
             }
         }
     }
@@ -292,7 +345,8 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     __syncthreads();
     tc::fence_after_sync();
 
-    // ---------------- G1: state deviations to cubature and face points
+    // ---------------- G1: state deviations to cubature and face points; the
+    // viscous chunks of G2 start at once
     if (tid == 0) {
         issue_mma<PREC>(tD1, A1, smem + S::sB1, N1, NPK, false);
         if constexpr (AV) {
@@ -300,6 +354,12 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
             issue_mma<PREC>(tD1q + NFP, A1 + 2 * S::A1_BYTES, smem + S::sB1Q, NFP, NPK, false);
         }
         tc::mma_commit(&bars[2]);
+        if constexpr (AV)
+            for (int ca = 0; ca < CA; ++ca) issue_chunk(ca, CF + CQ + ca);
+    }
+    if constexpr (AV) {
+        for (int ca = 0; ca < CA; ++ca) ph.commits[ca & 1]++;
+        seq = CA;
     }
     if (tid < 128) {   // flux of the element-mean state, one (element, variable) per thread
         float Ub[4], Fb[4], Gb[4];
@@ -309,44 +369,70 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
         sFb[e * 8 + v] = Fb[v];
         sFb[e * 8 + 4 + v] = Gb[v];
     }
-    if (!tc::mbar_wait(&bars[2], ph.g1 & 1)) atomicOr(err, 1);
-    ph.g1++;
-    tc::fence_after_sync();
+
     // out-of-tile neighbours' traces at the reversed face points, from their
-    // states in L2, into the G1 operand region (G1 has completed)
+    // states in L2, into the G1 operand region once G1 has completed.  One
+    // item per (face, variable, half of the face points); the item's loads
+    // are issued before the wait for G1 so that their latency overlaps it.
     float* sNbv = reinterpret_cast<float*>(smem + S::sA1);
-    const int nlist = sList[0];
-    for (int it = tid; it < nlist * NG; it += blockDim.x) {
-        const int entry = sList[1 + it / NG], gg = it % NG;
-        const int ee = entry / 3, f = entry - ee * 3, fg = f * NG + gg;
-        const int4 nbw = sNb[ee];
-        const int nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
-        const int fgn = code_face(nbw.w, f) * NG + (NG - 1 - gg);
-        const float* ig = sIgF + fgn * NP;
-        const float* un = p.Us + (long long)nb * 4 * NP;
-        float* dst = sNbv + (ee * NF + fg) * S::NBV_C;
-#pragma unroll 1
-        for (int w = 0; w < 4; ++w) {
-            float a = 0.f;
-#pragma unroll 5
-            for (int j = 0; j < NP; ++j) a += ig[j] * __ldg(un + w * NP + j);
-            dst[w] = a;
-        }
-        if constexpr (AV) {
+    {
+        constexpr int GH = (NG + 1) / 2;
+        const int nitems = sList[0] * 8;
+        float un[NP], qx[AV ? NP : 1], qy[AV ? NP : 1];
+        float sen = 0.f;
+        auto load_item = [&](int it) {
+            const int entry = sList[1 + (it >> 3)], w = it & 3;
+            const int ee = entry / 3, f = entry - ee * 3;
+            const int4 nbw = sNb[ee];
+            const long long nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
+            const float* src = p.Us + (nb * 4 + w) * NP;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) un[j] = __ldg(src + j);
+            if constexpr (AV) {
+                const float* q0 = p.q + (nb * 8 + w) * NP;
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    qx[j] = __ldg(q0 + j);
+                    qy[j] = __ldg(q0 + 4 * NP + j);
+                }
+                sen = sqrtf(__ldg(p.eps + nb));
+            }
+        };
+        auto store_item = [&](int it) {
+            const int entry = sList[1 + (it >> 3)], w = it & 3, hp = (it >> 2) & 1;
+            const int ee = entry / 3, f = entry - ee * 3;
+            const int fn = code_face(sNb[ee].w, f);
             const float* ge = sGeo + ee * 16;
             const float nx = ge[5 + 3 * f], ny = ge[6 + 3 * f];
-            const float sen = sqrtf(__ldg(p.eps + nb));
-            const float* qn_ = p.q + (long long)nb * 8 * NP;
+            const int g1 = hp ? NG : GH;
 #pragma unroll 1
-            for (int w = 0; w < 4; ++w) {
-                float ax = 0.f, ay = 0.f;
-#pragma unroll 5
+            for (int gg = hp * GH; gg < g1; ++gg) {
+                const int fg = f * NG + gg;
+                const float* ig = sIgF + (fn * NG + (NG - 1 - gg)) * NP;
+                float* dst = sNbv + (ee * NF + fg) * S::NBV_C;
+                float a = 0.f, ax = 0.f, ay = 0.f;
+#pragma unroll
                 for (int j = 0; j < NP; ++j) {
-                    ax += ig[j] * __ldg(qn_ + w * NP + j);
-                    ay += ig[j] * __ldg(qn_ + (4 + w) * NP + j);
+                    a += ig[j] * un[j];
+                    if constexpr (AV) {
+                        ax += ig[j] * qx[j];
+                        ay += ig[j] * qy[j];
+                    }
                 }
-                dst[4 + w] = sen * (ax * nx + ay * ny);
+                dst[w] = a;
+                if constexpr (AV) dst[4 + w] = sen * (ax * nx + ay * ny);
             }
+        };
+        int it = tid;
+        const bool first = it < nitems;
+        if (first) load_item(it);
+        if (!tc::mbar_wait(&bars[2], ph.g1 & 1)) atomicOr(err, 1);
+        ph.g1++;
+        tc::fence_after_sync();
+        if (first) store_item(it);
+        for (it += blockDim.x; it < nitems; it += blockDim.x) {
+            load_item(it);
+            store_item(it);
         }
     }
 
@@ -382,66 +468,31 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     }
     __syncthreads();
 
-    // ---------------- G2 chunk pipeline
-    int chunk = 0;
-    auto begin_chunk = [&](int c) -> unsigned char* {
-        const int buf = c % S::NBUF;
-        // the buffer is free once every product issued from it has completed
-        while (ph.waits[buf] < ph.commits[buf]) {
-            if (!tc::mbar_wait(&bars[buf], ph.waits[buf] & 1)) atomicOr(err, 2);
-            ph.waits[buf]++;
-        }
-        return smem + S::sA2 + buf * S::A2_BYTES;
-    };
-    auto end_chunk = [&](int c) {
-        tc::fence_async_smem();
-        __syncthreads();
-        const int buf = c % S::NBUF;
-        if (tid == 0) {
-            tc::fence_after_sync();
-            issue_mma<PREC>(tD2, smem + S::sA2 + buf * S::A2_BYTES, smem + S::sB2 + c * TcLayout<N>::B2_CHUNK, N2,
-                            32, c > 0);
-            tc::mma_commit(&bars[buf]);
-        }
-        ph.commits[buf]++;
-    };
-    // rows of st2 (36 floats: 32 slots + 4 pad) to the A2 chunk, 16 slots per half
-    auto st2_to_a2 = [&](unsigned char* A2) {
-#pragma unroll
-        for (int s0 = 0; s0 < 16; s0 += 8) {
-            const float4 a = *reinterpret_cast<const float4*>(st2 + row * 36 + half * 16 + s0);
-            const float4 b = *reinterpret_cast<const float4*>(st2 + row * 36 + half * 16 + s0 + 4);
-            const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-            store8<PREC>(A2, row, half * 16 + s0, 32, x);
-        }
-    };
-
-    // face chunk: (F*.n - (sqrt(eps) q)*.n - F(Ubar).n) sJ for the 4 variables of (element, face point)
-    static_assert(D::CF == 1, "one face chunk");
+    // ---------------- face fluxes, once per face point, in place:
+    // (F*.n - (sqrt(eps) q)*.n - F(Ubar).n) sJ replaces the trace of each
+    // side.  F* from the other side of an in-tile face is -F*.
     {
-        unsigned char* A2 = begin_chunk(chunk);
-        for (int it = tid; it < 128 * 36 / 4; it += blockDim.x)
-            reinterpret_cast<float4*>(st2)[it] = make_float4(0.f, 0.f, 0.f, 0.f);
-        __syncthreads();
-        for (int it = tid; it < 32 * NF; it += blockDim.x) {
-            const int ee = it / NF, fg = it - ee * NF;
-            const int f = fg / NG, gg = fg - f * NG;
+        const int nitems = sFL[0] * NG;
+        for (int it = tid; it < nitems; it += blockDim.x) {
+            const int entry = sFL[1 + it / NG], gg = it % NG;
+            const int ee = entry / 3, f = entry - ee * 3, fg = f * NG + gg;
             const int4 nbw = sNb[ee];
             const int bc = code_bc(nbw.w, f);
             const int nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
-            const int fgn = code_face(nbw.w, f) * NG + (NG - 1 - gg);
+            const int fn = code_face(nbw.w, f), fgn = fn * NG + (NG - 1 - gg);
             const float* ge = sGeo + ee * 16;
             const float nx = ge[5 + 3 * f], ny = ge[6 + 3 * f], sJ = ge[7 + 3 * f];
+            const long long nbll = (long long)nb - e0;
+            const bool in_tile = (bc == 0) && nbll >= 0 && nbll < ne;
+            const int nbl = in_tile ? (int)nbll : 0;
             float Um[4], Up[4];
 #pragma unroll
             for (int w = 0; w < 4; ++w) Um[w] = sTr[(ee * 4 + w) * NFS + fg];
-            const long long nbl = (long long)nb - e0;
-            const bool in_tile = (bc == 0) && nbl >= 0 && nbl < ne;
             if (bc != 0) {
                 ghost_state(Um, bc, nx, ny, p.uinf, Up);
             } else if (in_tile) {
 #pragma unroll
-                for (int w = 0; w < 4; ++w) Up[w] = sTr[((int)nbl * 4 + w) * NFS + fgn];
+                for (int w = 0; w < 4; ++w) Up[w] = sTr[(nbl * 4 + w) * NFS + fgn];
             } else {
 #pragma unroll
                 for (int w = 0; w < 4; ++w) Up[w] = sNbv[(ee * NF + fg) * S::NBV_C + w];
@@ -456,7 +507,7 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
                     if (bc != 0) {
                         other = own;
                     } else if (in_tile) {
-                        other = -sQn[((int)nbl * 4 + w) * NFS + fgn];
+                        other = -sQn[(nbl * 4 + w) * NFS + fgn];
                     } else {
                         other = sNbv[(ee * NF + fg) * S::NBV_C + 4 + w];
                     }
@@ -465,90 +516,120 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
             }
 #pragma unroll
             for (int w = 0; w < 4; ++w)
-                st2[(ee * 4 + w) * 36 + fg] = (Fn[w] - (sFb[ee * 8 + w] * nx + sFb[ee * 8 + 4 + w] * ny)) * sJ;
+                sTr[(ee * 4 + w) * NFS + fg] = (Fn[w] - (sFb[ee * 8 + w] * nx + sFb[ee * 8 + 4 + w] * ny)) * sJ;
+            if (in_tile) {
+                const float* gn = sGeo + nbl * 16;
+                const float mx = gn[5 + 3 * fn], my = gn[6 + 3 * fn], sJn = gn[7 + 3 * fn];
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+                    sTr[(nbl * 4 + w) * NFS + fgn] =
+                        (-Fn[w] - (sFb[nbl * 8 + w] * mx + sFb[nbl * 8 + 4 + w] * my)) * sJn;
+            }
         }
+    }
+    __syncthreads();
+
+    // ---------------- face chunk: the rows of the flux region, 16 slots per half
+    static_assert(CF == 1, "one face chunk");
+    {
+        wait_buf(seq & 1);
+        unsigned char* A2 = a2_buf(seq);
+#pragma unroll
+        for (int s0 = 0; s0 < 16; s0 += 8) {
+            float x[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int c = half * 16 + s0 + i;
+                x[i] = (c < NF) ? sTr[row * NFS + c] : 0.f;
+            }
+            store8<PREC>(A2, row, half * 16 + s0, 32, x);
+        }
+        tc::fence_async_smem();
         __syncthreads();
-        st2_to_a2(A2);
-        end_chunk(chunk);
-        ++chunk;
+        if (tid == 0) {
+            tc::fence_after_sync();
+            issue_chunk(seq, 0);
+        }
+        ph.commits[seq & 1]++;
+        ++seq;
     }
 
-    // cubature chunks: contravariant flux deviations, one flux per (element, point)
+    // ---------------- cubature chunks: contravariant flux deviations.  Each
+    // warp owns 8 elements (its 32 rows) and 8 of the 16 points of the chunk;
+    // the (variable x point) block is transposed through the warp's own slice
+    // of the trace region, one flux per (element, point).
+    {
+        float* wst = sTr + warp * S::WST;
+        const int eb = (warp & 3) * 8;             // first element of this warp
 #pragma unroll 1
-    for (int cq = 0; cq < D::CQ; ++cq, ++chunk) {
-        unsigned char* A2 = begin_chunk(chunk);
-        {
+        for (int cq = 0; cq < CQ; ++cq, ++seq) {
             float x[8];
             tc::tmem_ld8(tD1 + lane_base + cq * 16 + half * 8, x);
             tc::tmem_ld_wait();
+            // [element][point][variable], element stride 36: conflict-free
 #pragma unroll
-            for (int i = 0; i < 8; ++i) st1[e * 68 + (half * 8 + i) * 4 + v] = x[i] + mean_v;
-        }
-        __syncthreads();
-        constexpr int LASTV = NQ - 16 * (D::CQ - 1);          // valid points in the last chunk
-        const int nvalid = (cq == D::CQ - 1) ? LASTV : 16;
-        for (int it = tid; it < 32 * nvalid; it += blockDim.x) {
-            const int ee = it / nvalid, ql = it - ee * nvalid;
-            const float4 U4 = *reinterpret_cast<const float4*>(st1 + ee * 68 + ql * 4);
-            const float Uc[4] = {U4.x, U4.y, U4.z, U4.w};
-            float F[4], G[4];
-            euler_flux(Uc, p.gamma, F, G);
-            const float* ge = sGeo + ee * 16;
-            const float jrx = ge[0], jry = ge[1], jsx = ge[2], jsy = ge[3];
+            for (int i = 0; i < 8; ++i) wst[(lane >> 2) * 36 + i * 4 + v] = x[i] + mean_v;
+            __syncwarp();
+            float4 U4[2];
 #pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                const float dF = F[w] - sFb[ee * 8 + w], dG = G[w] - sFb[ee * 8 + 4 + w];
-                st2[(ee * 4 + w) * 36 + ql] = jrx * dF + jry * dG;
-                st2[(ee * 4 + w) * 36 + 16 + ql] = jsx * dF + jsy * dG;
+            for (int r = 0; r < 2; ++r) {
+                const int pp = lane + 32 * r;
+                U4[r] = *reinterpret_cast<const float4*>(wst + (pp >> 3) * 36 + (pp & 7) * 4);
             }
-        }
-        if (nvalid < 16)   // padded points of the last chunk
-            for (int it = tid; it < 128 * (16 - nvalid); it += blockDim.x) {
-                const int r = it / (16 - nvalid), ql = nvalid + it % (16 - nvalid);
-                st2[r * 36 + ql] = 0.f;
-                st2[r * 36 + 16 + ql] = 0.f;
-            }
-        __syncthreads();
-        st2_to_a2(A2);
-        end_chunk(chunk);
-    }
-
-    // viscous chunks: sqrt(eps) (J r_x q_x + J r_y q_y), sqrt(eps) (J s_x q_x + J s_y q_y) at nodes
-    if constexpr (AV) {
-        const float* ge = sGeo + e * 16;
-        const float jrx = ge[0], jry = ge[1], jsx = ge[2], jsy = ge[3];
-        const float se = sSe[e];
-#pragma unroll 1
-        for (int ca = 0; ca < D::CA; ++ca, ++chunk) {
-            unsigned char* A2 = begin_chunk(chunk);
-            const int j0 = ca * 16 + half * 8;
-            float ar[8], as[8];
-            const float* qx = p.q + ((k * 2 + 0) * 4 + v) * NP;
-            const float* qy = p.q + ((k * 2 + 1) * 4 + v) * NP;
+            __syncwarp();
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int j = j0 + i;
-                const float a = (live && j < NP) ? qx[j] : 0.f;
-                const float b = (live && j < NP) ? qy[j] : 0.f;
-                ar[i] = se * (jrx * a + jry * b);
-                as[i] = se * (jsx * a + jsy * b);
+            for (int r = 0; r < 2; ++r) {
+                const int pp = lane + 32 * r, el = pp >> 3, ip = pp & 7;
+                const int qn = cq * 16 + half * 8 + ip;
+                const float Uc[4] = {U4[r].x, U4[r].y, U4[r].z, U4[r].w};
+                float F[4], G[4];
+                euler_flux(Uc, p.gamma, F, G);
+                const float* ge = sGeo + (eb + el) * 16;
+                const float* fb = sFb + (eb + el) * 8;
+                const float jrx = ge[0], jry = ge[1], jsx = ge[2], jsy = ge[3];
+                const bool valid = qn < NQ;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const float dF = F[w] - fb[w], dG = G[w] - fb[4 + w];
+                    // rows (element, variable) with stride 18: conflict-free
+                    wst[(el * 4 + w) * 18 + ip] = valid ? jrx * dF + jry * dG : 0.f;
+                    wst[(el * 4 + w) * 18 + 8 + ip] = valid ? jsx * dF + jsy * dG : 0.f;
+                }
             }
-            store8<PREC>(A2, row, half * 8, 32, ar);
-            store8<PREC>(A2, row, 16 + half * 8, 32, as);
-            end_chunk(chunk);
+            __syncwarp();
+            wait_buf(seq & 1);
+            unsigned char* A2 = a2_buf(seq);
+            {
+                const float2* rw = reinterpret_cast<const float2*>(wst + lane * 18);
+                float ar[8], as[8];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float2 a = rw[i], b = rw[4 + i];
+                    ar[2 * i] = a.x;
+                    ar[2 * i + 1] = a.y;
+                    as[2 * i] = b.x;
+                    as[2 * i + 1] = b.y;
+                }
+                store8<PREC>(A2, row, half * 8, 32, ar);
+                store8<PREC>(A2, row, 16 + half * 8, 32, as);
+            }
+            tc::fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                issue_chunk(seq, CF + cq);
+            }
+            ph.commits[seq & 1]++;
         }
     }
 
     // ---------------- epilogue: L = D2 / J into shared memory, then a
     // coalesced pass over the tile for the stage combination
-    for (int b = 0; b < 2; ++b)
-        while (ph.waits[b] < ph.commits[b]) {
-            if (!tc::mbar_wait(&bars[b], ph.waits[b] & 1)) atomicOr(err, 4);
-            ph.waits[b]++;
-        }
+    wait_buf(0);
+    wait_buf(1);
     tc::fence_after_sync();
     {
-        float* sOut = sIO;
+        float* sOut = sTr;
         const float invJ = sGeo[e * 16 + 4];
         constexpr int per_half = N2 / 2;
 #pragma unroll
