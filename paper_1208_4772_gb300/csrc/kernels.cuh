@@ -39,9 +39,14 @@ struct Tile {
     static constexpr size_t smem_grad() { return sizeof(Real) * (size_t)(OPS_G + E * PER_E_G); }
 };
 
+// Correctly rounded reciprocal (the same value as 1 / x, without the general
+// division sequence).
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+
 template <typename Real>
 __device__ __forceinline__ void euler_flux(const Real U[4], Real gamma, Real F[4], Real G[4]) {
-    const Real ir = Real(1) / U[0];
+    const Real ir = recip(U[0]);
     const Real u = U[1] * ir, v = U[2] * ir;
     const Real p = (gamma - Real(1)) * (U[3] - Real(0.5) * (U[1] * u + U[2] * v));
     F[0] = U[1];
@@ -62,7 +67,7 @@ __device__ __forceinline__ void llf_flux(const Real Um[4], const Real Up[4], Rea
     Real Fm[4], Gm[4], Fp[4], Gp[4];
     euler_flux(Um, gamma, Fm, Gm);
     euler_flux(Up, gamma, Fp, Gp);
-    const Real irm = Real(1) / Um[0], irp = Real(1) / Up[0];
+    const Real irm = recip(Um[0]), irp = recip(Up[0]);
     const Real pm = (gamma - Real(1)) * (Um[3] - Real(0.5) * (Um[1] * Um[1] + Um[2] * Um[2]) * irm);
     const Real pp = (gamma - Real(1)) * (Up[3] - Real(0.5) * (Up[1] * Up[1] + Up[2] * Up[2]) * irp);
     const Real lm = fabs((Um[1] * nx + Um[2] * ny) * irm) + sqrt(gamma * pm * irm);

@@ -32,18 +32,18 @@ struct TgSmem {
     static constexpr int A1_REGION = al(mx(A1_BYTES, 32 * D::NF * NBV_C * 4));
     static constexpr int A2_BYTES = 128 * 32 * 4;
     static constexpr int sA2 = sA1 + A1_REGION;                    // USx, USy operands
-    static constexpr int ST2 = 128 * 36;
-    static constexpr int sTR = sA2 + 2 * A2_BYTES;                 // [128][NFS] traces
-    static constexpr int sIO = al(sTR + 128 * D::NFS * 4);         // staging x, y; then q tile
-    static constexpr int IO_REGION = al(mx(2 * ST2 * 4, 32 * 8 * D::NP * 4));
-    static constexpr int sMEAN = sIO + IO_REGION;
+    static constexpr int sTR = sA2 + 2 * A2_BYTES;                 // [128][NFS] traces, then face terms
+    static constexpr int sIO = al(sTR + 128 * D::NFS * 4);         // q tile
+    static constexpr int IO_REGION = al(32 * 8 * D::NP * 4);
+    static constexpr int sMEAN = al(mx(sIO + IO_REGION, (int)Tile<N, float>::smem_grad()));  // curved tiles use all below
     static constexpr int sGEO = sMEAN + 128 * 4;
     static constexpr int sSE = sGEO + 32 * 16 * 4;
     static constexpr int sNB = sSE + 32 * 4;
     static constexpr int sBAR = sNB + 32 * 16;
     static constexpr int sTMEM = sBAR + 4 * 8;
     static constexpr int sLIST = sTMEM + 16;                       // out-of-tile faces: n, then (e,f)
-    static constexpr int TOTAL = sLIST + 100 * 4;
+    static constexpr int sFL = sLIST + 100 * 4;                    // faces owned by the tile: n, then (e,f)
+    static constexpr int TOTAL = sFL + 100 * 4;
     static constexpr int TMEM_COLS = (D::NFP + 4 * D::N2) <= 128 ? 128 : 256;
     static_assert(TOTAL <= 232448, "gradient tile exceeds the shared-memory limit");
     static_assert(Tile<N, float>::smem_grad() <= (size_t)sMEAN, "curved tile would clobber the tile state");
@@ -68,39 +68,12 @@ __device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q
     float* sSe = reinterpret_cast<float*>(smem + S::sSE);
     int4* sNb = reinterpret_cast<int4*>(smem + S::sNB);
     float* sTr = reinterpret_cast<float*>(smem + S::sTR);
-    float* stx = reinterpret_cast<float*>(smem + S::sIO);
-    float* sty = stx + S::ST2;
     const float* sIgF = reinterpret_cast<const float*>(smem + S::sIGF);
     unsigned char* A1 = smem + S::sA1;
 
     int* sList = reinterpret_cast<int*>(smem + S::sLIST);
-    if (tid < 32) {
-        int nout = 0, fo[3] = {0, 0, 0};
-        if (tid < ne) {
-            affine_geometry(p.geoA + (e0 + tid) * 4, sGeo + tid * 16);
-            const int4 c = p.conn[e0 + tid];
-            sNb[tid] = c;
-            sSe[tid] = sqrtf(p.eps[e0 + tid]);
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                const long long nbl = (long long)((f == 0) ? c.x : (f == 1) ? c.y : c.z) - e0;
-                if (code_bc(c.w, f) == 0 && (nbl < 0 || nbl >= ne)) fo[nout++] = f;
-            }
-        } else {
-            for (int i = 0; i < 16; ++i) sGeo[tid * 16 + i] = (i == 4 || i == 7 || i == 10 || i == 13) ? 1.f : 0.f;
-            sNb[tid] = make_int4(0, 0, 0, 0x888);
-            sSe[tid] = 0.f;
-        }
-        int incl = nout;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (tid >= o) incl += y;
-        }
-        const int excl = incl - nout;
-        for (int i = 0; i < nout; ++i) sList[1 + excl + i] = tid * 3 + fo[i];
-        if (tid == 31) sList[0] = incl;
-    }
+    int* sFL = reinterpret_cast<int*>(smem + S::sFL);
+    if (tid < 32) tile_info(p, e0, ne, true, sGeo, sNb, sSe, sList, sFL);
     const long long k = e0 + e;
     const bool live = e < ne;
     if (half == 0) {
@@ -195,56 +168,67 @@ __device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q
                 if (c0 + i < NF) sTr[row * NFS + c0 + i] = x[i] + mean_v;
         }
     }
-    for (int i = tid; i < 2 * S::ST2 / 4; i += blockDim.x)
-        reinterpret_cast<float4*>(stx)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
 
-    // face points: n_m sJ ((sqrt(eps) U)* - sqrt(eps) Ubar) for the 4 variables
-    for (int it = tid; it < 32 * NF; it += blockDim.x) {
-        const int ee = it / NF, fg = it - ee * NF;
-        const int f = fg / NG, gg = fg - f * NG;
-        const int4 nbw = sNb[ee];
-        const int bc = code_bc(nbw.w, f);
-        const int nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
-        const int fgn = code_face(nbw.w, f) * NG + (NG - 1 - gg);
-        const float* ge = sGeo + ee * 16;
-        const float nx = ge[5 + 3 * f], ny = ge[6 + 3 * f], sJ = ge[7 + 3 * f];
-        const float se = sSe[ee];
-        float Um[4], Up[4], sep;
+    // face points, once per point, in place: sJ ((sqrt(eps) U)* - sqrt(eps) Ubar)
+    // for the 4 variables replaces the trace of each side; (sqrt(eps) U)* is
+    // the central value, the same from both sides
+    {
+        const int nitems = sFL[0] * NG;
+        for (int it = tid; it < nitems; it += blockDim.x) {
+            const int entry = sFL[1 + it / NG], gg = it % NG;
+            const int ee = entry / 3, f = entry - ee * 3, fg = f * NG + gg;
+            const int4 nbw = sNb[ee];
+            const int bc = code_bc(nbw.w, f);
+            const int nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
+            const int fn = code_face(nbw.w, f), fgn = fn * NG + (NG - 1 - gg);
+            const float* ge = sGeo + ee * 16;
+            const float nx = ge[5 + 3 * f], ny = ge[6 + 3 * f], sJ = ge[7 + 3 * f];
+            const float se = sSe[ee];
+            const long long nbll = (long long)nb - e0;
+            const bool in_tile = (bc == 0) && nbll >= 0 && nbll < ne;
+            const int nbl = in_tile ? (int)nbll : 0;
+            float Um[4], Up[4], sep;
 #pragma unroll
-        for (int w = 0; w < 4; ++w) Um[w] = sTr[(ee * 4 + w) * NFS + fg];
-        const long long nbl = (long long)nb - e0;
-        if (bc != 0) {
-            ghost_state(Um, bc, nx, ny, p.uinf, Up);
-            sep = se;
-        } else if (nbl >= 0 && nbl < ne) {
+            for (int w = 0; w < 4; ++w) Um[w] = sTr[(ee * 4 + w) * NFS + fg];
+            if (bc != 0) {
+                ghost_state(Um, bc, nx, ny, p.uinf, Up);
+                sep = se;
+            } else if (in_tile) {
 #pragma unroll
-            for (int w = 0; w < 4; ++w) Up[w] = sTr[((int)nbl * 4 + w) * NFS + fgn];
-            sep = sSe[(int)nbl];
-        } else {
-            const float* src = sNbv + (ee * NF + fg) * S::NBV_C;
+                for (int w = 0; w < 4; ++w) Up[w] = sTr[(nbl * 4 + w) * NFS + fgn];
+                sep = sSe[nbl];
+            } else {
+                const float* src = sNbv + (ee * NF + fg) * S::NBV_C;
 #pragma unroll
-            for (int w = 0; w < 4; ++w) Up[w] = src[w];
-            sep = src[4];
-        }
+                for (int w = 0; w < 4; ++w) Up[w] = src[w];
+                sep = src[4];
+            }
+            float c[4];
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const float st = (0.5f * (se * Um[w] + sep * Up[w]) - se * sMean[ee * 4 + w]) * sJ;
-            stx[(ee * 4 + w) * 36 + fg] = nx * st;
-            sty[(ee * 4 + w) * 36 + fg] = ny * st;
+            for (int w = 0; w < 4; ++w) {
+                c[w] = 0.5f * (se * Um[w] + sep * Up[w]);
+                sTr[(ee * 4 + w) * NFS + fg] = (c[w] - se * sMean[ee * 4 + w]) * sJ;
+            }
+            if (in_tile) {
+                const float sJn = sGeo[nbl * 16 + 7 + 3 * fn];
+#pragma unroll
+                for (int w = 0; w < 4; ++w) sTr[(nbl * 4 + w) * NFS + fgn] = (c[w] - sep * sMean[nbl * 4 + w]) * sJn;
+            }
         }
     }
     __syncthreads();
-    {
-        unsigned char* Ax = smem + S::sA2;
-        unsigned char* Ay = smem + S::sA2 + S::A2_BYTES;
-        const float* src = half == 0 ? stx : sty;
-        unsigned char* dst = half == 0 ? Ax : Ay;
+    {   // n_x (half 0) or n_y (half 1) times the face terms of the row
+        unsigned char* dst = smem + S::sA2 + half * S::A2_BYTES;
+        const float* ge = sGeo + e * 16 + 5 + half;
 #pragma unroll
         for (int s0 = 0; s0 < 32; s0 += 8) {
-            const float4 a = *reinterpret_cast<const float4*>(src + row * 36 + s0);
-            const float4 b = *reinterpret_cast<const float4*>(src + row * 36 + s0 + 4);
-            const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            float x[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int c = s0 + i;
+                x[i] = (c < NF) ? ge[3 * (c / NG)] * sTr[row * NFS + c] : 0.f;
+            }
             store8<PREC>(dst, row, s0, 32, x);
         }
     }
@@ -262,7 +246,7 @@ __device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q
 
     // epilogue: q_m for (element, variable) rows, then a coalesced store
     {
-        float* sOut = stx;   // [e][2][4][NP]
+        float* sOut = reinterpret_cast<float*>(smem + S::sIO);   // [e][2][4][NP]
         const float* ge = sGeo + e * 16;
         const float jrx = ge[0], jry = ge[1], jsx = ge[2], jsy = ge[3], invJ = ge[4];
         const float se = sSe[e];

@@ -177,6 +177,50 @@ __device__ __forceinline__ void issue_mma(uint32_t d_tmem, const unsigned char* 
     }
 }
 
+// Per-element data of a tensor-core tile, by warp 0: affine geometry,
+// connectivity word, sqrt(eps) (when av), and two compact face lists (count
+// first, then element * 3 + face): sList the faces whose neighbour lies
+// outside the tile, sFL the faces whose flux the tile computes -- boundary
+// and out-of-tile faces by the element itself, an in-tile pair by its
+// lower-numbered element, so that each face point is computed once.
+__device__ __forceinline__ void tile_info(const StageArgs<float>& p, long long e0, int ne, bool av, float* sGeo,
+                                          int4* sNb, float* sSe, int* sList, int* sFL) {
+    const int tid = threadIdx.x;
+    int nout = 0, nown = 0, fo[3] = {0, 0, 0}, fw[3] = {0, 0, 0};
+    if (tid < ne) {
+        affine_geometry(p.geoA + (e0 + tid) * 4, sGeo + tid * 16);
+        const int4 c = p.conn[e0 + tid];
+        sNb[tid] = c;
+        sSe[tid] = av ? sqrtf(p.eps[e0 + tid]) : 0.f;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            const long long nbl = (long long)((f == 0) ? c.x : (f == 1) ? c.y : c.z) - e0;
+            const bool bnd = code_bc(c.w, f) != 0;
+            const bool out = !bnd && (nbl < 0 || nbl >= ne);
+            if (out) fo[nout++] = f;
+            if (bnd || out || nbl > tid) fw[nown++] = f;
+        }
+    } else {  // padding element: unit geometry, farfield faces, never stored
+        for (int i = 0; i < 16; ++i) sGeo[tid * 16 + i] = (i == 4 || i == 7 || i == 10 || i == 13) ? 1.f : 0.f;
+        sNb[tid] = make_int4(0, 0, 0, 0x888);
+        sSe[tid] = 0.f;
+    }
+    // both lists by one warp scan of the packed counts
+    int incl = nout | (nown << 16);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (tid >= o) incl += y;
+    }
+    const int excl_o = (incl & 0xffff) - nout, excl_w = (incl >> 16) - nown;
+    for (int i = 0; i < nout; ++i) sList[1 + excl_o + i] = tid * 3 + fo[i];
+    for (int i = 0; i < nown; ++i) sFL[1 + excl_w + i] = tid * 3 + fw[i];
+    if (tid == 31) {
+        sList[0] = incl & 0xffff;
+        sFL[0] = incl >> 16;
+    }
+}
+
 // Tile body: one tile of up to 32 affine elements.  The operator tables,
 // mbarriers and TMEM are set up once per CTA by the persistent kernel;
 // ph tracks the phases of the mbarriers across tiles.
@@ -229,44 +273,7 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     int seq = 0;
 
     // ---------------- per-element data, the lists of faces, and the G1 operands
-    if (tid < 32) {
-        int nout = 0, nown = 0, fo[3] = {0, 0, 0}, fw[3] = {0, 0, 0};
-        if (tid < ne) {
-            affine_geometry(p.geoA + (e0 + tid) * 4, sGeo + tid * 16);
-            const int4 c = p.conn[e0 + tid];
-            sNb[tid] = c;
-            sSe[tid] = AV ? sqrtf(p.eps[e0 + tid]) : 0.f;
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                const long long nbl = (long long)((f == 0) ? c.x : (f == 1) ? c.y : c.z) - e0;
-                const bool bnd = code_bc(c.w, f) != 0;
-                const bool out = !bnd && (nbl < 0 || nbl >= ne);
-                if (out) fo[nout++] = f;
-                // each face point's flux is computed once: by the element itself
-                // on boundary and out-of-tile faces, by the lower-numbered
-                // element of an in-tile pair
-                if (bnd || out || nbl > tid) fw[nown++] = f;
-            }
-        } else {  // padding element: unit geometry, farfield faces, never stored
-            for (int i = 0; i < 16; ++i) sGeo[tid * 16 + i] = (i == 4 || i == 7 || i == 10 || i == 13) ? 1.f : 0.f;
-            sNb[tid] = make_int4(0, 0, 0, 0x888);
-            sSe[tid] = 0.f;
-        }
-        // both lists as compact arrays (one warp scan of the packed counts)
-        int incl = nout | (nown << 16);
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (tid >= o) incl += y;
-        }
-        const int excl_o = (incl & 0xffff) - nout, excl_w = (incl >> 16) - nown;
-        for (int i = 0; i < nout; ++i) sList[1 + excl_o + i] = tid * 3 + fo[i];
-        for (int i = 0; i < nown; ++i) sFL[1 + excl_w + i] = tid * 3 + fw[i];
-        if (tid == 31) {
-            sList[0] = incl & 0xffff;
-            sFL[0] = incl >> 16;
-        }
-    }
+    if (tid < 32) tile_info(p, e0, ne, AV, sGeo, sNb, sSe, sList, sFL);
     const long long k = e0 + e;
     const bool live = e < ne;
     if (half == 0) {
@@ -561,6 +568,17 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     {
         float* wst = sTr + warp * S::WST;
         const int eb = (warp & 3) * 8;             // first element of this warp
+        // the lane's two (element, point) pairs keep their elements across
+        // chunks: contravariant factors and mean flux in registers
+        float cg[2][4], cf[2][8];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int el = (lane >> 3) + 4 * r;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) cg[r][i] = sGeo[(eb + el) * 16 + i];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) cf[r][i] = sFb[(eb + el) * 8 + i];
+        }
 #pragma unroll 1
         for (int cq = 0; cq < CQ; ++cq, ++seq) {
             float x[8];
@@ -579,21 +597,18 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
             __syncwarp();
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
+                // padded points (beyond NQ) carry the element mean, a finite
+                // value, and meet zero operator columns
                 const int pp = lane + 32 * r, el = pp >> 3, ip = pp & 7;
-                const int qn = cq * 16 + half * 8 + ip;
                 const float Uc[4] = {U4[r].x, U4[r].y, U4[r].z, U4[r].w};
                 float F[4], G[4];
                 euler_flux(Uc, p.gamma, F, G);
-                const float* ge = sGeo + (eb + el) * 16;
-                const float* fb = sFb + (eb + el) * 8;
-                const float jrx = ge[0], jry = ge[1], jsx = ge[2], jsy = ge[3];
-                const bool valid = qn < NQ;
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
-                    const float dF = F[w] - fb[w], dG = G[w] - fb[4 + w];
+                    const float dF = F[w] - cf[r][w], dG = G[w] - cf[r][4 + w];
                     // rows (element, variable) with stride 18: conflict-free
-                    wst[(el * 4 + w) * 18 + ip] = valid ? jrx * dF + jry * dG : 0.f;
-                    wst[(el * 4 + w) * 18 + 8 + ip] = valid ? jsx * dF + jsy * dG : 0.f;
+                    wst[(el * 4 + w) * 18 + ip] = cg[r][0] * dF + cg[r][1] * dG;
+                    wst[(el * 4 + w) * 18 + 8 + ip] = cg[r][2] * dF + cg[r][3] * dG;
                 }
             }
             __syncwarp();
