@@ -32,8 +32,11 @@ struct TgSmem {
     static constexpr int A1_REGION = al(mx(A1_BYTES, 32 * D::NF * NBV_C * 4));
     static constexpr int A2_BYTES = 128 * 32 * 4;
     static constexpr int sA2 = sA1 + A1_REGION;                    // USx, USy operands
-    static constexpr int sTR = sA2 + 2 * A2_BYTES;                 // [128][NFS] traces, then face terms
-    static constexpr int sIO = al(sTR + 128 * D::NFS * 4);         // q tile
+    static constexpr int sTR = sA2 + 2 * A2_BYTES;                 // U tile, neighbour records, traces, face terms
+    static constexpr int REC = 4 * D::NP;                          // floats of one element's U record
+    static constexpr int TR_BYTES = al(mx(128 * D::NFS * 4, 32 * REC * 4));
+    static constexpr int NBB = TR_BYTES / (REC * 4);               // neighbour records per batch
+    static constexpr int sIO = sTR + TR_BYTES;                     // q tile
     static constexpr int IO_REGION = al(32 * 8 * D::NP * 4);
     static constexpr int sMEAN = al(mx(sIO + IO_REGION, (int)Tile<N, float>::smem_grad()));  // curved tiles use all below
     static constexpr int sGEO = sMEAN + 128 * 4;
@@ -46,12 +49,13 @@ struct TgSmem {
     static constexpr int TOTAL = sFL + 100 * 4;
     static constexpr int TMEM_COLS = (D::NFP + 4 * D::N2) <= 128 ? 128 : 256;
     static_assert(TOTAL <= 232448, "gradient tile exceeds the shared-memory limit");
+    static_assert(NBB >= 32 && (REC * 4) % 16 == 0, "bulk-copy staging layout");
     static_assert(Tile<N, float>::smem_grad() <= (size_t)sMEAN, "curved tile would clobber the tile state");
 };
 
 template <int N, int PREC>
 __device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q_out, long long e0, int ne,
-                                             unsigned char* smem, uint32_t tmem, uint32_t& nwait, int* err) {
+                                             unsigned char* smem, uint32_t tmem, uint32_t& nwait, uint32_t& nld, int* err) {
     using D = TcDims<N>;
     using S = TgSmem<N>;
     constexpr int NP = D::NP, NG = D::NG, NF = D::NF, NPK = D::NPK, NFP = D::NFP, N2 = D::N2, NFS = D::NFS;
@@ -73,14 +77,22 @@ __device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q
 
     int* sList = reinterpret_cast<int*>(smem + S::sLIST);
     int* sFL = reinterpret_cast<int*>(smem + S::sFL);
+    // the tile's U rows by a TMA bulk copy into the trace region
+    if (tid == 32) {
+        tc::fence_async_smem();
+        const uint32_t bu = (uint32_t)ne * 4 * NP * 4;
+        tc::mbar_expect_tx(&bars[1], bu);
+        tc::bulk_g2s(sTr, p.Us + e0 * 4 * NP, bu, &bars[1]);
+    }
     if (tid < 32) tile_info(p, e0, ne, true, sGeo, sNb, sSe, sList, sFL);
-    const long long k = e0 + e;
+    if (!tc::mbar_wait(&bars[1], nld & 1)) atomicOr(err, 8);
+    ++nld;
     const bool live = e < ne;
     if (half == 0) {
         float u[NP];
         float mean = 0.f;
         if (live) {
-            const float* src = p.Us + (k * 4 + v) * NP;
+            const float* src = sTr + row * NP;
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
                 u[j] = src[j];
@@ -110,52 +122,69 @@ __device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q
         issue_mma<PREC>(tDQ, A1, smem + S::sBQ, 2 * N2, NPK, false);
         tc::mma_commit(&bars[0]);
     }
-    // out-of-tile neighbours: trace at the reversed point and sqrt(eps); one
-    // item per (face, variable, half of the face points), loads issued
-    // before the wait for G1 (the traces overwrite its operand region)
+    // out-of-tile neighbours: their U records by 16-byte asynchronous copies
+    // into the trace region, in batches of NBB faces (the first batch
+    // overlaps G1), then the trace at the reversed point and sqrt(eps) into
+    // the G1 operand region, one item per (face, variable, half of the face
+    // points)
     float* sNbv = reinterpret_cast<float*>(smem + S::sA1);
-    {
-        constexpr int GH = (NG + 1) / 2;
-        const int nitems = sList[0] * 8;
-        float un[NP], sen = 0.f;
-        auto load_item = [&](int it) {
-            const int entry = sList[1 + (it >> 3)], w = it & 3;
+    const int nlist = sList[0];
+    auto issue_batch = [&](int b0) {
+        constexpr int CH = S::REC / 4;
+        const int nc = min(S::NBB, nlist - b0) * CH;
+        for (int c = tid; c < nc; c += blockDim.x) {
+            const int i = c / CH, j = c - i * CH;
+            const int entry = sList[1 + b0 + i];
             const int ee = entry / 3, f = entry - ee * 3;
             const int4 nbw = sNb[ee];
             const long long nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
-            const float* src = p.Us + (nb * 4 + w) * NP;
-#pragma unroll
-            for (int j = 0; j < NP; ++j) un[j] = __ldg(src + j);
-            sen = sqrtf(__ldg(p.eps + nb));
-        };
-        auto store_item = [&](int it) {
-            const int entry = sList[1 + (it >> 3)], w = it & 3, hp = (it >> 2) & 1;
-            const int ee = entry / 3, f = entry - ee * 3;
-            const int fn = code_face(sNb[ee].w, f);
-            const int g1 = hp ? NG : GH;
-#pragma unroll 1
-            for (int gg = hp * GH; gg < g1; ++gg) {
-                const float* ig = sIgF + (fn * NG + (NG - 1 - gg)) * NP;
-                float* dst = sNbv + (ee * NF + f * NG + gg) * S::NBV_C;
-                float a = 0.f;
-#pragma unroll
-                for (int j = 0; j < NP; ++j) a += ig[j] * un[j];
-                dst[w] = a;
-                if (w == 0) dst[4] = sen;
+            tc::cp_async16(sTr + i * S::REC + j * 4, p.Us + nb * 4 * NP + j * 4);
+        }
+    };
+    if (nlist > 0) issue_batch(0);
+    if (!tc::mbar_wait(&bars[0], nwait & 1)) atomicOr(err, 8);
+    ++nwait;
+    tc::fence_after_sync();
+    {
+        constexpr int GH = (NG + 1) / 2;
+        for (int b0 = 0; b0 < nlist; b0 += S::NBB) {
+            if (b0 > 0) {
+                __syncthreads();   // the previous batch is consumed
+                issue_batch(b0);
             }
-        };
-        int it = tid;
-        const bool first = it < nitems;
-        if (first) load_item(it);
-        if (!tc::mbar_wait(&bars[0], nwait & 1)) atomicOr(err, 8);
-        ++nwait;
-        tc::fence_after_sync();
-        if (first) store_item(it);
-        for (it += blockDim.x; it < nitems; it += blockDim.x) {
-            load_item(it);
-            store_item(it);
+            tc::cp_async_wait_all();
+            __syncthreads();
+            const int nitems = min(S::NBB, nlist - b0) * 8;
+            for (int it = tid; it < nitems; it += blockDim.x) {
+                const int fi = it >> 3, w = it & 3, hp = (it >> 2) & 1;
+                const int entry = sList[1 + b0 + fi];
+                const int ee = entry / 3, f = entry - ee * 3;
+                const int4 nbw = sNb[ee];
+                const int fn = code_face(nbw.w, f);
+                const float* rec = sTr + fi * S::REC + w * NP;
+                float un[NP];
+#pragma unroll
+                for (int j = 0; j < NP; ++j) un[j] = rec[j];
+                float sen = 0.f;
+                if (w == 0) {
+                    const long long nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
+                    sen = sqrtf(__ldg(p.eps + nb));
+                }
+                const int g1 = hp ? NG : GH;
+#pragma unroll 1
+                for (int gg = hp * GH; gg < g1; ++gg) {
+                    const float* ig = sIgF + (fn * NG + (NG - 1 - gg)) * NP;
+                    float* dst = sNbv + (ee * NF + f * NG + gg) * S::NBV_C;
+                    float a = 0.f;
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) a += ig[j] * un[j];
+                    dst[w] = a;
+                    if (w == 0) dst[4] = sen;
+                }
+            }
         }
     }
+    __syncthreads();   // the trace region is free again
     const float mean_v = sMean[row];
     if (half == 0) {
 #pragma unroll
@@ -316,7 +345,7 @@ __global__ void __launch_bounds__(THREADS, 2) grad_kernel_tc(StageArgs<float> p,
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *slot;
-    uint32_t nwait = 0;
+    uint32_t nwait = 0, nld = 0;
     bool ops_loaded = false;
     while (true) {
         if (tid == 0) s_tile = atomicAdd(counter, 1);
@@ -339,7 +368,7 @@ __global__ void __launch_bounds__(THREADS, 2) grad_kernel_tc(StageArgs<float> p,
                 ops_loaded = true;
             }
             const long long e0 = (t - nCur) * ET;
-            grad_tile_tc<N, PREC>(p, q_out, e0, (int)min((long long)ET, p.Kaff - e0), smem_g, tmem, nwait, err);
+            grad_tile_tc<N, PREC>(p, q_out, e0, (int)min((long long)ET, p.Kaff - e0), smem_g, tmem, nwait, nld, err);
         }
     }
     tc::fence_before_sync();
@@ -387,6 +416,8 @@ int launch_grad_tc(const StageArgs<float>& a, float* q_out, int prec, const unsi
     if (tiles == 0) return 0;
     const int ctas = prec == PREC_TF32 ? TgGrid<N, PREC_TF32>::ctas : TgGrid<N, PREC_BF16X3>::ctas;
     if (ctas <= 0) return (int)cudaErrorNotReady;
+    // the tile and neighbour records travel by TMA bulk copies: 16-byte aligned
+    if (((uintptr_t)a.Us | (uintptr_t)q_out | (uintptr_t)ops_tc) & 15) return (int)cudaErrorMisalignedAddress;
     cudaError_t e = cudaMemsetAsync(err + 2, 0, sizeof(int), st);
     if (e != cudaSuccess) return (int)e;
     const unsigned grid = (unsigned)(tiles < ctas ? tiles : ctas);

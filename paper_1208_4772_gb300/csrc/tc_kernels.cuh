@@ -101,7 +101,10 @@ struct TcSmem {
     static constexpr int NBUF = 2;
     static constexpr int TR_FLOATS = 128 * D::NFS;
     static constexpr int WST = 32 * 18;                                      // floats per warp: cubature transpose
-    static constexpr int TR_REGION = al(mx(mx(TR_FLOATS * 4 * (AV ? 2 : 1), 8 * WST * 4), 32 * 4 * D::NP * 4));
+    static constexpr int REC = (AV ? 12 : 4) * D::NP;                       // floats of one element's U (and q) record
+    static constexpr int TR_REGION =
+        al(mx(mx(TR_FLOATS * 4 * (AV ? 2 : 1), 8 * WST * 4), mx(32 * 4 * D::NP * 4, 32 * REC * 4)));
+    static constexpr int NBB = TR_REGION / (REC * 4);                        // neighbour records per batch
     static constexpr int sA2 = sA1 + A1_REGION;
     static constexpr int sTR = sA2 + NBUF * A2_BYTES;
     static constexpr int sMEAN = sTR + TR_REGION;                            // [128]
@@ -116,6 +119,7 @@ struct TcSmem {
     static constexpr int TOTAL = sFL + 100 * 4;
     static_assert(TOTAL <= 232448, "tensor-core tile exceeds the shared-memory limit");
     static_assert(D::CA <= NBUF, "viscous chunks are written at tile start, one per A2 buffer");
+    static_assert(NBB >= 32 && (REC * 4) % 16 == 0 && (32 * 4 * D::NP * 4) % 16 == 0, "bulk-copy staging layout");
     // a curved tile (CUDA-core body) may overwrite everything before sMEAN
     static_assert(Tile<N, float>::smem_stage(AV) <= (size_t)sMEAN, "curved tile would clobber the tile state");
 };
@@ -225,6 +229,7 @@ __device__ __forceinline__ void tile_info(const StageArgs<float>& p, long long e
 // mbarriers and TMEM are set up once per CTA by the persistent kernel;
 // ph tracks the phases of the mbarriers across tiles.
 struct TcPhase {
+    uint32_t ld = 0;            // completions consumed on the bulk-copy barrier
     uint32_t g1 = 0;            // completions consumed on the G1 barrier
     uint32_t commits[2] = {0, 0};
     uint32_t waits[2] = {0, 0};
@@ -272,15 +277,33 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     };
     int seq = 0;
 
-    // ---------------- per-element data, the lists of faces, and the G1 operands
-    if (tid < 32) tile_info(p, e0, ne, AV, sGeo, sNb, sSe, sList, sFL);
+    // ---------------- tile inputs: the U (and q) rows of the tile by TMA bulk
+    // copies into the trace region; per-element data and face lists by warp 0
+    float* sStU = sTr;                          // [32][4][NP]
+    float* sStQ = sTr + 32 * 4 * NP;            // [32][8][NP]
+    if (tid == 32) {
+        tc::fence_async_smem();
+        const uint32_t bu = (uint32_t)ne * 4 * NP * 4, bq = AV ? (uint32_t)ne * 8 * NP * 4 : 0u;
+        tc::mbar_expect_tx(&bars[3], bu + bq);
+        tc::bulk_g2s(sStU, p.Us + e0 * 4 * NP, bu, &bars[3]);
+        if constexpr (AV) tc::bulk_g2s(sStQ, p.q + e0 * 8 * NP, bq, &bars[3]);
+    }
     const long long k = e0 + e;
     const bool live = e < ne;
+    float4 gk = make_float4(0.f, 0.f, 0.f, 0.f);   // AV rows: x_r, x_s, y_r, y_s and eps, loaded early
+    float epk = 0.f;
+    if (AV && half == 1 && live) {
+        gk = __ldg(reinterpret_cast<const float4*>(p.geoA + k * 4));
+        epk = __ldg(p.eps + k);
+    }
+    if (tid < 32) tile_info(p, e0, ne, AV, sGeo, sNb, sSe, sList, sFL);
+    if (!tc::mbar_wait(&bars[3], ph.ld & 1)) atomicOr(err, 8);
+    ph.ld++;
     if (half == 0) {
         float u[NP];
         float mean = 0.f;
         if (live) {
-            const float* src = p.Us + (k * 4 + v) * NP;
+            const float* src = sStU + row * NP;
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
                 u[j] = src[j];
@@ -305,20 +328,15 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
         // sqrt(eps) (J r_x q_x + J r_y q_y), sqrt(eps) (J s_x q_x + J s_y q_y)
         // at the nodes, written straight into the first A2 buffers
         float qx[NP], qy[NP];
-        const float* src = p.q + (k * 8 + v) * NP;
+        const float* src = sStQ + (e * 8 + v) * NP;
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
             qx[j] = live ? src[j] : 0.f;
             qy[j] = live ? src[4 * NP + j] : 0.f;
         }
-        float g[16];
-        float se = 0.f;
-        if (live) {
-            affine_geometry(p.geoA + k * 4, g);
-            se = sqrtf(p.eps[k]);
-        } else {
-            g[0] = g[1] = g[2] = g[3] = 0.f;
-        }
+        // J r_x = y_s, J r_y = -x_s, J s_x = -y_r, J s_y = x_r (zero for padding rows)
+        const float g[4] = {gk.w, -gk.y, -gk.z, gk.x};
+        const float se = sqrtf(epk);
 #pragma unroll
         for (int j0 = 0; j0 < NPK; j0 += 8) {
             float x[8], y[8];
@@ -368,6 +386,27 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
         for (int ca = 0; ca < CA; ++ca) ph.commits[ca & 1]++;
         seq = CA;
     }
+
+    // out-of-tile neighbours: their U (and q) records by 16-byte asynchronous
+    // copies into the trace region, in batches of NBB faces (the first batch
+    // overlaps G1), then their traces at the reversed face points into the G1
+    // operand region, one item per (face, variable, half of the face points)
+    float* sNbv = reinterpret_cast<float*>(smem + S::sA1);
+    const int nlist = sList[0];
+    auto issue_batch = [&](int b0) {
+        constexpr int CU = NP, CH = S::REC / 4;    // 16-byte pieces: U part, whole record
+        const int nc = min(S::NBB, nlist - b0) * CH;
+        for (int c = tid; c < nc; c += blockDim.x) {
+            const int i = c / CH, j = c - i * CH;
+            const int entry = sList[1 + b0 + i];
+            const int ee = entry / 3, f = entry - ee * 3;
+            const int4 nbw = sNb[ee];
+            const long long nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
+            const float* src = (j < CU) ? p.Us + nb * 4 * NP + j * 4 : p.q + nb * 8 * NP + (j - CU) * 4;
+            tc::cp_async16(sTr + i * S::REC + j * 4, src);
+        }
+    };
+    if (nlist > 0) issue_batch(0);
     if (tid < 128) {   // flux of the element-mean state, one (element, variable) per thread
         float Ub[4], Fb[4], Gb[4];
 #pragma unroll
@@ -376,72 +415,60 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
         sFb[e * 8 + v] = Fb[v];
         sFb[e * 8 + 4 + v] = Gb[v];
     }
-
-    // out-of-tile neighbours' traces at the reversed face points, from their
-    // states in L2, into the G1 operand region once G1 has completed.  One
-    // item per (face, variable, half of the face points); the item's loads
-    // are issued before the wait for G1 so that their latency overlaps it.
-    float* sNbv = reinterpret_cast<float*>(smem + S::sA1);
+    if (!tc::mbar_wait(&bars[2], ph.g1 & 1)) atomicOr(err, 1);
+    ph.g1++;
+    tc::fence_after_sync();
     {
         constexpr int GH = (NG + 1) / 2;
-        const int nitems = sList[0] * 8;
-        float un[NP], qx[AV ? NP : 1], qy[AV ? NP : 1];
-        float sen = 0.f;
-        auto load_item = [&](int it) {
-            const int entry = sList[1 + (it >> 3)], w = it & 3;
-            const int ee = entry / 3, f = entry - ee * 3;
-            const int4 nbw = sNb[ee];
-            const long long nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
-            const float* src = p.Us + (nb * 4 + w) * NP;
-#pragma unroll
-            for (int j = 0; j < NP; ++j) un[j] = __ldg(src + j);
-            if constexpr (AV) {
-                const float* q0 = p.q + (nb * 8 + w) * NP;
-#pragma unroll
-                for (int j = 0; j < NP; ++j) {
-                    qx[j] = __ldg(q0 + j);
-                    qy[j] = __ldg(q0 + 4 * NP + j);
-                }
-                sen = sqrtf(__ldg(p.eps + nb));
+        for (int b0 = 0; b0 < nlist; b0 += S::NBB) {
+            if (b0 > 0) {
+                __syncthreads();   // the previous batch is consumed
+                issue_batch(b0);
             }
-        };
-        auto store_item = [&](int it) {
-            const int entry = sList[1 + (it >> 3)], w = it & 3, hp = (it >> 2) & 1;
-            const int ee = entry / 3, f = entry - ee * 3;
-            const int fn = code_face(sNb[ee].w, f);
-            const float* ge = sGeo + ee * 16;
-            const float nx = ge[5 + 3 * f], ny = ge[6 + 3 * f];
-            const int g1 = hp ? NG : GH;
-#pragma unroll 1
-            for (int gg = hp * GH; gg < g1; ++gg) {
-                const int fg = f * NG + gg;
-                const float* ig = sIgF + (fn * NG + (NG - 1 - gg)) * NP;
-                float* dst = sNbv + (ee * NF + fg) * S::NBV_C;
-                float a = 0.f, ax = 0.f, ay = 0.f;
+            tc::cp_async_wait_all();
+            __syncthreads();
+            const int nitems = min(S::NBB, nlist - b0) * 8;
+            for (int it = tid; it < nitems; it += blockDim.x) {
+                const int fi = it >> 3, w = it & 3, hp = (it >> 2) & 1;
+                const int entry = sList[1 + b0 + fi];
+                const int ee = entry / 3, f = entry - ee * 3;
+                const int4 nbw = sNb[ee];
+                const int fn = code_face(nbw.w, f);
+                const float* rec = sTr + fi * S::REC;
+                float un[NP];
 #pragma unroll
-                for (int j = 0; j < NP; ++j) {
-                    a += ig[j] * un[j];
+                for (int j = 0; j < NP; ++j) un[j] = rec[w * NP + j];
+                float sen = 0.f, nx = 0.f, ny = 0.f;
+                if constexpr (AV) {
+                    const long long nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
+                    sen = sqrtf(__ldg(p.eps + nb));
+                    nx = sGeo[ee * 16 + 5 + 3 * f];
+                    ny = sGeo[ee * 16 + 6 + 3 * f];
+                }
+                const int g1 = hp ? NG : GH;
+#pragma unroll 1
+                for (int gg = hp * GH; gg < g1; ++gg) {
+                    const int fg = f * NG + gg;
+                    const float* ig = sIgF + (fn * NG + (NG - 1 - gg)) * NP;
+                    float* dst = sNbv + (ee * NF + fg) * S::NBV_C;
+                    float a = 0.f;
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) a += ig[j] * un[j];
+                    dst[w] = a;
                     if constexpr (AV) {
-                        ax += ig[j] * qx[j];
-                        ay += ig[j] * qy[j];
+                        float ax = 0.f, ay = 0.f;
+#pragma unroll
+                        for (int j = 0; j < NP; ++j) {
+                            ax += ig[j] * rec[(4 + w) * NP + j];
+                            ay += ig[j] * rec[(8 + w) * NP + j];
+                        }
+                        dst[4 + w] = sen * (ax * nx + ay * ny);
                     }
                 }
-                dst[w] = a;
-                if constexpr (AV) dst[4 + w] = sen * (ax * nx + ay * ny);
             }
-        };
-        int it = tid;
-        const bool first = it < nitems;
-        if (first) load_item(it);
-        if (!tc::mbar_wait(&bars[2], ph.g1 & 1)) atomicOr(err, 1);
-        ph.g1++;
-        tc::fence_after_sync();
-        if (first) store_item(it);
-        for (it += blockDim.x; it < nitems; it += blockDim.x) {
-            load_item(it);
-            store_item(it);
         }
     }
+    __syncthreads();   // the trace region is free again
 
     // ---------------- own traces (and sqrt(eps) q.n) to shared memory
     const float mean_v = sMean[row];
@@ -798,6 +825,9 @@ int launch_stage_tc_t(const StageArgs<float>& a, const unsigned char* ops_tc, in
     if (tiles == 0) return 0;
     const int ctas = TcGrid<N, AV, PREC>::ctas;
     if (ctas <= 0) return (int)cudaErrorNotReady;   // prepare_tc was not called
+    // the tile and neighbour records travel by TMA bulk copies: 16-byte aligned
+    if (((uintptr_t)a.Us | (uintptr_t)a.Un | (uintptr_t)a.Uout | (uintptr_t)a.q | (uintptr_t)ops_tc) & 15)
+        return (int)cudaErrorMisalignedAddress;
     cudaError_t e = cudaMemsetAsync(err + 1, 0, sizeof(int), st);
     if (e != cudaSuccess) return (int)e;
     const unsigned grid = (unsigned)(tiles < ctas ? tiles : ctas);
