@@ -717,8 +717,9 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
         free_mesh(m);
         return e;
     }
-    if ((e = alloc(ctx, *m, (void**)&m->err, 16))) { free_mesh(m); return e; }
-    if (cudaMemset(m->err, 0, 16) != cudaSuccess) { free_mesh(m); return fail(ctx, DG_ECUDA, "memset failed"); }
+    // error word and the persistent kernels' tile / done counters
+    if ((e = alloc(ctx, *m, (void**)&m->err, 32))) { free_mesh(m); return e; }
+    if (cudaMemset(m->err, 0, 32) != cudaSuccess) { free_mesh(m); return fail(ctx, DG_ECUDA, "memset failed"); }
     if (tensor_prec(p->prec)) {
         const int tkey = N * 16 + 4 + p->prec;
         auto tit = ctx->ops.find(tkey);
@@ -746,7 +747,8 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
         m->ops_tc = tit->second;
     }
     if (p->av_on) {
-        if ((e = alloc(ctx, *m, &m->eps, (size_t)K * rs))) { free_mesh(m); return e; }
+        // padded to whole tiles of 32: the tensor-core kernels copy eps per tile
+        if ((e = alloc(ctx, *m, &m->eps, (size_t)((K + 31) / 32 * 32) * rs))) { free_mesh(m); return e; }
         if ((e = alloc(ctx, *m, &m->q, (size_t)K * 8 * NP * rs))) { free_mesh(m); return e; }
     }
     // operators (shared per context, degree and precision)
@@ -797,7 +799,7 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
         free_mesh(m);
         return fail(ctx, DG_ECUDA, "mesh upload copy failed");
     }
-    if (p->av_on && (cudaMemset(m->eps, 0, (size_t)K * rs) != cudaSuccess ||
+    if (p->av_on && (cudaMemset(m->eps, 0, (size_t)((K + 31) / 32 * 32) * rs) != cudaSuccess ||
                      cudaMemset(m->q, 0, (size_t)K * 8 * NP * rs) != cudaSuccess)) {
         free_mesh(m);
         return fail(ctx, DG_ECUDA, "mesh upload memset failed");

@@ -1,6 +1,7 @@
 // Device-side data layout and kernel launch interface shared by the host
 // library (dg_api.cpp) and the per-degree kernel translation units.
 #pragma once
+#include <utility>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -120,6 +121,25 @@ inline int resident_ctas(const void* kern, int threads, size_t dyn_smem) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&api, kern, threads, dyn_smem) != cudaSuccess) api = 0;
     cudaGetLastError();
     return api > manual ? api : manual;
+}
+
+// Launch with programmatic stream serialization: the kernel may begin
+// before the previous kernel of the stream has finished and must wait for it
+// (griddepcontrol.wait) before touching that kernel's results.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned threads, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 // Generic kernels (kernels_common.cu)

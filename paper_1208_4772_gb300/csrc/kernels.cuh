@@ -395,6 +395,8 @@ __global__ void __launch_bounds__(SENSOR_THREADS) sensor_kernel(StageArgs<Real> 
     constexpr int NP = np_of(N), NQ = nq_of(N);
     constexpr int NLOW = N * (N + 1) / 2;  // modes of degree <= N-1 come first
     constexpr OpsLayout L = ops_layout(N);
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // the state comes from the previous kernel
     if ((int)blockIdx.x < ncb) {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const long long k = p.Kaff + (long long)blockIdx.x * SENSOR_CURVED_PER_BLOCK + warp;
@@ -653,8 +655,7 @@ int launch_sensor(const StageArgs<Real>& a, Real* eps_out, cudaStream_t st) {
     const int ncb = (int)((Kc + SENSOR_CURVED_PER_BLOCK - 1) / SENSOR_CURVED_PER_BLOCK);
     const unsigned grid = (unsigned)(ncb + (a.Kaff + SENSOR_THREADS - 1) / SENSOR_THREADS);
     if (grid == 0) return 0;
-    sensor_kernel<N, Real><<<grid, SENSOR_THREADS, 0, st>>>(a, eps_out, ncb);
-    return (int)cudaGetLastError();
+    return (int)launch_pdl(sensor_kernel<N, Real>, grid, SENSOR_THREADS, 0, st, a, eps_out, ncb);
 }
 
 template <int N, typename Real>

@@ -34,7 +34,7 @@ struct TgSmem {
     static constexpr int sA2 = sA1 + A1_REGION;                    // USx, USy operands
     static constexpr int sTR = sA2 + 2 * A2_BYTES;                 // U tile, neighbour records, traces, face terms
     static constexpr int REC = 4 * D::NP;                          // floats of one element's U record
-    static constexpr int TR_BYTES = al(mx(128 * D::NFS * 4, 32 * REC * 4));
+    static constexpr int TR_BYTES = al(mx(mx(128 * D::NFS * 4, 32 * REC * 4), TileStage<N, false>::FLOATS * 4));
     static constexpr int NBB = TR_BYTES / (REC * 4);               // neighbour records per batch
     static constexpr int sIO = sTR + TR_BYTES;                     // q tile
     static constexpr int IO_REGION = al(32 * 8 * D::NP * 4);
@@ -54,8 +54,10 @@ struct TgSmem {
 };
 
 template <int N, int PREC>
-__device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q_out, long long e0, int ne,
-                                             unsigned char* smem, uint32_t tmem, uint32_t& nwait, uint32_t& nld, int* err) {
+__device__ __forceinline__ bool grad_tile_tc(const StageArgs<float>& p, float* q_out, long long e0, int ne,
+                                             unsigned char* smem, uint32_t tmem, uint32_t& nwait, uint32_t& nld, int* err,
+                                             bool rows_ready, int claim, int* next_tile, long long nCur,
+                                             long long nAff) {
     using D = TcDims<N>;
     using S = TgSmem<N>;
     constexpr int NP = D::NP, NG = D::NG, NF = D::NF, NPK = D::NPK, NFP = D::NFP, N2 = D::N2, NFS = D::NFS;
@@ -78,21 +80,19 @@ __device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q
     int* sList = reinterpret_cast<int*>(smem + S::sLIST);
     int* sFL = reinterpret_cast<int*>(smem + S::sFL);
     // the tile's U rows by a TMA bulk copy into the trace region
-    if (tid == 32) {
-        tc::fence_async_smem();
-        const uint32_t bu = (uint32_t)ne * 4 * NP * 4;
-        tc::mbar_expect_tx(&bars[1], bu);
-        tc::bulk_g2s(sTr, p.Us + e0 * 4 * NP, bu, &bars[1]);
-    }
-    if (tid < 32) tile_info(p, e0, ne, true, sGeo, sNb, sSe, sList, sFL);
+    using TS = TileStage<N, false>;
+    if (tid == 32 && !rows_ready) issue_tile_rows<N, false, true>(p, e0, ne, sTr, &bars[1]);
     if (!tc::mbar_wait(&bars[1], nld & 1)) atomicOr(err, 8);
     ++nld;
+    if (tid < 32)
+        tile_info(e0, ne, true, sTr + TS::G, reinterpret_cast<const int4*>(sTr + TS::C), sTr + TS::E, sGeo, sNb, sSe,
+                  sList, sFL);
     const bool live = e < ne;
     if (half == 0) {
         float u[NP];
         float mean = 0.f;
         if (live) {
-            const float* src = sTr + row * NP;
+            const float* src = sTr + TS::U + row * NP;
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
                 u[j] = src[j];
@@ -191,7 +191,7 @@ __device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q
         for (int c0 = 0; c0 < NF; c0 += 8) {
             float x[8];
             tc::tmem_ld8(tD1 + lane_base + c0, x);
-            tc::tmem_ld_wait();
+            tc::tmem_ld_wait(x);
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 if (c0 + i < NF) sTr[row * NFS + c0 + i] = x[i] + mean_v;
@@ -246,6 +246,7 @@ __device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q
             }
         }
     }
+    if (tid == THREADS - 1) *next_tile = claim;   // the claim made at the start of this tile
     __syncthreads();
     {   // n_x (half 0) or n_y (half 1) times the face terms of the row
         unsigned char* dst = smem + S::sA2 + half * S::A2_BYTES;
@@ -269,6 +270,18 @@ __device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q
         issue_mma<PREC>(tDLy, smem + S::sA2 + S::A2_BYTES, smem + S::sB2F, N2, 32, false);
         tc::mma_commit(&bars[0]);
     }
+    // the next tile's rows into the (now free) trace region
+    bool pre = false;
+    {
+        const long long tn = *next_tile;
+        if (tn >= nCur && tn < nCur + nAff) {
+            pre = true;
+            if (tid == 32) {
+                const long long en = (tn - nCur) * D::E;
+                issue_tile_rows<N, false, true>(p, en, (int)min((long long)D::E, p.Kaff - en), sTr, &bars[1]);
+            }
+        }
+    }
     if (!tc::mbar_wait(&bars[0], nwait & 1)) atomicOr(err, 16);
     ++nwait;
     tc::fence_after_sync();
@@ -288,7 +301,7 @@ __device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q
             tc::tmem_ld8(tDQ + N2 + lane_base + i0, qs);
             tc::tmem_ld8(tDLx + lane_base + i0, lx);
             tc::tmem_ld8(tDLy + lane_base + i0, ly);
-            tc::tmem_ld_wait();
+            tc::tmem_ld_wait(qr, qs, lx, ly);
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 if (i0 + i < NP) {
@@ -304,6 +317,7 @@ __device__ __forceinline__ void grad_tile_tc(const StageArgs<float>& p, float* q
         for (int i = tid; i < n4; i += blockDim.x) qo[i] = so[i];
         __syncthreads();
     }
+    return pre;
 }
 
 template <int N>
@@ -326,14 +340,17 @@ __device__ __forceinline__ void load_grad_operators(const unsigned char* ops_tc,
 // (CUDA-core body), then affine tiles on the tensor cores.
 template <int N, int PREC>
 __global__ void __launch_bounds__(THREADS, 2) grad_kernel_tc(StageArgs<float> p, float* q_out,
-                                                             const unsigned char* ops_tc, int* err, int* counter) {
+                                                             const unsigned char* ops_tc, int* err, int* counter,
+                                                             int* done) {
     extern __shared__ __align__(128) unsigned char smem_g[];
     using S = TgSmem<N>;
     constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
     const int tid = threadIdx.x;
     const long long nAff = (p.Kaff + ET - 1) / ET;
     const long long nCur = (p.K - p.Kaff + EC - 1) / EC;
-    __shared__ long long s_tile;
+    __shared__ int s_tile;
+    // prologue (barriers, TMEM, operators) overlaps the previous kernel
+    tc::pdl_trigger();
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_g + S::sBAR);
     if (tid == 0) {
         for (int b = 0; b < 4; ++b) tc::mbar_init(&bars[b], 1);
@@ -341,18 +358,21 @@ __global__ void __launch_bounds__(THREADS, 2) grad_kernel_tc(StageArgs<float> p,
     }
     uint32_t* slot = reinterpret_cast<uint32_t*>(smem_g + S::sTMEM);
     if ((tid >> 5) == 0) tc::tmem_alloc(slot, S::TMEM_COLS);
+    load_grad_operators<N>(ops_tc, smem_g);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *slot;
     uint32_t nwait = 0, nld = 0;
-    bool ops_loaded = false;
-    while (true) {
-        if (tid == 0) s_tile = atomicAdd(counter, 1);
-        __syncthreads();
-        const long long t = s_tile;
-        __syncthreads();
-        if (t >= nCur + nAff) break;
+    bool ops_loaded = true, rows_ready = false;
+    tc::pdl_wait();
+    if (tid == 0) s_tile = atomicAdd(counter, 1);
+    __syncthreads();
+    long long t = s_tile;
+    while (t < nCur + nAff) {
+        __syncthreads();   // every thread has read s_tile
+        // claim the following tile now; the result is stored late in the tile
+        const int claim = (tid == THREADS - 1) ? atomicAdd(counter, 1) : 0;
         if (t < nCur) {
             TileRange tr;
             tr.curved = true;
@@ -360,6 +380,8 @@ __global__ void __launch_bounds__(THREADS, 2) grad_kernel_tc(StageArgs<float> p,
             tr.ne = (int)min((long long)EC, p.K - tr.e0);
             grad_tile_call<N, float>(p, q_out, tr, smem_g);
             ops_loaded = false;
+            rows_ready = false;
+            if (tid == THREADS - 1) s_tile = claim;
             __syncthreads();
         } else {
             if (!ops_loaded) {
@@ -368,11 +390,20 @@ __global__ void __launch_bounds__(THREADS, 2) grad_kernel_tc(StageArgs<float> p,
                 ops_loaded = true;
             }
             const long long e0 = (t - nCur) * ET;
-            grad_tile_tc<N, PREC>(p, q_out, e0, (int)min((long long)ET, p.Kaff - e0), smem_g, tmem, nwait, nld, err);
+            rows_ready = grad_tile_tc<N, PREC>(p, q_out, e0, (int)min((long long)ET, p.Kaff - e0), smem_g, tmem, nwait,
+                                               nld, err, rows_ready, claim, &s_tile, nCur, nAff);
         }
+        t = s_tile;
     }
+    // the last CTA to leave resets the counters for the next launch
+    __threadfence();
     tc::fence_before_sync();
     __syncthreads();
+    if (tid == 0 && atomicAdd(done, 1) == (int)gridDim.x - 1) {
+        __threadfence();
+        *counter = 0;
+        *done = 0;
+    }
     if ((tid >> 5) == 0) tc::tmem_free(tmem, S::TMEM_COLS);
 }
 
@@ -407,7 +438,8 @@ int prepare_grad_tc() {
     return e;
 }
 
-// err[2]: tile counter of this launch (zeroed first).
+// err[2]: tile counter, err[4]: CTAs done (zero between launches: the last
+// CTA resets them).
 template <int N>
 int launch_grad_tc(const StageArgs<float>& a, float* q_out, int prec, const unsigned char* ops_tc, int* err,
                    cudaStream_t st) {
@@ -418,14 +450,12 @@ int launch_grad_tc(const StageArgs<float>& a, float* q_out, int prec, const unsi
     if (ctas <= 0) return (int)cudaErrorNotReady;
     // the tile and neighbour records travel by TMA bulk copies: 16-byte aligned
     if (((uintptr_t)a.Us | (uintptr_t)q_out | (uintptr_t)ops_tc) & 15) return (int)cudaErrorMisalignedAddress;
-    cudaError_t e = cudaMemsetAsync(err + 2, 0, sizeof(int), st);
-    if (e != cudaSuccess) return (int)e;
     const unsigned grid = (unsigned)(tiles < ctas ? tiles : ctas);
     if (prec == PREC_TF32)
-        grad_kernel_tc<N, PREC_TF32><<<grid, THREADS, TgSmem<N>::TOTAL, st>>>(a, q_out, ops_tc, err, err + 2);
-    else
-        grad_kernel_tc<N, PREC_BF16X3><<<grid, THREADS, TgSmem<N>::TOTAL, st>>>(a, q_out, ops_tc, err, err + 2);
-    return (int)cudaGetLastError();
+        return (int)launch_pdl(grad_kernel_tc<N, PREC_TF32>, grid, THREADS, TgSmem<N>::TOTAL, st, a, q_out, ops_tc,
+                               err, err + 2, err + 4);
+    return (int)launch_pdl(grad_kernel_tc<N, PREC_BF16X3>, grid, THREADS, TgSmem<N>::TOTAL, st, a, q_out, ops_tc, err,
+                           err + 2, err + 4);
 }
 
 }  // namespace dgc

@@ -56,6 +56,20 @@ struct TcDims {
     static constexpr int TMEM_COLS = (N1 + 2 * NFP + N2) <= 128 ? 128 : 256;
 };
 
+// Staging of one tile's inputs (float offsets): the U rows, the q rows
+// (when Q), then x_r, x_s, y_r, y_s, the connectivity words and eps of the
+// 32 elements.  Every piece starts on a 16-byte boundary.
+template <int N, bool Q>
+struct TileStage {
+    static constexpr int NP = TcDims<N>::NP;
+    static constexpr int U = 0;
+    static constexpr int QR = 32 * 4 * NP;
+    static constexpr int G = QR + (Q ? 32 * 8 * NP : 0);
+    static constexpr int C = G + 32 * 4;
+    static constexpr int E = C + 32 * 4;
+    static constexpr int FLOATS = E + 32;
+};
+
 // Operator table of the tensor-core path (bytes; built by the host).
 template <int N>
 struct TcLayout {
@@ -103,7 +117,7 @@ struct TcSmem {
     static constexpr int WST = 32 * 18;                                      // floats per warp: cubature transpose
     static constexpr int REC = (AV ? 12 : 4) * D::NP;                       // floats of one element's U (and q) record
     static constexpr int TR_REGION =
-        al(mx(mx(TR_FLOATS * 4 * (AV ? 2 : 1), 8 * WST * 4), mx(32 * 4 * D::NP * 4, 32 * REC * 4)));
+        al(mx(mx(TR_FLOATS * 4 * (AV ? 2 : 1), 8 * WST * 4), mx(TileStage<N, AV>::FLOATS * 4, 32 * REC * 4)));
     static constexpr int NBB = TR_REGION / (REC * 4);                        // neighbour records per batch
     static constexpr int sA2 = sA1 + A1_REGION;
     static constexpr int sTR = sA2 + NBUF * A2_BYTES;
@@ -120,6 +134,7 @@ struct TcSmem {
     static_assert(TOTAL <= 232448, "tensor-core tile exceeds the shared-memory limit");
     static_assert(D::CA <= NBUF, "viscous chunks are written at tile start, one per A2 buffer");
     static_assert(NBB >= 32 && (REC * 4) % 16 == 0 && (32 * 4 * D::NP * 4) % 16 == 0, "bulk-copy staging layout");
+    static_assert(A1_REGION >= 32 * 4 * D::NP * 4, "epilogue rows live in the G1 operand region");
     // a curved tile (CUDA-core body) may overwrite everything before sMEAN
     static_assert(Tile<N, float>::smem_stage(AV) <= (size_t)sMEAN, "curved tile would clobber the tile state");
 };
@@ -181,34 +196,39 @@ __device__ __forceinline__ void issue_mma(uint32_t d_tmem, const unsigned char* 
     }
 }
 
-// Per-element data of a tensor-core tile, by warp 0: affine geometry,
+// Per-element data of a tensor-core tile, by warp 0, from the staged copies
+// of x_r, x_s, y_r, y_s, the connectivity words and eps: affine geometry,
 // connectivity word, sqrt(eps) (when av), and two compact face lists (count
 // first, then element * 3 + face): sList the faces whose neighbour lies
 // outside the tile, sFL the faces whose flux the tile computes -- boundary
 // and out-of-tile faces by the element itself, an in-tile pair by its
 // lower-numbered element, so that each face point is computed once.
-__device__ __forceinline__ void tile_info(const StageArgs<float>& p, long long e0, int ne, bool av, float* sGeo,
-                                          int4* sNb, float* sSe, int* sList, int* sFL) {
+__device__ __forceinline__ void tile_info(long long e0, int ne, bool av, const float* stG, const int4* stC,
+                                          const float* stE, float* sGeo, int4* sNb, float* sSe, int* sList,
+                                          int* sFL) {
     const int tid = threadIdx.x;
-    int nout = 0, nown = 0, fo[3] = {0, 0, 0}, fw[3] = {0, 0, 0};
+    int mout = 0, mown = 0;   // bit f: face f is out of tile / computed here
     if (tid < ne) {
-        affine_geometry(p.geoA + (e0 + tid) * 4, sGeo + tid * 16);
-        const int4 c = p.conn[e0 + tid];
+        const int4 c = stC[tid];
+        const float se = av ? sqrtf(stE[tid]) : 0.f;
+        affine_geometry(stG + tid * 4, sGeo + tid * 16);
         sNb[tid] = c;
-        sSe[tid] = av ? sqrtf(p.eps[e0 + tid]) : 0.f;
+        sSe[tid] = se;
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
             const long long nbl = (long long)((f == 0) ? c.x : (f == 1) ? c.y : c.z) - e0;
             const bool bnd = code_bc(c.w, f) != 0;
             const bool out = !bnd && (nbl < 0 || nbl >= ne);
-            if (out) fo[nout++] = f;
-            if (bnd || out || nbl > tid) fw[nown++] = f;
+            if (out) mout |= 1 << f;
+            if (bnd || out || nbl > tid) mown |= 1 << f;
         }
     } else {  // padding element: unit geometry, farfield faces, never stored
+#pragma unroll
         for (int i = 0; i < 16; ++i) sGeo[tid * 16 + i] = (i == 4 || i == 7 || i == 10 || i == 13) ? 1.f : 0.f;
         sNb[tid] = make_int4(0, 0, 0, 0x888);
         sSe[tid] = 0.f;
     }
+    const int nout = __popc(mout), nown = __popc(mown);
     // both lists by one warp scan of the packed counts
     int incl = nout | (nown << 16);
 #pragma unroll
@@ -216,9 +236,12 @@ __device__ __forceinline__ void tile_info(const StageArgs<float>& p, long long e
         const int y = __shfl_up_sync(0xffffffffu, incl, o);
         if (tid >= o) incl += y;
     }
-    const int excl_o = (incl & 0xffff) - nout, excl_w = (incl >> 16) - nown;
-    for (int i = 0; i < nout; ++i) sList[1 + excl_o + i] = tid * 3 + fo[i];
-    for (int i = 0; i < nown; ++i) sFL[1 + excl_w + i] = tid * 3 + fw[i];
+    int po = (incl & 0xffff) - nout, pw = (incl >> 16) - nown;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        if (mout & (1 << f)) sList[1 + po++] = tid * 3 + f;
+        if (mown & (1 << f)) sFL[1 + pw++] = tid * 3 + f;
+    }
     if (tid == 31) {
         sList[0] = incl & 0xffff;
         sFL[0] = incl >> 16;
@@ -231,13 +254,41 @@ __device__ __forceinline__ void tile_info(const StageArgs<float>& p, long long e
 struct TcPhase {
     uint32_t ld = 0;            // completions consumed on the bulk-copy barrier
     uint32_t g1 = 0;            // completions consumed on the G1 barrier
-    uint32_t commits[2] = {0, 0};
-    uint32_t waits[2] = {0, 0};
+    uint32_t c0 = 0, c1 = 0;    // products committed on the A2 buffer barriers 0, 1
+    uint32_t w0 = 0, w1 = 0;    // completions consumed on them
+    // (scalars rather than arrays: a runtime index would put them in local memory)
+    __device__ __forceinline__ void commit(int b) {
+        if (b) ++c1; else ++c0;
+    }
 };
 
+// Bulk copies of one tile's inputs into the staging region, signalled on bar
+// (one thread).  eps is copied for all 32 slots of the tile: its device array
+// is padded to a multiple of 32 elements.
+template <int N, bool Q, bool EPS>
+__device__ __forceinline__ void issue_tile_rows(const StageArgs<float>& p, long long e0, int ne, float* dst,
+                                                uint64_t* bar) {
+    using T = TileStage<N, Q>;
+    constexpr int NP = TcDims<N>::NP;
+    tc::fence_async_smem();
+    const uint32_t bu = (uint32_t)ne * 4 * NP * 4, bq = Q ? (uint32_t)ne * 8 * NP * 4 : 0u, bg = (uint32_t)ne * 16;
+    tc::mbar_expect_tx(bar, bu + bq + 2 * bg + (EPS ? 128u : 0u));
+    tc::bulk_g2s(dst + T::U, p.Us + e0 * 4 * NP, bu, bar);
+    if constexpr (Q) tc::bulk_g2s(dst + T::QR, p.q + e0 * 8 * NP, bq, bar);
+    tc::bulk_g2s(dst + T::G, p.geoA + e0 * 4, bg, bar);
+    tc::bulk_g2s(dst + T::C, p.conn + e0, bg, bar);
+    if constexpr (EPS) tc::bulk_g2s(dst + T::E, p.eps + e0, 128u, bar);
+}
+
+// Tile body.  rows_ready: this tile's rows were requested by the previous
+// tile.  claim: in the last thread, the index of this CTA's next tile from
+// the atomic counter; it is stored to *next_tile once the face phase is
+// done (its latency is long hidden by then) and read after the cubature
+// chunks.  Returns true if the next tile's rows were requested here.
 template <int N, bool AV, int PREC>
-__device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long long e0, int ne, unsigned char* smem,
-                                              uint32_t tmem, TcPhase& ph, int* err) {
+__device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long long e0, int ne, unsigned char* smem,
+                                              uint32_t tmem, TcPhase& ph, int* err, bool rows_ready,
+                                              int claim, int* next_tile, long long nCur, long long nAff) {
     using D = TcDims<N>;
     using S = TcSmem<N, AV>;
     constexpr int NP = D::NP, NQ = D::NQ, NG = D::NG, NF = D::NF, NPK = D::NPK, FOFF = D::FOFF;
@@ -266,9 +317,11 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
     // G2 runs as a sequence of K chunks; chunk number s uses A2 buffer s % 2.
     auto a2_buf = [&](int s) { return smem + S::sA2 + (s & 1) * S::A2_BYTES; };
     auto wait_buf = [&](int b) {   // every product issued from buffer b has completed
-        while (ph.waits[b] < ph.commits[b]) {
-            if (!tc::mbar_wait(&bars[b], ph.waits[b] & 1)) atomicOr(err, 2);
-            ph.waits[b]++;
+        uint32_t& w = b ? ph.w1 : ph.w0;
+        const uint32_t c = b ? ph.c1 : ph.c0;
+        while (w < c) {
+            if (!tc::mbar_wait(&bars[b], w & 1)) atomicOr(err, 2);
+            ++w;
         }
     };
     auto issue_chunk = [&](int s, int op_chunk) {   // thread 0, after the operand is visible
@@ -279,31 +332,20 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
 
     // ---------------- tile inputs: the U (and q) rows of the tile by TMA bulk
     // copies into the trace region; per-element data and face lists by warp 0
-    float* sStU = sTr;                          // [32][4][NP]
-    float* sStQ = sTr + 32 * 4 * NP;            // [32][8][NP]
-    if (tid == 32) {
-        tc::fence_async_smem();
-        const uint32_t bu = (uint32_t)ne * 4 * NP * 4, bq = AV ? (uint32_t)ne * 8 * NP * 4 : 0u;
-        tc::mbar_expect_tx(&bars[3], bu + bq);
-        tc::bulk_g2s(sStU, p.Us + e0 * 4 * NP, bu, &bars[3]);
-        if constexpr (AV) tc::bulk_g2s(sStQ, p.q + e0 * 8 * NP, bq, &bars[3]);
-    }
+    if (tid == 32 && !rows_ready) issue_tile_rows<N, AV, AV>(p, e0, ne, sTr, &bars[3]);
     const long long k = e0 + e;
     const bool live = e < ne;
-    float4 gk = make_float4(0.f, 0.f, 0.f, 0.f);   // AV rows: x_r, x_s, y_r, y_s and eps, loaded early
-    float epk = 0.f;
-    if (AV && half == 1 && live) {
-        gk = __ldg(reinterpret_cast<const float4*>(p.geoA + k * 4));
-        epk = __ldg(p.eps + k);
-    }
-    if (tid < 32) tile_info(p, e0, ne, AV, sGeo, sNb, sSe, sList, sFL);
+    using TS = TileStage<N, AV>;
     if (!tc::mbar_wait(&bars[3], ph.ld & 1)) atomicOr(err, 8);
     ph.ld++;
+    if (tid < 32)
+        tile_info(e0, ne, AV, sTr + TS::G, reinterpret_cast<const int4*>(sTr + TS::C), sTr + TS::E, sGeo, sNb, sSe,
+                  sList, sFL);
     if (half == 0) {
         float u[NP];
         float mean = 0.f;
         if (live) {
-            const float* src = sStU + row * NP;
+            const float* src = sTr + TS::U + row * NP;
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
                 u[j] = src[j];
@@ -328,15 +370,16 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
         // sqrt(eps) (J r_x q_x + J r_y q_y), sqrt(eps) (J s_x q_x + J s_y q_y)
         // at the nodes, written straight into the first A2 buffers
         float qx[NP], qy[NP];
-        const float* src = sStQ + (e * 8 + v) * NP;
+        const float* src = sTr + TS::QR + (e * 8 + v) * NP;
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
             qx[j] = live ? src[j] : 0.f;
             qy[j] = live ? src[4 * NP + j] : 0.f;
         }
         // J r_x = y_s, J r_y = -x_s, J s_x = -y_r, J s_y = x_r (zero for padding rows)
+        const float4 gk = live ? *reinterpret_cast<const float4*>(sTr + TS::G + e * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float g[4] = {gk.w, -gk.y, -gk.z, gk.x};
-        const float se = sqrtf(epk);
+        const float se = live ? sqrtf(sTr[TS::E + e]) : 0.f;
 #pragma unroll
         for (int j0 = 0; j0 < NPK; j0 += 8) {
             float x[8], y[8];
@@ -383,7 +426,7 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
             for (int ca = 0; ca < CA; ++ca) issue_chunk(ca, CF + CQ + ca);
     }
     if constexpr (AV) {
-        for (int ca = 0; ca < CA; ++ca) ph.commits[ca & 1]++;
+        for (int ca = 0; ca < CA; ++ca) ph.commit(ca & 1);
         seq = CA;
     }
 
@@ -477,7 +520,7 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
         for (int c0 = 0; c0 < NF; c0 += 8) {
             float x[8];
             tc::tmem_ld8(tD1 + lane_base + FOFF + c0, x);
-            tc::tmem_ld_wait();
+            tc::tmem_ld_wait(x);
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 if (c0 + i < NF) sTr[row * NFS + c0 + i] = x[i] + mean_v;
@@ -489,7 +532,7 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
             float qx[8], qy[8];
             tc::tmem_ld8(tD1q + lane_base + c0, qx);
             tc::tmem_ld8(tD1q + NFP + lane_base + c0, qy);
-            tc::tmem_ld_wait();
+            tc::tmem_ld_wait(qx, qy);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int fg = c0 + i;
@@ -561,6 +604,7 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
             }
         }
     }
+    if (tid == THREADS - 1) *next_tile = claim;
     __syncthreads();
 
     // ---------------- face chunk: the rows of the flux region, 16 slots per half
@@ -584,7 +628,7 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
             tc::fence_after_sync();
             issue_chunk(seq, 0);
         }
-        ph.commits[seq & 1]++;
+        ph.commit(seq & 1);
         ++seq;
     }
 
@@ -610,7 +654,7 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
         for (int cq = 0; cq < CQ; ++cq, ++seq) {
             float x[8];
             tc::tmem_ld8(tD1 + lane_base + cq * 16 + half * 8, x);
-            tc::tmem_ld_wait();
+            tc::tmem_ld_wait(x);
             // [element][point][variable], element stride 36: conflict-free
 #pragma unroll
             for (int i = 0; i < 8; ++i) wst[(lane >> 2) * 36 + i * 4 + v] = x[i] + mean_v;
@@ -661,17 +705,31 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
                 tc::fence_after_sync();
                 issue_chunk(seq, CF + cq);
             }
-            ph.commits[seq & 1]++;
+            ph.commit(seq & 1);
         }
     }
 
-    // ---------------- epilogue: L = D2 / J into shared memory, then a
-    // coalesced pass over the tile for the stage combination
+    // ---------------- the next tile's rows into the (now free) trace region
+    bool pre = false;
+    {
+        const long long tn = *next_tile;
+        if (tn >= nCur && tn < nCur + nAff) {
+            pre = true;
+            if (tid == 32) {
+                const long long en = (tn - nCur) * D::E;
+                issue_tile_rows<N, AV, AV>(p, en, (int)min((long long)D::E, p.Kaff - en), sTr, &bars[3]);
+            }
+        }
+    }
+
+    // ---------------- epilogue: L = D2 / J into shared memory (the G1
+    // operand region), then a coalesced pass over the tile for the stage
+    // combination
     wait_buf(0);
     wait_buf(1);
     tc::fence_after_sync();
     {
-        float* sOut = sTr;
+        float* sOut = reinterpret_cast<float*>(smem + S::sA1);
         const float invJ = sGeo[e * 16 + 4];
         constexpr int per_half = N2 / 2;
 #pragma unroll
@@ -679,7 +737,7 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
             float x[8];
             const int i0 = half * per_half + c0;
             tc::tmem_ld8(tD2 + lane_base + i0, x);
-            tc::tmem_ld_wait();
+            tc::tmem_ld_wait(x);
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 if (i0 + i < NP) sOut[row * NP + i0 + i] = x[i] * invJ;
@@ -713,6 +771,7 @@ __device__ __forceinline__ void stage_tile_tc(const StageArgs<float>& p, long lo
         }
         __syncthreads();   // staging and per-element data are reused by the next tile
     }
+    return pre;
 }
 
 template <int N, bool AV>
@@ -740,15 +799,17 @@ __device__ __forceinline__ void load_tc_operators(const unsigned char* ops_tc, u
 // lets them overlap the affine work instead of forming a tail.
 template <int N, bool AV, int PREC>
 __global__ void __launch_bounds__(THREADS, 2) stage_kernel_tc(StageArgs<float> p, const unsigned char* ops_tc, int* err,
-                                                              int* counter) {
+                                                              int* counter, int* done) {
     extern __shared__ __align__(128) unsigned char smem_tc[];
     using S = TcSmem<N, AV>;
     constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
     const int tid = threadIdx.x;
     const long long nAff = (p.Kaff + ET - 1) / ET;
     const long long nCur = (p.K - p.Kaff + EC - 1) / EC;
-    __shared__ long long s_tile;
+    __shared__ int s_tile;
 
+    // prologue (barriers, TMEM, operators) overlaps the previous kernel
+    tc::pdl_trigger();
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_tc + S::sBAR);
     if (tid == 0) {
         for (int b = 0; b < 4; ++b) tc::mbar_init(&bars[b], 1);
@@ -756,18 +817,21 @@ __global__ void __launch_bounds__(THREADS, 2) stage_kernel_tc(StageArgs<float> p
     }
     uint32_t* slot = reinterpret_cast<uint32_t*>(smem_tc + S::sTMEM);
     if ((tid >> 5) == 0) tc::tmem_alloc(slot, TcDims<N>::TMEM_COLS);
+    load_tc_operators<N, AV>(ops_tc, smem_tc);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *slot;
     TcPhase ph;
-    bool ops_loaded = false;
-    while (true) {
-        if (tid == 0) s_tile = atomicAdd(counter, 1);
-        __syncthreads();
-        const long long t = s_tile;
-        __syncthreads();
-        if (t >= nCur + nAff) break;
+    bool ops_loaded = true, rows_ready = false;
+    tc::pdl_wait();
+    if (tid == 0) s_tile = atomicAdd(counter, 1);
+    __syncthreads();
+    long long t = s_tile;
+    while (t < nCur + nAff) {
+        __syncthreads();   // every thread has read s_tile
+        // claim the following tile now; the result is stored late in the tile
+        const int claim = (tid == THREADS - 1) ? atomicAdd(counter, 1) : 0;
         if (t < nCur) {
             TileRange tr;
             tr.curved = true;
@@ -775,6 +839,8 @@ __global__ void __launch_bounds__(THREADS, 2) stage_kernel_tc(StageArgs<float> p
             tr.ne = (int)min((long long)EC, p.K - tr.e0);
             stage_tile_call<N, float, AV>(p, tr, smem_tc);
             ops_loaded = false;
+            rows_ready = false;
+            if (tid == THREADS - 1) s_tile = claim;
             __syncthreads();
         } else {
             if (!ops_loaded) {
@@ -783,11 +849,20 @@ __global__ void __launch_bounds__(THREADS, 2) stage_kernel_tc(StageArgs<float> p
                 ops_loaded = true;
             }
             const long long e0 = (t - nCur) * ET;
-            stage_tile_tc<N, AV, PREC>(p, e0, (int)min((long long)ET, p.Kaff - e0), smem_tc, tmem, ph, err);
+            rows_ready = stage_tile_tc<N, AV, PREC>(p, e0, (int)min((long long)ET, p.Kaff - e0), smem_tc, tmem, ph,
+                                                    err, rows_ready, claim, &s_tile, nCur, nAff);
         }
+        t = s_tile;
     }
+    // the last CTA to leave resets the counters for the next launch
+    __threadfence();
     tc::fence_before_sync();
     __syncthreads();
+    if (tid == 0 && atomicAdd(done, 1) == (int)gridDim.x - 1) {
+        __threadfence();
+        *counter = 0;
+        *done = 0;
+    }
     if ((tid >> 5) == 0) tc::tmem_free(tmem, TcDims<N>::TMEM_COLS);
 }
 
@@ -817,7 +892,8 @@ int prepare_tc_t() {
     return 0;
 }
 
-// err[0]: error word; err[1]: tile counter of this launch (zeroed first).
+// err[0]: error word; err[1]: tile counter, err[3]: CTAs done (both zero
+// between launches: the last CTA resets them).
 template <int N, bool AV, int PREC>
 int launch_stage_tc_t(const StageArgs<float>& a, const unsigned char* ops_tc, int* err, cudaStream_t st) {
     constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
@@ -828,11 +904,9 @@ int launch_stage_tc_t(const StageArgs<float>& a, const unsigned char* ops_tc, in
     // the tile and neighbour records travel by TMA bulk copies: 16-byte aligned
     if (((uintptr_t)a.Us | (uintptr_t)a.Un | (uintptr_t)a.Uout | (uintptr_t)a.q | (uintptr_t)ops_tc) & 15)
         return (int)cudaErrorMisalignedAddress;
-    cudaError_t e = cudaMemsetAsync(err + 1, 0, sizeof(int), st);
-    if (e != cudaSuccess) return (int)e;
     const unsigned grid = (unsigned)(tiles < ctas ? tiles : ctas);
-    stage_kernel_tc<N, AV, PREC><<<grid, THREADS, tc_smem_bytes<N, AV>(), st>>>(a, ops_tc, err, err + 1);
-    return (int)cudaGetLastError();
+    return (int)launch_pdl(stage_kernel_tc<N, AV, PREC>, grid, THREADS, tc_smem_bytes<N, AV>(), st, a, ops_tc, err,
+                           err + 1, err + 3);
 }
 
 template <int N>

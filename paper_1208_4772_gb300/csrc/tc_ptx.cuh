@@ -66,7 +66,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
     for (uint32_t it = 0; it < limit; ++it) {
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(done) : "r"(smem_addr(mbar)), "r"(parity));
+                     : "=r"(done) : "r"(smem_addr(mbar)), "r"(parity) : "memory");
         if (done) return true;
     }
     return false;
@@ -93,6 +93,12 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Programmatic dependent launch: let the next kernel of the stream start its
+// prologue on SMs this grid leaves, and wait for the previous kernel of the
+// stream to complete (with its memory visible) before reading its results.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -116,7 +122,29 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
+// Wait for this thread's TMEM loads; the loaded registers pass through the
+// statements below, so that no use of them is scheduled before the wait.
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void reg_fence8(float v[8]) {
+    asm volatile("" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7])
+                 :: "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait(float a[8]) {
+    tmem_ld_wait();
+    reg_fence8(a);
+}
+__device__ __forceinline__ void tmem_ld_wait(float a[8], float b[8]) {
+    tmem_ld_wait();
+    reg_fence8(a);
+    reg_fence8(b);
+}
+__device__ __forceinline__ void tmem_ld_wait(float a[8], float b[8], float c[8], float d[8]) {
+    tmem_ld_wait();
+    reg_fence8(a);
+    reg_fence8(b);
+    reg_fence8(c);
+    reg_fence8(d);
+}
 
 __device__ __forceinline__ float to_tf32(float x) {
     uint32_t r;

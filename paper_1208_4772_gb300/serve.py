@@ -85,9 +85,9 @@ def estimate_bytes(K, N, curved=0, prec_bytes=4, av=False):
     b += (K - curved) * 4 * prec_bytes           # affine geometry
     b += curved * (5 * Nq + 3 * Nf + Np * Np) * prec_bytes
     b += 2 * K * 8                               # permutation maps
-    b += (304 * 8 + 8) * 8 + 16                  # reduction scratch, error word
+    b += (304 * 8 + 8) * 8 + 32                  # reduction scratch, error word and counters
     if av:
-        b += K * prec_bytes + K * 8 * Np * prec_bytes
+        b += (K + 31) // 32 * 32 * prec_bytes + K * 8 * Np * prec_bytes   # eps padded to whole tiles
     return b
 
 
