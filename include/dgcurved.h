@@ -153,7 +153,10 @@ int dg_residual(dg_ctx* ctx, dg_mesh m, double out_linf[4], double out_l2[4]);
 /* Advance n meshes (any mix of N and K) by nsteps SSP-RK3 steps each, with
  * per-mesh step sizes dts[n], using one persistent launch per RK stage that
  * walks a work list over all n meshes, replayed from a captured CUDA graph.
- * All meshes must share one precision mode and have av_on = 0.
+ * All meshes must share one precision mode and have av_on = 0.  DG_FP32 and
+ * DG_FP64_DEBUG run the CUDA-core tile body; DG_TF32 and DG_BF16X3 the
+ * tensor-core tile body (degrees 2..5 in one launch per stage, degree 6 in
+ * a second).  Each mesh ends in the state dg_step would give it.
  * Asynchronous. */
 int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* ms, const double* dts, int nsteps);
 

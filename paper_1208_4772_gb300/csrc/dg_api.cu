@@ -450,6 +450,83 @@ static int build_batch(dg_ctx* ctx, const std::vector<MeshData*>& ms, const doub
     return DG_OK;
 }
 
+// Tensor-core batch: affine tiles of 32 elements and curved tiles of the
+// CUDA-core size; degrees 2..5 in one persistent launch per stage, degree 6
+// (a larger shared-memory layout) in a second one.
+static int build_batch_tc(dg_ctx* ctx, const std::vector<MeshData*>& ms, const double* dts) {
+    const int n = (int)ms.size();
+    const int prec = ms[0]->prec == DG_TF32 ? 1 : 2;
+    std::vector<BatchItem> lo, hi;
+    for (int i = 0; i < n; ++i) {
+        const MeshData& m = *ms[i];
+        std::vector<BatchItem>& v = (m.N == 6) ? hi : lo;
+        const int EC = batch_tile_e(m.N, 4);
+        for (long long e0 = m.Kaff; e0 < m.K; e0 += EC)
+            v.push_back(BatchItem{i, m.N, e0, (int)std::min<long long>(EC, m.K - e0), 1});
+        for (long long e0 = 0; e0 < m.Kaff; e0 += 32)
+            v.push_back(BatchItem{i, m.N, e0, (int)std::min<long long>(32, m.Kaff - e0), 0});
+    }
+    // curved tiles first (slowest), then affine tiles grouped by degree,
+    // highest first, so that each CTA reloads its operators rarely
+    auto order = [](const BatchItem& a, const BatchItem& b) {
+        if (a.curved != b.curved) return a.curved > b.curved;
+        return a.N > b.N;
+    };
+    std::stable_sort(lo.begin(), lo.end(), order);
+    std::stable_sort(hi.begin(), hi.end(), order);
+    std::vector<StageArgs<float>> args(3 * (size_t)n);
+    std::vector<const unsigned char*> ops(7, nullptr);
+    for (int i = 0; i < n; ++i) {
+        const MeshData& m = *ms[i];
+        args[i] = make_args<float>(m, m.U[0], nullptr, m.U[1], 0.0, 1.0, dts[i], 0);
+        args[n + i] = make_args<float>(m, m.U[1], m.U[0], m.U[2], 0.75, 0.25, dts[i], 0);
+        args[2 * n + i] = make_args<float>(m, m.U[2], m.U[0], m.U[0], 1.0 / 3.0, 2.0 / 3.0, dts[i], 0);
+        ops[m.N] = (const unsigned char*)m.ops_tc;
+    }
+    std::vector<BatchItem> items(lo);
+    items.insert(items.end(), hi.begin(), hi.end());
+    void *dargs = nullptr, *ditems = nullptr, *dops = nullptr, *dcnt = nullptr;
+    if (cudaMalloc(&dargs, args.size() * sizeof(StageArgs<float>)) != cudaSuccess ||
+        cudaMalloc(&ditems, items.size() * sizeof(BatchItem)) != cudaSuccess ||
+        cudaMalloc(&dops, ops.size() * sizeof(void*)) != cudaSuccess ||
+        cudaMalloc(&dcnt, 8 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        for (void* b : {dargs, ditems, dops, dcnt})
+            if (b) cudaFree(b);
+        return fail(ctx, DG_ENOMEM, "batch work-list allocation failed");
+    }
+    ctx->batch_bufs = {dargs, ditems, dops, dcnt};
+    CUDA_OK(ctx, cudaMemcpy(dargs, args.data(), args.size() * sizeof(StageArgs<float>), cudaMemcpyHostToDevice));
+    CUDA_OK(ctx, cudaMemcpy(ditems, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
+    CUDA_OK(ctx, cudaMemcpy(dops, ops.data(), ops.size() * sizeof(void*), cudaMemcpyHostToDevice));
+    const int glo = lo.empty() ? 0 : batch_tc_grid(ctx->device, prec, false);
+    const int ghi = hi.empty() ? 0 : batch_tc_grid(ctx->device, prec, true);
+    if ((!lo.empty() && glo <= 0) || (!hi.empty() && ghi <= 0))
+        return fail(ctx, DG_ECUDA, "tensor-core batch kernel set-up failed");
+    CUDA_OK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    int e = (int)cudaMemsetAsync(dcnt, 0, 8 * sizeof(int), ctx->stream);
+    const size_t as = sizeof(StageArgs<float>);
+    const BatchItem* dl = (const BatchItem*)ditems;
+    for (int st = 0; st < 3 && !e; ++st) {
+        const char* a = (const char*)dargs + (size_t)st * n * as;
+        e = launch_batch_stage_tc(prec, false, a, dl, (int)lo.size(), (const unsigned char* const*)dops, ms[0]->err,
+                                  (int*)dcnt + 2 * st, glo, ctx->stream);
+        if (!e)
+            e = launch_batch_stage_tc(prec, true, a, dl + lo.size(), (int)hi.size(),
+                                      (const unsigned char* const*)dops, ms[0]->err, (int*)dcnt + 2 * st + 1, ghi,
+                                      ctx->stream);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+    if (e || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(ctx, DG_ECUDA, "graph capture of the batched step failed");
+    }
+    ctx->batch_graph = g;
+    CUDA_OK(ctx, cudaGraphInstantiate(&ctx->batch_gexec, g, 0));
+    return DG_OK;
+}
+
 extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* hs, const double* dts, int nsteps) {
     if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
     if (n <= 0 || !hs || !dts || nsteps < 0) return fail(ctx, DG_EINVAL, "bad argument");
@@ -459,8 +536,6 @@ extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* hs, const double
         if (!ms[i]) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle in batch");
         if (ms[i]->p.av_on) return fail(ctx, DG_EINVAL, "batched path runs meshes without artificial viscosity");
         if (ms[i]->prec != ms[0]->prec) return fail(ctx, DG_EINVAL, "batch mixes precision modes");
-        if (tensor_prec(ms[i]->prec))
-            return fail(ctx, DG_EINVAL, "batched path runs DG_FP32 or DG_FP64_DEBUG meshes");
         if (!std::isfinite(dts[i])) return fail(ctx, DG_EINVAL, "bad dt");
         for (int j = 0; j < i; ++j)
             if (hs[j] == hs[i]) return fail(ctx, DG_EINVAL, "mesh listed twice in batch");
@@ -472,7 +547,9 @@ extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* hs, const double
     if (!ctx->batch_gexec || key != ctx->batch_key_meshes || kdt != ctx->batch_key_dts) {
         CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
         reset_batch(ctx);
-        const int e = (ms[0]->rsize == 8) ? build_batch<double>(ctx, ms, dts) : build_batch<float>(ctx, ms, dts);
+        const int e = tensor_prec(ms[0]->prec) ? build_batch_tc(ctx, ms, dts)
+                      : (ms[0]->rsize == 8)    ? build_batch<double>(ctx, ms, dts)
+                                               : build_batch<float>(ctx, ms, dts);
         if (e) {
             reset_batch(ctx);
             return e;

@@ -18,4 +18,10 @@ template <typename Real>
 int launch_batch_stage(const void* args, const BatchItem* items, int nitems, int* counter, int grid,
                        cudaStream_t st);
 
+// Tensor-core batched stage (kernels_batch_tc.cu): prec 1 = TF32, 2 = BF16x3;
+// deg6 selects the instantiation for degree-6 items (the others take 2..5).
+int batch_tc_grid(int device, int prec, bool deg6);
+int launch_batch_stage_tc(int prec, bool deg6, const void* args, const BatchItem* items, int nitems,
+                          const unsigned char* const* ops_by_n, int* err, int* counter, int grid, cudaStream_t st);
+
 }  // namespace dgc

@@ -284,11 +284,13 @@ __device__ __forceinline__ void issue_tile_rows(const StageArgs<float>& p, long 
 // tile.  claim: in the last thread, the index of this CTA's next tile from
 // the atomic counter; it is stored to *next_tile once the face phase is
 // done (its latency is long hidden by then) and read after the cubature
-// chunks.  Returns true if the next tile's rows were requested here.
+// chunks.  bars: the CTA's four mbarriers (A2 buffers 0 and 1, G1, bulk
+// copies).  Returns true if the next tile's rows were requested here.
 template <int N, bool AV, int PREC>
 __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long long e0, int ne, unsigned char* smem,
                                               uint32_t tmem, TcPhase& ph, int* err, bool rows_ready,
-                                              int claim, int* next_tile, long long nCur, long long nAff) {
+                                              int claim, int* next_tile, long long nCur, long long nAff,
+                                              uint64_t* bars) {
     using D = TcDims<N>;
     using S = TcSmem<N, AV>;
     constexpr int NP = D::NP, NQ = D::NQ, NG = D::NG, NF = D::NF, NPK = D::NPK, FOFF = D::FOFF;
@@ -301,7 +303,6 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     const uint32_t tD1 = tmem, tD1q = tmem + N1, tD2 = tmem + N1 + (AV ? 2 * NFP : 0);
 
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::sBAR);
     float* sMean = reinterpret_cast<float*>(smem + S::sMEAN);
     float* sGeo = reinterpret_cast<float*>(smem + S::sGEO);
     float* sFb = reinterpret_cast<float*>(smem + S::sFB);
@@ -850,7 +851,7 @@ __global__ void __launch_bounds__(THREADS, 2) stage_kernel_tc(StageArgs<float> p
             }
             const long long e0 = (t - nCur) * ET;
             rows_ready = stage_tile_tc<N, AV, PREC>(p, e0, (int)min((long long)ET, p.Kaff - e0), smem_tc, tmem, ph,
-                                                    err, rows_ready, claim, &s_tile, nCur, nAff);
+                                                    err, rows_ready, claim, &s_tile, nCur, nAff, bars);
         }
         t = s_tile;
     }
