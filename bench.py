@@ -43,6 +43,13 @@ WORKLOADS = {
                                          "N=4, artificial viscosity on"),
     "cylinder_m0.38_n6": dict(kind="cyl", N=6, n_t=500, n_r=250, mach=0.38, aoa=0.0, av=False,
                               describe="cylinder in a channel, Mach 0.38, 250k triangles, N=6"),
+    # many meshes at once (dg_batch_step): not a single-mesh workload
+    "batch64": dict(kind="batch", describe="64 meshes, K log-uniform in [2k, 200k], N uniform in {2,3,4,5}, "
+                                           "airfoil and cylinder alternating, Mach U[0.3,0.85], AoA U[-2,4] deg, "
+                                           "no artificial viscosity; one persistent launch per RK stage"),
+    "serve": dict(kind="serve", describe="continuous batching: Poisson arrivals, K log-uniform in [1k, 500k], "
+                                         "N uniform in {2..6}, admission by an HBM budget, retirement at a 1e-6 "
+                                         "residual drop or a step cap"),
 }
 
 
@@ -58,6 +65,11 @@ def parse_args():
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-meshes", type=int, default=64, help="batch64: number of meshes")
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-rate", type=float, default=4.0, help="serve: Poisson arrival rate (1/s)")
+    ap.add_argument("--serve-max-steps", type=int, default=2000)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--cpu-sample", default="", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -192,6 +204,10 @@ def run_cpu_baseline(name, budget_s):
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return 0
+    if WORKLOADS[args.workload]["kind"] in ("batch", "serve"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm is timed on the single-mesh "
+                                                              "workloads only"}), flush=True)
         return 0
     for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"          # before numpy loads: the oracle runs on one core
@@ -416,6 +432,154 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ batch and serving
+def make_batch(n, seed0=2000):
+    """Seeded batch of n mesh requests (inputs only): K log-uniform in
+    [2k, 200k], N uniform in {2..5}, airfoil / cylinder alternating, Mach
+    U[0.3, 0.85], AoA U[-2, 4] deg; item i draws from seed seed0 + i."""
+    import math
+    import numpy as np
+    from paper_1208_4772_gb300 import serve
+    reqs = []
+    for i in range(n):
+        rng = np.random.default_rng(seed0 + i)
+        K = math.exp(rng.uniform(math.log(2000), math.log(200000)))
+        n_r = max(2, int(round(math.sqrt(K / 6.0))))
+        n_t = max(8, int(round(K / (2 * n_r))))
+        reqs.append(serve.Request(rid=i, arrival=0.0, kind="naca" if i % 2 == 0 else "cyl", n_t=n_t, n_r=n_r,
+                                  N=int(rng.integers(2, 6)), mach=float(rng.uniform(0.3, 0.85)),
+                                  aoa=float(rng.uniform(-2.0, 4.0)), seed=seed0 + i))
+    return reqs
+
+
+def run_batch(args):
+    """All meshes of the batch advanced together by dg_batch_step; one
+    timed step = one SSP-RK3 step of every mesh.  The batch's device
+    footprint is far above L2, so no flush is needed between steps."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1208_4772_gb300 import binding as B, serve
+    B.load()
+    torch.cuda.set_device(0)
+    reqs = make_batch(args.batch_meshes)
+    nodes = {N: B.dg_reference_nodes(N) for N in range(2, 7)}
+    for r in reqs:
+        serve.prepare(r, *nodes[r.N])
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = B.dg_create(0, stream.cuda_stream)
+    hs, dts = [], []
+    for r in reqs:
+        p = B.make_params(u_inf=r.u_inf, prec=args.prec)
+        hs.append(B.dg_mesh_upload(ctx, r.N, r.mesh.EToE, r.mesh.EToF, r.mesh.bc, r.xy, p))
+        B.dg_set_state(ctx, hs[-1], r.U0)
+        dts.append(r.dt)
+    dev_bytes = sum(B.dg_mesh_bytes(ctx, h) for h in hs)
+    for _ in range(args.warmup):
+        B.dg_batch_step(ctx, hs, dts, 1)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        B.dg_batch_step(ctx, hs, dts, 1)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    total_ms = float(sum(times))
+    dof_step = sum(3 * r.mesh.K * (r.N + 1) * (r.N + 2) // 2 * 4 for r in reqs)
+    value = dof_step * args.steps / (total_ms / 1e3)
+    curved = [int(np.any(r.mesh.bc == 1, axis=1).sum()) for r in reqs]
+    bytes_step = sum(3 * stage_kernel_bytes(r.mesh.K, c, r.N, False) for r, c in zip(reqs, curved))
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = 6800.0, "fallback"
+    if os.path.exists(peaks_path):
+        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+    achieved = bytes_step / (total_ms / args.steps * 1e-3) / 1e9
+    # end to end: host FP64 states in, steps, host FP64 states out
+    e2e = None
+    if not args.no_e2e:
+        t0 = time.perf_counter()
+        for r, h in zip(reqs, hs):
+            B.dg_set_state(ctx, h, r.U0)
+        B.dg_batch_step(ctx, hs, dts, args.steps)
+        out_bytes = 0
+        for r, h in zip(reqs, hs):
+            out_bytes += B.dg_get_state(ctx, h, r.mesh.K, r.U0.shape[2]).nbytes
+        el = time.perf_counter() - t0
+        e2e = {"value": dof_step * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": sum(r.U0.nbytes for r in reqs) / args.steps,
+               "d2h_bytes_per_step": out_bytes / args.steps,
+               "how": "dg_set_state x%d (host FP64) + dg_batch_step(%d) + dg_get_state x%d, wall clock"
+                      % (len(reqs), args.steps, len(reqs))}
+    B.dg_destroy(ctx)
+    Ks = [int(r.mesh.K) for r in reqs]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch64", "describe": WORKLOADS["batch64"]["describe"],
+                       "meshes": len(reqs), "total_K": int(sum(Ks)), "K_min": min(Ks), "K_max": max(Ks),
+                       "N_counts": {str(N): sum(1 for r in reqs if r.N == N) for N in range(2, 6)},
+                       "dof_per_step": int(dof_step), "device_bytes": int(dev_bytes),
+                       "state_precision": "fp32", "products": args.prec, "time_integrator": "SSP-RK3",
+                       "l2": "not flushed: the batch's device footprint is far above L2",
+                       "parallelism": "one GPU, all meshes in one persistent launch per stage"},
+            "roofline": {"kernel": "batched stage kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                         "bytes_per_step": bytes_step},
+            "cpu_baseline": None, "e2e": e2e, "gpu_launches": 3 * args.steps * (2 if any(r.N == 6 for r in reqs) else 1),
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Continuous batching over Poisson arrivals (serve.ServeLoop): latency
+    from arrival to result and the throughput over the run."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1208_4772_gb300 import binding as B, serve
+    B.load()
+    torch.cuda.set_device(0)
+    reqs = serve.poisson_requests(args.serve_requests, args.serve_rate, seed=3000)
+    nodes = {N: B.dg_reference_nodes(N) for N in range(2, 7)}
+    for r in reqs:
+        serve.prepare(r, *nodes[r.N])
+    ctx = B.dg_create(0)
+    loop = serve.ServeLoop(ctx, budget_bytes=args.serve_budget_gb * 1e9, check_every=100,
+                           max_steps=args.serve_max_steps, prec=args.prec)
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    done = loop.run(reqs, keep_states=False)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    B.dg_destroy(ctx)
+    st = serve.latency_stats(done)
+    line = {"metric": METRIC, "value": st["dof_updates"] / wall, "unit": UNIT, "n_gpus": 1,
+            "steps": None, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serve", "describe": WORKLOADS["serve"]["describe"],
+                       "requests": len(done), "arrival_rate_per_s": args.serve_rate,
+                       "step_cap": args.serve_max_steps, "check_every": 100, "drop": 1e-6,
+                       "budget_GB": args.serve_budget_gb, "products": args.prec,
+                       "peak_active": loop.peak_active, "peak_bytes": loop.peak_used,
+                       "retired": {k: sum(1 for r in done if r.reason == k) for k in set(r.reason for r in done)},
+                       "nonfinite": [[r.rid, r.kind, r.N, int(r.K), round(r.mach, 3)] for r in done
+                                     if r.reason == "nonfinite"]},
+            "latency": {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"]},
+            "wall_s": wall, "cpu_baseline": None, "e2e": None, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     faulthandler.enable()
     args = parse_args()
@@ -424,6 +588,10 @@ def main():
         return 0
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -169,7 +169,8 @@ class CircleCurve:
 def _omesh(name, surf, outer, n_r, ratio, jitter, rng, curve, wall_param=None):
     """Structured O-grid between a closed inner curve surf [n_t, 2] and an
     outer curve outer [n_t, 2], geometric radial spacing, random diagonal per
-    quad, interior vertices jittered by up to jitter * local spacing."""
+    quad (wall-adjacent quads: the better-shaped wall triangle), interior
+    vertices jittered by up to jitter * local spacing."""
     n_t = surf.shape[0]
     g = (ratio ** np.arange(n_r + 1) - 1.0) / (ratio ** n_r - 1.0)
     P = surf[None, :, :] + (outer - surf)[None, :, :] * g[:, None, None]   # [n_r+1, n_t, 2]
@@ -190,6 +191,18 @@ def _omesh(name, surf, outer, n_r, ratio, jitter, rng, curve, wall_param=None):
         return l * n_t + (i % n_t)
 
     verts, ids, diag = [], [], rng.integers(0, 2, size=(n_r, n_t))
+
+    def wall_quality(p0, p1, p2):   # 2 area / longest edge^2 of a wall triangle
+        e = [np.sum((P[q[0], q[1] % n_t] - P[r[0], r[1] % n_t]) ** 2) for q, r in ((p0, p1), (p1, p2), (p2, p0))]
+        u, w = P[p1[0], p1[1] % n_t] - P[p0[0], p0[1] % n_t], P[p2[0], p2[1] % n_t] - P[p0[0], p0[1] % n_t]
+        return abs(u[0] * w[1] - u[1] * w[0]) / max(e)
+
+    # wall-adjacent quads: the diagonal whose wall triangle is better shaped
+    # (where a grid line leaves a corner of the wall, e.g. a trailing edge,
+    # the other choice gives a sliver that curving the wall edge inverts)
+    for i in range(n_t):
+        a, b, c, d = (0, i), (0, i + 1), (1, i + 1), (1, i)
+        diag[0, i] = 0 if wall_quality(a, b, c) >= wall_quality(a, b, d) else 1
     for l in range(n_r):
         for i in range(n_t):
             a, b, c, d = (l, i), (l, i + 1), (l + 1, i + 1), (l + 1, i)
