@@ -36,6 +36,15 @@ if ROOT not in sys.path:
 
 METRIC = "RK-stage DOF-updates/s"
 UNIT = "DOF-updates/s"
+# arithmetic of the path per --prec: FP32 state and fluxes throughout; the
+# element-local operator products in TF32 or split BF16 on the tensor cores
+DTYPE = {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3", "fp64": "f64"}
+
+# DRAM bytes (read + write) of one stage-kernel launch from an ncu capture of
+# the default command (summary in profiles/stage_kernel_tc_naca0012_n4_av.md);
+# keyed by (workload, products) and only valid for the kernel source it was
+# taken on.
+TRAFFIC = {("naca0012_m0.8_n4_av", "tf32"): 60.585728e6 + 1.391360e6}
 
 WORKLOADS = {
     "naca0012_m0.8_n4_av": dict(kind="naca", N=4, n_t=300, n_r=100, mach=0.8, aoa=1.25, av=True,
@@ -60,8 +69,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="naca0012_m0.8_n4_av", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="fp32")
-    ap.add_argument("--compare-prec", default="", help="also time this precision (e.g. fp32)")
+    ap.add_argument("--prec", default="tf32", help="products: tf32 (default), bf16x3, fp32, fp64")
+    ap.add_argument("--compare-prec", default="fp32", help="also time this precision ('' to skip)")
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -381,7 +390,7 @@ def run_ours(args):
     achieved = bytes_launch / (stage_launch_ms * 1e-3) / 1e9
     roofline = {"kernel": "stage_kernel (N=%d, AV %s)" % (N, "on" if wl["av"] else "off"), "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_src, "traffic": None,
+                "peak_source": peak_src, "traffic": TRAFFIC.get((args.workload, args.prec)),
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": stage_launch_ms,
                 "dominant_kind_by_time": kinds[dom]}
 
@@ -419,7 +428,7 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec != "fp64" else "f64",
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec],
                 "data": "synthetic", "config": config_of(args, wl), "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches * world),
                 "clocks": clk,
@@ -522,7 +531,7 @@ def run_batch(args):
     Ks = [int(r.mesh.K) for r in reqs]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
             "config": {"workload": "batch64", "describe": WORKLOADS["batch64"]["describe"],
                        "meshes": len(reqs), "total_K": int(sum(Ks)), "K_min": min(Ks), "K_max": max(Ks),
                        "N_counts": {str(N): sum(1 for r in reqs if r.N == N) for N in range(2, 6)},
@@ -565,7 +574,7 @@ def run_serve(args):
     st = serve.latency_stats(done)
     line = {"metric": METRIC, "value": st["dof_updates"] / wall, "unit": UNIT, "n_gpus": 1,
             "steps": None, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
             "config": {"workload": "serve", "describe": WORKLOADS["serve"]["describe"],
                        "requests": len(done), "arrival_rate_per_s": args.serve_rate,
                        "step_cap": args.serve_max_steps, "check_every": 100, "drop": 1e-6,
