@@ -48,11 +48,16 @@ struct TcDims {
     static constexpr int NFP = (NF + 15) / 16 * 16;        // columns of each q-trace block
     static constexpr int N2 = (NP + 15) / 16 * 16;         // columns of D2
     static constexpr int CF = (NF + 31) / 32;              // face chunks
-    static constexpr int CQ = (NQ + 15) / 16;              // cubature chunks
+    // the points of a partial last cubature chunk ride in the face chunk's
+    // spare K slots when they fit (2 slots each: r and s parts; N = 4: the
+    // 49th point), saving a chunk
+    static constexpr int NQR = NQ % 16;
+    static constexpr int NQF = (NQR != 0 && 2 * NQR <= 32 * CF - NF) ? NQR : 0;   // folded points
+    static constexpr int CQ = NQF ? NQ / 16 : (NQ + 15) / 16;                     // cubature chunks
     static constexpr int CA = (NP + 15) / 16;              // viscous chunks
     static constexpr int NCH = CF + CQ + CA;               // chunks in the operator table
     static constexpr int E = 32;
-    static constexpr int NFS = NF | 1;                     // odd row stride of the trace exchange
+    static constexpr int NFS = (NF + 2 * NQF) | 1;         // odd row stride of the trace exchange
     static constexpr int TMEM_COLS = (N1 + 2 * NFP + N2) <= 128 ? 128 : 256;
 };
 
@@ -526,6 +531,13 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             for (int i = 0; i < 8; ++i)
                 if (c0 + i < NF) sTr[row * NFS + c0 + i] = x[i] + mean_v;
         }
+        if constexpr (D::NQF > 0) {   // the folded cubature points' values
+            float x[8];
+            tc::tmem_ld8(tD1 + lane_base + CQ * 16, x);
+            tc::tmem_ld_wait(x);
+#pragma unroll
+            for (int m = 0; m < D::NQF; ++m) sTr[row * NFS + NF + 2 * m] = x[m] + mean_v;
+        }
     } else if constexpr (AV) {
         const float se = sSe[e];
 #pragma unroll
@@ -550,8 +562,27 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     // (F*.n - (sqrt(eps) q)*.n - F(Ubar).n) sJ replaces the trace of each
     // side.  F* from the other side of an in-tile face is -F*.
     {
-        const int nitems = sFL[0] * NG;
+        const int nface = sFL[0] * NG;
+        const int nitems = nface + 32 * D::NQF;
         for (int it = tid; it < nitems; it += blockDim.x) {
+            if (D::NQF > 0 && it >= nface) {
+                // a folded cubature point of one element: its contravariant
+                // flux deviations into the two slots after the face points
+                const int ee = (it - nface) & 31, m = (it - nface) >> 5;
+                float* tr = sTr + ee * 4 * NFS + NF + 2 * m;
+                const float Uc[4] = {tr[0], tr[NFS], tr[2 * NFS], tr[3 * NFS]};
+                float F[4], G[4];
+                euler_flux(Uc, p.gamma, F, G);
+                const float* ge = sGeo + ee * 16;
+                const float* fb = sFb + ee * 8;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const float dF = F[w] - fb[w], dG = G[w] - fb[4 + w];
+                    tr[w * NFS] = ge[0] * dF + ge[1] * dG;
+                    tr[w * NFS + 1] = ge[2] * dF + ge[3] * dG;
+                }
+                continue;
+            }
             const int entry = sFL[1 + it / NG], gg = it % NG;
             const int ee = entry / 3, f = entry - ee * 3, fg = f * NG + gg;
             const int4 nbw = sNb[ee];
@@ -619,7 +650,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int c = half * 16 + s0 + i;
-                x[i] = (c < NF) ? sTr[row * NFS + c] : 0.f;
+                x[i] = (c < NF + 2 * D::NQF) ? sTr[row * NFS + c] : 0.f;
             }
             store8<PREC>(A2, row, half * 16 + s0, 32, x);
         }
@@ -997,7 +1028,12 @@ std::vector<uint8_t> pack_ops_tc(const RefOps& R, int prec) {
             if (i >= NP) return 0.0;
             if (c < D::CF) {
                 const int fg = c * 32 + s;
-                return fg < NF ? -R.MLift[(size_t)i * NF + fg] : 0.0;
+                if (fg < NF) return -R.MLift[(size_t)i * NF + fg];
+                if (fg < NF + 2 * D::NQF) {   // folded cubature point: r part, then s part
+                    const int q = D::CQ * 16 + (fg - NF) / 2;
+                    return ((fg - NF) & 1) ? R.MsW[(size_t)i * NQ + q] : R.MrW[(size_t)i * NQ + q];
+                }
+                return 0.0;
             }
             if (c < D::CF + D::CQ) {
                 const int q = (c - D::CF) * 16 + (s & 15);
