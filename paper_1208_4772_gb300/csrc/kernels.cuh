@@ -60,22 +60,32 @@ __device__ __forceinline__ void euler_flux(const Real U[4], Real gamma, Real F[4
 }
 
 // F*.n by local Lax-Friedrichs with the pointwise wave speed
-// lam = max(|u-.n| + c-, |u+.n| + c+).
+// lam = max(|u-.n| + c-, |u+.n| + c+).  The normal flux of a state is formed
+// directly, F.n = (m.n, m_x u_n + p n_x, m_y u_n + p n_y, (E + p) u_n) with
+// u_n = m.n / rho, sharing p and 1/rho with the wave speed.
+template <typename Real>
+__device__ __forceinline__ void normal_flux(const Real U[4], Real nx, Real ny, Real gamma, Real Fn[4],
+                                            Real& speed) {
+    const Real ir = recip(U[0]);
+    const Real mn = U[1] * nx + U[2] * ny;
+    const Real un = mn * ir;
+    const Real p = (gamma - Real(1)) * (U[3] - Real(0.5) * (U[1] * U[1] + U[2] * U[2]) * ir);
+    Fn[0] = mn;
+    Fn[1] = U[1] * un + p * nx;
+    Fn[2] = U[2] * un + p * ny;
+    Fn[3] = (U[3] + p) * un;
+    speed = fabs(un) + sqrt(gamma * p * ir);
+}
+
 template <typename Real>
 __device__ __forceinline__ void llf_flux(const Real Um[4], const Real Up[4], Real nx, Real ny, Real gamma,
                                          Real Fn[4]) {
-    Real Fm[4], Gm[4], Fp[4], Gp[4];
-    euler_flux(Um, gamma, Fm, Gm);
-    euler_flux(Up, gamma, Fp, Gp);
-    const Real irm = recip(Um[0]), irp = recip(Up[0]);
-    const Real pm = (gamma - Real(1)) * (Um[3] - Real(0.5) * (Um[1] * Um[1] + Um[2] * Um[2]) * irm);
-    const Real pp = (gamma - Real(1)) * (Up[3] - Real(0.5) * (Up[1] * Up[1] + Up[2] * Up[2]) * irp);
-    const Real lm = fabs((Um[1] * nx + Um[2] * ny) * irm) + sqrt(gamma * pm * irm);
-    const Real lp = fabs((Up[1] * nx + Up[2] * ny) * irp) + sqrt(gamma * pp * irp);
+    Real Fm[4], Fp[4], lm, lp;
+    normal_flux(Um, nx, ny, gamma, Fm, lm);
+    normal_flux(Up, nx, ny, gamma, Fp, lp);
     const Real lam = fmax(lm, lp);
 #pragma unroll
-    for (int v = 0; v < 4; ++v)
-        Fn[v] = Real(0.5) * ((Fm[v] + Fp[v]) * nx + (Gm[v] + Gp[v]) * ny) - Real(0.5) * lam * (Up[v] - Um[v]);
+    for (int v = 0; v < 4; ++v) Fn[v] = Real(0.5) * (Fm[v] + Fp[v]) - Real(0.5) * lam * (Up[v] - Um[v]);
 }
 
 template <typename Real>

@@ -33,7 +33,7 @@ struct TgSmem {
     static constexpr int A2_BYTES = 128 * 32 * 4;
     static constexpr int sA2 = sA1 + A1_REGION;                    // USx, USy operands
     static constexpr int sTR = sA2 + 2 * A2_BYTES;                 // U tile, neighbour records, traces, face terms
-    static constexpr int REC = 4 * D::NP;                          // floats of one element's U record
+    static constexpr int REC = 4 * D::NP + 4;                      // one element's U record and eps
     static constexpr int TR_BYTES = al(mx(mx(128 * D::NFS * 4, 32 * REC * 4), TileStage<N, false>::FLOATS * 4));
     static constexpr int NBB = TR_BYTES / (REC * 4);               // neighbour records per batch
     static constexpr int sIO = sTR + TR_BYTES;                     // q tile
@@ -130,7 +130,7 @@ __device__ __forceinline__ bool grad_tile_tc(const StageArgs<float>& p, float* q
     float* sNbv = reinterpret_cast<float*>(smem + S::sA1);
     const int nlist = sList[0];
     auto issue_batch = [&](int b0) {
-        constexpr int CH = S::REC / 4;
+        constexpr int CH = NP + 1;   // 16-byte pieces of the U rows, then the eps word
         const int nc = min(S::NBB, nlist - b0) * CH;
         for (int c = tid; c < nc; c += blockDim.x) {
             const int i = c / CH, j = c - i * CH;
@@ -138,7 +138,10 @@ __device__ __forceinline__ bool grad_tile_tc(const StageArgs<float>& p, float* q
             const int ee = entry / 3, f = entry - ee * 3;
             const int4 nbw = sNb[ee];
             const long long nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
-            tc::cp_async16(sTr + i * S::REC + j * 4, p.Us + nb * 4 * NP + j * 4);
+            if (j == NP)
+                tc::cp_async4(sTr + i * S::REC + 4 * NP, p.eps + nb);
+            else
+                tc::cp_async16(sTr + i * S::REC + j * 4, p.Us + nb * 4 * NP + j * 4);
         }
     };
     if (nlist > 0) issue_batch(0);
@@ -161,15 +164,11 @@ __device__ __forceinline__ bool grad_tile_tc(const StageArgs<float>& p, float* q
                 const int ee = entry / 3, f = entry - ee * 3;
                 const int4 nbw = sNb[ee];
                 const int fn = code_face(nbw.w, f);
-                const float* rec = sTr + fi * S::REC + w * NP;
+                const float* rec = sTr + fi * S::REC;
                 float un[NP];
 #pragma unroll
-                for (int j = 0; j < NP; ++j) un[j] = rec[j];
-                float sen = 0.f;
-                if (w == 0) {
-                    const long long nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
-                    sen = sqrtf(__ldg(p.eps + nb));
-                }
+                for (int j = 0; j < NP; ++j) un[j] = rec[w * NP + j];
+                const float sen = sqrtf(rec[4 * NP]);
                 const int g1 = hp ? NG : GH;
 #pragma unroll 1
                 for (int gg = hp * GH; gg < g1; ++gg) {

@@ -120,7 +120,7 @@ struct TcSmem {
     static constexpr int NBUF = 2;
     static constexpr int TR_FLOATS = 128 * D::NFS;
     static constexpr int WST = 32 * 18;                                      // floats per warp: cubature transpose
-    static constexpr int REC = (AV ? 12 : 4) * D::NP;                       // floats of one element's U (and q) record
+    static constexpr int REC = (AV ? 12 : 4) * D::NP + (AV ? 4 : 0);        // one element's U (and q, eps) record
     static constexpr int TR_REGION =
         al(mx(mx(TR_FLOATS * 4 * (AV ? 2 : 1), 8 * WST * 4), mx(TileStage<N, AV>::FLOATS * 4, 32 * REC * 4)));
     static constexpr int NBB = TR_REGION / (REC * 4);                        // neighbour records per batch
@@ -443,7 +443,9 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     float* sNbv = reinterpret_cast<float*>(smem + S::sA1);
     const int nlist = sList[0];
     auto issue_batch = [&](int b0) {
-        constexpr int CU = NP, CH = S::REC / 4;    // 16-byte pieces: U part, whole record
+        // 16-byte pieces: U rows, then q rows; with AV one more item per face
+        // copies its eps (4 bytes) to the last word of the record
+        constexpr int CU = NP, CH = (AV ? 12 : 4) * NP / 4 + (AV ? 1 : 0);
         const int nc = min(S::NBB, nlist - b0) * CH;
         for (int c = tid; c < nc; c += blockDim.x) {
             const int i = c / CH, j = c - i * CH;
@@ -451,6 +453,10 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             const int ee = entry / 3, f = entry - ee * 3;
             const int4 nbw = sNb[ee];
             const long long nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
+            if (AV && j == CH - 1) {
+                tc::cp_async4(sTr + i * S::REC + 12 * NP, p.eps + nb);
+                continue;
+            }
             const float* src = (j < CU) ? p.Us + nb * 4 * NP + j * 4 : p.q + nb * 8 * NP + (j - CU) * 4;
             tc::cp_async16(sTr + i * S::REC + j * 4, src);
         }
@@ -484,13 +490,17 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 const int4 nbw = sNb[ee];
                 const int fn = code_face(nbw.w, f);
                 const float* rec = sTr + fi * S::REC;
-                float un[NP];
+                float un[NP], qx[AV ? NP : 1], qy[AV ? NP : 1];
 #pragma unroll
                 for (int j = 0; j < NP; ++j) un[j] = rec[w * NP + j];
                 float sen = 0.f, nx = 0.f, ny = 0.f;
                 if constexpr (AV) {
-                    const long long nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
-                    sen = sqrtf(__ldg(p.eps + nb));
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        qx[j] = rec[(4 + w) * NP + j];
+                        qy[j] = rec[(8 + w) * NP + j];
+                    }
+                    sen = sqrtf(rec[12 * NP]);
                     nx = sGeo[ee * 16 + 5 + 3 * f];
                     ny = sGeo[ee * 16 + 6 + 3 * f];
                 }
@@ -500,19 +510,18 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                     const int fg = f * NG + gg;
                     const float* ig = sIgF + (fn * NG + (NG - 1 - gg)) * NP;
                     float* dst = sNbv + (ee * NF + fg) * S::NBV_C;
-                    float a = 0.f;
+                    float a = 0.f, ax = 0.f, ay = 0.f;
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) a += ig[j] * un[j];
-                    dst[w] = a;
-                    if constexpr (AV) {
-                        float ax = 0.f, ay = 0.f;
-#pragma unroll
-                        for (int j = 0; j < NP; ++j) {
-                            ax += ig[j] * rec[(4 + w) * NP + j];
-                            ay += ig[j] * rec[(8 + w) * NP + j];
+                    for (int j = 0; j < NP; ++j) {
+                        const float g = ig[j];
+                        a += g * un[j];
+                        if constexpr (AV) {
+                            ax += g * qx[j];
+                            ay += g * qy[j];
                         }
-                        dst[4 + w] = sen * (ax * nx + ay * ny);
                     }
+                    dst[w] = a;
+                    if constexpr (AV) dst[4 + w] = sen * (ax * nx + ay * ny);
                 }
             }
         }
