@@ -160,6 +160,23 @@ int dg_residual(dg_ctx* ctx, dg_mesh m, double out_linf[4], double out_l2[4]);
  * Asynchronous. */
 int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* ms, const double* dts, int nsteps);
 
+/* Tile-size autotuner for the CUDA-core path (DG_FP32, DG_FP64_DEBUG): times
+ * nsteps (1..1000) SSP-RK3 steps of mesh m with dt = 0 (the full work of a
+ * step, the state unchanged; it is also saved and restored) for each
+ * candidate tile size -- E/2, E, 3E/2, 2E, 3E elements per CTA around the
+ * degree's default E, where the tile's shared-memory layout fits one CTA --
+ * and keeps the fastest for m.  The choice also applies to the context's
+ * other meshes of the same degree, precision and viscosity setting, and to
+ * those uploaded later (and so to dg_batch_step).  Outputs: *tile_e_out (the
+ * chosen size; 32 for DG_TF32 / DG_BF16X3, whose tensor-core tiles are
+ * fixed at the 128 rows of the products, nothing timed); optional
+ * cand_out[8], ms_out[8] (candidates and milliseconds per step) and
+ * *ncand_out (number of candidates), each may be NULL.  Synchronises the
+ * context's stream.  The paper has no counterpart (its block per element is
+ * fixed); a step's work distribution over CTAs is the tuned quantity. */
+int dg_autotune(dg_ctx* ctx, dg_mesh m, int nsteps, int32_t* tile_e_out, int32_t* cand_out, double* ms_out,
+                int32_t* ncand_out);
+
 /* Kernel timing for profiling (paper Sec. 4 reports run times of the time
  * loop).  dg_set_profiling(ctx, m, 1) puts CUDA event-record nodes around
  * every kernel of the step graph of mesh m (the graph is re-captured);

@@ -78,6 +78,8 @@ def load():
         "dg_set_profiling": (I, [P, C.c_int32, I]),
         "dg_residual_norms_noalloc": (I, [P, I64, C.c_int32, P, P]),
         "dg_kernel_times": (I, [P, C.c_int32, dp]),
+        "dg_autotune": (I, [P, C.c_int32, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32), dp,
+                            C.POINTER(C.c_int32)]),
         "dg_last_error": (C.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -202,6 +204,18 @@ def dg_residual_norms_noalloc(values_dev_ptr, K, Np, out8_dev_ptr, stream=None):
 
 def dg_set_profiling(ctx, m, on):
     return _check(load().dg_set_profiling(ctx, m, int(on)), ctx)
+
+
+def dg_autotune(ctx, m, nsteps=5):
+    """Tile-size autotuner of the CUDA-core path: returns (chosen elements
+    per tile, {candidate: ms per step}); the tensor-core path reports its
+    fixed 32 and an empty table."""
+    best = C.c_int32(0)
+    cand = (C.c_int32 * 8)()
+    ms = np.zeros(8)
+    n = C.c_int32(0)
+    _check(load().dg_autotune(ctx, m, int(nsteps), C.byref(best), cand, _dptr(ms), C.byref(n)), ctx)
+    return int(best.value), {int(cand[i]): float(ms[i]) for i in range(n.value)}
 
 
 def dg_kernel_times(ctx, m):

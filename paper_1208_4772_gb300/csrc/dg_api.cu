@@ -59,6 +59,30 @@ int dispatch_prepare(int N) {
     return (int)cudaErrorInvalidValue;
 }
 template <typename Real>
+int dispatch_tile_default(int N) {
+    switch (N) {
+        case 2: return tile_e_default<2, Real>();
+        case 3: return tile_e_default<3, Real>();
+        case 4: return tile_e_default<4, Real>();
+        case 5: return tile_e_default<5, Real>();
+        case 6: return tile_e_default<6, Real>();
+    }
+    return 0;
+}
+template <typename Real>
+bool dispatch_tile_fits(int N, int e, int av) {
+    switch (N) {
+        case 2: return tile_e_fits<2, Real>(e, av);
+        case 3: return tile_e_fits<3, Real>(e, av);
+        case 4: return tile_e_fits<4, Real>(e, av);
+        case 5: return tile_e_fits<5, Real>(e, av);
+        case 6: return tile_e_fits<6, Real>(e, av);
+    }
+    return false;
+}
+int tune_key(int N, size_t rsize, int av) { return N * 32 + (int)rsize * 2 + (av ? 1 : 0); }
+
+template <typename Real>
 int dispatch_stage(int N, const StageArgs<Real>& a, int av, cudaStream_t st) {
     switch (N) {
         case 2: return launch_stage<2, Real>(a, av, st);
@@ -316,6 +340,7 @@ StageArgs<Real> make_args(const MeshData& m, const void* Us, const void* Un, voi
     s.eps0 = m.p.eps0;
     s.S_lo = std::pow(10.0, m.s0 - m.p.kappa);
     s.S_hi = std::pow(10.0, m.s0 + m.p.kappa);
+    s.tile_e = tensor_prec(m.prec) ? 0 : m.tile_e;   // the tensor-core path has fixed tiles
     return s;
 }
 
@@ -398,9 +423,11 @@ template <typename Real>
 static int build_batch(dg_ctx* ctx, const std::vector<MeshData*>& ms, const double* dts) {
     const int n = (int)ms.size();
     std::vector<BatchItem> items;
+    int e_by_n[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int i = 0; i < n; ++i) {
         const MeshData& m = *ms[i];
-        const int E = batch_tile_e(m.N, (int)m.rsize);
+        const int E = m.tile_e > 0 ? m.tile_e : batch_tile_e(m.N, (int)m.rsize);
+        e_by_n[m.N] = std::max(e_by_n[m.N], E);
         for (long long e0 = 0; e0 < m.Kaff; e0 += E)
             items.push_back(BatchItem{i, m.N, e0, (int)std::min<long long>(E, m.Kaff - e0), 0});
         for (long long e0 = m.Kaff; e0 < m.K; e0 += E)
@@ -431,14 +458,15 @@ static int build_batch(dg_ctx* ctx, const std::vector<MeshData*>& ms, const doub
     ctx->batch_bufs = {dargs, ditems, dcnt};
     CUDA_OK(ctx, cudaMemcpy(dargs, args.data(), args.size() * sizeof(StageArgs<Real>), cudaMemcpyHostToDevice));
     CUDA_OK(ctx, cudaMemcpy(ditems, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
-    const int grid = batch_grid<Real>(ctx->device, 0);
+    const size_t smem = batch_smem_bytes<Real>(e_by_n);
+    const int grid = batch_grid<Real>(ctx->device, 0, smem);
     if (grid <= 0) return fail(ctx, DG_ECUDA, "batch kernel occupancy query failed");
     CUDA_OK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     int e = (int)cudaMemsetAsync(dcnt, 0, 4 * sizeof(int), ctx->stream);
     const size_t as = sizeof(StageArgs<Real>);
     for (int st = 0; st < 3 && !e; ++st)
         e = launch_batch_stage<Real>((const char*)dargs + (size_t)st * n * as, (const BatchItem*)ditems,
-                                     (int)items.size(), (int*)dcnt + st, grid, ctx->stream);
+                                     (int)items.size(), (int*)dcnt + st, grid, smem, ctx->stream);
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
     if (e || ce != cudaSuccess) {
@@ -881,6 +909,10 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
         free_mesh(m);
         return fail(ctx, DG_ECUDA, "mesh upload memset failed");
     }
+    if (!tensor_prec(m->prec)) {   // a tile size tuned earlier for this kind of mesh
+        auto it = ctx->tuned_e.find(tune_key(m->N, m->rsize, m->p.av_on));
+        if (it != ctx->tuned_e.end()) m->tile_e = it->second;
+    }
     const dg_mesh h = ctx->next_id++;
     ctx->meshes[h] = m;
     *out = h;
@@ -1069,6 +1101,84 @@ int dg_sync(dg_ctx* ctx, double timeout_s) {
         if (el > timeout_s) return fail(ctx, DG_ETIMEOUT, "work still in flight after the timeout");
         std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
+}
+
+int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t* cand_out, double* ms_out,
+                int32_t* ncand_out) {
+    if (!ctx || !tile_e_out) return fail(ctx, DG_EINVAL, "NULL argument");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    if (nsteps < 1 || nsteps > 1000) return fail(ctx, DG_EINVAL, "nsteps must be in 1..1000");
+    if (ncand_out) *ncand_out = 0;
+    if (tensor_prec(m->prec)) {   // fixed tiles of 32 elements = the 128 rows of the products
+        *tile_e_out = 32;
+        return DG_OK;
+    }
+    cudaSetDevice(ctx->device);
+    const bool dbl = m->rsize == 8;
+    const int av = m->p.av_on;
+    const int E0 = dbl ? dispatch_tile_default<double>(m->N) : dispatch_tile_default<float>(m->N);
+    std::vector<int> cands;
+    for (int twice : {1, 2, 3, 4, 6}) {   // E0/2, E0, 3E0/2, 2E0, 3E0
+        const int e = std::max(1, E0 * twice / 2);
+        const bool fits = dbl ? dispatch_tile_fits<double>(m->N, e, av) : dispatch_tile_fits<float>(m->N, e, av);
+        if (fits && std::find(cands.begin(), cands.end(), e) == cands.end()) cands.push_back(e);
+    }
+    if (cands.empty()) return fail(ctx, DG_EINVAL, "no tile size fits the shared memory");
+    // timed steps with dt = 0 (the full work of a step, the state unchanged);
+    // the state is saved and restored all the same
+    const size_t bytes = (size_t)m->K * 4 * m->Np * m->rsize;
+    CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
+    CUDA_OK(ctx, cudaMemcpyAsync(m->rhs, m->U[0], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    CUDA_OK(ctx, cudaEventCreate(&ea));
+    if (cudaEventCreate(&eb) != cudaSuccess) {
+        cudaEventDestroy(ea);
+        return fail(ctx, DG_ECUDA, "event creation failed");
+    }
+    std::vector<double> ms(cands.size(), 0.0);
+    int err = 0;
+    for (size_t c = 0; c < cands.size() && !err; ++c) {
+        m->tile_e = cands[c];
+        err = enqueue_step(*m, 0.0, ctx->stream);   // warm-up
+        if (!err) err = (int)cudaEventRecord(ea, ctx->stream);
+        for (int k = 0; k < nsteps && !err; ++k) err = enqueue_step(*m, 0.0, ctx->stream);
+        if (!err) err = (int)cudaEventRecord(eb, ctx->stream);
+        if (!err) err = (int)cudaEventSynchronize(eb);
+        float t = 0.f;
+        if (!err) err = (int)cudaEventElapsedTime(&t, ea, eb);
+        ms[c] = t;
+    }
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    const cudaError_t ce = cudaMemcpyAsync(m->U[0], m->rhs, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    const cudaError_t cs = cudaStreamSynchronize(ctx->stream);
+    size_t best = 0;
+    for (size_t c = 1; c < cands.size(); ++c)
+        if (ms[c] < ms[best]) best = c;
+    m->tile_e = err ? 0 : cands[best];
+    // graphs captured with the old tile size are rebuilt on their next use
+    if (m->gexec) { cudaGraphExecDestroy(m->gexec); m->gexec = nullptr; }
+    if (m->graph) { cudaGraphDestroy(m->graph); m->graph = nullptr; }
+    reset_batch(ctx);
+    if (err) return fail(ctx, DG_ECUDA, std::string("autotune step failed: ") + cudaGetErrorString((cudaError_t)err));
+    if (ce != cudaSuccess || cs != cudaSuccess) return fail(ctx, DG_ECUDA, "autotune state restore failed");
+    const int key = tune_key(m->N, m->rsize, av);
+    ctx->tuned_e[key] = m->tile_e;
+    for (auto& kv : ctx->meshes) {   // the context's other meshes of this kind follow
+        MeshData* o = kv.second;
+        if (o == m || tensor_prec(o->prec) || tune_key(o->N, o->rsize, o->p.av_on) != key) continue;
+        o->tile_e = m->tile_e;
+        if (o->gexec) { cudaGraphExecDestroy(o->gexec); o->gexec = nullptr; }
+        if (o->graph) { cudaGraphDestroy(o->graph); o->graph = nullptr; }
+    }
+    *tile_e_out = m->tile_e;
+    if (ncand_out) *ncand_out = (int32_t)cands.size();
+    for (size_t c = 0; c < cands.size() && c < 8; ++c) {
+        if (cand_out) cand_out[c] = cands[c];
+        if (ms_out) ms_out[c] = ms[c] / nsteps;
+    }
+    return check_device_errors(ctx);
 }
 
 int dg_set_profiling(dg_ctx* ctx, dg_mesh h, int on) {

@@ -1,6 +1,7 @@
 // Work list of the persistent batched stage kernel.
 #pragma once
 #include <cuda_runtime.h>
+#include <cstddef>
 
 namespace dgc {
 
@@ -13,9 +14,10 @@ struct BatchItem {
 };
 
 int batch_tile_e(int N, int rsize);
-template <typename Real> int batch_grid(int device, int ctas_per_sm);
+template <typename Real> size_t batch_smem_bytes(const int* e_by_n);
+template <typename Real> int batch_grid(int device, int ctas_per_sm, size_t smem);
 template <typename Real>
-int launch_batch_stage(const void* args, const BatchItem* items, int nitems, int* counter, int grid,
+int launch_batch_stage(const void* args, const BatchItem* items, int nitems, int* counter, int grid, size_t smem,
                        cudaStream_t st);
 
 // Tensor-core batched stage (kernels_batch_tc.cu): prec 1 = TF32, 2 = BF16x3;

@@ -75,6 +75,9 @@ struct StageArgs {
     // sensor parameters (AV); ramp band of S = 10^(s0 -+ kappa), set on the host
     double s0, kappa, eps0;
     double S_lo, S_hi;
+    // elements per CUDA-core tile (0: the degree's default); sets the grid,
+    // the shared-memory layout and the launch's shared memory
+    int tile_e;
 };
 
 // Per-degree launchers (kernels_n<N>.cu).  Return cudaError_t as int.
@@ -84,6 +87,10 @@ template <int N, typename Real> int launch_grad(const StageArgs<Real>& a, Real* 
 // Set the dynamic shared-memory limits of the degree-N kernels (call once
 // per device before the first launch or stream capture).
 template <int N, typename Real> int prepare_kernels();
+// CUDA-core tile sizes: the default, and whether a tile of e elements fits
+// the shared-memory limit of one CTA in both the stage and gradient kernels.
+template <int N, typename Real> int tile_e_default();
+template <int N, typename Real> bool tile_e_fits(int e, int av);
 
 // Tensor-core stage kernel (tc_kernels.cuh): prec 1 = TF32, 2 = BF16 x3.
 template <int N>

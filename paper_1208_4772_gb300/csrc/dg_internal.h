@@ -16,6 +16,7 @@ struct MeshData {
     dg_params p{};
     int prec = 0;
     size_t rsize = 4;             // bytes of the device real type
+    int tile_e = 0;               // elements per CUDA-core tile (0: default; see dg_autotune)
     double s0 = 0.0;              // sensor offset actually used
     std::vector<long long> perm;  // device element d is caller element perm[d]
     void* U[3] = {nullptr, nullptr, nullptr};  // U^n, stage buffers
@@ -58,6 +59,7 @@ struct dg_ctx {
     std::map<int, dgc::MeshData*> meshes;
     int next_id = 1;
     std::map<int, void*> ops;         // operator tables by (N, precision)
+    std::map<int, int> tuned_e;       // tile sizes found by dg_autotune, by (N, real size, av)
     std::vector<void*> batch_bufs;    // work lists of the batched path
     // batched-step graph cache
     std::vector<int> batch_key_meshes;

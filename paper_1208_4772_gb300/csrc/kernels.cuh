@@ -30,13 +30,15 @@ struct Tile {
     static constexpr int OPS = 3 * NP * NQ + 2 * NP * NF;
     static constexpr int PER_E = 4 * NP + 8 * NQ + 4 * NF + 16 + 4 * NP;
     static constexpr int PER_E_AV = 8 * NP + 1;
-    static constexpr size_t smem_stage(bool av) {
-        return sizeof(Real) * (size_t)(OPS + E * (PER_E + (av ? PER_E_AV : 0)));
+    static constexpr size_t smem_stage(bool av, int e = E) {
+        return sizeof(Real) * (size_t)(OPS + e * (PER_E + (av ? PER_E_AV : 0)));
     }
     // gradient kernel: ops IcubT, DrT, DsT (curved) or QrT, QsT (affine), IgT, LT / MLT
     static constexpr int OPS_G = 3 * NP * NQ + 2 * NP * NF;
     static constexpr int PER_E_G = 4 * NP + 16 * NQ + 8 * NF + 16 + 8 * NP + 1;
-    static constexpr size_t smem_grad() { return sizeof(Real) * (size_t)(OPS_G + E * PER_E_G); }
+    static constexpr size_t smem_grad(int e = E) { return sizeof(Real) * (size_t)(OPS_G + e * PER_E_G); }
+    // the tile size of a launch: the mesh's tuned value or the default
+    static __host__ __device__ int cap(int tile_e) { return tile_e > 0 ? tile_e : E; }
 };
 
 // Correctly rounded reciprocal (the same value as 1 / x, without the general
@@ -136,15 +138,15 @@ struct TileRange {
     int ne;
     bool curved;
 };
-template <int E>
-__device__ __forceinline__ TileRange tile_range(long long K, long long Kaff) {
-    const long long nAff = (Kaff + E - 1) / E;
+__device__ __forceinline__ TileRange tile_range(long long K, long long Kaff, int E) {
     TileRange t;
-    t.curved = blockIdx.x >= nAff;
-    if (!t.curved) {
+    const long long nAff = (Kaff + E - 1) / E;
+    if ((long long)blockIdx.x < nAff) {
+        t.curved = false;
         t.e0 = (long long)blockIdx.x * E;
         t.ne = (int)min((long long)E, Kaff - t.e0);
     } else {
+        t.curved = true;
         t.e0 = Kaff + (long long)(blockIdx.x - nAff) * E;
         t.ne = (int)min((long long)E, K - t.e0);
     }
@@ -157,7 +159,8 @@ __device__ __forceinline__ TileRange tile_range(long long K, long long Kaff) {
 template <int N, typename Real, bool AV>
 __device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileRange& t, unsigned char* smem_raw) {
     using T = Tile<N, Real>;
-    constexpr int NP = T::NP, NQ = T::NQ, NG = T::NG, NF = T::NF, E = T::E;
+    constexpr int NP = T::NP, NQ = T::NQ, NG = T::NG, NF = T::NF;
+    const int E = T::cap(p.tile_e);   // capacity of this launch's layout
     constexpr OpsLayout L = ops_layout(N);
     Real* sIcubT = reinterpret_cast<Real*>(smem_raw);
     Real* sXrT = sIcubT + NP * NQ;
@@ -359,7 +362,7 @@ __device__ __noinline__ void stage_tile_call(const StageArgs<Real>& p, const Til
 template <int N, typename Real, bool AV>
 __global__ void __launch_bounds__(THREADS) stage_kernel(StageArgs<Real> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const TileRange t = tile_range<Tile<N, Real>::E>(p.K, p.Kaff);
+    const TileRange t = tile_range(p.K, p.Kaff, Tile<N, Real>::cap(p.tile_e));
     if (t.ne <= 0) return;
     stage_tile<N, Real, AV>(p, t, smem_raw);
 }
@@ -472,7 +475,8 @@ template <int N, typename Real>
 __device__ __forceinline__ void grad_tile(const StageArgs<Real>& p, Real* q_out, const TileRange& t,
                                           unsigned char* smem_raw) {
     using T = Tile<N, Real>;
-    constexpr int NP = T::NP, NQ = T::NQ, NG = T::NG, NF = T::NF, E = T::E;
+    constexpr int NP = T::NP, NQ = T::NQ, NG = T::NG, NF = T::NF;
+    const int E = T::cap(p.tile_e);   // capacity of this launch's layout
     constexpr OpsLayout L = ops_layout(N);
     Real* sIcubT = reinterpret_cast<Real*>(smem_raw);   // curved only
     Real* sXrT = sIcubT + NP * NQ;                      // DrT [NQ][NP] or QrT [NP][NP]
@@ -615,7 +619,7 @@ __device__ __forceinline__ void grad_tile(const StageArgs<Real>& p, Real* q_out,
 template <int N, typename Real>
 __global__ void __launch_bounds__(THREADS) grad_kernel(StageArgs<Real> p, Real* q_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const TileRange t = tile_range<Tile<N, Real>::E>(p.K, p.Kaff);
+    const TileRange t = tile_range(p.K, p.Kaff, Tile<N, Real>::cap(p.tile_e));
     if (t.ne <= 0) return;
     grad_tile<N, Real>(p, q_out, t, smem_raw);
 }
@@ -626,36 +630,48 @@ __device__ __noinline__ void grad_tile_call(const StageArgs<Real>& p, Real* q_ou
     grad_tile<N, Real>(p, q_out, t, smem);
 }
 
-// Curved tiles only, after a tensor-core gradient launch over the affine ones.
-template <int N, typename Real>
-__global__ void __launch_bounds__(THREADS) grad_kernel_curved(StageArgs<Real> p, Real* q_out) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int E = Tile<N, Real>::E;
-    TileRange t;
-    t.curved = true;
-    t.e0 = p.Kaff + (long long)blockIdx.x * E;
-    t.ne = (int)min((long long)E, p.K - t.e0);
-    if (t.ne > 0) grad_tile<N, Real>(p, q_out, t, smem_raw);
-}
-
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <int N, typename Real>
-inline unsigned tiles_of(long long K, long long Kaff) {
-    constexpr int E = Tile<N, Real>::E;
+inline unsigned tiles_of(long long K, long long Kaff, int E) {
     return (unsigned)((Kaff + E - 1) / E + (K - Kaff + E - 1) / E);
+}
+
+// largest shared-memory request of one CTA on this architecture
+constexpr size_t SMEM_CTA_MAX = 232448;
+
+// Let a kernel take up to the largest dynamic shared memory it can have next
+// to its static shared memory.
+inline cudaError_t allow_max_dynamic_smem(const void* kern) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(SMEM_CTA_MAX - fa.sharedSizeBytes));
+}
+
+template <int N, typename Real>
+int tile_e_default() {
+    return Tile<N, Real>::E;
+}
+
+template <int N, typename Real>
+bool tile_e_fits(int e, int av) {
+    using T = Tile<N, Real>;
+    return e >= 1 && T::smem_stage(av != 0, e) <= SMEM_CTA_MAX && T::smem_grad(e) <= SMEM_CTA_MAX;
 }
 
 template <int N, typename Real>
 int launch_stage(const StageArgs<Real>& a, int av, cudaStream_t st) {
     using T = Tile<N, Real>;
-    const unsigned grid = tiles_of<N, Real>(a.K, a.Kaff);
+    const int E = T::cap(a.tile_e);
+    if (!tile_e_fits<N, Real>(E, av)) return (int)cudaErrorInvalidValue;
+    const unsigned grid = tiles_of(a.K, a.Kaff, E);
     if (grid == 0) return 0;
     if (av)
-        stage_kernel<N, Real, true><<<grid, THREADS, T::smem_stage(true), st>>>(a);
+        stage_kernel<N, Real, true><<<grid, THREADS, T::smem_stage(true, E), st>>>(a);
     else
-        stage_kernel<N, Real, false><<<grid, THREADS, T::smem_stage(false), st>>>(a);
+        stage_kernel<N, Real, false><<<grid, THREADS, T::smem_stage(false, E), st>>>(a);
     return (int)cudaGetLastError();
 }
 
@@ -671,21 +687,20 @@ int launch_sensor(const StageArgs<Real>& a, Real* eps_out, cudaStream_t st) {
 template <int N, typename Real>
 int launch_grad(const StageArgs<Real>& a, Real* q_out, cudaStream_t st) {
     using T = Tile<N, Real>;
-    const unsigned grid = tiles_of<N, Real>(a.K, a.Kaff);
+    const int E = T::cap(a.tile_e);
+    if (!tile_e_fits<N, Real>(E, 1)) return (int)cudaErrorInvalidValue;
+    const unsigned grid = tiles_of(a.K, a.Kaff, E);
     if (grid == 0) return 0;
-    grad_kernel<N, Real><<<grid, THREADS, T::smem_grad(), st>>>(a, q_out);
+    grad_kernel<N, Real><<<grid, THREADS, T::smem_grad(E), st>>>(a, q_out);
     return (int)cudaGetLastError();
 }
 
+// The limits admit every tile size that tile_e_fits accepts.
 template <int N, typename Real>
 int prepare_kernels() {
-    using T = Tile<N, Real>;
-    cudaError_t e1 = cudaFuncSetAttribute(stage_kernel<N, Real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)T::smem_stage(true));
-    cudaError_t e2 = cudaFuncSetAttribute(stage_kernel<N, Real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)T::smem_stage(false));
-    cudaError_t e3 = cudaFuncSetAttribute(grad_kernel<N, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)T::smem_grad());
+    cudaError_t e1 = allow_max_dynamic_smem((const void*)stage_kernel<N, Real, true>);
+    cudaError_t e2 = allow_max_dynamic_smem((const void*)stage_kernel<N, Real, false>);
+    cudaError_t e3 = allow_max_dynamic_smem((const void*)grad_kernel<N, Real>);
     return (int)(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3);
 }
 

@@ -1,8 +1,8 @@
 // Persistent batched stage kernel: one launch per RK stage walks a work list
 // of (mesh, tile) items over many meshes of any degree 2..6, each tile
-// running the same fused stage body as the single-mesh kernel.  Items are
-// claimed from an atomic counter (reset by a memset node in the captured
-// step graph), largest tiles first.
+// running the same fused stage body as the single-mesh kernel (each mesh at
+// its own tile size).  Items are claimed from an atomic counter (reset by a
+// memset node in the captured step graph), largest tiles first.
 #include "kernels.cuh"
 #include "dg_batch.h"
 
@@ -35,13 +35,15 @@ __global__ void __launch_bounds__(THREADS) batch_stage_kernel(const StageArgs<Re
     }
 }
 
+// Shared memory of a launch: the largest stage layout among the degrees
+// present, each at the tile size its meshes use (e_by_n[N], 0 = absent).
 template <typename Real>
-size_t batch_smem_bytes() {
-    size_t m = Tile<2, Real>::smem_stage(false);
-    m = m > Tile<3, Real>::smem_stage(false) ? m : Tile<3, Real>::smem_stage(false);
-    m = m > Tile<4, Real>::smem_stage(false) ? m : Tile<4, Real>::smem_stage(false);
-    m = m > Tile<5, Real>::smem_stage(false) ? m : Tile<5, Real>::smem_stage(false);
-    m = m > Tile<6, Real>::smem_stage(false) ? m : Tile<6, Real>::smem_stage(false);
+size_t batch_smem_bytes(const int* e_by_n) {
+    size_t m = 0;
+#define DGC_BS(n) \
+    if (e_by_n[n] > 0 && Tile<n, Real>::smem_stage(false, e_by_n[n]) > m) m = Tile<n, Real>::smem_stage(false, e_by_n[n]);
+    DGC_BS(2) DGC_BS(3) DGC_BS(4) DGC_BS(5) DGC_BS(6)
+#undef DGC_BS
     return m;
 }
 
@@ -57,11 +59,9 @@ int batch_tile_e(int N, int rsize) {
 }
 
 template <typename Real>
-int batch_grid(int device, int ctas_per_sm) {
-    const size_t sm = batch_smem_bytes<Real>();
-    if (cudaFuncSetAttribute(batch_stage_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-        cudaSuccess)
-        return -1;
+int batch_grid(int device, int ctas_per_sm, size_t sm) {
+    if (sm + sizeof(int) > SMEM_CTA_MAX) return -1;
+    if (allow_max_dynamic_smem((const void*)batch_stage_kernel<Real>) != cudaSuccess) return -1;
     int occ = 0, nsm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_stage_kernel<Real>, THREADS, sm) != cudaSuccess)
         return -1;
@@ -72,16 +72,17 @@ int batch_grid(int device, int ctas_per_sm) {
 }
 
 template <typename Real>
-int launch_batch_stage(const void* args, const BatchItem* items, int nitems, int* counter, int grid,
+int launch_batch_stage(const void* args, const BatchItem* items, int nitems, int* counter, int grid, size_t sm,
                        cudaStream_t st) {
-    batch_stage_kernel<Real><<<grid, THREADS, batch_smem_bytes<Real>(), st>>>((const StageArgs<Real>*)args, items,
-                                                                              nitems, counter);
+    batch_stage_kernel<Real><<<grid, THREADS, sm, st>>>((const StageArgs<Real>*)args, items, nitems, counter);
     return (int)cudaGetLastError();
 }
 
-template int batch_grid<float>(int, int);
-template int batch_grid<double>(int, int);
-template int launch_batch_stage<float>(const void*, const BatchItem*, int, int*, int, cudaStream_t);
-template int launch_batch_stage<double>(const void*, const BatchItem*, int, int*, int, cudaStream_t);
+template size_t batch_smem_bytes<float>(const int*);
+template size_t batch_smem_bytes<double>(const int*);
+template int batch_grid<float>(int, int, size_t);
+template int batch_grid<double>(int, int, size_t);
+template int launch_batch_stage<float>(const void*, const BatchItem*, int, int*, int, size_t, cudaStream_t);
+template int launch_batch_stage<double>(const void*, const BatchItem*, int, int*, int, size_t, cudaStream_t);
 
 }  // namespace dgc

@@ -14,6 +14,10 @@ template int launch_grad<2, double>(const StageArgs<double>&, double*, cudaStrea
 namespace dgc {
 template int prepare_kernels<2, float>();
 template int prepare_kernels<2, double>();
+template int tile_e_default<2, float>();
+template int tile_e_default<2, double>();
+template bool tile_e_fits<2, float>(int, int);
+template bool tile_e_fits<2, double>(int, int);
 }  // namespace dgc
 namespace dgc {
 template int launch_stage_tc<2>(const StageArgs<float>&, int, int, const unsigned char*, int*, cudaStream_t);

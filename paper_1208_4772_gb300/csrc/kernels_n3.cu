@@ -14,6 +14,10 @@ template int launch_grad<3, double>(const StageArgs<double>&, double*, cudaStrea
 namespace dgc {
 template int prepare_kernels<3, float>();
 template int prepare_kernels<3, double>();
+template int tile_e_default<3, float>();
+template int tile_e_default<3, double>();
+template bool tile_e_fits<3, float>(int, int);
+template bool tile_e_fits<3, double>(int, int);
 }  // namespace dgc
 namespace dgc {
 template int launch_stage_tc<3>(const StageArgs<float>&, int, int, const unsigned char*, int*, cudaStream_t);

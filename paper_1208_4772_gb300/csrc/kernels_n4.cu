@@ -14,6 +14,10 @@ template int launch_grad<4, double>(const StageArgs<double>&, double*, cudaStrea
 namespace dgc {
 template int prepare_kernels<4, float>();
 template int prepare_kernels<4, double>();
+template int tile_e_default<4, float>();
+template int tile_e_default<4, double>();
+template bool tile_e_fits<4, float>(int, int);
+template bool tile_e_fits<4, double>(int, int);
 }  // namespace dgc
 namespace dgc {
 template int launch_stage_tc<4>(const StageArgs<float>&, int, int, const unsigned char*, int*, cudaStream_t);

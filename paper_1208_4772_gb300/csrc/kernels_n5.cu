@@ -14,6 +14,10 @@ template int launch_grad<5, double>(const StageArgs<double>&, double*, cudaStrea
 namespace dgc {
 template int prepare_kernels<5, float>();
 template int prepare_kernels<5, double>();
+template int tile_e_default<5, float>();
+template int tile_e_default<5, double>();
+template bool tile_e_fits<5, float>(int, int);
+template bool tile_e_fits<5, double>(int, int);
 }  // namespace dgc
 namespace dgc {
 template int launch_stage_tc<5>(const StageArgs<float>&, int, int, const unsigned char*, int*, cudaStream_t);

@@ -14,6 +14,10 @@ template int launch_grad<6, double>(const StageArgs<double>&, double*, cudaStrea
 namespace dgc {
 template int prepare_kernels<6, float>();
 template int prepare_kernels<6, double>();
+template int tile_e_default<6, float>();
+template int tile_e_default<6, double>();
+template bool tile_e_fits<6, float>(int, int);
+template bool tile_e_fits<6, double>(int, int);
 }  // namespace dgc
 namespace dgc {
 template int launch_stage_tc<6>(const StageArgs<float>&, int, int, const unsigned char*, int*, cudaStream_t);

@@ -71,3 +71,11 @@ def test_params_struct_layout(B):
     import ctypes
     assert ctypes.sizeof(B.dg_params) == 80
     assert B.dg_params.u_inf.offset == 40 and B.dg_params.prec.offset == 72
+
+
+def test_autotune_argument_errors(B):
+    """The autotuner rejects a missing context or output before touching a GPU."""
+    import ctypes
+    lib = B.load()
+    out = ctypes.c_int32(0)
+    assert lib.dg_autotune(None, 1, 5, ctypes.byref(out), None, None, None) == B.DG_EINVAL
