@@ -363,13 +363,21 @@ struct ProfScope {
 
 template <typename Real>
 int enqueue_stage_t(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
-                    int rhs_only, cudaStream_t st) {
+                    int rhs_only, cudaStream_t st, int stage) {
     StageArgs<Real> s = make_args<Real>(m, Us, Un, out, a, b, dt, rhs_only);
     int e;
     if (m.p.av_on) {
-        {
+        if (fused_sensor(m) && stage >= 0 && !rhs_only) {
+            // eps of this stage's input was written by the previous stage kernel
+            s.eps = (const Real*)m.eps_ring[stage];
+            s.eps_next = (Real*)m.eps_ring[(stage + 1) % 3];
+        } else {
+            // a right-hand-side evaluation on the tensor-core path uses the
+            // ring slot that the next step's first stage rewrites
+            Real* ebuf = (Real*)(fused_sensor(m) ? m.eps_ring[1] : m.eps);
             ProfScope ps(m, st, 0);
-            if ((e = dispatch_sensor<Real>(m.N, s, (Real*)m.eps, st))) return e;
+            if ((e = dispatch_sensor<Real>(m.N, s, ebuf, st))) return e;
+            s.eps = ebuf;
         }
         {
             ProfScope ps(m, st, 1);
@@ -402,18 +410,31 @@ namespace dgc {
 void set_global_error(const std::string& msg) { g_err = msg; }
 
 int enqueue_stage(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
-                  int rhs_only, cudaStream_t st) {
-    if (m.prec == DG_FP64_DEBUG) return enqueue_stage_t<double>(m, Us, Un, out, a, b, dt, rhs_only, st);
-    return enqueue_stage_t<float>(m, Us, Un, out, a, b, dt, rhs_only, st);
+                  int rhs_only, cudaStream_t st, int stage) {
+    if (m.prec == DG_FP64_DEBUG) return enqueue_stage_t<double>(m, Us, Un, out, a, b, dt, rhs_only, st, stage);
+    return enqueue_stage_t<float>(m, Us, Un, out, a, b, dt, rhs_only, st, stage);
+}
+
+// The tensor-core path with AV computes each stage's eps in the previous
+// stage kernel's epilogue (no sensor kernel in the step graph).
+bool fused_sensor(const MeshData& m) { return m.p.av_on && tensor_prec(m.prec); }
+
+int enqueue_sensor(const MeshData& m, const void* U, void* eps_out, cudaStream_t st) {
+    if (m.prec == DG_FP64_DEBUG) {
+        const StageArgs<double> s = make_args<double>(m, U, nullptr, nullptr, 0.0, 0.0, 0.0, 1);
+        return dispatch_sensor<double>(m.N, s, (double*)eps_out, st);
+    }
+    const StageArgs<float> s = make_args<float>(m, U, nullptr, nullptr, 0.0, 0.0, 0.0, 1);
+    return dispatch_sensor<float>(m.N, s, (float*)eps_out, st);
 }
 
 // One SSP-RK3 step: U0 -> U1 -> U2 -> U0 (stage 3 writes U^n in place; each
 // thread reads U^n only for the value it overwrites).
 int enqueue_step(const MeshData& m, double dt, cudaStream_t st) {
     int e;
-    if ((e = enqueue_stage(m, m.U[0], nullptr, m.U[1], 0.0, 1.0, dt, 0, st))) return e;
-    if ((e = enqueue_stage(m, m.U[1], m.U[0], m.U[2], 0.75, 0.25, dt, 0, st))) return e;
-    return enqueue_stage(m, m.U[2], m.U[0], m.U[0], 1.0 / 3.0, 2.0 / 3.0, dt, 0, st);
+    if ((e = enqueue_stage(m, m.U[0], nullptr, m.U[1], 0.0, 1.0, dt, 0, st, 0))) return e;
+    if ((e = enqueue_stage(m, m.U[1], m.U[0], m.U[2], 0.75, 0.25, dt, 0, st, 1))) return e;
+    return enqueue_stage(m, m.U[2], m.U[0], m.U[0], 1.0 / 3.0, 2.0 / 3.0, dt, 0, st, 2);
 }
 
 }  // namespace dgc
@@ -853,7 +874,12 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
     }
     if (p->av_on) {
         // padded to whole tiles of 32: the tensor-core kernels copy eps per tile
-        if ((e = alloc(ctx, *m, &m->eps, (size_t)((K + 31) / 32 * 32) * rs))) { free_mesh(m); return e; }
+        const size_t eb = (size_t)((K + 31) / 32 * 32) * rs;
+        if ((e = alloc(ctx, *m, &m->eps, eb))) { free_mesh(m); return e; }
+        m->eps_ring[0] = m->eps;
+        if (tensor_prec(p->prec))
+            for (int b = 1; b < 3; ++b)
+                if ((e = alloc(ctx, *m, &m->eps_ring[b], eb))) { free_mesh(m); return e; }
         if ((e = alloc(ctx, *m, &m->q, (size_t)K * 8 * NP * rs))) { free_mesh(m); return e; }
     }
     // operators (shared per context, degree and precision)
@@ -904,6 +930,11 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
         free_mesh(m);
         return fail(ctx, DG_ECUDA, "mesh upload copy failed");
     }
+    for (int b = 1; b < 3; ++b)
+        if (m->eps_ring[b] && cudaMemset(m->eps_ring[b], 0, (size_t)((K + 31) / 32 * 32) * rs) != cudaSuccess) {
+            free_mesh(m);
+            return fail(ctx, DG_ECUDA, "mesh upload memset failed");
+        }
     if (p->av_on && (cudaMemset(m->eps, 0, (size_t)((K + 31) / 32 * 32) * rs) != cudaSuccess ||
                      cudaMemset(m->q, 0, (size_t)K * 8 * NP * rs) != cudaSuccess)) {
         free_mesh(m);
@@ -985,6 +1016,7 @@ int dg_set_state(dg_ctx* ctx, dg_mesh h, const double* U) {
     MeshData* m = find(ctx, h);
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
     cudaSetDevice(ctx->device);
+    m->eps_valid = false;
     return put_host(ctx, m, U, m->U[0]);
 }
 
@@ -1002,6 +1034,7 @@ int dg_set_state_device(dg_ctx* ctx, dg_mesh h, const float* U_dev) {
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
     if (m->rsize != 4) return fail(ctx, DG_EINVAL, "device state I/O needs an FP32 precision mode");
     cudaSetDevice(ctx->device);
+    m->eps_valid = false;
     // device row d <- canonical row perm[d]
     int e = launch_permute<float>(U_dev, (float*)m->U[0], m->dperm, m->K, 4 * m->Np, ctx->stream);
     if (e) return fail(ctx, DG_ECUDA, cudaGetErrorString((cudaError_t)e));
@@ -1055,6 +1088,11 @@ int dg_step(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
         m->graph = g;
         CUDA_OK(ctx, cudaGraphInstantiate(&m->gexec, g, 0));
         m->gdt = dt;
+    }
+    if (fused_sensor(*m) && !m->eps_valid) {   // eps(U^n) for the first stage
+        const int e = enqueue_sensor(*m, m->U[0], m->eps_ring[0], ctx->stream);
+        if (e) return fail(ctx, DG_ECUDA, std::string("sensor launch failed: ") + cudaGetErrorString((cudaError_t)e));
+        m->eps_valid = true;
     }
     for (int s = 0; s < nsteps; ++s) CUDA_OK(ctx, cudaGraphLaunch(m->gexec, ctx->stream));
     return DG_OK;

@@ -68,6 +68,7 @@ struct StageArgs {
     const Real* geoC;   // [Kc][curved_stride]
     const Real* ops;    // packed operator table
     const Real* eps;    // [K] viscosity (AV)
+    Real* eps_next;     // AV, tensor-core path: eps of the state this stage writes (null: none)
     const Real* q;      // [K][2][4][NP] sqrt(eps) grad U (AV)
     long long K, Kaff;
     Real gamma;

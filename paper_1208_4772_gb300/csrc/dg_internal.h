@@ -21,7 +21,12 @@ struct MeshData {
     std::vector<long long> perm;  // device element d is caller element perm[d]
     void* U[3] = {nullptr, nullptr, nullptr};  // U^n, stage buffers
     void* rhs = nullptr;          // L(U) scratch
-    void* eps = nullptr;          // [K] viscosity (AV)
+    void* eps = nullptr;          // [K] viscosity (AV); eps_ring[0]
+    // tensor-core path with AV: the stage kernel of stage s reads eps_ring[s]
+    // and writes the sensor of its new state to eps_ring[(s+1) % 3], so that a
+    // step starts and ends with eps_ring[0] = eps(U^n)
+    void* eps_ring[3] = {nullptr, nullptr, nullptr};
+    bool eps_valid = false;       // eps_ring[0] holds eps(U^n)
     void* q = nullptr;            // [K][2][4][Np] (AV)
     void* geoA = nullptr;         // [Kaff][4]
     void* geoC = nullptr;         // [Kc][curved_stride]
@@ -47,7 +52,9 @@ struct MeshData {
 };
 
 int enqueue_stage(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
-                  int rhs_only, cudaStream_t st);
+                  int rhs_only, cudaStream_t st, int stage = -1);
+bool fused_sensor(const MeshData& m);
+int enqueue_sensor(const MeshData& m, const void* U, void* eps_out, cudaStream_t st);
 int enqueue_step(const MeshData& m, double dt, cudaStream_t st);
 
 }  // namespace dgc

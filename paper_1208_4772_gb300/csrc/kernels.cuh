@@ -153,6 +153,67 @@ __device__ __forceinline__ TileRange tile_range(long long K, long long Kaff, int
     return t;
 }
 
+// eps from the two sensor integrals.  s = log10(num/den) is needed only
+// inside the ramp band: outside it two comparisons (in FP64, without a
+// division) decide, which keeps the FP64 transcendentals off the elements
+// where eps is 0 or eps0.
+template <typename Real>
+__device__ __forceinline__ Real sensor_eps(const StageArgs<Real>& p, Real num, Real den) {
+    double eps = 0.0;
+    const double dn = (double)num, dd = (double)den;
+    if (dn > 0.0 && dd > 0.0 && dn >= p.S_lo * dd) {
+        if (dn > p.S_hi * dd) {
+            eps = p.eps0;
+        } else {
+            const double s = log10(dn / dd);
+            if (s > p.s0 + p.kappa)
+                eps = p.eps0;
+            else if (s >= p.s0 - p.kappa)
+                eps = 0.5 * p.eps0 * (1.0 + sin(M_PI * (s - p.s0) / (2.0 * p.kappa)));
+        }
+    }
+    return (Real)eps;
+}
+
+// The sensor of one element of the state being written (the next stage's
+// eps), by one warp: affine elements over the modes u = V^-1 rho, curved
+// ones over the cubature points with J (the same integrals as the sensor
+// kernel).  rho: the element's density row in the new state.
+template <int N, typename Real>
+__device__ __forceinline__ Real element_sensor_warp(const StageArgs<Real>& p, long long k, const Real* rho) {
+    constexpr int NP = np_of(N), NQ = nq_of(N);
+    constexpr int NLOW = N * (N + 1) / 2;
+    constexpr OpsLayout L = ops_layout(N);
+    const int lane = threadIdx.x & 31;
+    Real num = 0, den = 0;
+    if (k < p.Kaff) {
+        for (int m = lane; m < NP; m += 32) {
+            Real um = 0;
+            for (int j = 0; j < NP; ++j) um += p.ops[L.vinvt + j * NP + m] * rho[j];
+            den += um * um;
+            if (m >= NLOW) num += um * um;
+        }
+    } else {
+        const Real* g = p.geoC + (k - p.Kaff) * curved_stride(N);
+        for (int qn = lane; qn < NQ; qn += 32) {
+            Real a = 0, b = 0;
+            for (int j = 0; j < NP; ++j) {
+                a += p.ops[L.icub + j * NQ + qn] * rho[j];
+                b += p.ops[L.itopt + j * NQ + qn] * rho[j];
+            }
+            const Real wj = p.ops[L.w + qn] * g[4 * NQ + qn];
+            den += wj * a * a;
+            num += wj * b * b;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    return sensor_eps(p, num, den);
+}
+
 // ---------------------------------------------------------------------------
 // Stage kernel: L(Us) and the SSP-RK combination (or L alone).
 // ---------------------------------------------------------------------------
@@ -349,6 +410,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileR
             p.Uout[base + it] = p.rhs_only ? Lv : p.a * (p.a != Real(0) ? p.Un[base + it] : Real(0)) + p.b * (sU[it] + p.dt * Lv);
         }
     }
+    if constexpr (AV) {
+        if (p.eps_next != nullptr && !p.rhs_only) {   // eps of the new state, one warp per element
+            __syncthreads();                            // the tile's new state is written
+            for (int e = threadIdx.x >> 5; e < t.ne; e += blockDim.x >> 5) {
+                const Real eps = element_sensor_warp<N, Real>(p, t.e0 + e, p.Uout + (t.e0 + e) * 4 * NP);
+                if ((threadIdx.x & 31) == 0) p.eps_next[t.e0 + e] = eps;
+            }
+        }
+    }
 }
 
 // Out-of-line copies of the CUDA-core tile bodies, called from the
@@ -380,28 +450,6 @@ __global__ void __launch_bounds__(THREADS) stage_kernel(StageArgs<Real> p) {
 // ---------------------------------------------------------------------------
 constexpr int SENSOR_THREADS = 128;
 constexpr int SENSOR_CURVED_PER_BLOCK = SENSOR_THREADS / 32;
-
-// eps from the two sensor integrals.  s = log10(num/den) is needed only
-// inside the ramp band: outside it two comparisons (in FP64, without a
-// division) decide, which keeps the FP64 transcendentals off the elements
-// where eps is 0 or eps0.
-template <typename Real>
-__device__ __forceinline__ Real sensor_eps(const StageArgs<Real>& p, Real num, Real den) {
-    double eps = 0.0;
-    const double dn = (double)num, dd = (double)den;
-    if (dn > 0.0 && dd > 0.0 && dn >= p.S_lo * dd) {
-        if (dn > p.S_hi * dd) {
-            eps = p.eps0;
-        } else {
-            const double s = log10(dn / dd);
-            if (s > p.s0 + p.kappa)
-                eps = p.eps0;
-            else if (s >= p.s0 - p.kappa)
-                eps = 0.5 * p.eps0 * (1.0 + sin(M_PI * (s - p.s0) / (2.0 * p.kappa)));
-        }
-    }
-    return (Real)eps;
-}
 
 template <int N, typename Real>
 __global__ void __launch_bounds__(SENSOR_THREADS) sensor_kernel(StageArgs<Real> p, Real* eps_out, int ncb) {

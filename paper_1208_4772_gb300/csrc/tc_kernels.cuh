@@ -88,7 +88,8 @@ struct TcLayout {
     static constexpr int IGF = B2 + D::NCH * B2_CHUNK;             // I_g fp32 [NF][NP]
     static constexpr int BQ = (IGF + D::NF * D::NP * 4 + 15) / 16 * 16;  // [2 N2 rows][NPK]: Q_r; Q_s
     static constexpr int BQ_BYTES = 2 * D::N2 * D::NPK * 4;
-    static constexpr int TOTAL = BQ + BQ_BYTES;
+    static constexpr int VINV = BQ + BQ_BYTES;                      // V^-1 transposed, fp32 [NP][NP] (sensor)
+    static constexpr int TOTAL = VINV + D::NP * D::NP * 4;
 };
 
 // Shared-memory carve-up of the tensor-core kernel.  Regions whose
@@ -114,7 +115,8 @@ struct TcSmem {
     static constexpr int A1_BYTES = 128 * D::NPK * 4;
     static constexpr int NBV_C = AV ? 8 : 4;                                  // values per face point
     static constexpr int NBV_BYTES = 32 * D::NF * NBV_C * 4;
-    static constexpr int sA1 = al(sIGF + D::NF * D::NP * 4);                  // G1 operands, then neighbour traces
+    static constexpr int sVI = sIGF + D::NF * D::NP * 4;                     // V^-1 transposed (AV: the sensor)
+    static constexpr int sA1 = al(sVI + (AV ? D::NP * D::NP * 4 : 0));         // G1 operands, then neighbour traces
     static constexpr int A1_REGION = al(mx(A1_BYTES * (AV ? 3 : 1), NBV_BYTES));
     static constexpr int A2_BYTES = 128 * 32 * 4;
     static constexpr int NBUF = 2;
@@ -135,7 +137,8 @@ struct TcSmem {
     static constexpr int sTMEM = sBAR + 4 * 8;
     static constexpr int sLIST = sTMEM + 16;                                 // out-of-tile faces: n, then (e,f)
     static constexpr int sFL = sLIST + 100 * 4;                              // faces owned by the tile: n, then (e,f)
-    static constexpr int TOTAL = sFL + 100 * 4;
+    static constexpr int sND = sFL + 100 * 4;                                // [32][2] sensor sums of the new state
+    static constexpr int TOTAL = sND + 64 * 4;
     static_assert(TOTAL <= 232448, "tensor-core tile exceeds the shared-memory limit");
     static_assert(D::CA <= NBUF, "viscous chunks are written at tile start, one per A2 buffer");
     static_assert(NBB >= 32 && (REC * 4) % 16 == 0 && (32 * 4 * D::NP * 4) % 16 == 0, "bulk-copy staging layout");
@@ -319,6 +322,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     unsigned char* A1 = smem + S::sA1;
     int* sList = reinterpret_cast<int*>(smem + S::sLIST);
     int* sFL = reinterpret_cast<int*>(smem + S::sFL);
+    float* sND = reinterpret_cast<float*>(smem + S::sND);
 
     // G2 runs as a sequence of K chunks; chunk number s uses A2 buffer s % 2.
     auto a2_buf = [&](int s) { return smem + S::sA2 + (s & 1) * S::A2_BYTES; };
@@ -790,7 +794,8 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         const float4* us = reinterpret_cast<const float4*>(p.Us + base);
         const float4* un = reinterpret_cast<const float4*>(p.Un + base);
         float4* uo = reinterpret_cast<float4*>(p.Uout + base);
-        const float4* lo = reinterpret_cast<const float4*>(sOut);
+        float4* lo = reinterpret_cast<float4*>(sOut);
+        const bool sense = AV && p.eps_next != nullptr && !p.rhs_only;
         for (int i = tid; i < n4; i += blockDim.x) {
             const float4 L4 = lo[i];
             float4 r;
@@ -809,6 +814,55 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 }
             }
             uo[i] = r;
+            if (sense) lo[i] = r;
+        }
+        if constexpr (AV) {
+            // the next stage's eps: the sensor of the new state, 4 threads per
+            // element over the modes u = V^-1 rho (FP32 sums, FP64 ratio)
+            if (sense) {
+                __syncthreads();
+                {
+                    constexpr int NLOW = N * (N + 1) / 2;
+                    constexpr int MT = (NP + 7) / 8;   // modes per thread, 8 threads per element
+                    const float* sVinvT = reinterpret_cast<const float*>(smem + S::sVI);
+                    const int ee = tid >> 3, sub = tid & 7;
+                    const float* rho = sOut + ee * 4 * NP;
+                    float um[MT];
+#pragma unroll
+                    for (int t = 0; t < MT; ++t) um[t] = 0.f;
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        const float rj = rho[j];
+#pragma unroll
+                        for (int t = 0; t < MT; ++t) {
+                            const int m = sub + 8 * t;
+                            if (m < NP) um[t] += sVinvT[j * NP + m] * rj;
+                        }
+                    }
+                    float num = 0.f, den = 0.f;
+#pragma unroll
+                    for (int t = 0; t < MT; ++t) {
+                        const int m = sub + 8 * t;
+                        if (m < NP) {
+                            den += um[t] * um[t];
+                            if (m >= NLOW) num += um[t] * um[t];
+                        }
+                    }
+#pragma unroll
+                    for (int o = 1; o < 8; o <<= 1) {
+                        num += __shfl_xor_sync(0xffffffffu, num, o);
+                        den += __shfl_xor_sync(0xffffffffu, den, o);
+                    }
+                    if (sub == 0) {
+                        sND[2 * ee] = num;
+                        sND[2 * ee + 1] = den;
+                    }
+                }
+                __syncthreads();
+                // the FP64 ratio, log10 and ramp for the 32 elements by one warp
+                // (one lane per element): GB300's FP64 pipe is narrow
+                if (warp == 7 && lane < ne) p.eps_next[e0 + lane] = sensor_eps(p, sND[2 * lane], sND[2 * lane + 1]);
+            }
         }
         __syncthreads();   // staging and per-element data are reused by the next tile
     }
@@ -830,6 +884,11 @@ __device__ __forceinline__ void load_tc_operators(const unsigned char* ops_tc, u
     const float* igs = reinterpret_cast<const float*>(ops_tc + L::IGF);
     float* igd = reinterpret_cast<float*>(smem + S::sIGF);
     for (int i = tid; i < NF * NP; i += blockDim.x) igd[i] = igs[i];
+    if constexpr (AV) {
+        const float* vs = reinterpret_cast<const float*>(ops_tc + L::VINV);
+        float* vd = reinterpret_cast<float*>(smem + S::sVI);
+        for (int i = tid; i < NP * NP; i += blockDim.x) vd[i] = vs[i];
+    }
 }
 
 // Persistent grid (SMs x resident CTAs).  Each CTA sets up its mbarriers and
@@ -1058,6 +1117,11 @@ std::vector<uint8_t> pack_ops_tc(const RefOps& R, int prec) {
         for (int j = 0; j < NP; ++j) {
             const float f = (float)Ig(fg, j);
             std::memcpy(&out[L::IGF + ((size_t)fg * NP + j) * 4], &f, 4);
+        }
+    for (int j = 0; j < NP; ++j)
+        for (int m = 0; m < NP; ++m) {
+            const float f = (float)R.Vinv[(size_t)m * NP + j];
+            std::memcpy(&out[L::VINV + ((size_t)j * NP + m) * 4], &f, 4);
         }
     pack_operand(out, L::BQ, 2 * D::N2, D::NPK, prec, [&](int r, int j) -> double {
         if (j >= NP) return 0.0;

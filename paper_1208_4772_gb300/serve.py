@@ -73,10 +73,11 @@ def prepare(req, r, s):
     return req
 
 
-def estimate_bytes(K, N, curved=0, prec_bytes=4, av=False):
+def estimate_bytes(K, N, curved=0, prec_bytes=4, av=False, tensor=False):
     """Device bytes dg_mesh_upload allocates for a mesh (without the shared
     operator tables): three state buffers and the right-hand-side scratch,
-    connectivity, geometry, permutation maps, reduction scratch."""
+    connectivity, geometry, permutation maps, reduction scratch; with AV eps
+    (three copies on the tensor-core path) and q."""
     Np = (N + 1) * (N + 2) // 2
     q = (3 * N + 2) // 2
     Nq, Nf = q * q, 3 * q
@@ -87,7 +88,8 @@ def estimate_bytes(K, N, curved=0, prec_bytes=4, av=False):
     b += 2 * K * 8                               # permutation maps
     b += (304 * 8 + 8) * 8 + 32                  # reduction scratch, error word and counters
     if av:
-        b += (K + 31) // 32 * 32 * prec_bytes + K * 8 * Np * prec_bytes   # eps padded to whole tiles
+        b += (3 if tensor else 1) * ((K + 31) // 32 * 32) * prec_bytes    # eps padded to whole tiles
+        b += K * 8 * Np * prec_bytes
     return b
 
 
