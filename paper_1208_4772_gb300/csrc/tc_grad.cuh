@@ -3,9 +3,10 @@
 // tiles of 32 affine elements, products on tcgen05 with FP32 accumulate:
 //   G1: D1 = dU I_g^T (own traces), DQ = dU [Q_r; Q_s]^T with
 //       Q_r = Mref^-1 D_r^T W I_cub (node to node);
-//   GL: DLx = USx (-Mref^-1 Lift)^T, DLy = USy (-Mref^-1 Lift)^T with
-//       USm = n_m sJ ((sqrt(eps) U)* - sqrt(eps) Ubar) at the face points;
-//   q_m = (1/J) (-sqrt(eps) (J r_m Q_r dU + J s_m Q_s dU) - DLm).
+//   GL: D_f = US (-Mref^-1 Lift_f)^T for the three faces f in one product
+//       (the lift table split by face), US = sJ ((sqrt(eps) U)* - sqrt(eps)
+//       Ubar) at the face points, and DL_m = sum_f n_m(f) D_f;
+//   q_m = (1/J) (-sqrt(eps) (J r_m Q_r dU + J s_m Q_s dU) - DL_m).
 // dU is the state minus its element mean; the mean drops out exactly
 // because the discrete gradient of a constant vanishes.  Curved tiles run
 // the CUDA-core body in a second launch.
@@ -24,15 +25,15 @@ struct TgSmem {
     static constexpr int mx(int a, int b) { return a > b ? a : b; }
     static constexpr int sB1Q = 0;                                 // I_g rows
     static constexpr int sBQ = sB1Q + L::B1Q_BYTES;                // Q_r; Q_s rows
-    static constexpr int sB2F = sBQ + L::BQ_BYTES;                 // -Mref^-1 Lift (face chunk)
-    static constexpr int sIGF = sB2F + L::B2_CHUNK;
+    static constexpr int sB2F = sBQ + L::BQ_BYTES;                 // -Mref^-1 Lift split by face
+    static constexpr int sIGF = sB2F + L::B2F3_BYTES;
     static constexpr int A1_BYTES = 128 * D::NPK * 4;
     static constexpr int NBV_C = 5;                                // U+ (4) and sqrt(eps+)
     static constexpr int sA1 = al(sIGF + D::NF * D::NP * 4);       // G1 operand, then neighbour traces
     static constexpr int A1_REGION = al(mx(A1_BYTES, 32 * D::NF * NBV_C * 4));
     static constexpr int A2_BYTES = 128 * 32 * 4;
-    static constexpr int sA2 = sA1 + A1_REGION;                    // USx, USy operands
-    static constexpr int sTR = sA2 + 2 * A2_BYTES;                 // U tile, neighbour records, traces, face terms
+    static constexpr int sA2 = sA1 + A1_REGION;                    // face-term operand
+    static constexpr int sTR = sA2 + A2_BYTES;                     // U tile, neighbour records, traces, face terms
     static constexpr int REC = 4 * D::NP + 4;                      // one element's U record and eps
     static constexpr int TR_BYTES = al(mx(mx(128 * D::NFS * 4, 32 * REC * 4), TileStage<N, false>::FLOATS * 4));
     static constexpr int NBB = TR_BYTES / (REC * 4);               // neighbour records per batch
@@ -47,7 +48,7 @@ struct TgSmem {
     static constexpr int sLIST = sTMEM + 16;                       // out-of-tile faces: n, then (e,f)
     static constexpr int sFL = sLIST + 100 * 4;                    // faces owned by the tile: n, then (e,f)
     static constexpr int TOTAL = sFL + 100 * 4;
-    static constexpr int TMEM_COLS = (D::NFP + 4 * D::N2) <= 128 ? 128 : 256;
+    static constexpr int TMEM_COLS = (D::NFP + 5 * D::N2) <= 128 ? 128 : 256;
     static_assert(TOTAL <= 232448, "gradient tile exceeds the shared-memory limit");
     static_assert(NBB >= 32 && (REC * 4) % 16 == 0, "bulk-copy staging layout");
     static_assert(Tile<N, float>::smem_grad() <= (size_t)sMEAN, "curved tile would clobber the tile state");
@@ -66,7 +67,7 @@ __device__ __forceinline__ bool grad_tile_tc(const StageArgs<float>& p, float* q
     const int half = warp >> 2;
     const int e = row >> 2, v = row & 3;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    const uint32_t tD1 = tmem, tDQ = tmem + NFP, tDLx = tDQ + 2 * N2, tDLy = tDLx + N2;
+    const uint32_t tD1 = tmem, tDQ = tmem + NFP, tDL = tDQ + 2 * N2;   // DL: 3 faces x N2
 
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::sBAR);
     float* sMean = reinterpret_cast<float*>(smem + S::sMEAN);
@@ -88,7 +89,7 @@ __device__ __forceinline__ bool grad_tile_tc(const StageArgs<float>& p, float* q
         tile_info(e0, ne, true, sTr + TS::G, reinterpret_cast<const int4*>(sTr + TS::C), sTr + TS::E, sGeo, sNb, sSe,
                   sList, sFL);
     const bool live = e < ne;
-    if (half == 0) {
+    {   // both halves: the row's mean, then half h writes K values [h NPK/2, (h+1) NPK/2)
         float u[NP];
         float mean = 0.f;
         if (live) {
@@ -104,13 +105,19 @@ __device__ __forceinline__ bool grad_tile_tc(const StageArgs<float>& p, float* q
 #pragma unroll
             for (int j = 0; j < NP; ++j) u[j] = mean;
         }
-        sMean[row] = mean;
+        if (half == 0) sMean[row] = mean;
 #pragma unroll
-        for (int j0 = 0; j0 < NPK; j0 += 8) {
+        for (int j0 = 0; j0 < NPK / 2; j0 += 8) {
             float x[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) x[i] = (j0 + i < NP) ? u[j0 + i] - mean : 0.f;
-            store8<PREC>(A1, row, j0, NPK, x);
+            for (int i = 0; i < 8; ++i) {   // compile-time indices for either half
+                constexpr int H = NPK / 2;
+                const int jl = j0 + i, jh = H + j0 + i;
+                const float lo = (jl < NP) ? u[jl < NP ? jl : 0] - mean : 0.f;
+                const float hi = (jh < NP) ? u[jh < NP ? jh : 0] - mean : 0.f;
+                x[i] = half ? hi : lo;
+            }
+            store8<PREC>(A1, row, half * (NPK / 2) + j0, NPK, x);
         }
     }
     tc::fence_async_smem();
@@ -247,26 +254,25 @@ __device__ __forceinline__ bool grad_tile_tc(const StageArgs<float>& p, float* q
     }
     if (tid == THREADS - 1) *next_tile = claim;   // the claim made at the start of this tile
     __syncthreads();
-    {   // n_x (half 0) or n_y (half 1) times the face terms of the row
-        unsigned char* dst = smem + S::sA2 + half * S::A2_BYTES;
-        const float* ge = sGeo + e * 16 + 5 + half;
+    {   // the face terms of the row, 16 slots per half; the normals enter per
+        // face in the epilogue (the lift table is split by face)
+        unsigned char* dst = smem + S::sA2;
 #pragma unroll
-        for (int s0 = 0; s0 < 32; s0 += 8) {
+        for (int s0 = 0; s0 < 16; s0 += 8) {
             float x[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const int c = s0 + i;
-                x[i] = (c < NF) ? ge[3 * (c / NG)] * sTr[row * NFS + c] : 0.f;
+                const int c = half * 16 + s0 + i;
+                x[i] = (c < NF) ? sTr[row * NFS + c] : 0.f;
             }
-            store8<PREC>(dst, row, s0, 32, x);
+            store8<PREC>(dst, row, half * 16 + s0, 32, x);
         }
     }
     tc::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
         tc::fence_after_sync();
-        issue_mma<PREC>(tDLx, smem + S::sA2, smem + S::sB2F, N2, 32, false);
-        issue_mma<PREC>(tDLy, smem + S::sA2 + S::A2_BYTES, smem + S::sB2F, N2, 32, false);
+        issue_mma<PREC>(tDL, smem + S::sA2, smem + S::sB2F, 3 * N2, 32, false);
         tc::mma_commit(&bars[0]);
     }
     // the next tile's rows into the (now free) trace region
@@ -290,22 +296,27 @@ __device__ __forceinline__ bool grad_tile_tc(const StageArgs<float>& p, float* q
         float* sOut = reinterpret_cast<float*>(smem + S::sIO);   // [e][2][4][NP]
         const float* ge = sGeo + e * 16;
         const float jrx = ge[0], jry = ge[1], jsx = ge[2], jsy = ge[3], invJ = ge[4];
+        const float nx0 = ge[5], ny0 = ge[6], nx1 = ge[8], ny1 = ge[9], nx2 = ge[11], ny2 = ge[12];
         const float se = sSe[e];
         constexpr int per_half = N2 / 2;
 #pragma unroll
         for (int c0 = 0; c0 < per_half; c0 += 8) {
             const int i0 = half * per_half + c0;
-            float qr[8], qs[8], lx[8], ly[8];
+            float qr[8], qs[8], d0[8], d1[8], d2[8];
             tc::tmem_ld8(tDQ + lane_base + i0, qr);
             tc::tmem_ld8(tDQ + N2 + lane_base + i0, qs);
-            tc::tmem_ld8(tDLx + lane_base + i0, lx);
-            tc::tmem_ld8(tDLy + lane_base + i0, ly);
-            tc::tmem_ld_wait(qr, qs, lx, ly);
+            tc::tmem_ld8(tDL + lane_base + i0, d0);
+            tc::tmem_ld8(tDL + N2 + lane_base + i0, d1);
+            tc::tmem_ld_wait(qr, qs, d0, d1);
+            tc::tmem_ld8(tDL + 2 * N2 + lane_base + i0, d2);
+            tc::tmem_ld_wait(d2);
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 if (i0 + i < NP) {
-                    sOut[(e * 8 + v) * NP + i0 + i] = invJ * (-se * (jrx * qr[i] + jsx * qs[i]) - lx[i]);
-                    sOut[(e * 8 + 4 + v) * NP + i0 + i] = invJ * (-se * (jry * qr[i] + jsy * qs[i]) - ly[i]);
+                    const float lx = nx0 * d0[i] + nx1 * d1[i] + nx2 * d2[i];
+                    const float ly = ny0 * d0[i] + ny1 * d1[i] + ny2 * d2[i];
+                    sOut[(e * 8 + v) * NP + i0 + i] = invJ * (-se * (jrx * qr[i] + jsx * qs[i]) - lx);
+                    sOut[(e * 8 + 4 + v) * NP + i0 + i] = invJ * (-se * (jry * qr[i] + jsy * qs[i]) - ly);
                 }
         }
         tc::fence_before_sync();
@@ -329,7 +340,7 @@ __device__ __forceinline__ void load_grad_operators(const unsigned char* ops_tc,
     int4* dst = reinterpret_cast<int4*>(smem);
     for (int i = tid; i < L::B1Q_BYTES / 16; i += blockDim.x) dst[S::sB1Q / 16 + i] = src[L::B1Q / 16 + i];
     for (int i = tid; i < L::BQ_BYTES / 16; i += blockDim.x) dst[S::sBQ / 16 + i] = src[L::BQ / 16 + i];
-    for (int i = tid; i < L::B2_CHUNK / 16; i += blockDim.x) dst[S::sB2F / 16 + i] = src[L::B2 / 16 + i];
+    for (int i = tid; i < L::B2F3_BYTES / 16; i += blockDim.x) dst[S::sB2F / 16 + i] = src[L::B2F3 / 16 + i];
     const float* igs = reinterpret_cast<const float*>(ops_tc + L::IGF);
     float* igd = reinterpret_cast<float*>(smem + S::sIGF);
     for (int i = tid; i < NF * NP; i += blockDim.x) igd[i] = igs[i];

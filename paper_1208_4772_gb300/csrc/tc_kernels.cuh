@@ -89,7 +89,11 @@ struct TcLayout {
     static constexpr int BQ = (IGF + D::NF * D::NP * 4 + 15) / 16 * 16;  // [2 N2 rows][NPK]: Q_r; Q_s
     static constexpr int BQ_BYTES = 2 * D::N2 * D::NPK * 4;
     static constexpr int VINV = BQ + BQ_BYTES;                      // V^-1 transposed, fp32 [NP][NP] (sensor)
-    static constexpr int TOTAL = VINV + D::NP * D::NP * 4;
+    // gradient face terms: -Mref^-1 Lift split by face, [3 N2 rows][32]
+    // (row f N2 + i keeps the columns of face f)
+    static constexpr int B2F3 = (VINV + D::NP * D::NP * 4 + 15) / 16 * 16;
+    static constexpr int B2F3_BYTES = 3 * B2_CHUNK;
+    static constexpr int TOTAL = B2F3 + B2F3_BYTES;
 };
 
 // Shared-memory carve-up of the tensor-core kernel.  Regions whose
@@ -1123,6 +1127,11 @@ std::vector<uint8_t> pack_ops_tc(const RefOps& R, int prec) {
             const float f = (float)R.Vinv[(size_t)m * NP + j];
             std::memcpy(&out[L::VINV + ((size_t)j * NP + m) * 4], &f, 4);
         }
+    pack_operand(out, L::B2F3, 3 * D::N2, 32, prec, [&](int r, int c) -> double {
+        const int f = r / D::N2, i = r - f * D::N2;
+        if (i >= NP || c < f * D::NG || c >= (f + 1) * D::NG) return 0.0;
+        return -R.MLift[(size_t)i * NF + c];
+    });
     pack_operand(out, L::BQ, 2 * D::N2, D::NPK, prec, [&](int r, int j) -> double {
         if (j >= NP) return 0.0;
         if (r < D::N2) return r < NP ? R.Qr[(size_t)r * NP + j] : 0.0;
