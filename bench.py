@@ -56,6 +56,9 @@ WORKLOADS = {
     "batch64": dict(kind="batch", describe="64 meshes, K log-uniform in [2k, 200k], N uniform in {2,3,4,5}, "
                                            "airfoil and cylinder alternating, Mach U[0.3,0.85], AoA U[-2,4] deg, "
                                            "no artificial viscosity; one persistent launch per RK stage"),
+    "prefine": dict(kind="prefine", describe="p-refinement (paper Sec. 5): cylinder channel, 15,360 elements, "
+                                             "Mach 0.38, no AV; degrees 2 -> 3 -> 4 against N = 4 from the "
+                                             "freestream, to the same residual"),
     "serve": dict(kind="serve", describe="continuous batching: Poisson arrivals, K log-uniform in [1k, 500k], "
                                          "N uniform in {2..6}, admission by an HBM budget, retirement at a 1e-6 "
                                          "residual drop or a step cap"),
@@ -75,6 +78,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-meshes", type=int, default=64, help="batch64: number of meshes")
+    ap.add_argument("--prefine-drop", type=float, default=0.1, help="prefine: residual drop of the lower levels")
+    ap.add_argument("--prefine-max-steps", type=int, default=20000, help="prefine: steps of the N = 4 runs")
+    ap.add_argument("--prefine-max-steps-low", type=int, default=5000, help="prefine: steps of the lower levels")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-rate", type=float, default=4.0, help="serve: Poisson arrival rate (1/s)")
     ap.add_argument("--serve-max-steps", type=int, default=2000)
@@ -214,7 +220,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    if WORKLOADS[args.workload]["kind"] in ("batch", "serve"):
+    if WORKLOADS[args.workload]["kind"] in ("batch", "serve", "prefine"):
         print(json.dumps({"impl": "reference", "unavailable": "the oracle arm is timed on the single-mesh "
                                                               "workloads only"}), flush=True)
         return 0
@@ -604,6 +610,50 @@ def run_serve(args):
     return 0
 
 
+def run_prefine(args):
+    """Time to a steady residual: N = 4 from the freestream for
+    --prefine-max-steps steps, against degrees 2 and 3 first (each to a
+    residual drop of --prefine-drop or --prefine-max-steps-low steps), then
+    N = 4 until it reaches the residual the direct run ended with."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1208_4772_gb300 import binding as B, prefine
+    from paper_1208_4772_gb300.inputs import meshes, states
+    B.load()
+    torch.cuda.set_device(0)
+    mesh = meshes.cylinder_channel(n_t=160, n_r=48, seed=1002)
+    ui = states.freestream(0.38, 0.0)
+    ctx = B.dg_create(0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    h, direct = prefine.run_levels(ctx, mesh, [4], ui, prec=args.prec, drop=args.prefine_drop,
+                                   max_steps=args.prefine_max_steps)
+    B.dg_mesh_free(ctx, h)
+    target = direct[-1]["r_last"]
+    h, levels = prefine.run_levels(ctx, mesh, [2, 3, 4], ui, prec=args.prec, drop=args.prefine_drop, target=target,
+                                   max_steps=args.prefine_max_steps, max_steps_low=args.prefine_max_steps_low)
+    B.dg_mesh_free(ctx, h)
+    clk = clocks.stop()
+    B.dg_destroy(ctx)
+    t_direct = sum(l["seconds"] for l in direct)
+    t_pref = sum(l["seconds"] for l in levels)
+    dof = sum(l["dof_updates"] for l in direct + levels)
+    strip = lambda ls: [{k: v for k, v in l.items() if k != "history"} for l in ls]
+    line = {"metric": METRIC, "value": dof / (t_direct + t_pref), "unit": UNIT, "n_gpus": 1, "steps": None,
+            "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.prec], "data": "synthetic",
+            "config": {"workload": "prefine", "describe": WORKLOADS["prefine"]["describe"], "K": int(mesh.K),
+                       "drop_lower_levels": args.prefine_drop, "max_steps_N4": args.prefine_max_steps,
+                       "max_steps_lower_levels": args.prefine_max_steps_low,
+                       "products": args.prec},
+            "prefine": {"direct_N4_s": t_direct, "levels_2_3_4_s": t_pref, "speedup": t_direct / t_pref,
+                        "target_residual": target, "direct": strip(direct), "levels": strip(levels)},
+            "cpu_baseline": None, "e2e": None, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     faulthandler.enable()
     args = parse_args()
@@ -616,6 +666,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "prefine":
+        return run_prefine(args)
     return run_ours(args)
 
 

@@ -160,6 +160,17 @@ int dg_residual(dg_ctx* ctx, dg_mesh m, double out_linf[4], double out_l2[4]);
  * Asynchronous. */
 int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* ms, const double* dts, int nsteps);
 
+/* p-refinement (paper Sec. 5, Table 2: converge at a low degree, then raise
+ * it): sets the state of mesh `to` to the state of mesh `from` embedded
+ * exactly at the higher degree -- the nodal values at to's nodes of from's
+ * degree-N polynomial in every element, i.e. the modal coefficients of
+ * degree <= N carried over and the higher ones zero (the basis is
+ * hierarchical).  `from` and `to` must be two uploads of the same mesh
+ * (same K, connectivity and element order) with N_from <= N_to and the same
+ * state type (FP32 precisions together, or FP64_DEBUG with FP64_DEBUG).
+ * DG_EINVAL otherwise.  Synchronises the context's stream. */
+int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to);
+
 /* Tile-size autotuner for the CUDA-core path (DG_FP32, DG_FP64_DEBUG): times
  * nsteps (1..1000) SSP-RK3 steps of mesh m with dt = 0 (the full work of a
  * step, the state unchanged; it is also saved and restored) for each

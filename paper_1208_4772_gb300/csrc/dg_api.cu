@@ -1141,6 +1141,44 @@ int dg_sync(dg_ctx* ctx, double timeout_s) {
     }
 }
 
+int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to) {
+    if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    MeshData* a = find(ctx, from);
+    MeshData* b = find(ctx, to);
+    if (!a || !b) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    if (a == b || a->K != b->K || a->N > b->N || a->rsize != b->rsize || a->perm != b->perm)
+        return fail(ctx, DG_EINVAL,
+                    "prolongation needs two uploads of one mesh, the target of degree >= the source, one state type");
+    std::vector<double> P;
+    std::string err;
+    if (!build_prolongation(a->N, b->N, P, err)) return fail(ctx, DG_EINVAL, err);
+    cudaSetDevice(ctx->device);
+    void* dP = nullptr;
+    const size_t rs = a->rsize;
+    if (cudaMalloc(&dP, P.size() * rs) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, DG_ENOMEM, "prolongation operator allocation failed");
+    }
+    cudaError_t ce;
+    if (rs == 8) {
+        ce = cudaMemcpy(dP, P.data(), P.size() * 8, cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> Pf(P.begin(), P.end());
+        ce = cudaMemcpy(dP, Pf.data(), Pf.size() * 4, cudaMemcpyHostToDevice);
+    }
+    int e = (int)ce;
+    if (!e)
+        e = rs == 8 ? launch_prolong<double>((const double*)a->U[0], (double*)b->U[0], (const double*)dP, a->K,
+                                             a->Np, b->Np, ctx->stream)
+                    : launch_prolong<float>((const float*)a->U[0], (float*)b->U[0], (const float*)dP, a->K, a->Np,
+                                            b->Np, ctx->stream);
+    if (!e) e = (int)cudaStreamSynchronize(ctx->stream);
+    cudaFree(dP);
+    if (e) return fail(ctx, DG_ECUDA, std::string("prolongation failed: ") + cudaGetErrorString((cudaError_t)e));
+    b->eps_valid = false;
+    return DG_OK;
+}
+
 int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t* cand_out, double* ms_out,
                 int32_t* ncand_out) {
     if (!ctx || !tile_e_out) return fail(ctx, DG_EINVAL, "NULL argument");

@@ -156,6 +156,8 @@ int launch_residual(const Real* L, long long n_per_var_block, long long K, int N
                     double* out8, cudaStream_t st);
 template <typename Real>
 int launch_permute(const Real* src, Real* dst, const long long* map, long long K, int rowlen, cudaStream_t st);
+template <typename Real>
+int launch_prolong(const Real* in, Real* out, const Real* P, long long K, int npf, int npt, cudaStream_t st);
 int residual_blocks();
 
 }  // namespace dgc

@@ -351,4 +351,27 @@ bool build_refops(int N, int q, RefOps& o, std::string& err) {
     return true;
 }
 
+// Prolongation between degrees (paper Sec. 5, p-refinement): the nodal
+// values at the degree-Nt nodes of the degree-Nf interpolant,
+// P = V_f(r_t) V_f^-1 ([Np(Nt)][Np(Nf)]).  The modal basis is hierarchical,
+// so the embedded solution has zero modes of degree above Nf.
+bool build_prolongation(int Nf, int Nt, std::vector<double>& P, std::string& err) {
+    if (Nf < 1 || Nt < Nf) {
+        err = "prolongation needs 1 <= Nf <= Nt";
+        return false;
+    }
+    RefOps from;
+    if (!build_refops(Nf, 0, from, err)) return false;
+    std::vector<double> rt, st;
+    nodes_2d(Nt, rt, st);
+    std::vector<int> I, J;
+    mode_ij(Nf, I, J);
+    const int npf = n_modes(Nf), npt = (int)rt.size();
+    std::vector<double> Vft((size_t)npt * npf);
+    for (int k = 0; k < npt; ++k)
+        for (int m = 0; m < npf; ++m) psi(I[m], J[m], rt[k], st[k], &Vft[(size_t)k * npf + m], nullptr, nullptr);
+    matmul(Vft, from.Vinv, P, npt, npf, npf);
+    return true;
+}
+
 }  // namespace dgc

@@ -34,6 +34,8 @@ struct RefOps {
 int default_q(int N);
 int n_modes(int N);
 bool build_refops(int N, int q, RefOps& out, std::string& err);
+// P = V_f(r_t) V_f^-1 [Np(Nt)][Np(Nf)]: degree-Nf interpolant at the degree-Nt nodes.
+bool build_prolongation(int Nf, int Nt, std::vector<double>& P, std::string& err);
 
 // Dense helpers (row-major), used by the geometry set-up as well.
 bool invert(std::vector<double>& A, int n);            // Gauss-Jordan, partial pivoting

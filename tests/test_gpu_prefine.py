@@ -1,0 +1,69 @@
+"""dg_prolong (paper Sec. 5, p-refinement) against the oracle's
+prolongation: the state of one upload of a mesh embedded into an upload of
+the same mesh at a higher degree.  FP64-debug to 1e-12, FP32 to 1e-6
+(FP32 operator and sums); bad pairs are refused."""
+import numpy as np
+import pytest
+
+import __graft_entry__
+from oracle.prefine import prolong_state
+from paper_1208_4772_gb300.inputs import curving, meshes, states
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    __graft_entry__.build()
+    from paper_1208_4772_gb300 import binding
+    binding.load()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.dg_create(0)
+    yield c
+    B.dg_destroy(c)
+
+
+def upload(B, ctx, mesh, N, prec, ui):
+    r, s = B.dg_reference_nodes(N)
+    xy, _ = curving.curve_mesh(mesh, N, r, s)
+    p = B.make_params(u_inf=ui, prec=prec)
+    return B.dg_mesh_upload(ctx, N, mesh.EToE, mesh.EToF, mesh.bc, xy, p), xy
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-6), ("tf32", 1e-6)])
+@pytest.mark.parametrize("N,M", [(2, 3), (3, 4), (2, 4), (4, 6)])
+def test_prolong_matches_oracle(B, ctx, prec, tol, N, M):
+    mesh = meshes.cylinder_channel(n_t=24, n_r=4, seed=1002)
+    ui = states.freestream(0.38, 0.0)
+    hN, xy = upload(B, ctx, mesh, N, prec, ui)
+    hM, _ = upload(B, ctx, mesh, M, prec, ui)
+    rng = np.random.default_rng(N + M)
+    U = states.uniform_state(mesh.K, xy.shape[1], ui) * (1 + 0.05 * rng.standard_normal((mesh.K, 4, xy.shape[1])))
+    B.dg_set_state(ctx, hN, U)
+    Uin = B.dg_get_state(ctx, hN, mesh.K, xy.shape[1])      # as stored (FP32 rounding included)
+    B.dg_prolong(ctx, hN, hM)
+    Np_M = (M + 1) * (M + 2) // 2
+    got = B.dg_get_state(ctx, hM, mesh.K, Np_M)
+    ref = prolong_state(Uin, N, M)
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    with pytest.raises(B.DgError):
+        B.dg_prolong(ctx, hM, hN)          # to a lower degree
+    B.dg_mesh_free(ctx, hN)
+    B.dg_mesh_free(ctx, hM)
+
+
+def test_prolong_refuses_other_mesh(B, ctx):
+    ui = states.freestream(0.38, 0.0)
+    m1 = meshes.cylinder_channel(n_t=24, n_r=4, seed=1002)
+    m2 = meshes.cylinder_channel(n_t=24, n_r=5, seed=1002)
+    h1, _ = upload(B, ctx, m1, 2, "fp32", ui)
+    h2, _ = upload(B, ctx, m2, 3, "fp32", ui)
+    with pytest.raises(B.DgError) as e:
+        B.dg_prolong(ctx, h1, h2)
+    assert e.value.status == B.DG_EINVAL
+    B.dg_mesh_free(ctx, h1)
+    B.dg_mesh_free(ctx, h2)

@@ -1,0 +1,44 @@
+"""Pins of the p-refinement prolongation (paper Sec. 5): exact on
+polynomials of degree <= N (checked against the polynomial itself, not the
+operator), hierarchical (the embedded field has no modes above degree N
+and the same low modes), and the identity at equal degree."""
+import numpy as np
+import pytest
+
+from oracle import basis, nodes
+from oracle.prefine import prolongation, prolong_state
+
+
+def poly(c, r, s, N):
+    return sum(c[a, b] * r ** a * s ** b for a in range(N + 1) for b in range(N + 1 - a))
+
+
+@pytest.mark.parametrize("N,M", [(2, 3), (2, 4), (3, 4), (4, 5), (5, 6), (2, 6)])
+def test_exact_on_degree_n_polynomials(N, M):
+    rng = np.random.default_rng(N * 10 + M)
+    c = rng.standard_normal((N + 1, N + 1))
+    rN, sN = nodes.warp_blend_nodes(N)
+    rM, sM = nodes.warp_blend_nodes(M)
+    assert np.abs(prolongation(N, M) @ poly(c, rN, sN, N) - poly(c, rM, sM, N)).max() < 1e-12
+
+
+@pytest.mark.parametrize("N,M", [(2, 3), (3, 5), (4, 5), (4, 6)])
+def test_hierarchical_modes(N, M):
+    rng = np.random.default_rng(7)
+    u = rng.standard_normal(basis.n_modes(N))
+    rN, sN = nodes.warp_blend_nodes(N)
+    rM, sM = nodes.warp_blend_nodes(M)
+    uhat_N = np.linalg.solve(basis.vandermonde(N, rN, sN), u)
+    uhat_M = np.linalg.solve(basis.vandermonde(M, rM, sM), prolongation(N, M) @ u)
+    deg = basis.mode_degrees(M)
+    assert np.abs(uhat_M[deg > N]).max() < 1e-12
+    assert np.abs(uhat_M[: basis.n_modes(N)] - uhat_N).max() < 1e-12
+
+
+def test_identity_and_state_shape():
+    for N in (2, 3, 4):
+        assert np.abs(prolongation(N, N) - np.eye(basis.n_modes(N))).max() < 1e-12
+    U = np.random.default_rng(3).standard_normal((5, 4, 6))
+    assert prolong_state(U, 2, 4).shape == (5, 4, 15)
+    with pytest.raises(ValueError):
+        prolongation(4, 3)
