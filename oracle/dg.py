@@ -240,6 +240,23 @@ class Oracle:
         U2 = 0.75 * U + 0.25 * (U1 + dt * self.rhs(U1))
         return U / 3.0 + 2.0 / 3.0 * (U2 + dt * self.rhs(U2))
 
+    # The paper's integrator (Sec. 2): Carpenter and Kennedy's five-stage,
+    # fourth-order Runge-Kutta in 2N storage (NASA TM 109112, 1994, the
+    # (5,4) coefficient set).  For i = 1..5:
+    #     dU <- A_i dU + dt L(U),   U <- U + B_i dU,   with A_1 = 0.
+    LSERK_A = (0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+               -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0)
+    LSERK_B = (1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+               2277821191437.0 / 14882151754819.0)
+
+    def lserk54_step(self, U, dt):
+        dU = np.zeros_like(U)
+        for a, b in zip(self.LSERK_A, self.LSERK_B):
+            dU = a * dU + dt * self.rhs(U)
+            U = U + b * dU
+        return U
+
     def residual(self, U):
         L = self.rhs(U)
         linf = np.max(np.abs(L), axis=(0, 2))

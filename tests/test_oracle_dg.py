@@ -195,6 +195,44 @@ def test_ssp_rk3_stability_polynomial():
     assert np.abs(o.ssp_rk3_step(U, dt) - (1 + z + z * z / 2 + z ** 3 / 6)).max() < 1e-15
 
 
+def test_lserk54_is_fourth_order_on_linear_problems():
+    """One LSERK(5,4) step on u' = lam u multiplies u by a degree-5
+    polynomial R(z), z = lam dt; a fourth-order method has R(z) = 1 + z +
+    z^2/2 + z^3/6 + z^4/24 + c5 z^5.  R is recovered exactly from six values
+    of z and its coefficients compared with those of exp."""
+    m, xy, _ = periodic_case(2, n=3)
+    zs = np.array([0.3, -0.5, 0.8 + 0.2j, -1.1 - 0.4j, 0.6j, -0.2 + 0.9j])   # well inside the stability region
+    vals = []
+    for z in zs:
+        class Linear(Oracle):
+            def rhs(self, U, idx=None, eps=None, q=None, parts=False):
+                return z * U
+        o = Linear(2, m.EToE, m.EToF, m.bc, xy)
+        vals.append(o.lserk54_step(np.ones((m.K, 4, 6), dtype=complex), 1.0)[0, 0, 0])
+    c = np.linalg.solve(np.vander(zs, 6, increasing=True), np.array(vals))
+    assert np.abs(c[:5] - np.array([1, 1, 1 / 2, 1 / 6, 1 / 24])).max() < 1e-12
+    assert abs(c[5] - 1 / 120) > 1e-4          # fourth, not fifth order
+
+
+def test_lserk54_temporal_order_on_the_vortex():
+    """Nonlinear check: the time error of LSERK(5,4) on a vortex mesh
+    (fixed spatial discretisation) falls by ~16 when dt halves."""
+    N = 2
+    m, xy, o = periodic_case(N, n=4)
+    U0 = states.vortex_state(xy, period=(10.0, 10.0))
+    T = 0.4
+
+    def run(nst):
+        U = U0.copy()
+        for _ in range(nst):
+            U = o.lserk54_step(U, T / nst)
+        return U
+    ref = run(64)
+    e1 = np.abs(run(4) - ref).max()
+    e2 = np.abs(run(8) - ref).max()
+    assert np.log2(e1 / e2) >= 3.5, np.log2(e1 / e2)
+
+
 # ------------------------------------------------------------------ sensor
 def test_sensor_closed_forms():
     N = 4
