@@ -144,6 +144,14 @@ int dg_eval_rhs(dg_ctx* ctx, dg_mesh m, double* rhs_out);
  * replayed from a captured CUDA graph).  Asynchronous. */
 int dg_step(dg_ctx* ctx, dg_mesh m, double dt, int nsteps);
 
+/* Advance U^n by nsteps steps of the paper's integrator (Sec. 2): the
+ * five-stage, fourth-order low-storage Runge-Kutta of Carpenter and
+ * Kennedy, dU <- A_i dU + dt L(U), U <- U + B_i dU (i = 1..5), each stage's
+ * combination fused into its right-hand-side kernel; a fixed step replayed
+ * from its own captured CUDA graph.  Same arguments and errors as dg_step.
+ * Asynchronous. */
+int dg_step_lserk(dg_ctx* ctx, dg_mesh m, double dt, int nsteps);
+
 /* Residual norms of L(U^n) per variable, accumulated in FP64 on the device
  * (paper Sec. 5 checks the residual norm): out_linf[v] = max |L|,
  * out_l2[v] = sqrt(sum L^2) over all nodal values.  Returns DG_ENONFINITE

@@ -79,6 +79,7 @@ def load():
         "dg_residual_norms_noalloc": (I, [P, I64, C.c_int32, P, P]),
         "dg_kernel_times": (I, [P, C.c_int32, dp]),
         "dg_prolong": (I, [P, C.c_int32, C.c_int32]),
+        "dg_step_lserk": (I, [P, C.c_int32, D, I]),
         "dg_autotune": (I, [P, C.c_int32, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32), dp,
                             C.POINTER(C.c_int32)]),
         "dg_last_error": (C.c_char_p, [P]),
@@ -205,6 +206,11 @@ def dg_residual_norms_noalloc(values_dev_ptr, K, Np, out8_dev_ptr, stream=None):
 
 def dg_set_profiling(ctx, m, on):
     return _check(load().dg_set_profiling(ctx, m, int(on)), ctx)
+
+
+def dg_step_lserk(ctx, m, dt, nsteps):
+    """nsteps steps of the five-stage fourth-order low-storage RK."""
+    return _check(load().dg_step_lserk(ctx, m, float(dt), int(nsteps)), ctx)
 
 
 def dg_prolong(ctx, m_from, m_to):

@@ -281,8 +281,7 @@ int alloc(dg_ctx* ctx, MeshData& m, void** p, size_t bytes) {
 void free_mesh(MeshData* m) {
     if (!m) return;
     for (cudaEvent_t e : m->prof_ev) cudaEventDestroy(e);
-    if (m->gexec) cudaGraphExecDestroy(m->gexec);
-    if (m->graph) cudaGraphDestroy(m->graph);
+    drop_graphs(*m);
     for (void* p : m->allocs) cudaFree(p);
     delete m;
 }
@@ -363,8 +362,9 @@ struct ProfScope {
 
 template <typename Real>
 int enqueue_stage_t(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
-                    int rhs_only, cudaStream_t st, int stage) {
+                    int rhs_only, cudaStream_t st, int stage, void* dU) {
     StageArgs<Real> s = make_args<Real>(m, Us, Un, out, a, b, dt, rhs_only);
+    s.dU = (Real*)dU;
     int e;
     if (m.p.av_on) {
         if (fused_sensor(m) && stage >= 0 && !rhs_only) {
@@ -410,9 +410,9 @@ namespace dgc {
 void set_global_error(const std::string& msg) { g_err = msg; }
 
 int enqueue_stage(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
-                  int rhs_only, cudaStream_t st, int stage) {
-    if (m.prec == DG_FP64_DEBUG) return enqueue_stage_t<double>(m, Us, Un, out, a, b, dt, rhs_only, st, stage);
-    return enqueue_stage_t<float>(m, Us, Un, out, a, b, dt, rhs_only, st, stage);
+                  int rhs_only, cudaStream_t st, int stage, void* dU) {
+    if (m.prec == DG_FP64_DEBUG) return enqueue_stage_t<double>(m, Us, Un, out, a, b, dt, rhs_only, st, stage, dU);
+    return enqueue_stage_t<float>(m, Us, Un, out, a, b, dt, rhs_only, st, stage, dU);
 }
 
 // The tensor-core path with AV computes each stage's eps in the previous
@@ -435,6 +435,32 @@ int enqueue_step(const MeshData& m, double dt, cudaStream_t st) {
     if ((e = enqueue_stage(m, m.U[0], nullptr, m.U[1], 0.0, 1.0, dt, 0, st, 0))) return e;
     if ((e = enqueue_stage(m, m.U[1], m.U[0], m.U[2], 0.75, 0.25, dt, 0, st, 1))) return e;
     return enqueue_stage(m, m.U[2], m.U[0], m.U[0], 1.0 / 3.0, 2.0 / 3.0, dt, 0, st, 2);
+}
+
+// One step of Carpenter and Kennedy's five-stage fourth-order low-storage
+// RK (the paper's integrator): dU <- A_i dU + dt L(U), U <- U + B_i dU.  Each
+// stage reads one state buffer and writes another (neighbours read a state
+// no tile is writing): U0 -> U1 -> U2 -> U1 -> U2 -> U0; dU lives in the
+// right-hand-side scratch.  The sensor runs as its own kernel every stage.
+int enqueue_step_lserk(const MeshData& m, double dt, cudaStream_t st) {
+    static const double A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                                -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+    static const double Bc[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                                 1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                                 2277821191437.0 / 14882151754819.0};
+    static const int in[5] = {0, 1, 2, 1, 2}, out[5] = {1, 2, 1, 2, 0};
+    for (int i = 0; i < 5; ++i) {
+        const int e = enqueue_stage(m, m.U[in[i]], nullptr, m.U[out[i]], A[i], Bc[i], dt, 0, st, -1, m.rhs);
+        if (e) return e;
+    }
+    return 0;
+}
+
+void drop_graphs(MeshData& m) {
+    if (m.gexec) { cudaGraphExecDestroy(m.gexec); m.gexec = nullptr; }
+    if (m.graph) { cudaGraphDestroy(m.graph); m.graph = nullptr; }
+    if (m.gexec_ls) { cudaGraphExecDestroy(m.gexec_ls); m.gexec_ls = nullptr; }
+    if (m.graph_ls) { cudaGraphDestroy(m.graph_ls); m.graph_ls = nullptr; }
 }
 
 }  // namespace dgc
@@ -1141,6 +1167,34 @@ int dg_sync(dg_ctx* ctx, double timeout_s) {
     }
 }
 
+int dg_step_lserk(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
+    if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    if (nsteps < 0 || !std::isfinite(dt)) return fail(ctx, DG_EINVAL, "bad dt or nsteps");
+    if (nsteps == 0) return DG_OK;
+    cudaSetDevice(ctx->device);
+    if (!m->gexec_ls || m->gdt_ls != dt) {
+        if (m->gexec_ls) { cudaGraphExecDestroy(m->gexec_ls); m->gexec_ls = nullptr; }
+        if (m->graph_ls) { cudaGraphDestroy(m->graph_ls); m->graph_ls = nullptr; }
+        CUDA_OK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        m->prof_capturing = false;
+        const int e = enqueue_step_lserk(*m, dt, ctx->stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+        if (e || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(ctx, DG_ECUDA, "graph capture of the low-storage RK step failed");
+        }
+        m->graph_ls = g;
+        CUDA_OK(ctx, cudaGraphInstantiate(&m->gexec_ls, g, 0));
+        m->gdt_ls = dt;
+    }
+    for (int s = 0; s < nsteps; ++s) CUDA_OK(ctx, cudaGraphLaunch(m->gexec_ls, ctx->stream));
+    m->eps_valid = false;   // the eps rotation of the three-stage step is not maintained here
+    return DG_OK;
+}
+
 int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to) {
     if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
     MeshData* a = find(ctx, from);
@@ -1234,8 +1288,7 @@ int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t
         if (ms[c] < ms[best]) best = c;
     m->tile_e = err ? 0 : cands[best];
     // graphs captured with the old tile size are rebuilt on their next use
-    if (m->gexec) { cudaGraphExecDestroy(m->gexec); m->gexec = nullptr; }
-    if (m->graph) { cudaGraphDestroy(m->graph); m->graph = nullptr; }
+    drop_graphs(*m);
     reset_batch(ctx);
     if (err) return fail(ctx, DG_ECUDA, std::string("autotune step failed: ") + cudaGetErrorString((cudaError_t)err));
     if (ce != cudaSuccess || cs != cudaSuccess) return fail(ctx, DG_ECUDA, "autotune state restore failed");
@@ -1245,8 +1298,7 @@ int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t
         MeshData* o = kv.second;
         if (o == m || tensor_prec(o->prec) || tune_key(o->N, o->rsize, o->p.av_on) != key) continue;
         o->tile_e = m->tile_e;
-        if (o->gexec) { cudaGraphExecDestroy(o->gexec); o->gexec = nullptr; }
-        if (o->graph) { cudaGraphDestroy(o->graph); o->graph = nullptr; }
+        drop_graphs(*o);
     }
     *tile_e_out = m->tile_e;
     if (ncand_out) *ncand_out = (int32_t)cands.size();

@@ -42,6 +42,9 @@ struct MeshData {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     double gdt = 0.0;
+    cudaGraph_t graph_ls = nullptr;       // low-storage RK(5,4) step
+    cudaGraphExec_t gexec_ls = nullptr;
+    double gdt_ls = 0.0;
     // profiling: event pairs around each kernel of one step, with its kind
     bool profiling = false;
     std::vector<cudaEvent_t> prof_ev;
@@ -52,10 +55,12 @@ struct MeshData {
 };
 
 int enqueue_stage(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
-                  int rhs_only, cudaStream_t st, int stage = -1);
+                  int rhs_only, cudaStream_t st, int stage = -1, void* dU = nullptr);
 bool fused_sensor(const MeshData& m);
 int enqueue_sensor(const MeshData& m, const void* U, void* eps_out, cudaStream_t st);
 int enqueue_step(const MeshData& m, double dt, cudaStream_t st);
+int enqueue_step_lserk(const MeshData& m, double dt, cudaStream_t st);
+void drop_graphs(MeshData& m);
 
 }  // namespace dgc
 

@@ -214,6 +214,20 @@ __device__ __forceinline__ Real element_sensor_warp(const StageArgs<Real>& p, lo
     return sensor_eps(p, num, den);
 }
 
+// The stage combination of one value: L alone, the SSP form a Un + b (Us +
+// dt L), or the low-storage form dU <- a dU + dt L, Uout = Us + b dU (a = 0
+// on the first stage, where dU is not read).
+template <typename Real>
+__device__ __forceinline__ Real stage_value(const StageArgs<Real>& p, long long n, Real us, Real L) {
+    if (p.rhs_only) return L;
+    if (p.dU) {
+        const Real d = (p.a != Real(0) ? p.a * p.dU[n] : Real(0)) + p.dt * L;
+        p.dU[n] = d;
+        return us + p.b * d;
+    }
+    return p.a * (p.a != Real(0) ? p.Un[n] : Real(0)) + p.b * (us + p.dt * L);
+}
+
 // ---------------------------------------------------------------------------
 // Stage kernel: L(Us) and the SSP-RK combination (or L alone).
 // ---------------------------------------------------------------------------
@@ -394,7 +408,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileR
         for (int fg = 0; fg < NF; ++fg) acc -= sXLT[fg * NP + i] * fl[fg];
         if (!t.curved) {
             const Real Lv = acc * sGeo[e * 16 + 4];
-            p.Uout[base + it] = p.rhs_only ? Lv : p.a * (p.a != Real(0) ? p.Un[base + it] : Real(0)) + p.b * (sU[it] + p.dt * Lv);
+            p.Uout[base + it] = stage_value(p, base + it, sU[it], Lv);
         } else {
             sR[it] = acc;
         }
@@ -407,7 +421,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileR
             const Real* rr = sR + (e * 4 + v) * NP;
             Real Lv = 0;
             for (int j = 0; j < NP; ++j) Lv += mi[j * NP + i] * rr[j];
-            p.Uout[base + it] = p.rhs_only ? Lv : p.a * (p.a != Real(0) ? p.Un[base + it] : Real(0)) + p.b * (sU[it] + p.dt * Lv);
+            p.Uout[base + it] = stage_value(p, base + it, sU[it], Lv);
         }
     }
     if constexpr (AV) {

@@ -805,6 +805,14 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             float4 r;
             if (p.rhs_only) {
                 r = L4;
+            } else if (p.dU) {   // low-storage RK: dU <- a dU + dt L, U = Us + b dU
+                float4* du = reinterpret_cast<float4*>(p.dU + base);
+                const float4 s4 = us[i];
+                float4 d = p.a != 0.f ? du[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                d = make_float4(p.a * d.x + p.dt * L4.x, p.a * d.y + p.dt * L4.y, p.a * d.z + p.dt * L4.z,
+                                p.a * d.w + p.dt * L4.w);
+                du[i] = d;
+                r = make_float4(s4.x + p.b * d.x, s4.y + p.b * d.y, s4.z + p.b * d.z, s4.w + p.b * d.w);
             } else {
                 const float4 s4 = us[i];
                 r = make_float4(p.b * (s4.x + p.dt * L4.x), p.b * (s4.y + p.dt * L4.y), p.b * (s4.z + p.dt * L4.z),
@@ -1006,7 +1014,8 @@ int launch_stage_tc_t(const StageArgs<float>& a, const unsigned char* ops_tc, in
     const int ctas = TcGrid<N, AV, PREC>::ctas;
     if (ctas <= 0) return (int)cudaErrorNotReady;   // prepare_tc was not called
     // the tile and neighbour records travel by TMA bulk copies: 16-byte aligned
-    if (((uintptr_t)a.Us | (uintptr_t)a.Un | (uintptr_t)a.Uout | (uintptr_t)a.q | (uintptr_t)ops_tc) & 15)
+    if (((uintptr_t)a.Us | (uintptr_t)a.Un | (uintptr_t)a.Uout | (uintptr_t)a.q | (uintptr_t)a.dU | (uintptr_t)ops_tc) &
+        15)
         return (int)cudaErrorMisalignedAddress;
     const unsigned grid = (unsigned)(tiles < ctas ? tiles : ctas);
     return (int)launch_pdl(stage_kernel_tc<N, AV, PREC>, grid, THREADS, tc_smem_bytes<N, AV>(), st, a, ops_tc, err,

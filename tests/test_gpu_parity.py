@@ -289,3 +289,51 @@ def test_autotune_keeps_state_and_results(B, ctx, prec):
     finally:
         B.dg_destroy(c2)
     assert np.array_equal(Ut, Ud)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5), ("tf32", 1e-4), ("bf16x3", 1e-5)])
+def test_lserk_steps_match_oracle(B, ctx, prec, tol):
+    """The paper's integrator, LSERK(5,4), fused into the stage kernels:
+    50 vortex steps against the oracle's LSERK(5,4) (per-variable relative
+    L2, the step tolerances of SSP-RK3)."""
+    N = 3
+    r, s = B.dg_reference_nodes(N)
+    m = meshes.periodic_square(8, length=10.0, jitter=0.1, seed=1000)
+    xy = meshes.straight_nodes(m.verts, r, s)
+    U0 = states.vortex_state(xy, period=(10.0, 10.0))
+    dt = states.time_step(m.verts, U0, N, cfl=0.3)
+    o = Oracle(N, m.EToE, m.EToF, m.bc, xy)
+    Uo = U0.copy()
+    for _ in range(50):
+        Uo = o.lserk54_step(Uo, dt)
+    case = dict(mesh=m, xy=xy, u_inf=states.freestream(0.5), U=U0, av=False, N=N)
+    h = upload(B, ctx, case, prec)
+    B.dg_step_lserk(ctx, h, dt, 50)
+    Ug = B.dg_get_state(ctx, h, m.K, len(r))
+    B.dg_mesh_free(ctx, h)
+    assert np.all(rel_l2_per_var(Ug, Uo) <= tol), rel_l2_per_var(Ug, Uo)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+def test_lserk_with_viscosity_and_curved(B, ctx, prec):
+    """LSERK(5,4) on a curved NACA mesh with artificial viscosity (sensor
+    kernel every stage): 5 steps against the oracle; then an SSP-RK3 step on
+    the same mesh still matches (eps of the new state is recomputed)."""
+    N = 3
+    r, s = B.dg_reference_nodes(N)
+    case = make_case("naca", N, r, s, av=True)
+    m = case["mesh"]
+    dt = 0.2 * states.time_step(m.verts, case["U"], N, eps0=0.3)
+    o = oracle_of(case)
+    U = case["U"].astype(np.float32).astype(np.float64)
+    h = upload(B, ctx, case, prec, U=U)
+    B.dg_step_lserk(ctx, h, dt, 5)
+    B.dg_step(ctx, h, dt, 1)
+    Ug = B.dg_get_state(ctx, h, m.K, len(r))
+    B.dg_mesh_free(ctx, h)
+    Uo = U.copy()
+    for _ in range(5):
+        Uo = o.lserk54_step(Uo, dt)
+    Uo = o.ssp_rk3_step(Uo, dt)
+    tol = 1e-5 if prec == "fp32" else 1e-4
+    assert np.all(rel_l2_per_var(Ug, Uo) <= tol), rel_l2_per_var(Ug, Uo)
