@@ -66,7 +66,7 @@ class Oracle:
     """
 
     def __init__(self, N, EToE, EToF, bc, node_xy, gamma=1.4, u_inf=None,
-                 av=False, kappa=4.0, eps0=0.3, s0=None, q=None):
+                 av=False, kappa=4.0, eps0=0.3, s0=None, q=None, flux="llf"):
         self.ref = ReferenceElement(N, q)
         self.N = N
         self.EToE = np.asarray(EToE, dtype=np.int64)
@@ -75,6 +75,7 @@ class Oracle:
         self.node_xy = np.asarray(node_xy, dtype=np.float64)
         self.K = self.EToE.shape[0]
         self.gamma = float(gamma)
+        self.numflux = {"llf": euler.llf, "hllc": euler.hllc}[flux]
         self.u_inf = None if u_inf is None else np.asarray(u_inf, dtype=np.float64)
         self.av = bool(av)
         self.kappa, self.eps0 = float(kappa), float(eps0)
@@ -215,7 +216,7 @@ class Oracle:
         nx, ny = geo.nx, geo.ny
         bci = self.bc[idx]
         Up = self._exterior(U, idx, Um, lambda T: self._ghost(T, bci, nx, ny))
-        Fs = euler.llf(Um.transpose(0, 2, 1, 3), Up.transpose(0, 2, 1, 3), nx, ny, g)
+        Fs = self.numflux(Um.transpose(0, 2, 1, 3), Up.transpose(0, 2, 1, 3), nx, ny, g)
         Fs = Fs.transpose(0, 2, 1, 3)                          # [n,4,3,Ng]
         if self.av:
             n = len(idx)

@@ -56,6 +56,75 @@ def test_llf_consistency_and_conservation():
     assert np.abs(a + b).max() < 1e-14
 
 
+def _hllc_states(seed, n=9):
+    rng = np.random.default_rng(seed)
+    mk = lambda: states.conserved(rng.uniform(0.5, 2, n), rng.normal(size=n), rng.normal(size=n),
+                                  rng.uniform(0.5, 2, n))
+    th = rng.uniform(0, 2 * np.pi, n)
+    return mk(), mk(), np.cos(th), np.sin(th)
+
+
+def test_hllc_consistency_and_antisymmetry():
+    U1, U2, nx, ny = _hllc_states(3)
+    F, G = euler.flux(U1, GAMMA)
+    assert np.abs(euler.hllc(U1, U1, nx, ny, GAMMA) - (F * nx + G * ny)).max() < 1e-13
+    a = euler.hllc(U1, U2, nx, ny, GAMMA)
+    b = euler.hllc(U2, U1, -nx, -ny, GAMMA)
+    assert np.abs(a + b).max() < 1e-13
+
+
+def test_hllc_resolves_stationary_contact_and_shear():
+    """Two states with the same pressure and zero normal velocity but
+    different densities and tangential velocities: HLLC carries no mass,
+    tangential momentum or energy across (flux (0, p n, 0)); LLF does."""
+    n = 5
+    rng = np.random.default_rng(4)
+    th = rng.uniform(0, 2 * np.pi, n)
+    nx, ny = np.cos(th), np.sin(th)
+    tx, ty = -ny, nx
+    p = rng.uniform(0.5, 2, n)
+    wl, wr = rng.normal(size=n), rng.normal(size=n)
+    UL = states.conserved(rng.uniform(0.5, 2, n), wl * tx, wl * ty, p)
+    UR = states.conserved(rng.uniform(0.5, 2, n), wr * tx, wr * ty, p)
+    fh = euler.hllc(UL, UR, nx, ny, GAMMA)
+    exact = np.stack([np.zeros(n), p * nx, p * ny, np.zeros(n)])
+    assert np.abs(fh - exact).max() < 1e-13
+    assert np.abs(euler.llf(UL, UR, nx, ny, GAMMA)[0]).max() > 1e-3
+
+
+def test_hllc_supersonic_upwinding():
+    """u.n > c on both sides: the flux is F(U-).n; u.n < -c: F(U+).n."""
+    n = 6
+    rng = np.random.default_rng(5)
+    th = rng.uniform(0, 2 * np.pi, n)
+    nx, ny = np.cos(th), np.sin(th)
+    for sgn, pick in ((1.0, 0), (-1.0, 1)):
+        U = [states.conserved(rng.uniform(0.5, 2, n), sgn * 3.0 * nx, sgn * 3.0 * ny, rng.uniform(0.2, 0.5, n))
+             for _ in range(2)]
+        F, G = euler.flux(U[pick], GAMMA)
+        assert np.abs(euler.hllc(U[0], U[1], nx, ny, GAMMA) - (F * nx + G * ny)).max() < 1e-13
+
+
+def test_hllc_wall_and_operator_pins():
+    """No mass or energy through a slip wall; with HLLC in the operator,
+    free stream on a curved mesh and conservation on a periodic one."""
+    U, _, nx, ny = _hllc_states(6)
+    fn = euler.hllc(U, euler.wall_ghost(U, nx, ny), nx, ny, GAMMA)
+    assert np.abs(fn[0]).max() < 1e-13 and np.abs(fn[3]).max() < 1e-13
+    N = 4
+    ref = ReferenceElement(N)
+    m = meshes.naca_omesh(n_t=32, n_r=5)
+    xy, curved = curving.curve_mesh(m, N, ref.r, ref.s)
+    ui = states.freestream(0.8, 1.25)
+    o = Oracle(N, m.EToE, m.EToF, np.where(m.bc != 0, 2, 0), xy, u_inf=ui, flux="hllc")
+    assert _relative(o, states.uniform_state(m.K, o.ref.Np, ui)) < 1e-12
+    m, xy, o = periodic_case(3, flux="hllc")
+    Uv = states.vortex_state(xy, period=(10.0, 10.0))
+    L, vol, surf = o.rhs(Uv, parts=True)
+    total = np.einsum('kij,kvj->v', o.geometry(None).M, L)
+    assert np.all(np.abs(total) < 1e-12 * np.sum(np.abs(surf), axis=(0, 2)))
+
+
 def test_wall_ghost_no_mass_flux():
     rng = np.random.default_rng(1)
     U = states.conserved(rng.uniform(0.5, 2, 9), rng.normal(size=9), rng.normal(size=9), rng.uniform(0.5, 2, 9))
