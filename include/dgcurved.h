@@ -64,7 +64,8 @@ typedef int32_t dg_mesh;        /* mesh handle within one context */
 
 /* Physical and numerical parameters of one mesh (paper Sec. 2 and Sec. 5).
  *   gamma      adiabatic index
- *   flux       0 = local Lax-Friedrichs (Sec. 2 approximate Riemann solver)
+ *   flux       0 = local Lax-Friedrichs (Sec. 2 approximate Riemann solver);
+ *              1 = HLLC (the alternative Sec. 2 names; Davis wave speeds)
  *   av_on      1 = Persson-Peraire artificial viscosity (Sec. 2)
  *   kappa, eps0, s0   sensor ramp parameters; s0 = NaN -> log10(1/N^4)
  *   u_inf      conserved farfield state used by DG_BC_FARFIELD faces

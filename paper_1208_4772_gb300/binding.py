@@ -30,11 +30,14 @@ class dg_params(C.Structure):
                 ("u_inf", C.c_double * 4), ("prec", C.c_int32), ("cub_q", C.c_int32)]
 
 
+FLUX = {"llf": 0, "hllc": 1}
+
+
 def make_params(gamma=1.4, av_on=False, kappa=4.0, eps0=0.3, s0=None, u_inf=(1.0, 0.0, 0.0, 2.5),
-                prec="fp32", cub_q=0):
+                prec="fp32", cub_q=0, flux="llf"):
     p = dg_params()
     p.gamma = gamma
-    p.flux = 0
+    p.flux = FLUX[flux] if isinstance(flux, str) else int(flux)
     p.av_on = int(bool(av_on))
     p.kappa, p.eps0 = kappa, eps0
     p.s0 = math.nan if s0 is None else float(s0)

@@ -340,6 +340,7 @@ StageArgs<Real> make_args(const MeshData& m, const void* Us, const void* Un, voi
     s.S_lo = std::pow(10.0, m.s0 - m.p.kappa);
     s.S_hi = std::pow(10.0, m.s0 + m.p.kappa);
     s.tile_e = tensor_prec(m.prec) ? 0 : m.tile_e;   // the tensor-core path has fixed tiles
+    s.flux = m.p.flux;
     return s;
 }
 
@@ -712,7 +713,7 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
         return fail(ctx, DG_EINVAL, "device path uses cub_q = ceil((3N+1)/2) only");
     if (p->prec != DG_FP32 && p->prec != DG_FP64_DEBUG && p->prec != DG_TF32 && p->prec != DG_BF16X3)
         return fail(ctx, DG_EINVAL, "unknown precision mode");
-    if (p->flux != 0) return fail(ctx, DG_EINVAL, "only the local Lax-Friedrichs flux (0) is built");
+    if (p->flux != 0 && p->flux != 1) return fail(ctx, DG_EINVAL, "flux must be 0 (local Lax-Friedrichs) or 1 (HLLC)");
     if (!(p->gamma > 1.0)) return fail(ctx, DG_EINVAL, "gamma must exceed 1");
     std::string err;
     const RefOps* R = get_refops(N, err);

@@ -62,6 +62,7 @@ struct StageArgs {
     const Real* Un;     // U^n (read when a != 0)
     Real* Uout;         // output
     Real a, b, dt;      // Uout = a Un + b (Us + dt L(Us));  rhs_only: Uout = L(Us)
+    int flux;           // numerical flux: 0 local Lax-Friedrichs, 1 HLLC
     Real* dU;           // low-storage RK register: dU = a dU + dt L(Us), Uout = Us + b dU (null: the form above)
     int rhs_only;
     const int4* conn;   // [K]

@@ -90,6 +90,50 @@ __device__ __forceinline__ void llf_flux(const Real Um[4], const Real Up[4], Rea
     for (int v = 0; v < 4; ++v) Fn[v] = Real(0.5) * (Fm[v] + Fp[v]) - Real(0.5) * lam * (Up[v] - Um[v]);
 }
 
+// F*.n by HLLC (Toro, Spruce and Speares) with Davis wave-speed estimates
+// S_L = min(u_n- - c-, u_n+ - c+), S_R = max(u_n- + c-, u_n+ + c+), the
+// contact speed S_M and the star states of each side; the branch order
+// (S_L >= 0, S_M >= 0, S_R > 0) is the flux's upwinding.
+template <typename Real>
+__device__ __forceinline__ void hllc_flux(const Real Um[4], const Real Up[4], Real nx, Real ny, Real gamma,
+                                          Real Fn[4]) {
+    const Real g1 = gamma - Real(1);
+    const Real irl = recip(Um[0]), irr = recip(Up[0]);
+    const Real ul = Um[1] * irl, vl = Um[2] * irl, ur = Up[1] * irr, vr = Up[2] * irr;
+    const Real unl = ul * nx + vl * ny, unr = ur * nx + vr * ny;
+    const Real pl = g1 * (Um[3] - Real(0.5) * (Um[1] * ul + Um[2] * vl));
+    const Real pr = g1 * (Up[3] - Real(0.5) * (Up[1] * ur + Up[2] * vr));
+    const Real cl = sqrt(gamma * pl * irl), cr = sqrt(gamma * pr * irr);
+    const Real SL = fmin(unl - cl, unr - cr), SR = fmax(unl + cl, unr + cr);
+    const Real SM = (pr - pl + Um[0] * unl * (SL - unl) - Up[0] * unr * (SR - unr)) /
+                    (Um[0] * (SL - unl) - Up[0] * (SR - unr));
+    // the side whose flux (and star state) is used, and its wave speed
+    const bool left = SM >= Real(0);
+    const Real* U = left ? Um : Up;
+    const Real un = left ? unl : unr, u = left ? ul : ur, v = left ? vl : vr, pk = left ? pl : pr;
+    const Real S = left ? SL : SR;
+    Fn[0] = U[0] * un;
+    Fn[1] = U[1] * un + pk * nx;
+    Fn[2] = U[2] * un + pk * ny;
+    Fn[3] = (U[3] + pk) * un;
+    if ((left && SL >= Real(0)) || (!left && SR <= Real(0))) return;   // supersonic: the upwind flux
+    const Real f = U[0] * (S - un) / (S - SM);
+    const Real us[4] = {f, f * (u + (SM - un) * nx), f * (v + (SM - un) * ny),
+                        f * (U[3] / U[0] + (SM - un) * (SM + pk / (U[0] * (S - un))))};
+#pragma unroll
+    for (int w = 0; w < 4; ++w) Fn[w] += S * (us[w] - U[w]);
+}
+
+// The numerical flux selected by p.flux.
+template <typename Real>
+__device__ __forceinline__ void num_flux(int which, const Real Um[4], const Real Up[4], Real nx, Real ny, Real gamma,
+                                         Real Fn[4]) {
+    if (which == 1)
+        hllc_flux(Um, Up, nx, ny, gamma, Fn);
+    else
+        llf_flux(Um, Up, nx, ny, gamma, Fn);
+}
+
 template <typename Real>
 __device__ __forceinline__ void ghost_state(const Real Um[4], int bc, Real nx, Real ny, const Real* uinf,
                                             Real Up[4]) {
@@ -354,7 +398,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileR
             ghost_state(Um, bc, nx, ny, p.uinf, Up);
         }
         Real Fn[4];
-        llf_flux(Um, Up, nx, ny, gamma, Fn);
+        num_flux(p.flux, Um, Up, nx, ny, gamma, Fn);
         if constexpr (AV) {
             const Real se = sEps[e];
             const Real* qe = sQ + e * 8 * NP;

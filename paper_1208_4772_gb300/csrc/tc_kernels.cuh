@@ -624,7 +624,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 for (int w = 0; w < 4; ++w) Up[w] = sNbv[(ee * NF + fg) * S::NBV_C + w];
             }
             float Fn[4];
-            llf_flux(Um, Up, nx, ny, p.gamma, Fn);
+            num_flux(p.flux, Um, Up, nx, ny, p.gamma, Fn);
             if constexpr (AV) {
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
