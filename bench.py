@@ -42,9 +42,9 @@ DTYPE = {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3", "fp64": "f64"}
 
 # DRAM bytes (read + write) of one stage-kernel launch from an ncu capture of
 # the default command (summary in profiles/stage_kernel_tc_naca0012_n4_av.md);
-# keyed by (workload, products) and only valid for the kernel source it was
+# keyed by (workload, products, flux) and only valid for the kernel source it was
 # taken on.
-TRAFFIC = {}
+TRAFFIC = {("naca0012_m0.8_n4_av", "tf32", "llf"): 62.18e6}
 
 WORKLOADS = {
     "naca0012_m0.8_n4_av": dict(kind="naca", N=4, n_t=300, n_r=100, mach=0.8, aoa=1.25, av=True,
@@ -76,6 +76,7 @@ def parse_args():
     ap.add_argument("--compare-prec", default="fp32", help="also time this precision ('' to skip)")
     ap.add_argument("--integrator", default="ssp3", choices=["ssp3", "lserk"],
                     help="SSP-RK3 (3 stages) or the paper's low-storage RK(5,4) (5 stages)")
+    ap.add_argument("--flux", default="llf", choices=["llf", "hllc"], help="numerical flux at the faces")
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -181,7 +182,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_sample(name, budget_s):
+def cpu_sample(name, budget_s, flux="llf"):
     """Time the FP64 oracle on the workload (fresh single-thread process)."""
     import numpy as np
     from oracle.dg import Oracle
@@ -189,7 +190,7 @@ def cpu_sample(name, budget_s):
     ref = ReferenceElement(WORKLOADS[name]["N"])
     wl = make_workload(name, ref.r, ref.s)
     m = wl["mesh"]
-    o = Oracle(wl["N"], m.EToE, m.EToF, m.bc, wl["xy"], u_inf=wl["u_inf"], av=wl["av"])
+    o = Oracle(wl["N"], m.EToE, m.EToF, m.bc, wl["xy"], u_inf=wl["u_inf"], av=wl["av"], flux=flux)
     o.geometry(None)
     U = wl["U0"]
     t0 = time.perf_counter()
@@ -206,11 +207,11 @@ def cpu_sample(name, budget_s):
                       "oracle geometry set-up excluded" % (steps, 3 * steps, m.K)}
 
 
-def run_cpu_baseline(name, budget_s):
+def run_cpu_baseline(name, budget_s, flux="llf"):
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", name,
-                        "--cpu-budget-s", str(budget_s)], capture_output=True, text=True, env=env, timeout=900)
+                        "--cpu-budget-s", str(budget_s), "--flux", flux], capture_output=True, text=True, env=env, timeout=900)
     if r.returncode != 0:
         return {"error": r.stderr[-500:]}
     out = json.loads(r.stdout.strip().splitlines()[-1])
@@ -235,7 +236,7 @@ def run_reference(args):
     ref = ReferenceElement(wl_def["N"])
     wl = make_workload(args.workload, ref.r, ref.s)
     m = wl["mesh"]
-    o = Oracle(wl["N"], m.EToE, m.EToF, m.bc, wl["xy"], u_inf=wl["u_inf"], av=wl["av"])
+    o = Oracle(wl["N"], m.EToE, m.EToF, m.bc, wl["xy"], u_inf=wl["u_inf"], av=wl["av"], flux=args.flux)
     # each step: one SSP-RK3 step (3 RHS evaluations) on a fixed sample of
     # elements, sized so that warm-up + timed steps take about 150 s
     t0 = time.perf_counter()
@@ -280,6 +281,7 @@ def config_of(args, wl):
             "curved_elements": int(wl["curved"].sum()), "artificial_viscosity": bool(wl["av"]),
             "state_precision": "fp32" if args.prec != "fp64" else "fp64", "products": args.prec,
             "time_integrator": "LSERK(5,4)" if getattr(args, "integrator", "ssp3") == "lserk" else "SSP-RK3",
+            "flux": getattr(args, "flux", "llf").upper(),
             "dt": wl["dt"], "dof_per_stage": int(m.K * Np * 4),
             "l2": "flushed before every timed step (%d MiB memset, outside the step events)" % args.flush_mb,
             "parallelism": "replicas (one independent solve per GPU)"}
@@ -343,7 +345,7 @@ def run_ours(args):
     flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device="cuda")
 
     def upload(prec):
-        p = B.make_params(u_inf=wl["u_inf"], av_on=wl["av"], prec=prec)
+        p = B.make_params(u_inf=wl["u_inf"], av_on=wl["av"], prec=prec, flux=args.flux)
         h = B.dg_mesh_upload(ctx, N, m.EToE, m.EToF, m.bc, wl["xy"], p)
         B.dg_set_state(ctx, h, wl["U0"])
         return h
@@ -410,7 +412,7 @@ def run_ours(args):
     achieved = bytes_launch / (stage_launch_ms * 1e-3) / 1e9
     roofline = {"kernel": "stage_kernel (N=%d, AV %s)" % (N, "on" if wl["av"] else "off"), "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_src, "traffic": TRAFFIC.get((args.workload, args.prec)),
+                "peak_source": peak_src, "traffic": TRAFFIC.get((args.workload, args.prec, args.flux)),
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": stage_launch_ms,
                 "dominant_kind_by_time": kinds[dom]}
 
@@ -449,7 +451,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = run_cpu_baseline(args.workload, args.cpu_budget_s)
+        cpu = run_cpu_baseline(args.workload, args.cpu_budget_s, args.flux)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -670,7 +672,7 @@ def main():
     faulthandler.enable()
     args = parse_args()
     if args.cpu_sample:
-        print(json.dumps(cpu_sample(args.cpu_sample, args.cpu_budget_s)))
+        print(json.dumps(cpu_sample(args.cpu_sample, args.cpu_budget_s, args.flux)))
         return 0
     if args.impl == "reference":
         return run_reference(args)
