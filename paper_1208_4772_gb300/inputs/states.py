@@ -80,3 +80,52 @@ def time_step(verts, U, N, cfl=0.3, gamma=1.4, eps0=None):
     if eps0:
         dt = min(dt, 0.5 * cfl * h * h / ((N + 1) ** 4 * eps0))
     return dt
+
+
+# ------------------------------------------------------------------ 3D
+# Five conserved variables (rho, rho u, rho v, rho w, E).  The extruded
+# isentropic vortex (the 2D vortex above with w = 0, independent of z) is an
+# exact solution of the 3D Euler equations.
+
+def conserved3(rho, u, v, w, p, gamma=1.4):
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+    return np.stack([rho, rho * u, rho * v, rho * w, E], axis=-2)
+
+
+def freestream3(mach, aoa_deg=0.0, gamma=1.4):
+    """rho = 1, p = 1/gamma, velocity M (cos a, 0, sin a) (angle in the x-z plane)."""
+    a = np.deg2rad(aoa_deg)
+    u, w = mach * np.cos(a), mach * np.sin(a)
+    p = 1.0 / gamma
+    return np.array([1.0, u, 0.0, w, p / (gamma - 1.0) + 0.5 * (u * u + w * w)])
+
+
+def vortex3_state(node_xyz, t=0.0, **kw):
+    """U [K, 5, Np]: the 2D isentropic vortex in (x, y), w = 0."""
+    U2 = vortex(node_xyz[..., 0], node_xyz[..., 1], t, **kw)
+    out = np.zeros(U2.shape[:-2] + (5,) + U2.shape[-1:])
+    out[..., 0, :], out[..., 1, :], out[..., 2, :], out[..., 4, :] = U2[..., 0, :], U2[..., 1, :], U2[..., 2, :], U2[..., 3, :]
+    return out
+
+
+def uniform_state3(K, Np, u_inf):
+    return np.broadcast_to(np.asarray(u_inf, dtype=np.float64)[None, :, None], (K, 5, Np)).copy()
+
+
+def inradius3(verts):
+    """3 volume / surface area of each tetrahedron [K, 4, 3]."""
+    e1, e2, e3 = verts[:, 1] - verts[:, 0], verts[:, 2] - verts[:, 0], verts[:, 3] - verts[:, 0]
+    vol = np.abs(np.einsum('ki,ki->k', np.cross(e1, e2), e3)) / 6.0
+    area = 0.0
+    for (a, b, c) in ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)):
+        area = area + 0.5 * np.linalg.norm(np.cross(verts[:, b] - verts[:, a], verts[:, c] - verts[:, a]), axis=1)
+    return 3.0 * vol / area
+
+
+def time_step3(verts, U, N, cfl=0.3, gamma=1.4):
+    """dt = CFL h_min / ((N+1)^2 max(|u| + c)) with h the inradius."""
+    rho = U[:, 0]
+    vel2 = (U[:, 1] ** 2 + U[:, 2] ** 2 + U[:, 3] ** 2) / rho ** 2
+    p = (gamma - 1.0) * (U[:, 4] - 0.5 * rho * vel2)
+    smax = float(np.max(np.sqrt(vel2) + np.sqrt(gamma * p / rho)))
+    return cfl * float(np.min(inradius3(verts))) / ((N + 1) ** 2 * smax)
