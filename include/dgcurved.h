@@ -1,9 +1,12 @@
 /*
  * dgcurved.h -- C ABI of libdgcurved.so, a GB300 (sm_103a) implementation of
  * the right-hand side and Runge-Kutta stage update of the curved-element
- * discontinuous Galerkin method for the 2D Euler equations of Siebenborn,
+ * discontinuous Galerkin method for the Euler equations of Siebenborn,
  * Schulz & Schmidt, "A curved-element unstructured discontinuous Galerkin
- * method on GPUs for the Euler equations" (arXiv 1208.4772).
+ * method on GPUs for the Euler equations" (arXiv 1208.4772): on triangles
+ * (2D, four variables; every entry point) and on tetrahedra (the paper's 3D
+ * setting, five variables; dg_tet_mesh_upload and the state, stepping and
+ * residual calls, see "Tetrahedra" below).
  *
  * Conventions (all calls)
  *   - Every function returns an int status: DG_OK (0) or a negative DG_E*
@@ -26,6 +29,24 @@
  *   - Calls that read results back (dg_get_state, dg_eval_rhs, dg_residual)
  *     synchronise the context's stream; dg_step and dg_batch_step only
  *     enqueue work (use dg_sync to wait).
+ *
+ * Tetrahedra (paper Sec. 2 with d = 3)
+ *   - Reference tetrahedron: vertices (-1,-1,-1), (1,-1,-1), (-1,1,-1),
+ *     (-1,-1,1); elements positively oriented (det[v1-v0, v2-v0, v3-v0] >
+ *     0).  Face f has the local vertices (0,2,1), (0,1,3), (1,2,3), (0,3,2)
+ *     for f = 0..3.
+ *   - N_p = (N+1)(N+2)(N+3)/6, 2 <= N <= 4 on the device; state layout
+ *     double U[K][5][N_p], variables (rho, rho u, rho v, rho w, E), nodes in
+ *     the order of dg_tet_reference_nodes.
+ *   - Face integrals use the triangle rule (q^2 points) placed in each
+ *     face's canonical frame, its vertices ordered by global vertex number,
+ *     so both elements of a face evaluate the flux at the same points.
+ *   - dg_set_state, dg_get_state, dg_set_state_device, dg_get_state_device,
+ *     dg_eval_rhs, dg_step, dg_step_lserk, dg_residual, dg_mesh_info,
+ *     dg_mesh_bytes, dg_mesh_free, dg_set_profiling and dg_kernel_times
+ *     accept tetrahedral meshes with the five-variable layout; dg_batch_step,
+ *     dg_prolong and dg_autotune return DG_EINVAL for them.  Precisions
+ *     DG_FP32 and DG_FP64_DEBUG; no artificial viscosity.
  */
 #ifndef DGCURVED_H
 #define DGCURVED_H
@@ -68,7 +89,8 @@ typedef int32_t dg_mesh;        /* mesh handle within one context */
  *              1 = HLLC (the alternative Sec. 2 names; Davis wave speeds)
  *   av_on      1 = Persson-Peraire artificial viscosity (Sec. 2)
  *   kappa, eps0, s0   sensor ramp parameters; s0 = NaN -> log10(1/N^4)
- *   u_inf      conserved farfield state used by DG_BC_FARFIELD faces
+ *   u_inf      conserved farfield state used by DG_BC_FARFIELD faces: the
+ *              first four entries on triangles, all five on tetrahedra
  *   prec       enum dg_prec
  *   cub_q      points per direction of the volume rule and points per edge
  *              of the face rule; 0 -> ceil((3N+1)/2) (exact to degree 3N) */
@@ -77,7 +99,7 @@ typedef struct {
     int32_t flux;
     int32_t av_on;
     double kappa, eps0, s0;
-    double u_inf[4];
+    double u_inf[5];
     int32_t prec;
     int32_t cub_q;
 } dg_params;
@@ -118,6 +140,41 @@ int dg_sizes(int N, int cub_q, int32_t* out4);
 int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int8_t* EToF,
                    const int8_t* bc, const double* node_xy, const dg_params* p, dg_mesh* out);
 
+/* Tetrahedral counterparts of dg_reference_nodes, dg_sizes and
+ * dg_mesh_upload (paper Sec. 2 with d = 3).
+ *
+ * dg_tet_reference_nodes: collocation nodes of degree N (1..6) on the
+ * reference tetrahedron, the warp & blend construction with blending
+ * parameter 0 (each face carries the triangle's nodes, each edge the
+ * Gauss-Lobatto-Legendre points), written as rst_out[N_p][3]; order: the
+ * equidistant lattice index of t outer, of s, of r inner.  Host-only.
+ *
+ * dg_tet_sizes: out4 = {N_p, N_q = q^3, N_g = q^2 (points per face),
+ * N_fp = (N+1)(N+2)/2 (nodes per face)}, q = ceil((3N+1)/2).  Host-only.
+ *
+ * dg_tet_mesh_upload: K tetrahedra of degree N (2..4):
+ *   EToV[K][4]   global vertex numbers (periodic images share a number); the
+ *                library matches faces by their vertex sets and orients the
+ *                face rule by them
+ *   bc[K][4]     enum dg_bc per face; exactly the unmatched faces must be
+ *                DG_BC_WALL or DG_BC_FARFIELD
+ *   node_xyz[K][N_p][3]  collocation-node coordinates (FP64); elements
+ *                whose nodes are not the affine image of their vertex nodes
+ *                are treated as curved (per-point geometric factors and their
+ *                own mass matrix)
+ *   p            parameters (copied); prec DG_FP32 or DG_FP64_DEBUG, av_on 0
+ * The state is set to 0.  Errors: DG_EINVAL (N, K, prec or av_on out of
+ * range, a face shared by more than two elements, bc inconsistent with the
+ * face matching, J <= 0 at a cubature point), DG_ENOMEM, DG_ECUDA. */
+int dg_tet_reference_nodes(int N, double* rst_out);
+int dg_tet_sizes(int N, int32_t* out4);
+int dg_tet_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const int8_t* bc,
+                       const double* node_xyz, const dg_params* p, dg_mesh* out);
+
+/* Shape of mesh m: out6 = {dimension (2 or 3), variables (4 or 5), N, N_p,
+ * K, curved elements}. */
+int dg_mesh_info(dg_ctx* ctx, dg_mesh m, int64_t* out6);
+
 /* Release a mesh and its device memory. */
 int dg_mesh_free(dg_ctx* ctx, dg_mesh m);
 
@@ -125,11 +182,12 @@ int dg_mesh_free(dg_ctx* ctx, dg_mesh m);
 int dg_mesh_bytes(dg_ctx* ctx, dg_mesh m, int64_t* out);
 
 /* Set / read the state U^n from / to host memory, canonical layout
- * double[K][4][N_p].  The device holds it in the precision of p->prec. */
+ * double[K][4][N_p] (tetrahedra: [K][5][N_p]).  The device holds it in the
+ * precision of p->prec. */
 int dg_set_state(dg_ctx* ctx, dg_mesh m, const double* U);
 int dg_get_state(dg_ctx* ctx, dg_mesh m, double* U_out);
 
-/* Device-resident variants: U is a device pointer to float[K][4][N_p] in
+/* Device-resident variants: U is a device pointer to float[K][4][N_p] (tetrahedra [K][5][N_p]) in
  * canonical order (FP32 precision modes only).  Asynchronous on the
  * context's stream.  Errors: DG_EINVAL for DG_FP64_DEBUG meshes. */
 int dg_set_state_device(dg_ctx* ctx, dg_mesh m, const float* U_dev);
@@ -137,7 +195,7 @@ int dg_get_state_device(dg_ctx* ctx, dg_mesh m, float* U_dev_out);
 
 /* Right-hand side L(U^n) of the semi-discrete system (paper Sec. 2, eq.
  * semidiscrete; with the artificial-viscosity terms when av_on) written to
- * rhs_out[K][4][N_p] (host, FP64, canonical layout). */
+ * rhs_out[K][4][N_p] (tetrahedra [K][5][N_p]; host, FP64, canonical layout). */
 int dg_eval_rhs(dg_ctx* ctx, dg_mesh m, double* rhs_out);
 
 /* Advance U^n by nsteps SSP-RK3 steps of size dt (three right-hand-side
@@ -155,9 +213,11 @@ int dg_step_lserk(dg_ctx* ctx, dg_mesh m, double dt, int nsteps);
 
 /* Residual norms of L(U^n) per variable, accumulated in FP64 on the device
  * (paper Sec. 5 checks the residual norm): out_linf[v] = max |L|,
- * out_l2[v] = sqrt(sum L^2) over all nodal values.  Returns DG_ENONFINITE
- * (with the norms still written) if any norm is NaN or Inf. */
-int dg_residual(dg_ctx* ctx, dg_mesh m, double out_linf[4], double out_l2[4]);
+ * out_l2[v] = sqrt(sum L^2) over all nodal values, v over the mesh's 4
+ * (triangles) or 5 (tetrahedra) variables: out_linf and out_l2 hold that
+ * many doubles each.  Returns DG_ENONFINITE (with the norms still written)
+ * if any norm is NaN or Inf. */
+int dg_residual(dg_ctx* ctx, dg_mesh m, double* out_linf, double* out_l2);
 
 /* Advance n meshes (any mix of N and K) by nsteps SSP-RK3 steps each, with
  * per-mesh step sizes dts[n], using one persistent launch per RK stage that

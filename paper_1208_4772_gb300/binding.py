@@ -27,7 +27,7 @@ class DgError(RuntimeError):
 class dg_params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("flux", C.c_int32), ("av_on", C.c_int32),
                 ("kappa", C.c_double), ("eps0", C.c_double), ("s0", C.c_double),
-                ("u_inf", C.c_double * 4), ("prec", C.c_int32), ("cub_q", C.c_int32)]
+                ("u_inf", C.c_double * 5), ("prec", C.c_int32), ("cub_q", C.c_int32)]
 
 
 FLUX = {"llf": 0, "hllc": 1}
@@ -41,7 +41,7 @@ def make_params(gamma=1.4, av_on=False, kappa=4.0, eps0=0.3, s0=None, u_inf=(1.0
     p.av_on = int(bool(av_on))
     p.kappa, p.eps0 = kappa, eps0
     p.s0 = math.nan if s0 is None else float(s0)
-    for i in range(4):
+    for i in range(len(u_inf)):      # four values on triangles, five on tetrahedra
         p.u_inf[i] = float(u_inf[i])
     p.prec = PREC[prec] if isinstance(prec, str) else int(prec)
     p.cub_q = cub_q
@@ -85,6 +85,10 @@ def load():
         "dg_step_lserk": (I, [P, C.c_int32, D, I]),
         "dg_autotune": (I, [P, C.c_int32, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32), dp,
                             C.POINTER(C.c_int32)]),
+        "dg_tet_reference_nodes": (I, [I, dp]),
+        "dg_tet_sizes": (I, [I, C.POINTER(C.c_int32)]),
+        "dg_tet_mesh_upload": (I, [P, I, I64, P, P, dp, C.POINTER(dg_params), C.POINTER(C.c_int32)]),
+        "dg_mesh_info": (I, [P, C.c_int32, C.POINTER(I64)]),
         "dg_last_error": (C.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -141,6 +145,43 @@ def dg_mesh_upload(ctx, N, EToE, EToF, bc, node_xy, params):
     return h.value
 
 
+def dg_mesh_info(ctx, m):
+    out = (C.c_int64 * 6)()
+    _check(load().dg_mesh_info(ctx, m, out), ctx)
+    return dict(zip(("dim", "nvar", "N", "Np", "K", "curved"), (int(v) for v in out)))
+
+
+def _state_shape(ctx, m, K, Np):
+    info = dg_mesh_info(ctx, m)
+    if (K is not None and K != info["K"]) or (Np is not None and Np != info["Np"]):
+        raise ValueError("K / Np do not match the mesh (%d, %d)" % (info["K"], info["Np"]))
+    return (info["K"], info["nvar"], info["Np"])
+
+
+def dg_tet_reference_nodes(N):
+    np_ = (N + 1) * (N + 2) * (N + 3) // 6
+    out = np.zeros((np_, 3))
+    _check(load().dg_tet_reference_nodes(N, _dptr(out)), None)
+    return out[:, 0].copy(), out[:, 1].copy(), out[:, 2].copy()
+
+
+def dg_tet_sizes(N):
+    out = (C.c_int32 * 4)()
+    _check(load().dg_tet_sizes(N, out), None)
+    return tuple(out)
+
+
+def dg_tet_mesh_upload(ctx, N, EToV, bc, node_xyz, params):
+    EToV = np.ascontiguousarray(EToV, dtype=np.int64)
+    bc = np.ascontiguousarray(bc, dtype=np.int8)
+    node_xyz = np.ascontiguousarray(node_xyz, dtype=np.float64)
+    K = EToV.shape[0]
+    h = C.c_int32()
+    _check(load().dg_tet_mesh_upload(ctx, N, K, EToV.ctypes.data, bc.ctypes.data, _dptr(node_xyz),
+                                     C.byref(params), C.byref(h)), ctx)
+    return h.value
+
+
 def dg_mesh_free(ctx, m):
     return _check(load().dg_mesh_free(ctx, m), ctx)
 
@@ -156,8 +197,8 @@ def dg_set_state(ctx, m, U):
     return _check(load().dg_set_state(ctx, m, _dptr(U)), ctx)
 
 
-def dg_get_state(ctx, m, K, Np):
-    out = np.zeros((K, 4, Np))
+def dg_get_state(ctx, m, K=None, Np=None):
+    out = np.zeros(_state_shape(ctx, m, K, Np))
     _check(load().dg_get_state(ctx, m, _dptr(out)), ctx)
     return out
 
@@ -170,8 +211,8 @@ def dg_get_state_device(ctx, m, dev_ptr):
     return _check(load().dg_get_state_device(ctx, m, C.c_void_p(dev_ptr)), ctx)
 
 
-def dg_eval_rhs(ctx, m, K, Np):
-    out = np.zeros((K, 4, Np))
+def dg_eval_rhs(ctx, m, K=None, Np=None):
+    out = np.zeros(_state_shape(ctx, m, K, Np))
     _check(load().dg_eval_rhs(ctx, m, _dptr(out)), ctx)
     return out
 
@@ -181,8 +222,9 @@ def dg_step(ctx, m, dt, nsteps):
 
 
 def dg_residual(ctx, m, allow_nonfinite=False):
-    linf = np.zeros(4)
-    l2 = np.zeros(4)
+    nv = dg_mesh_info(ctx, m)["nvar"]
+    linf = np.zeros(nv)
+    l2 = np.zeros(nv)
     st = load().dg_residual(ctx, m, _dptr(linf), _dptr(l2))
     if not (allow_nonfinite and st == DG_ENONFINITE):
         _check(st, ctx)

@@ -1,0 +1,80 @@
+// Device-side data layout and launch interface of the tetrahedral stage
+// kernel (the method of paper Sec. 2 with d = 3: five conserved variables,
+// triangle faces).
+#pragma once
+#include "dg_device.h"
+
+namespace dgc {
+
+__host__ __device__ constexpr int np3_of(int N) { return (N + 1) * (N + 2) * (N + 3) / 6; }
+__host__ __device__ constexpr int nfp3_of(int N) { return (N + 1) * (N + 2) / 2; }
+__host__ __device__ constexpr int nq3_of(int N) { return q_of(N) * q_of(N) * q_of(N); }
+__host__ __device__ constexpr int ng3_of(int N) { return q_of(N) * q_of(N); }
+
+// Operator table of degree N in the real type (offsets in elements):
+//   Icub [NQ][NP], D_r^T W, D_s^T W, D_t^T W [NP][NQ] each,
+//   I2 [6][NG][NFP] (face nodes -> face-frame points, by orientation),
+//   face weights [NG], M_ref^-1 [NP][NP].
+struct Ops3Layout {
+    int icub, drw, dsw, dtw, i2, wg, mi, total;
+};
+__host__ __device__ constexpr Ops3Layout ops3_layout(int N) {
+    const int NP = np3_of(N), NQ = nq3_of(N), NG = ng3_of(N), NFP = nfp3_of(N);
+    Ops3Layout o{};
+    o.icub = 0;
+    o.drw = o.icub + NQ * NP;
+    o.dsw = o.drw + NP * NQ;
+    o.dtw = o.dsw + NP * NQ;
+    o.i2 = o.dtw + NP * NQ;
+    o.wg = o.i2 + 6 * NG * NFP;
+    o.mi = o.wg + NG;
+    o.total = o.mi + NP * NP;
+    return o;
+}
+// Integer table: fmask [4][NFP] (element node of each face node),
+// fpos [4][NP] (face-local index of each element node, -1 off the face).
+__host__ __device__ constexpr int opsi3_size(int N) { return 4 * nfp3_of(N) + 4 * np3_of(N); }
+
+// Curved-element record (stride curved3_stride):
+//   [(3 d + a) NQ + q]          J dr_a/dx_d at cubature point q (cofactors)
+//   [9 NQ + c 4NG + f NG + g]   c = 0..3: n_x, n_y, n_z, sJ at face-frame point g of face f
+//   [9 NQ + 16 NG + i NP + j]   M_k^-1
+__host__ __device__ constexpr int curved3_stride(int N) {
+    return 9 * nq3_of(N) + 16 * ng3_of(N) + np3_of(N) * np3_of(N);
+}
+
+// Per-element face codes: int2 {faces 0 and 1, faces 2 and 3}, 16 bits per
+// face: neighbour face (2) | bc (2) << 2 | own orientation (3) << 4 |
+// neighbour's orientation (3) << 7.
+__host__ __device__ constexpr int code3_face(int c) { return c & 3; }
+__host__ __device__ constexpr int code3_bc(int c) { return (c >> 2) & 3; }
+__host__ __device__ constexpr int code3_own(int c) { return (c >> 4) & 7; }
+__host__ __device__ constexpr int code3_nbr(int c) { return (c >> 7) & 7; }
+
+template <typename Real>
+struct StageArgs3 {
+    const Real* Us;     // stage input [K][5][NP] (device order)
+    const Real* Un;     // U^n (read when a != 0, SSP form)
+    Real* Uout;
+    Real* dU;           // low-storage register (null: SSP form)
+    Real a, b, dt;      // SSP: Uout = a Un + b (Us + dt L); low-storage: dU = a dU + dt L, Uout = Us + b dU
+    int rhs_only;       // Uout = L(Us)
+    int flux;           // 0 local Lax-Friedrichs, 1 HLLC
+    const int4* conn;   // [K] neighbours of faces 0..3 (own index on boundary faces)
+    const int2* code;   // [K] face codes
+    const Real* geoA;   // [Kaff][9] dx_d/dr_a, row d
+    const Real* geoC;   // [Kc][curved3_stride]
+    const Real* ops;    // ops3_layout
+    const int* opsi;    // fmask, fpos
+    long long K, Kaff;
+    Real gamma;
+    Real uinf[5];
+};
+
+bool supported_degree3(int N);
+int prepare_stage3(int N, int rsize);
+size_t stage3_smem(int N, int rsize);
+int launch_stage3(int N, const StageArgs3<float>& a, cudaStream_t st);
+int launch_stage3(int N, const StageArgs3<double>& a, cudaStream_t st);
+
+}  // namespace dgc

@@ -410,15 +410,23 @@ namespace dgc {
 
 void set_global_error(const std::string& msg) { g_err = msg; }
 
+int api_fail(dg_ctx* ctx, int code, const std::string& msg) { return fail(ctx, code, msg); }
+int api_alloc(dg_ctx* ctx, MeshData& m, void** p, size_t bytes) { return alloc(ctx, m, p, bytes); }
+void api_free_mesh(MeshData* m) { free_mesh(m); }
+
 int enqueue_stage(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
                   int rhs_only, cudaStream_t st, int stage, void* dU) {
+    if (m.dim == 3) {
+        ProfScope ps(m, st, 2);
+        return enqueue_stage3(m, Us, Un, out, a, b, dt, rhs_only, st, dU);
+    }
     if (m.prec == DG_FP64_DEBUG) return enqueue_stage_t<double>(m, Us, Un, out, a, b, dt, rhs_only, st, stage, dU);
     return enqueue_stage_t<float>(m, Us, Un, out, a, b, dt, rhs_only, st, stage, dU);
 }
 
 // The tensor-core path with AV computes each stage's eps in the previous
 // stage kernel's epilogue (no sensor kernel in the step graph).
-bool fused_sensor(const MeshData& m) { return m.p.av_on && tensor_prec(m.prec); }
+bool fused_sensor(const MeshData& m) { return m.dim == 2 && m.p.av_on && tensor_prec(m.prec); }
 
 int enqueue_sensor(const MeshData& m, const void* U, void* eps_out, cudaStream_t st) {
     if (m.prec == DG_FP64_DEBUG) {
@@ -610,6 +618,7 @@ extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* hs, const double
     for (int i = 0; i < n; ++i) {
         ms[i] = find(ctx, hs[i]);
         if (!ms[i]) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle in batch");
+        if (ms[i]->dim != 2) return fail(ctx, DG_EINVAL, "batched path runs triangle meshes only");
         if (ms[i]->p.av_on) return fail(ctx, DG_EINVAL, "batched path runs meshes without artificial viscosity");
         if (ms[i]->prec != ms[0]->prec) return fail(ctx, DG_EINVAL, "batch mixes precision modes");
         if (!std::isfinite(dts[i])) return fail(ctx, DG_EINVAL, "bad dt");
@@ -866,7 +875,7 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
     if ((e = alloc(ctx, *m, &m->geoC, geoC.size() * rs))) { free_mesh(m); return e; }
     if ((e = alloc(ctx, *m, (void**)&m->dperm, (size_t)K * sizeof(long long)))) { free_mesh(m); return e; }
     if ((e = alloc(ctx, *m, (void**)&m->diperm, (size_t)K * sizeof(long long)))) { free_mesh(m); return e; }
-    if ((e = alloc(ctx, *m, (void**)&m->red, (size_t)(residual_blocks() * 8 + 8) * sizeof(double)))) {
+    if ((e = alloc(ctx, *m, (void**)&m->red, (size_t)(residual_blocks() * 10 + 10) * sizeof(double)))) {
         free_mesh(m);
         return e;
     }
@@ -999,7 +1008,7 @@ int dg_mesh_bytes(dg_ctx* ctx, dg_mesh h, int64_t* out) {
 
 // host FP64 canonical <-> device order in the mesh precision
 static int put_host(dg_ctx* ctx, MeshData* m, const double* U, void* dst) {
-    const size_t row = 4 * (size_t)m->Np, n = (size_t)m->K * row;
+    const size_t row = (size_t)m->nvar * m->Np, n = (size_t)m->K * row;
     cudaError_t ce;
     if (m->rsize == 8) {
         std::vector<double> buf(n);
@@ -1018,7 +1027,7 @@ static int put_host(dg_ctx* ctx, MeshData* m, const double* U, void* dst) {
 }
 
 static int get_host(dg_ctx* ctx, MeshData* m, const void* src, double* U) {
-    const size_t row = 4 * (size_t)m->Np, n = (size_t)m->K * row;
+    const size_t row = (size_t)m->nvar * m->Np, n = (size_t)m->K * row;
     cudaError_t ce;
     if (m->rsize == 8) {
         std::vector<double> buf(n);
@@ -1063,7 +1072,7 @@ int dg_set_state_device(dg_ctx* ctx, dg_mesh h, const float* U_dev) {
     cudaSetDevice(ctx->device);
     m->eps_valid = false;
     // device row d <- canonical row perm[d]
-    int e = launch_permute<float>(U_dev, (float*)m->U[0], m->dperm, m->K, 4 * m->Np, ctx->stream);
+    int e = launch_permute<float>(U_dev, (float*)m->U[0], m->dperm, m->K, m->nvar * m->Np, ctx->stream);
     if (e) return fail(ctx, DG_ECUDA, cudaGetErrorString((cudaError_t)e));
     return DG_OK;
 }
@@ -1075,7 +1084,7 @@ int dg_get_state_device(dg_ctx* ctx, dg_mesh h, float* U_dev_out) {
     if (m->rsize != 4) return fail(ctx, DG_EINVAL, "device state I/O needs an FP32 precision mode");
     cudaSetDevice(ctx->device);
     // canonical row k <- device row iperm[k]
-    int e = launch_permute<float>((const float*)m->U[0], U_dev_out, m->diperm, m->K, 4 * m->Np, ctx->stream);
+    int e = launch_permute<float>((const float*)m->U[0], U_dev_out, m->diperm, m->K, m->nvar * m->Np, ctx->stream);
     if (e) return fail(ctx, DG_ECUDA, cudaGetErrorString((cudaError_t)e));
     return DG_OK;
 }
@@ -1125,27 +1134,28 @@ int dg_step(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
     return DG_OK;
 }
 
-int dg_residual(dg_ctx* ctx, dg_mesh h, double out_linf[4], double out_l2[4]) {
+int dg_residual(dg_ctx* ctx, dg_mesh h, double* out_linf, double* out_l2) {
     if (!ctx || !out_linf || !out_l2) return fail(ctx, DG_EINVAL, "NULL argument");
     MeshData* m = find(ctx, h);
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
     cudaSetDevice(ctx->device);
     int e = enqueue_stage(*m, m->U[0], nullptr, m->rhs, 0.0, 0.0, 0.0, 1, ctx->stream);
     if (e) return fail(ctx, DG_ECUDA, "stage launch failed");
-    double* out8 = m->red + residual_blocks() * 8;
+    const int nv = m->nvar;
+    double* out = m->red + residual_blocks() * 10;
     if (m->rsize == 8)
-        e = launch_residual<double>((const double*)m->rhs, 0, m->K, m->Np, m->red, out8, ctx->stream);
+        e = launch_residual<double>((const double*)m->rhs, nv, m->K, m->Np, m->red, out, ctx->stream);
     else
-        e = launch_residual<float>((const float*)m->rhs, 0, m->K, m->Np, m->red, out8, ctx->stream);
+        e = launch_residual<float>((const float*)m->rhs, nv, m->K, m->Np, m->red, out, ctx->stream);
     if (e) return fail(ctx, DG_ECUDA, "residual launch failed");
-    double h8[8];
-    CUDA_OK(ctx, cudaMemcpyAsync(h8, out8, sizeof(h8), cudaMemcpyDeviceToHost, ctx->stream));
+    double hv[10];
+    CUDA_OK(ctx, cudaMemcpyAsync(hv, out, 2 * nv * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
     bool finite = true;
-    for (int v = 0; v < 4; ++v) {
-        out_linf[v] = h8[v];
-        out_l2[v] = h8[4 + v];
-        finite = finite && std::isfinite(h8[v]) && std::isfinite(h8[4 + v]);
+    for (int v = 0; v < nv; ++v) {
+        out_linf[v] = hv[v];
+        out_l2[v] = hv[nv + v];
+        finite = finite && std::isfinite(hv[v]) && std::isfinite(hv[nv + v]);
     }
     return finite ? DG_OK : fail(ctx, DG_ENONFINITE, "non-finite residual norm");
 }
@@ -1201,6 +1211,7 @@ int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to) {
     MeshData* a = find(ctx, from);
     MeshData* b = find(ctx, to);
     if (!a || !b) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    if (a->dim != 2 || b->dim != 2) return fail(ctx, DG_EINVAL, "prolongation is built for triangle meshes");
     if (a == b || a->K != b->K || a->N > b->N || a->rsize != b->rsize || a->perm != b->perm)
         return fail(ctx, DG_EINVAL,
                     "prolongation needs two uploads of one mesh, the target of degree >= the source, one state type");
@@ -1241,6 +1252,7 @@ int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
     if (nsteps < 1 || nsteps > 1000) return fail(ctx, DG_EINVAL, "nsteps must be in 1..1000");
     if (ncand_out) *ncand_out = 0;
+    if (m->dim == 3) return fail(ctx, DG_EINVAL, "the tile autotuner covers the triangle path");
     if (tensor_prec(m->prec)) {   // fixed tiles of 32 elements = the 128 rows of the products
         *tile_e_out = 32;
         return DG_OK;

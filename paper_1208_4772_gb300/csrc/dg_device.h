@@ -154,8 +154,8 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned threads, 
 
 // Generic kernels (kernels_common.cu)
 template <typename Real>
-int launch_residual(const Real* L, long long n_per_var_block, long long K, int NP, double* partial,
-                    double* out8, cudaStream_t st);
+int launch_residual(const Real* L, int nvar, long long K, int NP, double* partial, double* out,
+                    cudaStream_t st);   // out: nvar max-norms, then nvar Euclidean norms
 template <typename Real>
 int launch_permute(const Real* src, Real* dst, const long long* map, long long K, int rowlen, cudaStream_t st);
 template <typename Real>

@@ -11,7 +11,12 @@
 namespace dgc {
 
 struct MeshData {
+    int dim = 2;                  // 2: triangles, 4 variables; 3: tetrahedra, 5 variables
+    int nvar = 4;
     int N = 0, Np = 0, Nq = 0, Ng = 0, Nf = 0;
+    int Nfp = 0;                  // tetrahedra: nodes per face
+    int2* code3 = nullptr;        // tetrahedra: face codes [K]
+    const int* opsi3 = nullptr;   // tetrahedra: fmask / fpos table (owned by the context)
     long long K = 0, Kaff = 0, Kc = 0;
     dg_params p{};
     int prec = 0;
@@ -56,6 +61,12 @@ struct MeshData {
 
 int enqueue_stage(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
                   int rhs_only, cudaStream_t st, int stage = -1, void* dU = nullptr);
+int enqueue_stage3(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
+                   int rhs_only, cudaStream_t st, void* dU);
+// helpers of the C ABI shared by dg_api.cu and dg3_api.cu
+int api_fail(dg_ctx* ctx, int code, const std::string& msg);
+int api_alloc(dg_ctx* ctx, MeshData& m, void** p, size_t bytes);
+void api_free_mesh(MeshData* m);
 bool fused_sensor(const MeshData& m);
 int enqueue_sensor(const MeshData& m, const void* U, void* eps_out, cudaStream_t st);
 int enqueue_step(const MeshData& m, double dt, cudaStream_t st);

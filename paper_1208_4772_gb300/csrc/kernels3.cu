@@ -1,0 +1,390 @@
+// Stage kernel of the tetrahedral method (paper Sec. 2 with d = 3) on the
+// CUDA cores: L(U) and the Runge-Kutta stage combination for a tile of E
+// elements per CTA pass, persistent over tiles.
+//
+// Per tile (all in shared memory):
+//   0  state rows, face codes, affine geometry (cofactors of dx/dr, 1/J);
+//      the neighbours' face-node values (gathered through fmask)
+//   1  per cubature point: U^cub = I_cub U, the Euler fluxes and the
+//      contravariant fluxes sum_d (J dr_a/dx_d) F_d, a = r, s, t
+//   2  vol = D_r^T W Fr + D_s^T W Fs + D_t^T W Ft
+//   3  per face-frame point: U- and U+ from the face nodes by I2 of the
+//      face's orientation (the neighbour's with its own orientation), ghost
+//      states on boundary faces, outward normal and area factor, the
+//      numerical flux times w_g sJ
+//   4  R = vol - sum_f I2_f^T (w sJ F*) scattered to the face nodes
+//   5  L = M_k^-1 R (affine: M_ref^-1 / J) and the stage update
+#include <algorithm>
+
+#include "dg3_device.h"
+
+namespace dgc {
+
+namespace {
+
+template <int N, typename Real>
+struct T3 {
+    static constexpr int NP = np3_of(N), NFP = nfp3_of(N), NQ = nq3_of(N), NG = ng3_of(N);
+    static constexpr int E = sizeof(Real) == 4 ? (N <= 2 ? 16 : N == 3 ? 8 : 3) : (N <= 2 ? 8 : N == 3 ? 4 : 1);
+    static constexpr int O_I2 = 0;
+    static constexpr int O_W = O_I2 + 6 * NG * NFP;
+    static constexpr int O_MI = O_W + NG;
+    static constexpr int O_U = (O_MI + NP * NP + 3) / 4 * 4;
+    static constexpr int O_F = O_U + E * 5 * NP;
+    static constexpr int O_NB = O_F + E * 15 * NQ;
+    static constexpr int O_FS = O_NB + E * 20 * NFP;
+    static constexpr int O_R = O_FS + E * 20 * NG;
+    static constexpr int O_G = O_R + E * 5 * NP;
+    static constexpr int O_END = O_G + E * 16;
+    static constexpr int NINT = 4 * NFP + 4 * NP + 8 * E;
+    static constexpr size_t BYTES = (size_t)O_END * sizeof(Real) + (size_t)NINT * sizeof(int);
+};
+
+// outward reference face vectors (t_u x t_v of each face's parametrisation)
+__device__ __constant__ float kFaceRef[4][3] = {{0, 0, -1}, {0, -1, 0}, {1, 1, 1}, {-1, 0, 0}};
+
+template <typename Real>
+__device__ __forceinline__ void normal_flux3(const Real* u, Real nx, Real ny, Real nz, Real gamma, Real* fn,
+                                             Real& un, Real& c) {
+    const Real ir = Real(1) / u[0];
+    un = (u[1] * nx + u[2] * ny + u[3] * nz) * ir;
+    const Real p = (gamma - Real(1)) * (u[4] - Real(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * ir);
+    c = sqrt(gamma * p * ir);
+    fn[0] = u[0] * un;
+    fn[1] = u[1] * un + p * nx;
+    fn[2] = u[2] * un + p * ny;
+    fn[3] = u[3] * un + p * nz;
+    fn[4] = (u[4] + p) * un;
+}
+
+template <typename Real>
+__device__ __forceinline__ void llf3(const Real* um, const Real* up, Real nx, Real ny, Real nz, Real gamma,
+                                     Real* F) {
+    Real fm[5], fp[5], unm, cm, unp, cp;
+    normal_flux3(um, nx, ny, nz, gamma, fm, unm, cm);
+    normal_flux3(up, nx, ny, nz, gamma, fp, unp, cp);
+    const Real lam = fmax(fabs(unm) + cm, fabs(unp) + cp);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[v] = Real(0.5) * (fm[v] + fp[v]) - Real(0.5) * lam * (up[v] - um[v]);
+}
+
+// HLLC (Toro, Spruce and Speares) with Davis wave-speed estimates.
+template <typename Real>
+__device__ __forceinline__ void hllc3(const Real* um, const Real* up, Real nx, Real ny, Real nz, Real gamma,
+                                      Real* F) {
+    Real fm[5], fp[5], unl, cl, unr, cr;
+    normal_flux3(um, nx, ny, nz, gamma, fm, unl, cl);
+    normal_flux3(up, nx, ny, nz, gamma, fp, unr, cr);
+    const Real SL = fmin(unl - cl, unr - cr), SR = fmax(unl + cl, unr + cr);
+    if (SL >= Real(0)) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) F[v] = fm[v];
+        return;
+    }
+    if (SR <= Real(0)) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) F[v] = fp[v];
+        return;
+    }
+    const Real rl = um[0], rr = up[0];
+    const Real pl = (gamma - Real(1)) * (um[4] - Real(0.5) * (um[1] * um[1] + um[2] * um[2] + um[3] * um[3]) / rl);
+    const Real pr = (gamma - Real(1)) * (up[4] - Real(0.5) * (up[1] * up[1] + up[2] * up[2] + up[3] * up[3]) / rr);
+    const Real SM = (pr - pl + rl * unl * (SL - unl) - rr * unr * (SR - unr)) / (rl * (SL - unl) - rr * (SR - unr));
+    const bool left = SM >= Real(0);
+    const Real* u = left ? um : up;
+    const Real* f = left ? fm : fp;
+    const Real S = left ? SL : SR, un = left ? unl : unr, p = left ? pl : pr, rho = u[0];
+    const Real fac = rho * (S - un) / (S - SM);
+    const Real ir = Real(1) / rho;
+    const Real n[3] = {nx, ny, nz};
+    Real us[5];
+    us[0] = fac;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) us[1 + d] = fac * (u[1 + d] * ir + (SM - un) * n[d]);
+    us[4] = fac * (u[4] * ir + (SM - un) * (SM + p / (rho * (S - un))));
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[v] = f[v] + S * (us[v] - u[v]);
+}
+
+template <typename Real>
+__device__ __forceinline__ Real stage_value3(const StageArgs3<Real>& p, long long n, Real us, Real L) {
+    if (p.rhs_only) return L;
+    if (p.dU) {
+        const Real d = (p.a != Real(0) ? p.a * p.dU[n] : Real(0)) + p.dt * L;
+        p.dU[n] = d;
+        return us + p.b * d;
+    }
+    return p.a * (p.a != Real(0) ? p.Un[n] : Real(0)) + p.b * (us + p.dt * L);
+}
+
+template <int N, typename Real>
+__global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> p) {
+    using T = T3<N, Real>;
+    constexpr int NP = T::NP, NFP = T::NFP, NQ = T::NQ, NG = T::NG, E = T::E;
+    constexpr Ops3Layout L = ops3_layout(N);
+    constexpr int CS = curved3_stride(N);
+    extern __shared__ __align__(16) unsigned char smem3[];
+    Real* S = reinterpret_cast<Real*>(smem3);
+    Real* sI2 = S + T::O_I2;
+    Real* sW = S + T::O_W;
+    Real* sMiT = S + T::O_MI;
+    Real* sU = S + T::O_U;
+    Real* sF = S + T::O_F;
+    Real* sNb = S + T::O_NB;
+    Real* sFs = S + T::O_FS;
+    Real* sR = S + T::O_R;
+    Real* sG = S + T::O_G;
+    int* sFmask = reinterpret_cast<int*>(S + T::O_END);
+    int* sFpos = sFmask + 4 * NFP;
+    int* sNbr = sFpos + 4 * NP;
+    int* sCode = sNbr + 4 * E;
+    const int tid = threadIdx.x;
+    const Real* __restrict__ IcubT = p.ops + L.icub;
+    const Real* __restrict__ DrWT = p.ops + L.drw;
+    const Real* __restrict__ DsWT = p.ops + L.dsw;
+    const Real* __restrict__ DtWT = p.ops + L.dtw;
+
+    for (int i = tid; i < 6 * NG * NFP; i += THREADS) sI2[i] = p.ops[L.i2 + i];
+    for (int i = tid; i < NG; i += THREADS) sW[i] = p.ops[L.wg + i];
+    for (int i = tid; i < NP * NP; i += THREADS) sMiT[i] = p.ops[L.mi + i];
+    for (int i = tid; i < 4 * NFP + 4 * NP; i += THREADS) sFmask[i] = p.opsi[i];
+
+    const long long ntiles = (p.K + E - 1) / E;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long e0 = tile * E;
+        const int ne = (int)min((long long)E, p.K - e0);
+        __syncthreads();
+        // ---- phase 0: rows, codes, affine geometry
+        const Real* Ug = p.Us + e0 * 5 * NP;
+        for (int i = tid; i < ne * 5 * NP; i += THREADS) sU[i] = Ug[i];
+        for (int i = tid; i < ne * 4; i += THREADS) {
+            const int e = i >> 2, f = i & 3;
+            const int4 nb = p.conn[e0 + e];
+            const int2 cw = p.code[e0 + e];
+            sNbr[i] = f == 0 ? nb.x : f == 1 ? nb.y : f == 2 ? nb.z : nb.w;
+            sCode[i] = ((f < 2 ? cw.x : cw.y) >> (16 * (f & 1))) & 0xffff;
+        }
+        for (int e = tid; e < ne; e += THREADS) {
+            if (e0 + e >= p.Kaff) continue;
+            const Real* J = p.geoA + (e0 + e) * 9;   // J[3 d + a] = dx_d / dr_a
+            Real* g = sG + e * 16;
+            // cofactors: g[3 d + a] = J dr_a / dx_d
+            g[0] = J[4] * J[8] - J[5] * J[7];
+            g[1] = J[5] * J[6] - J[3] * J[8];
+            g[2] = J[3] * J[7] - J[4] * J[6];
+            g[3] = J[2] * J[7] - J[1] * J[8];
+            g[4] = J[0] * J[8] - J[2] * J[6];
+            g[5] = J[1] * J[6] - J[0] * J[7];
+            g[6] = J[1] * J[5] - J[2] * J[4];
+            g[7] = J[2] * J[3] - J[0] * J[5];
+            g[8] = J[0] * J[4] - J[1] * J[3];
+            const Real det = J[0] * g[0] + J[1] * g[1] + J[2] * g[2];
+            g[9] = Real(1) / det;
+        }
+        __syncthreads();
+        // neighbours' face nodes
+        for (int i = tid; i < ne * 20 * NFP; i += THREADS) {
+            const int e = i / (20 * NFP), r = i - e * 20 * NFP, f = r / (5 * NFP), r2 = r - f * 5 * NFP;
+            const int v = r2 / NFP, n = r2 - v * NFP;
+            const int code = sCode[e * 4 + f];
+            if (code3_bc(code) == 0) {
+                const long long nb = sNbr[e * 4 + f];
+                sNb[i] = p.Us[nb * 5 * NP + v * NP + sFmask[code3_face(code) * NFP + n]];
+            }
+        }
+        // ---- phase 1: cubature-point fluxes
+        for (int i = tid; i < ne * NQ; i += THREADS) {
+            const int e = i / NQ, q = i - e * NQ;
+            const Real* ue = sU + e * 5 * NP;
+            Real u[5] = {0, 0, 0, 0, 0};
+            for (int j = 0; j < NP; ++j) {
+                const Real w = IcubT[j * NQ + q];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) u[v] += w * ue[v * NP + j];
+            }
+            Real cof[9];
+            const long long eg = e0 + e;
+            if (eg < p.Kaff) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) cof[k] = sG[e * 16 + k];
+            } else {
+                const Real* gc = p.geoC + (eg - p.Kaff) * CS;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) cof[k] = gc[k * NQ + q];
+            }
+            const Real ir = Real(1) / u[0];
+            const Real vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
+            const Real pr = (p.gamma - Real(1)) * (u[4] - Real(0.5) * (u[1] * vx + u[2] * vy + u[3] * vz));
+            const Real H = u[4] + pr;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                // contravariant velocity and pressure direction for direction a
+                const Real c0 = cof[a], c1 = cof[3 + a], c2 = cof[6 + a];
+                const Real U = c0 * vx + c1 * vy + c2 * vz;
+                Real* out = sF + (e * 15 + a * 5) * NQ + q;
+                out[0] = u[0] * U;
+                out[NQ] = u[1] * U + pr * c0;
+                out[2 * NQ] = u[2] * U + pr * c1;
+                out[3 * NQ] = u[3] * U + pr * c2;
+                out[4 * NQ] = H * U;
+            }
+        }
+        __syncthreads();
+        // ---- phase 2: volume term
+        for (int i = tid; i < ne * 5 * NP; i += THREADS) {
+            const int e = i / (5 * NP), r = i - e * 5 * NP, v = r / NP, n = r - v * NP;
+            const Real* fr = sF + (e * 15 + v) * NQ;
+            const Real* fs = fr + 5 * NQ;
+            const Real* ft = fs + 5 * NQ;
+            Real acc = 0;
+            for (int q = 0; q < NQ; ++q)
+                acc += DrWT[q * NP + n] * fr[q] + DsWT[q * NP + n] * fs[q] + DtWT[q * NP + n] * ft[q];
+            sR[i] = acc;
+        }
+        // ---- phase 3: face-frame points
+        for (int i = tid; i < ne * 4 * NG; i += THREADS) {
+            const int e = i / (4 * NG), r = i - e * 4 * NG, f = r / NG, g = r - f * NG;
+            const int code = sCode[e * 4 + f];
+            const long long eg = e0 + e;
+            const Real* I2o = sI2 + (code3_own(code) * NG + g) * NFP;
+            const Real* ue = sU + e * 5 * NP;
+            Real um[5] = {0, 0, 0, 0, 0}, up[5];
+            for (int n = 0; n < NFP; ++n) {
+                const Real w = I2o[n];
+                const int node = sFmask[f * NFP + n];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) um[v] += w * ue[v * NP + node];
+            }
+            Real nx, ny, nz, sJ;
+            if (eg < p.Kaff) {
+                const Real* c = sG + e * 16;
+                const Real a0 = kFaceRef[f][0], a1 = kFaceRef[f][1], a2 = kFaceRef[f][2];
+                const Real x = c[0] * a0 + c[1] * a1 + c[2] * a2;
+                const Real y = c[3] * a0 + c[4] * a1 + c[5] * a2;
+                const Real z = c[6] * a0 + c[7] * a1 + c[8] * a2;
+                sJ = sqrt(x * x + y * y + z * z);
+                const Real is = Real(1) / sJ;
+                nx = x * is; ny = y * is; nz = z * is;
+            } else {
+                const Real* gf = p.geoC + (eg - p.Kaff) * CS + 9 * NQ + f * NG + g;
+                nx = gf[0]; ny = gf[4 * NG]; nz = gf[8 * NG]; sJ = gf[12 * NG];
+            }
+            const int bc = code3_bc(code);
+            if (bc == 0) {
+                const Real* I2p = sI2 + (code3_nbr(code) * NG + g) * NFP;
+                const Real* nbv = sNb + (e * 4 + f) * 5 * NFP;
+#pragma unroll
+                for (int v = 0; v < 5; ++v) up[v] = 0;
+                for (int n = 0; n < NFP; ++n) {
+                    const Real w = I2p[n];
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) up[v] += w * nbv[v * NFP + n];
+                }
+            } else if (bc == 1) {
+                const Real mn = um[1] * nx + um[2] * ny + um[3] * nz;
+                up[0] = um[0];
+                up[1] = um[1] - Real(2) * mn * nx;
+                up[2] = um[2] - Real(2) * mn * ny;
+                up[3] = um[3] - Real(2) * mn * nz;
+                up[4] = um[4];
+            } else {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) up[v] = p.uinf[v];
+            }
+            Real F[5];
+            if (p.flux == 1)
+                hllc3(um, up, nx, ny, nz, p.gamma, F);
+            else
+                llf3(um, up, nx, ny, nz, p.gamma, F);
+            const Real ws = sW[g] * sJ;
+            Real* out = sFs + (e * 4 + f) * 5 * NG + g;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) out[v * NG] = ws * F[v];
+        }
+        __syncthreads();
+        // ---- phase 4: R = vol - surf
+        for (int i = tid; i < ne * 5 * NP; i += THREADS) {
+            const int e = i / (5 * NP), r = i - e * 5 * NP, v = r / NP, n = r - v * NP;
+            Real acc = 0;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const int pos = sFpos[f * NP + n];
+                if (pos < 0) continue;
+                const Real* I2o = sI2 + code3_own(sCode[e * 4 + f]) * NG * NFP + pos;
+                const Real* fs = sFs + ((e * 4 + f) * 5 + v) * NG;
+                for (int g = 0; g < NG; ++g) acc += I2o[g * NFP] * fs[g];
+            }
+            sR[i] -= acc;
+        }
+        __syncthreads();
+        // ---- phase 5: inverse mass and the stage update
+        for (int i = tid; i < ne * 5 * NP; i += THREADS) {
+            const int e = i / (5 * NP), r = i - e * 5 * NP, v = r / NP, n = r - v * NP;
+            const Real* rr = sR + (e * 5 + v) * NP;
+            const long long eg = e0 + e;
+            Real Lv = 0;
+            if (eg < p.Kaff) {
+                for (int j = 0; j < NP; ++j) Lv += sMiT[j * NP + n] * rr[j];
+                Lv *= sG[e * 16 + 9];
+            } else {
+                const Real* mi = p.geoC + (eg - p.Kaff) * CS + 9 * NQ + 16 * NG;
+                for (int j = 0; j < NP; ++j) Lv += mi[j * NP + n] * rr[j];
+            }
+            const long long at = e0 * 5 * NP + i;
+            p.Uout[at] = stage_value3(p, at, sU[i], Lv);
+        }
+    }
+}
+
+template <int N, typename Real>
+int prepare_t(void) {
+    const cudaError_t e = cudaFuncSetAttribute(stage3_kernel<N, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)T3<N, Real>::BYTES);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return (int)e;
+    }
+    return 0;
+}
+
+template <int N, typename Real>
+int launch_t(const StageArgs3<Real>& a, cudaStream_t st) {
+    using T = T3<N, Real>;
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const int occ = std::max(1, resident_ctas((const void*)stage3_kernel<N, Real>, THREADS, T::BYTES));
+        grid = nsm * occ;
+    }
+    const long long ntiles = (a.K + T::E - 1) / T::E;
+    const int g = (int)std::min<long long>(ntiles, grid);
+    if (g <= 0) return 0;
+    stage3_kernel<N, Real><<<g, THREADS, T::BYTES, st>>>(a);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+bool supported_degree3(int N) { return N >= 2 && N <= 4; }
+
+size_t stage3_smem(int N, int rsize) {
+    if (rsize == 8) return N == 2 ? T3<2, double>::BYTES : N == 3 ? T3<3, double>::BYTES : T3<4, double>::BYTES;
+    return N == 2 ? T3<2, float>::BYTES : N == 3 ? T3<3, float>::BYTES : T3<4, float>::BYTES;
+}
+
+int prepare_stage3(int N, int rsize) {
+    if (rsize == 8) return N == 2 ? prepare_t<2, double>() : N == 3 ? prepare_t<3, double>() : prepare_t<4, double>();
+    return N == 2 ? prepare_t<2, float>() : N == 3 ? prepare_t<3, float>() : prepare_t<4, float>();
+}
+
+int launch_stage3(int N, const StageArgs3<float>& a, cudaStream_t st) {
+    return N == 2 ? launch_t<2, float>(a, st) : N == 3 ? launch_t<3, float>(a, st) : launch_t<4, float>(a, st);
+}
+
+int launch_stage3(int N, const StageArgs3<double>& a, cudaStream_t st) {
+    return N == 2 ? launch_t<2, double>(a, st) : N == 3 ? launch_t<3, double>(a, st) : launch_t<4, double>(a, st);
+}
+
+}  // namespace dgc

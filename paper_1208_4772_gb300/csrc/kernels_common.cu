@@ -11,30 +11,33 @@ namespace {
 
 constexpr int RED_THREADS = 256;
 
-// Per-variable max |L| and sum L^2 of L[K][4][NP] in FP64.  Each block
-// writes 8 partials; the order of accumulation is fixed by the launch shape,
-// so the result is deterministic.
-template <typename Real>
+// Per-variable max |L| and sum L^2 of L[K][NV][NP] in FP64 (NV = 4 on
+// triangles, 5 on tetrahedra).  Each block writes 2 NV partials; the order
+// of accumulation is fixed by the launch shape, so the result is
+// deterministic.
+template <typename Real, int NV>
 __global__ void __launch_bounds__(RED_THREADS) residual_partial(const Real* L, long long total, int NP,
                                                                  double* partial) {
-    double mx[4] = {0, 0, 0, 0}, ss[4] = {0, 0, 0, 0};
+    double mx[NV], ss[NV];
+#pragma unroll
+    for (int w = 0; w < NV; ++w) mx[w] = ss[w] = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += stride) {
-        const int v = (int)((n / NP) & 3);
+        const int v = (int)((n / NP) % NV);
         const double x = (double)L[n];
         const double ax = fabs(x);
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
+        for (int w = 0; w < NV; ++w) {
             if (w == v) {
                 mx[w] = (ax > mx[w] || ax != ax) ? ax : mx[w];
                 ss[w] += x * x;
             }
         }
     }
-    __shared__ double sm[8][RED_THREADS / 32];
+    __shared__ double sm[2 * NV][RED_THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
+    for (int w = 0; w < NV; ++w) {
         double a = mx[w], b = ss[w];
         for (int o = 16; o > 0; o >>= 1) {
             const double ao = __shfl_xor_sync(0xffffffffu, a, o);
@@ -43,36 +46,36 @@ __global__ void __launch_bounds__(RED_THREADS) residual_partial(const Real* L, l
         }
         if (lane == 0) {
             sm[w][warp] = a;
-            sm[4 + w][warp] = b;
+            sm[NV + w][warp] = b;
         }
     }
     __syncthreads();
-    if (threadIdx.x < 8) {
+    if (threadIdx.x < 2 * NV) {
         const int w = threadIdx.x;
         double acc = 0.0;
         for (int i = 0; i < RED_THREADS / 32; ++i) {
             const double x = sm[w][i];
-            if (w < 4)
+            if (w < NV)
                 acc = (x > acc || x != x) ? x : acc;
             else
                 acc += x;
         }
-        partial[(long long)blockIdx.x * 8 + w] = acc;
+        partial[(long long)blockIdx.x * 2 * NV + w] = acc;
     }
 }
 
-__global__ void residual_final(const double* partial, int nblocks, double* out8) {
-    if (threadIdx.x < 8) {
+__global__ void residual_final(const double* partial, int nblocks, int nv, double* out) {
+    if (threadIdx.x < 2 * nv) {
         const int w = threadIdx.x;
         double acc = 0.0;
         for (int b = 0; b < nblocks; ++b) {
-            const double x = partial[(long long)b * 8 + w];
-            if (w < 4)
+            const double x = partial[(long long)b * 2 * nv + w];
+            if (w < nv)
                 acc = (x > acc || x != x) ? x : acc;
             else
                 acc += x;
         }
-        out8[w] = (w < 4) ? acc : sqrt(acc);
+        out[w] = (w < nv) ? acc : sqrt(acc);
     }
 }
 
@@ -116,11 +119,13 @@ int launch_prolong(const Real* in, Real* out, const Real* P, long long K, int np
 int residual_blocks() { return 304; }
 
 template <typename Real>
-int launch_residual(const Real* L, long long /*unused*/, long long K, int NP, double* partial, double* out8,
-                    cudaStream_t st) {
+int launch_residual(const Real* L, int nvar, long long K, int NP, double* partial, double* out, cudaStream_t st) {
     const int nb = residual_blocks();
-    residual_partial<Real><<<nb, RED_THREADS, 0, st>>>(L, K * 4 * NP, NP, partial);
-    residual_final<<<1, 32, 0, st>>>(partial, nb, out8);
+    if (nvar == 5)
+        residual_partial<Real, 5><<<nb, RED_THREADS, 0, st>>>(L, K * 5 * NP, NP, partial);
+    else
+        residual_partial<Real, 4><<<nb, RED_THREADS, 0, st>>>(L, K * 4 * NP, NP, partial);
+    residual_final<<<1, 32, 0, st>>>(partial, nb, nvar, out);
     return (int)cudaGetLastError();
 }
 
@@ -133,8 +138,8 @@ int launch_permute(const Real* src, Real* dst, const long long* map, long long K
     return (int)cudaGetLastError();
 }
 
-template int launch_residual<float>(const float*, long long, long long, int, double*, double*, cudaStream_t);
-template int launch_residual<double>(const double*, long long, long long, int, double*, double*, cudaStream_t);
+template int launch_residual<float>(const float*, int, long long, int, double*, double*, cudaStream_t);
+template int launch_residual<double>(const double*, int, long long, int, double*, double*, cudaStream_t);
 template int launch_permute<float>(const float*, float*, const long long*, long long, int, cudaStream_t);
 template int launch_permute<double>(const double*, double*, const long long*, long long, int, cudaStream_t);
 template int launch_prolong<float>(const float*, float*, const float*, long long, int, int, cudaStream_t);

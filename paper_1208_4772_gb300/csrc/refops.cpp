@@ -6,7 +6,7 @@
 
 namespace dgc {
 
-namespace {
+namespace detail {
 
 // Orthonormal Jacobi polynomial of degree n for the weight (1-x)^a (1+x)^b,
 // by the three-term recurrence of the orthonormal family
@@ -170,7 +170,9 @@ void matmul(const std::vector<double>& A, const std::vector<double>& B, std::vec
         }
 }
 
-}  // namespace
+}  // namespace detail
+
+using namespace detail;
 
 int default_q(int N) { return (3 * N + 2) / 2; }
 int n_modes(int N) { return (N + 1) * (N + 2) / 2; }

@@ -37,6 +37,19 @@ bool build_refops(int N, int q, RefOps& out, std::string& err);
 // P = V_f(r_t) V_f^-1 [Np(Nt)][Np(Nf)]: degree-Nf interpolant at the degree-Nt nodes.
 bool build_prolongation(int Nf, int Nt, std::vector<double>& P, std::string& err);
 
+// Building blocks shared with the tetrahedral operators (refops3.cpp).
+namespace detail {
+double jac(double x, double a, double b, int n);     // orthonormal Jacobi polynomial
+double djac(double x, double a, double b, int n);    // its derivative
+void gauss_jacobi(int n, double a, double b, std::vector<double>& x, std::vector<double>& w);
+std::vector<double> gll(int N);                       // Gauss-Lobatto-Legendre points
+void nodes_2d(int N, std::vector<double>& r, std::vector<double>& s);   // triangle warp & blend nodes
+void mode_ij(int N, std::vector<int>& I, std::vector<int>& J);
+void psi(int i, int j, double r, double s, double* val, double* dr, double* ds);   // triangle basis
+void matmul(const std::vector<double>& A, const std::vector<double>& B, std::vector<double>& C, int n, int k,
+            int m);
+}  // namespace detail
+
 // Dense helpers (row-major), used by the geometry set-up as well.
 bool invert(std::vector<double>& A, int n);            // Gauss-Jordan, partial pivoting
 bool spd_inverse(const double* A, double* Ainv, int n); // via Cholesky, false if not SPD

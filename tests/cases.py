@@ -42,3 +42,52 @@ def make_case(kind, N, r, s, seed=0, av=False, size="small", perturb=0.02):
     else:
         raise ValueError(kind)
     return dict(mesh=m, xy=xy, curved=curved, u_inf=ui, U=U, av=av, name=kind, N=N)
+
+
+# ------------------------------------------------------------------ tetrahedra
+def warp_box_nodes(X, L, amp=0.3):
+    """Smooth periodic displacement of the box nodes (every element curved)."""
+    k = 2 * np.pi / L
+    d = amp * np.sin(k * X[..., [0]] + 0.3) * np.sin(k * X[..., [1]]) * np.sin(k * X[..., [2]])
+    return X + d * np.array([1.0, 0.5, -0.7])
+
+
+def make_case3(kind, N, r, s, t, seed=0, size="small", perturb=0.02):
+    """Tetrahedral cases.  Returns dict(mesh, xyz, u_inf, U, name, N).
+      box   periodic jittered cube (affine), extruded vortex plus noise
+      wbox  the same cube with a smooth periodic warp (every element curved)
+      bump  channel with a curved bump on the floor: slip walls, farfield
+            inflow/outflow, uniform flow with smooth perturbations and noise"""
+    from paper_1208_4772_gb300.inputs import meshes3d
+    rng = np.random.default_rng(seed)
+    if kind in ("box", "wbox"):
+        n = {"tiny": 2, "small": 3, "medium": 5}.get(size, size) if isinstance(size, str) else size
+        L = 10.0
+        m = meshes3d.box(n, L=L, seed=1000 + seed)
+        X = meshes3d.node_coords(m, r, s, t)
+        if kind == "wbox":
+            X = warp_box_nodes(X, L)
+        ui = states.freestream3(0.5, 10.0)
+        U = states.vortex3_state(X, period=(L, L))
+        U *= 1.0 + 0.1 * perturb * rng.standard_normal(U.shape)
+    elif kind == "bump":
+        nx, ny, nz = {"tiny": (4, 2, 2), "small": (6, 3, 4), "medium": (12, 6, 8)}[size]
+        m = meshes3d.bump_channel(nx, ny, nz, seed=2000 + seed)
+        X = meshes3d.node_coords(m, r, s, t)
+        ui = states.freestream3(0.5, 0.0)
+        U = states.uniform_state3(m.K, len(r), ui)
+        x, y, z = X[..., 0], X[..., 1], X[..., 2]
+        U[:, 0] *= 1.0 + perturb * np.sin(1.3 * x) * np.cos(0.7 * y + z)
+        U[:, 4] *= 1.0 + perturb * np.cos(0.9 * x + 0.4 * y)
+        U[:, 2] += perturb * np.sin(2 * z)
+        U[:, 3] += perturb * np.cos(x + y)
+        U *= 1.0 + 0.1 * perturb * rng.standard_normal(U.shape)
+    else:
+        raise ValueError(kind)
+    return dict(mesh=m, xyz=X, u_inf=ui, U=U, name=kind, N=N)
+
+
+def rel_l2_per_var5(a, b):
+    nv = a.shape[1]
+    return np.linalg.norm((a - b).transpose(1, 0, 2).reshape(nv, -1), axis=1) / \
+        np.linalg.norm(b.transpose(1, 0, 2).reshape(nv, -1), axis=1)

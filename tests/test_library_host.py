@@ -69,8 +69,9 @@ def test_errors_are_status_codes(B):
 
 def test_params_struct_layout(B):
     import ctypes
-    assert ctypes.sizeof(B.dg_params) == 80
-    assert B.dg_params.u_inf.offset == 40 and B.dg_params.prec.offset == 72
+    # the C layout of include/dgcurved.h: u_inf[5] at 40, prec at 80, cub_q at 84
+    assert ctypes.sizeof(B.dg_params) == 88
+    assert B.dg_params.u_inf.offset == 40 and B.dg_params.prec.offset == 80 and B.dg_params.cub_q.offset == 84
 
 
 def test_autotune_argument_errors(B):
@@ -79,3 +80,13 @@ def test_autotune_argument_errors(B):
     lib = B.load()
     out = ctypes.c_int32(0)
     assert lib.dg_autotune(None, 1, 5, ctypes.byref(out), None, None, None) == B.DG_EINVAL
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+def test_tet_reference_nodes_match_oracle(B, N):
+    from oracle import tet
+    r, s, t = B.dg_tet_reference_nodes(N)
+    R = tet.warp_blend_nodes_3d(N)
+    assert max(np.abs(r - R[0]).max(), np.abs(s - R[1]).max(), np.abs(t - R[2]).max()) < 1e-14
+    q = default_q(N)
+    assert B.dg_tet_sizes(N) == (tet.n_modes(N), q ** 3, q ** 2, tet.n_face_nodes(N))
