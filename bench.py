@@ -59,6 +59,12 @@ WORKLOADS = {
     "prefine": dict(kind="prefine", describe="p-refinement (paper Sec. 5): cylinder channel, 15,360 elements, "
                                              "Mach 0.38, no AV; degrees 2 -> 3 -> 4 against N = 4 from the "
                                              "freestream, to the same residual"),
+    # the tetrahedral method (the paper's 3D setting): a single mesh
+    "bump3d_m0.5_n3": dict(kind="tet", N=3, cells=(50, 25, 40), Zd=0.4, mach=0.5,
+                           describe="tetrahedra: channel 3 x 1.5 x 0.8 over a smooth floor bump of height 0.1, "
+                                    "50 x 25 x 40 Kuhn-split cells = 300k tetrahedra (curved below z = 0.4 over "
+                                    "the bump), "
+                                    "N=3, Mach 0.5, slip walls, farfield in/outflow, LLF"),
     "serve": dict(kind="serve", describe="continuous batching: Poisson arrivals, K log-uniform in [1k, 500k], "
                                          "N uniform in {2..6}, admission by an HBM budget, retirement at a 1e-6 "
                                          "residual drop or a step cap"),
@@ -107,6 +113,48 @@ def make_workload(name, r, s):
     U0 = states.uniform_state(mesh.K, len(r), ui)
     dt = states.time_step(mesh.verts, U0, w["N"], cfl=0.3, eps0=0.3 if w["av"] else None)
     return dict(mesh=mesh, xy=xy, curved=curved, u_inf=ui, U0=U0, dt=dt, **w)
+
+
+def make_tet_workload(name, r, s, t):
+    """Seeded tetrahedral mesh, nodes, initial state and time step (inputs only)."""
+    from paper_1208_4772_gb300.inputs import meshes3d, states
+    w = WORKLOADS[name]
+    mesh = meshes3d.bump_channel(*w["cells"], Zd=w["Zd"], seed=2000)
+    X = meshes3d.node_coords(mesh, r, s, t)
+    ui = states.freestream3(w["mach"], 0.0)
+    U0 = states.uniform_state3(mesh.K, len(r), ui)
+    dt = states.time_step3(mesh.verts, U0, w["N"], cfl=0.3)
+    curved = meshes3d.mapped_elements(mesh, r, s, t)
+    return dict(mesh=mesh, xyz=X, curved=curved, u_inf=ui, U0=U0, dt=dt, **w)
+
+
+def tet_sizes(N):
+    q = (3 * N + 2) // 2
+    return (N + 1) * (N + 2) * (N + 3) // 6, q ** 3, q * q, (N + 1) * (N + 2) // 2
+
+
+def tet_stage_flops(N):
+    """Algorithmic FP32 operations of one element in one tetrahedral stage:
+    interpolation to the cubature points (2 N_q N_p per variable), the three
+    weighted derivative products (6 N_p N_q per variable), face-node ->
+    face-point interpolation on both sides and its transpose for the lift
+    (3 x 2 N_g N_fp per face and variable), the inverse mass (2 N_p^2 per
+    variable), the Euler flux with its contravariant form (~40 per cubature
+    point) and the numerical flux (~70 per face point)."""
+    Np, Nq, Ng, Nfp = tet_sizes(N)
+    return 5 * (2 * Nq * Np + 6 * Np * Nq + 4 * 3 * 2 * Ng * Nfp + 2 * Np * Np) + 40 * Nq + 70 * 4 * Ng
+
+
+def tet_stage_bytes(K, Kc, N):
+    """Algorithmic HBM bytes of one tetrahedral stage launch (SSP-RK3
+    average): read U_s, read U^n in stages 2 and 3, write U_out (5 N_p FP32
+    each), affine geometry 36 B, neighbours 16 B and face codes 8 B per
+    element, the curved elements' record (cofactors at the cubature points,
+    face normals and area factors, M_k^-1); neighbour face nodes are L2
+    hits and count 0."""
+    Np, Nq, Ng, Nfp = tet_sizes(N)
+    state = 5 * Np * 4
+    return K * (state * (1 + 2.0 / 3.0 + 1) + 24) + (K - Kc) * 36 + Kc * (9 * Nq + 16 * Ng + Np * Np) * 4
 
 
 def stage_kernel_bytes(K, Kc, N, av):
@@ -185,6 +233,8 @@ class ClockSampler:
 def cpu_sample(name, budget_s, flux="llf"):
     """Time the FP64 oracle on the workload (fresh single-thread process)."""
     import numpy as np
+    if WORKLOADS[name]["kind"] == "tet":
+        return cpu_sample_tet(name, budget_s, flux)
     from oracle.dg import Oracle
     from oracle.operators import ReferenceElement
     ref = ReferenceElement(WORKLOADS[name]["N"])
@@ -205,6 +255,34 @@ def cpu_sample(name, budget_s, flux="llf"):
     return {"value": dof * 3 * steps / el, "seconds": el,
             "sample": "%d full SSP-RK3 step(s) (%d RHS evaluations) of the whole %d-element mesh, "
                       "oracle geometry set-up excluded" % (steps, 3 * steps, m.K)}
+
+
+def cpu_sample_tet(name, budget_s, flux):
+    """The tetrahedral oracle as it stands on a sample of elements:
+    right-hand sides of every 100th element, repeated within the budget (each
+    call computes the sample's geometry, as the oracle does for a subset);
+    DOF-updates/s of the sample."""
+    import numpy as np
+    from oracle.dg3 import Oracle3
+    from oracle.tet import ReferenceTet
+    w = WORKLOADS[name]
+    ref = ReferenceTet(w["N"])
+    wl = make_tet_workload(name, ref.r, ref.s, ref.t)
+    m = wl["mesh"]
+    o = Oracle3(w["N"], m.EToV, m.bc, wl["xyz"], u_inf=wl["u_inf"], flux=flux)
+    idx = np.arange(0, m.K, 100)
+    U = wl["U0"]
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.rhs(U, idx)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": len(idx) * ref.Np * 5 * n / el, "seconds": el,
+            "sample": "%d right-hand sides of %d of the %d elements (every 100th), the sample's geometry "
+                      "computed in each call" % (n, len(idx), m.K)}
 
 
 def run_cpu_baseline(name, budget_s, flux="llf"):
@@ -229,6 +307,8 @@ def run_reference(args):
         return 0
     for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"          # before numpy loads: the oracle runs on one core
+    if WORKLOADS[args.workload]["kind"] == "tet":
+        return run_reference_tet(args)
     import numpy as np
     from oracle.dg import Oracle
     from oracle.operators import ReferenceElement
@@ -470,6 +550,159 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ tetrahedra
+def run_tet(args):
+    """The tetrahedral stage kernel on one mesh: SSP-RK3 steps through
+    dg_step, L2 flushed before every timed step; a second pass with events
+    around every kernel gives the stage kernel's launch time.  The path runs
+    on the CUDA cores in FP32, so the roofline is the FP32 ALU peak."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1208_4772_gb300 import binding as B
+    B.load()
+    torch.cuda.set_device(0)
+    w = WORKLOADS[args.workload]
+    N = w["N"]
+    prec = args.prec if args.prec in ("fp32", "fp64") else "fp32"
+    r, s_, t = B.dg_tet_reference_nodes(N)
+    wl = make_tet_workload(args.workload, r, s_, t)
+    m = wl["mesh"]
+    Np = len(r)
+    dof_stage = m.K * Np * 5
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = B.dg_create(0, stream.cuda_stream)
+    flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device="cuda")
+    p = B.make_params(u_inf=wl["u_inf"], prec=prec, flux=args.flux)
+    h = B.dg_tet_mesh_upload(ctx, N, m.EToV, m.bc, wl["xyz"], p)
+    info = B.dg_mesh_info(ctx, h)
+    B.dg_set_state(ctx, h, wl["U0"])
+    step = B.dg_step_lserk if args.integrator == "lserk" else B.dg_step
+    nstage = 5 if args.integrator == "lserk" else 3
+
+    def warm():
+        for _ in range(args.warmup):
+            flush.zero_()
+            step(ctx, h, wl["dt"], 1)
+        torch.cuda.synchronize()
+
+    warm()
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    times, _, _ = timed_steps(B, ctx, h, wl["dt"], args.steps, stream, flush, torch, step=step)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = float(sum(times))
+    value = dof_stage * nstage * args.steps / (total_ms / 1e3)
+    linf, l2 = B.dg_residual(ctx, h, allow_nonfinite=True)
+    n_prof = min(args.steps, 200)
+    if args.integrator == "ssp3":
+        B.dg_set_profiling(ctx, h, 1)
+        warm()
+        _, kt, launches = timed_steps(B, ctx, h, wl["dt"], n_prof, stream, flush, torch, profiled=True)
+        B.dg_set_profiling(ctx, h, 0)
+        launch_ms = kt[2] / (3 * n_prof)
+        launches = launches * args.steps // n_prof
+    else:
+        launch_ms = total_ms / args.steps / 5
+        launches = args.steps * 5
+    flops = tet_stage_flops(N) * m.K
+    bytes_launch = tet_stage_bytes(m.K, info["curved"], N)
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (launch_ms * 1e-3) / 1e12
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm = float(json.load(open(peaks_path))["hbm_gbs"]) if os.path.exists(peaks_path) else 6800.0
+    roofline = {"kernel": "stage3_kernel (tetrahedra, N=%d, %s)" % (N, prec), "bound": "alu",
+                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock %.0f MHz" % sm_max,
+                "traffic": TRAFFIC.get((args.workload, prec, args.flux)), "flops_per_launch": flops,
+                "bytes_per_launch": bytes_launch, "avg_launch_ms": launch_ms,
+                "hbm_gbs": bytes_launch / (launch_ms * 1e-3) / 1e9,
+                "hbm_frac": bytes_launch / (launch_ms * 1e-3) / 1e9 / hbm}
+    e2e = None
+    if not args.no_e2e:
+        step(ctx, h, wl["dt"], 1)
+        torch.cuda.synchronize()
+        U_host = np.ascontiguousarray(wl["U0"])
+        n_e2e = min(args.steps, 500)
+        t0 = time.perf_counter()
+        B.dg_set_state(ctx, h, U_host)
+        step(ctx, h, wl["dt"], n_e2e)
+        U_out = B.dg_get_state(ctx, h)
+        el = time.perf_counter() - t0
+        e2e = {"value": dof_stage * nstage * n_e2e / el, "unit": UNIT, "h2d_bytes_per_step": U_host.nbytes / n_e2e,
+               "d2h_bytes_per_step": U_out.nbytes / n_e2e,
+               "how": "dg_set_state(host FP64) + %s(%d) + dg_get_state(host FP64), wall clock"
+                      % ("dg_step_lserk" if args.integrator == "lserk" else "dg_step", n_e2e)}
+    B.dg_destroy(ctx)
+    cpu = None if args.no_cpu_baseline else run_cpu_baseline(args.workload, args.cpu_budget_s, args.flux)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+            "config": {"workload": args.workload, "describe": w["describe"], "K": int(m.K), "N": N, "Np": Np,
+                       "variables": 5, "curved_elements": int(info["curved"]), "state_precision": prec,
+                       "time_integrator": "LSERK(5,4)" if args.integrator == "lserk" else "SSP-RK3",
+                       "flux": args.flux.upper(), "dt": wl["dt"], "dof_per_stage": int(dof_stage),
+                       "l2": "flushed before every timed step (%d MiB memset, outside the step events)"
+                             % args.flush_mb,
+                       "parallelism": "replicas (one independent solve per GPU)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "residual_linf": [float(x) for x in linf]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_tet(args):
+    """The tetrahedral oracle as it stands, one SSP-RK3 step per timed step
+    on a fixed sample of elements sized so the run ends within minutes."""
+    import numpy as np
+    from oracle.dg3 import Oracle3
+    from oracle.tet import ReferenceTet
+    w = WORKLOADS[args.workload]
+    ref = ReferenceTet(w["N"])
+    wl = make_tet_workload(args.workload, ref.r, ref.s, ref.t)
+    m = wl["mesh"]
+    o = Oracle3(w["N"], m.EToV, m.bc, wl["xyz"], u_inf=wl["u_inf"], flux=args.flux)
+    t0 = time.perf_counter()
+    probe = np.arange(0, m.K, max(1, m.K // 256))
+    o.rhs(wl["U0"], probe)
+    per_elt = (time.perf_counter() - t0) / len(probe)
+    per_step = 150.0 / max(1, args.steps + args.warmup)
+    S = int(max(16, min(m.K, per_step / (3 * per_elt))))
+    idx = np.linspace(0, m.K - 1, S).astype(np.int64)
+    U = wl["U0"].copy()
+
+    def step():
+        Us = U
+        for a, b in ((0.0, 1.0), (0.75, 0.25), (1 / 3, 2 / 3)):
+            L = o.rhs(Us, idx)
+            Us = Us.copy()
+            Us[idx] = a * U[idx] + b * (Us[idx] + wl["dt"] * L)
+        return Us
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = S * ref.Np * 5 * 3 * args.steps / el
+    sample = "%d of %d elements per SSP-RK3 step (3 RHS evaluations on the sample)" % (S, m.K)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "describe": w["describe"], "K": int(m.K),
+                                            "N": w["N"], "flux": args.flux.upper()},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ batch and serving
 def make_batch(n, seed0=2000):
     """Seeded batch of n mesh requests (inputs only): K log-uniform in
@@ -682,6 +915,8 @@ def main():
         return run_serve(args)
     if args.workload == "prefine":
         return run_prefine(args)
+    if WORKLOADS[args.workload]["kind"] == "tet":
+        return run_tet(args)
     return run_ours(args)
 
 

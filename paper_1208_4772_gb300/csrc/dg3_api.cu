@@ -37,25 +37,28 @@ const RefOps3* get_refops3(int N, std::string& err) {
     return p;
 }
 
-// Operator tables in the kernel's layout (ops3_layout): transposed so that
-// consecutive threads read consecutive entries.
+// Operator tables in the kernel's layout (ops3_layout): the volume products
+// in blocks of four along their summation index, so that one 16-byte load
+// gives a thread four consecutive terms.
 std::vector<double> pack_ops3(const RefOps3& R) {
-    const int NP = R.Np, NQ = R.Nq, NG = R.Ng, NFP = R.Nfp;
+    const int NP = R.Np, NQ = R.Nq, NG = R.Ng;
+    const int NPP = pad4(NP), NQP = pad4(NQ);
     const Ops3Layout L = ops3_layout(R.N);
     std::vector<double> o((size_t)L.total, 0.0);
     for (int j = 0; j < NP; ++j)
-        for (int q = 0; q < NQ; ++q) o[L.icub + (size_t)j * NQ + q] = R.Icub[(size_t)q * NP + j];
+        for (int q = 0; q < NQ; ++q)
+            o[L.icub + ((size_t)(j / 4) * NQP + q) * 4 + j % 4] = R.Icub[(size_t)q * NP + j];
     for (int q = 0; q < NQ; ++q)
         for (int n = 0; n < NP; ++n) {
-            o[L.drw + (size_t)q * NP + n] = R.DrW[(size_t)n * NQ + q];
-            o[L.dsw + (size_t)q * NP + n] = R.DsW[(size_t)n * NQ + q];
-            o[L.dtw + (size_t)q * NP + n] = R.DtW[(size_t)n * NQ + q];
+            const size_t at = ((size_t)(q / 4) * NPP + n) * 4 + q % 4;
+            o[L.drw + at] = R.DrW[(size_t)n * NQ + q];
+            o[L.dsw + at] = R.DsW[(size_t)n * NQ + q];
+            o[L.dtw + at] = R.DtW[(size_t)n * NQ + q];
         }
     std::copy(R.I2.begin(), R.I2.end(), o.begin() + L.i2);
     for (int g = 0; g < NG; ++g) o[L.wg + g] = R.wg[g];
     for (int j = 0; j < NP; ++j)
         for (int n = 0; n < NP; ++n) o[L.mi + (size_t)j * NP + n] = R.Mrefinv[(size_t)n * NP + j];
-    (void)NFP;
     return o;
 }
 

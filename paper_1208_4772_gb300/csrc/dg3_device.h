@@ -11,24 +11,29 @@ __host__ __device__ constexpr int nfp3_of(int N) { return (N + 1) * (N + 2) / 2;
 __host__ __device__ constexpr int nq3_of(int N) { return q_of(N) * q_of(N) * q_of(N); }
 __host__ __device__ constexpr int ng3_of(int N) { return q_of(N) * q_of(N); }
 
-// Operator table of degree N in the real type (offsets in elements):
-//   Icub [NQ][NP], D_r^T W, D_s^T W, D_t^T W [NP][NQ] each,
+__host__ __device__ constexpr int pad4(int n) { return (n + 3) / 4 * 4; }
+
+// Operator table of degree N in the real type (offsets in elements, each a
+// multiple of 4; NPP = pad4(NP), NQP = pad4(NQ), padding entries zero):
+//   Icub as [NPP/4][NQP][4]: (j, q) at ((j/4) NQP + q) 4 + j%4
+//   D_r^T W, D_s^T W, D_t^T W as [NQP/4][NPP][4]: (q, n) at ((q/4) NPP + n) 4 + q%4
 //   I2 [6][NG][NFP] (face nodes -> face-frame points, by orientation),
-//   face weights [NG], M_ref^-1 [NP][NP].
+//   face weights [NG], (M_ref^-1)^T [NP][NP].
 struct Ops3Layout {
     int icub, drw, dsw, dtw, i2, wg, mi, total;
 };
 __host__ __device__ constexpr Ops3Layout ops3_layout(int N) {
     const int NP = np3_of(N), NQ = nq3_of(N), NG = ng3_of(N), NFP = nfp3_of(N);
+    const int NPP = pad4(NP), NQP = pad4(NQ);
     Ops3Layout o{};
     o.icub = 0;
-    o.drw = o.icub + NQ * NP;
-    o.dsw = o.drw + NP * NQ;
-    o.dtw = o.dsw + NP * NQ;
-    o.i2 = o.dtw + NP * NQ;
-    o.wg = o.i2 + 6 * NG * NFP;
-    o.mi = o.wg + NG;
-    o.total = o.mi + NP * NP;
+    o.drw = o.icub + NPP * NQP;
+    o.dsw = o.drw + NQP * NPP;
+    o.dtw = o.dsw + NQP * NPP;
+    o.i2 = o.dtw + NQP * NPP;
+    o.wg = pad4(o.i2 + 6 * NG * NFP);
+    o.mi = pad4(o.wg + NG);
+    o.total = pad4(o.mi + NP * NP);
     return o;
 }
 // Integer table: fmask [4][NFP] (element node of each face node),

@@ -25,20 +25,47 @@ namespace {
 template <int N, typename Real>
 struct T3 {
     static constexpr int NP = np3_of(N), NFP = nfp3_of(N), NQ = nq3_of(N), NG = ng3_of(N);
+    static constexpr int NPP = pad4(NP), NQP = pad4(NQ);
     static constexpr int E = sizeof(Real) == 4 ? (N <= 2 ? 16 : N == 3 ? 8 : 3) : (N <= 2 ? 8 : N == 3 ? 4 : 1);
     static constexpr int O_I2 = 0;
     static constexpr int O_W = O_I2 + 6 * NG * NFP;
     static constexpr int O_MI = O_W + NG;
-    static constexpr int O_U = (O_MI + NP * NP + 3) / 4 * 4;
-    static constexpr int O_F = O_U + E * 5 * NP;
-    static constexpr int O_NB = O_F + E * 15 * NQ;
-    static constexpr int O_FS = O_NB + E * 20 * NFP;
-    static constexpr int O_R = O_FS + E * 20 * NG;
-    static constexpr int O_G = O_R + E * 5 * NP;
+    static constexpr int O_U = pad4(O_MI + NP * NP);   // [E][5][NPP]
+    static constexpr int O_F = O_U + E * 5 * NPP;      // [E][3][5][NQP] contravariant fluxes
+    static constexpr int O_NB = O_F + E * 15 * NQP;    // [E][4][5][NFP] neighbours' face nodes
+    static constexpr int O_FS = O_NB + E * 20 * NFP;   // [E][4][5][NG] w sJ F*
+    static constexpr int O_R = O_FS + E * 20 * NG;     // [3][E][5][NP] volume parts, then R
+    static constexpr int O_G = O_R + 3 * E * 5 * NP;   // [E][16] affine cofactors, 1/J
     static constexpr int O_END = O_G + E * 16;
     static constexpr int NINT = 4 * NFP + 4 * NP + 8 * E;
     static constexpr size_t BYTES = (size_t)O_END * sizeof(Real) + (size_t)NINT * sizeof(int);
 };
+
+// Four consecutive reals by one 16-byte access (two for double).
+template <typename Real>
+struct V4 {
+    Real x, y, z, w;
+};
+__device__ __forceinline__ V4<float> lds4(const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ V4<double> lds4(const double* p) {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ V4<float> ldg4(const float* p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ V4<double> ldg4(const double* p) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p + 2));
+    return {a.x, a.y, b.x, b.y};
+}
+template <typename Real>
+__device__ __forceinline__ Real dot4(const V4<Real>& a, const V4<Real>& b) {
+    return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
 
 // outward reference face vectors (t_u x t_v of each face's parametrisation)
 __device__ __constant__ float kFaceRef[4][3] = {{0, 0, -1}, {0, -1, 0}, {1, 1, 1}, {-1, 0, 0}};
@@ -120,7 +147,7 @@ __device__ __forceinline__ Real stage_value3(const StageArgs3<Real>& p, long lon
 template <int N, typename Real>
 __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> p) {
     using T = T3<N, Real>;
-    constexpr int NP = T::NP, NFP = T::NFP, NQ = T::NQ, NG = T::NG, E = T::E;
+    constexpr int NP = T::NP, NFP = T::NFP, NQ = T::NQ, NG = T::NG, E = T::E, NPP = T::NPP, NQP = T::NQP;
     constexpr Ops3Layout L = ops3_layout(N);
     constexpr int CS = curved3_stride(N);
     extern __shared__ __align__(16) unsigned char smem3[];
@@ -139,11 +166,10 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
     int* sNbr = sFpos + 4 * NP;
     int* sCode = sNbr + 4 * E;
     const int tid = threadIdx.x;
-    const Real* __restrict__ IcubT = p.ops + L.icub;
-    const Real* __restrict__ DrWT = p.ops + L.drw;
-    const Real* __restrict__ DsWT = p.ops + L.dsw;
-    const Real* __restrict__ DtWT = p.ops + L.dtw;
+    const Real* __restrict__ IcubB = p.ops + L.icub;
 
+    // the padding of the state rows and flux rows stays zero
+    for (int i = tid; i < E * 5 * NPP + E * 15 * NQP; i += THREADS) sU[i] = Real(0);
     for (int i = tid; i < 6 * NG * NFP; i += THREADS) sI2[i] = p.ops[L.i2 + i];
     for (int i = tid; i < NG; i += THREADS) sW[i] = p.ops[L.wg + i];
     for (int i = tid; i < NP * NP; i += THREADS) sMiT[i] = p.ops[L.mi + i];
@@ -156,7 +182,10 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
         __syncthreads();
         // ---- phase 0: rows, codes, affine geometry
         const Real* Ug = p.Us + e0 * 5 * NP;
-        for (int i = tid; i < ne * 5 * NP; i += THREADS) sU[i] = Ug[i];
+        for (int i = tid; i < ne * 5 * NP; i += THREADS) {
+            const int row = i / NP;
+            sU[row * NPP + (i - row * NP)] = Ug[i];
+        }
         for (int i = tid; i < ne * 4; i += THREADS) {
             const int e = i >> 2, f = i & 3;
             const int4 nb = p.conn[e0 + e];
@@ -195,12 +224,13 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
         // ---- phase 1: cubature-point fluxes
         for (int i = tid; i < ne * NQ; i += THREADS) {
             const int e = i / NQ, q = i - e * NQ;
-            const Real* ue = sU + e * 5 * NP;
+            const Real* ue = sU + e * 5 * NPP;
             Real u[5] = {0, 0, 0, 0, 0};
-            for (int j = 0; j < NP; ++j) {
-                const Real w = IcubT[j * NQ + q];
+#pragma unroll 2
+            for (int jb = 0; jb < NPP / 4; ++jb) {
+                const V4<Real> w = ldg4(IcubB + (jb * NQP + q) * 4);
 #pragma unroll
-                for (int v = 0; v < 5; ++v) u[v] += w * ue[v * NP + j];
+                for (int v = 0; v < 5; ++v) u[v] += dot4(w, lds4(ue + v * NPP + 4 * jb));
             }
             Real cof[9];
             const long long eg = e0 + e;
@@ -221,25 +251,30 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
                 // contravariant velocity and pressure direction for direction a
                 const Real c0 = cof[a], c1 = cof[3 + a], c2 = cof[6 + a];
                 const Real U = c0 * vx + c1 * vy + c2 * vz;
-                Real* out = sF + (e * 15 + a * 5) * NQ + q;
+                Real* out = sF + (e * 15 + a * 5) * NQP + q;
                 out[0] = u[0] * U;
-                out[NQ] = u[1] * U + pr * c0;
-                out[2 * NQ] = u[2] * U + pr * c1;
-                out[3 * NQ] = u[3] * U + pr * c2;
-                out[4 * NQ] = H * U;
+                out[NQP] = u[1] * U + pr * c0;
+                out[2 * NQP] = u[2] * U + pr * c1;
+                out[3 * NQP] = u[3] * U + pr * c2;
+                out[4 * NQP] = H * U;
             }
         }
         __syncthreads();
-        // ---- phase 2: volume term
-        for (int i = tid; i < ne * 5 * NP; i += THREADS) {
-            const int e = i / (5 * NP), r = i - e * 5 * NP, v = r / NP, n = r - v * NP;
-            const Real* fr = sF + (e * 15 + v) * NQ;
-            const Real* fs = fr + 5 * NQ;
-            const Real* ft = fs + 5 * NQ;
-            Real acc = 0;
-            for (int q = 0; q < NQ; ++q)
-                acc += DrWT[q * NP + n] * fr[q] + DsWT[q * NP + n] * fs[q] + DtWT[q * NP + n] * ft[q];
-            sR[i] = acc;
+        // ---- phase 2: volume term, one direction a per item (summed in phase 4)
+        for (int i = tid; i < 3 * ne * NP; i += THREADS) {
+            const int n = i % NP, rest = i / NP, e = rest % ne, a = rest / ne;
+            const Real* DB = p.ops + (a == 0 ? L.drw : a == 1 ? L.dsw : L.dtw);
+            const Real* fa = sF + (e * 15 + a * 5) * NQP;
+            Real acc[5] = {0, 0, 0, 0, 0};
+#pragma unroll 2
+            for (int qb = 0; qb < NQP / 4; ++qb) {
+                const V4<Real> d = ldg4(DB + (qb * NPP + n) * 4);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) acc[v] += dot4(d, lds4(fa + v * NQP + 4 * qb));
+            }
+            Real* out = sR + (a * E + e) * 5 * NP + n;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) out[v * NP] = acc[v];
         }
         // ---- phase 3: face-frame points
         for (int i = tid; i < ne * 4 * NG; i += THREADS) {
@@ -247,13 +282,13 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
             const int code = sCode[e * 4 + f];
             const long long eg = e0 + e;
             const Real* I2o = sI2 + (code3_own(code) * NG + g) * NFP;
-            const Real* ue = sU + e * 5 * NP;
+            const Real* ue = sU + e * 5 * NPP;
             Real um[5] = {0, 0, 0, 0, 0}, up[5];
             for (int n = 0; n < NFP; ++n) {
                 const Real w = I2o[n];
                 const int node = sFmask[f * NFP + n];
 #pragma unroll
-                for (int v = 0; v < 5; ++v) um[v] += w * ue[v * NP + node];
+                for (int v = 0; v < 5; ++v) um[v] += w * ue[v * NPP + node];
             }
             Real nx, ny, nz, sJ;
             if (eg < p.Kaff) {
@@ -314,7 +349,7 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
                 const Real* fs = sFs + ((e * 4 + f) * 5 + v) * NG;
                 for (int g = 0; g < NG; ++g) acc += I2o[g * NFP] * fs[g];
             }
-            sR[i] -= acc;
+            sR[i] = sR[i] + sR[E * 5 * NP + i] + sR[2 * E * 5 * NP + i] - acc;
         }
         __syncthreads();
         // ---- phase 5: inverse mass and the stage update
@@ -331,7 +366,7 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
                 for (int j = 0; j < NP; ++j) Lv += mi[j * NP + n] * rr[j];
             }
             const long long at = e0 * 5 * NP + i;
-            p.Uout[at] = stage_value3(p, at, sU[i], Lv);
+            p.Uout[at] = stage_value3(p, at, sU[(e * 5 + v) * NPP + n], Lv);
         }
     }
 }

@@ -51,24 +51,25 @@ class TetMesh:
 
 
 def _kuhn(n_cells, vid, coord):
-    """Six tetrahedra per cell; vid(i, j, l) -> global number, coord(i, j, l)
-    -> coordinates of lattice point (i, j, l) (unwrapped)."""
+    """Six tetrahedra per cell, cells ordered l (z) outer, j, i inner, the six
+    paths through each cell in the order of the axis permutations.
+    vid(I, J, L) -> global numbers and coord(I, J, L) -> [..., 3] coordinates
+    of lattice points (unwrapped), both on integer arrays."""
     nx, ny, nz = n_cells
-    E, V = [], []
-    steps = np.eye(3, dtype=np.int64)
-    for l in range(nz):
-        for j in range(ny):
-            for i in range(nx):
-                for perm in permutations(range(3)):
-                    p = np.array([i, j, l])
-                    path = [p.copy()]
-                    for ax in perm:
-                        p = p + steps[ax]
-                        path.append(p.copy())
-                    E.append([vid(*q) for q in path])
-                    V.append([coord(*q) for q in path])
-    EToV = np.array(E, dtype=np.int64)
-    verts = np.array(V, dtype=np.float64)
+    L, J, I = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cells = np.stack([I.ravel(), J.ravel(), L.ravel()], axis=1)            # [C, 3]
+    paths = []
+    for perm in permutations(range(3)):
+        p = [np.zeros(3, dtype=np.int64)]
+        for ax in perm:
+            q = p[-1].copy()
+            q[ax] += 1
+            p.append(q)
+        paths.append(np.stack(p))                                           # [4, 3]
+    pts = cells[:, None, None, :] + np.stack(paths)[None]                   # [C, 6, 4, 3]
+    pts = pts.reshape(-1, 4, 3)
+    EToV = vid(pts[..., 0], pts[..., 1], pts[..., 2]).astype(np.int64)
+    verts = coord(pts[..., 0], pts[..., 1], pts[..., 2]).astype(np.float64)
     vol = np.einsum('ki,ki->k', np.cross(verts[:, 1] - verts[:, 0], verts[:, 2] - verts[:, 0]),
                     verts[:, 3] - verts[:, 0])
     flip = vol < 0
@@ -86,7 +87,7 @@ def box(n, L=10.0, jitter=0.1, seed=1000):
         return (i % n) + n * ((j % n) + n * (l % n))
 
     def coord(i, j, l):
-        return np.array([i * h, j * h, l * h]) + jit[i % n, j % n, l % n]
+        return np.stack([i * h, j * h, l * h], axis=-1) + jit[i % n, j % n, l % n]
 
     EToV, verts = _kuhn((n, n, n), vid, coord)
     bc = np.zeros((len(EToV), 4), dtype=np.int8)
@@ -94,6 +95,9 @@ def box(n, L=10.0, jitter=0.1, seed=1000):
 
 
 def bump_channel(nx, ny, nz, Lx=3.0, Ly=1.5, H=0.8, A=0.1, R=0.4, Zd=0.4, jitter=0.1, seed=2000):
+    # dz'/dz = 1 - 2 bump (1 - z/Zd) / Zd >= 1 - 2 A / Zd: keep it >= 1/2
+    if Zd < 4.0 * A:
+        raise ValueError("the bump map needs Zd >= 4 A to stay well inside one-to-one")
     rng = np.random.default_rng(seed)
     hx, hy, hz = Lx / nx, Ly / ny, H / nz
     jit = rng.uniform(-jitter, jitter, size=(nx + 1, ny, nz + 1, 3)) * np.array([hx, hy, hz])
@@ -104,7 +108,7 @@ def bump_channel(nx, ny, nz, Lx=3.0, Ly=1.5, H=0.8, A=0.1, R=0.4, Zd=0.4, jitter
         return i + (nx + 1) * ((j % ny) + ny * l)
 
     def coord(i, j, l):
-        return np.array([i * hx, j * hy, l * hz]) + jit[i, j % ny, l]
+        return np.stack([i * hx, j * hy, l * hz], axis=-1) + jit[i, j % ny, l]
 
     EToV, verts = _kuhn((nx, ny, nz), vid, coord)
     K = len(EToV)
