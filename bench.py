@@ -579,6 +579,7 @@ def run_tet(args):
     h = B.dg_tet_mesh_upload(ctx, N, m.EToV, m.bc, wl["xyz"], p)
     info = B.dg_mesh_info(ctx, h)
     B.dg_set_state(ctx, h, wl["U0"])
+    tuned = B.dg_autotune(ctx, h, 5)       # elements per tile for this mesh
     step = B.dg_step_lserk if args.integrator == "lserk" else B.dg_step
     nstage = 5 if args.integrator == "lserk" else 3
 
@@ -651,6 +652,7 @@ def run_tet(args):
                              % args.flush_mb,
                        "parallelism": "replicas (one independent solve per GPU)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "tile_e": tuned[0], "autotune_ms_per_step": {str(k): v for k, v in tuned[1].items()},
             "residual_linf": [float(x) for x in linf]}
     print(json.dumps(line), flush=True)
     return 0

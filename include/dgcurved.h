@@ -43,9 +43,9 @@
  *     so both elements of a face evaluate the flux at the same points.
  *   - dg_set_state, dg_get_state, dg_set_state_device, dg_get_state_device,
  *     dg_eval_rhs, dg_step, dg_step_lserk, dg_residual, dg_mesh_info,
- *     dg_mesh_bytes, dg_mesh_free, dg_set_profiling and dg_kernel_times
- *     accept tetrahedral meshes with the five-variable layout; dg_batch_step,
- *     dg_prolong and dg_autotune return DG_EINVAL for them.  Precisions
+ *     dg_mesh_bytes, dg_mesh_free, dg_set_profiling, dg_kernel_times and
+ *     dg_autotune accept tetrahedral meshes with the five-variable layout;
+ *     dg_batch_step and dg_prolong return DG_EINVAL for them.  Precisions
  *     DG_FP32 and DG_FP64_DEBUG; no artificial viscosity.
  */
 #ifndef DGCURVED_H
@@ -240,10 +240,11 @@ int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* ms, const double* dts, int 
  * DG_EINVAL otherwise.  Synchronises the context's stream. */
 int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to);
 
-/* Tile-size autotuner for the CUDA-core path (DG_FP32, DG_FP64_DEBUG): times
+/* Tile-size autotuner for the CUDA-core paths (DG_FP32, DG_FP64_DEBUG; triangle
+ * and tetrahedral meshes, each with its own tile sizes): times
  * nsteps (1..1000) SSP-RK3 steps of mesh m with dt = 0 (the full work of a
  * step, the state unchanged; it is also saved and restored) for each
- * candidate tile size -- E/2, E, 3E/2, 2E, 3E elements per CTA around the
+ * candidate tile size -- E/4, E/2, E, 3E/2, 2E, 3E elements per CTA around the
  * degree's default E, where the tile's shared-memory layout fits one CTA --
  * and keeps the fastest for m.  The choice also applies to the context's
  * other meshes of the same degree, precision and viscosity setting, and to

@@ -101,6 +101,7 @@ StageArgs3<Real> make_args3(const MeshData& m, const void* Us, const void* Un, v
     s.Kaff = m.Kaff;
     s.gamma = (Real)m.p.gamma;
     for (int v = 0; v < 5; ++v) s.uinf[v] = (Real)m.p.u_inf[v];
+    s.tile_e = m.tile_e;
     return s;
 }
 
@@ -424,6 +425,10 @@ int dg_tet_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const
         cudaMemset(m->U[0], 0, nstate * rs) != cudaSuccess) {
         api_free_mesh(m);
         return api_fail(ctx, DG_ECUDA, "mesh upload copy failed");
+    }
+    {   // a tile size tuned earlier for this kind of mesh
+        auto it = ctx->tuned_e.find(3000 + N * 32 + (int)rs * 2);
+        if (it != ctx->tuned_e.end()) m->tile_e = it->second;
     }
     const dg_mesh h = ctx->next_id++;
     ctx->meshes[h] = m;

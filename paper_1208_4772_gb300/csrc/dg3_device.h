@@ -74,11 +74,13 @@ struct StageArgs3 {
     long long K, Kaff;
     Real gamma;
     Real uinf[5];
+    int tile_e;         // elements per tile (0: the default of the degree and real type)
 };
 
 bool supported_degree3(int N);
 int prepare_stage3(int N, int rsize);
-size_t stage3_smem(int N, int rsize);
+int tile3_default(int N, int rsize);
+bool tile3_fits(int N, int rsize, int E);
 int launch_stage3(int N, const StageArgs3<float>& a, cudaStream_t st);
 int launch_stage3(int N, const StageArgs3<double>& a, cudaStream_t st);
 

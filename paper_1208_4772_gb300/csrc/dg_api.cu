@@ -19,6 +19,7 @@
 #include <thread>
 #include <vector>
 
+#include "dg3_device.h"
 #include "dg_device.h"
 #include "dgcurved.h"
 #include "refops.h"
@@ -80,7 +81,7 @@ bool dispatch_tile_fits(int N, int e, int av) {
     }
     return false;
 }
-int tune_key(int N, size_t rsize, int av) { return N * 32 + (int)rsize * 2 + (av ? 1 : 0); }
+int tune_key(int dim, int N, size_t rsize, int av) { return dim * 1000 + N * 32 + (int)rsize * 2 + (av ? 1 : 0); }
 
 template <typename Real>
 int dispatch_stage(int N, const StageArgs<Real>& a, int av, cudaStream_t st) {
@@ -977,7 +978,7 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
         return fail(ctx, DG_ECUDA, "mesh upload memset failed");
     }
     if (!tensor_prec(m->prec)) {   // a tile size tuned earlier for this kind of mesh
-        auto it = ctx->tuned_e.find(tune_key(m->N, m->rsize, m->p.av_on));
+        auto it = ctx->tuned_e.find(tune_key(m->dim, m->N, m->rsize, m->p.av_on));
         if (it != ctx->tuned_e.end()) m->tile_e = it->second;
     }
     const dg_mesh h = ctx->next_id++;
@@ -1252,7 +1253,6 @@ int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
     if (nsteps < 1 || nsteps > 1000) return fail(ctx, DG_EINVAL, "nsteps must be in 1..1000");
     if (ncand_out) *ncand_out = 0;
-    if (m->dim == 3) return fail(ctx, DG_EINVAL, "the tile autotuner covers the triangle path");
     if (tensor_prec(m->prec)) {   // fixed tiles of 32 elements = the 128 rows of the products
         *tile_e_out = 32;
         return DG_OK;
@@ -1260,17 +1260,21 @@ int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t
     cudaSetDevice(ctx->device);
     const bool dbl = m->rsize == 8;
     const int av = m->p.av_on;
-    const int E0 = dbl ? dispatch_tile_default<double>(m->N) : dispatch_tile_default<float>(m->N);
+    const int E0 = m->dim == 3 ? tile3_default(m->N, (int)m->rsize)
+                   : dbl       ? dispatch_tile_default<double>(m->N)
+                               : dispatch_tile_default<float>(m->N);
     std::vector<int> cands;
-    for (int twice : {1, 2, 3, 4, 6}) {   // E0/2, E0, 3E0/2, 2E0, 3E0
-        const int e = std::max(1, E0 * twice / 2);
-        const bool fits = dbl ? dispatch_tile_fits<double>(m->N, e, av) : dispatch_tile_fits<float>(m->N, e, av);
+    for (int quarters : {1, 2, 4, 6, 8, 12}) {   // E0/4, E0/2, E0, 3E0/2, 2E0, 3E0
+        const int e = std::max(1, E0 * quarters / 4);
+        const bool fits = m->dim == 3 ? tile3_fits(m->N, (int)m->rsize, e)
+                          : dbl       ? dispatch_tile_fits<double>(m->N, e, av)
+                                      : dispatch_tile_fits<float>(m->N, e, av);
         if (fits && std::find(cands.begin(), cands.end(), e) == cands.end()) cands.push_back(e);
     }
     if (cands.empty()) return fail(ctx, DG_EINVAL, "no tile size fits the shared memory");
     // timed steps with dt = 0 (the full work of a step, the state unchanged);
     // the state is saved and restored all the same
-    const size_t bytes = (size_t)m->K * 4 * m->Np * m->rsize;
+    const size_t bytes = (size_t)m->K * m->nvar * m->Np * m->rsize;
     CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
     CUDA_OK(ctx, cudaMemcpyAsync(m->rhs, m->U[0], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     cudaEvent_t ea = nullptr, eb = nullptr;
@@ -1305,11 +1309,11 @@ int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t
     reset_batch(ctx);
     if (err) return fail(ctx, DG_ECUDA, std::string("autotune step failed: ") + cudaGetErrorString((cudaError_t)err));
     if (ce != cudaSuccess || cs != cudaSuccess) return fail(ctx, DG_ECUDA, "autotune state restore failed");
-    const int key = tune_key(m->N, m->rsize, av);
+    const int key = tune_key(m->dim, m->N, m->rsize, av);
     ctx->tuned_e[key] = m->tile_e;
     for (auto& kv : ctx->meshes) {   // the context's other meshes of this kind follow
         MeshData* o = kv.second;
-        if (o == m || tensor_prec(o->prec) || tune_key(o->N, o->rsize, o->p.av_on) != key) continue;
+        if (o == m || tensor_prec(o->prec) || tune_key(o->dim, o->N, o->rsize, o->p.av_on) != key) continue;
         o->tile_e = m->tile_e;
         drop_graphs(*o);
     }

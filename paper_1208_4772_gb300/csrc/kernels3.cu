@@ -22,24 +22,30 @@ namespace dgc {
 
 namespace {
 
+// Shared-memory layout of a CTA for tiles of E elements (offsets in reals).
 template <int N, typename Real>
 struct T3 {
     static constexpr int NP = np3_of(N), NFP = nfp3_of(N), NQ = nq3_of(N), NG = ng3_of(N);
     static constexpr int NPP = pad4(NP), NQP = pad4(NQ);
-    static constexpr int E = sizeof(Real) == 4 ? (N <= 2 ? 16 : N == 3 ? 8 : 3) : (N <= 2 ? 8 : N == 3 ? 4 : 1);
     static constexpr int O_I2 = 0;
     static constexpr int O_W = O_I2 + 6 * NG * NFP;
     static constexpr int O_MI = O_W + NG;
     static constexpr int O_U = pad4(O_MI + NP * NP);   // [E][5][NPP]
-    static constexpr int O_F = O_U + E * 5 * NPP;      // [E][3][5][NQP] contravariant fluxes
-    static constexpr int O_NB = O_F + E * 15 * NQP;    // [E][4][5][NFP] neighbours' face nodes
-    static constexpr int O_FS = O_NB + E * 20 * NFP;   // [E][4][5][NG] w sJ F*
-    static constexpr int O_R = O_FS + E * 20 * NG;     // [3][E][5][NP] volume parts, then R
-    static constexpr int O_G = O_R + 3 * E * 5 * NP;   // [E][16] affine cofactors, 1/J
-    static constexpr int O_END = O_G + E * 16;
-    static constexpr int NINT = 4 * NFP + 4 * NP + 8 * E;
-    static constexpr size_t BYTES = (size_t)O_END * sizeof(Real) + (size_t)NINT * sizeof(int);
+    int O_F, O_NB, O_FS, O_R, O_G, O_END;
+    size_t bytes;
+    __host__ __device__ constexpr explicit T3(int E)
+        : O_F(O_U + E * 5 * NPP),                      // [E][3][5][NQP] contravariant fluxes
+          O_NB(O_F + E * 15 * NQP),                    // [E][4][5][NFP] neighbours' face nodes
+          O_FS(O_NB + E * 20 * NFP),                   // [E][4][5][NG] w sJ F*
+          O_R(O_FS + E * 20 * NG),                     // [3][E][5][NP] volume parts, then R
+          O_G(O_R + 3 * E * 5 * NP),                   // [E][16] affine cofactors, 1/J
+          O_END(O_G + E * 16),
+          bytes((size_t)O_END * sizeof(Real) + (size_t)(4 * NFP + 4 * NP + 8 * E) * sizeof(int)) {}
+    static constexpr int default_e() { return sizeof(Real) == 4 ? (N <= 2 ? 16 : N == 3 ? 8 : 3) : (N <= 2 ? 8 : N == 3 ? 4 : 1); }
 };
+
+// Largest dynamic shared memory of one CTA.
+constexpr size_t SMEM3_MAX = 232448;
 
 // Four consecutive reals by one 16-byte access (two for double).
 template <typename Real>
@@ -146,22 +152,24 @@ __device__ __forceinline__ Real stage_value3(const StageArgs3<Real>& p, long lon
 
 template <int N, typename Real>
 __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> p) {
-    using T = T3<N, Real>;
-    constexpr int NP = T::NP, NFP = T::NFP, NQ = T::NQ, NG = T::NG, E = T::E, NPP = T::NPP, NQP = T::NQP;
+    using TT = T3<N, Real>;
+    constexpr int NP = TT::NP, NFP = TT::NFP, NQ = TT::NQ, NG = TT::NG, NPP = TT::NPP, NQP = TT::NQP;
+    const int E = p.tile_e;
+    const TT T(E);
     constexpr Ops3Layout L = ops3_layout(N);
     constexpr int CS = curved3_stride(N);
     extern __shared__ __align__(16) unsigned char smem3[];
     Real* S = reinterpret_cast<Real*>(smem3);
-    Real* sI2 = S + T::O_I2;
-    Real* sW = S + T::O_W;
-    Real* sMiT = S + T::O_MI;
-    Real* sU = S + T::O_U;
-    Real* sF = S + T::O_F;
-    Real* sNb = S + T::O_NB;
-    Real* sFs = S + T::O_FS;
-    Real* sR = S + T::O_R;
-    Real* sG = S + T::O_G;
-    int* sFmask = reinterpret_cast<int*>(S + T::O_END);
+    Real* sI2 = S + TT::O_I2;
+    Real* sW = S + TT::O_W;
+    Real* sMiT = S + TT::O_MI;
+    Real* sU = S + TT::O_U;
+    Real* sF = S + T.O_F;
+    Real* sNb = S + T.O_NB;
+    Real* sFs = S + T.O_FS;
+    Real* sR = S + T.O_R;
+    Real* sG = S + T.O_G;
+    int* sFmask = reinterpret_cast<int*>(S + T.O_END);
     int* sFpos = sFmask + 4 * NFP;
     int* sNbr = sFpos + 4 * NP;
     int* sCode = sNbr + 4 * E;
@@ -373,8 +381,11 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
 
 template <int N, typename Real>
 int prepare_t(void) {
-    const cudaError_t e = cudaFuncSetAttribute(stage3_kernel<N, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)T3<N, Real>::BYTES);
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, stage3_kernel<N, Real>);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stage3_kernel<N, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(SMEM3_MAX - fa.sharedSizeBytes));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return (int)e;
@@ -384,29 +395,40 @@ int prepare_t(void) {
 
 template <int N, typename Real>
 int launch_t(const StageArgs3<Real>& a, cudaStream_t st) {
-    using T = T3<N, Real>;
-    static int grid = 0;
-    if (grid == 0) {
-        int dev = 0, nsm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const int occ = std::max(1, resident_ctas((const void*)stage3_kernel<N, Real>, THREADS, T::BYTES));
-        grid = nsm * occ;
-    }
-    const long long ntiles = (a.K + T::E - 1) / T::E;
-    const int g = (int)std::min<long long>(ntiles, grid);
+    const int E = a.tile_e > 0 ? a.tile_e : T3<N, Real>::default_e();
+    const size_t bytes = T3<N, Real>(E).bytes;
+    if (bytes > SMEM3_MAX) return (int)cudaErrorInvalidValue;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int occ = std::max(1, resident_ctas((const void*)stage3_kernel<N, Real>, THREADS, bytes));
+    const long long ntiles = (a.K + E - 1) / E;
+    const int g = (int)std::min<long long>(ntiles, (long long)nsm * occ);
     if (g <= 0) return 0;
-    stage3_kernel<N, Real><<<g, THREADS, T::BYTES, st>>>(a);
+    StageArgs3<Real> b = a;
+    b.tile_e = E;
+    stage3_kernel<N, Real><<<g, THREADS, bytes, st>>>(b);
     return (int)cudaGetLastError();
+}
+
+template <int N, typename Real>
+bool fits_t(int E) {
+    return E >= 1 && T3<N, Real>(E).bytes <= SMEM3_MAX;
 }
 
 }  // namespace
 
 bool supported_degree3(int N) { return N >= 2 && N <= 4; }
 
-size_t stage3_smem(int N, int rsize) {
-    if (rsize == 8) return N == 2 ? T3<2, double>::BYTES : N == 3 ? T3<3, double>::BYTES : T3<4, double>::BYTES;
-    return N == 2 ? T3<2, float>::BYTES : N == 3 ? T3<3, float>::BYTES : T3<4, float>::BYTES;
+int tile3_default(int N, int rsize) {
+    if (rsize == 8) return N == 2 ? T3<2, double>::default_e() : N == 3 ? T3<3, double>::default_e()
+                                                                          : T3<4, double>::default_e();
+    return N == 2 ? T3<2, float>::default_e() : N == 3 ? T3<3, float>::default_e() : T3<4, float>::default_e();
+}
+
+bool tile3_fits(int N, int rsize, int E) {
+    if (rsize == 8) return N == 2 ? fits_t<2, double>(E) : N == 3 ? fits_t<3, double>(E) : fits_t<4, double>(E);
+    return N == 2 ? fits_t<2, float>(E) : N == 3 ? fits_t<3, float>(E) : fits_t<4, float>(E);
 }
 
 int prepare_stage3(int N, int rsize) {

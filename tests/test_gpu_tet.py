@@ -149,9 +149,35 @@ def test_tet_argument_errors(B, ctx):
     with pytest.raises(B.DgError):
         B.dg_tet_mesh_upload(ctx, 5, m.EToV, m.bc, case["xyz"], p)
     h = B.dg_tet_mesh_upload(ctx, 2, m.EToV, m.bc, case["xyz"], p)
-    for call in (lambda: B.dg_autotune(ctx, h), lambda: B.dg_prolong(ctx, h, h),
+    for call in (lambda: B.dg_prolong(ctx, h, h),
                  lambda: B.dg_batch_step(ctx, [h], [1e-3], 1)):
         with pytest.raises(B.DgError) as e:
             call()
         assert e.value.status == B.DG_EINVAL
     B.dg_mesh_free(ctx, h)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_tet_autotune_keeps_state_and_results(B, ctx, prec):
+    """The tile autotuner on a tetrahedral mesh: candidates timed, state
+    unchanged, and the tuned tiles step bitwise like the default ones (each
+    element's arithmetic is independent of its tile)."""
+    case, U, h, o = setup(B, ctx, "bump", 3, prec, size="medium")
+    dt = 0.5 * states.time_step3(case["mesh"].verts, U, 3)
+    U0 = B.dg_get_state(ctx, h)
+    best, table = B.dg_autotune(ctx, h, 2)
+    assert len(table) >= 2 and best in table and all(t > 0 for t in table.values()), table
+    assert np.array_equal(B.dg_get_state(ctx, h), U0)
+    B.dg_step(ctx, h, dt, 2)
+    Ut = B.dg_get_state(ctx, h)
+    B.dg_mesh_free(ctx, h)
+    c2 = B.dg_create(0)
+    try:
+        m = case["mesh"]
+        h2 = B.dg_tet_mesh_upload(c2, 3, m.EToV, m.bc, case["xyz"], B.make_params(u_inf=case["u_inf"], prec=prec))
+        B.dg_set_state(c2, h2, U)
+        B.dg_step(c2, h2, dt, 2)
+        Ud = B.dg_get_state(c2, h2)
+    finally:
+        B.dg_destroy(c2)
+    assert np.array_equal(Ut, Ud)
