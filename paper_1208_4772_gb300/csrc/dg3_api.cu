@@ -55,7 +55,14 @@ std::vector<double> pack_ops3(const RefOps3& R) {
             o[L.dsw + at] = R.DsW[(size_t)n * NQ + q];
             o[L.dtw + at] = R.DtW[(size_t)n * NQ + q];
         }
-    std::copy(R.I2.begin(), R.I2.end(), o.begin() + L.i2);
+    const int NFP = R.Nfp, NFPP = pad4(NFP), NGP = pad4(NG);
+    for (int c = 0; c < 6; ++c)
+        for (int g = 0; g < NG; ++g)
+            for (int i = 0; i < NFP; ++i) {
+                const double v = R.I2[((size_t)c * NG + g) * NFP + i];
+                o[L.i2 + ((size_t)c * NG + g) * NFPP + i] = v;
+                o[L.i2t + ((size_t)c * NFP + i) * NGP + g] = v;
+            }
     for (int g = 0; g < NG; ++g) o[L.wg + g] = R.wg[g];
     for (int j = 0; j < NP; ++j)
         for (int n = 0; n < NP; ++n) o[L.mi + (size_t)j * NP + n] = R.Mrefinv[(size_t)n * NP + j];

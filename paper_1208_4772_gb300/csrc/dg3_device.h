@@ -14,24 +14,27 @@ __host__ __device__ constexpr int ng3_of(int N) { return q_of(N) * q_of(N); }
 __host__ __device__ constexpr int pad4(int n) { return (n + 3) / 4 * 4; }
 
 // Operator table of degree N in the real type (offsets in elements, each a
-// multiple of 4; NPP = pad4(NP), NQP = pad4(NQ), padding entries zero):
+// multiple of 4; NPP = pad4(NP), NQP = pad4(NQ), NFPP = pad4(NFP),
+// NGP = pad4(NG), padding entries zero):
 //   Icub as [NPP/4][NQP][4]: (j, q) at ((j/4) NQP + q) 4 + j%4
 //   D_r^T W, D_s^T W, D_t^T W as [NQP/4][NPP][4]: (q, n) at ((q/4) NPP + n) 4 + q%4
-//   I2 [6][NG][NFP] (face nodes -> face-frame points, by orientation),
+//   I2 [6][NG][NFPP]: face nodes -> face-frame points, by orientation
+//   I2^T [6][NFP][NGP]: its transpose (the lift to the face nodes)
 //   face weights [NG], (M_ref^-1)^T [NP][NP].
 struct Ops3Layout {
-    int icub, drw, dsw, dtw, i2, wg, mi, total;
+    int icub, drw, dsw, dtw, i2, i2t, wg, mi, total;
 };
 __host__ __device__ constexpr Ops3Layout ops3_layout(int N) {
     const int NP = np3_of(N), NQ = nq3_of(N), NG = ng3_of(N), NFP = nfp3_of(N);
-    const int NPP = pad4(NP), NQP = pad4(NQ);
+    const int NPP = pad4(NP), NQP = pad4(NQ), NFPP = pad4(NFP), NGP = pad4(NG);
     Ops3Layout o{};
     o.icub = 0;
     o.drw = o.icub + NPP * NQP;
     o.dsw = o.drw + NQP * NPP;
     o.dtw = o.dsw + NQP * NPP;
     o.i2 = o.dtw + NQP * NPP;
-    o.wg = pad4(o.i2 + 6 * NG * NFP);
+    o.i2t = o.i2 + 6 * NG * NFPP;
+    o.wg = o.i2t + 6 * NFP * NGP;
     o.mi = pad4(o.wg + NG);
     o.total = pad4(o.mi + NP * NP);
     return o;

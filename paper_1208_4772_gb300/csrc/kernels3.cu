@@ -26,22 +26,25 @@ namespace {
 template <int N, typename Real>
 struct T3 {
     static constexpr int NP = np3_of(N), NFP = nfp3_of(N), NQ = nq3_of(N), NG = ng3_of(N);
-    static constexpr int NPP = pad4(NP), NQP = pad4(NQ);
-    static constexpr int O_I2 = 0;
-    static constexpr int O_W = O_I2 + 6 * NG * NFP;
-    static constexpr int O_MI = O_W + NG;
-    static constexpr int O_U = pad4(O_MI + NP * NP);   // [E][5][NPP]
-    int O_F, O_NB, O_FS, O_R, O_G, O_END;
+    static constexpr int NPP = pad4(NP), NQP = pad4(NQ), NFPP = pad4(NFP), NGP = pad4(NG);
+    static constexpr int O_I2 = 0;                           // [6][NG][NFPP]
+    static constexpr int O_I2T = O_I2 + 6 * NG * NFPP;       // [6][NFP][NGP]
+    static constexpr int O_W = O_I2T + 6 * NFP * NGP;
+    static constexpr int O_MI = pad4(O_W + NG);
+    static constexpr int O_U = pad4(O_MI + NP * NP);         // [E][5][NPP]
+    int O_F, O_UF, O_NB, O_FS, O_T, O_R, O_G, O_END;
     size_t bytes;
     __host__ __device__ constexpr explicit T3(int E)
-        : O_F(O_U + E * 5 * NPP),                      // [E][3][5][NQP] contravariant fluxes
-          O_NB(O_F + E * 15 * NQP),                    // [E][4][5][NFP] neighbours' face nodes
-          O_FS(O_NB + E * 20 * NFP),                   // [E][4][5][NG] w sJ F*
-          O_R(O_FS + E * 20 * NG),                     // [3][E][5][NP] volume parts, then R
-          O_G(O_R + 3 * E * 5 * NP),                   // [E][16] affine cofactors, 1/J
+        : O_F(O_U + E * 5 * NPP),          // [E][3][5][NQP] contravariant fluxes
+          O_UF(O_F + E * 15 * NQP),        // [E][4][5][NFPP] own face nodes
+          O_NB(O_UF + E * 20 * NFPP),      // [E][4][5][NFPP] neighbours' face nodes
+          O_FS(O_NB + E * 20 * NFPP),      // [E][4][5][NGP] w sJ F*
+          O_T(O_FS + E * 20 * NGP),        // [E][4][5][NFPP] lifted face terms
+          O_R(O_T + E * 20 * NFPP),        // [3][E][5][NP] volume parts, then R
+          O_G(O_R + 3 * E * 5 * NP),       // [E][16] affine cofactors, 1/J
           O_END(O_G + E * 16),
           bytes((size_t)O_END * sizeof(Real) + (size_t)(4 * NFP + 4 * NP + 8 * E) * sizeof(int)) {}
-    static constexpr int default_e() { return sizeof(Real) == 4 ? (N <= 2 ? 16 : N == 3 ? 8 : 3) : (N <= 2 ? 8 : N == 3 ? 4 : 1); }
+    static constexpr int default_e() { return sizeof(Real) == 4 ? (N <= 2 ? 8 : N == 3 ? 4 : 2) : (N <= 2 ? 4 : N == 3 ? 2 : 1); }
 };
 
 // Largest dynamic shared memory of one CTA.
@@ -154,6 +157,7 @@ template <int N, typename Real>
 __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> p) {
     using TT = T3<N, Real>;
     constexpr int NP = TT::NP, NFP = TT::NFP, NQ = TT::NQ, NG = TT::NG, NPP = TT::NPP, NQP = TT::NQP;
+    constexpr int NFPP = TT::NFPP, NGP = TT::NGP, NH = (NP + 1) / 2;
     const int E = p.tile_e;
     const TT T(E);
     constexpr Ops3Layout L = ops3_layout(N);
@@ -161,12 +165,15 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
     extern __shared__ __align__(16) unsigned char smem3[];
     Real* S = reinterpret_cast<Real*>(smem3);
     Real* sI2 = S + TT::O_I2;
+    Real* sI2T = S + TT::O_I2T;
     Real* sW = S + TT::O_W;
     Real* sMiT = S + TT::O_MI;
     Real* sU = S + TT::O_U;
     Real* sF = S + T.O_F;
+    Real* sUf = S + T.O_UF;
     Real* sNb = S + T.O_NB;
     Real* sFs = S + T.O_FS;
+    Real* sT = S + T.O_T;
     Real* sR = S + T.O_R;
     Real* sG = S + T.O_G;
     int* sFmask = reinterpret_cast<int*>(S + T.O_END);
@@ -176,9 +183,9 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
     const int tid = threadIdx.x;
     const Real* __restrict__ IcubB = p.ops + L.icub;
 
-    // the padding of the state rows and flux rows stays zero
-    for (int i = tid; i < E * 5 * NPP + E * 15 * NQP; i += THREADS) sU[i] = Real(0);
-    for (int i = tid; i < 6 * NG * NFP; i += THREADS) sI2[i] = p.ops[L.i2 + i];
+    // the padding of the state, flux, face-node and face-flux rows stays zero
+    for (int i = tid; i < T.O_T - TT::O_U; i += THREADS) sU[i] = Real(0);
+    for (int i = tid; i < 6 * NG * NFPP + 6 * NFP * NGP; i += THREADS) sI2[i] = p.ops[L.i2 + i];
     for (int i = tid; i < NG; i += THREADS) sW[i] = p.ops[L.wg + i];
     for (int i = tid; i < NP * NP; i += THREADS) sMiT[i] = p.ops[L.mi + i];
     for (int i = tid; i < 4 * NFP + 4 * NP; i += THREADS) sFmask[i] = p.opsi[i];
@@ -219,14 +226,15 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
             g[9] = Real(1) / det;
         }
         __syncthreads();
-        // neighbours' face nodes
+        // own and neighbours' face-node values, rows of NFPP
         for (int i = tid; i < ne * 20 * NFP; i += THREADS) {
-            const int e = i / (20 * NFP), r = i - e * 20 * NFP, f = r / (5 * NFP), r2 = r - f * 5 * NFP;
-            const int v = r2 / NFP, n = r2 - v * NFP;
+            const int row = i / NFP, n = i - row * NFP;   // row = (e * 4 + f) * 5 + v
+            const int e = row / 20, f = (row / 5) & 3, v = row % 5;
             const int code = sCode[e * 4 + f];
+            sUf[row * NFPP + n] = sU[(e * 5 + v) * NPP + sFmask[f * NFP + n]];
             if (code3_bc(code) == 0) {
                 const long long nb = sNbr[e * 4 + f];
-                sNb[i] = p.Us[nb * 5 * NP + v * NP + sFmask[code3_face(code) * NFP + n]];
+                sNb[row * NFPP + n] = p.Us[nb * 5 * NP + v * NP + sFmask[code3_face(code) * NFP + n]];
             }
         }
         // ---- phase 1: cubature-point fluxes
@@ -268,35 +276,47 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
             }
         }
         __syncthreads();
-        // ---- phase 2: volume term, one direction a per item (summed in phase 4)
-        for (int i = tid; i < 3 * ne * NP; i += THREADS) {
-            const int n = i % NP, rest = i / NP, e = rest % ne, a = rest / ne;
+        // ---- phase 2: volume term; one direction a and two nodes per item
+        const int n2 = 3 * ne * NH;
+        for (int i = tid; i < n2; i += THREADS) {
+            const int n = i % NH, rest = i / NH, e = rest % ne, a = rest / ne;
+            const int m = n + NH < NP ? n + NH : n;
             const Real* DB = p.ops + (a == 0 ? L.drw : a == 1 ? L.dsw : L.dtw);
             const Real* fa = sF + (e * 15 + a * 5) * NQP;
-            Real acc[5] = {0, 0, 0, 0, 0};
+            Real acc0[5] = {0, 0, 0, 0, 0}, acc1[5] = {0, 0, 0, 0, 0};
 #pragma unroll 2
             for (int qb = 0; qb < NQP / 4; ++qb) {
-                const V4<Real> d = ldg4(DB + (qb * NPP + n) * 4);
+                const V4<Real> d0 = ldg4(DB + (qb * NPP + n) * 4);
+                const V4<Real> d1 = ldg4(DB + (qb * NPP + m) * 4);
 #pragma unroll
-                for (int v = 0; v < 5; ++v) acc[v] += dot4(d, lds4(fa + v * NQP + 4 * qb));
+                for (int v = 0; v < 5; ++v) {
+                    const V4<Real> f = lds4(fa + v * NQP + 4 * qb);
+                    acc0[v] += dot4(d0, f);
+                    acc1[v] += dot4(d1, f);
+                }
             }
-            Real* out = sR + (a * E + e) * 5 * NP + n;
+            Real* out = sR + (a * E + e) * 5 * NP;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) out[v * NP] = acc[v];
+            for (int v = 0; v < 5; ++v) out[v * NP + n] = acc0[v];
+            if (n + NH < NP) {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) out[v * NP + m] = acc1[v];
+            }
         }
-        // ---- phase 3: face-frame points
-        for (int i = tid; i < ne * 4 * NG; i += THREADS) {
+        // ---- phase 3: face-frame points (first on the threads phase 2 left idle)
+        const int rot = (tid + THREADS - n2 % THREADS) % THREADS;
+        for (int i = rot; i < ne * 4 * NG; i += THREADS) {
             const int e = i / (4 * NG), r = i - e * 4 * NG, f = r / NG, g = r - f * NG;
             const int code = sCode[e * 4 + f];
             const long long eg = e0 + e;
-            const Real* I2o = sI2 + (code3_own(code) * NG + g) * NFP;
-            const Real* ue = sU + e * 5 * NPP;
-            Real um[5] = {0, 0, 0, 0, 0}, up[5];
-            for (int n = 0; n < NFP; ++n) {
-                const Real w = I2o[n];
-                const int node = sFmask[f * NFP + n];
+            const Real* I2o = sI2 + (code3_own(code) * NG + g) * NFPP;
+            const Real* uf = sUf + (e * 4 + f) * 5 * NFPP;
+            Real um[5] = {0, 0, 0, 0, 0}, up[5] = {0, 0, 0, 0, 0};
 #pragma unroll
-                for (int v = 0; v < 5; ++v) um[v] += w * ue[v * NPP + node];
+            for (int ib = 0; ib < NFPP / 4; ++ib) {
+                const V4<Real> w = lds4(I2o + 4 * ib);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) um[v] += dot4(w, lds4(uf + v * NFPP + 4 * ib));
             }
             Real nx, ny, nz, sJ;
             if (eg < p.Kaff) {
@@ -314,14 +334,13 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
             }
             const int bc = code3_bc(code);
             if (bc == 0) {
-                const Real* I2p = sI2 + (code3_nbr(code) * NG + g) * NFP;
-                const Real* nbv = sNb + (e * 4 + f) * 5 * NFP;
+                const Real* I2p = sI2 + (code3_nbr(code) * NG + g) * NFPP;
+                const Real* nbv = sNb + (e * 4 + f) * 5 * NFPP;
 #pragma unroll
-                for (int v = 0; v < 5; ++v) up[v] = 0;
-                for (int n = 0; n < NFP; ++n) {
-                    const Real w = I2p[n];
+                for (int ib = 0; ib < NFPP / 4; ++ib) {
+                    const V4<Real> w = lds4(I2p + 4 * ib);
 #pragma unroll
-                    for (int v = 0; v < 5; ++v) up[v] += w * nbv[v * NFP + n];
+                    for (int v = 0; v < 5; ++v) up[v] += dot4(w, lds4(nbv + v * NFPP + 4 * ib));
                 }
             } else if (bc == 1) {
                 const Real mn = um[1] * nx + um[2] * ny + um[3] * nz;
@@ -340,22 +359,36 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
             else
                 llf3(um, up, nx, ny, nz, p.gamma, F);
             const Real ws = sW[g] * sJ;
-            Real* out = sFs + (e * 4 + f) * 5 * NG + g;
+            Real* out = sFs + (e * 4 + f) * 5 * NGP + g;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) out[v * NG] = ws * F[v];
+            for (int v = 0; v < 5; ++v) out[v * NGP] = ws * F[v];
         }
         __syncthreads();
-        // ---- phase 4: R = vol - surf
+        // ---- phase 4a: lift of each face's flux to its face nodes
+        for (int i = tid; i < ne * 4 * NFP; i += THREADS) {
+            const int ef = i / NFP, n = i - ef * NFP;   // ef = e * 4 + f
+            const Real* I2t = sI2T + (code3_own(sCode[ef]) * NFP + n) * NGP;
+            const Real* fs = sFs + ef * 5 * NGP;
+            Real t[5] = {0, 0, 0, 0, 0};
+#pragma unroll 2
+            for (int gb = 0; gb < NGP / 4; ++gb) {
+                const V4<Real> w = lds4(I2t + 4 * gb);
+#pragma unroll
+                for (int v = 0; v < 5; ++v) t[v] += dot4(w, lds4(fs + v * NGP + 4 * gb));
+            }
+            Real* out = sT + ef * 5 * NFPP + n;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) out[v * NFPP] = t[v];
+        }
+        __syncthreads();
+        // ---- phase 4b: R = vol - surf
         for (int i = tid; i < ne * 5 * NP; i += THREADS) {
             const int e = i / (5 * NP), r = i - e * 5 * NP, v = r / NP, n = r - v * NP;
             Real acc = 0;
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
                 const int pos = sFpos[f * NP + n];
-                if (pos < 0) continue;
-                const Real* I2o = sI2 + code3_own(sCode[e * 4 + f]) * NG * NFP + pos;
-                const Real* fs = sFs + ((e * 4 + f) * 5 + v) * NG;
-                for (int g = 0; g < NG; ++g) acc += I2o[g * NFP] * fs[g];
+                if (pos >= 0) acc += sT[((e * 4 + f) * 5 + v) * NFPP + pos];
             }
             sR[i] = sR[i] + sR[E * 5 * NP + i] + sR[2 * E * 5 * NP + i] - acc;
         }
