@@ -24,6 +24,7 @@
 // tensor core works on the previous chunk (two smem buffers, one mbarrier
 // each).  Curved tiles run the CUDA-core tile body in the same launch.
 #pragma once
+#include <type_traits>
 #include <cstdio>
 #include <cstdlib>
 #include <cuda_bf16.h>
@@ -578,7 +579,9 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     // ---------------- face fluxes, once per face point, in place:
     // (F*.n - (sqrt(eps) q)*.n - F(Ubar).n) sJ replaces the trace of each
     // side.  F* from the other side of an in-tile face is -F*.
-    {
+    // (one loop per numerical flux, so that each carries only its own code)
+    auto face_phase = [&](auto flux_tag) {
+        constexpr int FLUX = decltype(flux_tag)::value;
         const int nface = sFL[0] * NG;
         const int nitems = nface + 32 * D::NQF;
         for (int it = tid; it < nitems; it += blockDim.x) {
@@ -624,7 +627,10 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 for (int w = 0; w < 4; ++w) Up[w] = sNbv[(ee * NF + fg) * S::NBV_C + w];
             }
             float Fn[4];
-            num_flux(p.flux, Um, Up, nx, ny, p.gamma, Fn);
+            if constexpr (FLUX == 1)
+                hllc_flux(Um, Up, nx, ny, p.gamma, Fn);
+            else
+                llf_flux(Um, Up, nx, ny, p.gamma, Fn);
             if constexpr (AV) {
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
@@ -652,7 +658,11 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                         (-Fn[w] - (sFb[nbl * 8 + w] * mx + sFb[nbl * 8 + 4 + w] * my)) * sJn;
             }
         }
-    }
+    };
+    if (p.flux == 1)
+        face_phase(std::integral_constant<int, 1>{});
+    else
+        face_phase(std::integral_constant<int, 0>{});
     if (tid == THREADS - 1) *next_tile = claim;
     __syncthreads();
 
