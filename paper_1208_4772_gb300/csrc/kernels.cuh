@@ -596,6 +596,20 @@ __device__ __forceinline__ void grad_tile(const StageArgs<Real>& p, Real* q_out,
     Real* sR = sGeo + E * 16;          // [e][m][v][NP]
     Real* sEps = sR + E * 8 * NP;
 
+    // q enters the stage only as sqrt(eps) q of its own element, so a tile
+    // whose elements all have eps = 0 needs none: it is neither computed nor
+    // written
+    {
+        __shared__ int s_visc;
+        __syncthreads();   // a previous tile of a persistent caller is done with s_visc
+        if (threadIdx.x == 0) s_visc = 0;
+        __syncthreads();
+        for (int e = threadIdx.x; e < t.ne; e += blockDim.x)
+            if (p.eps[t.e0 + e] > Real(0)) s_visc = 1;
+        __syncthreads();
+        if (!s_visc) return;
+    }
+
     const Real* ops = p.ops;
     if (t.curved) {
         copy_to_smem(sIcubT, ops + L.icub, NP * NQ);

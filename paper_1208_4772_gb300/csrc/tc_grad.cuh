@@ -359,6 +359,7 @@ __global__ void __launch_bounds__(THREADS, 2) grad_kernel_tc(StageArgs<float> p,
     const long long nAff = (p.Kaff + ET - 1) / ET;
     const long long nCur = (p.K - p.Kaff + EC - 1) / EC;
     __shared__ int s_tile;
+    __shared__ bool s_visc;
     // prologue (barriers, TMEM, operators) overlaps the previous kernel
     tc::pdl_trigger();
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_g + S::sBAR);
@@ -368,13 +369,12 @@ __global__ void __launch_bounds__(THREADS, 2) grad_kernel_tc(StageArgs<float> p,
     }
     uint32_t* slot = reinterpret_cast<uint32_t*>(smem_g + S::sTMEM);
     if ((tid >> 5) == 0) tc::tmem_alloc(slot, S::TMEM_COLS);
-    load_grad_operators<N>(ops_tc, smem_g);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *slot;
     uint32_t nwait = 0, nld = 0;
-    bool ops_loaded = true, rows_ready = false;
+    bool ops_loaded = false, rows_ready = false;   // operators loaded with the first tile that needs them
     tc::pdl_wait();
     if (tid == 0) s_tile = atomicAdd(counter, 1);
     __syncthreads();
@@ -394,14 +394,34 @@ __global__ void __launch_bounds__(THREADS, 2) grad_kernel_tc(StageArgs<float> p,
             if (tid == THREADS - 1) s_tile = claim;
             __syncthreads();
         } else {
-            if (!ops_loaded) {
-                load_grad_operators<N>(ops_tc, smem_g);
-                __syncthreads();
-                ops_loaded = true;
-            }
             const long long e0 = (t - nCur) * ET;
-            rows_ready = grad_tile_tc<N, PREC>(p, q_out, e0, (int)min((long long)ET, p.Kaff - e0), smem_g, tmem, nwait,
-                                               nld, err, rows_ready, claim, &s_tile, nCur, nAff);
+            const int ne = (int)min((long long)ET, p.Kaff - e0);
+            // q enters the stage only as sqrt(eps) q of its own element, so a
+            // tile whose 32 elements all have eps = 0 needs none: its q is
+            // neither computed nor written (the eps array is padded to whole
+            // tiles with zeros)
+            if (tid < 32) {
+                const bool any = __any_sync(0xffffffffu, tid < ne && p.eps[e0 + tid] > 0.f);
+                if (tid == 0) s_visc = any;
+            }
+            __syncthreads();
+            if (!s_visc) {
+                if (rows_ready) {   // this tile's rows were prefetched: complete that copy
+                    if (!tc::mbar_wait(&bars[1], nld & 1)) atomicOr(err, 8);
+                    ++nld;
+                    rows_ready = false;
+                }
+                if (tid == THREADS - 1) s_tile = claim;
+                __syncthreads();
+            } else {
+                if (!ops_loaded) {
+                    load_grad_operators<N>(ops_tc, smem_g);
+                    __syncthreads();
+                    ops_loaded = true;
+                }
+                rows_ready = grad_tile_tc<N, PREC>(p, q_out, e0, ne, smem_g, tmem, nwait, nld, err, rows_ready, claim,
+                                                   &s_tile, nCur, nAff);
+            }
         }
         t = s_tile;
     }
