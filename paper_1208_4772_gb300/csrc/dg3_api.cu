@@ -376,8 +376,8 @@ int dg_tet_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const
         api_free_mesh(m);
         return e;
     }
-    if ((e = api_alloc(ctx, *m, (void**)&m->err, 32))) { api_free_mesh(m); return e; }
-    if (cudaMemset(m->err, 0, 32) != cudaSuccess) {
+    if ((e = api_alloc(ctx, *m, (void**)&m->err, ERR_WORDS * sizeof(int)))) { api_free_mesh(m); return e; }
+    if (cudaMemset(m->err, 0, ERR_WORDS * sizeof(int)) != cudaSuccess) {
         api_free_mesh(m);
         return api_fail(ctx, DG_ECUDA, "memset failed");
     }

@@ -368,11 +368,14 @@ int enqueue_stage_t(const MeshData& m, const void* Us, const void* Un, void* out
     StageArgs<Real> s = make_args<Real>(m, Us, Un, out, a, b, dt, rhs_only);
     s.dU = (Real*)dU;
     int e;
+    const bool fused = fused_sensor(m) && stage >= 0 && !rhs_only;
     if (m.p.av_on) {
-        if (fused_sensor(m) && stage >= 0 && !rhs_only) {
-            // eps of this stage's input was written by the previous stage kernel
+        if (fused) {
+            // eps of this stage's input was written by the previous stage
+            // kernel, with the count of its viscous tiles
             s.eps = (const Real*)m.eps_ring[stage];
             s.eps_next = (Real*)m.eps_ring[(stage + 1) % 3];
+            s.visc = m.err + VISC_SLOT + stage;
         } else {
             // a right-hand-side evaluation on the tensor-core path uses the
             // ring slot that the next step's first stage rewrites
@@ -396,6 +399,7 @@ int enqueue_stage_t(const MeshData& m, const void* Us, const void* Un, void* out
             }
         }
     }
+    s.visc = fused ? m.err + VISC_SLOT + (stage + 1) % 3 : nullptr;   // counts the tiles eps_next makes viscous
     ProfScope ps(m, st, 2);
     if constexpr (sizeof(Real) == 4) {
         if (tensor_prec(m.prec))
@@ -429,12 +433,14 @@ int enqueue_stage(const MeshData& m, const void* Us, const void* Un, void* out, 
 // stage kernel's epilogue (no sensor kernel in the step graph).
 bool fused_sensor(const MeshData& m) { return m.dim == 2 && m.p.av_on && tensor_prec(m.prec); }
 
-int enqueue_sensor(const MeshData& m, const void* U, void* eps_out, cudaStream_t st) {
+int enqueue_sensor(const MeshData& m, const void* U, void* eps_out, cudaStream_t st, int* visc) {
     if (m.prec == DG_FP64_DEBUG) {
-        const StageArgs<double> s = make_args<double>(m, U, nullptr, nullptr, 0.0, 0.0, 0.0, 1);
+        StageArgs<double> s = make_args<double>(m, U, nullptr, nullptr, 0.0, 0.0, 0.0, 1);
+        s.visc = visc;
         return dispatch_sensor<double>(m.N, s, (double*)eps_out, st);
     }
-    const StageArgs<float> s = make_args<float>(m, U, nullptr, nullptr, 0.0, 0.0, 0.0, 1);
+    StageArgs<float> s = make_args<float>(m, U, nullptr, nullptr, 0.0, 0.0, 0.0, 1);
+    s.visc = visc;
     return dispatch_sensor<float>(m.N, s, (float*)eps_out, st);
 }
 
@@ -880,9 +886,12 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
         free_mesh(m);
         return e;
     }
-    // error word and the persistent kernels' tile / done counters
-    if ((e = alloc(ctx, *m, (void**)&m->err, 32))) { free_mesh(m); return e; }
-    if (cudaMemset(m->err, 0, 32) != cudaSuccess) { free_mesh(m); return fail(ctx, DG_ECUDA, "memset failed"); }
+    // error word, the persistent kernels' tile / done counters, viscous counts
+    if ((e = alloc(ctx, *m, (void**)&m->err, ERR_WORDS * sizeof(int)))) { free_mesh(m); return e; }
+    if (cudaMemset(m->err, 0, ERR_WORDS * sizeof(int)) != cudaSuccess) {
+        free_mesh(m);
+        return fail(ctx, DG_ECUDA, "memset failed");
+    }
     if (tensor_prec(p->prec)) {
         const int tkey = N * 16 + 4 + p->prec;
         auto tit = ctx->ops.find(tkey);
@@ -1126,8 +1135,9 @@ int dg_step(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
         CUDA_OK(ctx, cudaGraphInstantiate(&m->gexec, g, 0));
         m->gdt = dt;
     }
-    if (fused_sensor(*m) && !m->eps_valid) {   // eps(U^n) for the first stage
-        const int e = enqueue_sensor(*m, m->U[0], m->eps_ring[0], ctx->stream);
+    if (fused_sensor(*m) && !m->eps_valid) {   // eps(U^n) for the first stage, with its viscous count
+        CUDA_OK(ctx, cudaMemsetAsync(m->err + VISC_SLOT, 0, sizeof(int), ctx->stream));
+        const int e = enqueue_sensor(*m, m->U[0], m->eps_ring[0], ctx->stream, m->err + VISC_SLOT);
         if (e) return fail(ctx, DG_ECUDA, std::string("sensor launch failed: ") + cudaGetErrorString((cudaError_t)e));
         m->eps_valid = true;
     }

@@ -71,6 +71,10 @@ struct StageArgs {
     const Real* ops;    // packed operator table
     const Real* eps;    // [K] viscosity (AV)
     Real* eps_next;     // AV, tensor-core path: eps of the state this stage writes (null: none)
+    // AV: count of tiles (sensor kernel: elements) with eps > 0 -- incremented
+    // where eps is written (eps_next or a sensor launch), read and reset by the
+    // tensor-core gradient kernel, which does nothing when it is 0 (null: none)
+    int* visc;
     const Real* q;      // [K][2][4][NP] sqrt(eps) grad U (AV)
     long long K, Kaff;
     Real gamma;

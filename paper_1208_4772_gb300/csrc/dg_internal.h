@@ -37,7 +37,7 @@ struct MeshData {
     void* geoC = nullptr;         // [Kc][curved_stride]
     void* ops = nullptr;          // shared operator table (owned by the context)
     void* ops_tc = nullptr;       // tensor-core operator table (owned by the context)
-    int* err = nullptr;           // device error word (bounded waits that ran out)
+    int* err = nullptr;           // device error words (ERR_WORDS ints; see below)
     int4* conn = nullptr;         // [K]
     long long* dperm = nullptr;   // device copy of perm
     long long* diperm = nullptr;  // inverse permutation
@@ -68,7 +68,10 @@ int api_fail(dg_ctx* ctx, int code, const std::string& msg);
 int api_alloc(dg_ctx* ctx, MeshData& m, void** p, size_t bytes);
 void api_free_mesh(MeshData* m);
 bool fused_sensor(const MeshData& m);
-int enqueue_sensor(const MeshData& m, const void* U, void* eps_out, cudaStream_t st);
+int enqueue_sensor(const MeshData& m, const void* U, void* eps_out, cudaStream_t st, int* visc = nullptr);
+// error word block: [0] error bits, [1..4] tile / done counters of the
+// persistent kernels, [VISC_SLOT + s] viscous-tile count of eps ring slot s
+constexpr int ERR_WORDS = 16, VISC_SLOT = 8;
 int enqueue_step(const MeshData& m, double dt, cudaStream_t st);
 int enqueue_step_lserk(const MeshData& m, double dt, cudaStream_t st);
 void drop_graphs(MeshData& m);

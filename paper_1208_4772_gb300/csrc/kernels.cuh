@@ -473,7 +473,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileR
             __syncthreads();                            // the tile's new state is written
             for (int e = threadIdx.x >> 5; e < t.ne; e += blockDim.x >> 5) {
                 const Real eps = element_sensor_warp<N, Real>(p, t.e0 + e, p.Uout + (t.e0 + e) * 4 * NP);
-                if ((threadIdx.x & 31) == 0) p.eps_next[t.e0 + e] = eps;
+                if ((threadIdx.x & 31) == 0) {
+                    p.eps_next[t.e0 + e] = eps;
+                    if (p.visc && eps > Real(0)) atomicAdd(p.visc, 1);
+                }
             }
         }
     }
@@ -540,7 +543,11 @@ __global__ void __launch_bounds__(SENSOR_THREADS) sensor_kernel(StageArgs<Real> 
             num += __shfl_xor_sync(0xffffffffu, num, o);
             den += __shfl_xor_sync(0xffffffffu, den, o);
         }
-        if (lane == 0) eps_out[k] = sensor_eps(p, num, den);
+        if (lane == 0) {
+            const Real ev = sensor_eps(p, num, den);
+            eps_out[k] = ev;
+            if (p.visc && ev > Real(0)) atomicAdd(p.visc, 1);
+        }
         return;
     }
     constexpr int RS = NP | 1;   // odd row stride: conflict-free column reads
@@ -566,7 +573,9 @@ __global__ void __launch_bounds__(SENSOR_THREADS) sensor_kernel(StageArgs<Real> 
         den += um * um;
         if (m >= NLOW) num += um * um;
     }
-    eps_out[k0 + e] = sensor_eps(p, num, den);
+    const Real ev = sensor_eps(p, num, den);
+    eps_out[k0 + e] = ev;
+    if (p.visc && ev > Real(0)) atomicAdd(p.visc, 1);
 }
 
 // ---------------------------------------------------------------------------

@@ -883,7 +883,14 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 __syncthreads();
                 // the FP64 ratio, log10 and ramp for the 32 elements by one warp
                 // (one lane per element): GB300's FP64 pipe is narrow
-                if (warp == 7 && lane < ne) p.eps_next[e0 + lane] = sensor_eps(p, sND[2 * lane], sND[2 * lane + 1]);
+                if (warp == 7) {
+                    float ev = 0.f;
+                    if (lane < ne) {
+                        ev = sensor_eps(p, sND[2 * lane], sND[2 * lane + 1]);
+                        p.eps_next[e0 + lane] = ev;
+                    }
+                    if (p.visc != nullptr && __any_sync(0xffffffffu, ev > 0.f) && lane == 0) atomicAdd(p.visc, 1);
+                }
             }
         }
         __syncthreads();   // staging and per-element data are reused by the next tile

@@ -86,7 +86,7 @@ def estimate_bytes(K, N, curved=0, prec_bytes=4, av=False, tensor=False):
     b += (K - curved) * 4 * prec_bytes           # affine geometry
     b += curved * (5 * Nq + 3 * Nf + Np * Np) * prec_bytes
     b += 2 * K * 8                               # permutation maps
-    b += (304 * 10 + 10) * 8 + 32                # reduction scratch, error word and counters
+    b += (304 * 10 + 10) * 8 + 64                # reduction scratch, error words, counters
     if av:
         b += (3 if tensor else 1) * ((K + 31) // 32 * 32) * prec_bytes    # eps padded to whole tiles
         b += K * 8 * Np * prec_bytes

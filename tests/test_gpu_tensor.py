@@ -209,3 +209,38 @@ def test_tc_av_steps_match_fp32_path(B, ctx, prec):
     Ub = B.dg_get_state(ctx, h, K, Np)
     B.dg_mesh_free(ctx, h)
     assert np.array_equal(Ua, Ub)
+
+
+@pytest.mark.parametrize("prec", ["tf32"])
+def test_av_viscous_switching_matches_fp32_path(B, ctx, prec):
+    """Tiles with eps = 0 skip the gradient (their q is multiplied by
+    sqrt(eps) = 0 wherever it enters), and a launch with no viscous tile at
+    all does nothing; the count of viscous tiles travels with eps from
+    kernel to kernel.  States that switch between inviscid (smooth) and
+    viscous (noisy) between steps give the FP32 path's result each time,
+    and LSERK steps and right-hand-side evaluations in between do not
+    disturb the counts."""
+    N = 4
+    r, s = B.dg_reference_nodes(N)
+    noisy = make_case("naca", N, r, s, av=True)
+    smooth = make_case("naca", N, r, s, av=True, perturb=0.0)
+    K, Np = noisy["mesh"].K, len(r)
+    dt = 0.2 * states.time_step(noisy["mesh"].verts, noisy["U"], N, eps0=0.3)
+    seq = [smooth["U"], noisy["U"], smooth["U"], noisy["U"]]
+    out = {}
+    for pr in ("fp32", prec):
+        h = upload(B, ctx, noisy, pr, U=seq[0])
+        res = []
+        for i, U in enumerate(seq):
+            B.dg_set_state(ctx, h, U)
+            B.dg_step(ctx, h, dt, 4)
+            if i == 1:
+                B.dg_eval_rhs(ctx, h, K, Np)
+                B.dg_step_lserk(ctx, h, dt, 1)
+                B.dg_step(ctx, h, dt, 2)
+            res.append(B.dg_get_state(ctx, h, K, Np))
+        out[pr] = res
+        B.dg_mesh_free(ctx, h)
+    for a, b in zip(out[prec], out["fp32"]):
+        err = rel_l2_per_var(a, b)
+        assert np.all(err <= STEP_TOL[prec]), err
