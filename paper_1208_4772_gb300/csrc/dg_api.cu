@@ -400,6 +400,7 @@ int enqueue_stage_t(const MeshData& m, const void* Us, const void* Un, void* out
         }
     }
     s.visc = fused ? m.err + VISC_SLOT + (stage + 1) % 3 : nullptr;   // counts the tiles eps_next makes viscous
+    s.visc_in = fused ? m.err + VISC_SLOT + stage : nullptr;          // the count of this stage's eps
     ProfScope ps(m, st, 2);
     if constexpr (sizeof(Real) == 4) {
         if (tensor_prec(m.prec))

@@ -72,9 +72,10 @@ struct StageArgs {
     const Real* eps;    // [K] viscosity (AV)
     Real* eps_next;     // AV, tensor-core path: eps of the state this stage writes (null: none)
     // AV: count of tiles (sensor kernel: elements) with eps > 0 -- incremented
-    // where eps is written (eps_next or a sensor launch), read and reset by the
-    // tensor-core gradient kernel, which does nothing when it is 0 (null: none)
+    // where eps is written (eps_next or a sensor launch); the tensor-core
+    // gradient kernel reads it and does nothing when it is 0 (null: none)
     int* visc;
+    int* visc_in;       // AV stage kernel: the count of the eps it reads (its last CTA resets it; null: viscous)
     const Real* q;      // [K][2][4][NP] sqrt(eps) grad U (AV)
     long long K, Kaff;
     Real gamma;

@@ -377,8 +377,8 @@ __global__ void __launch_bounds__(THREADS, 2) grad_kernel_tc(StageArgs<float> p,
     bool ops_loaded = false, rows_ready = false;   // operators loaded with the first tile that needs them
     tc::pdl_wait();
     // no element anywhere with eps > 0 (the count comes with eps from the
-    // previous kernel): q is not needed at all.  Every CTA sees the same
-    // count, which only the last CTA of a launch that works resets.
+    // kernel that wrote it; the stage kernel that follows resets it): q is
+    // not needed at all
     if (p.visc != nullptr && *reinterpret_cast<volatile int*>(p.visc) == 0) {
         tc::fence_before_sync();
         __syncthreads();
@@ -442,7 +442,6 @@ __global__ void __launch_bounds__(THREADS, 2) grad_kernel_tc(StageArgs<float> p,
         __threadfence();
         *counter = 0;
         *done = 0;
-        if (p.visc != nullptr) *p.visc = 0;
     }
     if ((tid >> 5) == 0) tc::tmem_free(tmem, S::TMEM_COLS);
 }

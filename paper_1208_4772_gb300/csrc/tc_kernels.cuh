@@ -104,7 +104,7 @@ struct TcLayout {
 // transposes of the cubature chunks, then the epilogue rows.  Two A2
 // buffers, so that the tensor core works on one chunk while the next is
 // written.
-template <int N, bool AV>
+template <int N, bool AV, bool SENSE = AV>   // SENSE: the epilogue computes the next stage's eps
 struct TcSmem {
     using D = TcDims<N>;
     using L = TcLayout<N>;
@@ -121,7 +121,7 @@ struct TcSmem {
     static constexpr int NBV_C = AV ? 8 : 4;                                  // values per face point
     static constexpr int NBV_BYTES = 32 * D::NF * NBV_C * 4;
     static constexpr int sVI = sIGF + D::NF * D::NP * 4;                     // V^-1 transposed (AV: the sensor)
-    static constexpr int sA1 = al(sVI + (AV ? D::NP * D::NP * 4 : 0));         // G1 operands, then neighbour traces
+    static constexpr int sA1 = al(sVI + (SENSE ? D::NP * D::NP * 4 : 0));      // G1 operands, then neighbour traces
     static constexpr int A1_REGION = al(mx(A1_BYTES * (AV ? 3 : 1), NBV_BYTES));
     static constexpr int A2_BYTES = 128 * 32 * 4;
     static constexpr int NBUF = 2;
@@ -138,18 +138,18 @@ struct TcSmem {
     static constexpr int sFB = sGEO + 32 * 16 * 4;                           // [32][8] mean flux
     static constexpr int sSE = sFB + 32 * 8 * 4;                             // [32] sqrt(eps)
     static constexpr int sNB = sSE + 32 * 4;                                 // [32] int4
-    static constexpr int sBAR = sNB + 32 * 16;                               // 4 mbarriers
-    static constexpr int sTMEM = sBAR + 4 * 8;
-    static constexpr int sLIST = sTMEM + 16;                                 // out-of-tile faces: n, then (e,f)
+    static constexpr int sLIST = sNB + 32 * 16;                              // out-of-tile faces: n, then (e,f)
     static constexpr int sFL = sLIST + 100 * 4;                              // faces owned by the tile: n, then (e,f)
     static constexpr int sND = sFL + 100 * 4;                                // [32][2] sensor sums of the new state
     static constexpr int TOTAL = sND + 64 * 4;
-    static_assert(TOTAL <= 232448, "tensor-core tile exceeds the shared-memory limit");
+    static_assert(TOTAL + 256 <= 232448, "tensor-core tile exceeds the shared-memory limit");
     static_assert(D::CA <= NBUF, "viscous chunks are written at tile start, one per A2 buffer");
     static_assert(NBB >= 32 && (REC * 4) % 16 == 0 && (32 * 4 * D::NP * 4) % 16 == 0, "bulk-copy staging layout");
     static_assert(A1_REGION >= 32 * 4 * D::NP * 4, "epilogue rows live in the G1 operand region");
-    // a curved tile (CUDA-core body) may overwrite everything before sMEAN
-    static_assert(Tile<N, float>::smem_stage(AV) <= (size_t)sMEAN, "curved tile would clobber the tile state");
+    // a curved tile (CUDA-core body, with viscosity in either kind of
+    // launch) overwrites the dynamic region; the mbarriers and the TMEM slot
+    // live in static shared memory and the operators are reloaded after it
+    static_assert(Tile<N, float>::smem_stage(AV) <= (size_t)TOTAL, "curved tile exceeds the tile's region");
 };
 
 template <int N, bool AV>
@@ -299,13 +299,13 @@ __device__ __forceinline__ void issue_tile_rows(const StageArgs<float>& p, long 
 // done (its latency is long hidden by then) and read after the cubature
 // chunks.  bars: the CTA's four mbarriers (A2 buffers 0 and 1, G1, bulk
 // copies).  Returns true if the next tile's rows were requested here.
-template <int N, bool AV, int PREC>
+template <int N, bool AV, int PREC, bool SENSE = AV>
 __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long long e0, int ne, unsigned char* smem,
                                               uint32_t tmem, TcPhase& ph, int* err, bool rows_ready,
                                               int claim, int* next_tile, long long nCur, long long nAff,
                                               uint64_t* bars) {
     using D = TcDims<N>;
-    using S = TcSmem<N, AV>;
+    using S = TcSmem<N, AV, SENSE>;
     constexpr int NP = D::NP, NQ = D::NQ, NG = D::NG, NF = D::NF, NPK = D::NPK, FOFF = D::FOFF;
     constexpr int N1 = D::N1, NFP = D::NFP, N2 = D::N2, NFS = D::NFS, CF = D::CF, CQ = D::CQ, CA = D::CA;
     constexpr int B2C = TcLayout<N>::B2_CHUNK;
@@ -809,7 +809,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         const float4* un = reinterpret_cast<const float4*>(p.Un + base);
         float4* uo = reinterpret_cast<float4*>(p.Uout + base);
         float4* lo = reinterpret_cast<float4*>(sOut);
-        const bool sense = AV && p.eps_next != nullptr && !p.rhs_only;
+        const bool sense = SENSE && p.eps_next != nullptr && !p.rhs_only;
         for (int i = tid; i < n4; i += blockDim.x) {
             const float4 L4 = lo[i];
             float4 r;
@@ -838,7 +838,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             uo[i] = r;
             if (sense) lo[i] = r;
         }
-        if constexpr (AV) {
+        if constexpr (SENSE) {
             // the next stage's eps: the sensor of the new state, 4 threads per
             // element over the modes u = V^-1 rho (FP32 sums, FP64 ratio)
             if (sense) {
@@ -898,9 +898,9 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     return pre;
 }
 
-template <int N, bool AV>
+template <int N, bool AV, bool SENSE = AV>
 __device__ __forceinline__ void load_tc_operators(const unsigned char* ops_tc, unsigned char* smem) {
-    using S = TcSmem<N, AV>;
+    using S = TcSmem<N, AV, SENSE>;
     using L = TcLayout<N>;
     constexpr int NF = TcDims<N>::NF, NP = TcDims<N>::NP;
     const int tid = threadIdx.x;
@@ -913,7 +913,7 @@ __device__ __forceinline__ void load_tc_operators(const unsigned char* ops_tc, u
     const float* igs = reinterpret_cast<const float*>(ops_tc + L::IGF);
     float* igd = reinterpret_cast<float*>(smem + S::sIGF);
     for (int i = tid; i < NF * NP; i += blockDim.x) igd[i] = igs[i];
-    if constexpr (AV) {
+    if constexpr (SENSE) {
         const float* vs = reinterpret_cast<const float*>(ops_tc + L::VINV);
         float* vd = reinterpret_cast<float*>(smem + S::sVI);
         for (int i = tid; i < NP * NP; i += blockDim.x) vd[i] = vs[i];
@@ -926,31 +926,54 @@ __device__ __forceinline__ void load_tc_operators(const unsigned char* ops_tc, u
 // are reloaded before the next tensor-core tile), then the affine tiles of
 // 32 elements on the tensor cores.  Handing the slow curved tiles out first
 // lets them overlap the affine work instead of forming a tail.
+//
+// With artificial viscosity, a launch whose input state has no element with
+// eps > 0 (the count of viscous tiles comes with eps from the kernel that
+// wrote it) runs the inviscid tile body with the next stage's sensor in its
+// epilogue: the viscous terms are sqrt(eps) q, all zero then.  The last CTA
+// resets that count for the slot's next use.
 template <int N, bool AV, int PREC>
 __global__ void __launch_bounds__(THREADS, 2) stage_kernel_tc(StageArgs<float> p, const unsigned char* ops_tc, int* err,
                                                               int* counter, int* done) {
     extern __shared__ __align__(128) unsigned char smem_tc[];
-    using S = TcSmem<N, AV>;
+    __shared__ __align__(8) uint64_t bars[4];
+    __shared__ uint32_t slot;
+    __shared__ int s_tile;
+    __shared__ int s_visc;
     constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
     const int tid = threadIdx.x;
     const long long nAff = (p.Kaff + ET - 1) / ET;
     const long long nCur = (p.K - p.Kaff + EC - 1) / EC;
-    __shared__ int s_tile;
 
     // prologue (barriers, TMEM, operators) overlaps the previous kernel
     tc::pdl_trigger();
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_tc + S::sBAR);
     if (tid == 0) {
         for (int b = 0; b < 4; ++b) tc::mbar_init(&bars[b], 1);
         tc::mbar_fence_init();
     }
-    uint32_t* slot = reinterpret_cast<uint32_t*>(smem_tc + S::sTMEM);
-    if ((tid >> 5) == 0) tc::tmem_alloc(slot, TcDims<N>::TMEM_COLS);
-    load_tc_operators<N, AV>(ops_tc, smem_tc);
+    if ((tid >> 5) == 0) tc::tmem_alloc(&slot, TcDims<N>::TMEM_COLS);
+    bool viscous = true;
+    if constexpr (AV) {   // the kind of launch is known once the previous kernel is done
+        tc::pdl_wait();
+        if (tid == 0) s_visc = (p.visc_in == nullptr) || *reinterpret_cast<volatile int*>(p.visc_in) > 0;
+        __syncthreads();
+        viscous = s_visc != 0;
+    }
+    auto load_ops = [&]() {
+        if constexpr (AV) {
+            if (viscous)
+                load_tc_operators<N, true>(ops_tc, smem_tc);
+            else
+                load_tc_operators<N, false, true>(ops_tc, smem_tc);
+        } else {
+            load_tc_operators<N, false>(ops_tc, smem_tc);
+        }
+    };
+    load_ops();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = *slot;
+    const uint32_t tmem = slot;
     TcPhase ph;
     bool ops_loaded = true, rows_ready = false;
     tc::pdl_wait();
@@ -973,13 +996,23 @@ __global__ void __launch_bounds__(THREADS, 2) stage_kernel_tc(StageArgs<float> p
             __syncthreads();
         } else {
             if (!ops_loaded) {
-                load_tc_operators<N, AV>(ops_tc, smem_tc);
+                load_ops();
                 __syncthreads();
                 ops_loaded = true;
             }
             const long long e0 = (t - nCur) * ET;
-            rows_ready = stage_tile_tc<N, AV, PREC>(p, e0, (int)min((long long)ET, p.Kaff - e0), smem_tc, tmem, ph,
-                                                    err, rows_ready, claim, &s_tile, nCur, nAff, bars);
+            const int ne = (int)min((long long)ET, p.Kaff - e0);
+            if constexpr (AV) {
+                if (viscous)
+                    rows_ready = stage_tile_tc<N, true, PREC>(p, e0, ne, smem_tc, tmem, ph, err, rows_ready, claim,
+                                                              &s_tile, nCur, nAff, bars);
+                else
+                    rows_ready = stage_tile_tc<N, false, PREC, true>(p, e0, ne, smem_tc, tmem, ph, err, rows_ready,
+                                                                     claim, &s_tile, nCur, nAff, bars);
+            } else {
+                rows_ready = stage_tile_tc<N, false, PREC>(p, e0, ne, smem_tc, tmem, ph, err, rows_ready, claim,
+                                                           &s_tile, nCur, nAff, bars);
+            }
         }
         t = s_tile;
     }
@@ -991,6 +1024,7 @@ __global__ void __launch_bounds__(THREADS, 2) stage_kernel_tc(StageArgs<float> p
         __threadfence();
         *counter = 0;
         *done = 0;
+        if (AV && p.visc_in != nullptr) *p.visc_in = 0;
     }
     if ((tid >> 5) == 0) tc::tmem_free(tmem, TcDims<N>::TMEM_COLS);
 }
