@@ -44,7 +44,7 @@ DTYPE = {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3", "fp64": "f64"}
 # the default command (summary in profiles/stage_kernel_tc_naca0012_n4_av.md);
 # keyed by (workload, products, flux) and only valid for the kernel source it was
 # taken on.
-TRAFFIC = {("naca0012_m0.8_n4_av", "tf32", "llf"): 62.18e6}
+TRAFFIC = {("naca0012_m0.8_n4_av", "tf32", "llf"): 31.90e6}
 
 WORKLOADS = {
     "naca0012_m0.8_n4_av": dict(kind="naca", N=4, n_t=300, n_r=100, mach=0.8, aoa=1.25, av=True,
@@ -157,18 +157,22 @@ def tet_stage_bytes(K, Kc, N):
     return K * (state * (1 + 2.0 / 3.0 + 1) + 24) + (K - Kc) * 36 + Kc * (9 * Nq + 16 * Ng + Np * Np) * 4
 
 
-def stage_kernel_bytes(K, Kc, N, av):
+def stage_kernel_bytes(K, Kc, N, av, viscous=True):
     """Algorithmic HBM bytes of one stage-kernel launch, averaged over the
     three SSP-RK3 stages: read U_s, read U^n (stages 2 and 3), write U_out
     (4 N_p FP32 each), affine geometry 16 B + connectivity 16 B per element,
-    curved elements' factor record, and with viscosity q (8 N_p FP32) and
-    eps (4 B).  Neighbour traces are L2 hits and count 0."""
+    curved elements' factor record; with artificial viscosity the next
+    stage's eps (4 B written) and, in a launch whose input has viscous
+    elements, q (8 N_p FP32) and eps (4 B) read.  Neighbour traces are L2
+    hits and count 0."""
     q = (3 * N + 2) // 2
     Np, Nq, Nf = (N + 1) * (N + 2) // 2, q * q, 3 * q
     state = 4 * Np * 4
     b = K * (state * (1 + 2.0 / 3.0 + 1) + 16) + (K - Kc) * 16 + Kc * (5 * Nq + 3 * Nf + Np * Np) * 4
     if av:
-        b += K * (8 * Np * 4 + 4)
+        b += K * 4
+        if viscous:
+            b += K * (8 * Np * 4 + 4)
     return b
 
 
@@ -440,6 +444,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     h = upload(args.prec)
+    visc = {"start": B.dg_av_count(ctx, h)} if wl["av"] else None
     tuned = {}
     if args.prec in ("fp32", "fp64"):     # CUDA-core tile size for this mesh
         tuned[args.prec] = B.dg_autotune(ctx, h, 5)
@@ -464,6 +469,8 @@ def run_ours(args):
         total_ms = float(t.item())
     value = world * dof_stage * nstage * args.steps / (total_ms / 1e3)
     linf, l2 = B.dg_residual(ctx, h, allow_nonfinite=True)
+    if visc is not None:
+        visc["end"] = B.dg_av_count(ctx, h)
 
     # per-kernel breakdown: a second pass with CUDA events recorded around
     # every kernel inside the step graph (on the library's stream)
@@ -484,7 +491,9 @@ def run_ours(args):
     stage_launch_ms = kt[2] / (3 * args.steps) if args.integrator == "ssp3" else total_ms / args.steps / 5
     kinds = ["sensor", "gradient", "stage"]
     dom = int(np.argmax(kt))
-    bytes_launch = stage_kernel_bytes(m.K, int(wl["curved"].sum()), N, wl["av"])
+    # launches on an input without viscous elements read neither q nor eps
+    viscous = visc is None or visc["start"] > 0 or visc["end"] > 0
+    bytes_launch = stage_kernel_bytes(m.K, int(wl["curved"].sum()), N, wl["av"], viscous)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak, peak_src = 6800.0, "fallback"
     if os.path.exists(peaks_path):
@@ -543,7 +552,8 @@ def run_ours(args):
                 "kernel_ms_per_step": {k: float(kt[i] / args.steps) for i, k in enumerate(kinds)},
                 "profiled_ms_per_step": float(sum(ptimes) / n_prof),
                 "tile_e": tuned[args.prec][0] if args.prec in tuned else 32,
-                "residual_linf": [float(x) for x in linf], **extra}
+                "residual_linf": [float(x) for x in linf],
+                "viscous_elements": visc, **extra}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

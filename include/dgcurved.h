@@ -290,6 +290,14 @@ int dg_kernel_times(dg_ctx* ctx, dg_mesh m, double out_ms[4]);
 int dg_residual_norms_noalloc(const float* values_dev, int64_t K, int32_t Np, double* out8_dev,
                               void* cuda_stream);
 
+/* Number of elements of mesh m whose artificial viscosity is positive for
+ * the current state U^n (the sensor of paper Sec. 2, eps_k > 0), in *out.
+ * The stage kernels compute the viscous terms only where they are non-zero
+ * (a launch with none runs the inviscid tile body), so this is also a
+ * measure of the viscous work.  Synchronises the context's stream.  Errors:
+ * DG_EINVAL for meshes without artificial viscosity. */
+int dg_av_count(dg_ctx* ctx, dg_mesh m, int64_t* out);
+
 /* Wait for the context's stream, polling at most timeout_s seconds
  * (<= 0: wait without limit).  DG_ETIMEOUT if work is still in flight then;
  * the work itself is not cancelled. */

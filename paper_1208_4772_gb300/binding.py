@@ -89,6 +89,7 @@ def load():
         "dg_tet_sizes": (I, [I, C.POINTER(C.c_int32)]),
         "dg_tet_mesh_upload": (I, [P, I, I64, P, P, dp, C.POINTER(dg_params), C.POINTER(C.c_int32)]),
         "dg_mesh_info": (I, [P, C.c_int32, C.POINTER(I64)]),
+        "dg_av_count": (I, [P, C.c_int32, C.POINTER(I64)]),
         "dg_last_error": (C.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -180,6 +181,13 @@ def dg_tet_mesh_upload(ctx, N, EToV, bc, node_xyz, params):
     _check(load().dg_tet_mesh_upload(ctx, N, K, EToV.ctypes.data, bc.ctypes.data, _dptr(node_xyz),
                                      C.byref(params), C.byref(h)), ctx)
     return h.value
+
+
+def dg_av_count(ctx, m):
+    """Elements with eps > 0 for the current state."""
+    out = C.c_int64()
+    _check(load().dg_av_count(ctx, m, C.byref(out)), ctx)
+    return int(out.value)
 
 
 def dg_mesh_free(ctx, m):

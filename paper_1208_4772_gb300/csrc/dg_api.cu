@@ -1172,6 +1172,25 @@ int dg_residual(dg_ctx* ctx, dg_mesh h, double* out_linf, double* out_l2) {
     return finite ? DG_OK : fail(ctx, DG_ENONFINITE, "non-finite residual norm");
 }
 
+int dg_av_count(dg_ctx* ctx, dg_mesh h, int64_t* out) {
+    if (!ctx || !out) return fail(ctx, DG_EINVAL, "NULL argument");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    if (m->dim != 2 || !m->p.av_on) return fail(ctx, DG_EINVAL, "the mesh has no artificial viscosity");
+    cudaSetDevice(ctx->device);
+    // the sensor of U^n into the right-hand-side scratch, counting its
+    // elements with eps > 0 in a scratch word of the error block
+    int* cnt = m->err + VISC_SLOT + 3;
+    CUDA_OK(ctx, cudaMemsetAsync(cnt, 0, sizeof(int), ctx->stream));
+    const int e = enqueue_sensor(*m, m->U[0], m->rhs, ctx->stream, cnt);
+    if (e) return fail(ctx, DG_ECUDA, std::string("sensor launch failed: ") + cudaGetErrorString((cudaError_t)e));
+    int hv = 0;
+    CUDA_OK(ctx, cudaMemcpyAsync(&hv, cnt, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
+    *out = hv;
+    return DG_OK;
+}
+
 int dg_sync(dg_ctx* ctx, double timeout_s) {
     if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
     cudaSetDevice(ctx->device);

@@ -244,3 +244,20 @@ def test_av_viscous_switching_matches_fp32_path(B, ctx, prec):
     for a, b in zip(out[prec], out["fp32"]):
         err = rel_l2_per_var(a, b)
         assert np.all(err <= STEP_TOL[prec]), err
+
+
+def test_av_count_matches_oracle_sensor(B, ctx):
+    """dg_av_count = the number of elements the oracle's sensor gives eps > 0."""
+    from oracle.dg import Oracle
+    N = 4
+    r, s = B.dg_reference_nodes(N)
+    for perturb in (0.0, 0.02):
+        case = make_case("naca", N, r, s, av=True, perturb=perturb)
+        m = case["mesh"]
+        U = case["U"].astype(np.float32).astype(np.float64)
+        h = upload(B, ctx, case, "fp64", U=U)
+        n = B.dg_av_count(ctx, h)
+        B.dg_mesh_free(ctx, h)
+        eps = Oracle(N, m.EToE, m.EToF, m.bc, case["xy"], u_inf=case["u_inf"], av=True).sensor(U)
+        assert n == int(np.sum(eps > 0)), (perturb, n, int(np.sum(eps > 0)))
+        assert (n == 0) == (perturb == 0.0)
