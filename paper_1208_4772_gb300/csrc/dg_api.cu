@@ -364,7 +364,7 @@ struct ProfScope {
 
 template <typename Real>
 int enqueue_stage_t(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
-                    int rhs_only, cudaStream_t st, int stage, void* dU) {
+                    int rhs_only, cudaStream_t st, int stage, void* dU, int ring) {
     StageArgs<Real> s = make_args<Real>(m, Us, Un, out, a, b, dt, rhs_only);
     s.dU = (Real*)dU;
     int e;
@@ -374,7 +374,7 @@ int enqueue_stage_t(const MeshData& m, const void* Us, const void* Un, void* out
             // eps of this stage's input was written by the previous stage
             // kernel, with the count of its viscous tiles
             s.eps = (const Real*)m.eps_ring[stage];
-            s.eps_next = (Real*)m.eps_ring[(stage + 1) % 3];
+            s.eps_next = (Real*)m.eps_ring[(stage + 1) % ring];
             s.visc = m.err + VISC_SLOT + stage;
         } else {
             // a right-hand-side evaluation on the tensor-core path uses the
@@ -399,7 +399,7 @@ int enqueue_stage_t(const MeshData& m, const void* Us, const void* Un, void* out
             }
         }
     }
-    s.visc = fused ? m.err + VISC_SLOT + (stage + 1) % 3 : nullptr;   // counts the tiles eps_next makes viscous
+    s.visc = fused ? m.err + VISC_SLOT + (stage + 1) % ring : nullptr;   // counts the tiles eps_next makes viscous
     s.visc_in = fused ? m.err + VISC_SLOT + stage : nullptr;          // the count of this stage's eps
     ProfScope ps(m, st, 2);
     if constexpr (sizeof(Real) == 4) {
@@ -421,13 +421,14 @@ int api_alloc(dg_ctx* ctx, MeshData& m, void** p, size_t bytes) { return alloc(c
 void api_free_mesh(MeshData* m) { free_mesh(m); }
 
 int enqueue_stage(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
-                  int rhs_only, cudaStream_t st, int stage, void* dU) {
+                  int rhs_only, cudaStream_t st, int stage, void* dU, int ring) {
     if (m.dim == 3) {
         ProfScope ps(m, st, 2);
         return enqueue_stage3(m, Us, Un, out, a, b, dt, rhs_only, st, dU);
     }
-    if (m.prec == DG_FP64_DEBUG) return enqueue_stage_t<double>(m, Us, Un, out, a, b, dt, rhs_only, st, stage, dU);
-    return enqueue_stage_t<float>(m, Us, Un, out, a, b, dt, rhs_only, st, stage, dU);
+    if (m.prec == DG_FP64_DEBUG)
+        return enqueue_stage_t<double>(m, Us, Un, out, a, b, dt, rhs_only, st, stage, dU, ring);
+    return enqueue_stage_t<float>(m, Us, Un, out, a, b, dt, rhs_only, st, stage, dU, ring);
 }
 
 // The tensor-core path with AV computes each stage's eps in the previous
@@ -458,7 +459,10 @@ int enqueue_step(const MeshData& m, double dt, cudaStream_t st) {
 // RK (the paper's integrator): dU <- A_i dU + dt L(U), U <- U + B_i dU.  Each
 // stage reads one state buffer and writes another (neighbours read a state
 // no tile is writing): U0 -> U1 -> U2 -> U1 -> U2 -> U0; dU lives in the
-// right-hand-side scratch.  The sensor runs as its own kernel every stage.
+// right-hand-side scratch.  On the tensor-core path with AV the eps of each
+// stage comes from the previous stage kernel through a ring of five
+// buffers, so that the step begins and ends with eps(U^n) in buffer 0, as
+// the three-stage step does.
 int enqueue_step_lserk(const MeshData& m, double dt, cudaStream_t st) {
     static const double A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
                                 -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
@@ -467,7 +471,7 @@ int enqueue_step_lserk(const MeshData& m, double dt, cudaStream_t st) {
                                  2277821191437.0 / 14882151754819.0};
     static const int in[5] = {0, 1, 2, 1, 2}, out[5] = {1, 2, 1, 2, 0};
     for (int i = 0; i < 5; ++i) {
-        const int e = enqueue_stage(m, m.U[in[i]], nullptr, m.U[out[i]], A[i], Bc[i], dt, 0, st, -1, m.rhs);
+        const int e = enqueue_stage(m, m.U[in[i]], nullptr, m.U[out[i]], A[i], Bc[i], dt, 0, st, i, m.rhs, EPS_RING);
         if (e) return e;
     }
     return 0;
@@ -925,7 +929,7 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
         if ((e = alloc(ctx, *m, &m->eps, eb))) { free_mesh(m); return e; }
         m->eps_ring[0] = m->eps;
         if (tensor_prec(p->prec))
-            for (int b = 1; b < 3; ++b)
+            for (int b = 1; b < EPS_RING; ++b)
                 if ((e = alloc(ctx, *m, &m->eps_ring[b], eb))) { free_mesh(m); return e; }
         if ((e = alloc(ctx, *m, &m->q, (size_t)K * 8 * NP * rs))) { free_mesh(m); return e; }
     }
@@ -977,7 +981,7 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
         free_mesh(m);
         return fail(ctx, DG_ECUDA, "mesh upload copy failed");
     }
-    for (int b = 1; b < 3; ++b)
+    for (int b = 1; b < EPS_RING; ++b)
         if (m->eps_ring[b] && cudaMemset(m->eps_ring[b], 0, (size_t)((K + 31) / 32 * 32) * rs) != cudaSuccess) {
             free_mesh(m);
             return fail(ctx, DG_ECUDA, "mesh upload memset failed");
@@ -1180,7 +1184,7 @@ int dg_av_count(dg_ctx* ctx, dg_mesh h, int64_t* out) {
     cudaSetDevice(ctx->device);
     // the sensor of U^n into the right-hand-side scratch, counting its
     // elements with eps > 0 in a scratch word of the error block
-    int* cnt = m->err + VISC_SLOT + 3;
+    int* cnt = m->err + VISC_SLOT + EPS_RING;
     CUDA_OK(ctx, cudaMemsetAsync(cnt, 0, sizeof(int), ctx->stream));
     const int e = enqueue_sensor(*m, m->U[0], m->rhs, ctx->stream, cnt);
     if (e) return fail(ctx, DG_ECUDA, std::string("sensor launch failed: ") + cudaGetErrorString((cudaError_t)e));
@@ -1232,8 +1236,13 @@ int dg_step_lserk(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
         CUDA_OK(ctx, cudaGraphInstantiate(&m->gexec_ls, g, 0));
         m->gdt_ls = dt;
     }
+    if (fused_sensor(*m) && !m->eps_valid) {   // eps(U^n) for the first stage, with its viscous count
+        CUDA_OK(ctx, cudaMemsetAsync(m->err + VISC_SLOT, 0, sizeof(int), ctx->stream));
+        const int e = enqueue_sensor(*m, m->U[0], m->eps_ring[0], ctx->stream, m->err + VISC_SLOT);
+        if (e) return fail(ctx, DG_ECUDA, std::string("sensor launch failed: ") + cudaGetErrorString((cudaError_t)e));
+        m->eps_valid = true;
+    }
     for (int s = 0; s < nsteps; ++s) CUDA_OK(ctx, cudaGraphLaunch(m->gexec_ls, ctx->stream));
-    m->eps_valid = false;   // the eps rotation of the three-stage step is not maintained here
     return DG_OK;
 }
 

@@ -28,9 +28,10 @@ struct MeshData {
     void* rhs = nullptr;          // L(U) scratch
     void* eps = nullptr;          // [K] viscosity (AV); eps_ring[0]
     // tensor-core path with AV: the stage kernel of stage s reads eps_ring[s]
-    // and writes the sensor of its new state to eps_ring[(s+1) % 3], so that a
-    // step starts and ends with eps_ring[0] = eps(U^n)
-    void* eps_ring[3] = {nullptr, nullptr, nullptr};
+    // and writes the sensor of its new state to eps_ring[(s+1) % R] (R = 3
+    // for SSP-RK3, 5 for the low-storage RK), so that a step of either kind
+    // starts and ends with eps_ring[0] = eps(U^n)
+    void* eps_ring[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool eps_valid = false;       // eps_ring[0] holds eps(U^n)
     void* q = nullptr;            // [K][2][4][Np] (AV)
     void* geoA = nullptr;         // [Kaff][4]
@@ -60,7 +61,7 @@ struct MeshData {
 };
 
 int enqueue_stage(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
-                  int rhs_only, cudaStream_t st, int stage = -1, void* dU = nullptr);
+                  int rhs_only, cudaStream_t st, int stage = -1, void* dU = nullptr, int ring = 3);
 int enqueue_stage3(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
                    int rhs_only, cudaStream_t st, void* dU);
 // helpers of the C ABI shared by dg_api.cu and dg3_api.cu
@@ -71,7 +72,8 @@ bool fused_sensor(const MeshData& m);
 int enqueue_sensor(const MeshData& m, const void* U, void* eps_out, cudaStream_t st, int* visc = nullptr);
 // error word block: [0] error bits, [1..4] tile / done counters of the
 // persistent kernels, [VISC_SLOT + s] viscous-tile count of eps ring slot s
-constexpr int ERR_WORDS = 16, VISC_SLOT = 8;
+// (s < 5), [VISC_SLOT + 5] scratch count of dg_av_count
+constexpr int ERR_WORDS = 16, VISC_SLOT = 8, EPS_RING = 5;
 int enqueue_step(const MeshData& m, double dt, cudaStream_t st);
 int enqueue_step_lserk(const MeshData& m, double dt, cudaStream_t st);
 void drop_graphs(MeshData& m);
