@@ -111,17 +111,21 @@ struct TcSmem {
     static constexpr int NCHU = D::CF + D::CQ + (AV ? D::CA : 0);  // chunks used
     static constexpr int al(int x) { return (x + 127) / 128 * 128; }
     static constexpr int mx(int a, int b) { return a > b ? a : b; }
-    // constant region: operators, loaded once per CTA
+    // constant region: operators, loaded once per CTA.  The viscous layout
+    // extends the inviscid one with the sensor (SENSE) at its end: the
+    // viscous chunks follow the face and cubature chunks, then I_g for q, so
+    // a launch can load the common part before it knows which it is.
     static constexpr int sB1 = 0;
-    static constexpr int sB1Q = sB1 + L::B1_BYTES;
-    static constexpr int sB2 = sB1Q + (AV ? L::B1Q_BYTES : 0);
-    static constexpr int sIGF = sB2 + NCHU * L::B2_CHUNK;
+    static constexpr int sIGF = sB1 + L::B1_BYTES;
+    static constexpr int sVI = sIGF + D::NF * D::NP * 4;                     // V^-1 transposed (the sensor)
+    static constexpr int sB2 = al(sVI + (SENSE ? D::NP * D::NP * 4 : 0));
+    static constexpr int sB1Q = sB2 + NCHU * L::B2_CHUNK;
+    static constexpr int OPS_END = sB1Q + (AV ? L::B1Q_BYTES : 0);
     // per-tile region
     static constexpr int A1_BYTES = 128 * D::NPK * 4;
     static constexpr int NBV_C = AV ? 8 : 4;                                  // values per face point
     static constexpr int NBV_BYTES = 32 * D::NF * NBV_C * 4;
-    static constexpr int sVI = sIGF + D::NF * D::NP * 4;                     // V^-1 transposed (AV: the sensor)
-    static constexpr int sA1 = al(sVI + (SENSE ? D::NP * D::NP * 4 : 0));      // G1 operands, then neighbour traces
+    static constexpr int sA1 = al(OPS_END);                                  // G1 operands, then neighbour traces
     static constexpr int A1_REGION = al(mx(A1_BYTES * (AV ? 3 : 1), NBV_BYTES));
     static constexpr int A2_BYTES = 128 * 32 * 4;
     static constexpr int NBUF = 2;
@@ -899,24 +903,35 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
 }
 
 template <int N, bool AV, bool SENSE = AV>
-__device__ __forceinline__ void load_tc_operators(const unsigned char* ops_tc, unsigned char* smem) {
+__device__ __forceinline__ void load_tc_operators(const unsigned char* ops_tc, unsigned char* smem,
+                                                  bool common = true, bool extra = true) {
     using S = TcSmem<N, AV, SENSE>;
     using L = TcLayout<N>;
+    using D = TcDims<N>;
     constexpr int NF = TcDims<N>::NF, NP = TcDims<N>::NP;
     const int tid = threadIdx.x;
     const int4* src = reinterpret_cast<const int4*>(ops_tc);
     int4* dst = reinterpret_cast<int4*>(smem);
-    for (int i = tid; i < L::B1_BYTES / 16; i += blockDim.x) dst[i] = src[i];
-    if constexpr (AV)
-        for (int i = tid; i < L::B1Q_BYTES / 16; i += blockDim.x) dst[S::sB1Q / 16 + i] = src[L::B1Q / 16 + i];
-    for (int i = tid; i < S::NCHU * L::B2_CHUNK / 16; i += blockDim.x) dst[S::sB2 / 16 + i] = src[L::B2 / 16 + i];
-    const float* igs = reinterpret_cast<const float*>(ops_tc + L::IGF);
-    float* igd = reinterpret_cast<float*>(smem + S::sIGF);
-    for (int i = tid; i < NF * NP; i += blockDim.x) igd[i] = igs[i];
-    if constexpr (SENSE) {
-        const float* vs = reinterpret_cast<const float*>(ops_tc + L::VINV);
-        float* vd = reinterpret_cast<float*>(smem + S::sVI);
-        for (int i = tid; i < NP * NP; i += blockDim.x) vd[i] = vs[i];
+    if (common) {   // the part every launch of this kind of kernel uses
+        for (int i = tid; i < L::B1_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+        constexpr int NC = D::CF + D::CQ;   // face and cubature chunks
+        for (int i = tid; i < NC * L::B2_CHUNK / 16; i += blockDim.x) dst[S::sB2 / 16 + i] = src[L::B2 / 16 + i];
+        const float* igs = reinterpret_cast<const float*>(ops_tc + L::IGF);
+        float* igd = reinterpret_cast<float*>(smem + S::sIGF);
+        for (int i = tid; i < NF * NP; i += blockDim.x) igd[i] = igs[i];
+        if constexpr (SENSE) {
+            const float* vs = reinterpret_cast<const float*>(ops_tc + L::VINV);
+            float* vd = reinterpret_cast<float*>(smem + S::sVI);
+            for (int i = tid; i < NP * NP; i += blockDim.x) vd[i] = vs[i];
+        }
+    }
+    if constexpr (AV) {
+        if (extra) {   // the viscous chunks and I_g for q
+            constexpr int NC = D::CF + D::CQ;
+            for (int i = tid; i < D::CA * L::B2_CHUNK / 16; i += blockDim.x)
+                dst[(S::sB2 + NC * L::B2_CHUNK) / 16 + i] = src[(L::B2 + NC * L::B2_CHUNK) / 16 + i];
+            for (int i = tid; i < L::B1Q_BYTES / 16; i += blockDim.x) dst[S::sB1Q / 16 + i] = src[L::B1Q / 16 + i];
+        }
     }
 }
 
@@ -953,13 +968,19 @@ __global__ void __launch_bounds__(THREADS, 2) stage_kernel_tc(StageArgs<float> p
     }
     if ((tid >> 5) == 0) tc::tmem_alloc(&slot, TcDims<N>::TMEM_COLS);
     bool viscous = true;
-    if constexpr (AV) {   // the kind of launch is known once the previous kernel is done
+    if constexpr (AV) {
+        // the operators both kinds of launch use, then the kind of launch
+        // (known once the previous kernel is done) and the viscous extras
+        load_tc_operators<N, true>(ops_tc, smem_tc, true, false);
         tc::pdl_wait();
         if (tid == 0) s_visc = (p.visc_in == nullptr) || *reinterpret_cast<volatile int*>(p.visc_in) > 0;
         __syncthreads();
         viscous = s_visc != 0;
+        if (viscous) load_tc_operators<N, true>(ops_tc, smem_tc, false, true);
+    } else {
+        load_tc_operators<N, false>(ops_tc, smem_tc);
     }
-    auto load_ops = [&]() {
+    auto load_ops = [&]() {   // after a curved tile: everything again
         if constexpr (AV) {
             if (viscous)
                 load_tc_operators<N, true>(ops_tc, smem_tc);
@@ -969,7 +990,6 @@ __global__ void __launch_bounds__(THREADS, 2) stage_kernel_tc(StageArgs<float> p
             load_tc_operators<N, false>(ops_tc, smem_tc);
         }
     };
-    load_ops();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
