@@ -371,6 +371,26 @@ def config_of(args, wl):
             "parallelism": "replicas (one independent solve per GPU)"}
 
 
+# ------------------------------------------------------------------ ranks
+# One independent replica per GPU (the path does not shard): every rank
+# times its own steps, the job's time is the slowest rank's, and the job's
+# rate counts the work of all ranks.
+def max_over_ranks(ms, dist, device):
+    """The largest of the ranks' times (ms); the value itself without
+    torch.distributed."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, job_ms):
+    """Units per second of the whole job: all ranks' units over the job's time."""
+    return world * units_per_rank / (job_ms / 1e3)
+
+
 # ------------------------------------------------------------------ our arm
 def timed_steps(B, ctx, h, dt, steps, stream, flush, torch, profiled=False, step=None):
     """Time `steps` single-step graph replays; returns (step_ms list, summed
@@ -462,12 +482,8 @@ def run_ours(args):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = float(sum(times))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * dof_stage * nstage * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(sum(times)), dist, "cuda")
+    value = whole_job_rate(world, dof_stage * nstage * args.steps, total_ms)
     linf, l2 = B.dg_residual(ctx, h, allow_nonfinite=True)
     if visc is not None:
         visc["end"] = B.dg_av_count(ctx, h)
