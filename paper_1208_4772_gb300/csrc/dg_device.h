@@ -11,6 +11,19 @@ namespace dgc {
 
 constexpr int THREADS = 256;
 
+// Reciprocal and square root of the flux evaluations.  FP32: the hardware
+// approximations (relative error a few units in the last place, far below
+// the FP32 and tensor-core tolerances); FP64 (the debug path): correctly
+// rounded.
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float fsqrt(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
+
 __host__ __device__ constexpr int np_of(int N) { return (N + 1) * (N + 2) / 2; }
 __host__ __device__ constexpr int q_of(int N) { return (3 * N + 2) / 2; }
 __host__ __device__ constexpr int nq_of(int N) { return q_of(N) * q_of(N); }

@@ -41,10 +41,6 @@ struct Tile {
     static __host__ __device__ int cap(int tile_e) { return tile_e > 0 ? tile_e : E; }
 };
 
-// Correctly rounded reciprocal (the same value as 1 / x, without the general
-// division sequence).
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
 
 template <typename Real>
 __device__ __forceinline__ void euler_flux(const Real U[4], Real gamma, Real F[4], Real G[4]) {
@@ -76,7 +72,7 @@ __device__ __forceinline__ void normal_flux(const Real U[4], Real nx, Real ny, R
     Fn[1] = U[1] * un + p * nx;
     Fn[2] = U[2] * un + p * ny;
     Fn[3] = (U[3] + p) * un;
-    speed = fabs(un) + sqrt(gamma * p * ir);
+    speed = fabs(un) + fsqrt(gamma * p * ir);
 }
 
 template <typename Real>
@@ -103,7 +99,7 @@ __device__ __forceinline__ void hllc_flux(const Real Um[4], const Real Up[4], Re
     const Real unl = ul * nx + vl * ny, unr = ur * nx + vr * ny;
     const Real pl = g1 * (Um[3] - Real(0.5) * (Um[1] * ul + Um[2] * vl));
     const Real pr = g1 * (Up[3] - Real(0.5) * (Up[1] * ur + Up[2] * vr));
-    const Real cl = sqrt(gamma * pl * irl), cr = sqrt(gamma * pr * irr);
+    const Real cl = fsqrt(gamma * pl * irl), cr = fsqrt(gamma * pr * irr);
     const Real SL = fmin(unl - cl, unr - cr), SR = fmax(unl + cl, unr + cr);
     const Real SM = (pr - pl + Um[0] * unl * (SL - unl) - Up[0] * unr * (SR - unr)) /
                     (Um[0] * (SL - unl) - Up[0] * (SR - unr));

@@ -82,10 +82,10 @@ __device__ __constant__ float kFaceRef[4][3] = {{0, 0, -1}, {0, -1, 0}, {1, 1, 1
 template <typename Real>
 __device__ __forceinline__ void normal_flux3(const Real* u, Real nx, Real ny, Real nz, Real gamma, Real* fn,
                                              Real& un, Real& c) {
-    const Real ir = Real(1) / u[0];
+    const Real ir = recip(u[0]);
     un = (u[1] * nx + u[2] * ny + u[3] * nz) * ir;
     const Real p = (gamma - Real(1)) * (u[4] - Real(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * ir);
-    c = sqrt(gamma * p * ir);
+    c = fsqrt(gamma * p * ir);
     fn[0] = u[0] * un;
     fn[1] = u[1] * un + p * nx;
     fn[2] = u[2] * un + p * ny;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
 #pragma unroll
                 for (int k = 0; k < 9; ++k) cof[k] = gc[k * NQ + q];
             }
-            const Real ir = Real(1) / u[0];
+            const Real ir = recip(u[0]);
             const Real vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
             const Real pr = (p.gamma - Real(1)) * (u[4] - Real(0.5) * (u[1] * vx + u[2] * vy + u[3] * vz));
             const Real H = u[4] + pr;
