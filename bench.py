@@ -44,7 +44,7 @@ DTYPE = {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3", "fp64": "f64"}
 # the default command (summary in profiles/stage_kernel_tc_naca0012_n4_av.md);
 # keyed by (workload, products, flux) and only valid for the kernel source it was
 # taken on.
-TRAFFIC = {("naca0012_m0.8_n4_av", "tf32", "llf"): 31.90e6}
+TRAFFIC = {("naca0012_m0.8_n4_av", "tf32", "llf"): 31.89e6}
 
 WORKLOADS = {
     "naca0012_m0.8_n4_av": dict(kind="naca", N=4, n_t=300, n_r=100, mach=0.8, aoa=1.25, av=True,
