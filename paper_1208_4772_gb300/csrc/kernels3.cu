@@ -32,11 +32,14 @@ struct T3 {
     static constexpr int O_W = O_I2T + 6 * NFP * NGP;
     static constexpr int O_MI = pad4(O_W + NG);
     static constexpr int O_U = pad4(O_MI + NP * NP);         // [E][5][NPP]
+    // flux rows of one (element, direction): 5 rows of NQP plus 4 reals, so
+    // that the blocks the lanes of one warp read start in different banks
+    static constexpr int FST = 5 * NQP + 4;
     int O_F, O_UF, O_NB, O_FS, O_T, O_R, O_G, O_END;
     size_t bytes;
     __host__ __device__ constexpr explicit T3(int E)
-        : O_F(O_U + E * 5 * NPP),          // [E][3][5][NQP] contravariant fluxes
-          O_UF(O_F + E * 15 * NQP),        // [E][4][5][NFPP] own face nodes
+        : O_F(O_U + E * 5 * NPP),          // [E][3][FST] contravariant fluxes
+          O_UF(O_F + E * 3 * FST),         // [E][4][5][NFPP] own face nodes
           O_NB(O_UF + E * 20 * NFPP),      // [E][4][5][NFPP] neighbours' face nodes
           O_FS(O_NB + E * 20 * NFPP),      // [E][4][5][NGP] w sJ F*
           O_T(O_FS + E * 20 * NGP),        // [E][4][5][NFPP] lifted face terms
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
                 // contravariant velocity and pressure direction for direction a
                 const Real c0 = cof[a], c1 = cof[3 + a], c2 = cof[6 + a];
                 const Real U = c0 * vx + c1 * vy + c2 * vz;
-                Real* out = sF + (e * 15 + a * 5) * NQP + q;
+                Real* out = sF + (e * 3 + a) * TT::FST + q;
                 out[0] = u[0] * U;
                 out[NQP] = u[1] * U + pr * c0;
                 out[2 * NQP] = u[2] * U + pr * c1;
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
             const int n = i % NH, rest = i / NH, e = rest % ne, a = rest / ne;
             const int m = n + NH < NP ? n + NH : n;
             const Real* DB = p.ops + (a == 0 ? L.drw : a == 1 ? L.dsw : L.dtw);
-            const Real* fa = sF + (e * 15 + a * 5) * NQP;
+            const Real* fa = sF + (e * 3 + a) * TT::FST;
             Real acc0[5] = {0, 0, 0, 0, 0}, acc1[5] = {0, 0, 0, 0, 0};
 #pragma unroll 2
             for (int qb = 0; qb < NQP / 4; ++qb) {

@@ -70,9 +70,22 @@ def make_case3(kind, N, r, s, t, seed=0, size="small", perturb=0.02):
         ui = states.freestream3(0.5, 10.0)
         U = states.vortex3_state(X, period=(L, L))
         U *= 1.0 + 0.1 * perturb * rng.standard_normal(U.shape)
+    elif kind in ("single", "pair"):
+        m = minimal_tet_mesh(kind)
+        X = meshes3d.node_coords(m, r, s, t)
+        ui = states.freestream3(0.5, 10.0)
+        U = states.uniform_state3(m.K, len(r), ui)
+        x, y, z = X[..., 0], X[..., 1], X[..., 2]
+        U[:, 0] *= 1.0 + perturb * np.sin(2.1 * x + y) * np.cos(1.7 * z)
+        U[:, 4] *= 1.0 + perturb * np.cos(1.9 * y - z)
+        U[:, 3] += perturb * np.sin(3 * x)
+        U *= 1.0 + 0.1 * perturb * rng.standard_normal(U.shape)
     elif kind == "bump":
-        nx, ny, nz = {"tiny": (4, 2, 2), "small": (6, 3, 4), "medium": (12, 6, 8)}[size]
-        m = meshes3d.bump_channel(nx, ny, nz, seed=2000 + seed)
+        if size == "config":     # the 300,000-tetrahedron bump channel of the benchmark
+            m = meshes3d.bump_channel(50, 25, 40, Zd=0.4, seed=2000 + seed)
+        else:
+            nx, ny, nz = {"tiny": (4, 2, 2), "small": (6, 3, 4), "medium": (12, 6, 8)}[size]
+            m = meshes3d.bump_channel(nx, ny, nz, seed=2000 + seed)
         X = meshes3d.node_coords(m, r, s, t)
         ui = states.freestream3(0.5, 0.0)
         U = states.uniform_state3(m.K, len(r), ui)
@@ -85,6 +98,29 @@ def make_case3(kind, N, r, s, t, seed=0, size="small", perturb=0.02):
     else:
         raise ValueError(kind)
     return dict(mesh=m, xyz=X, u_inf=ui, U=U, name=kind, N=N)
+
+
+def minimal_tet_mesh(kind):
+    """One tetrahedron ("single"), or two sharing one face with their vertices
+    numbered in different orders ("pair"); faces 0 and 1 of each element are
+    slip walls, the other outer faces farfield."""
+    from paper_1208_4772_gb300.inputs import meshes3d
+    P = np.array([[0.0, 0.0, 0.0], [1.0, 0.1, 0.0], [0.2, 1.1, 0.1], [0.1, 0.2, 0.9], [1.0, 1.0, 1.0]])
+    EToV = np.array([[0, 1, 2, 3]] if kind == "single" else [[0, 1, 2, 3], [4, 3, 2, 1]])
+    for k in range(len(EToV)):       # positive orientation
+        v = P[EToV[k]]
+        if np.linalg.det(np.stack([v[1] - v[0], v[2] - v[0], v[3] - v[0]])) < 0:
+            EToV[k, [1, 2]] = EToV[k, [2, 1]]
+    bc = np.zeros((len(EToV), 4), dtype=np.int8)
+    sets = [[frozenset(EToV[k, list(f)]) for f in meshes3d.FACES] for k in range(len(EToV))]
+    count = {}
+    for row in sets:
+        for f in row:
+            count[f] = count.get(f, 0) + 1
+    for k, row in enumerate(sets):
+        for j, f in enumerate(row):
+            bc[k, j] = 0 if count[f] == 2 else (1 if j < 2 else 2)
+    return meshes3d.TetMesh(kind, P[EToV], EToV, bc)
 
 
 def rel_l2_per_var5(a, b):

@@ -3,7 +3,8 @@ configuration the bench times, on sampled outputs.
 
 The meshes are the bench workloads' own (same generators and seeds): the
 NACA 0012 O-mesh with 60,000 elements at N = 4 with artificial viscosity,
-and the 250,000-element cylinder channel at N = 6.  The state is the
+the 250,000-element cylinder channel at N = 6, and the 300,000-tetrahedron
+bump channel at N = 3.  The state is the
 freestream with a smooth perturbation and a little noise, so every term is
 exercised.  The library evaluates the right-hand side of the whole mesh; the
 FP64 oracle evaluates it on 192 random elements and 64 curved wall
@@ -25,7 +26,8 @@ import pytest
 
 import __graft_entry__
 from oracle.dg import Oracle
-from cases import make_case
+from oracle.dg3 import Oracle3
+from cases import make_case, make_case3
 
 pytestmark = pytest.mark.gpu
 
@@ -72,3 +74,33 @@ def test_fullsize_rhs_sampled(B, ctx, kind, N, av, prec):
     err = np.linalg.norm((L[idx] - Lo).transpose(1, 0, 2).reshape(4, -1), axis=1) / scale
     assert np.all(np.isfinite(L)), "non-finite right-hand side"
     assert np.all(err <= TOL[av][prec]), (kind, N, prec, err)
+
+
+@pytest.mark.parametrize("flux", ["llf", "hllc"])
+def test_fullsize_tet_rhs_sampled(B, ctx, flux):
+    """The tetrahedral bump channel of the benchmark (300,000 elements, N = 3,
+    FP32, the tuned tile size), sampled like the triangle meshes; the
+    tolerance is that of the small tetrahedral meshes (1e-5)."""
+    from paper_1208_4772_gb300.inputs import meshes3d
+    N = 3
+    r, s, t = B.dg_tet_reference_nodes(N)
+    case = make_case3("bump", N, r, s, t, size="config")
+    m = case["mesh"]
+    U = case["U"].astype(np.float32).astype(np.float64)
+    p = B.make_params(u_inf=case["u_inf"], prec="fp32", flux=flux)
+    h = B.dg_tet_mesh_upload(ctx, N, m.EToV, m.bc, case["xyz"], p)
+    B.dg_autotune(ctx, h)
+    B.dg_set_state(ctx, h, U)
+    L = B.dg_eval_rhs(ctx, h)
+    B.dg_mesh_free(ctx, h)
+
+    rng = np.random.default_rng(11)
+    curved = np.where(meshes3d.mapped_elements(m, r, s, t))[0]
+    idx = np.unique(np.concatenate([rng.choice(m.K, 192, replace=False), rng.choice(curved, 64, replace=False)]))
+    o = Oracle3(N, m.EToV, m.bc, case["xyz"], u_inf=case["u_inf"], flux=flux)
+    Lo, vol, _ = o.rhs(U, idx, parts=True)
+    V = np.einsum('kij,kvj->kvi', o.geometry(idx).Minv, vol)
+    scale = np.linalg.norm(V.transpose(1, 0, 2).reshape(5, -1), axis=1)
+    err = np.linalg.norm((L[idx] - Lo).transpose(1, 0, 2).reshape(5, -1), axis=1) / scale
+    assert np.all(np.isfinite(L)), "non-finite right-hand side"
+    assert np.all(err <= 1e-5), (flux, err)

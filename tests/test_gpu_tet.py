@@ -71,6 +71,24 @@ def test_tet_rhs_matches_oracle(B, ctx, kind, N, flux, prec, tol):
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+@pytest.mark.parametrize("flux", ["llf", "hllc"])
+@pytest.mark.parametrize("kind,N", [("single", 2), ("single", 4), ("pair", 3), ("pair", 4)])
+def test_tet_minimal_meshes_match_oracle(B, ctx, kind, N, flux, prec, tol):
+    """One element with only boundary faces, and two elements whose shared
+    face has different orientation codes on its two sides (a tile far from
+    full)."""
+    case, U, h, o = setup(B, ctx, kind, N, prec, flux)
+    L = B.dg_eval_rhs(ctx, h)
+    B.dg_mesh_free(ctx, h)
+    Lo, vol, _ = o.rhs(U, parts=True)
+    V = np.einsum('kij,kvj->kvi', o.geometry().Minv, vol)
+    scale = np.linalg.norm(V.transpose(1, 0, 2).reshape(5, -1), axis=1)
+    err = np.linalg.norm((L - Lo).transpose(1, 0, 2).reshape(5, -1), axis=1) / scale
+    assert L.shape == Lo.shape
+    assert np.all(err <= tol), (kind, N, flux, prec, err)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
 @pytest.mark.parametrize("kind,N", [("box", 2), ("bump", 3)])
 def test_tet_steps_match_oracle(B, ctx, kind, N, prec, tol):
     case, U, h, o = setup(B, ctx, kind, N, prec)
