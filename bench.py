@@ -591,7 +591,7 @@ def run_tet(args):
     torch.cuda.set_device(0)
     w = WORKLOADS[args.workload]
     N = w["N"]
-    prec = args.prec if args.prec in ("fp32", "fp64") else "fp32"
+    prec = args.prec if args.prec in ("fp32", "fp64", "tf32") else "fp32"
     r, s_, t = B.dg_tet_reference_nodes(N)
     wl = make_tet_workload(args.workload, r, s_, t)
     m = wl["mesh"]
@@ -643,7 +643,8 @@ def run_tet(args):
     achieved = flops / (launch_ms * 1e-3) / 1e12
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm = float(json.load(open(peaks_path))["hbm_gbs"]) if os.path.exists(peaks_path) else 6800.0
-    roofline = {"kernel": "stage3_kernel (tetrahedra, N=%d, %s)" % (N, prec), "bound": "alu",
+    kname = "stage3_tc_kernel" if prec == "tf32" else "stage3_kernel"
+    roofline = {"kernel": "%s (tetrahedra, N=%d, %s)" % (kname, N, prec), "bound": "alu",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock %.0f MHz" % sm_max,
                 "traffic": TRAFFIC.get((args.workload, prec, args.flux)), "flops_per_launch": flops,

@@ -109,6 +109,7 @@ StageArgs3<Real> make_args3(const MeshData& m, const void* Us, const void* Un, v
     s.gamma = (Real)m.p.gamma;
     for (int v = 0; v < 5; ++v) s.uinf[v] = (Real)m.p.u_inf[v];
     s.tile_e = m.tile_e;
+    s.err = m.err;
     return s;
 }
 
@@ -125,6 +126,8 @@ namespace dgc {
 int enqueue_stage3(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
                    int rhs_only, cudaStream_t st, void* dU) {
     if (m.rsize == 8) return launch_stage3(m.N, make_args3<double>(m, Us, Un, out, a, b, dt, rhs_only, dU), st);
+    if (m.prec == DG_TF32)
+        return launch_stage3_tc(m.N, make_args3<float>(m, Us, Un, out, a, b, dt, rhs_only, dU), st);
     return launch_stage3(m.N, make_args3<float>(m, Us, Un, out, a, b, dt, rhs_only, dU), st);
 }
 
@@ -164,8 +167,10 @@ int dg_tet_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const
     if (K <= 0 || K > (int64_t)1 << 30) return api_fail(ctx, DG_EINVAL, "K out of range");
     if (p->cub_q != 0 && p->cub_q != default_q(N))
         return api_fail(ctx, DG_EINVAL, "device path uses cub_q = ceil((3N+1)/2) only");
-    if (p->prec != DG_FP32 && p->prec != DG_FP64_DEBUG)
-        return api_fail(ctx, DG_EINVAL, "the tetrahedral path computes in DG_FP32 or DG_FP64_DEBUG");
+    if (p->prec != DG_FP32 && p->prec != DG_FP64_DEBUG && p->prec != DG_TF32)
+        return api_fail(ctx, DG_EINVAL, "the tetrahedral path computes in DG_FP32, DG_TF32 or DG_FP64_DEBUG");
+    if (p->prec == DG_TF32 && !supported_degree3_tc(N))
+        return api_fail(ctx, DG_EINVAL, "DG_TF32 on tetrahedra supports N = 2 and 3");
     if (p->av_on) return api_fail(ctx, DG_EINVAL, "artificial viscosity is built for the triangle path");
     if (p->flux != 0 && p->flux != 1)
         return api_fail(ctx, DG_EINVAL, "flux must be 0 (local Lax-Friedrichs) or 1 (HLLC)");
@@ -415,6 +420,14 @@ int dg_tet_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const
         }
         ctx->ops[ikey] = d;
     }
+    if (p->prec == DG_TF32) {
+        const int pe = prepare_stage3_tc(N);
+        if (pe) {
+            api_free_mesh(m);
+            return api_fail(ctx, DG_ECUDA, std::string("tetrahedral tensor-core kernel set-up failed: ") +
+                                               cudaGetErrorString((cudaError_t)pe));
+        }
+    }
     m->ops = ctx->ops[okey];
     m->opsi3 = (const int*)ctx->ops[ikey];
 
@@ -433,7 +446,7 @@ int dg_tet_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const
         api_free_mesh(m);
         return api_fail(ctx, DG_ECUDA, "mesh upload copy failed");
     }
-    {   // a tile size tuned earlier for this kind of mesh
+    if (p->prec != DG_TF32) {   // a tile size tuned earlier for this kind of mesh
         auto it = ctx->tuned_e.find(3000 + N * 32 + (int)rs * 2);
         if (it != ctx->tuned_e.end()) m->tile_e = it->second;
     }

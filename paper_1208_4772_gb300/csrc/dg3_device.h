@@ -78,6 +78,7 @@ struct StageArgs3 {
     Real gamma;
     Real uinf[5];
     int tile_e;         // elements per tile (0: the default of the degree and real type)
+    int* err;           // device error word (tensor-core kernel: a bounded wait ran out)
 };
 
 bool supported_degree3(int N);
@@ -86,5 +87,12 @@ int tile3_default(int N, int rsize);
 bool tile3_fits(int N, int rsize, int E);
 int launch_stage3(int N, const StageArgs3<float>& a, cudaStream_t st);
 int launch_stage3(int N, const StageArgs3<double>& a, cudaStream_t st);
+
+// Tensor-core variant (TF32 products for the two volume terms, FP32 state;
+// degrees 2 and 3, fixed tiles of tile3_tc(N) elements).
+bool supported_degree3_tc(int N);
+int tile3_tc(int N);
+int prepare_stage3_tc(int N);
+int launch_stage3_tc(int N, const StageArgs3<float>& a, cudaStream_t st);
 
 }  // namespace dgc

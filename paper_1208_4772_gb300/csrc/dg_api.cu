@@ -1292,8 +1292,8 @@ int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
     if (nsteps < 1 || nsteps > 1000) return fail(ctx, DG_EINVAL, "nsteps must be in 1..1000");
     if (ncand_out) *ncand_out = 0;
-    if (tensor_prec(m->prec)) {   // fixed tiles of 32 elements = the 128 rows of the products
-        *tile_e_out = 32;
+    if (tensor_prec(m->prec)) {   // fixed tiles: the rows of the products (32 triangles, 5 E <= 128 tetrahedra)
+        *tile_e_out = m->dim == 3 ? tile3_tc(m->N) : 32;
         return DG_OK;
     }
     cudaSetDevice(ctx->device);

@@ -31,6 +31,16 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t row_bytes
     return d;
 }
 
+// The same descriptor with explicit strides (bytes, multiples of 128): lbo
+// between core matrices adjacent along K, sbo between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
 // Instruction descriptor: FP32 accumulate, K-major A and B, M x N.
 // fmt: 2 = TF32 (kind::tf32), 1 = BF16 (kind::f16).
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, uint32_t M, uint32_t N) {

@@ -9,6 +9,11 @@ Tolerances (the arithmetic behind them), as on triangles:
     over sums of N_q (up to 343) terms against the volume term that L is a
     small difference of -> <= 1e-5 of that term's norm per variable.
   * Steps: relative L2 per variable <= 1e-11 (FP64), 1e-5 (FP32).
+  * DG_TF32 (N = 2, 3: the two volume products on the tensor cores): the
+    operands are rounded to TF32 (11-bit significand, relative 2^-11) but
+    act on deviations from the element's mean state and its flux, which
+    are small against the volume term -> <= 2e-3 of the volume term's norm
+    (the bound of the triangle tensor-core path); steps <= 1e-4.
 """
 import numpy as np
 import pytest
@@ -48,13 +53,17 @@ def setup(B, ctx, kind, N, prec, flux="llf", size="small"):
     return case, U, h, o
 
 
+TF32_TOL = 2e-3        # DG_TF32: the products round their operands to TF32
+TF32_STEP_TOL = 1e-4
 CASES = [("box", 2), ("box", 3), ("box", 4), ("wbox", 3), ("bump", 2), ("bump", 3), ("bump", 4)]
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5), ("tf32", TF32_TOL)])
 @pytest.mark.parametrize("flux", ["llf", "hllc"])
 @pytest.mark.parametrize("kind,N", CASES)
 def test_tet_rhs_matches_oracle(B, ctx, kind, N, flux, prec, tol):
+    if prec == "tf32" and N > 3:
+        pytest.skip("the tensor-core tetrahedral kernel covers N = 2, 3")
     case, U, h, o = setup(B, ctx, kind, N, prec, flux)
     info = B.dg_mesh_info(ctx, h)
     assert (info["dim"], info["nvar"], info["N"]) == (3, 5, N)
@@ -70,10 +79,12 @@ def test_tet_rhs_matches_oracle(B, ctx, kind, N, flux, prec, tol):
     assert np.all(err <= tol), (kind, N, flux, prec, err)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5), ("tf32", TF32_TOL)])
 @pytest.mark.parametrize("flux", ["llf", "hllc"])
 @pytest.mark.parametrize("kind,N", [("single", 2), ("single", 4), ("pair", 3), ("pair", 4)])
 def test_tet_minimal_meshes_match_oracle(B, ctx, kind, N, flux, prec, tol):
+    if prec == "tf32" and N > 3:
+        pytest.skip("the tensor-core tetrahedral kernel covers N = 2, 3")
     """One element with only boundary faces, and two elements whose shared
     face has different orientation codes on its two sides (a tile far from
     full)."""
@@ -88,7 +99,7 @@ def test_tet_minimal_meshes_match_oracle(B, ctx, kind, N, flux, prec, tol):
     assert np.all(err <= tol), (kind, N, flux, prec, err)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5), ("tf32", TF32_STEP_TOL)])
 @pytest.mark.parametrize("kind,N", [("box", 2), ("bump", 3)])
 def test_tet_steps_match_oracle(B, ctx, kind, N, prec, tol):
     case, U, h, o = setup(B, ctx, kind, N, prec)
@@ -154,11 +165,17 @@ def test_tet_argument_errors(B, ctx):
     r, s, t = B.dg_tet_reference_nodes(2)
     case = make_case3("bump", 2, r, s, t, size="tiny")
     m = case["mesh"]
-    for kw in ({"prec": "tf32"}, {"prec": "fp32", "av_on": True}):
+    for kw in ({"prec": "bf16x3"}, {"prec": "fp32", "av_on": True}):
         p = B.make_params(u_inf=case["u_inf"], **kw)
         with pytest.raises(B.DgError) as e:
             B.dg_tet_mesh_upload(ctx, 2, m.EToV, m.bc, case["xyz"], p)
         assert e.value.status == B.DG_EINVAL
+    r4, s4, t4 = B.dg_tet_reference_nodes(4)
+    c4 = make_case3("box", 4, r4, s4, t4, size="tiny")
+    with pytest.raises(B.DgError) as e:   # the tensor-core tetrahedral kernel covers N = 2, 3
+        B.dg_tet_mesh_upload(ctx, 4, c4["mesh"].EToV, c4["mesh"].bc, c4["xyz"],
+                             B.make_params(u_inf=c4["u_inf"], prec="tf32"))
+    assert e.value.status == B.DG_EINVAL
     p = B.make_params(u_inf=case["u_inf"], prec="fp32")
     bad = m.bc.copy()
     bad[np.argwhere(m.bc == 0)[0][0], np.argwhere(m.bc == 0)[0][1]] = 1
