@@ -372,6 +372,20 @@ __global__ void __launch_bounds__(THREADS, 2) stage3_tc_kernel(const StageArgs3<
             atomicOr(p.err, 16);
             s_abort = 1;
         }
+        // the second operand of the stage combination (U^n, or the
+        // low-storage register) for this thread's outputs, loaded now so that
+        // its latency overlaps the face terms
+        constexpr int NIT = (E * 5 * NP + THREADS - 1) / THREADS;
+        float aux[NIT];
+        {
+            const bool need = !p.rhs_only && p.a != 0.f;
+#pragma unroll
+            for (int k = 0; k < NIT; ++k) {
+                const int i = tid + k * THREADS;
+                const long long at = e0 * 5 * NP + i;
+                aux[k] = (need && i < ne * 5 * NP) ? (p.dU ? p.dU[at] : p.Un[at]) : 0.f;
+            }
+        }
         tc::fence_before_sync();
         __syncthreads();
         // ---- face terms on the CUDA cores (the volume operands' storage is free)
@@ -395,7 +409,38 @@ __global__ void __launch_bounds__(THREADS, 2) stage3_tc_kernel(const StageArgs3<
         __syncthreads();
         combine3<N, float, 1>(ne, 0, sUf, sFpos, sR);
         __syncthreads();
-        update3<N, float, GST>(p, e0, ne, sR, sMiT, sG, sU);
+        // L = M_k^-1 R and the stage combination
+#pragma unroll
+        for (int k = 0; k < NIT; ++k) {
+            const int i = tid + k * THREADS;
+            if (i >= ne * 5 * NP) break;
+            const int e = i / (5 * NP), r = i - e * 5 * NP, v = r / NP, n = r - v * NP;
+            const float* rr = sR + (e * 5 + v) * NP;
+            const long long eg = e0 + e;
+            float Lv = 0.f;
+            if (eg < p.Kaff) {
+#pragma unroll
+                for (int j = 0; j < NP; ++j) Lv += sMiT[j * NP + n] * rr[j];
+                Lv *= sG[e * GST + 9];
+            } else {
+                const float* mi = p.geoC + (eg - p.Kaff) * CS + 9 * NQ + 16 * NG;
+#pragma unroll
+                for (int j = 0; j < NP; ++j) Lv += mi[j * NP + n] * rr[j];
+            }
+            const long long at = e0 * 5 * NP + i;
+            const float us = sU[(e * 5 + v) * NPP + n];
+            float out;
+            if (p.rhs_only) {
+                out = Lv;
+            } else if (p.dU) {
+                const float d = p.a * aux[k] + p.dt * Lv;
+                p.dU[at] = d;
+                out = us + p.b * d;
+            } else {
+                out = p.a * aux[k] + p.b * (us + p.dt * Lv);
+            }
+            p.Uout[at] = out;
+        }
     }
     // every copy and MMA of this CTA complete before it exits
     tc::cp_async_wait_all();
