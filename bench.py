@@ -580,8 +580,10 @@ def run_ours(args):
 def run_tet(args):
     """The tetrahedral stage kernel on one mesh: SSP-RK3 steps through
     dg_step, L2 flushed before every timed step; a second pass with events
-    around every kernel gives the stage kernel's launch time.  The path runs
-    on the CUDA cores in FP32, so the roofline is the FP32 ALU peak."""
+    around every kernel gives the stage kernel's launch time.  FP32 runs on
+    the CUDA cores, TF32 (the default) puts the two volume products on the
+    tensor cores; the roofline is the FP32 ALU peak on the method's
+    algorithmic flops either way."""
     import numpy as np
     import torch
     import __graft_entry__

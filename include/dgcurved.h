@@ -46,7 +46,11 @@
  *     dg_mesh_bytes, dg_mesh_free, dg_set_profiling, dg_kernel_times and
  *     dg_autotune accept tetrahedral meshes with the five-variable layout;
  *     dg_batch_step and dg_prolong return DG_EINVAL for them.  Precisions
- *     DG_FP32 and DG_FP64_DEBUG; no artificial viscosity.
+ *     DG_FP32, DG_FP64_DEBUG and, for N = 2 and 3, DG_TF32 (the
+ *     interpolation to the cubature points and the three weighted
+ *     derivative products on the tensor cores, on deviations from each
+ *     element's mean state and its flux; the face terms in FP32); no
+ *     artificial viscosity.
  */
 #ifndef DGCURVED_H
 #define DGCURVED_H
@@ -162,7 +166,8 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
  *                whose nodes are not the affine image of their vertex nodes
  *                are treated as curved (per-point geometric factors and their
  *                own mass matrix)
- *   p            parameters (copied); prec DG_FP32 or DG_FP64_DEBUG, av_on 0
+ *   p            parameters (copied); prec DG_FP32, DG_FP64_DEBUG, or DG_TF32
+ *                with N <= 3; av_on 0
  * The state is set to 0.  Errors: DG_EINVAL (N, K, prec or av_on out of
  * range, a face shared by more than two elements, bc inconsistent with the
  * face matching, J <= 0 at a cubature point), DG_ENOMEM, DG_ECUDA. */
@@ -249,8 +254,9 @@ int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to);
  * and keeps the fastest for m.  The choice also applies to the context's
  * other meshes of the same degree, precision and viscosity setting, and to
  * those uploaded later (and so to dg_batch_step).  Outputs: *tile_e_out (the
- * chosen size; 32 for DG_TF32 / DG_BF16X3, whose tensor-core tiles are
- * fixed at the 128 rows of the products, nothing timed); optional
+ * chosen size; for DG_TF32 / DG_BF16X3, whose tensor-core tiles are fixed
+ * by the 128 rows of the products, the fixed size -- 32 triangles, 8
+ * tetrahedra at N = 3, 16 at N = 2 -- and nothing timed); optional
  * cand_out[8], ms_out[8] (candidates and milliseconds per step) and
  * *ncand_out (number of candidates), each may be NULL.  Synchronises the
  * context's stream.  The paper has no counterpart (its block per element is
