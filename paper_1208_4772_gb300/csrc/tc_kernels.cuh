@@ -787,7 +787,27 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
 
     // ---------------- epilogue: L = D2 / J into shared memory (the G1
     // operand region), then a coalesced pass over the tile for the stage
-    // combination
+    // combination, whose inputs from global memory (U_s, and U^n or the
+    // low-storage register) are loaded here, while the last products run
+    const long long base = e0 * 4 * NP;
+    const int n4 = ne * NP;   // float4 groups: ne * 4 * NP / 4
+    constexpr int NI = (32 * NP + THREADS - 1) / THREADS;
+    float4 pre_s[NI], pre_n[NI];
+    {
+        const float4* us = reinterpret_cast<const float4*>(p.Us + base);
+        const float4* un = reinterpret_cast<const float4*>((p.dU ? p.dU : p.Un) + base);
+        const bool need = !p.rhs_only && p.a != 0.f;
+#pragma unroll
+        for (int k = 0; k < NI; ++k) {
+            const int i = tid + k * THREADS;
+            pre_s[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            pre_n[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < n4) {
+                if (!p.rhs_only) pre_s[k] = us[i];
+                if (need) pre_n[k] = un[i];
+            }
+        }
+    }
     wait_buf(0);
     wait_buf(1);
     tc::fence_after_sync();
@@ -807,32 +827,30 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         }
         tc::fence_before_sync();
         __syncthreads();
-        const long long base = e0 * 4 * NP;
-        const int n4 = ne * NP;   // float4 groups: ne * 4 * NP / 4
-        const float4* us = reinterpret_cast<const float4*>(p.Us + base);
-        const float4* un = reinterpret_cast<const float4*>(p.Un + base);
         float4* uo = reinterpret_cast<float4*>(p.Uout + base);
         float4* lo = reinterpret_cast<float4*>(sOut);
         const bool sense = SENSE && p.eps_next != nullptr && !p.rhs_only;
-        for (int i = tid; i < n4; i += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < NI; ++k) {
+            const int i = tid + k * THREADS;
+            if (i >= n4) break;
             const float4 L4 = lo[i];
+            const float4 s4 = pre_s[k];
             float4 r;
             if (p.rhs_only) {
                 r = L4;
             } else if (p.dU) {   // low-storage RK: dU <- a dU + dt L, U = Us + b dU
                 float4* du = reinterpret_cast<float4*>(p.dU + base);
-                const float4 s4 = us[i];
-                float4 d = p.a != 0.f ? du[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-                d = make_float4(p.a * d.x + p.dt * L4.x, p.a * d.y + p.dt * L4.y, p.a * d.z + p.dt * L4.z,
-                                p.a * d.w + p.dt * L4.w);
+                const float4 d0 = pre_n[k];   // zero when a = 0
+                const float4 d = make_float4(p.a * d0.x + p.dt * L4.x, p.a * d0.y + p.dt * L4.y,
+                                             p.a * d0.z + p.dt * L4.z, p.a * d0.w + p.dt * L4.w);
                 du[i] = d;
                 r = make_float4(s4.x + p.b * d.x, s4.y + p.b * d.y, s4.z + p.b * d.z, s4.w + p.b * d.w);
             } else {
-                const float4 s4 = us[i];
                 r = make_float4(p.b * (s4.x + p.dt * L4.x), p.b * (s4.y + p.dt * L4.y), p.b * (s4.z + p.dt * L4.z),
                                 p.b * (s4.w + p.dt * L4.w));
                 if (p.a != 0.f) {
-                    const float4 n4v = un[i];
+                    const float4 n4v = pre_n[k];
                     r.x += p.a * n4v.x;
                     r.y += p.a * n4v.y;
                     r.z += p.a * n4v.z;
