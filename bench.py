@@ -41,10 +41,11 @@ UNIT = "DOF-updates/s"
 DTYPE = {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3", "fp64": "f64"}
 
 # DRAM bytes (read + write) of one stage-kernel launch from an ncu capture of
-# the default command (summary in profiles/stage_kernel_tc_naca0012_n4_av.md);
-# keyed by (workload, products, flux) and only valid for the kernel source it was
-# taken on.
-TRAFFIC = {("naca0012_m0.8_n4_av", "tf32", "llf"): 31.89e6}
+# the command (summaries in profiles/stage_kernel_tc_naca0012_n4_av.md and
+# profiles/stage3_tc_kernel_bump3d_n3.md); keyed by (workload, products, flux)
+# and only valid for the kernel source it was taken on.
+TRAFFIC = {("naca0012_m0.8_n4_av", "tf32", "llf"): 31.893e6,
+           ("bump3d_m0.5_n3", "tf32", "llf"): 536.98e6}
 
 WORKLOADS = {
     "naca0012_m0.8_n4_av": dict(kind="naca", N=4, n_t=300, n_r=100, mach=0.8, aoa=1.25, av=True,
