@@ -309,6 +309,17 @@ int dg_av_count(dg_ctx* ctx, dg_mesh m, int64_t* out);
  * the work itself is not cancelled. */
 int dg_sync(dg_ctx* ctx, double timeout_s);
 
+/* Diagnostics of the device-side waits.  Every wait inside the library's
+ * kernels (on an mbarrier: tensor-core products, bulk copies) polls a
+ * bounded number of times; a wait that runs out sets a bit in the mesh's
+ * error word, the kernel finishes without the result, and the next call
+ * that checks the word returns DG_ETIMEOUT.  This call runs one such wait
+ * on a barrier of one expected arrival -- with arrive = 0 nothing arrives --
+ * polling at most `limit` (1..2^26) times, on the context's stream, and
+ * stores 1 in *out if the wait ran out, 0 if it completed.  The context
+ * stays usable either way.  Synchronises the context's stream. */
+int dg_selftest_bounded_wait(dg_ctx* ctx, uint32_t limit, int arrive, int32_t* out);
+
 /* Description of the last failure on ctx (or of the last failure of a call
  * without a context when ctx is NULL). */
 const char* dg_last_error(dg_ctx* ctx);

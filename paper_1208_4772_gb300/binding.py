@@ -78,6 +78,7 @@ def load():
         "dg_residual": (I, [P, C.c_int32, dp, dp]),
         "dg_batch_step": (I, [P, I, C.POINTER(C.c_int32), dp, I]),
         "dg_sync": (I, [P, D]),
+        "dg_selftest_bounded_wait": (I, [P, C.c_uint32, I, C.POINTER(C.c_int32)]),
         "dg_set_profiling": (I, [P, C.c_int32, I]),
         "dg_residual_norms_noalloc": (I, [P, I64, C.c_int32, P, P]),
         "dg_kernel_times": (I, [P, C.c_int32, dp]),
@@ -247,6 +248,13 @@ def dg_batch_step(ctx, meshes, dts, nsteps):
 
 def dg_sync(ctx, timeout_s=0.0):
     return _check(load().dg_sync(ctx, float(timeout_s)), ctx)
+
+
+def dg_selftest_bounded_wait(ctx, limit, arrive):
+    """1 if a bounded device wait with nothing arriving ran out, 0 if it completed."""
+    out = C.c_int32(-1)
+    _check(load().dg_selftest_bounded_wait(ctx, C.c_uint32(int(limit)), int(arrive), C.byref(out)), ctx)
+    return out.value
 
 
 def dg_residual_norms_noalloc(values_dev_ptr, K, Np, out8_dev_ptr, stream=None):

@@ -1213,6 +1213,23 @@ int dg_sync(dg_ctx* ctx, double timeout_s) {
     }
 }
 
+int dg_selftest_bounded_wait(dg_ctx* ctx, uint32_t limit, int arrive, int32_t* out) {
+    if (!ctx || !out) return fail(ctx, DG_EINVAL, "NULL argument");
+    if (limit == 0 || limit > (1u << 26)) return fail(ctx, DG_EINVAL, "limit must be in 1..2^26");
+    cudaSetDevice(ctx->device);
+    int* d = nullptr;
+    CUDA_OK(ctx, cudaMalloc(&d, sizeof(int)));
+    int h = -1;
+    cudaError_t e = cudaMemsetAsync(d, 0xff, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = (cudaError_t)launch_bounded_wait(limit, arrive ? 1 : 0, d, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(ctx, DG_ECUDA, std::string("bounded-wait self-test: ") + cudaGetErrorString(e));
+    *out = h;
+    return DG_OK;
+}
+
 int dg_step_lserk(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
     if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
     MeshData* m = find(ctx, h);

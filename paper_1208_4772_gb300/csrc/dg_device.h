@@ -171,6 +171,9 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned threads, 
 }
 
 // Generic kernels (kernels_common.cu)
+// Diagnostics: one bounded mbarrier wait (see dg_selftest_bounded_wait).
+int launch_bounded_wait(uint32_t limit, int arrive, int* status, cudaStream_t st);
+
 template <typename Real>
 int launch_residual(const Real* L, int nvar, long long K, int NP, double* partial, double* out,
                     cudaStream_t st);   // out: nvar max-norms, then nvar Euclidean norms

@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include "dg_device.h"
+#include "tc_ptx.cuh"
 
 namespace dgc {
 
@@ -144,5 +145,27 @@ template int launch_permute<float>(const float*, float*, const long long*, long 
 template int launch_permute<double>(const double*, double*, const long long*, long long, int, cudaStream_t);
 template int launch_prolong<float>(const float*, float*, const float*, long long, int, int, cudaStream_t);
 template int launch_prolong<double>(const double*, double*, const double*, long long, int, int, cudaStream_t);
+
+namespace {
+
+// One thread waits, with the bounded mbarrier wait every kernel of the
+// library uses, on a barrier of one expected arrival; with arrive = 0
+// nothing arrives, so the wait runs out after `limit` polls and the kernel
+// records that in *status (1) instead of hanging.
+__global__ void bounded_wait_kernel(uint32_t limit, int arrive, int* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    tc::mbar_init(&bar, 1);
+    tc::mbar_fence_init();
+    if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(tc::smem_addr(&bar)) : "memory");
+    *status = tc::mbar_wait(&bar, 0, limit) ? 0 : 1;
+}
+
+}  // namespace
+
+int launch_bounded_wait(uint32_t limit, int arrive, int* status, cudaStream_t st) {
+    bounded_wait_kernel<<<1, 32, 0, st>>>(limit, arrive, status);
+    return (int)cudaGetLastError();
+}
 
 }  // namespace dgc
