@@ -42,8 +42,8 @@ DTYPE = {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3", "fp64": "f64"}
 
 # DRAM bytes (read + write) of one stage-kernel launch from an ncu capture of
 # the command (summaries in profiles/stage_kernel_tc_naca0012_n4_av.md and
-# profiles/stage3_tc_kernel_bump3d_n3.md); keyed by (workload, products, flux)
-# and only valid for the kernel source it was taken on.
+# profiles/stage3_tc_kernel_bump3d_n3.md); keyed by (workload, products, flux),
+# SSP-RK3 stages only, and only valid for the kernel source it was taken on.
 TRAFFIC = {("naca0012_m0.8_n4_av", "tf32", "llf"): 31.893e6,
            ("bump3d_m0.5_n3", "tf32", "llf"): 536.98e6}
 
@@ -518,7 +518,7 @@ def run_ours(args):
     achieved = bytes_launch / (stage_launch_ms * 1e-3) / 1e9
     roofline = {"kernel": "stage_kernel (N=%d, AV %s)" % (N, "on" if wl["av"] else "off"), "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_src, "traffic": TRAFFIC.get((args.workload, args.prec, args.flux)),
+                "peak_source": peak_src, "traffic": TRAFFIC.get((args.workload, args.prec, args.flux)) if args.integrator == "ssp3" else None,
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": stage_launch_ms,
                 "dominant_kind_by_time": kinds[dom]}
 
@@ -650,7 +650,8 @@ def run_tet(args):
     roofline = {"kernel": "%s (tetrahedra, N=%d, %s)" % (kname, N, prec), "bound": "alu",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock %.0f MHz" % sm_max,
-                "traffic": TRAFFIC.get((args.workload, prec, args.flux)), "flops_per_launch": flops,
+                "traffic": TRAFFIC.get((args.workload, prec, args.flux)) if args.integrator == "ssp3" else None,
+                "flops_per_launch": flops,
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": launch_ms,
                 "hbm_gbs": bytes_launch / (launch_ms * 1e-3) / 1e9,
                 "hbm_frac": bytes_launch / (launch_ms * 1e-3) / 1e9 / hbm}
