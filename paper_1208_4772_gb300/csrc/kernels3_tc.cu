@@ -80,8 +80,8 @@ struct TC3 {
     // the volume operands, then (same storage) the face arrays
     static constexpr int O_A1 = al(O_SU + E * 5 * NP * 4);                // NPK / 4 columns x RG groups
     static constexpr int O_A2 = al(O_A1 + NPK / 4 * LBO_A);               // KC / 4 columns x RG groups
-    static constexpr int O_UQ = al(O_A2 + KC / 4 * LBO_A);                // [QC][ROWS]
-    static constexpr int VOL_END = O_UQ + QC * ROWS * 4;
+    static constexpr int O_UQ = al(O_A2 + KC / 4 * LBO_A);                // [2][QC][ROWS]
+    static constexpr int VOL_END = O_UQ + 2 * QC * ROWS * 4;
     static constexpr int O_UF = O_A1;                                     // [E][4][5][NFPP], then the lifted terms
     static constexpr int O_FS = al(O_UF + E * 20 * NFPP * 4);             // [E][4][5][NGP]
     static constexpr int FACE_END = O_FS + E * 20 * NGP * 4;
@@ -268,9 +268,10 @@ __global__ void __launch_bounds__(THREADS, 2) stage3_tc_kernel(const StageArgs3<
         bool ok = tc::mbar_wait(&bars[0], ph1 & 1);
         ph1++;
         tc::fence_after_sync();
-        for (int c = 0; c < C::NCH; ++c) {
-            // ---- the chunk's states at its cubature points (plus the mean)
-            // to sUq [QC][ROWS]; the two halves of the CTA take half the columns
+        // ---- a chunk's states at its cubature points (plus the mean) to
+        // sUq[b] [QC][ROWS], by the warps whose TMEM lanes hold rows; the two
+        // halves of the CTA take half the columns each
+        auto readout = [&](int c, float* dst) {
             if (quad < C::QU) {
                 constexpr int HC = QC / 2;
                 float x[HC];
@@ -282,22 +283,27 @@ __global__ void __launch_bounds__(THREADS, 2) stage3_tc_kernel(const StageArgs3<
                 if (row < ROWS) {
                     const float m = sBar[(row / 5) * BST + row % 5];
 #pragma unroll
-                    for (int k = 0; k < HC; ++k) sUq[(half * HC + k) * ROWS + row] = x[k] + m;
+                    for (int k = 0; k < HC; ++k) dst[(half * HC + k) * ROWS + row] = x[k] + m;
                 }
             }
-            tc::fence_before_sync();
+        };
+        readout(0, sUq);
+        tc::fence_before_sync();
+        __syncthreads();
+        for (int c = 0; c < C::NCH; ++c) {
+            // the next chunk's readout overlaps the previous chunk's G2
+            if (c + 1 < C::NCH) readout(c + 1, sUq + ((c + 1) & 1) * QC * ROWS);
             if (c > 0) {   // the previous chunk's G2 has read A2
                 ok &= tc::mbar_wait(&bars[1], ph2 & 1);
                 ph2++;
             }
-            __syncthreads();
             // ---- one point of one element per thread: the contravariant flux
             // deviations, rounded to TF32, as A2 (row 5 e + v, K = a QC + point)
             {
                 const int e = tid % E, qq = tid / E, q = c * QC + qq;
                 float g[3][5];
                 if (e < ne && q < NQ) {
-                    const float* uq = sUq + qq * ROWS + 5 * e;
+                    const float* uq = sUq + (c & 1) * QC * ROWS + qq * ROWS + 5 * e;
                     float u[5];
 #pragma unroll
                     for (int v = 0; v < 5; ++v) u[v] = uq[v];
@@ -340,6 +346,7 @@ __global__ void __launch_bounds__(THREADS, 2) stage3_tc_kernel(const StageArgs3<
                             tc::to_tf32(g[a][v]);
             }
             tc::fence_async_smem();
+            tc::fence_before_sync();
             __syncthreads();
             if (tid == 0) {   // G2: this chunk's share of the volume term
                 tc::fence_after_sync();
