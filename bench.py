@@ -942,6 +942,8 @@ def main():
         return 0
     if args.impl == "reference":
         return run_reference(args)
+    if WORKLOADS[args.workload]["kind"] in ("batch", "serve", "prefine", "tet") and int(os.environ.get("RANK", "0")) != 0:
+        return 0    # these workloads run on one GPU: under a multi-rank launch rank 0 alone runs and prints
     if args.workload == "batch64":
         return run_batch(args)
     if args.workload == "serve":
