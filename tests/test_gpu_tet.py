@@ -222,7 +222,7 @@ def test_tet_tf32_autotune_reports_fixed_tiles(B, ctx):
     """The tensor-core tetrahedral kernel has fixed tiles (the rows of its
     products): the autotuner times nothing and reports them."""
     for N, E in ((2, 16), (3, 8)):
-        case, U, h, o = setup(B, ctx, "box", N, "tf32", size="tiny")
+        case, U, h, o = setup(B, ctx, "box", N, "tf32")
         best, table = B.dg_autotune(ctx, h, 2)
         B.dg_mesh_free(ctx, h)
         assert best == E and table == {}
