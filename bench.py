@@ -45,7 +45,7 @@ DTYPE = {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3", "fp64": "f64"}
 # profiles/stage3_tc_kernel_bump3d_n3.md); keyed by (workload, products, flux),
 # SSP-RK3 stages only, and only valid for the kernel source it was taken on.
 TRAFFIC = {("naca0012_m0.8_n4_av", "tf32", "llf"): 31.893e6,
-           ("bump3d_m0.5_n3", "tf32", "llf"): 536.98e6}
+           ("bump3d_m0.5_n3", "tf32", "llf"): 537.36e6}
 
 WORKLOADS = {
     "naca0012_m0.8_n4_av": dict(kind="naca", N=4, n_t=300, n_r=100, mach=0.8, aoa=1.25, av=True,
