@@ -44,8 +44,8 @@
  *   - dg_set_state, dg_get_state, dg_set_state_device, dg_get_state_device,
  *     dg_eval_rhs, dg_step, dg_step_lserk, dg_residual, dg_mesh_info,
  *     dg_mesh_bytes, dg_mesh_free, dg_set_profiling, dg_kernel_times and
- *     dg_autotune accept tetrahedral meshes with the five-variable layout;
- *     dg_batch_step and dg_prolong return DG_EINVAL for them.  Precisions
+ *     dg_autotune and dg_prolong accept tetrahedral meshes with the
+ *     five-variable layout; dg_batch_step returns DG_EINVAL for them.  Precisions
  *     DG_FP32, DG_FP64_DEBUG and, for N = 2 and 3, DG_TF32 (the
  *     interpolation to the cubature points and the three weighted
  *     derivative products on the tensor cores, on deviations from each
@@ -240,8 +240,9 @@ int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* ms, const double* dts, int 
  * degree-N polynomial in every element, i.e. the modal coefficients of
  * degree <= N carried over and the higher ones zero (the basis is
  * hierarchical).  `from` and `to` must be two uploads of the same mesh
- * (same K, connectivity and element order) with N_from <= N_to and the same
- * state type (FP32 precisions together, or FP64_DEBUG with FP64_DEBUG).
+ * (both triangle or both tetrahedral meshes; same K, connectivity and
+ * element order) with N_from <= N_to and the same state type (FP32
+ * precisions together, or FP64_DEBUG with FP64_DEBUG).
  * DG_EINVAL otherwise.  Synchronises the context's stream. */
 int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to);
 

@@ -13,7 +13,7 @@ Test infrastructure only.
 """
 import numpy as np
 
-from . import basis, nodes
+from . import basis, nodes, tet
 
 
 def prolongation(N, M):
@@ -28,3 +28,18 @@ def prolongation(N, M):
 def prolong_state(U, N, M):
     """U[K][4][N_p(N)] -> [K][4][N_p(M)]."""
     return np.einsum('ij,kvj->kvi', prolongation(N, M), U)
+
+
+def prolongation3(N, M):
+    """The same on tetrahedra (paper Sec. 5 refines its 3D runs from p = 2
+    to 3 and 4): P = V_N(r_M) V_N^-1 with the tetrahedral modes and nodes."""
+    if M < N:
+        raise ValueError("prolongation goes from a lower to a higher degree")
+    rN, sN, tN = tet.warp_blend_nodes_3d(N)
+    rM, sM, tM = tet.warp_blend_nodes_3d(M)
+    return tet.vandermonde(N, rM, sM, tM) @ np.linalg.inv(tet.vandermonde(N, rN, sN, tN))
+
+
+def prolong_state3(U, N, M):
+    """U[K][5][N_p(N)] -> [K][5][N_p(M)]."""
+    return np.einsum('ij,kvj->kvi', prolongation3(N, M), U)

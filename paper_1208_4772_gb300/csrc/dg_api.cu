@@ -23,6 +23,7 @@
 #include "dg_device.h"
 #include "dgcurved.h"
 #include "refops.h"
+#include "refops3.h"
 #include "dg_internal.h"
 #include "dg_batch.h"
 
@@ -1268,13 +1269,13 @@ int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to) {
     MeshData* a = find(ctx, from);
     MeshData* b = find(ctx, to);
     if (!a || !b) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
-    if (a->dim != 2 || b->dim != 2) return fail(ctx, DG_EINVAL, "prolongation is built for triangle meshes");
-    if (a == b || a->K != b->K || a->N > b->N || a->rsize != b->rsize || a->perm != b->perm)
+    if (a == b || a->dim != b->dim || a->K != b->K || a->N > b->N || a->rsize != b->rsize || a->perm != b->perm)
         return fail(ctx, DG_EINVAL,
                     "prolongation needs two uploads of one mesh, the target of degree >= the source, one state type");
     std::vector<double> P;
     std::string err;
-    if (!build_prolongation(a->N, b->N, P, err)) return fail(ctx, DG_EINVAL, err);
+    const bool ok = a->dim == 3 ? build_prolongation3(a->N, b->N, P, err) : build_prolongation(a->N, b->N, P, err);
+    if (!ok) return fail(ctx, DG_EINVAL, err);
     cudaSetDevice(ctx->device);
     void* dP = nullptr;
     const size_t rs = a->rsize;
@@ -1292,9 +1293,9 @@ int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to) {
     int e = (int)ce;
     if (!e)
         e = rs == 8 ? launch_prolong<double>((const double*)a->U[0], (double*)b->U[0], (const double*)dP, a->K,
-                                             a->Np, b->Np, ctx->stream)
-                    : launch_prolong<float>((const float*)a->U[0], (float*)b->U[0], (const float*)dP, a->K, a->Np,
-                                            b->Np, ctx->stream);
+                                             a->nvar, a->Np, b->Np, ctx->stream)
+                    : launch_prolong<float>((const float*)a->U[0], (float*)b->U[0], (const float*)dP, a->K, a->nvar,
+                                            a->Np, b->Np, ctx->stream);
     if (!e) e = (int)cudaStreamSynchronize(ctx->stream);
     cudaFree(dP);
     if (e) return fail(ctx, DG_ECUDA, std::string("prolongation failed: ") + cudaGetErrorString((cudaError_t)e));

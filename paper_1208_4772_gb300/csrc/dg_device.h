@@ -180,7 +180,8 @@ int launch_residual(const Real* L, int nvar, long long K, int NP, double* partia
 template <typename Real>
 int launch_permute(const Real* src, Real* dst, const long long* map, long long K, int rowlen, cudaStream_t st);
 template <typename Real>
-int launch_prolong(const Real* in, Real* out, const Real* P, long long K, int npf, int npt, cudaStream_t st);
+int launch_prolong(const Real* in, Real* out, const Real* P, long long K, int nvar, int npf, int npt,
+                   cudaStream_t st);
 int residual_blocks();
 
 }  // namespace dgc

@@ -340,4 +340,29 @@ bool build_refops3(int N, RefOps3& o, std::string& err) {
     return true;
 }
 
+// Prolongation between tetrahedral degrees (paper Sec. 5, p-refinement):
+// the nodal values at the degree-Nt nodes of the degree-Nf interpolant,
+// P = V_f(r_t) V_f^-1 ([Np(Nt)][Np(Nf)]); the modes are hierarchical, so
+// the embedded field has no modes of degree above Nf.
+bool build_prolongation3(int Nf, int Nt, std::vector<double>& P, std::string& err) {
+    if (Nf < 1 || Nt < Nf) {
+        err = "prolongation needs 1 <= Nf <= Nt";
+        return false;
+    }
+    RefOps3 from;
+    if (!build_refops3(Nf, from, err)) return false;
+    std::vector<double> rt, st, tt;
+    nodes3(Nt, rt, st, tt, nullptr);
+    std::vector<std::tuple<int, int, int>> M;
+    modes3(Nf, M);
+    const int npf = (int)M.size(), npt = (int)rt.size();
+    std::vector<double> Vft((size_t)npt * npf);
+    for (int k = 0; k < npt; ++k)
+        for (int m = 0; m < npf; ++m)
+            psi3(std::get<0>(M[m]), std::get<1>(M[m]), std::get<2>(M[m]), rt[k], st[k], tt[k],
+                 &Vft[(size_t)k * npf + m], nullptr, nullptr, nullptr);
+    detail::matmul(Vft, from.Vinv, P, npt, npf, npf);
+    return true;
+}
+
 }  // namespace dgc

@@ -39,5 +39,6 @@ struct RefOps3 {
 int n_modes3(int N);
 int n_face_nodes3(int N);
 bool build_refops3(int N, RefOps3& out, std::string& err);
+bool build_prolongation3(int Nf, int Nt, std::vector<double>& P, std::string& err);
 
 }  // namespace dgc

@@ -1,7 +1,8 @@
 """dg_prolong (paper Sec. 5, p-refinement) against the oracle's
 prolongation: the state of one upload of a mesh embedded into an upload of
-the same mesh at a higher degree.  FP64-debug to 1e-12, FP32 to 1e-6
-(FP32 operator and sums); bad pairs are refused."""
+the same mesh at a higher degree, on triangles and on tetrahedra.
+FP64-debug to 1e-12, FP32 to 1e-6 (FP32 operator and sums); bad pairs are
+refused."""
 import numpy as np
 import pytest
 
@@ -62,6 +63,59 @@ def test_prolong_refuses_other_mesh(B, ctx):
     m2 = meshes.cylinder_channel(n_t=24, n_r=5, seed=1002)
     h1, _ = upload(B, ctx, m1, 2, "fp32", ui)
     h2, _ = upload(B, ctx, m2, 3, "fp32", ui)
+    with pytest.raises(B.DgError) as e:
+        B.dg_prolong(ctx, h1, h2)
+    assert e.value.status == B.DG_EINVAL
+    B.dg_mesh_free(ctx, h1)
+    B.dg_mesh_free(ctx, h2)
+
+
+@pytest.mark.parametrize("kind", ["box", "wbox"])
+@pytest.mark.parametrize("prec,tol,N,M", [("fp64", 1e-12, 2, 3), ("fp64", 1e-12, 2, 4), ("fp64", 1e-12, 3, 4),
+                                          ("fp32", 1e-6, 2, 4), ("tf32", 1e-6, 2, 3)])
+def test_prolong_tetrahedra_matches_oracle(B, ctx, kind, prec, tol, N, M):
+    """The paper's own use (Sec. 5): 3D runs refined from p = 2 to 3 and 4.
+    Two uploads of one tetrahedral mesh (affine, or every element curved);
+    the prolonged state against the oracle's, then one SSP-RK3 step at the
+    higher degree against the oracle's step of the prolonged state."""
+    from cases import make_case3
+    from oracle.dg3 import Oracle3
+    from oracle.prefine import prolong_state3
+    rN, sN, tN = B.dg_tet_reference_nodes(N)
+    rM, sM, tM = B.dg_tet_reference_nodes(M)
+    cN = make_case3(kind, N, rN, sN, tN)
+    cM = make_case3(kind, M, rM, sM, tM)
+    m = cN["mesh"]
+    hN = B.dg_tet_mesh_upload(ctx, N, m.EToV, m.bc, cN["xyz"], B.make_params(u_inf=cN["u_inf"], prec=prec))
+    mprec = "fp32" if (prec == "tf32" and M > 3) else prec
+    hM = B.dg_tet_mesh_upload(ctx, M, m.EToV, m.bc, cM["xyz"], B.make_params(u_inf=cM["u_inf"], prec=mprec))
+    B.dg_set_state(ctx, hN, cN["U"])
+    Uin = B.dg_get_state(ctx, hN)
+    B.dg_prolong(ctx, hN, hM)
+    got = B.dg_get_state(ctx, hM)
+    ref = prolong_state3(Uin, N, M)
+    assert got.shape == ref.shape
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    with pytest.raises(B.DgError):
+        B.dg_prolong(ctx, hM, hN)          # to a lower degree
+    dt = 0.25 * states.time_step3(m.verts, ref, M)
+    B.dg_step(ctx, hM, dt, 1)
+    U1 = B.dg_get_state(ctx, hM)
+    B.dg_mesh_free(ctx, hN)
+    B.dg_mesh_free(ctx, hM)
+    ref1 = Oracle3(M, m.EToV, m.bc, cM["xyz"], u_inf=cM["u_inf"]).ssp_rk3_step(got, dt)
+    step_tol = {"fp64": 1e-11, "fp32": 1e-5, "tf32": 1e-4}[prec]
+    assert np.linalg.norm(U1 - ref1) / np.linalg.norm(ref1) < step_tol
+
+
+def test_prolong_refuses_triangle_to_tetrahedron(B, ctx):
+    from cases import make_case3
+    ui = states.freestream(0.38, 0.0)
+    m1 = meshes.cylinder_channel(n_t=24, n_r=4, seed=1002)
+    h1, _ = upload(B, ctx, m1, 2, "fp32", ui)
+    r, s, t = B.dg_tet_reference_nodes(3)
+    c = make_case3("box", 3, r, s, t)
+    h2 = B.dg_tet_mesh_upload(ctx, 3, c["mesh"].EToV, c["mesh"].bc, c["xyz"], B.make_params(u_inf=c["u_inf"]))
     with pytest.raises(B.DgError) as e:
         B.dg_prolong(ctx, h1, h2)
     assert e.value.status == B.DG_EINVAL
