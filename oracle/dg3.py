@@ -22,9 +22,15 @@ share a number), bc [K, 4] per face (0 interior, 1 slip wall, 2 farfield)
 and the collocation-node coordinates node_xyz [K, Np, 3] in the canonical
 node order.  States are [K, 5, Np].
 
+With artificial viscosity (av=True) the Persson-Peraire sensor and the BR1
+gradient q = sqrt(eps) grad U of the triangle oracle carry over to three
+directions (same readings).
+
 Parity: pinned by tests/test_oracle_tet.py (rules, basis, nodes, operators,
 geometry identities, free stream, conservation, convergence order on the
-extruded isentropic vortex, flux properties, planted mistakes).
+extruded isentropic vortex, flux properties, planted mistakes; the sensor's
+modal ratio, the gradient exact on linear states, the viscous terms of a
+constant viscous flux cancelling).
 
 Test infrastructure only.
 """
@@ -32,7 +38,7 @@ import numpy as np
 
 from . import euler3
 from .dg import Oracle as _Oracle2
-from .tet import FACE_VERTS, PERMS3, ReferenceTet
+from .tet import FACE_VERTS, PERMS3, ReferenceTet, mode_degrees
 
 BC_INTERIOR, BC_WALL, BC_FARFIELD = 0, 1, 2
 
@@ -99,8 +105,13 @@ class Oracle3:
     LSERK_A = _Oracle2.LSERK_A
     LSERK_B = _Oracle2.LSERK_B
 
-    def __init__(self, N, EToV, bc, node_xyz, gamma=1.4, u_inf=None, flux="llf", q=None):
+    def __init__(self, N, EToV, bc, node_xyz, gamma=1.4, u_inf=None, flux="llf", q=None,
+                 av=False, kappa=4.0, eps0=0.3, s0=None):
         self.ref = ReferenceTet(N, q)
+        self.av = bool(av)
+        self.kappa, self.eps0 = float(kappa), float(eps0)
+        self.s0 = np.log10(1.0 / N ** 4) if s0 is None else float(s0)
+        self.degrees = mode_degrees(N)
         self.N = N
         self.EToV = np.asarray(EToV, dtype=np.int64)
         self.bc = np.asarray(bc, dtype=np.int64)
@@ -126,7 +137,105 @@ class Oracle3:
         """I_g[f][o] for arrays of faces and orientation codes."""
         return self.ref.Ig[faces, orient]
 
-    def rhs(self, U, idx=None, parts=False):
+    def _face_values(self, V, idx):
+        """Face-point values of the nodal fields V [K, nv, Np] on both sides
+        of every face of the elements idx: (I_g of each own face, own [n,4,
+        nv,Ng], neighbour's at the same points [n,4,nv,Ng]; on boundary faces
+        the neighbour's are the element's own, for the caller to replace)."""
+        n = len(idx)
+        fidx = np.arange(4)[None, :].repeat(n, 0)
+        Igm = self._face_interp(fidx, self.orient[idx])          # [n,4,Ng,Np]
+        Vm = np.einsum('nfgj,nvj->nfvg', Igm, V[idx])
+        nb, fn = self.EToE[idx], self.EToF[idx]
+        bnd = self.bc[idx] != BC_INTERIOR
+        nbs, fns = np.where(bnd, idx[:, None], nb), np.where(bnd, 0, fn)
+        Igp = self._face_interp(fns, self.orient[nbs, fns])
+        Vp = np.einsum('nfgj,nfvj->nfvg', Igp, V[nbs])
+        Vp = np.where(bnd[:, :, None, None], Vm, Vp)
+        return Igm, Vm, Vp
+
+    def _ghost(self, Um, Up, idx, geo):
+        """Exterior states on boundary faces: slip-wall reflection, farfield."""
+        nx, ny, nz = geo.nrm[..., 0], geo.nrm[..., 1], geo.nrm[..., 2]
+        Up = Up.copy()
+        wall = self.bc[idx] == BC_WALL
+        if np.any(wall):
+            Up[wall] = euler3.wall_ghost(Um[wall], nx[wall], ny[wall], nz[wall])
+        far = self.bc[idx] == BC_FARFIELD
+        if np.any(far):
+            Up[far] = self.u_inf[None, :, None]
+        return Up
+
+    def _sqrt_eps_faces(self, eps, idx):
+        """sqrt(eps) of the element (own) and of the face's other side,
+        which is the element itself on boundary faces."""
+        se = np.sqrt(eps[idx])
+        sep = np.where(self.bc[idx] == BC_INTERIOR, np.sqrt(eps[np.maximum(self.EToE[idx], 0)]), se[:, None])
+        return se, sep
+
+    def neighbours(self, idx):
+        idx = np.asarray(idx)
+        nb = self.EToE[idx].ravel()
+        return np.unique(np.concatenate([idx, nb[nb >= 0]]))
+
+    # ------------------------------------------------------------ sensor
+    def sensor(self, U, idx=None):
+        """Persson-Peraire viscosity eps_k (Sec. 2): S_k = the L2 norm of the
+        density's highest-degree modes over that of the density, both by the
+        cubature rule with J; s_k = log10 S_k; the sine ramp of width kappa
+        around s0 up to eps0."""
+        idx = np.arange(self.K) if idx is None else np.asarray(idx)
+        ref = self.ref
+        geo = self.geometry(idx)
+        rho = U[idx, 0, :]
+        modal = rho @ ref.Vinv.T
+        low = np.where(self.degrees[None, :] <= self.N - 1, modal, 0.0)
+        rho_low = low @ ref.V.T
+        WJ = geo.J * ref.wq[None, :]
+        num = np.sum(WJ * ((rho - rho_low) @ ref.Icub.T) ** 2, axis=1)
+        den = np.sum(WJ * (rho @ ref.Icub.T) ** 2, axis=1)
+        eps = np.zeros(len(idx))
+        ok = (num > 0.0) & (den > 0.0)
+        s = np.full(len(idx), -np.inf)
+        s[ok] = np.log10(num[ok] / den[ok])
+        lo, hi = self.s0 - self.kappa, self.s0 + self.kappa
+        mid = ok & (s >= lo) & (s <= hi)
+        eps[mid] = 0.5 * self.eps0 * (1.0 + np.sin(np.pi * (s[mid] - self.s0) / (2.0 * self.kappa)))
+        eps[ok & (s > hi)] = self.eps0
+        return eps
+
+    # ------------------------------------------------------------ AV q
+    def gradient_q(self, U, eps, idx):
+        """q_m = sqrt(eps) dU/dx_m by the DG weak form with central face
+        values (BR1) for elements idx: M q_m = -sum_a D_a^T [W J (dr_a/dx_m)
+        sqrt(eps) U^cub] + sum_f I_g^T [w_g sJ n_m (sqrt(eps) U)*], with
+        (sqrt(eps) U)* the mean of the two sides' and, on boundary faces,
+        the ghost state with the element's own eps.  eps over all elements
+        (idx and their neighbours are read).  Returns q [n, 3, 5, Np]."""
+        ref = self.ref
+        idx = np.asarray(idx)
+        geo = self.geometry(idx)
+        U = np.asarray(U, dtype=np.float64)
+        se, sep = self._sqrt_eps_faces(eps, idx)
+        Uc = (U[idx] @ ref.Icub.T) * se[:, None, None]
+        WJ = (ref.wq[None, :] * geo.J)[:, None, :]
+        Igm, Um, Up = self._face_values(U, idx)
+        Up = self._ghost(Um, Up, idx, geo)
+        ustar = 0.5 * (se[:, None, None, None] * Um + sep[:, :, None, None] * Up)
+        wsJ = ref.wg[None, None, :] * geo.sJ
+        q = np.zeros((len(idx), 3, 5, ref.Np))
+        for m in range(3):
+            vol = sum((WJ * geo.inv[:, None, :, a, m] * Uc) @ D for a, D in enumerate((ref.Dr, ref.Ds, ref.Dt)))
+            surf = np.einsum('nfgj,nfvg->nvj', Igm, (wsJ * geo.nrm[..., m])[:, :, None, :] * ustar)
+            q[:, m] = (-vol + surf) @ geo.Minv.transpose(0, 2, 1)
+        return q
+
+    def rhs(self, U, idx=None, parts=False, eps=None, q=None):
+        """L(U) on elements idx (all by default).  With artificial viscosity
+        the physical fluxes lose sqrt(eps) q at the cubature points and the
+        numerical flux the mean of the two sides' sqrt(eps) q.n; eps and q
+        are computed on the neighbourhood idx needs unless given over all
+        elements."""
         ref = self.ref
         idx = np.arange(self.K) if idx is None else np.asarray(idx)
         geo = self.geometry(None if len(idx) == self.K and np.all(idx == np.arange(self.K)) else idx)
@@ -135,6 +244,20 @@ class Oracle3:
         Ui = U[idx]
         Uc = Ui @ ref.Icub.T                                     # [n,5,Nq]
         F, G, H = euler3.flux(Uc, g)
+        if self.av:
+            if eps is None or q is None:
+                ring1 = self.neighbours(idx)
+                ring2 = self.neighbours(ring1)
+                eps_full = np.zeros(self.K)
+                eps_full[ring2] = self.sensor(U, ring2)
+                q_full = np.zeros((self.K, 3, 5, ref.Np))
+                q_full[ring1] = self.gradient_q(U, eps_full, ring1)
+                eps, q = eps_full, q_full
+            se = np.sqrt(eps[idx])
+            qc = q[idx] @ ref.Icub.T                             # [n,3,5,Nq]
+            F = F - se[:, None, None] * qc[:, 0]
+            G = G - se[:, None, None] * qc[:, 1]
+            H = H - se[:, None, None] * qc[:, 2]
         WJ = (ref.wq[None, :] * geo.J)[:, None, :]
         vol = np.zeros_like(Ui)
         for a, D in enumerate((ref.Dr, ref.Ds, ref.Dt)):
@@ -142,23 +265,19 @@ class Oracle3:
                            + geo.inv[:, None, :, a, 2] * H)
             vol += contra @ D                                    # D^T [W J (grad r_a . Fvec)]
 
-        n = len(idx)
-        fidx = np.arange(4)[None, :].repeat(n, 0)
-        Igm = self._face_interp(fidx, self.orient[idx])          # [n,4,Ng,Np]
-        Um = np.einsum('nfgj,nvj->nfvg', Igm, Ui)                # [n,4,5,Ng]
-        nb, fn = self.EToE[idx], self.EToF[idx]
-        bnd = self.bc[idx] != BC_INTERIOR
-        nbs, fns = np.where(bnd, idx[:, None], nb), np.where(bnd, 0, fn)
-        Igp = self._face_interp(fns, self.orient[nbs, fns])
-        Up = np.einsum('nfgj,nfvj->nfvg', Igp, U[nbs])
+        Igm, Um, Up = self._face_values(U, idx)                  # [n,4,5,Ng]
+        Up = self._ghost(Um, Up, idx, geo)
         nx, ny, nz = geo.nrm[..., 0], geo.nrm[..., 1], geo.nrm[..., 2]
-        wall = self.bc[idx] == BC_WALL
-        if np.any(wall):
-            Up[wall] = euler3.wall_ghost(Um[wall], nx[wall], ny[wall], nz[wall])
-        far = self.bc[idx] == BC_FARFIELD
-        if np.any(far):
-            Up[far] = self.u_inf[None, :, None]
         Fs = self.numflux(Um, Up, nx, ny, nz, g)                 # [n,4,5,Ng]
+        if self.av:
+            n = len(idx)
+            _, qm, qp = self._face_values(q.reshape(self.K, 15, ref.Np), idx)   # q+ = q- on boundary faces
+            qm = qm.reshape(n, 4, 3, 5, ref.Ng)
+            qp = qp.reshape(n, 4, 3, 5, ref.Ng)
+            se, sep = self._sqrt_eps_faces(eps, idx)
+            qn_m = sum(qm[:, :, m] * geo.nrm[..., m][:, :, None, :] for m in range(3))
+            qn_p = sum(qp[:, :, m] * geo.nrm[..., m][:, :, None, :] for m in range(3))
+            Fs = Fs - 0.5 * (se[:, None, None, None] * qn_m + sep[:, :, None, None] * qn_p)
         wsJ = ref.wg[None, None, :] * geo.sJ                      # [n,4,Ng]
         surf = np.einsum('nfgj,nfvg->nvj', Igm, wsJ[:, :, None, :] * Fs)
         L = (vol - surf) @ geo.Minv.transpose(0, 2, 1)
