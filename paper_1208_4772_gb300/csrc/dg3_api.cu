@@ -110,6 +110,10 @@ StageArgs3<Real> make_args3(const MeshData& m, const void* Us, const void* Un, v
     for (int v = 0; v < 5; ++v) s.uinf[v] = (Real)m.p.u_inf[v];
     s.tile_e = m.tile_e;
     s.err = m.err;
+    s.eps = (const Real*)m.eps;
+    s.q = (const Real*)m.q;
+    s.qout = (Real*)m.q;
+    s.grad_m = 0;
     return s;
 }
 
@@ -123,8 +127,28 @@ struct FaceKey {
 
 namespace dgc {
 
+// With artificial viscosity a stage is: the sensor of U_s into eps, the
+// gradient pass q = sqrt(eps) grad U_s (one launch per direction), the
+// stage with the viscous terms.
+template <typename Real>
+int enqueue_av_stage3(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
+                      int rhs_only, cudaStream_t st, void* dU) {
+    int e = launch_sensor3(m.N, (const Real*)Us, (Real*)m.eps, (const Real*)m.ops, (const Real*)m.ops_av3,
+                           (const Real*)m.geoC, m.K, m.Kaff, m.p.kappa, m.p.eps0, m.s0, st);
+    StageArgs3<Real> s = make_args3<Real>(m, Us, Un, out, a, b, dt, rhs_only, dU);
+    for (int d = 0; d < 3 && !e; ++d) {
+        s.grad_m = d;
+        e = launch_stage3(m.N, s, st, 2);
+    }
+    if (!e) e = launch_stage3(m.N, s, st, 1);
+    return e;
+}
+
 int enqueue_stage3(const MeshData& m, const void* Us, const void* Un, void* out, double a, double b, double dt,
                    int rhs_only, cudaStream_t st, void* dU) {
+    if (m.p.av_on)
+        return m.rsize == 8 ? enqueue_av_stage3<double>(m, Us, Un, out, a, b, dt, rhs_only, st, dU)
+                            : enqueue_av_stage3<float>(m, Us, Un, out, a, b, dt, rhs_only, st, dU);
     if (m.rsize == 8) return launch_stage3(m.N, make_args3<double>(m, Us, Un, out, a, b, dt, rhs_only, dU), st);
     if (m.prec == DG_TF32)
         return launch_stage3_tc(m.N, make_args3<float>(m, Us, Un, out, a, b, dt, rhs_only, dU), st);
@@ -171,7 +195,10 @@ int dg_tet_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const
         return api_fail(ctx, DG_EINVAL, "the tetrahedral path computes in DG_FP32, DG_TF32 or DG_FP64_DEBUG");
     if (p->prec == DG_TF32 && !supported_degree3_tc(N))
         return api_fail(ctx, DG_EINVAL, "DG_TF32 on tetrahedra supports N = 2 and 3");
-    if (p->av_on) return api_fail(ctx, DG_EINVAL, "artificial viscosity is built for the triangle path");
+    if (p->av_on && p->prec == DG_TF32)
+        return api_fail(ctx, DG_EINVAL, "artificial viscosity on tetrahedra runs in DG_FP32 or DG_FP64_DEBUG");
+    if (p->av_on && !(p->kappa > 0.0 && p->eps0 >= 0.0))
+        return api_fail(ctx, DG_EINVAL, "artificial viscosity needs kappa > 0 and eps0 >= 0");
     if (p->flux != 0 && p->flux != 1)
         return api_fail(ctx, DG_EINVAL, "flux must be 0 (local Lax-Friedrichs) or 1 (HLLC)");
     if (!(p->gamma > 1.0)) return api_fail(ctx, DG_EINVAL, "gamma must exceed 1");
@@ -371,6 +398,11 @@ int dg_tet_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const
     for (int b = 0; b < 3; ++b)
         if ((e = api_alloc(ctx, *m, &m->U[b], nstate * rs))) { api_free_mesh(m); return e; }
     if ((e = api_alloc(ctx, *m, &m->rhs, nstate * rs))) { api_free_mesh(m); return e; }
+    if (p->av_on) {   // eps [K] and q [K][3][5][NP]
+        if ((e = api_alloc(ctx, *m, &m->eps, (size_t)K * rs))) { api_free_mesh(m); return e; }
+        if ((e = api_alloc(ctx, *m, &m->q, 3 * nstate * rs))) { api_free_mesh(m); return e; }
+        m->s0 = std::isnan(p->s0) ? std::log10(1.0 / std::pow((double)N, 4)) : p->s0;
+    }
     if ((e = api_alloc(ctx, *m, (void**)&m->conn, (size_t)K * sizeof(int4)))) { api_free_mesh(m); return e; }
     if ((e = api_alloc(ctx, *m, (void**)&m->code3, (size_t)K * sizeof(int2)))) { api_free_mesh(m); return e; }
     if ((e = api_alloc(ctx, *m, &m->geoA, geoA.size() * rs))) { api_free_mesh(m); return e; }
@@ -428,6 +460,27 @@ int dg_tet_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const
                                                cudaGetErrorString((cudaError_t)pe));
         }
     }
+    // the sensor's table: F_h = I - V diag(deg <= N-1) V^-1, cubature weights
+    const int akey = 300000 + N * 16 + (rs == 8 ? 1 : 0);
+    if (p->av_on && ctx->ops.find(akey) == ctx->ops.end()) {
+        const int nlow = n_modes3(N - 1);
+        std::vector<double> av((size_t)av3_size(N), 0.0);
+        for (int i = 0; i < NP; ++i)
+            for (int j = 0; j < NP; ++j) {
+                double lowp = 0.0;
+                for (int k = 0; k < nlow; ++k) lowp += R->V[(size_t)i * NP + k] * R->Vinv[(size_t)k * NP + j];
+                av[(size_t)i * NP + j] = (i == j ? 1.0 : 0.0) - lowp;
+            }
+        for (int q = 0; q < NQ; ++q) av[(size_t)NP * NP + q] = R->wq[q];
+        void* d = nullptr;
+        const int ce = rs == 8 ? copy_table<double>(av, &d) : copy_table<float>(av, &d);
+        if (ce) {
+            api_free_mesh(m);
+            return api_fail(ctx, ce, "sensor table upload failed");
+        }
+        ctx->ops[akey] = d;
+    }
+    if (p->av_on) m->ops_av3 = ctx->ops[akey];
     m->ops = ctx->ops[okey];
     m->opsi3 = (const int*)ctx->ops[ikey];
 

@@ -39,6 +39,10 @@ __host__ __device__ constexpr Ops3Layout ops3_layout(int N) {
     o.total = pad4(o.mi + NP * NP);
     return o;
 }
+// Sensor table: the high-degree filter F_h = I - V diag(deg <= N-1) V^-1
+// [NP][NP] (row-major), then the cubature weights [NQP].
+__host__ __device__ constexpr int av3_size(int N) { return np3_of(N) * np3_of(N) + pad4(nq3_of(N)); }
+
 // Integer table: fmask [4][NFP] (element node of each face node),
 // fpos [4][NP] (face-local index of each element node, -1 off the face).
 __host__ __device__ constexpr int opsi3_size(int N) { return 4 * nfp3_of(N) + 4 * np3_of(N); }
@@ -79,14 +83,30 @@ struct StageArgs3 {
     Real uinf[5];
     int tile_e;         // elements per tile (0: the default of the degree and real type)
     int* err;           // device error word (tensor-core kernel: a bounded wait ran out)
+    // artificial viscosity (CUDA-core kernels): eps [K]; q [K][3][5][NP]
+    // (rows m * 5 + v: sqrt(eps) dU_v/dx_m), read by the viscous stage and
+    // written, one direction grad_m per launch, by the gradient pass
+    const Real* eps;
+    const Real* q;
+    Real* qout;
+    int grad_m;
 };
 
 bool supported_degree3(int N);
 int prepare_stage3(int N, int rsize);
 int tile3_default(int N, int rsize);
 bool tile3_fits(int N, int rsize, int E);
-int launch_stage3(int N, const StageArgs3<float>& a, cudaStream_t st);
-int launch_stage3(int N, const StageArgs3<double>& a, cudaStream_t st);
+// mode 0: the Euler stage; 1: the stage with the viscous terms (eps, q);
+// 2: the gradient pass for direction grad_m (q out, no stage update).
+int launch_stage3(int N, const StageArgs3<float>& a, cudaStream_t st, int mode = 0);
+int launch_stage3(int N, const StageArgs3<double>& a, cudaStream_t st, int mode = 0);
+// The element sensor (paper Sec. 2): eps [K] of the state U [K][5][NP];
+// ops_av = av3_layout(N).
+int launch_sensor3(int N, const float* U, float* eps, const float* ops, const float* ops_av, const float* geoC,
+                   long long K, long long Kaff, double kappa, double eps0, double s0, cudaStream_t st);
+int launch_sensor3(int N, const double* U, double* eps, const double* ops, const double* ops_av,
+                   const double* geoC, long long K, long long Kaff, double kappa, double eps0, double s0,
+                   cudaStream_t st);
 
 // Tensor-core variant (TF32 products for the two volume terms, FP32 state;
 // degrees 2 and 3, fixed tiles of tile3_tc(N) elements).

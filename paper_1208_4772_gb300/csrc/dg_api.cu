@@ -1181,8 +1181,32 @@ int dg_av_count(dg_ctx* ctx, dg_mesh h, int64_t* out) {
     if (!ctx || !out) return fail(ctx, DG_EINVAL, "NULL argument");
     MeshData* m = find(ctx, h);
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
-    if (m->dim != 2 || !m->p.av_on) return fail(ctx, DG_EINVAL, "the mesh has no artificial viscosity");
+    if (!m->p.av_on) return fail(ctx, DG_EINVAL, "the mesh has no artificial viscosity");
     cudaSetDevice(ctx->device);
+    if (m->dim == 3) {   // the sensor of U^n into the scratch, counted on the host
+        const int e = m->rsize == 8
+            ? launch_sensor3(m->N, (const double*)m->U[0], (double*)m->rhs, (const double*)m->ops,
+                             (const double*)m->ops_av3, (const double*)m->geoC, m->K, m->Kaff, m->p.kappa,
+                             m->p.eps0, m->s0, ctx->stream)
+            : launch_sensor3(m->N, (const float*)m->U[0], (float*)m->rhs, (const float*)m->ops,
+                             (const float*)m->ops_av3, (const float*)m->geoC, m->K, m->Kaff, m->p.kappa,
+                             m->p.eps0, m->s0, ctx->stream);
+        if (e) return fail(ctx, DG_ECUDA, std::string("sensor launch failed: ") + cudaGetErrorString((cudaError_t)e));
+        std::vector<double> ev((size_t)m->K);
+        if (m->rsize == 8) {
+            CUDA_OK(ctx, cudaMemcpyAsync(ev.data(), m->rhs, (size_t)m->K * 8, cudaMemcpyDeviceToHost, ctx->stream));
+            CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
+        } else {
+            std::vector<float> ef((size_t)m->K);
+            CUDA_OK(ctx, cudaMemcpyAsync(ef.data(), m->rhs, (size_t)m->K * 4, cudaMemcpyDeviceToHost, ctx->stream));
+            CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
+            ev.assign(ef.begin(), ef.end());
+        }
+        int64_t c = 0;
+        for (double x : ev) c += x > 0.0;
+        *out = c;
+        return DG_OK;
+    }
     // the sensor of U^n into the right-hand-side scratch, counting its
     // elements with eps > 0 in a scratch word of the error block
     int* cnt = m->err + VISC_SLOT + EPS_RING;

@@ -33,7 +33,8 @@ struct MeshData {
     // starts and ends with eps_ring[0] = eps(U^n)
     void* eps_ring[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool eps_valid = false;       // eps_ring[0] holds eps(U^n)
-    void* q = nullptr;            // [K][2][4][Np] (AV)
+    void* q = nullptr;            // [K][2][4][Np] (AV; tetrahedra [K][3][5][Np])
+    const void* ops_av3 = nullptr;   // tetrahedral sensor table (AV)
     void* geoA = nullptr;         // [Kaff][4]
     void* geoC = nullptr;         // [Kc][curved_stride]
     void* ops = nullptr;          // shared operator table (owned by the context)

@@ -138,10 +138,20 @@ __device__ __forceinline__ void affine_cofactors3(const Real* J, Real* g) {
 // enthalpy, BST reals per element) the normal flux of that state is
 // subtracted first.  Items start at thread `first`, so that a phase with
 // fewer items than threads before it can hand this one its idle threads.
-template <int N, typename Real, int GST, int BST>
+//
+// MODE 1 (artificial viscosity) also takes the q face-node rows of both
+// sides (sQf, sQnb: [e][4][15][NFPP]) and sqrt(eps) of the element and of
+// each face's other side (sSe [e][5]), and subtracts the mean of the two
+// sides' sqrt(eps) q.n (q+ = q- and eps+ = eps- on boundary faces).
+// MODE 2 (the BR1 gradient, direction gm) replaces the numerical flux by the
+// central value n_gm (sqrt(eps) U)*, the exterior state being the ghost on
+// boundary faces.
+template <int N, typename Real, int GST, int BST, int MODE = 0>
 __device__ __forceinline__ void face_points3(const StageArgs3<Real>& p, long long e0, int ne, int first,
                                              const Real* sI2, const Real* sW, const Real* sUf, const Real* sNb,
-                                             const int* sCode, const Real* sG, const Real* Bar, Real* sFs) {
+                                             const int* sCode, const Real* sG, const Real* Bar, Real* sFs,
+                                             const Real* sSe = nullptr, const Real* sQf = nullptr,
+                                             const Real* sQnb = nullptr, int gm = 0) {
     constexpr int NQ = nq3_of(N), NG = ng3_of(N), NFPP = pad4(nfp3_of(N)), NGP = pad4(NG);
     constexpr int CS = curved3_stride(N);
     for (int i = first; i < ne * 4 * NG; i += THREADS) {
@@ -193,10 +203,47 @@ __device__ __forceinline__ void face_points3(const StageArgs3<Real>& p, long lon
             for (int v = 0; v < 5; ++v) up[v] = p.uinf[v];
         }
         Real F[5];
-        if (p.flux == 1)
-            hllc3(um, up, nx, ny, nz, p.gamma, F);
-        else
-            llf3(um, up, nx, ny, nz, p.gamma, F);
+        if constexpr (MODE == 2) {
+            const Real se = sSe[e * 5], sp = bc == 0 ? sSe[e * 5 + 1 + f] : se;
+            const Real nm = gm == 0 ? nx : gm == 1 ? ny : nz;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) F[v] = nm * Real(0.5) * (se * um[v] + sp * up[v]);
+        } else {
+            if (p.flux == 1)
+                hllc3(um, up, nx, ny, nz, p.gamma, F);
+            else
+                llf3(um, up, nx, ny, nz, p.gamma, F);
+        }
+        if constexpr (MODE == 1) {   // minus the mean of the two sides' sqrt(eps) q.n
+            const Real se = sSe[e * 5], sp = bc == 0 ? sSe[e * 5 + 1 + f] : se;
+            const Real* qf = sQf + (e * 4 + f) * 15 * NFPP;
+            const Real* qn = sQnb + (e * 4 + f) * 15 * NFPP;
+            const Real* I2p = sI2 + (code3_nbr(code) * NG + g) * NFPP;
+            Real qm[15], qp[15];
+#pragma unroll
+            for (int r = 0; r < 15; ++r) qm[r] = qp[r] = Real(0);
+#pragma unroll
+            for (int ib = 0; ib < NFPP / 4; ++ib) {
+                const V4<Real> w = lds4(I2o + 4 * ib);
+#pragma unroll
+                for (int r = 0; r < 15; ++r) qm[r] += dot4(w, lds4(qf + r * NFPP + 4 * ib));
+            }
+            if (bc == 0) {
+#pragma unroll
+                for (int ib = 0; ib < NFPP / 4; ++ib) {
+                    const V4<Real> w = lds4(I2p + 4 * ib);
+#pragma unroll
+                    for (int r = 0; r < 15; ++r) qp[r] += dot4(w, lds4(qn + r * NFPP + 4 * ib));
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < 15; ++r) qp[r] = qm[r];
+            }
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+                F[v] -= Real(0.5) * (se * (nx * qm[v] + ny * qm[5 + v] + nz * qm[10 + v]) +
+                                     sp * (nx * qp[v] + ny * qp[5 + v] + nz * qp[10 + v]));
+        }
         if (Bar) {   // minus the normal flux of the element's mean state
             const Real* b = Bar + e * BST;
             const Real un = nx * b[5] + ny * b[6] + nz * b[7];

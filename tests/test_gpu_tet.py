@@ -165,7 +165,7 @@ def test_tet_argument_errors(B, ctx):
     r, s, t = B.dg_tet_reference_nodes(2)
     case = make_case3("bump", 2, r, s, t, size="tiny")
     m = case["mesh"]
-    for kw in ({"prec": "bf16x3"}, {"prec": "fp32", "av_on": True}):
+    for kw in ({"prec": "bf16x3"}, {"prec": "tf32", "av_on": True}):
         p = B.make_params(u_inf=case["u_inf"], **kw)
         with pytest.raises(B.DgError) as e:
             B.dg_tet_mesh_upload(ctx, 2, m.EToV, m.bc, case["xyz"], p)
