@@ -84,6 +84,8 @@ def parse_args():
     ap.add_argument("--integrator", default="ssp3", choices=["ssp3", "lserk"],
                     help="SSP-RK3 (3 stages) or the paper's low-storage RK(5,4) (5 stages)")
     ap.add_argument("--flux", default="llf", choices=["llf", "hllc"], help="numerical flux at the faces")
+    ap.add_argument("--tet-av", action="store_true",
+                    help="tetrahedra: artificial viscosity on (sensor, gradient pass, viscous stage; FP32/FP64)")
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -595,6 +597,8 @@ def run_tet(args):
     w = WORKLOADS[args.workload]
     N = w["N"]
     prec = args.prec if args.prec in ("fp32", "fp64", "tf32") else "fp32"
+    if args.tet_av and prec == "tf32":
+        prec = "fp32"    # the viscous path runs on the CUDA cores
     r, s_, t = B.dg_tet_reference_nodes(N)
     wl = make_tet_workload(args.workload, r, s_, t)
     m = wl["mesh"]
@@ -604,7 +608,7 @@ def run_tet(args):
     torch.cuda.set_stream(stream)
     ctx = B.dg_create(0, stream.cuda_stream)
     flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device="cuda")
-    p = B.make_params(u_inf=wl["u_inf"], prec=prec, flux=args.flux)
+    p = B.make_params(u_inf=wl["u_inf"], prec=prec, flux=args.flux, av_on=args.tet_av)
     h = B.dg_tet_mesh_upload(ctx, N, m.EToV, m.bc, wl["xyz"], p)
     info = B.dg_mesh_info(ctx, h)
     B.dg_set_state(ctx, h, wl["U0"])
@@ -646,7 +650,8 @@ def run_tet(args):
     achieved = flops / (launch_ms * 1e-3) / 1e12
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm = float(json.load(open(peaks_path))["hbm_gbs"]) if os.path.exists(peaks_path) else 6800.0
-    kname = "stage3_tc_kernel" if prec == "tf32" else "stage3_kernel"
+    kname = "stage3_tc_kernel" if prec == "tf32" else \
+        ("sensor3_kernel + 3 gradient passes + viscous stage3_kernel" if args.tet_av else "stage3_kernel")
     roofline = {"kernel": "%s (tetrahedra, N=%d, %s)" % (kname, N, prec), "bound": "alu",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock %.0f MHz" % sm_max,
@@ -655,6 +660,9 @@ def run_tet(args):
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": launch_ms,
                 "hbm_gbs": bytes_launch / (launch_ms * 1e-3) / 1e9,
                 "hbm_frac": bytes_launch / (launch_ms * 1e-3) / 1e9 / hbm}
+    if args.tet_av:
+        roofline["note"] = ("with artificial viscosity the timed unit is the whole viscous stage (five launches); "
+                            "flops and bytes are those of the inviscid stage, so the fractions understate the work")
     e2e = None
     if not args.no_e2e:
         step(ctx, h, wl["dt"], 1)
@@ -679,6 +687,7 @@ def run_tet(args):
                        "variables": 5, "curved_elements": int(info["curved"]), "state_precision": prec,
                        "time_integrator": "LSERK(5,4)" if args.integrator == "lserk" else "SSP-RK3",
                        "flux": args.flux.upper(), "dt": wl["dt"], "dof_per_stage": int(dof_stage),
+                       "artificial_viscosity": bool(args.tet_av),
                        "l2": "flushed before every timed step (%d MiB memset, outside the step events)"
                              % args.flush_mb,
                        "parallelism": "replicas (one independent solve per GPU)"},

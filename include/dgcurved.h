@@ -49,8 +49,11 @@
  *     DG_FP32, DG_FP64_DEBUG and, for N = 2 and 3, DG_TF32 (the
  *     interpolation to the cubature points and the three weighted
  *     derivative products on the tensor cores, on deviations from each
- *     element's mean state and its flux; the face terms in FP32); no
- *     artificial viscosity.
+ *     element's mean state and its flux; the face terms in FP32).
+ *   - Artificial viscosity (av_on, DG_FP32 or DG_FP64_DEBUG): per stage the
+ *     element sensor, the gradient pass q = sqrt(eps) grad U (BR1, one
+ *     launch per direction) and the stage with the viscous terms, all on
+ *     the CUDA cores; dg_av_count counts eps > 0.
  */
 #ifndef DGCURVED_H
 #define DGCURVED_H
@@ -167,7 +170,7 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
  *                are treated as curved (per-point geometric factors and their
  *                own mass matrix)
  *   p            parameters (copied); prec DG_FP32, DG_FP64_DEBUG, or DG_TF32
- *                with N <= 3; av_on 0
+ *                with N <= 3 and av_on 0
  * The state is set to 0.  Errors: DG_EINVAL (N, K, prec or av_on out of
  * range, a face shared by more than two elements, bc inconsistent with the
  * face matching, J <= 0 at a cubature point), DG_ENOMEM, DG_ECUDA. */
