@@ -26,7 +26,9 @@ cases       closed-form isentropic vortex used by the convergence pins
 
 Parity status of each function is stated in its docstring; every function
 listed above is pinned by ``tests/test_oracle_*.py`` against closed forms,
-library routines, invariants or brute force, except the artificial-viscosity
-right-hand side beyond free-stream and conservation (see ``dg.av_rhs``):
-parity unpinned by printed values (the paper prints none).
+library routines, invariants or brute force.  The paper prints no values
+for the artificial-viscosity right-hand side; it is pinned by closed forms
+(the sensor's modal ratio, the gradient exact on linear states, a constant
+viscous flux cancelling) in ``tests/test_oracle_av_pins.py`` and
+``tests/test_oracle_tet_av.py``.
 """

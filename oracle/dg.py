@@ -42,9 +42,11 @@ norm and Euclidean norm over all nodal values.
 Parity: the Euler right-hand side, mass, sensor, SSP-RK3 and residual are
 pinned by tests/test_oracle_*.py (free stream, conservation, LLF symmetries,
 vortex convergence order, sensor closed forms, stability polynomial).  The
-artificial-viscosity right-hand side is pinned only by free-stream
-preservation and conservation: beyond those, parity unpinned (the paper
-prints no values for it).
+artificial-viscosity right-hand side (the paper prints no values for it) is
+pinned by free stream, conservation and the closed forms of
+tests/test_oracle_av_pins.py: the gradient exact on linear states, a
+constant viscous flux cancelling, eps = 0 giving the inviscid right-hand
+side.
 
 Test infrastructure only.
 """
