@@ -4,7 +4,7 @@ configuration the bench times, on sampled outputs.
 The meshes are the bench workloads' own (same generators and seeds): the
 NACA 0012 O-mesh with 60,000 elements at N = 4 with artificial viscosity,
 the 250,000-element cylinder channel at N = 6, and the 300,000-tetrahedron
-bump channel at N = 3.  The state is the
+bump channel at N = 3 (without and with artificial viscosity).  The state is the
 freestream with a smooth perturbation and a little noise, so every term is
 exercised.  The library evaluates the right-hand side of the whole mesh; the
 FP64 oracle evaluates it on 192 random elements and 64 curved wall
@@ -106,3 +106,35 @@ def test_fullsize_tet_rhs_sampled(B, ctx, flux, prec, tol):
     err = np.linalg.norm((L[idx] - Lo).transpose(1, 0, 2).reshape(5, -1), axis=1) / scale
     assert np.all(np.isfinite(L)), "non-finite right-hand side"
     assert np.all(err <= tol), (flux, prec, err)
+
+
+def test_fullsize_tet_av_rhs_sampled(B, ctx):
+    """The 300,000-tetrahedron bench mesh with artificial viscosity (FP32,
+    CUDA cores): the bench state with a jump of all variables by half across
+    the plane x = 1.37, so that the elements the plane cuts have eps > 0;
+    sampled among those elements and at random.  Tolerance that of the small
+    meshes with viscosity (1e-4: the sensor's FP32 sums)."""
+    from paper_1208_4772_gb300.inputs import meshes3d
+    N = 3
+    r, s, t = B.dg_tet_reference_nodes(N)
+    case = make_case3("bump", N, r, s, t, size="config")
+    m = case["mesh"]
+    X = case["xyz"]
+    U = (case["U"] * np.where(X[..., 0] > 1.37, 1.5, 1.0)[:, None, :]).astype(np.float32).astype(np.float64)
+    p = B.make_params(u_inf=case["u_inf"], prec="fp32", av_on=True)
+    h = B.dg_tet_mesh_upload(ctx, N, m.EToV, m.bc, X, p)
+    B.dg_set_state(ctx, h, U)
+    nvisc = B.dg_av_count(ctx, h)
+    L = B.dg_eval_rhs(ctx, h)
+    B.dg_mesh_free(ctx, h)
+    assert nvisc > 100
+    rng = np.random.default_rng(13)
+    cut = np.nonzero(np.any(X[..., 0] > 1.37, axis=1) & np.any(X[..., 0] <= 1.37, axis=1))[0]
+    idx = np.unique(np.concatenate([rng.choice(m.K, 128, replace=False), rng.choice(cut, 128, replace=False)]))
+    o = Oracle3(N, m.EToV, m.bc, X, u_inf=case["u_inf"], av=True)
+    Lo, vol, _ = o.rhs(U, idx, parts=True)
+    V = np.einsum('kij,kvj->kvi', o.geometry(idx).Minv, vol)
+    scale = np.linalg.norm(V.transpose(1, 0, 2).reshape(5, -1), axis=1)
+    err = np.linalg.norm((L[idx] - Lo).transpose(1, 0, 2).reshape(5, -1), axis=1) / scale
+    assert np.all(np.isfinite(L)), "non-finite right-hand side"
+    assert np.all(err <= 1e-4), err
