@@ -261,3 +261,44 @@ def test_av_count_matches_oracle_sensor(B, ctx):
         eps = Oracle(N, m.EToE, m.EToF, m.bc, case["xy"], u_inf=case["u_inf"], av=True).sensor(U)
         assert n == int(np.sum(eps > 0)), (perturb, n, int(np.sum(eps > 0)))
         assert (n == 0) == (perturb == 0.0)
+
+
+def _vortex_error_gpu(B, ctx, N, n, prec, T=0.2, length=10.0):
+    from oracle import basis
+    from oracle.operators import ReferenceElement
+    ref = ReferenceElement(N)
+    r, s = B.dg_reference_nodes(N)
+    # interpolation to the cubature points from the library's own nodes
+    Icub = ref.Vq @ np.linalg.inv(basis.vandermonde(N, r, s))
+    m = meshes.periodic_square(n, length=length, seed=7)
+    xy = meshes.straight_nodes(m.verts, r, s)
+    U = states.vortex_state(xy, period=(length, length))
+    dt0 = states.time_step(m.verts, U, N, cfl=0.3)
+    nst = int(np.ceil(T / dt0))
+    h = B.dg_mesh_upload(ctx, N, m.EToE, m.EToF, m.bc, xy, B.make_params(u_inf=states.freestream(0.5, 45.0), prec=prec))
+    B.dg_set_state(ctx, h, U)
+    B.dg_step(ctx, h, T / nst, nst)
+    Ug = B.dg_get_state(ctx, h, m.K, len(r))
+    B.dg_mesh_free(ctx, h)
+    Ue = states.vortex_state(xy, t=T, period=(length, length))
+    e = (Ug - Ue)[:, 0, :] @ Icub.T
+    # affine elements: J is the constant area ratio
+    v = m.verts
+    J = 0.25 * np.abs((v[:, 1, 0] - v[:, 0, 0]) * (v[:, 2, 1] - v[:, 0, 1])
+                      - (v[:, 2, 0] - v[:, 0, 0]) * (v[:, 1, 1] - v[:, 0, 1]))
+    return np.sqrt(np.sum(J[:, None] * ref.wq[None, :] * e * e))
+
+
+@pytest.mark.parametrize("N,n1", [(2, 16), (3, 8)])
+def test_mixed_precision_keeps_convergence_order(B, ctx, N, n1):
+    """The isentropic vortex at T = 0.2 on n and 2n periodic meshes (the
+    oracle's convergence pin, run through the library): the density L2
+    error falls at order >= N + 1/2 with TF32 and BF16 x3 products as with
+    FP32, and the mixed-precision errors stay within 10% of the FP32 ones."""
+    errs = {}
+    for prec in ("fp32", "tf32", "bf16x3"):
+        e1, e2 = _vortex_error_gpu(B, ctx, N, n1, prec), _vortex_error_gpu(B, ctx, N, 2 * n1, prec)
+        errs[prec] = (e1, e2)
+        assert np.log2(e1 / e2) >= N + 0.5, (prec, e1, e2)
+    for prec in ("tf32", "bf16x3"):
+        assert errs[prec][1] <= 1.1 * errs["fp32"][1], errs
