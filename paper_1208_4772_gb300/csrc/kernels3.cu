@@ -136,7 +136,27 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
             if (e0 + e >= p.Kaff) continue;
             affine_cofactors3(p.geoA + (e0 + e) * 9, sG + e * 16);
         }
-        __syncthreads();
+        // with artificial viscosity: does eps vanish on the tile's elements
+        // and on all their face neighbours?  Then q = 0 on the tile and its
+        // viscous terms vanish exactly: the gradient pass writes zeros, the
+        // stage runs the inviscid body.
+        bool visc = true;
+        if constexpr (MODE != 0) {
+            int any = 0;
+            for (int i = tid; i < ne * 5; i += THREADS) any |= sSe[i] != Real(0);
+            visc = __syncthreads_or(any) != 0;
+        } else {
+            __syncthreads();
+        }
+        if constexpr (MODE == 2) {
+            if (!visc) {
+                for (int i = tid; i < ne * 5 * NP; i += THREADS) {
+                    const int e = i / (5 * NP), r = i - e * 5 * NP;
+                    p.qout[(e0 + e) * 15 * NP + p.grad_m * 5 * NP + r] = Real(0);
+                }
+                continue;
+            }
+        }
         // own and neighbours' face-node values, rows of NFPP
         for (int i = tid; i < ne * 20 * NFP; i += THREADS) {
             const int row = i / NFP, n = i - row * NFP;   // row = (e * 4 + f) * 5 + v
@@ -149,7 +169,7 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
             }
         }
         if constexpr (MODE == 1) {   // q face nodes of both sides, rows (e * 4 + f) * 15 + r
-            for (int i = tid; i < ne * 60 * NFP; i += THREADS) {
+            for (int i = tid; i < (visc ? ne * 60 * NFP : 0); i += THREADS) {
                 const int row = i / NFP, n = i - row * NFP;
                 const int e = row / 60, f = (row / 15) & 3, r = row % 15;
                 const int code = sCode[e * 4 + f];
@@ -174,8 +194,10 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
 #pragma unroll
                 for (int v = 0; v < 5; ++v) u[v] += dot4(w, lds4(ue + v * NPP + 4 * jb));
                 if constexpr (MODE == 1) {
+                    if (visc) {
 #pragma unroll
-                    for (int r = 0; r < 15; ++r) qc[r] += dot4(w, lds4(sQ + (e * 15 + r) * NPP + 4 * jb));
+                        for (int r = 0; r < 15; ++r) qc[r] += dot4(w, lds4(sQ + (e * 15 + r) * NPP + 4 * jb));
+                    }
                 }
             }
             Real cof[9];
@@ -211,9 +233,12 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
                     const Real U = c0 * vx + c1 * vy + c2 * vz;
                     Real f[5] = {u[0] * U, u[1] * U + pr * c0, u[2] * U + pr * c1, u[3] * U + pr * c2, H * U};
                     if constexpr (MODE == 1) {   // minus sqrt(eps) q in the physical fluxes
-                        const Real se = sSe[e * 5];
+                        if (visc) {
+                            const Real se = sSe[e * 5];
 #pragma unroll
-                        for (int v = 0; v < 5; ++v) f[v] -= se * (c0 * qc[v] + c1 * qc[5 + v] + c2 * qc[10 + v]);
+                            for (int v = 0; v < 5; ++v)
+                                f[v] -= se * (c0 * qc[v] + c1 * qc[5 + v] + c2 * qc[10 + v]);
+                        }
                     }
                     Real* out = sF + (e * 3 + a) * TT::FST + q;
 #pragma unroll
@@ -250,8 +275,12 @@ __global__ void __launch_bounds__(THREADS) stage3_kernel(const StageArgs3<Real> 
             }
         }
         // ---- phase 3: face-frame points (first on the threads phase 2 left idle)
-        face_points3<N, Real, 16, 0, MODE>(p, e0, ne, (tid + THREADS - n2 % THREADS) % THREADS, sI2, sW, sUf, sNb,
-                                           sCode, sG, nullptr, sFs, sSe, sQf, sQn, p.grad_m);
+        if (MODE == 1 && !visc)
+            face_points3<N, Real, 16, 0, 0>(p, e0, ne, (tid + THREADS - n2 % THREADS) % THREADS, sI2, sW, sUf, sNb,
+                                             sCode, sG, nullptr, sFs);
+        else
+            face_points3<N, Real, 16, 0, MODE>(p, e0, ne, (tid + THREADS - n2 % THREADS) % THREADS, sI2, sW, sUf,
+                                               sNb, sCode, sG, nullptr, sFs, sSe, sQf, sQn, p.grad_m);
         __syncthreads();
         // ---- phase 4a: lift of each face's flux to its face nodes
         lift3<N, Real>(ne, sI2T, sFs, sCode, sT);
