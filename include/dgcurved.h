@@ -243,9 +243,11 @@ int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* ms, const double* dts, int 
  * degree-N polynomial in every element, i.e. the modal coefficients of
  * degree <= N carried over and the higher ones zero (the basis is
  * hierarchical).  `from` and `to` must be two uploads of the same mesh
- * (both triangle or both tetrahedral meshes; same K, connectivity and
- * element order) with N_from <= N_to and the same state type (FP32
- * precisions together, or FP64_DEBUG with FP64_DEBUG).
+ * (both triangle or both tetrahedral meshes; same K and connectivity, the
+ * elements in the same caller order -- the library maps its own device
+ * orders, which may differ where an element is curved at one degree only)
+ * with N_from <= N_to and the same state type (FP32 precisions together, or
+ * FP64_DEBUG with FP64_DEBUG).
  * DG_EINVAL otherwise.  Synchronises the context's stream. */
 int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to);
 

@@ -1293,9 +1293,19 @@ int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to) {
     MeshData* a = find(ctx, from);
     MeshData* b = find(ctx, to);
     if (!a || !b) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
-    if (a == b || a->dim != b->dim || a->K != b->K || a->N > b->N || a->rsize != b->rsize || a->perm != b->perm)
+    if (a == b || a->dim != b->dim || a->K != b->K || a->N > b->N || a->rsize != b->rsize)
         return fail(ctx, DG_EINVAL,
                     "prolongation needs two uploads of one mesh, the target of degree >= the source, one state type");
+    // the device orders of the two uploads (affine elements first) may
+    // differ where an element is curved at one degree only: target element
+    // d takes source element src[d]
+    std::vector<long long> src;
+    if (a->perm != b->perm) {
+        std::vector<long long> ia((size_t)a->K);
+        for (long long d = 0; d < a->K; ++d) ia[(size_t)a->perm[d]] = d;
+        src.resize((size_t)b->K);
+        for (long long d = 0; d < b->K; ++d) src[(size_t)d] = ia[(size_t)b->perm[d]];
+    }
     std::vector<double> P;
     std::string err;
     const bool ok = a->dim == 3 ? build_prolongation3(a->N, b->N, P, err) : build_prolongation(a->N, b->N, P, err);
@@ -1314,13 +1324,20 @@ int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to) {
         std::vector<float> Pf(P.begin(), P.end());
         ce = cudaMemcpy(dP, Pf.data(), Pf.size() * 4, cudaMemcpyHostToDevice);
     }
+    long long* dsrc = nullptr;
+    if (ce == cudaSuccess && !src.empty()) {
+        ce = cudaMalloc((void**)&dsrc, src.size() * sizeof(long long));
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(dsrc, src.data(), src.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    }
     int e = (int)ce;
     if (!e)
         e = rs == 8 ? launch_prolong<double>((const double*)a->U[0], (double*)b->U[0], (const double*)dP, a->K,
-                                             a->nvar, a->Np, b->Np, ctx->stream)
+                                             a->nvar, a->Np, b->Np, dsrc, ctx->stream)
                     : launch_prolong<float>((const float*)a->U[0], (float*)b->U[0], (const float*)dP, a->K, a->nvar,
-                                            a->Np, b->Np, ctx->stream);
+                                            a->Np, b->Np, dsrc, ctx->stream);
     if (!e) e = (int)cudaStreamSynchronize(ctx->stream);
+    if (dsrc) cudaFree(dsrc);
     cudaFree(dP);
     if (e) return fail(ctx, DG_ECUDA, std::string("prolongation failed: ") + cudaGetErrorString((cudaError_t)e));
     b->eps_valid = false;

@@ -181,7 +181,7 @@ template <typename Real>
 int launch_permute(const Real* src, Real* dst, const long long* map, long long K, int rowlen, cudaStream_t st);
 template <typename Real>
 int launch_prolong(const Real* in, Real* out, const Real* P, long long K, int nvar, int npf, int npt,
-                   cudaStream_t st);
+                   const long long* src, cudaStream_t st);
 int residual_blocks();
 
 }  // namespace dgc

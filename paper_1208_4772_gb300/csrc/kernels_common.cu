@@ -92,15 +92,17 @@ __global__ void permute_rows(const Real* src, Real* dst, const long long* map, l
 }
 
 // Prolongation of a state between degrees: out[k][v][i] = sum_j P[i][j]
-// in[k][v][j] (nvar variables), one thread per output value.
+// in[src[k]][v][j] (nvar variables; src null: src[k] = k), one thread per
+// output value.
 template <typename Real>
 __global__ void __launch_bounds__(256) prolong_kernel(const Real* in, Real* out, const Real* P, long long K, int nvar,
-                                                     int npf, int npt) {
+                                                     int npf, int npt, const long long* src) {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= K * nvar * npt) return;
     const long long row = n / npt;
     const int i = (int)(n - row * npt);
-    const Real* x = in + row * npf;
+    const long long k = row / nvar;
+    const Real* x = in + ((src ? src[k] : k) * nvar + (row - k * nvar)) * npf;
     const Real* pr = P + (long long)i * npf;
     Real acc = 0;
     for (int j = 0; j < npf; ++j) acc += pr[j] * x[j];
@@ -111,10 +113,10 @@ __global__ void __launch_bounds__(256) prolong_kernel(const Real* in, Real* out,
 
 template <typename Real>
 int launch_prolong(const Real* in, Real* out, const Real* P, long long K, int nvar, int npf, int npt,
-                   cudaStream_t st) {
+                   const long long* src, cudaStream_t st) {
     const long long total = K * nvar * npt;
     if (total == 0) return 0;
-    prolong_kernel<Real><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(in, out, P, K, nvar, npf, npt);
+    prolong_kernel<Real><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(in, out, P, K, nvar, npf, npt, src);
     return (int)cudaGetLastError();
 }
 
@@ -144,8 +146,10 @@ template int launch_residual<float>(const float*, int, long long, int, double*, 
 template int launch_residual<double>(const double*, int, long long, int, double*, double*, cudaStream_t);
 template int launch_permute<float>(const float*, float*, const long long*, long long, int, cudaStream_t);
 template int launch_permute<double>(const double*, double*, const long long*, long long, int, cudaStream_t);
-template int launch_prolong<float>(const float*, float*, const float*, long long, int, int, int, cudaStream_t);
-template int launch_prolong<double>(const double*, double*, const double*, long long, int, int, int, cudaStream_t);
+template int launch_prolong<float>(const float*, float*, const float*, long long, int, int, int, const long long*,
+                                   cudaStream_t);
+template int launch_prolong<double>(const double*, double*, const double*, long long, int, int, int,
+                                    const long long*, cudaStream_t);
 
 namespace {
 

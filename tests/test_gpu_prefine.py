@@ -70,12 +70,14 @@ def test_prolong_refuses_other_mesh(B, ctx):
     B.dg_mesh_free(ctx, h2)
 
 
-@pytest.mark.parametrize("kind", ["box", "wbox"])
+@pytest.mark.parametrize("kind", ["box", "wbox", "bump"])
 @pytest.mark.parametrize("prec,tol,N,M", [("fp64", 1e-12, 2, 3), ("fp64", 1e-12, 2, 4), ("fp64", 1e-12, 3, 4),
                                           ("fp32", 1e-6, 2, 4), ("tf32", 1e-6, 2, 3)])
 def test_prolong_tetrahedra_matches_oracle(B, ctx, kind, prec, tol, N, M):
     """The paper's own use (Sec. 5): 3D runs refined from p = 2 to 3 and 4.
-    Two uploads of one tetrahedral mesh (affine, or every element curved);
+    Two uploads of one tetrahedral mesh (affine, every element curved, or the
+    bump channel, whose elements at the edge of the bump are curved at some
+    degrees only, so that the two uploads order their elements differently);
     the prolonged state against the oracle's, then one SSP-RK3 step at the
     higher degree against the oracle's step of the prolonged state."""
     from cases import make_case3
@@ -121,3 +123,33 @@ def test_prolong_refuses_triangle_to_tetrahedron(B, ctx):
     assert e.value.status == B.DG_EINVAL
     B.dg_mesh_free(ctx, h1)
     B.dg_mesh_free(ctx, h2)
+
+
+def test_prefine_driver_on_tetrahedra(B, ctx):
+    """The level driver on a tetrahedral mesh (the paper's 3D setting, Sec. 5:
+    p = 2, then 3): its final state equals the same sequence done by hand --
+    freestream at N = 2, the level's steps, dg_prolong to N = 3, its steps --
+    bitwise."""
+    from paper_1208_4772_gb300 import prefine
+    from paper_1208_4772_gb300.inputs import meshes3d
+    m = meshes3d.bump_channel(6, 3, 4, seed=2000)
+    ui = states.freestream3(0.5, 0.0)
+    h, rep = prefine.run_levels(ctx, m, [2, 3], ui, prec="fp32", drop=1e-3, check_every=25, max_steps=50)
+    assert [r["N"] for r in rep] == [2, 3] and all(r["steps"] == 50 for r in rep)
+    assert all(np.isfinite(r["r_last"]) for r in rep)
+    U = B.dg_get_state(ctx, h)
+    B.dg_mesh_free(ctx, h)
+    hs = []
+    for N in (2, 3):
+        r, s, t = B.dg_tet_reference_nodes(N)
+        X = meshes3d.node_coords(m, r, s, t)
+        hs.append(B.dg_tet_mesh_upload(ctx, N, m.EToV, m.bc, X, B.make_params(u_inf=ui, prec="fp32")))
+    B.dg_set_state(ctx, hs[0], states.uniform_state3(m.K, 10, ui))
+    B.dg_step(ctx, hs[0], rep[0]["dt"], 50)
+    B.dg_prolong(ctx, hs[0], hs[1])
+    B.dg_step(ctx, hs[1], rep[1]["dt"], 50)
+    Uh = B.dg_get_state(ctx, hs[1])
+    for x in hs:
+        B.dg_mesh_free(ctx, x)
+    assert U.shape == (m.K, 5, 20)
+    assert np.array_equal(U, Uh)
