@@ -122,10 +122,16 @@ def inradius3(verts):
     return 3.0 * vol / area
 
 
-def time_step3(verts, U, N, cfl=0.3, gamma=1.4):
-    """dt = CFL h_min / ((N+1)^2 max(|u| + c)) with h the inradius."""
+def time_step3(verts, U, N, cfl=0.3, gamma=1.4, eps0=None):
+    """dt = CFL h_min / ((N+1)^2 max(|u| + c)) with h the inradius; with
+    artificial viscosity up to eps0 also at most CFL h_min^2 / (2 (N+1)^4
+    eps0), the limit of the triangle path."""
     rho = U[:, 0]
     vel2 = (U[:, 1] ** 2 + U[:, 2] ** 2 + U[:, 3] ** 2) / rho ** 2
     p = (gamma - 1.0) * (U[:, 4] - 0.5 * rho * vel2)
     smax = float(np.max(np.sqrt(vel2) + np.sqrt(gamma * p / rho)))
-    return cfl * float(np.min(inradius3(verts))) / ((N + 1) ** 2 * smax)
+    h = float(np.min(inradius3(verts)))
+    dt = cfl * h / ((N + 1) ** 2 * smax)
+    if eps0:
+        dt = min(dt, 0.5 * cfl * h * h / ((N + 1) ** 4 * eps0))
+    return dt
