@@ -46,7 +46,9 @@ artificial-viscosity right-hand side (the paper prints no values for it) is
 pinned by free stream, conservation and the closed forms of
 tests/test_oracle_av_pins.py: the gradient exact on linear states, a
 constant viscous flux cancelling, eps = 0 giving the inviscid right-hand
-side.
+side; the sqrt(eps) weighting of both central fluxes where eps jumps across
+a face by the discrete divergence identities of
+tests/test_oracle_br1_jump.py.
 
 Test infrastructure only.
 """
@@ -97,6 +99,14 @@ class Oracle:
     def neighbours(self, idx):
         nb = self.EToE[idx].ravel()
         return np.unique(np.concatenate([idx, nb]))
+
+    def _sqrt_eps_faces(self, eps, idx):
+        """sqrt(eps) of each element (own, [n]) and of the other side of each
+        of its faces ([n, 3]): the neighbour's, or the element's own on a
+        boundary face (eps+ = eps- there)."""
+        se = np.sqrt(eps[idx])
+        sep = np.where(self.bc[idx] == BC_INTERIOR, np.sqrt(eps[self.EToE[idx]]), se[:, None])
+        return se, sep
 
     def traces(self, V):
         """Own traces I_g^f V on all three faces: [n, nv, 3, Ng]."""
@@ -163,7 +173,7 @@ class Oracle:
         Returns q [n, 2, 4, Np] (m = x, y)."""
         ref = self.ref
         geo = self.geometry(idx)
-        se = np.sqrt(eps[idx])
+        se, sep = self._sqrt_eps_faces(eps, idx)
         Ui = U[idx]
         Uc = (Ui @ ref.Icub.T) * se[:, None, None]
         WJ = (ref.wq[None, :] * geo.J)[:, None, :]
@@ -171,7 +181,6 @@ class Oracle:
         nx, ny = geo.nx, geo.ny
         bci = self.bc[idx]
         Up = self._exterior(U, idx, Um, lambda T: self._ghost(T, bci, nx, ny))
-        sep = np.where(bci == BC_INTERIOR, np.sqrt(eps[self.EToE[idx]]), se[:, None])
         ustar = 0.5 * (se[:, None, None, None] * Um + sep[:, None, :, None] * Up)
         wsJ = (ref.wg[None, None, :] * geo.sJ)[:, None]
         q = np.zeros((len(idx), 2, 4, ref.Np))
@@ -226,8 +235,7 @@ class Oracle:
             qp = self._exterior(q.reshape(self.K, 8, ref.Np), idx, qm, lambda T: T)
             qm = qm.reshape(n, 2, 4, 3, ref.Ng)
             qp = qp.reshape(n, 2, 4, 3, ref.Ng)
-            se = np.sqrt(eps[idx])
-            sep = np.where(bci == BC_INTERIOR, np.sqrt(eps[self.EToE[idx]]), se[:, None])
+            se, sep = self._sqrt_eps_faces(eps, idx)
             qn_m = qm[:, 0] * nx[:, None] + qm[:, 1] * ny[:, None]
             qn_p = qp[:, 0] * nx[:, None] + qp[:, 1] * ny[:, None]
             Fs = Fs - 0.5 * (se[:, None, None, None] * qn_m + sep[:, None, :, None] * qn_p)
