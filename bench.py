@@ -1,11 +1,17 @@
 #!/usr/bin/env python3
 """Benchmark of the curved-element RKDG hot path on GB300.
 
-Metric: RK-stage DOF-updates/s = K * N_p * 4 * (RK stages) / device time.
-Default workload: transonic flow past a NACA 0012 profile (Mach 0.8, angle
-of attack 1.25 deg) on a seeded O-mesh of 60,000 triangles in a radius-20
-farfield, wall elements curved to degree N = 4 by the linear-elasticity
-set-up, Persson-Peraire artificial viscosity on, FP32 state, SSP-RK3.
+Metric: RK-stage DOF-updates/s = K * N_p * 4 * (RK stages) / device time,
+for the mixed-precision products and the FP32 path on the same GPU.
+Default workload: the precision sweep on a curved cylinder-in-channel mesh
+(Mach 0.38, 250,000 triangles, wall elements curved to degree N = 6 by the
+linear-elasticity set-up, FP32 state, SSP-RK3): TF32 products timed, FP32
+and split-BF16 products timed beside them, each precision's error against
+the FP64 oracle (and, on the isentropic-vortex twin of the same N and K,
+against the FP64 path and the exact solution) in `error_vs_oracle`.  The
+NACA 0012 workload (Mach 0.8, 60,000 triangles, N = 4, artificial viscosity
+on) starts from a state with troubled cells (a jump across the wake) and
+reports its viscous and inviscid stage launches.
 
 One "step" = one SSP-RK3 step = 3 right-hand-side evaluations with the stage
 update fused in (sensor, gradient and stage kernels per stage), replayed from
@@ -40,12 +46,33 @@ UNIT = "DOF-updates/s"
 # element-local operator products in TF32 or split BF16 on the tensor cores
 DTYPE = {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3", "fp64": "f64"}
 
-# DRAM bytes (read + write) of one stage-kernel launch from an ncu capture of
-# the command (summaries in profiles/stage_kernel_tc_naca0012_n4_av.md and
-# profiles/stage3_tc_kernel_bump3d_n3.md); keyed by (workload, products, flux),
-# SSP-RK3 stages only, and only valid for the kernel source it was taken on.
-TRAFFIC = {("naca0012_m0.8_n4_av", "tf32", "llf"): 31.893e6,
-           ("bump3d_m0.5_n3", "tf32", "llf"): 537.36e6}
+# DRAM bytes (read + write) of one stage-kernel launch from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload,
+# products, flux, launch kind), SSP-RK3 stages only.  Each entry carries the
+# hash of the kernel sources it was taken on; a line whose sources differ
+# reports traffic null.
+TRAFFIC = {}
+
+# the sources of each stage kernel, hashed into the traffic key above
+KERNEL_SOURCES = {"tri": ("tc_kernels.cuh", "tc_ptx.cuh", "kernels.cuh", "dg_device.h"),
+                  "tet": ("kernels3_tc.cu", "kernels3.cuh", "kernels3.cu", "dg3_device.h")}
+
+
+def kernel_source_hash(kind):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kind]:
+        with open(os.path.join(ROOT, "paper_1208_4772_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def traffic_of(workload, prec, flux, kind, launch="stage"):
+    """ncu DRAM bytes of one launch, if taken on the current sources."""
+    t = TRAFFIC.get((workload, prec, flux, launch))
+    if t is None or t[1] != kernel_source_hash(kind):
+        return None
+    return t[0]
 
 WORKLOADS = {
     "naca0012_m0.8_n4_av": dict(kind="naca", N=4, n_t=300, n_r=100, mach=0.8, aoa=1.25, av=True,
@@ -78,9 +105,13 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="naca0012_m0.8_n4_av", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cylinder_m0.38_n6", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="tf32", help="products: tf32 (default), bf16x3, fp32, fp64")
-    ap.add_argument("--compare-prec", default="fp32", help="also time this precision ('' to skip)")
+    ap.add_argument("--compare-prec", default="fp32,bf16x3",
+                    help="also time these precisions, comma-separated (none or '' to skip)")
+    ap.add_argument("--no-errors", action="store_true", help="skip the error_vs_oracle measurements")
+    ap.add_argument("--av-start", default="jump", choices=["jump", "freestream"],
+                    help="AV workloads: start from a state with troubled cells (jump) or the freestream")
     ap.add_argument("--integrator", default="ssp3", choices=["ssp3", "lserk"],
                     help="SSP-RK3 (3 stages) or the paper's low-storage RK(5,4) (5 stages)")
     ap.add_argument("--flux", default="llf", choices=["llf", "hllc"], help="numerical flux at the faces")
@@ -98,13 +129,19 @@ def parse_args():
     ap.add_argument("--serve-max-steps", type=int, default=2000)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--cpu-sample", default="", help=argparse.SUPPRESS)
-    ap.add_argument("--cpu-budget-s", type=float, default=20.0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-start", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ workload
-def make_workload(name, r, s):
-    """Seeded mesh, curved nodes, initial state and time step (inputs only)."""
+def make_workload(name, r, s, av_start="jump"):
+    """Seeded mesh, curved nodes, initial state and time step (inputs only).
+    With artificial viscosity and av_start == "jump" every variable is
+    multiplied by 1.5 downstream of x = 2 (a jump of density and energy at
+    unchanged velocity and sound speed), so that the elements the line cuts
+    are troubled cells (eps > 0) from the first step."""
+    import numpy as np
     from paper_1208_4772_gb300.inputs import curving, meshes, states
     w = WORKLOADS[name]
     if w["kind"] == "naca":
@@ -114,8 +151,22 @@ def make_workload(name, r, s):
     xy, curved = curving.curve_mesh(mesh, w["N"], r, s)
     ui = states.freestream(w["mach"], w["aoa"])
     U0 = states.uniform_state(mesh.K, len(r), ui)
+    if w["av"] and av_start == "jump":
+        U0 = U0 * np.where(xy[..., 0] > 2.0, 1.5, 1.0)[:, None, :]
     dt = states.time_step(mesh.verts, U0, w["N"], cfl=0.3, eps0=0.3 if w["av"] else None)
-    return dict(mesh=mesh, xy=xy, curved=curved, u_inf=ui, U0=U0, dt=dt, **w)
+    return dict(mesh=mesh, xy=xy, curved=curved, u_inf=ui, U0=U0, dt=dt, av_start=av_start if w["av"] else None, **w)
+
+
+def make_vortex_twin(N, n, r, s):
+    """The isentropic-vortex twin of a workload: the periodic square [0,10]^2
+    of n x n cells cut along one diagonal (K = 2 n^2), jittered vertices,
+    the vortex state; its exact solution is the translated vortex."""
+    from paper_1208_4772_gb300.inputs import meshes, states
+    mesh = meshes.periodic_square(n, length=10.0, seed=1000)
+    xy = meshes.straight_nodes(mesh.verts, r, s)
+    U0 = states.vortex_state(xy, period=(10.0, 10.0))
+    dt = states.time_step(mesh.verts, U0, N, cfl=0.3)
+    return dict(mesh=mesh, xy=xy, U0=U0, dt=dt, u_inf=states.freestream(0.5, 45.0))
 
 
 def make_tet_workload(name, r, s, t):
@@ -237,74 +288,172 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_sample(name, budget_s, flux="llf"):
-    """Time the FP64 oracle on the workload (fresh single-thread process)."""
+# The FP64 oracle as it stands, timed on the host cores on a bounded sample
+# of the workload: right-hand sides of one contiguous block of elements
+# (with the artificial viscosity, each call also computes the sensor and the
+# gradient on the rings of neighbours the block needs, as the oracle does
+# for any subset).  The oracle builds the geometry of a subset in every
+# call; here it is built once per subset before the timer, as the geometry
+# of the whole mesh is built once at set-up.  The single-core leg, the
+# all-cores leg (one process per core on disjoint blocks, like the paper's
+# OpenMP loop over elements) and the reference arm share this sampler.
+def oracle_inputs_path(wl, flux, kind):
+    """Write the oracle's inputs once (inputs only, no arithmetic of the
+    method) for the CPU legs' worker processes; returns the file's path."""
+    import tempfile
     import numpy as np
-    if WORKLOADS[name]["kind"] == "tet":
-        return cpu_sample_tet(name, budget_s, flux)
-    from oracle.dg import Oracle
-    from oracle.operators import ReferenceElement
-    ref = ReferenceElement(WORKLOADS[name]["N"])
-    wl = make_workload(name, ref.r, ref.s)
+    fd, path = tempfile.mkstemp(suffix=".npz", prefix="dg_oracle_inputs_")
+    os.close(fd)
     m = wl["mesh"]
-    o = Oracle(wl["N"], m.EToE, m.EToF, m.bc, wl["xy"], u_inf=wl["u_inf"], av=wl["av"], flux=flux)
-    o.geometry(None)
-    U = wl["U0"]
-    t0 = time.perf_counter()
-    U = o.ssp_rk3_step(U, wl["dt"])
-    full = time.perf_counter() - t0
-    steps = 1
-    while time.perf_counter() - t0 + full < budget_s:
-        U = o.ssp_rk3_step(U, wl["dt"])
-        steps += 1
-    el = time.perf_counter() - t0
-    dof = m.K * ref.Np * 4
-    return {"value": dof * 3 * steps / el, "seconds": el,
-            "sample": "%d full SSP-RK3 step(s) (%d RHS evaluations) of the whole %d-element mesh, "
-                      "oracle geometry set-up excluded" % (steps, 3 * steps, m.K)}
+    if kind == "tet":
+        np.savez(path, kind="tet", N=wl["N"], EToV=m.EToV, bc=m.bc, X=wl["xyz"], U0=wl["U0"],
+                 u_inf=wl["u_inf"], av=False, flux=flux)
+    else:
+        np.savez(path, kind="tri", N=wl["N"], EToE=m.EToE, EToF=m.EToF, bc=m.bc, X=wl["xy"], U0=wl["U0"],
+                 u_inf=wl["u_inf"], av=bool(wl["av"]), flux=flux)
+    return path
 
 
-def cpu_sample_tet(name, budget_s, flux):
-    """The tetrahedral oracle as it stands on a sample of elements:
-    right-hand sides of every 100th element, repeated within the budget (each
-    call computes the sample's geometry, as the oracle does for a subset);
-    DOF-updates/s of the sample."""
-    import numpy as np
-    from oracle.dg3 import Oracle3
-    from oracle.tet import ReferenceTet
-    w = WORKLOADS[name]
-    ref = ReferenceTet(w["N"])
-    wl = make_tet_workload(name, ref.r, ref.s, ref.t)
-    m = wl["mesh"]
-    o = Oracle3(w["N"], m.EToV, m.bc, wl["xyz"], u_inf=wl["u_inf"], flux=flux)
-    idx = np.arange(0, m.K, 100)
-    U = wl["U0"]
-    t0 = time.perf_counter()
-    n = 0
-    while True:
-        o.rhs(U, idx)
-        n += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    el = time.perf_counter() - t0
-    return {"value": len(idx) * ref.Np * 5 * n / el, "seconds": el,
-            "sample": "%d right-hand sides of %d of the %d elements (every 100th), the sample's geometry "
-                      "computed in each call" % (n, len(idx), m.K)}
+class OracleSampler:
+    """Right-hand sides of the oracle on one contiguous block of elements."""
+
+    def __init__(self, path):
+        import numpy as np
+        d = np.load(path)
+        self.kind = str(d["kind"])
+        self.N = int(d["N"])
+        self.U0 = d["U0"]
+        flux, av = str(d["flux"]), bool(d["av"])
+        if self.kind == "tet":
+            from oracle.dg3 import Oracle3
+            base, args = Oracle3, (self.N, d["EToV"], d["bc"], d["X"])
+            self.nv = 5
+        else:
+            from oracle.dg import Oracle
+            base, args = Oracle, (self.N, d["EToE"], d["EToF"], d["bc"], d["X"])
+            self.nv = 4
+        cache = {}
+
+        class Cached(base):
+            def geometry(self, idx=None):
+                if idx is None:
+                    return super().geometry(None)
+                key = np.asarray(idx).tobytes()
+                if key not in cache:
+                    cache[key] = super().geometry(idx)
+                return cache[key]
+        kw = dict(u_inf=d["u_inf"], flux=flux)
+        if av:
+            kw["av"] = True
+        self.o = Cached(*args, **kw)
+        self.K = self.o.K
+        self.Np = self.U0.shape[2]
+
+    def block(self, start, size):
+        import numpy as np
+        size = max(1, min(int(size), self.K))
+        start = int(start) % max(1, self.K - size + 1)
+        return np.arange(start, start + size)
+
+    def calibrate(self, start, seconds_per_call):
+        """Block size whose right-hand side takes about seconds_per_call
+        (after its geometry has been built)."""
+        import time as _t
+        S = 64
+        while True:
+            idx = self.block(start, S)
+            self.o.rhs(self.U0, idx)                        # builds and caches the geometry
+            t0 = _t.perf_counter()
+            self.o.rhs(self.U0, idx)
+            el = _t.perf_counter() - t0
+            if el > 0.5 * seconds_per_call or S >= self.K:
+                return max(16, min(self.K, int(S * seconds_per_call / max(el, 1e-6))))
+            S *= 4
+
+    def rate(self, idx, budget_s):
+        """DOF-updates/s of right-hand sides on idx, repeated for budget_s."""
+        import time as _t
+        self.o.rhs(self.U0, idx)                            # geometry of idx and its rings, untimed
+        t0 = _t.perf_counter()
+        n = 0
+        while True:
+            self.o.rhs(self.U0, idx)
+            n += 1
+            el = _t.perf_counter() - t0
+            if el > budget_s:
+                break
+        return len(idx) * self.Np * self.nv * n / el, n
 
 
-def run_cpu_baseline(name, budget_s, flux="llf"):
+def cpu_worker(path, start, budget_s):
+    """One process of a CPU leg: the oracle on the block at `start`."""
+    sm = OracleSampler(path)
+    S = sm.calibrate(start, 1.0)
+    idx = sm.block(start, S)
+    value, n = sm.rate(idx, budget_s)
+    return {"value": value, "evals": n, "block": [int(idx[0]), int(len(idx))], "K": int(sm.K)}
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def run_cpu_baseline(path, budget_s):
+    """The single-core leg and the all-cores leg (one single-threaded
+    worker process per core, each on its own block; the sum of their
+    rates).  Fresh processes: no CUDA context, one BLAS thread each."""
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", name,
-                        "--cpu-budget-s", str(budget_s), "--flux", flux], capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        return {"error": r.stderr[-500:]}
-    out = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": out["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": out["sample"]}
+
+    def launch(P):
+        procs = []
+        for i in range(P):
+            start = (i * 7919 * 64) if P > 1 else 0
+            procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-sample", path,
+                                           "--cpu-budget-s", str(budget_s), "--cpu-start", str(start)],
+                                          stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env))
+        res = []
+        for pr in procs:
+            out, err = pr.communicate(timeout=900)
+            if pr.returncode != 0:
+                return None, err[-500:]
+            res.append(json.loads(out.strip().splitlines()[-1]))
+        return res, None
+
+    one, err = launch(1)
+    if one is None:
+        return {"error": err}
+    ncores = os.cpu_count() or 1
+    allc, err = launch(ncores)
+    r1 = one[0]
+    line = {"value": r1["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "right-hand sides of a block of %d contiguous elements of the %d-element mesh, repeated "
+                      "for %.0f s (%d calls); the block's geometry built before the timer"
+                      % (r1["block"][1], r1["K"], budget_s, r1["evals"]),
+            "nproc": ncores, "cpu_model": cpu_model()}
+    if allc is not None:
+        line["all_cores"] = {"value": sum(r["value"] for r in allc), "unit": UNIT, "cores": ncores,
+                             "sample": "%d single-threaded processes, one block each (%s elements), the "
+                                       "sum of their rates" % (ncores, ",".join(str(r["block"][1]) for r in allc))}
+    else:
+        line["all_cores"] = {"error": err}
+    return line
 
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
+    """The oracle arm: each step is one SSP-RK3 step (three right-hand
+    sides with the stage combinations) on a contiguous block of elements
+    of about one second of oracle work per right-hand side (less when the
+    warm-up and timed steps would take more than 100 s)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -314,48 +463,53 @@ def run_reference(args):
         return 0
     for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"          # before numpy loads: the oracle runs on one core
-    if WORKLOADS[args.workload]["kind"] == "tet":
-        return run_reference_tet(args)
-    import numpy as np
-    from oracle.dg import Oracle
-    from oracle.operators import ReferenceElement
-    wl_def = WORKLOADS[args.workload]
-    ref = ReferenceElement(wl_def["N"])
-    wl = make_workload(args.workload, ref.r, ref.s)
-    m = wl["mesh"]
-    o = Oracle(wl["N"], m.EToE, m.EToF, m.bc, wl["xy"], u_inf=wl["u_inf"], av=wl["av"], flux=args.flux)
-    # each step: one SSP-RK3 step (3 RHS evaluations) on a fixed sample of
-    # elements, sized so that warm-up + timed steps take about 150 s
-    t0 = time.perf_counter()
-    probe = np.arange(0, m.K, max(1, m.K // 256))
-    o.rhs(wl["U0"], probe)
-    per_elt = (time.perf_counter() - t0) / len(probe)
-    per_step = 150.0 / max(1, args.steps + args.warmup)
-    S = int(max(16, min(m.K, per_step / (3 * per_elt))))
-    idx = np.linspace(0, m.K - 1, S).astype(np.int64)
-    U = wl["U0"].copy()
+    kind = "tet" if WORKLOADS[args.workload]["kind"] == "tet" else "tri"
+    if kind == "tet":
+        from oracle.tet import ReferenceTet
+        ref = ReferenceTet(WORKLOADS[args.workload]["N"])
+        wl = make_tet_workload(args.workload, ref.r, ref.s, ref.t)
+        cfg = {"workload": args.workload, "describe": wl["describe"], "K": int(wl["mesh"].K), "N": wl["N"],
+               "flux": args.flux.upper()}
+    else:
+        from oracle.operators import ReferenceElement
+        ref = ReferenceElement(WORKLOADS[args.workload]["N"])
+        wl = make_workload(args.workload, ref.r, ref.s, args.av_start)
+        cfg = config_of(args, wl)
+    path = oracle_inputs_path(wl, args.flux, kind)
+    try:
+        sm = OracleSampler(path)
+        per_step = 100.0 / max(1, args.steps + args.warmup)
+        S = int(sm.calibrate(0, 0.5) * min(1.0, per_step / 3.0) / 0.5)
+        idx = sm.block(sm.K // 2, S)
+        o, dt = sm.o, wl["dt"]
+        U = sm.U0.copy()
 
-    def step():
-        Us = U
-        for a, b in ((0.0, 1.0), (0.75, 0.25), (1 / 3, 2 / 3)):
-            L = o.rhs(Us, idx)
-            Us = Us.copy()
-            Us[idx] = a * U[idx] + b * (Us[idx] + wl["dt"] * L)
-        return Us
+        def step():
+            Us = U
+            for a, b in ((0.0, 1.0), (0.75, 0.25), (1 / 3, 2 / 3)):
+                L = o.rhs(Us, idx)
+                Us = Us.copy()
+                Us[idx] = a * U[idx] + b * (Us[idx] + dt * L)
+            return Us
 
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    el = time.perf_counter() - t0
-    value = S * ref.Np * 4 * 3 * args.steps / el
-    sample = "%d of %d elements per SSP-RK3 step (3 RHS evaluations on the sample)" % (S, m.K)
+        o.rhs(U, idx)             # geometry of the block and its rings, before the warm-up
+        for _ in range(args.warmup):
+            step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        el = time.perf_counter() - t0
+    finally:
+        os.unlink(path)
+    value = len(idx) * sm.Np * sm.nv * 3 * args.steps / el
+    sample = ("a block of %d contiguous elements of %d per SSP-RK3 step (3 right-hand sides on the block; its "
+              "geometry built before the timer)" % (len(idx), sm.K))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_of(args, wl),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -370,6 +524,8 @@ def config_of(args, wl):
             "time_integrator": "LSERK(5,4)" if getattr(args, "integrator", "ssp3") == "lserk" else "SSP-RK3",
             "flux": getattr(args, "flux", "llf").upper(),
             "dt": wl["dt"], "dof_per_stage": int(m.K * Np * 4),
+            "start_state": ("troubled cells: every variable x1.5 downstream of x = 2" if wl.get("av_start") == "jump"
+                            else "freestream"),
             "l2": "flushed before every timed step (%d MiB memset, outside the step events)" % args.flush_mb,
             "parallelism": "replicas (one independent solve per GPU)"}
 
@@ -419,6 +575,104 @@ def timed_steps(B, ctx, h, dt, steps, stream, flush, torch, profiled=False, step
     return times, kt, launches
 
 
+def oracle_step_sample(o, U, dt, idx, depth):
+    """One SSP-RK3 step of the oracle on the elements idx only: each stage
+    on the rings of neighbours the next stage needs (depth rings per stage:
+    1 for the Euler right-hand side, 2 with the artificial viscosity)."""
+    import numpy as np
+    rings = [np.asarray(idx)]
+    for _ in range(2 * depth):
+        rings.append(o.neighbours(rings[-1]))
+    S1, S2, S3 = rings[2 * depth], rings[depth], rings[0]
+    U1 = U.copy()
+    U1[S1] = U[S1] + dt * o.rhs(U, S1)
+    U2 = U.copy()
+    U2[S2] = 0.75 * U[S2] + 0.25 * (U1[S2] + dt * o.rhs(U1, S2))
+    return U[S3] / 3.0 + 2.0 / 3.0 * (U2[S3] + dt * o.rhs(U2, S3))
+
+
+def rel_l2_max(a, b):
+    """max over the conserved variables of ||a - b|| / ||b|| (arrays [n, nv, Np])."""
+    import numpy as np
+    nv = a.shape[1]
+    d = np.linalg.norm((a - b).transpose(1, 0, 2).reshape(nv, -1), axis=1)
+    return float(np.max(d / np.linalg.norm(b.transpose(1, 0, 2).reshape(nv, -1), axis=1)))
+
+
+def precision_errors(B, ctx, args, wl, precs, r, s):
+    """error_vs_oracle of the bench line, per precision of the products.
+
+    rhs_sampled: the right-hand side of the workload mesh for a perturbed
+    state (the AV workload: its start state, whose troubled cells are in the
+    sample) against the FP64 oracle on 160 random and 64 wall elements (and
+    64 troubled ones), relative L2, the largest over the variables.
+    vortex_twin (N = 6 workload): the isentropic vortex on the periodic
+    square of the same N and about the same K (n = 354, K = 250,632), 100
+    SSP-RK3 steps in each precision: the increment U_100 - U_0 against that
+    of the FP64 path (itself within 1e-12 of the oracle on the parity
+    meshes), the state against the exact (translated) vortex, and the
+    sampled right-hand side against the oracle."""
+    import numpy as np
+    from oracle.dg import Oracle
+    N = wl["N"]
+    m = wl["mesh"]
+    Np = len(r)
+    rng = np.random.default_rng(17)
+    out = {}
+    x, y = wl["xy"][..., 0], wl["xy"][..., 1]
+    U = wl["U0"].copy()
+    if not wl["av"]:
+        U[:, 0] *= 1.0 + 0.02 * np.sin(1.3 * x) * np.cos(0.7 * y)
+        U[:, 3] *= 1.0 + 0.02 * np.cos(0.9 * x + 0.4 * y)
+        U[:, 1] += 0.02 * np.sin(y)
+        U[:, 2] += 0.02 * np.cos(x)
+    U = U.astype(np.float32).astype(np.float64)
+    wall = np.nonzero(np.any(m.bc == 1, axis=1))[0]
+    parts = [rng.choice(m.K, 160, replace=False), rng.choice(wall, min(64, len(wall)), replace=False)]
+    if wl["av"]:
+        cut = np.nonzero((x.min(axis=1) < 2.0) & (x.max(axis=1) > 2.0))[0]
+        parts.append(rng.choice(cut, min(64, len(cut)), replace=False))
+    idx = np.unique(np.concatenate(parts))
+    o = Oracle(N, m.EToE, m.EToF, m.bc, wl["xy"], u_inf=wl["u_inf"], av=wl["av"], flux=args.flux)
+    Lo = o.rhs(U, idx)
+    rs = {}
+    for prec in precs:
+        h = B.dg_mesh_upload(ctx, N, m.EToE, m.EToF, m.bc, wl["xy"],
+                             B.make_params(u_inf=wl["u_inf"], av_on=wl["av"], prec=prec, flux=args.flux))
+        B.dg_set_state(ctx, h, U)
+        L = B.dg_eval_rhs(ctx, h, m.K, Np)
+        B.dg_mesh_free(ctx, h)
+        rs[prec] = rel_l2_max(L[idx], Lo)
+    out["rhs_sampled"] = {"elements": int(len(idx)), "rel_l2": rs,
+                          "state": "start state (troubled cells)" if wl["av"] else "smoothly perturbed freestream"}
+    if N == 6:
+        from paper_1208_4772_gb300.inputs import states
+        tw = make_vortex_twin(N, 354, r, s)
+        mt = tw["mesh"]
+        U0 = tw["U0"].astype(np.float32).astype(np.float64)
+        nsteps = 100
+        res = {}
+        for prec in list(precs) + (["fp64"] if "fp64" not in precs else []):
+            h = B.dg_mesh_upload(ctx, N, mt.EToE, mt.EToF, mt.bc, tw["xy"],
+                                 B.make_params(u_inf=tw["u_inf"], prec=prec, flux=args.flux))
+            B.dg_set_state(ctx, h, U0)
+            Lt = B.dg_eval_rhs(ctx, h, mt.K, Np)
+            B.dg_step(ctx, h, tw["dt"], nsteps)
+            res[prec] = (B.dg_get_state(ctx, h, mt.K, Np), Lt)
+            B.dg_mesh_free(ctx, h)
+        ref_inc = res["fp64"][0] - U0
+        exact = states.vortex_state(tw["xy"], t=nsteps * tw["dt"], period=(10.0, 10.0))
+        it = np.unique(rng.choice(mt.K, 192, replace=False))
+        ot = Oracle(N, mt.EToE, mt.EToF, mt.bc, tw["xy"], flux=args.flux)
+        Lot = ot.rhs(U0, it)
+        out["vortex_twin"] = {
+            "K": int(mt.K), "N": N, "steps": nsteps, "dt": tw["dt"],
+            "increment_vs_fp64_path": {p: rel_l2_max(v[0] - U0, ref_inc) for p, v in res.items() if p != "fp64"},
+            "state_vs_exact": {p: rel_l2_max(v[0], exact) for p, v in res.items()},
+            "rhs_sampled_vs_oracle": {p: rel_l2_max(v[1][it], Lot) for p, v in res.items()}}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -439,7 +693,7 @@ def run_ours(args):
     B.load()
     N = WORKLOADS[args.workload]["N"]
     r, s = B.dg_reference_nodes(N)
-    wl = make_workload(args.workload, r, s)
+    wl = make_workload(args.workload, r, s, args.av_start)
     m = wl["mesh"]
     Np = len(r)
     dof_stage = m.K * Np * 4
@@ -451,10 +705,10 @@ def run_ours(args):
     ctx = B.dg_create(local, stream.cuda_stream)
     flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device="cuda")
 
-    def upload(prec):
+    def upload(prec, U0=None):
         p = B.make_params(u_inf=wl["u_inf"], av_on=wl["av"], prec=prec, flux=args.flux)
         h = B.dg_mesh_upload(ctx, N, m.EToE, m.EToF, m.bc, wl["xy"], p)
-        B.dg_set_state(ctx, h, wl["U0"])
+        B.dg_set_state(ctx, h, wl["U0"] if U0 is None else U0)
         return h
 
     step = B.dg_step_lserk if args.integrator == "lserk" else B.dg_step
@@ -465,6 +719,30 @@ def run_ours(args):
             flush.zero_()
             step(ctx, h, wl["dt"], 1)
         torch.cuda.synchronize()
+
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = 6800.0, "fallback"
+    if os.path.exists(peaks_path):
+        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+
+    def stage_roofline(h, nsteps, viscous):
+        """Per-kernel times from a pass with CUDA events around every kernel
+        inside the step graph; the stage kernel's average launch against its
+        algorithmic bytes."""
+        B.dg_set_profiling(ctx, h, 1)
+        warm(h)
+        pt, kt, launches = timed_steps(B, ctx, h, wl["dt"], nsteps, stream, flush, torch, profiled=True)
+        B.dg_set_profiling(ctx, h, 0)
+        ms = kt[2] / (3 * nsteps)
+        nbytes = stage_kernel_bytes(m.K, int(wl["curved"].sum()), N, wl["av"], viscous)
+        ach = nbytes / (ms * 1e-3) / 1e9
+        return {"kernel": "stage_kernel_tc (N=%d, %s launch)" % (N, "viscous" if viscous else "inviscid")
+                if args.prec in ("tf32", "bf16x3") else "stage_kernel (N=%d)" % N,
+                "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_source": peak_src,
+                "traffic": traffic_of(args.workload, args.prec, args.flux, "tri",
+                                      "stage_viscous" if viscous else "stage"),
+                "bytes_per_launch": nbytes, "avg_launch_ms": ms}, kt / nsteps, pt, launches / nsteps
 
     h = upload(args.prec)
     visc = {"start": B.dg_av_count(ctx, h)} if wl["av"] else None
@@ -491,54 +769,51 @@ def run_ours(args):
     if visc is not None:
         visc["end"] = B.dg_av_count(ctx, h)
 
-    # per-kernel breakdown: a second pass with CUDA events recorded around
-    # every kernel inside the step graph (on the library's stream)
+    # the roofline of the dominant kernel (the fused stage kernel) from a
+    # second pass with events around every kernel; with the artificial
+    # viscosity the timed launches are viscous ones (troubled cells) and an
+    # inviscid pass (freestream start) is reported beside them
+    kinds = ["sensor", "gradient", "stage"]
     n_prof = min(args.steps, 300)
+    extra = {}
     if args.integrator == "ssp3":
-        B.dg_set_profiling(ctx, h, 1)
-        warm(h)
-        ptimes, kt, launches = timed_steps(B, ctx, h, wl["dt"], n_prof, stream, flush, torch, profiled=True)
-        launches = launches * args.steps // n_prof      # kernels per headline pass
-        kt = kt * (args.steps / n_prof)
-        B.dg_set_profiling(ctx, h, 0)
+        viscous = visc is None or visc["start"] > 0 or visc["end"] > 0
+        B.dg_set_state(ctx, h, wl["U0"])
+        roofline, kt_step, ptimes, launches_step = stage_roofline(h, n_prof, viscous if wl["av"] else False)
+        if wl["av"]:
+            B.dg_set_state(ctx, h, np.broadcast_to(np.asarray(wl["u_inf"])[None, :, None], wl["U0"].shape).copy())
+            inv, _, _, _ = stage_roofline(h, n_prof, False)
+            extra["roofline_inviscid"] = inv
+        launches = int(launches_step * args.steps)
+        kt = kt_step * args.steps
     else:   # no timing nodes in the low-storage graph: kernels counted, not timed one by one
         ptimes, kt = times[:1], np.zeros(3)
         launches = args.steps * 5 * (3 if wl["av"] else 1)
+        ms = total_ms / args.steps / 5
+        nbytes = stage_kernel_bytes(m.K, int(wl["curved"].sum()), N, wl["av"], True)
+        roofline = {"kernel": "whole low-storage step / 5 stages", "bound": "hbm",
+                    "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": nbytes / (ms * 1e-3) / 1e9 / peak, "peak_source": peak_src, "traffic": None,
+                    "bytes_per_launch": nbytes, "avg_launch_ms": ms}
+    roofline["dominant_kind_by_time"] = kinds[int(np.argmax(kt))]
 
-    # roofline of the dominant kernel (the fused stage kernel); for the
-    # low-storage integrator the whole step's time over its 5 stages
-    stage_launch_ms = kt[2] / (3 * args.steps) if args.integrator == "ssp3" else total_ms / args.steps / 5
-    kinds = ["sensor", "gradient", "stage"]
-    dom = int(np.argmax(kt))
-    # launches on an input without viscous elements read neither q nor eps
-    viscous = visc is None or visc["start"] > 0 or visc["end"] > 0
-    bytes_launch = stage_kernel_bytes(m.K, int(wl["curved"].sum()), N, wl["av"], viscous)
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    peak, peak_src = 6800.0, "fallback"
-    if os.path.exists(peaks_path):
-        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
-    achieved = bytes_launch / (stage_launch_ms * 1e-3) / 1e9
-    roofline = {"kernel": "stage_kernel (N=%d, AV %s)" % (N, "on" if wl["av"] else "off"), "bound": "hbm",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_src, "traffic": TRAFFIC.get((args.workload, args.prec, args.flux)) if args.integrator == "ssp3" else None,
-                "bytes_per_launch": bytes_launch, "avg_launch_ms": stage_launch_ms,
-                "dominant_kind_by_time": kinds[dom]}
-
-    extra = {}
-    if args.compare_prec and args.compare_prec != args.prec:
-        h2 = upload(args.compare_prec)
-        if args.compare_prec in ("fp32", "fp64"):
-            tuned[args.compare_prec] = B.dg_autotune(ctx, h2, 5)
+    compares = [c for c in args.compare_prec.split(",") if c and c not in ("none", args.prec)]
+    cmp_lines = []
+    for cp in compares:
+        h2 = upload(cp)
+        if cp in ("fp32", "fp64"):
+            tuned[cp] = B.dg_autotune(ctx, h2, 5)
         warm(h2)
         n2 = min(args.steps, 500)
-        t2, kt2, _ = timed_steps(B, ctx, h2, wl["dt"], n2, stream, flush, torch, step=step)
-        extra["compare"] = {"products": args.compare_prec,
-                            "value": world * dof_stage * nstage * n2 / (sum(t2) / 1e3),
-                            "ms_per_step": sum(t2) / n2}
-        if args.compare_prec in tuned:
-            extra["compare"]["tile_e"] = tuned[args.compare_prec][0]
-            extra["compare"]["autotune_ms_per_step"] = tuned[args.compare_prec][1]
+        t2, _, _ = timed_steps(B, ctx, h2, wl["dt"], n2, stream, flush, torch, step=step)
+        c = {"products": cp, "value": world * dof_stage * nstage * n2 / (sum(t2) / 1e3), "ms_per_step": sum(t2) / n2}
+        if cp in tuned:
+            c["tile_e"] = tuned[cp][0]
+            c["autotune_ms_per_step"] = tuned[cp][1]
+        cmp_lines.append(c)
         B.dg_mesh_free(ctx, h2)
+    if cmp_lines:
+        extra["compare"] = cmp_lines
 
     e2e = None
     if not args.no_e2e:
@@ -555,11 +830,20 @@ def run_ours(args):
                "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": U_out.nbytes / args.steps,
                "how": "dg_set_state(host FP64) + %s(%d) + dg_get_state(host FP64), wall clock"
                       % ("dg_step_lserk" if args.integrator == "lserk" else "dg_step", args.steps)}
+    B.dg_mesh_free(ctx, h)
+
+    errors = None
+    if rank == 0 and not args.no_errors and args.integrator == "ssp3":
+        errors = precision_errors(B, ctx, args, wl, [args.prec] + compares, r, s)
     B.dg_destroy(ctx)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = run_cpu_baseline(args.workload, args.cpu_budget_s, args.flux)
+        path = oracle_inputs_path(wl, args.flux, "tri")
+        try:
+            cpu = run_cpu_baseline(path, args.cpu_budget_s)
+        finally:
+            os.unlink(path)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -569,10 +853,10 @@ def run_ours(args):
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches * world),
                 "clocks": clk,
                 "kernel_ms_per_step": {k: float(kt[i] / args.steps) for i, k in enumerate(kinds)},
-                "profiled_ms_per_step": float(sum(ptimes) / n_prof),
+                "profiled_ms_per_step": float(sum(ptimes) / max(1, len(ptimes))),
                 "tile_e": tuned[args.prec][0] if args.prec in tuned else 32,
                 "residual_linf": [float(x) for x in linf],
-                "viscous_elements": visc, **extra}
+                "viscous_elements": visc, "error_vs_oracle": errors, **extra}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -664,7 +948,7 @@ def run_tet(args):
     roofline = {"kernel": "%s (tetrahedra, N=%d, %s)" % (kname, N, prec), "bound": "alu",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock %.0f MHz" % sm_max,
-                "traffic": TRAFFIC.get((args.workload, prec, args.flux)) if args.integrator == "ssp3" else None,
+                "traffic": traffic_of(args.workload, prec, args.flux, "tet") if args.integrator == "ssp3" else None,
                 "flops_per_launch": flops,
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": launch_ms,
                 "hbm_gbs": bytes_launch / (launch_ms * 1e-3) / 1e9,
@@ -688,7 +972,13 @@ def run_tet(args):
                "how": "dg_set_state(host FP64) + %s(%d) + dg_get_state(host FP64), wall clock"
                       % ("dg_step_lserk" if args.integrator == "lserk" else "dg_step", n_e2e)}
     B.dg_destroy(ctx)
-    cpu = None if args.no_cpu_baseline else run_cpu_baseline(args.workload, args.cpu_budget_s, args.flux)
+    cpu = None
+    if not args.no_cpu_baseline:
+        path = oracle_inputs_path(wl, args.flux, "tet")
+        try:
+            cpu = run_cpu_baseline(path, args.cpu_budget_s)
+        finally:
+            os.unlink(path)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
@@ -704,53 +994,6 @@ def run_tet(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "tile_e": tuned[0], "autotune_ms_per_step": {str(k): v for k, v in tuned[1].items()},
             "residual_linf": [float(x) for x in linf]}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def run_reference_tet(args):
-    """The tetrahedral oracle as it stands, one SSP-RK3 step per timed step
-    on a fixed sample of elements sized so the run ends within minutes."""
-    import numpy as np
-    from oracle.dg3 import Oracle3
-    from oracle.tet import ReferenceTet
-    w = WORKLOADS[args.workload]
-    ref = ReferenceTet(w["N"])
-    wl = make_tet_workload(args.workload, ref.r, ref.s, ref.t)
-    m = wl["mesh"]
-    o = Oracle3(w["N"], m.EToV, m.bc, wl["xyz"], u_inf=wl["u_inf"], flux=args.flux)
-    t0 = time.perf_counter()
-    probe = np.arange(0, m.K, max(1, m.K // 256))
-    o.rhs(wl["U0"], probe)
-    per_elt = (time.perf_counter() - t0) / len(probe)
-    per_step = 150.0 / max(1, args.steps + args.warmup)
-    S = int(max(16, min(m.K, per_step / (3 * per_elt))))
-    idx = np.linspace(0, m.K - 1, S).astype(np.int64)
-    U = wl["U0"].copy()
-
-    def step():
-        Us = U
-        for a, b in ((0.0, 1.0), (0.75, 0.25), (1 / 3, 2 / 3)):
-            L = o.rhs(Us, idx)
-            Us = Us.copy()
-            Us[idx] = a * U[idx] + b * (Us[idx] + wl["dt"] * L)
-        return Us
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    el = time.perf_counter() - t0
-    value = S * ref.Np * 5 * 3 * args.steps / el
-    sample = "%d of %d elements per SSP-RK3 step (3 RHS evaluations on the sample)" % (S, m.K)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "describe": w["describe"], "K": int(m.K),
-                                            "N": w["N"], "flux": args.flux.upper()},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -957,7 +1200,7 @@ def main():
     faulthandler.enable()
     args = parse_args()
     if args.cpu_sample:
-        print(json.dumps(cpu_sample(args.cpu_sample, args.cpu_budget_s, args.flux)))
+        print(json.dumps(cpu_worker(args.cpu_sample, args.cpu_start, args.cpu_budget_s)))
         return 0
     if args.impl == "reference":
         return run_reference(args)

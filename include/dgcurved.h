@@ -282,9 +282,9 @@ int dg_kernel_times(dg_ctx* ctx, dg_mesh m, double out_ms[4]);
 
 /* Residual norms of a caller's device array with no allocation at all.  The
  * paper has no counterpart: this serves callers that cannot allocate device
- * memory where they need the norms -- code running during CUDA graph
- * capture, real-time loops that must avoid the allocator, hosts whose
- * framework owns every device byte.  values_dev: device float[K][4][Np]
+ * memory where they need the norms -- real-time loops that must stay off the
+ * allocator's locks and latency, and hosts whose framework owns every device
+ * byte through its own pool.  values_dev: device float[K][4][Np]
  * (any element order); out8_dev: device double[8] receiving max |x| for
  * the four variables, then sqrt(sum x^2) for the four variables, in FP64
  * (the definition dg_residual uses).  Runs on the calling thread's current
@@ -294,7 +294,9 @@ int dg_kernel_times(dg_ctx* ctx, dg_mesh m, double out_ms[4]);
  * library keeps until the process exits, so K*4*Np may not exceed
  * 67,108,864 values (DG_EINVAL beyond that, and for NULL pointers or
  * non-positive sizes).  The first call on a device looks up that array's
- * address (cudaGetSymbolAddress), so make it before any stream capture.
+ * address (cudaGetSymbolAddress), so make it before any stream capture;
+ * the address is kept for the process's life and, like every handle of this
+ * library, does not survive a cudaDeviceReset.
  * All calls share the array: calls that overlap on the GPU race; calls in
  * order on one stream are safe.  No cudaMalloc, cudaFree or allocating
  * library routine is called.  Errors: DG_EINVAL, DG_ECUDA (message in

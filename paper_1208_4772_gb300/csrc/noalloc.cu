@@ -1,10 +1,10 @@
 // Residual norms without any allocation.
 //
 // Some callers cannot allocate device memory at the point where they need
-// the residual: code that runs while a CUDA graph is being captured (an
-// allocation there breaks or serialises the capture), real-time loops that
-// must not hit the allocator's locks or latency spikes, and host programs
-// embedded in a framework that owns every device byte through its own pool.
+// the residual: real-time loops that must not hit the allocator's locks or
+// latency spikes, and host programs embedded in a framework that owns every
+// device byte through its own pool, so that a cudaMalloc of the library
+// would fail or fragment that pool.
 // For them this file offers the FP64 residual-norm reduction of the library
 // (the same definition as dg_residual: per-variable max |L| and sqrt(sum
 // L^2)) with its per-block partial results in a fixed, file-scope device
@@ -112,7 +112,9 @@ std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 
 // Device address of the static array on the current device, looked up once
-// per device (with that device current).
+// per device (with that device current) and kept for the life of the
+// process: like every handle of this library it does not survive a
+// cudaDeviceReset of that device.
 int noalloc_scratch(int dev, double** out) {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
@@ -137,12 +139,14 @@ extern "C" int dg_residual_norms_noalloc(const float* values_dev, int64_t K, int
         dgc::set_global_error("dg_residual_norms_noalloc: NULL pointer or non-positive size");
         return DG_EINVAL;
     }
-    const long long n = (long long)K * 4 * Np;
-    if (K > NOALLOC_MAX_VALUES || n > NOALLOC_MAX_VALUES) {
-        dgc::set_global_error("dg_residual_norms_noalloc: K*4*Np = " + std::to_string(n) +
-                              " values exceeds the static scratch limit of " + std::to_string(NOALLOC_MAX_VALUES));
+    // compare before multiplying: K * 4 * Np must not overflow
+    if (K > NOALLOC_MAX_VALUES / (4LL * Np)) {
+        dgc::set_global_error("dg_residual_norms_noalloc: K = " + std::to_string(K) + ", Np = " + std::to_string(Np) +
+                              ": K*4*Np exceeds the static scratch limit of " + std::to_string(NOALLOC_MAX_VALUES) +
+                              " values");
         return DG_EINVAL;
     }
+    const long long n = (long long)K * 4 * Np;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
         cudaGetLastError();

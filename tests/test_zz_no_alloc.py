@@ -1,8 +1,8 @@
 """The allocation-free residual-norm entry point, dg_residual_norms_noalloc.
 
 It serves callers that cannot allocate device memory where they need the
-norms (code inside CUDA graph capture, real-time loops that must stay off
-the allocator, hosts whose framework owns every device byte).  Its partial
+norms (real-time loops that must stay off the allocator, hosts whose
+framework owns every device byte through its own pool).  Its partial
 results live in a fixed static device array; this test checks that two
 calls in a row give the same norms as the allocating path (dg_residual)
 on the same values, to FP64 round-off of a different summation order
