@@ -1462,4 +1462,20 @@ int dg_kernel_times(dg_ctx* ctx, dg_mesh h, double out_ms[4]) {
 
 const char* dg_last_error(dg_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
 
+#ifdef DGC_PHASE_CLOCKS
+// Profiling builds only: the per-phase cycle counts of the degree-N
+// tensor-core tile body (see DGC_PHASE_CLOCKS in tc_kernels.cuh), reset after
+// reading when reset != 0.
+int dg_debug_tc_phase_cycles(int N, unsigned long long out16[16], int reset) {
+    switch (N) {
+        case 2: return dgc::tc_phase_cycles<2>(out16, reset != 0);
+        case 3: return dgc::tc_phase_cycles<3>(out16, reset != 0);
+        case 4: return dgc::tc_phase_cycles<4>(out16, reset != 0);
+        case 5: return dgc::tc_phase_cycles<5>(out16, reset != 0);
+        case 6: return dgc::tc_phase_cycles<6>(out16, reset != 0);
+    }
+    return DG_EINVAL;
+}
+#endif
+
 }  // extern "C"

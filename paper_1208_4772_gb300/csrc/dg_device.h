@@ -118,6 +118,9 @@ template <int N>
 int launch_stage_tc(const StageArgs<float>& a, int av, int prec, const unsigned char* ops_tc, int* err,
                     cudaStream_t st);
 template <int N> int prepare_tc();
+#ifdef DGC_PHASE_CLOCKS
+template <int N> int tc_phase_cycles(unsigned long long* out16, bool reset);
+#endif
 template <int N>
 int launch_grad_tc(const StageArgs<float>& a, float* q_out, int prec, const unsigned char* ops_tc, int* err,
                    cudaStream_t st);

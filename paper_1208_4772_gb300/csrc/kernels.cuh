@@ -150,6 +150,25 @@ __device__ __forceinline__ void copy_to_smem(Real* dst, const Real* src, int n) 
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
+// The threads that run one CUDA-core tile: the whole CTA (barrier 0), or a
+// warp-aligned group of a larger CTA with a named barrier of its own.
+struct TileThreads {
+    int tid, n;
+    uint32_t bar;
+    __device__ __forceinline__ void sync() const {
+        if (bar == 0)
+            __syncthreads();
+        else
+            asm volatile("bar.sync %0, %1;" :: "r"(bar), "r"(n) : "memory");
+    }
+};
+__device__ __forceinline__ TileThreads cta_threads() { return TileThreads{(int)threadIdx.x, (int)blockDim.x, 0u}; }
+
+template <typename Real>
+__device__ __forceinline__ void copy_to_smem(const TileThreads& th, Real* dst, const Real* src, int n) {
+    for (int i = th.tid; i < n; i += th.n) dst[i] = src[i];
+}
+
 // Affine geometry of element k into g[16]: J r_x, J r_y, J s_x, J s_y, 1/J,
 // then per face (n_x, n_y, sJ).  From x_r, x_s, y_r, y_s of the affine map:
 // J r_x = y_s, J r_y = -x_s, J s_x = -y_r, J s_y = x_r; face tangents
@@ -272,10 +291,11 @@ __device__ __forceinline__ Real stage_value(const StageArgs<Real>& p, long long 
 // Stage kernel: L(Us) and the SSP-RK combination (or L alone).
 // ---------------------------------------------------------------------------
 template <int N, typename Real, bool AV>
-__device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileRange& t, unsigned char* smem_raw) {
+__device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileRange& t, unsigned char* smem_raw,
+                                           const TileThreads& th = cta_threads(), int cap_e = 0) {
     using T = Tile<N, Real>;
     constexpr int NP = T::NP, NQ = T::NQ, NG = T::NG, NF = T::NF;
-    const int E = T::cap(p.tile_e);   // capacity of this launch's layout
+    const int E = cap_e > 0 ? cap_e : T::cap(p.tile_e);   // capacity of this launch's layout
     constexpr OpsLayout L = ops_layout(N);
     Real* sIcubT = reinterpret_cast<Real*>(smem_raw);
     Real* sXrT = sIcubT + NP * NQ;
@@ -291,28 +311,28 @@ __device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileR
     Real* sEps = sQ + E * 8 * NP; // AV only
 
     const Real* ops = p.ops;
-    copy_to_smem(sIcubT, ops + L.icub, NP * NQ);
-    copy_to_smem(sXrT, ops + (t.curved ? L.drt : L.mrt), NQ * NP);
-    copy_to_smem(sXsT, ops + (t.curved ? L.dst : L.mst), NQ * NP);
-    copy_to_smem(sIgT, ops + L.igt, NP * NF);
-    copy_to_smem(sXLT, ops + (t.curved ? L.lt : L.mlt), NF * NP);
+    copy_to_smem(th, sIcubT, ops + L.icub, NP * NQ);
+    copy_to_smem(th, sXrT, ops + (t.curved ? L.drt : L.mrt), NQ * NP);
+    copy_to_smem(th, sXsT, ops + (t.curved ? L.dst : L.mst), NQ * NP);
+    copy_to_smem(th, sIgT, ops + L.igt, NP * NF);
+    copy_to_smem(th, sXLT, ops + (t.curved ? L.lt : L.mlt), NF * NP);
     const int nval = t.ne * 4 * NP;
     const Real* Us_tile = p.Us + t.e0 * 4 * NP;
-    for (int i = threadIdx.x; i < nval; i += blockDim.x) sU[i] = Us_tile[i];
+    for (int i = th.tid; i < nval; i += th.n) sU[i] = Us_tile[i];
     if (!t.curved)
-        for (int e = threadIdx.x; e < t.ne; e += blockDim.x) affine_geometry(p.geoA + (t.e0 + e) * 4, sGeo + e * 16);
+        for (int e = th.tid; e < t.ne; e += th.n) affine_geometry(p.geoA + (t.e0 + e) * 4, sGeo + e * 16);
     if constexpr (AV) {
         const Real* q_tile = p.q + t.e0 * 8 * NP;
-        for (int i = threadIdx.x; i < t.ne * 8 * NP; i += blockDim.x) sQ[i] = q_tile[i];
-        for (int e = threadIdx.x; e < t.ne; e += blockDim.x) sEps[e] = sqrt(p.eps[t.e0 + e]);
+        for (int i = th.tid; i < t.ne * 8 * NP; i += th.n) sQ[i] = q_tile[i];
+        for (int e = th.tid; e < t.ne; e += th.n) sEps[e] = sqrt(p.eps[t.e0 + e]);
     }
-    __syncthreads();
+    th.sync();
 
     const Real gamma = p.gamma;
     const Real* geoC = p.geoC + (t.curved ? (t.e0 - p.Kaff) * curved_stride(N) : 0);
 
     // phase A: cubature nodes
-    for (int it = threadIdx.x; it < t.ne * NQ; it += blockDim.x) {
+    for (int it = th.tid; it < t.ne * NQ; it += th.n) {
         const int e = it / NQ, qn = it - e * NQ;
         Real Uc[4] = {0, 0, 0, 0};
         const Real* u = sU + e * 4 * NP;
@@ -359,7 +379,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileR
     }
 
     // phase C: face points
-    for (int it = threadIdx.x; it < t.ne * NF; it += blockDim.x) {
+    for (int it = th.tid; it < t.ne * NF; it += th.n) {
         const int e = it / NF, fg = it - e * NF;
         const int f = fg / NG, g = fg - f * NG;
         const long long k = t.e0 + e;
@@ -432,11 +452,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileR
 #pragma unroll
         for (int v = 0; v < 4; ++v) fs[v * NF + fg] = Fn[v] * sJ;
     }
-    __syncthreads();
+    th.sync();
 
     // phase D: products, M^-1, stage combination
     const long long base = t.e0 * 4 * NP;
-    for (int it = threadIdx.x; it < nval; it += blockDim.x) {
+    for (int it = th.tid; it < nval; it += th.n) {
         const int e = it / (4 * NP), r = it - e * 4 * NP, v = r / NP, i = r - v * NP;
         const Real* fr = sF + e * 8 * NQ + v * NQ;
         const Real* fs = sF + e * 8 * NQ + (4 + v) * NQ;
@@ -454,8 +474,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileR
         }
     }
     if (t.curved) {
-        __syncthreads();
-        for (int it = threadIdx.x; it < nval; it += blockDim.x) {
+        th.sync();
+        for (int it = th.tid; it < nval; it += th.n) {
             const int e = it / (4 * NP), r = it - e * 4 * NP, v = r / NP, i = r - v * NP;
             const Real* mi = geoC + (long long)e * curved_stride(N) + 5 * NQ + 3 * NF;
             const Real* rr = sR + (e * 4 + v) * NP;
@@ -466,10 +486,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileR
     }
     if constexpr (AV) {
         if (p.eps_next != nullptr && !p.rhs_only) {   // eps of the new state, one warp per element
-            __syncthreads();                            // the tile's new state is written
-            for (int e = threadIdx.x >> 5; e < t.ne; e += blockDim.x >> 5) {
+            th.sync();                            // the tile's new state is written
+            for (int e = th.tid >> 5; e < t.ne; e += th.n >> 5) {
                 const Real eps = element_sensor_warp<N, Real>(p, t.e0 + e, p.Uout + (t.e0 + e) * 4 * NP);
-                if ((threadIdx.x & 31) == 0) {
+                if ((th.tid & 31) == 0) {
                     p.eps_next[t.e0 + e] = eps;
                     if (p.visc && eps > Real(0)) atomicAdd(p.visc, 1);
                 }
@@ -484,6 +504,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<Real>& p, const TileR
 template <int N, typename Real, bool AV>
 __device__ __noinline__ void stage_tile_call(const StageArgs<Real>& p, const TileRange& t, unsigned char* smem) {
     stage_tile<N, Real, AV>(p, t, smem);
+}
+template <int N, typename Real, bool AV>
+__device__ __noinline__ void stage_tile_call(const StageArgs<Real>& p, const TileRange& t, unsigned char* smem,
+                                             const TileThreads& th, int cap_e) {
+    stage_tile<N, Real, AV>(p, t, smem, th, cap_e);
 }
 
 template <int N, typename Real, bool AV>

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(THREADS, 2)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
+    const TcGroup grp{tid, 0u, 0u};   // one tile at a time, the whole CTA
     TcPhase ph;
     int loaded = 0;   // degree whose operators are in shared memory (0: none)
     if (tid == 0) s_tile = atomicAdd(counter, 1);
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(THREADS, 2)
     case n:                                                                                                 \
         if constexpr (n >= NLO && n <= NHI)                                                                 \
             stage_tile_tc<n, false, PREC>(p, b.e0, b.ne, smem_bt, tmem, ph, err, false, claim, &s_tile, 0, 0, \
-                                          bars);                                                            \
+                                          bars, grp);                                                       \
         break;
                 DGC_BT_TILE(2) DGC_BT_TILE(3) DGC_BT_TILE(4) DGC_BT_TILE(5) DGC_BT_TILE(6)
 #undef DGC_BT_TILE

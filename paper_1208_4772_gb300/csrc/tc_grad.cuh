@@ -86,7 +86,7 @@ __device__ __forceinline__ bool grad_tile_tc(const StageArgs<float>& p, float* q
     if (!tc::mbar_wait(&bars[1], nld & 1)) atomicOr(err, 8);
     ++nld;
     if (tid < 32)
-        tile_info(e0, ne, true, sTr + TS::G, reinterpret_cast<const int4*>(sTr + TS::C), sTr + TS::E, sGeo, sNb, sSe,
+        tile_info(threadIdx.x, e0, ne, true, sTr + TS::G, reinterpret_cast<const int4*>(sTr + TS::C), sTr + TS::E, sGeo, sNb, sSe,
                   sList, sFL);
     const bool live = e < ne;
     {   // both halves: the row's mean, then half h writes K values [h NPK/2, (h+1) NPK/2)

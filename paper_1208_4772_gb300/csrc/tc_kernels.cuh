@@ -145,7 +145,8 @@ struct TcSmem {
     static constexpr int sLIST = sNB + 32 * 16;                              // out-of-tile faces: n, then (e,f)
     static constexpr int sFL = sLIST + 100 * 4;                              // faces owned by the tile: n, then (e,f)
     static constexpr int sND = sFL + 100 * 4;                                // [32][2] sensor sums of the new state
-    static constexpr int TOTAL = sND + 64 * 4;
+    static constexpr int sFC = sND + 64 * 4;                                 // [32][8] contravariant mean flux
+    static constexpr int TOTAL = sFC + 32 * 8 * 4;
     static_assert(TOTAL + 256 <= 232448, "tensor-core tile exceeds the shared-memory limit");
     static_assert(D::CA <= NBUF, "viscous chunks are written at tile start, one per A2 buffer");
     static_assert(NBB >= 32 && (REC * 4) % 16 == 0 && (32 * 4 * D::NP * 4) % 16 == 0, "bulk-copy staging layout");
@@ -159,6 +160,29 @@ struct TcSmem {
 template <int N, bool AV>
 constexpr size_t tc_smem_bytes() {
     return TcSmem<N, AV>::TOTAL;
+}
+
+// The contravariant Euler flux of one point, less that of the element-mean
+// state: with the element's metric g = (J r_x, J r_y, J s_x, J s_y),
+//   Fr = g0 F + g1 G - fr,   Fs = g2 F + g3 G - fs,
+// formed from the contravariant momenta m_r = g0 m_x + g1 m_y (and m_s):
+//   g0 F + g1 G = (m_r, m_x u_r + g0 p, m_y u_r + g1 p, (E + p) u_r),
+// u_r = m_r / rho; fr, fs are the same quantities of the mean state.
+__device__ __forceinline__ void contra_flux_dev(const float U[4], float gamma, const float g[4], const float fr[4],
+                                                const float fs[4], float Fr[4], float Fs[4]) {
+    const float ir = recip(U[0]);
+    const float mr = g[0] * U[1] + g[1] * U[2], ms = g[2] * U[1] + g[3] * U[2];
+    const float ur = mr * ir, us = ms * ir;
+    const float p = (gamma - 1.f) * (U[3] - 0.5f * (U[1] * U[1] + U[2] * U[2]) * ir);
+    const float H = U[3] + p;
+    Fr[0] = mr - fr[0];
+    Fr[1] = fmaf(U[1], ur, fmaf(g[0], p, -fr[1]));
+    Fr[2] = fmaf(U[2], ur, fmaf(g[1], p, -fr[2]));
+    Fr[3] = fmaf(H, ur, -fr[3]);
+    Fs[0] = ms - fs[0];
+    Fs[1] = fmaf(U[1], us, fmaf(g[2], p, -fs[1]));
+    Fs[2] = fmaf(U[2], us, fmaf(g[3], p, -fs[2]));
+    Fs[3] = fmaf(H, us, -fs[3]);
 }
 
 // Writes 8 consecutive K values (k0 multiple of 8) of one row of an A
@@ -220,10 +244,9 @@ __device__ __forceinline__ void issue_mma(uint32_t d_tmem, const unsigned char* 
 // outside the tile, sFL the faces whose flux the tile computes -- boundary
 // and out-of-tile faces by the element itself, an in-tile pair by its
 // lower-numbered element, so that each face point is computed once.
-__device__ __forceinline__ void tile_info(long long e0, int ne, bool av, const float* stG, const int4* stC,
+__device__ __forceinline__ void tile_info(int tid, long long e0, int ne, bool av, const float* stG, const int4* stC,
                                           const float* stE, float* sGeo, int4* sNb, float* sSe, int* sList,
                                           int* sFL) {
-    const int tid = threadIdx.x;
     int mout = 0, mown = 0;   // bit f: face f is out of tile / computed here
     if (tid < ne) {
         const int4 c = stC[tid];
@@ -264,6 +287,57 @@ __device__ __forceinline__ void tile_info(long long e0, int ne, bool av, const f
         sFL[0] = incl >> 16;
     }
 }
+
+// The 256 threads (8 warps) that work on one tile: a whole CTA, or one of
+// the tile pipelines of a larger CTA that share its operator tables.  tid:
+// index within the group; bar: the group's named barrier (0 in a CTA of 256
+// threads); toff: byte offset of the group's per-tile shared-memory regions.
+struct TcGroup {
+    int tid;
+    uint32_t bar;
+    uint32_t toff;
+    __device__ __forceinline__ void sync() const {
+        asm volatile("bar.sync %0, %1;" :: "r"(bar), "n"(THREADS) : "memory");
+    }
+};
+
+// Optional per-phase cycle counts of the tensor-core tile body (a build with
+// DGC_PHASE_CLOCKS): thread 0 of each group adds the clock64 cycles of every
+// phase of every tile to g_tc_phase_cycles (phase k ends at mark k: 0 tile
+// inputs and G1 operand, 1 G1 and neighbour records, 2 neighbour traces, 3
+// own traces, 4 face fluxes, 5 face chunk, 6 cubature chunks, 7 epilogue);
+// slot 8 counts the tiles; the persistent kernel adds, per pipeline, the
+// cycles of its curved tiles (9) and their count (10), of the prologue up to
+// the first claim (11), of its lifetime (12) and the number of pipelines (13).
+#ifdef DGC_PHASE_CLOCKS
+static __device__ unsigned long long g_tc_phase_cycles[16];
+template <int N>
+int tc_phase_cycles(unsigned long long* out16, bool reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(out16, g_tc_phase_cycles, 16 * sizeof(unsigned long long));
+    if (e == cudaSuccess && reset) {
+        const unsigned long long z[16] = {};
+        e = cudaMemcpyToSymbol(g_tc_phase_cycles, z, sizeof(z));
+    }
+    return (int)e;
+}
+#define DGC_PHASE_BEGIN() long long dgc_t0 = clock64()
+#define DGC_PHASE_MARK(k)                                                     \
+    do {                                                                      \
+        if (g.tid == 0) {                                                     \
+            const long long dgc_t1 = clock64();                               \
+            atomicAdd(&g_tc_phase_cycles[k], (unsigned long long)(dgc_t1 - dgc_t0)); \
+            if ((k) == 7) atomicAdd(&g_tc_phase_cycles[8], 1ull);             \
+            dgc_t0 = dgc_t1;                                                  \
+        }                                                                     \
+    } while (0)
+#else
+#define DGC_PHASE_BEGIN() \
+    do {                  \
+    } while (0)
+#define DGC_PHASE_MARK(k) \
+    do {                  \
+    } while (0)
+#endif
 
 // Tile body: one tile of up to 32 affine elements.  The operator tables,
 // mbarriers and TMEM are set up once per CTA by the persistent kernel;
@@ -307,34 +381,35 @@ template <int N, bool AV, int PREC, bool SENSE = AV>
 __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long long e0, int ne, unsigned char* smem,
                                               uint32_t tmem, TcPhase& ph, int* err, bool rows_ready,
                                               int claim, int* next_tile, long long nCur, long long nAff,
-                                              uint64_t* bars) {
+                                              uint64_t* bars, const TcGroup& g) {
     using D = TcDims<N>;
     using S = TcSmem<N, AV, SENSE>;
     constexpr int NP = D::NP, NQ = D::NQ, NG = D::NG, NF = D::NF, NPK = D::NPK, FOFF = D::FOFF;
     constexpr int N1 = D::N1, NFP = D::NFP, N2 = D::N2, NFS = D::NFS, CF = D::CF, CQ = D::CQ, CA = D::CA;
     constexpr int B2C = TcLayout<N>::B2_CHUNK;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = g.tid, warp = tid >> 5, lane = tid & 31;
     const int row = (warp & 3) * 32 + lane;     // TMEM lane = (element, variable) row
     const int half = warp >> 2;                 // which half of the columns this thread loads
     const int e = row >> 2, v = row & 3;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     const uint32_t tD1 = tmem, tD1q = tmem + N1, tD2 = tmem + N1 + (AV ? 2 * NFP : 0);
 
-    float* sMean = reinterpret_cast<float*>(smem + S::sMEAN);
-    float* sGeo = reinterpret_cast<float*>(smem + S::sGEO);
-    float* sFb = reinterpret_cast<float*>(smem + S::sFB);
-    float* sSe = reinterpret_cast<float*>(smem + S::sSE);
-    int4* sNb = reinterpret_cast<int4*>(smem + S::sNB);
-    float* sTr = reinterpret_cast<float*>(smem + S::sTR);
+    float* sMean = reinterpret_cast<float*>(smem + g.toff + S::sMEAN);
+    float* sGeo = reinterpret_cast<float*>(smem + g.toff + S::sGEO);
+    float* sFb = reinterpret_cast<float*>(smem + g.toff + S::sFB);
+    float* sSe = reinterpret_cast<float*>(smem + g.toff + S::sSE);
+    int4* sNb = reinterpret_cast<int4*>(smem + g.toff + S::sNB);
+    float* sTr = reinterpret_cast<float*>(smem + g.toff + S::sTR);
     float* sQn = sTr + S::TR_FLOATS;            // AV: sqrt(eps) q.n at own face points
     const float* sIgF = reinterpret_cast<const float*>(smem + S::sIGF);
-    unsigned char* A1 = smem + S::sA1;
-    int* sList = reinterpret_cast<int*>(smem + S::sLIST);
-    int* sFL = reinterpret_cast<int*>(smem + S::sFL);
-    float* sND = reinterpret_cast<float*>(smem + S::sND);
+    unsigned char* A1 = smem + g.toff + S::sA1;
+    int* sList = reinterpret_cast<int*>(smem + g.toff + S::sLIST);
+    int* sFL = reinterpret_cast<int*>(smem + g.toff + S::sFL);
+    float* sND = reinterpret_cast<float*>(smem + g.toff + S::sND);
+    float* sFC = reinterpret_cast<float*>(smem + g.toff + S::sFC);
 
     // G2 runs as a sequence of K chunks; chunk number s uses A2 buffer s % 2.
-    auto a2_buf = [&](int s) { return smem + S::sA2 + (s & 1) * S::A2_BYTES; };
+    auto a2_buf = [&](int s) { return smem + g.toff + S::sA2 + (s & 1) * S::A2_BYTES; };
     auto wait_buf = [&](int b) {   // every product issued from buffer b has completed
         uint32_t& w = b ? ph.w1 : ph.w0;
         const uint32_t c = b ? ph.c1 : ph.c0;
@@ -348,6 +423,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         tc::mma_commit(&bars[s & 1]);
     };
     int seq = 0;
+    DGC_PHASE_BEGIN();
 
     // ---------------- tile inputs: the U (and q) rows of the tile by TMA bulk
     // copies into the trace region; per-element data and face lists by warp 0
@@ -358,7 +434,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     if (!tc::mbar_wait(&bars[3], ph.ld & 1)) atomicOr(err, 8);
     ph.ld++;
     if (tid < 32)
-        tile_info(e0, ne, AV, sTr + TS::G, reinterpret_cast<const int4*>(sTr + TS::C), sTr + TS::E, sGeo, sNb, sSe,
+        tile_info(tid, e0, ne, AV, sTr + TS::G, reinterpret_cast<const int4*>(sTr + TS::C), sTr + TS::E, sGeo, sNb, sSe,
                   sList, sFL);
     if (half == 0) {
         float u[NP];
@@ -429,7 +505,8 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
-    __syncthreads();
+    g.sync();
+    DGC_PHASE_MARK(0);
     tc::fence_after_sync();
 
     // ---------------- G1: state deviations to cubature and face points; the
@@ -453,14 +530,14 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     // copies into the trace region, in batches of NBB faces (the first batch
     // overlaps G1), then their traces at the reversed face points into the G1
     // operand region, one item per (face, variable, half of the face points)
-    float* sNbv = reinterpret_cast<float*>(smem + S::sA1);
+    float* sNbv = reinterpret_cast<float*>(smem + g.toff + S::sA1);
     const int nlist = sList[0];
     auto issue_batch = [&](int b0) {
         // 16-byte pieces: U rows, then q rows; with AV one more item per face
         // copies its eps (4 bytes) to the last word of the record
         constexpr int CU = NP, CH = (AV ? 12 : 4) * NP / 4 + (AV ? 1 : 0);
         const int nc = min(S::NBB, nlist - b0) * CH;
-        for (int c = tid; c < nc; c += blockDim.x) {
+        for (int c = tid; c < nc; c += THREADS) {
             const int i = c / CH, j = c - i * CH;
             const int entry = sList[1 + b0 + i];
             const int ee = entry / 3, f = entry - ee * 3;
@@ -482,21 +559,26 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         euler_flux(Ub, p.gamma, Fb, Gb);
         sFb[e * 8 + v] = Fb[v];
         sFb[e * 8 + 4 + v] = Gb[v];
+        // and its contravariant forms with the element's metric
+        const float* ge = sGeo + e * 16;
+        sFC[e * 8 + v] = ge[0] * Fb[v] + ge[1] * Gb[v];
+        sFC[e * 8 + 4 + v] = ge[2] * Fb[v] + ge[3] * Gb[v];
     }
     if (!tc::mbar_wait(&bars[2], ph.g1 & 1)) atomicOr(err, 1);
     ph.g1++;
     tc::fence_after_sync();
+    DGC_PHASE_MARK(1);
     {
         constexpr int GH = (NG + 1) / 2;
         for (int b0 = 0; b0 < nlist; b0 += S::NBB) {
             if (b0 > 0) {
-                __syncthreads();   // the previous batch is consumed
+                g.sync();   // the previous batch is consumed
                 issue_batch(b0);
             }
             tc::cp_async_wait_all();
-            __syncthreads();
+            g.sync();
             const int nitems = min(S::NBB, nlist - b0) * 8;
-            for (int it = tid; it < nitems; it += blockDim.x) {
+            for (int it = tid; it < nitems; it += THREADS) {
                 const int fi = it >> 3, w = it & 3, hp = (it >> 2) & 1;
                 const int entry = sList[1 + b0 + fi];
                 const int ee = entry / 3, f = entry - ee * 3;
@@ -539,7 +621,8 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             }
         }
     }
-    __syncthreads();   // the trace region is free again
+    g.sync();   // the trace region is free again
+    DGC_PHASE_MARK(2);
 
     // ---------------- own traces (and sqrt(eps) q.n) to shared memory
     const float mean_v = sMean[row];
@@ -578,7 +661,8 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             }
         }
     }
-    __syncthreads();
+    g.sync();
+    DGC_PHASE_MARK(3);
 
     // ---------------- face fluxes, once per face point, in place:
     // (F*.n - (sqrt(eps) q)*.n - F(Ubar).n) sJ replaces the trace of each
@@ -588,22 +672,19 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         constexpr int FLUX = decltype(flux_tag)::value;
         const int nface = sFL[0] * NG;
         const int nitems = nface + 32 * D::NQF;
-        for (int it = tid; it < nitems; it += blockDim.x) {
+        for (int it = tid; it < nitems; it += THREADS) {
             if (D::NQF > 0 && it >= nface) {
                 // a folded cubature point of one element: its contravariant
                 // flux deviations into the two slots after the face points
                 const int ee = (it - nface) & 31, m = (it - nface) >> 5;
                 float* tr = sTr + ee * 4 * NFS + NF + 2 * m;
                 const float Uc[4] = {tr[0], tr[NFS], tr[2 * NFS], tr[3 * NFS]};
-                float F[4], G[4];
-                euler_flux(Uc, p.gamma, F, G);
-                const float* ge = sGeo + ee * 16;
-                const float* fb = sFb + ee * 8;
+                float Fr[4], Fs[4];
+                contra_flux_dev(Uc, p.gamma, sGeo + ee * 16, sFC + ee * 8, sFC + ee * 8 + 4, Fr, Fs);
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
-                    const float dF = F[w] - fb[w], dG = G[w] - fb[4 + w];
-                    tr[w * NFS] = ge[0] * dF + ge[1] * dG;
-                    tr[w * NFS + 1] = ge[2] * dF + ge[3] * dG;
+                    tr[w * NFS] = Fr[w];
+                    tr[w * NFS + 1] = Fs[w];
                 }
                 continue;
             }
@@ -668,7 +749,8 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     else
         face_phase(std::integral_constant<int, 0>{});
     if (tid == THREADS - 1) *next_tile = claim;
-    __syncthreads();
+    g.sync();
+    DGC_PHASE_MARK(4);
 
     // ---------------- face chunk: the rows of the flux region, 16 slots per half
     static_assert(CF == 1, "one face chunk");
@@ -686,7 +768,8 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             store8<PREC>(A2, row, half * 16 + s0, 32, x);
         }
         tc::fence_async_smem();
-        __syncthreads();
+        g.sync();
+    DGC_PHASE_MARK(5);
         if (tid == 0) {
             tc::fence_after_sync();
             issue_chunk(seq, 0);
@@ -703,15 +786,17 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         float* wst = sTr + warp * S::WST;
         const int eb = (warp & 3) * 8;             // first element of this warp
         // the lane's two (element, point) pairs keep their elements across
-        // chunks: contravariant factors and mean flux in registers
-        float cg[2][4], cf[2][8];
+        // chunks: metric and contravariant mean flux in registers
+        float cg[2][4], cfr[2][4], cfs[2][4];
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const int el = (lane >> 3) + 4 * r;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) cg[r][i] = sGeo[(eb + el) * 16 + i];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) cf[r][i] = sFb[(eb + el) * 8 + i];
+            for (int i = 0; i < 4; ++i) {
+                cg[r][i] = sGeo[(eb + el) * 16 + i];
+                cfr[r][i] = sFC[(eb + el) * 8 + i];
+                cfs[r][i] = sFC[(eb + el) * 8 + 4 + i];
+            }
         }
 #pragma unroll 1
         for (int cq = 0; cq < CQ; ++cq, ++seq) {
@@ -735,14 +820,13 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 // value, and meet zero operator columns
                 const int pp = lane + 32 * r, el = pp >> 3, ip = pp & 7;
                 const float Uc[4] = {U4[r].x, U4[r].y, U4[r].z, U4[r].w};
-                float F[4], G[4];
-                euler_flux(Uc, p.gamma, F, G);
+                float Fr[4], Fs[4];
+                contra_flux_dev(Uc, p.gamma, cg[r], cfr[r], cfs[r], Fr, Fs);
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
-                    const float dF = F[w] - cf[r][w], dG = G[w] - cf[r][4 + w];
                     // rows (element, variable) with stride 18: conflict-free
-                    wst[(el * 4 + w) * 18 + ip] = cg[r][0] * dF + cg[r][1] * dG;
-                    wst[(el * 4 + w) * 18 + 8 + ip] = cg[r][2] * dF + cg[r][3] * dG;
+                    wst[(el * 4 + w) * 18 + ip] = Fr[w];
+                    wst[(el * 4 + w) * 18 + 8 + ip] = Fs[w];
                 }
             }
             __syncwarp();
@@ -763,7 +847,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 store8<PREC>(A2, row, 16 + half * 8, 32, as);
             }
             tc::fence_async_smem();
-            __syncthreads();
+            g.sync();
             if (tid == 0) {
                 tc::fence_after_sync();
                 issue_chunk(seq, CF + cq);
@@ -772,6 +856,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         }
     }
 
+    DGC_PHASE_MARK(6);
     // ---------------- the next tile's rows into the (now free) trace region
     bool pre = false;
     {
@@ -812,7 +897,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     wait_buf(1);
     tc::fence_after_sync();
     {
-        float* sOut = reinterpret_cast<float*>(smem + S::sA1);
+        float* sOut = reinterpret_cast<float*>(smem + g.toff + S::sA1);
         const float invJ = sGeo[e * 16 + 4];
         constexpr int per_half = N2 / 2;
 #pragma unroll
@@ -826,7 +911,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 if (i0 + i < NP) sOut[row * NP + i0 + i] = x[i] * invJ;
         }
         tc::fence_before_sync();
-        __syncthreads();
+        g.sync();
         float4* uo = reinterpret_cast<float4*>(p.Uout + base);
         float4* lo = reinterpret_cast<float4*>(sOut);
         const bool sense = SENSE && p.eps_next != nullptr && !p.rhs_only;
@@ -864,7 +949,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             // the next stage's eps: the sensor of the new state, 4 threads per
             // element over the modes u = V^-1 rho (FP32 sums, FP64 ratio)
             if (sense) {
-                __syncthreads();
+                g.sync();
                 {
                     constexpr int NLOW = N * (N + 1) / 2;
                     constexpr int MT = (NP + 7) / 8;   // modes per thread, 8 threads per element
@@ -902,7 +987,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                         sND[2 * ee + 1] = den;
                     }
                 }
-                __syncthreads();
+                g.sync();
                 // the FP64 ratio, log10 and ramp for the 32 elements by one warp
                 // (one lane per element): GB300's FP64 pipe is narrow
                 if (warp == 7) {
@@ -915,7 +1000,8 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 }
             }
         }
-        __syncthreads();   // staging and per-element data are reused by the next tile
+        g.sync();   // staging and per-element data are reused by the next tile
+    DGC_PHASE_MARK(7);
     }
     return pre;
 }
@@ -953,12 +1039,57 @@ __device__ __forceinline__ void load_tc_operators(const unsigned char* ops_tc, u
     }
 }
 
-// Persistent grid (SMs x resident CTAs).  Each CTA sets up its mbarriers and
-// TMEM once and claims tiles from an atomic counter: first the curved tiles
-// (CUDA-core body, which overwrites the operator region, so the operators
-// are reloaded before the next tensor-core tile), then the affine tiles of
-// 32 elements on the tensor cores.  Handing the slow curved tiles out first
-// lets them overlap the affine work instead of forming a tail.
+// Tile pipelines per CTA: as many groups of 256 threads as the shared memory
+// holds beside one copy of the operator tables (at most two).  Each group
+// works on its own tile with its own regions, mbarriers and TMEM columns; the
+// operators are loaded once per CTA and shared.  STRIDE: the byte distance
+// between the groups' per-tile regions (the larger of the viscous layout and
+// the inviscid one of an AV launch).
+#ifndef DGC_TC_PIPES
+#define DGC_TC_PIPES 3
+#endif
+template <int N, bool AV>
+struct TcPipes {
+    using SV = TcSmem<N, AV, AV>;
+    using SI = TcSmem<N, false, AV>;
+    static constexpr int mx(int a, int b) { return a > b ? a : b; }
+    static constexpr int STRIDE = (mx(SV::TOTAL - SV::sA1, SI::TOTAL - SI::sA1) + 127) / 128 * 128;
+    static constexpr int LIMIT = 232448 - 1024 - 512;   // dynamic shared memory beside the static part
+    // TMEM columns of one pipeline: D1, the q traces (AV), D2
+    static constexpr int COLS = TcDims<N>::N1 + (AV ? 2 * TcDims<N>::NFP : 0) + TcDims<N>::N2;
+    static constexpr int pow2(int c) { return c <= 32 ? 32 : 2 * pow2((c + 1) / 2); }
+    static constexpr int PMAX = DGC_TC_PIPES;
+    static constexpr int fit(int k) {
+        return (k <= 1 || (SV::TOTAL + (k - 1) * STRIDE <= LIMIT && pow2(k * COLS) <= 512)) ? k : fit(k - 1);
+    }
+    // two pipelines go into one CTA only when two CTAs of one pipeline do not
+    // fit an SM (measured: separate CTAs overlap the next kernel's start
+    // better, the shared operator copy only matters when the SM is full)
+    static constexpr bool TWO_CTAS = fit(PMAX) == 2 && 2 * (SV::TOTAL + 1024 + 512) <= 232448;
+    static constexpr int P = TWO_CTAS ? 1 : fit(PMAX);
+    static constexpr int MIN_CTAS = TWO_CTAS ? 2 : 1;
+    static constexpr int ALLOC = pow2(P * COLS);   // one allocation for all pipelines (a power of two)
+    static_assert(ALLOC <= 512 && P * COLS <= ALLOC, "TMEM of the pipelines");
+    static constexpr int BYTES = SV::TOTAL + (P - 1) * STRIDE;
+    static constexpr int CTA_THREADS = P * THREADS;
+    static_assert(SI::TOTAL <= SV::TOTAL, "the inviscid layout of an AV launch fits the viscous one");
+    // elements of a curved tile: a pipeline runs it on the CUDA-core body in
+    // its own per-tile region (of the smaller of the two layouts' regions)
+    static constexpr int REGION = mx(SV::TOTAL - SV::sA1, 0) < mx(SI::TOTAL - SI::sA1, 0)
+                                      ? SV::TOTAL - SV::sA1 : SI::TOTAL - SI::sA1;
+    static constexpr int ec_fit(int e) {
+        return (e <= 1 || Tile<N, float>::smem_stage(AV, e) <= (size_t)REGION) ? e : ec_fit(e - 1);
+    }
+    static constexpr int EC = ec_fit(Tile<N, float>::E);
+    static_assert(Tile<N, float>::smem_stage(AV, EC) <= (size_t)REGION, "a curved tile fits a pipeline's region");
+};
+
+// Persistent grid, one CTA per SM.  Each CTA sets up its mbarriers and TMEM
+// and loads the operator tables once; each tile pipeline then claims tiles
+// from an atomic counter on its own: first the curved tiles (CUDA-core body
+// in the pipeline's region), then the affine tiles of 32 elements on the
+// tensor cores.  Handing the slow curved tiles out first lets them overlap
+// the affine work instead of forming a tail.
 //
 // With artificial viscosity, a launch whose input state has no element with
 // eps > 0 (the count of viscous tiles comes with eps from the kernel that
@@ -966,25 +1097,31 @@ __device__ __forceinline__ void load_tc_operators(const unsigned char* ops_tc, u
 // epilogue: the viscous terms are sqrt(eps) q, all zero then.  The last CTA
 // resets that count for the slot's next use.
 template <int N, bool AV, int PREC>
-__global__ void __launch_bounds__(THREADS, 2) stage_kernel_tc(StageArgs<float> p, const unsigned char* ops_tc, int* err,
-                                                              int* counter, int* done) {
+__global__ void __launch_bounds__(TcPipes<N, AV>::CTA_THREADS, TcPipes<N, AV>::MIN_CTAS)
+    stage_kernel_tc(StageArgs<float> p, const unsigned char* ops_tc, int* err, int* counter, int* done) {
+    using PP = TcPipes<N, AV>;
+    constexpr int P = PP::P;
     extern __shared__ __align__(128) unsigned char smem_tc[];
-    __shared__ __align__(8) uint64_t bars[4];
+    __shared__ __align__(8) uint64_t bars[4 * P];
     __shared__ uint32_t slot;
-    __shared__ int s_tile;
+    __shared__ int s_tile[P];
     __shared__ int s_visc;
-    constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
-    const int tid = threadIdx.x;
+    constexpr int ET = TcDims<N>::E, EC = PP::EC, COLS = PP::COLS;
+    const int tid = threadIdx.x, pipe = tid / THREADS;
+    const TcGroup g{tid - pipe * THREADS, (uint32_t)(1 + pipe), (uint32_t)(pipe * PP::STRIDE)};
     const long long nAff = (p.Kaff + ET - 1) / ET;
     const long long nCur = (p.K - p.Kaff + EC - 1) / EC;
+#ifdef DGC_PHASE_CLOCKS
+    const long long dgc_k0 = clock64();
+#endif
 
     // prologue (barriers, TMEM, operators) overlaps the previous kernel
     tc::pdl_trigger();
     if (tid == 0) {
-        for (int b = 0; b < 4; ++b) tc::mbar_init(&bars[b], 1);
+        for (int b = 0; b < 4 * P; ++b) tc::mbar_init(&bars[b], 1);
         tc::mbar_fence_init();
     }
-    if ((tid >> 5) == 0) tc::tmem_alloc(&slot, TcDims<N>::TMEM_COLS);
+    if ((tid >> 5) == 0) tc::tmem_alloc(&slot, PP::ALLOC);
     bool viscous = true;
     if constexpr (AV) {
         // the operators both kinds of launch use, then the kind of launch
@@ -998,62 +1135,72 @@ __global__ void __launch_bounds__(THREADS, 2) stage_kernel_tc(StageArgs<float> p
     } else {
         load_tc_operators<N, false>(ops_tc, smem_tc);
     }
-    auto load_ops = [&]() {   // after a curved tile: everything again
-        if constexpr (AV) {
-            if (viscous)
-                load_tc_operators<N, true>(ops_tc, smem_tc);
-            else
-                load_tc_operators<N, false, true>(ops_tc, smem_tc);
-        } else {
-            load_tc_operators<N, false>(ops_tc, smem_tc);
-        }
-    };
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = slot;
+    const uint32_t tmem = slot + (uint32_t)(pipe * COLS);
     TcPhase ph;
-    bool ops_loaded = true, rows_ready = false;
     tc::pdl_wait();
-    if (tid == 0) s_tile = atomicAdd(counter, 1);
-    __syncthreads();
-    long long t = s_tile;
+
+    // each pipeline claims tiles on its own: first the curved tiles (the
+    // CUDA-core body in the pipeline's own region; the shared operator
+    // tables stay loaded), then affine tiles of 32 elements on the tensor
+    // cores
+    unsigned char* region = smem_tc + (viscous ? PP::SV::sA1 : PP::SI::sA1) + g.toff;
+    const TileThreads th{g.tid, THREADS, g.bar};
+#ifdef DGC_PHASE_CLOCKS
+    if (g.tid == 0) atomicAdd(&g_tc_phase_cycles[11], (unsigned long long)(clock64() - dgc_k0));
+#endif
+    if (g.tid == 0) s_tile[pipe] = atomicAdd(counter, 1);
+    g.sync();
+    long long t = s_tile[pipe];
+    bool rows_ready = false;
     while (t < nCur + nAff) {
-        __syncthreads();   // every thread has read s_tile
+        g.sync();   // every thread of the pipeline has read its s_tile
         // claim the following tile now; the result is stored late in the tile
-        const int claim = (tid == THREADS - 1) ? atomicAdd(counter, 1) : 0;
+        const int claim = (g.tid == THREADS - 1) ? atomicAdd(counter, 1) : 0;
         if (t < nCur) {
             TileRange tr;
             tr.curved = true;
             tr.e0 = p.Kaff + t * EC;
             tr.ne = (int)min((long long)EC, p.K - tr.e0);
-            stage_tile_call<N, float, AV>(p, tr, smem_tc);
-            ops_loaded = false;
-            rows_ready = false;
-            if (tid == THREADS - 1) s_tile = claim;
-            __syncthreads();
-        } else {
-            if (!ops_loaded) {
-                load_ops();
-                __syncthreads();
-                ops_loaded = true;
+#ifdef DGC_PHASE_CLOCKS
+            const long long dgc_c0 = clock64();
+#endif
+            stage_tile_call<N, float, AV>(p, tr, region, th, EC);
+#ifdef DGC_PHASE_CLOCKS
+            if (g.tid == 0) {
+                atomicAdd(&g_tc_phase_cycles[9], (unsigned long long)(clock64() - dgc_c0));
+                atomicAdd(&g_tc_phase_cycles[10], 1ull);
             }
+#endif
+            rows_ready = false;
+            if (g.tid == THREADS - 1) s_tile[pipe] = claim;
+            g.sync();
+        } else {
             const long long e0 = (t - nCur) * ET;
             const int ne = (int)min((long long)ET, p.Kaff - e0);
+            uint64_t* pb = bars + 4 * pipe;
             if constexpr (AV) {
                 if (viscous)
                     rows_ready = stage_tile_tc<N, true, PREC>(p, e0, ne, smem_tc, tmem, ph, err, rows_ready, claim,
-                                                              &s_tile, nCur, nAff, bars);
+                                                              &s_tile[pipe], nCur, nAff, pb, g);
                 else
                     rows_ready = stage_tile_tc<N, false, PREC, true>(p, e0, ne, smem_tc, tmem, ph, err, rows_ready,
-                                                                     claim, &s_tile, nCur, nAff, bars);
+                                                                     claim, &s_tile[pipe], nCur, nAff, pb, g);
             } else {
                 rows_ready = stage_tile_tc<N, false, PREC>(p, e0, ne, smem_tc, tmem, ph, err, rows_ready, claim,
-                                                           &s_tile, nCur, nAff, bars);
+                                                           &s_tile[pipe], nCur, nAff, pb, g);
             }
         }
-        t = s_tile;
+        t = s_tile[pipe];
     }
+#ifdef DGC_PHASE_CLOCKS
+    if (g.tid == 0) {
+        atomicAdd(&g_tc_phase_cycles[12], (unsigned long long)(clock64() - dgc_k0));
+        atomicAdd(&g_tc_phase_cycles[13], 1ull);
+    }
+#endif
     // the last CTA to leave resets the counters for the next launch
     __threadfence();
     tc::fence_before_sync();
@@ -1064,11 +1211,11 @@ __global__ void __launch_bounds__(THREADS, 2) stage_kernel_tc(StageArgs<float> p
         *done = 0;
         if (AV && p.visc_in != nullptr) *p.visc_in = 0;
     }
-    if ((tid >> 5) == 0) tc::tmem_free(tmem, TcDims<N>::TMEM_COLS);
+    if ((tid >> 5) == 0) tc::tmem_free(slot, PP::ALLOC);
 }
 
-// Persistent grid size per instantiation: SMs x resident CTAs (shared memory
-// and TMEM columns both limit residency), set by prepare_tc before any launch.
+// Persistent grid size per instantiation: SMs x resident CTAs (one, by the
+// shared memory of the pipelines), set by prepare_tc before any launch.
 template <int N, bool AV, int PREC>
 struct TcGrid {
     static inline int ctas = 0;
@@ -1076,19 +1223,22 @@ struct TcGrid {
 
 template <int N, bool AV, int PREC>
 int prepare_tc_t() {
+    using PP = TcPipes<N, AV>;
     auto kern = stage_kernel_tc<N, AV, PREC>;
-    const int sm = (int)tc_smem_bytes<N, AV>();
+    const int sm = PP::BYTES;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return (int)e;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
         return (int)e;
-    int occ = resident_ctas((const void*)kern, THREADS, sm), dev = 0, nsm = 0;
+    int occ = resident_ctas((const void*)kern, PP::CTA_THREADS, sm), dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)e;
-    const int by_tmem = 512 / TcDims<N>::TMEM_COLS;
+    const int by_tmem = 512 / PP::ALLOC;
     occ = occ < by_tmem ? occ : by_tmem;
     if (occ < 1) return (int)cudaErrorInvalidConfiguration;
-    if (getenv("DGC_VERBOSE")) fprintf(stderr, "dgcurved: %s N=%d: %d CTAs per SM\n", __func__, N, occ);
+    if (getenv("DGC_VERBOSE"))
+        fprintf(stderr, "dgcurved: %s N=%d AV=%d: %d CTAs per SM, %d tile pipelines, %d B shared memory\n", __func__,
+                N, (int)AV, occ, PP::P, sm);
     TcGrid<N, AV, PREC>::ctas = nsm * occ;
     return 0;
 }
@@ -1097,7 +1247,8 @@ int prepare_tc_t() {
 // between launches: the last CTA resets them).
 template <int N, bool AV, int PREC>
 int launch_stage_tc_t(const StageArgs<float>& a, const unsigned char* ops_tc, int* err, cudaStream_t st) {
-    constexpr int ET = TcDims<N>::E, EC = Tile<N, float>::E;
+    using PP = TcPipes<N, AV>;
+    constexpr int ET = TcDims<N>::E, EC = PP::EC;
     const long long tiles = (a.Kaff + ET - 1) / ET + (a.K - a.Kaff + EC - 1) / EC;
     if (tiles == 0) return 0;
     const int ctas = TcGrid<N, AV, PREC>::ctas;
@@ -1106,8 +1257,9 @@ int launch_stage_tc_t(const StageArgs<float>& a, const unsigned char* ops_tc, in
     if (((uintptr_t)a.Us | (uintptr_t)a.Un | (uintptr_t)a.Uout | (uintptr_t)a.q | (uintptr_t)a.dU | (uintptr_t)ops_tc) &
         15)
         return (int)cudaErrorMisalignedAddress;
-    const unsigned grid = (unsigned)(tiles < ctas ? tiles : ctas);
-    return (int)launch_pdl(stage_kernel_tc<N, AV, PREC>, grid, THREADS, tc_smem_bytes<N, AV>(), st, a, ops_tc, err,
+    const long long need = (tiles + PP::P - 1) / PP::P;
+    const unsigned grid = (unsigned)(need < ctas ? need : ctas);
+    return (int)launch_pdl(stage_kernel_tc<N, AV, PREC>, grid, PP::CTA_THREADS, (size_t)PP::BYTES, st, a, ops_tc, err,
                            err + 1, err + 3);
 }
 
