@@ -83,7 +83,9 @@ WORKLOADS = {
     # many meshes at once (dg_batch_step): not a single-mesh workload
     "batch64": dict(kind="batch", describe="64 meshes, K log-uniform in [2k, 200k], N uniform in {2,3,4,5}, "
                                            "airfoil and cylinder alternating, Mach U[0.3,0.85], AoA U[-2,4] deg, "
-                                           "no artificial viscosity; one persistent launch per RK stage"),
+                                           "artificial viscosity from Mach 0.5; one persistent launch per RK stage "
+                                           "for the meshes without viscosity, the others on branches of the step "
+                                           "graph"),
     "prefine": dict(kind="prefine", describe="p-refinement (paper Sec. 5): cylinder channel, 15,360 elements, "
                                              "Mach 0.38, no AV; degrees 2 -> 3 -> 4 against N = 4 from the "
                                              "freestream, to the same residual"),
@@ -94,8 +96,9 @@ WORKLOADS = {
                                     "the bump), "
                                     "N=3, Mach 0.5, slip walls, farfield in/outflow, LLF"),
     "serve": dict(kind="serve", describe="continuous batching: Poisson arrivals, K log-uniform in [1k, 500k], "
-                                         "N uniform in {2..6}, admission by an HBM budget, retirement at a 1e-6 "
-                                         "residual drop or a step cap"),
+                                         "N uniform in {2..6}, Mach U[0.3,0.85] (artificial viscosity from Mach "
+                                         "0.5), admission by an HBM budget, retirement at a 1e-6 residual drop or "
+                                         "20,000 steps"),
 }
 
 
@@ -121,12 +124,16 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-meshes", type=int, default=64, help="batch64: number of meshes")
+    ap.add_argument("--batch-av-mach", type=float, default=0.5,
+                    help="batch64: artificial viscosity for meshes at or above this Mach number")
     ap.add_argument("--prefine-drop", type=float, default=0.1, help="prefine: residual drop of the lower levels")
     ap.add_argument("--prefine-max-steps", type=int, default=20000, help="prefine: steps of the N = 4 runs")
     ap.add_argument("--prefine-max-steps-low", type=int, default=5000, help="prefine: steps of the lower levels")
     ap.add_argument("--serve-requests", type=int, default=32)
-    ap.add_argument("--serve-rate", type=float, default=4.0, help="serve: Poisson arrival rate (1/s)")
-    ap.add_argument("--serve-max-steps", type=int, default=2000)
+    ap.add_argument("--serve-max-steps", type=int, default=20000)
+    ap.add_argument("--serve-rates", default="0.5,1,2", help="serve: arrival rates as multiples of the service rate")
+    ap.add_argument("--serve-av-mach", type=float, default=0.5,
+                    help="serve: artificial viscosity for requests at or above this Mach number")
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--cpu-sample", default="", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-budget-s", type=float, default=15.0, help=argparse.SUPPRESS)
@@ -1032,13 +1039,13 @@ def run_batch(args):
     reqs = make_batch(args.batch_meshes)
     nodes = {N: B.dg_reference_nodes(N) for N in range(2, 7)}
     for r in reqs:
-        serve.prepare(r, *nodes[r.N])
+        serve.prepare(r, *nodes[r.N], av_mach=args.batch_av_mach)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = B.dg_create(0, stream.cuda_stream)
     hs, dts = [], []
     for r in reqs:
-        p = B.make_params(u_inf=r.u_inf, prec=args.prec)
+        p = B.make_params(u_inf=r.u_inf, prec=args.prec, av_on=r.av, eps0=r.eps0 if r.av else 0.3)
         hs.append(B.dg_mesh_upload(ctx, r.N, r.mesh.EToE, r.mesh.EToF, r.mesh.bc, r.xy, p))
         B.dg_set_state(ctx, hs[-1], r.U0)
         dts.append(r.dt)
@@ -1067,7 +1074,7 @@ def run_batch(args):
     dof_step = sum(3 * r.mesh.K * (r.N + 1) * (r.N + 2) // 2 * 4 for r in reqs)
     value = dof_step * args.steps / (total_ms / 1e3)
     curved = [int(np.any(r.mesh.bc == 1, axis=1).sum()) for r in reqs]
-    bytes_step = sum(3 * stage_kernel_bytes(r.mesh.K, c, r.N, False) for r, c in zip(reqs, curved))
+    bytes_step = sum(3 * stage_kernel_bytes(r.mesh.K, c, r.N, r.av, r.av) for r, c in zip(reqs, curved))
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak, peak_src = 6800.0, "fallback"
     if os.path.exists(peaks_path):
@@ -1096,6 +1103,7 @@ def run_batch(args):
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
             "config": {"workload": "batch64", "describe": WORKLOADS["batch64"]["describe"],
                        "meshes": len(reqs), "total_K": int(sum(Ks)), "K_min": min(Ks), "K_max": max(Ks),
+                       "viscous_meshes": sum(1 for r in reqs if r.av),
                        "N_counts": {str(N): sum(1 for r in reqs if r.N == N) for N in range(2, 6)},
                        "dof_per_step": int(dof_step), "device_bytes": int(dev_bytes),
                        "tile_e_by_degree": tuned or "32 (tensor-core tiles)",
@@ -1113,41 +1121,70 @@ def run_batch(args):
 
 def run_serve(args):
     """Continuous batching over Poisson arrivals (serve.ServeLoop): latency
-    from arrival to result and the throughput over the run."""
+    from arrival to result and the throughput over the run.  First all
+    requests at once (arrival rate unbounded) to measure the service rate
+    mu = requests / makespan, then Poisson arrivals at the multiples of mu
+    given by --serve-rates; the line's value and latencies are those of the
+    1x run."""
+    import numpy as np
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_1208_4772_gb300 import binding as B, serve
     B.load()
     torch.cuda.set_device(0)
-    reqs = serve.poisson_requests(args.serve_requests, args.serve_rate, seed=3000)
     nodes = {N: B.dg_reference_nodes(N) for N in range(2, 7)}
-    for r in reqs:
-        serve.prepare(r, *nodes[r.N])
-    ctx = B.dg_create(0)
-    loop = serve.ServeLoop(ctx, budget_bytes=args.serve_budget_gb * 1e9, check_every=100,
-                           max_steps=args.serve_max_steps, prec=args.prec)
+    base = serve.poisson_requests(args.serve_requests, 1.0, seed=3000)
+    gaps = np.diff([0.0] + [r.arrival for r in base])     # unit-rate inter-arrival times
+
+    def requests_at(rate):
+        reqs = serve.poisson_requests(args.serve_requests, 1.0, seed=3000)
+        t = np.cumsum(gaps / rate) if np.isfinite(rate) else np.zeros(len(reqs))
+        for r, ti in zip(reqs, t):
+            r.arrival = float(ti)
+            serve.prepare(r, *nodes[r.N], av_mach=args.serve_av_mach)
+        return reqs
+
+    def one_run(rate):
+        reqs = requests_at(rate)
+        ctx = B.dg_create(0)
+        loop = serve.ServeLoop(ctx, budget_bytes=args.serve_budget_gb * 1e9, check_every=100,
+                               max_steps=args.serve_max_steps, prec=args.prec)
+        t0 = time.perf_counter()
+        done = loop.run(reqs, keep_states=False)
+        wall = time.perf_counter() - t0
+        B.dg_destroy(ctx)
+        st = serve.latency_stats(done)
+        return {"arrival_rate_per_s": rate if np.isfinite(rate) else None, "wall_s": wall,
+                "throughput_dof_per_s": st["dof_updates"] / wall, "requests_per_s": len(done) / wall,
+                "p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"], "mean_service_s": st["service_s"],
+                "peak_active": loop.peak_active, "peak_bytes": loop.peak_used,
+                "retired": {k: sum(1 for r in done if r.reason == k) for k in sorted(set(r.reason for r in done))},
+                "viscous_requests": sum(1 for r in done if r.av),
+                "restarts_with_more_viscosity": sum(r.retries for r in done),
+                "nonfinite": [[r.rid, r.kind, r.N, int(r.K), round(r.mach, 3)] for r in done if r.reason == "nonfinite"],
+                "overlap": loop.overlap()}
+
     clocks = ClockSampler(0)
     clocks.start()
-    t0 = time.perf_counter()
-    done = loop.run(reqs, keep_states=False)
-    wall = time.perf_counter() - t0
+    calib = one_run(float("inf"))
+    mu = args.serve_requests / calib["wall_s"]
+    sweep = {}
+    for mult in [float(x) for x in args.serve_rates.split(",") if x]:
+        sweep["%gx" % mult] = one_run(mult * mu)
     clk = clocks.stop()
-    B.dg_destroy(ctx)
-    st = serve.latency_stats(done)
-    line = {"metric": METRIC, "value": st["dof_updates"] / wall, "unit": UNIT, "n_gpus": 1,
+    head = sweep.get("1x") or calib
+    line = {"metric": METRIC, "value": head["throughput_dof_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": None, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE[args.prec], "data": "synthetic",
             "config": {"workload": "serve", "describe": WORKLOADS["serve"]["describe"],
-                       "requests": len(done), "arrival_rate_per_s": args.serve_rate,
+                       "requests": args.serve_requests, "service_rate_per_s": mu,
                        "step_cap": args.serve_max_steps, "check_every": 100, "drop": 1e-6,
                        "budget_GB": args.serve_budget_gb, "products": args.prec,
-                       "peak_active": loop.peak_active, "peak_bytes": loop.peak_used,
-                       "retired": {k: sum(1 for r in done if r.reason == k) for k in set(r.reason for r in done)},
-                       "nonfinite": [[r.rid, r.kind, r.N, int(r.K), round(r.mach, 3)] for r in done
-                                     if r.reason == "nonfinite"]},
-            "latency": {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"]},
-            "wall_s": wall, "cpu_baseline": None, "e2e": None, "clocks": clk}
+                       "artificial_viscosity_from_mach": args.serve_av_mach},
+            "latency": {"p50_s": head["p50_s"], "p99_s": head["p99_s"], "mean_s": head["mean_s"]},
+            "all_at_once": calib, "rates": sweep,
+            "cpu_baseline": None, "e2e": None, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 

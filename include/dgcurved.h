@@ -147,6 +147,25 @@ int dg_sizes(int N, int cub_q, int32_t* out4);
 int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int8_t* EToF,
                    const int8_t* bc, const double* node_xy, const dg_params* p, dg_mesh* out);
 
+/* dg_mesh_upload in two halves, so that the host work of one mesh can run
+ * while the device works on others (the serving loop prepares arriving
+ * requests on a worker thread).  dg_mesh_prepare does everything
+ * dg_mesh_upload does on the host -- the checks, the affine / curved
+ * classification and device order, the FP64 geometric factors and curved
+ * mass inverses (paper Sec. 2, Sec. 4 "setup operators") -- with the same
+ * arguments and errors, needs no context or GPU, is safe to call from
+ * several threads at once, and returns an opaque host object in *out
+ * (errors in dg_last_error(NULL) of the calling thread).
+ * dg_mesh_upload_prepared allocates the device buffers and copies; it takes
+ * ownership of prep and frees it whatever the outcome.  dg_prepared_free
+ * discards a prepared mesh that is not uploaded.  Together they give the
+ * mesh dg_mesh_upload gives. */
+typedef struct dg_prepared dg_prepared;
+int dg_mesh_prepare(int N, int64_t K, const int32_t* EToE, const int8_t* EToF, const int8_t* bc,
+                    const double* node_xy, const dg_params* p, dg_prepared** out);
+int dg_mesh_upload_prepared(dg_ctx* ctx, dg_prepared* prep, dg_mesh* out);
+int dg_prepared_free(dg_prepared* prep);
+
 /* Tetrahedral counterparts of dg_reference_nodes, dg_sizes and
  * dg_mesh_upload (paper Sec. 2 with d = 3).
  *
@@ -227,14 +246,27 @@ int dg_step_lserk(dg_ctx* ctx, dg_mesh m, double dt, int nsteps);
  * if any norm is NaN or Inf. */
 int dg_residual(dg_ctx* ctx, dg_mesh m, double* out_linf, double* out_l2);
 
+/* dg_residual of n meshes with one synchronisation: every mesh's
+ * right-hand side and FP64 norms are enqueued, the norms copied to pinned
+ * host slots, and the stream synchronised once.  out10: caller-owned
+ * double[n][10]; mesh i's max norms in out10[10 i + v] and Euclidean norms in
+ * out10[10 i + 5 + v] for its variables v (4 on triangles, 5 on tetrahedra;
+ * unused slots 0).  Returns DG_ENONFINITE (all norms still written) if any
+ * norm is NaN or Inf; DG_EINVAL, DG_ENOTFOUND, DG_ECUDA. */
+int dg_batch_residual(dg_ctx* ctx, int n, const dg_mesh* ms, double* out10);
+
 /* Advance n meshes (any mix of N and K) by nsteps SSP-RK3 steps each, with
- * per-mesh step sizes dts[n], using one persistent launch per RK stage that
- * walks a work list over all n meshes, replayed from a captured CUDA graph.
- * All meshes must share one precision mode and have av_on = 0.  DG_FP32 and
- * DG_FP64_DEBUG run the CUDA-core tile body; DG_TF32 and DG_BF16X3 the
- * tensor-core tile body (degrees 2..5 in one launch per stage, degree 6 in
- * a second).  Each mesh ends in the state dg_step would give it.
- * Asynchronous. */
+ * per-mesh step sizes dts[n], replayed from one captured CUDA graph.  The
+ * meshes without artificial viscosity share one persistent launch per RK
+ * stage that walks a work list over all of them: DG_FP32 and DG_FP64_DEBUG
+ * run the CUDA-core tile body, DG_TF32 and DG_BF16X3 the tensor-core tile
+ * body (degrees 2..5 in one launch per stage, degree 6 in a second).  Each
+ * mesh with artificial viscosity (paper Sec. 2) runs its own sensor,
+ * gradient and stage kernels on a branch of the same graph (up to eight
+ * side streams of the context), concurrently with the other meshes; a
+ * state set from outside gets its sensor before the graph runs.  All meshes
+ * must share one precision mode.  Each mesh ends in the state dg_step would
+ * give it.  Asynchronous. */
 int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* ms, const double* dts, int nsteps);
 
 /* p-refinement (paper Sec. 5, Table 2: converge at a low degree, then raise

@@ -68,6 +68,10 @@ def load():
         "dg_sizes": (I, [I, I, C.POINTER(C.c_int32)]),
         "dg_mesh_upload": (I, [P, I, I64, P, P, P, dp, C.POINTER(dg_params), C.POINTER(C.c_int32)]),
         "dg_mesh_free": (I, [P, C.c_int32]),
+        "dg_mesh_prepare": (I, [I, I64, P, P, P, dp, C.POINTER(dg_params), C.POINTER(P)]),
+        "dg_mesh_upload_prepared": (I, [P, P, C.POINTER(C.c_int32)]),
+        "dg_prepared_free": (I, [P]),
+        "dg_batch_residual": (I, [P, I, C.POINTER(C.c_int32), dp]),
         "dg_mesh_bytes": (I, [P, C.c_int32, C.POINTER(I64)]),
         "dg_set_state": (I, [P, C.c_int32, dp]),
         "dg_get_state": (I, [P, C.c_int32, dp]),
@@ -145,6 +149,41 @@ def dg_mesh_upload(ctx, N, EToE, EToF, bc, node_xy, params):
     _check(load().dg_mesh_upload(ctx, N, K, EToE.ctypes.data, EToF.ctypes.data, bc.ctypes.data,
                                  _dptr(node_xy), C.byref(params), C.byref(h)), ctx)
     return h.value
+
+
+def dg_mesh_prepare(N, EToE, EToF, bc, node_xy, params):
+    """Host half of dg_mesh_upload (no context; may run on a worker thread:
+    ctypes releases the interpreter lock during the call).  Returns an
+    opaque handle for dg_mesh_upload_prepared or dg_prepared_free."""
+    EToE = np.ascontiguousarray(EToE, dtype=np.int32)
+    EToF = np.ascontiguousarray(EToF, dtype=np.int8)
+    bc = np.ascontiguousarray(bc, dtype=np.int8)
+    node_xy = np.ascontiguousarray(node_xy, dtype=np.float64)
+    out = C.c_void_p()
+    _check(load().dg_mesh_prepare(N, EToE.shape[0], EToE.ctypes.data, EToF.ctypes.data, bc.ctypes.data,
+                                  _dptr(node_xy), C.byref(params), C.byref(out)))
+    return out.value
+
+
+def dg_mesh_upload_prepared(ctx, prep):
+    h = C.c_int32()
+    _check(load().dg_mesh_upload_prepared(ctx, C.c_void_p(prep), C.byref(h)), ctx)
+    return h.value
+
+
+def dg_prepared_free(prep):
+    _check(load().dg_prepared_free(C.c_void_p(prep)))
+
+
+def dg_batch_residual(ctx, meshes, allow_nonfinite=False):
+    """(linf [n, 4], l2 [n, 4]) of n triangle meshes with one synchronisation."""
+    n = len(meshes)
+    hs = (C.c_int32 * n)(*meshes)
+    out = np.zeros((n, 10))
+    st = load().dg_batch_residual(ctx, n, hs, _dptr(out))
+    if not (allow_nonfinite and st == DG_ENONFINITE):
+        _check(st, ctx)
+    return out[:, :4].copy(), out[:, 5:9].copy()
 
 
 def dg_mesh_info(ctx, m):

@@ -530,21 +530,15 @@ static int build_batch(dg_ctx* ctx, const std::vector<MeshData*>& ms, const doub
     const size_t smem = batch_smem_bytes<Real>(e_by_n);
     const int grid = batch_grid<Real>(ctx->device, 0, smem);
     if (grid <= 0) return fail(ctx, DG_ECUDA, "batch kernel occupancy query failed");
+    // the capture of the step graph opens here; dg_batch_step adds the
+    // meshes with artificial viscosity and closes it
     CUDA_OK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     int e = (int)cudaMemsetAsync(dcnt, 0, 4 * sizeof(int), ctx->stream);
     const size_t as = sizeof(StageArgs<Real>);
     for (int st = 0; st < 3 && !e; ++st)
         e = launch_batch_stage<Real>((const char*)dargs + (size_t)st * n * as, (const BatchItem*)ditems,
                                      (int)items.size(), (int*)dcnt + st, grid, smem, ctx->stream);
-    cudaGraph_t g = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
-    if (e || ce != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        return fail(ctx, DG_ECUDA, "graph capture of the batched step failed");
-    }
-    ctx->batch_graph = g;
-    CUDA_OK(ctx, cudaGraphInstantiate(&ctx->batch_gexec, g, 0));
-    return DG_OK;
+    return e ? fail(ctx, DG_ECUDA, "batched stage launch failed") : DG_OK;
 }
 
 // Tensor-core batch: affine tiles of 32 elements and curved tiles of the
@@ -600,6 +594,8 @@ static int build_batch_tc(dg_ctx* ctx, const std::vector<MeshData*>& ms, const d
     const int ghi = hi.empty() ? 0 : batch_tc_grid(ctx->device, prec, true);
     if ((!lo.empty() && glo <= 0) || (!hi.empty() && ghi <= 0))
         return fail(ctx, DG_ECUDA, "tensor-core batch kernel set-up failed");
+    // the capture of the step graph opens here; dg_batch_step adds the
+    // meshes with artificial viscosity and closes it
     CUDA_OK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     int e = (int)cudaMemsetAsync(dcnt, 0, 8 * sizeof(int), ctx->stream);
     const size_t as = sizeof(StageArgs<float>);
@@ -613,14 +609,39 @@ static int build_batch_tc(dg_ctx* ctx, const std::vector<MeshData*>& ms, const d
                                       (const unsigned char* const*)dops, ms[0]->err, (int*)dcnt + 2 * st + 1, ghi,
                                       ctx->stream);
     }
-    cudaGraph_t g = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
-    if (e || ce != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        return fail(ctx, DG_ECUDA, "graph capture of the batched step failed");
+    return e ? fail(ctx, DG_ECUDA, "batched stage launch failed") : DG_OK;
+}
+
+// Meshes with artificial viscosity in a batch: each runs its own stage
+// chain (sensor, gradient and stage kernels, or the tensor-core gradient and
+// fused-sensor stage kernels) on a branch of the step graph forked from the
+// context's stream, on a side stream of the context; the branches of
+// different meshes and the persistent launches of the other meshes run
+// concurrently and join at the end of the step.
+static int enqueue_av_branches(dg_ctx* ctx, const std::vector<MeshData*>& av, const std::vector<double>& dts) {
+    if (av.empty()) return DG_OK;
+    while (ctx->side_streams.size() < std::min<size_t>(av.size(), 8)) {
+        cudaStream_t s = nullptr;
+        CUDA_OK(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        ctx->side_streams.push_back(s);
     }
-    ctx->batch_graph = g;
-    CUDA_OK(ctx, cudaGraphInstantiate(&ctx->batch_gexec, g, 0));
+    const size_t nb = std::min<size_t>(av.size(), ctx->side_streams.size());
+    while (ctx->side_events.size() < nb + 1) {
+        cudaEvent_t ev = nullptr;
+        CUDA_OK(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        ctx->side_events.push_back(ev);
+    }
+    CUDA_OK(ctx, cudaEventRecord(ctx->side_events[nb], ctx->stream));   // the fork
+    for (size_t b = 0; b < nb; ++b) CUDA_OK(ctx, cudaStreamWaitEvent(ctx->side_streams[b], ctx->side_events[nb], 0));
+    for (size_t i = 0; i < av.size(); ++i) {
+        cudaStream_t st = ctx->side_streams[i % nb];
+        const int e = enqueue_step(*av[i], dts[i], st);
+        if (e) return fail(ctx, DG_ECUDA, "stage launch of a mesh with artificial viscosity failed");
+    }
+    for (size_t b = 0; b < nb; ++b) {   // the join
+        CUDA_OK(ctx, cudaEventRecord(ctx->side_events[b], ctx->side_streams[b]));
+        CUDA_OK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->side_events[b], 0));
+    }
     return DG_OK;
 }
 
@@ -632,7 +653,6 @@ extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* hs, const double
         ms[i] = find(ctx, hs[i]);
         if (!ms[i]) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle in batch");
         if (ms[i]->dim != 2) return fail(ctx, DG_EINVAL, "batched path runs triangle meshes only");
-        if (ms[i]->p.av_on) return fail(ctx, DG_EINVAL, "batched path runs meshes without artificial viscosity");
         if (ms[i]->prec != ms[0]->prec) return fail(ctx, DG_EINVAL, "batch mixes precision modes");
         if (!std::isfinite(dts[i])) return fail(ctx, DG_EINVAL, "bad dt");
         for (int j = 0; j < i; ++j)
@@ -640,20 +660,55 @@ extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* hs, const double
     }
     if (nsteps == 0) return DG_OK;
     cudaSetDevice(ctx->device);
+    // meshes without viscosity share the persistent launches; the others
+    // run their own stage chains on branches of the same step graph
+    std::vector<MeshData*> plain, av;
+    std::vector<double> dplain, dav;
+    for (int i = 0; i < n; ++i) {
+        (ms[i]->p.av_on ? av : plain).push_back(ms[i]);
+        (ms[i]->p.av_on ? dav : dplain).push_back(dts[i]);
+    }
     const std::vector<int> key(hs, hs + n);
     const std::vector<double> kdt(dts, dts + n);
     if (!ctx->batch_gexec || key != ctx->batch_key_meshes || kdt != ctx->batch_key_dts) {
         CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
         reset_batch(ctx);
-        const int e = tensor_prec(ms[0]->prec) ? build_batch_tc(ctx, ms, dts)
-                      : (ms[0]->rsize == 8)    ? build_batch<double>(ctx, ms, dts)
-                                               : build_batch<float>(ctx, ms, dts);
-        if (e) {
+        int e = DG_OK;
+        if (!plain.empty()) {   // these open the capture
+            e = tensor_prec(ms[0]->prec) ? build_batch_tc(ctx, plain, dplain.data())
+                : (ms[0]->rsize == 8)    ? build_batch<double>(ctx, plain, dplain.data())
+                                         : build_batch<float>(ctx, plain, dplain.data());
+        } else {
+            CUDA_OK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        }
+        if (!e) e = enqueue_av_branches(ctx, av, dav);
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(ctx->stream, &cs);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = (cs != cudaStreamCaptureStatusNone) ? cudaStreamEndCapture(ctx->stream, &g)
+                                                                   : cudaErrorStreamCaptureInvalidated;
+        if (e || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
             reset_batch(ctx);
-            return e;
+            return e ? e : fail(ctx, DG_ECUDA, "graph capture of the batched step failed");
+        }
+        ctx->batch_graph = g;
+        if (cudaGraphInstantiate(&ctx->batch_gexec, g, 0) != cudaSuccess) {
+            cudaGetLastError();
+            reset_batch(ctx);
+            return fail(ctx, DG_ECUDA, "instantiation of the batched step graph failed");
         }
         ctx->batch_key_meshes = key;
         ctx->batch_key_dts = kdt;
+    }
+    for (MeshData* m : av) {   // eps(U^n) of the first stage where a state was set from outside
+        if (fused_sensor(*m) && !m->eps_valid) {
+            CUDA_OK(ctx, cudaMemsetAsync(m->err + VISC_SLOT, 0, sizeof(int), ctx->stream));
+            const int e = enqueue_sensor(*m, m->U[0], m->eps_ring[0], ctx->stream, m->err + VISC_SLOT);
+            if (e) return fail(ctx, DG_ECUDA, std::string("sensor launch failed: ") + cudaGetErrorString((cudaError_t)e));
+            m->eps_valid = true;
+        }
     }
     for (int s = 0; s < nsteps; ++s) CUDA_OK(ctx, cudaGraphLaunch(ctx->batch_gexec, ctx->stream));
     return DG_OK;
@@ -697,6 +752,9 @@ int dg_destroy(dg_ctx* ctx) {
     ctx->meshes.clear();
     for (auto& kv : ctx->ops) cudaFree(kv.second);
     reset_batch(ctx);
+    for (cudaStream_t s : ctx->side_streams) cudaStreamDestroy(s);
+    if (ctx->res_host) cudaFreeHost(ctx->res_host);
+    for (cudaEvent_t ev : ctx->side_events) cudaEventDestroy(ev);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return DG_OK;
@@ -725,10 +783,13 @@ int dg_sizes(int N, int cub_q, int32_t* out4) {
     return DG_OK;
 }
 
-int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int8_t* EToF, const int8_t* bc,
-                   const double* node_xy, const dg_params* p, dg_mesh* out) {
-    if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
-    if (!EToE || !EToF || !bc || !node_xy || !p || !out) return fail(ctx, DG_EINVAL, "NULL argument");
+// The host half of an upload (no context, no device): checks, element
+// classification and device order, connectivity words and the FP64
+// geometric factors.  Errors go to ctx when given, else to the calling
+// thread's message (dg_last_error(NULL)).
+static int prepare_mesh(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int8_t* EToF, const int8_t* bc,
+                        const double* node_xy, const dg_params* p, dg_prepared* pr) {
+    if (!EToE || !EToF || !bc || !node_xy || !p) return fail(ctx, DG_EINVAL, "NULL argument");
     if (!supported_degree(N)) return fail(ctx, DG_EINVAL, "device path supports 2 <= N <= 6");
     if (K <= 0 || K > (int64_t)1 << 31) return fail(ctx, DG_EINVAL, "K out of range");
     if (p->cub_q != 0 && p->cub_q != default_q(N))
@@ -772,6 +833,7 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
         if (!(dev <= 1e-12 * diam)) curved[k] = 1;
     }
     auto* m = new MeshData();
+    pr->m = m;
     m->N = N; m->Np = NP; m->Nq = NQ; m->Ng = NG; m->Nf = NF;
     m->perm.reserve(K);
     m->K = K;
@@ -790,11 +852,13 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
     for (int64_t k = 0; k < K; ++k)
         if (curved[k]) m->perm.push_back(k);
     m->Kc = K - m->Kaff;
-    std::vector<long long> iperm(K);
+    std::vector<long long>& iperm = pr->iperm;
+    iperm.assign(K, 0);
     for (int64_t d = 0; d < K; ++d) iperm[m->perm[d]] = d;
 
     // connectivity in device order
-    std::vector<int4> conn(K);
+    std::vector<int4>& conn = pr->conn;
+    conn.assign(K, int4{});
     for (int64_t d = 0; d < K; ++d) {
         const int64_t k = m->perm[d];
         int nb[3], code = 0;
@@ -808,19 +872,23 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
     }
 
     // geometry (FP64)
-    std::vector<double> geoA((size_t)m->Kaff * 4);
+    std::vector<double>& geoA = pr->geoA;
+    geoA.assign((size_t)m->Kaff * 4, 0.0);
     for (long long d = 0; d < m->Kaff; ++d) {
         const double* X = node_xy + (size_t)m->perm[d] * NP * 2;
         const double xr = 0.5 * (X[2 * iv1] - X[0]), xs = 0.5 * (X[2 * iv2] - X[0]);
         const double yr = 0.5 * (X[2 * iv1 + 1] - X[1]), ys = 0.5 * (X[2 * iv2 + 1] - X[1]);
         if (!(xr * ys - xs * yr > 0.0)) {
+            const long long bad = m->perm[d];
             free_mesh(m);
-            return fail(ctx, DG_EINVAL, "non-positive Jacobian at element " + std::to_string(m->perm[d]));
+            pr->m = nullptr;
+            return fail(ctx, DG_EINVAL, "non-positive Jacobian at element " + std::to_string(bad));
         }
         geoA[4 * d] = xr; geoA[4 * d + 1] = xs; geoA[4 * d + 2] = yr; geoA[4 * d + 3] = ys;
     }
     const int CS = curved_stride(N);
-    std::vector<double> geoC((size_t)m->Kc * CS);
+    std::vector<double>& geoC = pr->geoC;
+    geoC.assign((size_t)m->Kc * CS, 0.0);
     {
         std::vector<double> M((size_t)NP * NP), Mi((size_t)NP * NP);
         const double drdt[3] = {1.0, -1.0, 0.0}, dsdt[3] = {0.0, 1.0, -1.0};
@@ -840,6 +908,7 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
                 J[q] = xr * ys - xs * yr;
                 if (!(J[q] > 0.0)) {
                     free_mesh(m);
+                    pr->m = nullptr;
                     return fail(ctx, DG_EINVAL, "non-positive Jacobian at a cubature node of element " +
                                                     std::to_string(k));
                 }
@@ -869,13 +938,30 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
                 }
             if (!spd_inverse(M.data(), Mi.data(), NP)) {
                 free_mesh(m);
+                pr->m = nullptr;
                 return fail(ctx, DG_EINVAL, "curved mass matrix not SPD at element " + std::to_string(k));
             }
             for (int j = 0; j < NP; ++j)
                 for (int i = 0; i < NP; ++i) g[5 * NQ + 3 * NF + j * NP + i] = Mi[(size_t)i * NP + j];
         }
     }
+    pr->R = R;
+    return DG_OK;
+}
 
+// The device half of an upload: buffers, operator tables, copies.  The
+// prepared host mesh moves into the context on success.
+static int upload_prepared(dg_ctx* ctx, dg_prepared* pr, dg_mesh* out) {
+    MeshData* m = pr->m;
+    const RefOps* R = pr->R;
+    const dg_params* p = &m->p;
+    const int N = m->N, NP = m->Np;
+    const int64_t K = m->K;
+    const std::vector<long long>& iperm = pr->iperm;
+    const std::vector<int4>& conn = pr->conn;
+    const std::vector<double>& geoA = pr->geoA;
+    const std::vector<double>& geoC = pr->geoC;
+    pr->m = nullptr;   // from here on freed by this function or owned by the context
     // device buffers
     cudaSetDevice(ctx->device);
     const size_t rs = m->rsize, nstate = (size_t)K * 4 * NP;
@@ -999,6 +1085,48 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
     const dg_mesh h = ctx->next_id++;
     ctx->meshes[h] = m;
     *out = h;
+    return DG_OK;
+}
+
+int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int8_t* EToF, const int8_t* bc,
+                   const double* node_xy, const dg_params* p, dg_mesh* out) {
+    if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    if (!out) return fail(ctx, DG_EINVAL, "NULL argument");
+    dg_prepared pr;
+    const int e = prepare_mesh(ctx, N, K, EToE, EToF, bc, node_xy, p, &pr);
+    if (e) return e;
+    return upload_prepared(ctx, &pr, out);
+}
+
+int dg_mesh_prepare(int N, int64_t K, const int32_t* EToE, const int8_t* EToF, const int8_t* bc,
+                    const double* node_xy, const dg_params* p, dg_prepared** out) {
+    if (!out) return fail(nullptr, DG_EINVAL, "NULL argument");
+    *out = nullptr;
+    auto* pr = new dg_prepared();
+    const int e = prepare_mesh(nullptr, N, K, EToE, EToF, bc, node_xy, p, pr);
+    if (e) {
+        delete pr;
+        return e;
+    }
+    *out = pr;
+    return DG_OK;
+}
+
+int dg_mesh_upload_prepared(dg_ctx* ctx, dg_prepared* prep, dg_mesh* out) {
+    if (!prep) return fail(ctx, DG_EINVAL, "NULL prepared mesh");
+    if (!ctx || !out || !prep->m) {
+        dg_prepared_free(prep);
+        return fail(ctx, DG_EINVAL, !prep->m ? "prepared mesh already uploaded" : "NULL argument");
+    }
+    const int e = upload_prepared(ctx, prep, out);
+    delete prep;
+    return e;
+}
+
+int dg_prepared_free(dg_prepared* prep) {
+    if (!prep) return DG_OK;
+    if (prep->m) free_mesh(prep->m);
+    delete prep;
     return DG_OK;
 }
 
@@ -1173,6 +1301,49 @@ int dg_residual(dg_ctx* ctx, dg_mesh h, double* out_linf, double* out_l2) {
         out_linf[v] = hv[v];
         out_l2[v] = hv[nv + v];
         finite = finite && std::isfinite(hv[v]) && std::isfinite(hv[nv + v]);
+    }
+    return finite ? DG_OK : fail(ctx, DG_ENONFINITE, "non-finite residual norm");
+}
+
+int dg_batch_residual(dg_ctx* ctx, int n, const dg_mesh* hs, double* out10) {
+    if (!ctx || n <= 0 || !hs || !out10) return fail(ctx, DG_EINVAL, "bad argument");
+    std::vector<MeshData*> ms(n);
+    for (int i = 0; i < n; ++i) {
+        ms[i] = find(ctx, hs[i]);
+        if (!ms[i]) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    }
+    cudaSetDevice(ctx->device);
+    if (ctx->res_host_n < n) {   // pinned host slots, one per mesh
+        if (ctx->res_host) cudaFreeHost(ctx->res_host);
+        ctx->res_host = nullptr;
+        ctx->res_host_n = 0;
+        CUDA_OK(ctx, cudaMallocHost((void**)&ctx->res_host, (size_t)n * 10 * sizeof(double)));
+        ctx->res_host_n = n;
+    }
+    for (int i = 0; i < n; ++i) {
+        MeshData* m = ms[i];
+        int e = enqueue_stage(*m, m->U[0], nullptr, m->rhs, 0.0, 0.0, 0.0, 1, ctx->stream);
+        if (e) return fail(ctx, DG_ECUDA, "stage launch failed");
+        double* dout = m->red + residual_blocks() * 10;
+        if (m->rsize == 8)
+            e = launch_residual<double>((const double*)m->rhs, m->nvar, m->K, m->Np, m->red, dout, ctx->stream);
+        else
+            e = launch_residual<float>((const float*)m->rhs, m->nvar, m->K, m->Np, m->red, dout, ctx->stream);
+        if (e) return fail(ctx, DG_ECUDA, "residual launch failed");
+        CUDA_OK(ctx, cudaMemcpyAsync(ctx->res_host + 10 * i, dout, 2 * m->nvar * sizeof(double),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
+    bool finite = true;
+    for (int i = 0; i < n; ++i) {
+        const int nv = ms[i]->nvar;
+        const double* hv = ctx->res_host + 10 * i;
+        double* o = out10 + 10 * i;
+        for (int v = 0; v < 5; ++v) {
+            o[v] = v < nv ? hv[v] : 0.0;
+            o[5 + v] = v < nv ? hv[nv + v] : 0.0;
+            if (v < nv) finite = finite && std::isfinite(hv[v]) && std::isfinite(hv[nv + v]);
+        }
     }
     return finite ? DG_OK : fail(ctx, DG_ENONFINITE, "non-finite residual norm");
 }

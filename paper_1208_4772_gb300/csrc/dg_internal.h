@@ -81,6 +81,21 @@ void drop_graphs(MeshData& m);
 
 }  // namespace dgc
 
+namespace dgc {
+struct RefOps;
+}
+
+// The host half of a mesh upload (dg_mesh_prepare): the mesh's host fields
+// and device order, and the connectivity words and FP64 geometric factors
+// waiting to be copied.
+struct dg_prepared {
+    dgc::MeshData* m = nullptr;
+    const dgc::RefOps* R = nullptr;
+    std::vector<long long> iperm;
+    std::vector<int4> conn;
+    std::vector<double> geoA, geoC;
+};
+
 struct dg_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -95,5 +110,11 @@ struct dg_ctx {
     std::vector<double> batch_key_dts;
     cudaGraph_t batch_graph = nullptr;
     cudaGraphExec_t batch_gexec = nullptr;
+    // side streams and fork / join events of the batched step's branches
+    // (meshes with artificial viscosity)
+    std::vector<cudaStream_t> side_streams;
+    std::vector<cudaEvent_t> side_events;
+    double* res_host = nullptr;       // pinned slots of dg_batch_residual
+    int res_host_n = 0;
     std::string err;
 };

@@ -90,3 +90,38 @@ def test_tet_reference_nodes_match_oracle(B, N):
     assert max(np.abs(r - R[0]).max(), np.abs(s - R[1]).max(), np.abs(t - R[2]).max()) < 1e-14
     q = default_q(N)
     assert B.dg_tet_sizes(N) == (tet.n_modes(N), q ** 3, q ** 2, tet.n_face_nodes(N))
+
+
+def test_mesh_prepare_on_host_threads(B):
+    """dg_mesh_prepare is the host half of dg_mesh_upload: it needs no
+    context or GPU, runs on several threads at once, and reports bad input
+    as status codes (here a non-reciprocal neighbour and an inverted
+    element)."""
+    import concurrent.futures as cf
+    from paper_1208_4772_gb300.inputs import curving, meshes, states
+
+    def prep(N):
+        r, s = B.dg_reference_nodes(N)
+        m = meshes.cylinder_channel(n_t=24, n_r=4, seed=1002)
+        xy, _ = curving.curve_mesh(m, N, r, s)
+        return B.dg_mesh_prepare(N, m.EToE, m.EToF, m.bc, xy, B.make_params(u_inf=states.freestream(0.38, 0.0)))
+
+    with cf.ThreadPoolExecutor(4) as ex:
+        handles = list(ex.map(prep, [2, 3, 4, 5, 6, 4]))
+    assert all(h for h in handles)
+    for h in handles:
+        B.dg_prepared_free(h)
+    N = 2
+    r, s = B.dg_reference_nodes(N)
+    m = meshes.periodic_square(4, seed=1000)
+    xy = meshes.straight_nodes(m.verts, r, s)
+    bad = m.EToE.copy()
+    bad[0, 0] = (bad[0, 0] + 1) % m.K
+    with pytest.raises(B.DgError) as e:
+        B.dg_mesh_prepare(N, bad, m.EToF, m.bc, xy, B.make_params())
+    assert e.value.status == B.DG_EINVAL and "connectivity" in str(e.value)
+    flipped = xy.copy()
+    flipped[3, :, 0] = 2 * flipped[3, 0, 0] - flipped[3, :, 0]    # mirrored: clockwise, J < 0
+    with pytest.raises(B.DgError) as e:
+        B.dg_mesh_prepare(N, m.EToE, m.EToF, m.bc, flipped, B.make_params())
+    assert e.value.status == B.DG_EINVAL

@@ -30,6 +30,20 @@ class FakeLib:
         self.meshes[h] = dict(K=EToE.shape[0], N=N, steps=0, rid=p.get("rid"))
         return h
 
+    def dg_mesh_prepare(self, N, EToE, EToF, bc, xy, p):
+        return ("prepared", N, EToE, p)
+
+    def dg_mesh_upload_prepared(self, ctx, prep):
+        _, N, EToE, p = prep
+        return self.dg_mesh_upload(ctx, N, EToE, None, None, None, p)
+
+    def dg_prepared_free(self, prep):
+        pass
+
+    def dg_batch_residual(self, ctx, hs, allow_nonfinite=False):
+        res = [self.dg_residual(ctx, h) for h in hs]
+        return np.array([a for a, _ in res]), np.array([b for _, b in res])
+
     def dg_set_state(self, ctx, h, U):
         self.meshes[h]["U"] = U
 
@@ -133,3 +147,52 @@ def test_poisson_requests_shapes():
     assert Ks.min() >= 800 and Ks.max() <= 520000
     assert set(r.N for r in reqs) <= {2, 3, 4, 5, 6}
     assert math.isclose(np.mean(np.log(Ks)), 0.5 * (math.log(1000) + math.log(500000)), rel_tol=0.1)
+
+
+class FakeLibNeedsViscosity(FakeLib):
+    """A mesh without artificial viscosity returns a NaN residual (its flow
+    develops a shock); with viscosity of at least `need` it converges."""
+
+    def __init__(self, need):
+        super().__init__(decay=0.5)
+        self.need = need
+
+    def dg_mesh_upload(self, ctx, N, EToE, EToF, bc, xy, p):
+        h = super().dg_mesh_upload(ctx, N, EToE, EToF, bc, xy, p)
+        self.meshes[h]["eps0"] = p.get("eps0", 0.0) if p.get("av_on") else 0.0
+        return h
+
+    def dg_residual(self, ctx, h, allow_nonfinite=False):
+        if self.meshes[h]["eps0"] < self.need:
+            return np.full(4, np.nan), np.full(4, np.nan)
+        return super().dg_residual(ctx, h)
+
+
+def with_geometry(r):
+    """Vertices and a finite freestream state for the viscosity strength."""
+    K = r.K
+    r.mesh.verts = np.tile(np.array([[0.0, 0.0], [0.001, 0.0], [0.0, 0.001]]), (K, 1, 1))
+    r.U0 = np.zeros((K, 4, r.Np))
+    r.U0[:, 0], r.U0[:, 1], r.U0[:, 3] = 1.0, 0.5, 2.0
+    return r
+
+
+def test_nonfinite_requests_restart_with_more_viscosity(monkeypatch):
+    """A request that turns non-finite is restarted from its initial state
+    with artificial viscosity, then with ten times more, until it is finite
+    (here on the second restart) or the retries run out."""
+    r = with_geometry(fake_request(0, 0.0, 400))
+    eps_first = serve.av_eps0(r.mesh, r.U0, r.N)
+    fake = FakeLibNeedsViscosity(need=5 * eps_first)
+    monkeypatch.setattr(serve, "B", fake)
+    loop = serve.ServeLoop(ctx=None, budget_bytes=1e12, check_every=10, max_steps=500, clock=Clock(), workers=0)
+    done = loop.run([r])
+    assert done[0].reason == "converged" and done[0].retries == 2 and done[0].av
+    assert math.isclose(done[0].eps0, 10 * eps_first)
+    r2 = with_geometry(fake_request(1, 0.0, 400))
+    fake = FakeLibNeedsViscosity(need=1.0)          # more than the cap 0.3: never finite
+    monkeypatch.setattr(serve, "B", fake)
+    loop = serve.ServeLoop(ctx=None, budget_bytes=1e12, check_every=10, max_steps=500, clock=Clock(), workers=0,
+                           max_retries=5)
+    done = loop.run([r2])
+    assert done[0].reason == "nonfinite" and done[0].eps0 == 0.3
