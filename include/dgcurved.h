@@ -283,22 +283,29 @@ int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* ms, const double* dts, int 
  * DG_EINVAL otherwise.  Synchronises the context's stream. */
 int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to);
 
-/* Tile-size autotuner for the CUDA-core paths (DG_FP32, DG_FP64_DEBUG; triangle
- * and tetrahedral meshes, each with its own tile sizes): times
- * nsteps (1..1000) SSP-RK3 steps of mesh m with dt = 0 (the full work of a
- * step, the state unchanged; it is also saved and restored) for each
- * candidate tile size -- E/4, E/2, E, 3E/2, 2E, 3E elements per CTA around the
- * degree's default E, where the tile's shared-memory layout fits one CTA --
- * and keeps the fastest for m.  The choice also applies to the context's
- * other meshes of the same degree, precision and viscosity setting, and to
- * those uploaded later (and so to dg_batch_step).  Outputs: *tile_e_out (the
- * chosen size; for DG_TF32 / DG_BF16X3, whose tensor-core tiles are fixed
- * by the 128 rows of the products, the fixed size -- 32 triangles, 8
- * tetrahedra at N = 3, 16 at N = 2 -- and nothing timed); optional
- * cand_out[8], ms_out[8] (candidates and milliseconds per step) and
- * *ncand_out (number of candidates), each may be NULL.  Synchronises the
- * context's stream.  The paper has no counterpart (its block per element is
- * fixed); a step's work distribution over CTAs is the tuned quantity. */
+/* Autotuner of the work distribution over CTAs: times nsteps (1..1000)
+ * SSP-RK3 steps of mesh m with dt = 0 (the full work of a step, the state
+ * unchanged; it is also saved and restored) for each candidate and keeps the
+ * fastest for m.  The choice also applies to the context's other meshes of
+ * the same kind (dimension, degree, precision, viscosity setting), and to
+ * those uploaded later.
+ *   - CUDA-core paths (DG_FP32, DG_FP64_DEBUG; triangles and tetrahedra):
+ *     the tile size -- E/4, E/2, E, 3E/2, 2E, 3E elements per CTA around the
+ *     degree's default E, where the tile's layout fits one CTA (and so also
+ *     dg_batch_step's tiles).  *tile_e_out = the chosen size.
+ *   - Tensor-core path on triangles (DG_TF32, DG_BF16X3): the tiles are
+ *     fixed by the 128 rows of the products (32 elements, *tile_e_out = 32);
+ *     the candidates are the stage kernel's tile-pipeline configurations
+ *     10 C + P that fit an SM: C CTAs per SM of P groups of 256 threads, each
+ *     group working on its own tile and sharing the CTA's operator tables
+ *     (21, 13, 12, or 11 where nothing larger fits).
+ *   - Tensor-core path on tetrahedra: fixed tiles (8 tetrahedra at N = 3,
+ *     16 at N = 2), nothing timed.
+ * Optional outputs cand_out[8], ms_out[8] (candidates and milliseconds per
+ * step) and *ncand_out (number of candidates), each may be NULL.
+ * Synchronises the context's stream.  The paper has no counterpart (its
+ * block per element is fixed); a step's work distribution over the SMs is
+ * the tuned quantity. */
 int dg_autotune(dg_ctx* ctx, dg_mesh m, int nsteps, int32_t* tile_e_out, int32_t* cand_out, double* ms_out,
                 int32_t* ncand_out);
 

@@ -319,15 +319,18 @@ def dg_prolong(ctx, m_from, m_to):
 
 
 def dg_autotune(ctx, m, nsteps=5):
-    """Tile-size autotuner of the CUDA-core path: returns (chosen elements
-    per tile, {candidate: ms per step}); the tensor-core path reports its
-    fixed 32 and an empty table."""
+    """The autotuner: returns (elements per tile, {candidate: ms per step},
+    chosen candidate).  CUDA-core paths: the candidates are tile sizes and
+    the chosen one is the tile size; the tensor-core path on triangles: the
+    tiles are 32 elements and the candidates are the stage kernel's
+    tile-pipeline configurations 10 C + P (C CTAs per SM of P pipelines)."""
     best = C.c_int32(0)
     cand = (C.c_int32 * 8)()
     ms = np.zeros(8)
     n = C.c_int32(0)
     _check(load().dg_autotune(ctx, m, int(nsteps), C.byref(best), cand, _dptr(ms), C.byref(n)), ctx)
-    return int(best.value), {int(cand[i]): float(ms[i]) for i in range(n.value)}
+    table = {int(cand[i]): float(ms[i]) for i in range(n.value)}
+    return int(best.value), table, (min(table, key=table.get) if table else int(best.value))
 
 
 def dg_kernel_times(ctx, m):

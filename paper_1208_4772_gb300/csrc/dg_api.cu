@@ -14,6 +14,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -119,26 +120,43 @@ int dispatch_grad(int N, const StageArgs<Real>& a, Real* out, cudaStream_t st) {
 }
 
 int dispatch_stage_tc(int N, const StageArgs<float>& a, int av, int prec, const unsigned char* ops, int* err,
-                      cudaStream_t st) {
+                      cudaStream_t st, int cfg) {
+#define DGC_TC_CASE(n)                                                              \
+    case n:                                                                         \
+        return prec == 1 ? launch_stage_tc_prec<n, 1>(a, av, ops, err, st, cfg)   \
+                         : launch_stage_tc_prec<n, 2>(a, av, ops, err, st, cfg);
     switch (N) {
-        case 2: return launch_stage_tc<2>(a, av, prec, ops, err, st);
-        case 3: return launch_stage_tc<3>(a, av, prec, ops, err, st);
-        case 4: return launch_stage_tc<4>(a, av, prec, ops, err, st);
-        case 5: return launch_stage_tc<5>(a, av, prec, ops, err, st);
-        case 6: return launch_stage_tc<6>(a, av, prec, ops, err, st);
+        DGC_TC_CASE(2) DGC_TC_CASE(3) DGC_TC_CASE(4) DGC_TC_CASE(5) DGC_TC_CASE(6)
     }
+#undef DGC_TC_CASE
     return (int)cudaErrorInvalidValue;
 }
+
+int dispatch_tc_configs(int N, int av, int* out4) {
+    switch (N) {
+        case 2: return tc_configs_n<2>(av, out4);
+        case 3: return tc_configs_n<3>(av, out4);
+        case 4: return tc_configs_n<4>(av, out4);
+        case 5: return tc_configs_n<5>(av, out4);
+        case 6: return tc_configs_n<6>(av, out4);
+    }
+    return 0;
+}
+
 int dispatch_prepare_tc(int N) {
-    switch (N) {
-        case 2: { int e = prepare_tc<2>(); return e ? e : prepare_grad_tc<2>(); }
-        case 3: { int e = prepare_tc<3>(); return e ? e : prepare_grad_tc<3>(); }
-        case 4: { int e = prepare_tc<4>(); return e ? e : prepare_grad_tc<4>(); }
-        case 5: { int e = prepare_tc<5>(); return e ? e : prepare_grad_tc<5>(); }
-        case 6: { int e = prepare_tc<6>(); return e ? e : prepare_grad_tc<6>(); }
+#define DGC_TC_PREP(n)                                                  \
+    case n: {                                                           \
+        int e = prepare_tc_prec<n, 1>();                                \
+        if (!e) e = prepare_tc_prec<n, 2>();                            \
+        return e ? e : prepare_grad_tc<n>();                            \
     }
+    switch (N) {
+        DGC_TC_PREP(2) DGC_TC_PREP(3) DGC_TC_PREP(4) DGC_TC_PREP(5) DGC_TC_PREP(6)
+    }
+#undef DGC_TC_PREP
     return (int)cudaErrorInvalidValue;
 }
+
 int dispatch_grad_tc(int N, const StageArgs<float>& a, float* q, int prec, const unsigned char* ops, int* err,
                      cudaStream_t st) {
     switch (N) {
@@ -406,7 +424,7 @@ int enqueue_stage_t(const MeshData& m, const void* Us, const void* Un, void* out
     if constexpr (sizeof(Real) == 4) {
         if (tensor_prec(m.prec))
             return dispatch_stage_tc(m.N, s, m.p.av_on, m.prec == DG_TF32 ? 1 : 2,
-                                     (const unsigned char*)m.ops_tc, m.err, st);
+                                     (const unsigned char*)m.ops_tc, m.err, st, m.tc_cfg);
     }
     return dispatch_stage<Real>(m.N, s, m.p.av_on, st);
 }
@@ -1081,6 +1099,9 @@ static int upload_prepared(dg_ctx* ctx, dg_prepared* pr, dg_mesh* out) {
     if (!tensor_prec(m->prec)) {   // a tile size tuned earlier for this kind of mesh
         auto it = ctx->tuned_e.find(tune_key(m->dim, m->N, m->rsize, m->p.av_on));
         if (it != ctx->tuned_e.end()) m->tile_e = it->second;
+    } else {                       // a tile-pipeline configuration tuned earlier
+        auto it = ctx->tuned_e.find(tune_key(m->dim, m->N, 16 + m->prec, m->p.av_on));
+        if (it != ctx->tuned_e.end()) m->tc_cfg = it->second;
     }
     const dg_mesh h = ctx->next_id++;
     ctx->meshes[h] = m;
@@ -1515,6 +1536,86 @@ int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to) {
     return DG_OK;
 }
 
+// Time nsteps SSP-RK3 steps of m (dt = 0: the full work, the state
+// unchanged, and saved and restored as well) with each of the values set by
+// apply(c) for c in cands; returns the times (ms per nsteps) or an error.
+static int time_candidates(dg_ctx* ctx, MeshData* m, int nsteps, const std::vector<int>& cands,
+                           const std::function<void(int)>& apply, std::vector<double>& ms) {
+    const size_t bytes = (size_t)m->K * m->nvar * m->Np * m->rsize;
+    CUDA_OK(ctx, cudaStreamSynchronize(ctx->stream));
+    CUDA_OK(ctx, cudaMemcpyAsync(m->rhs, m->U[0], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    CUDA_OK(ctx, cudaEventCreate(&ea));
+    if (cudaEventCreate(&eb) != cudaSuccess) {
+        cudaEventDestroy(ea);
+        return fail(ctx, DG_ECUDA, "event creation failed");
+    }
+    ms.assign(cands.size(), 0.0);
+    int err = 0;
+    for (size_t c = 0; c < cands.size() && !err; ++c) {
+        apply(cands[c]);
+        err = enqueue_step(*m, 0.0, ctx->stream);   // warm-up
+        if (!err) err = (int)cudaEventRecord(ea, ctx->stream);
+        for (int k = 0; k < nsteps && !err; ++k) err = enqueue_step(*m, 0.0, ctx->stream);
+        if (!err) err = (int)cudaEventRecord(eb, ctx->stream);
+        if (!err) err = (int)cudaEventSynchronize(eb);
+        float t = 0.f;
+        if (!err) err = (int)cudaEventElapsedTime(&t, ea, eb);
+        ms[c] = t;
+    }
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    const cudaError_t ce = cudaMemcpyAsync(m->U[0], m->rhs, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    const cudaError_t cs = cudaStreamSynchronize(ctx->stream);
+    if (err) return fail(ctx, DG_ECUDA, std::string("autotune step failed: ") + cudaGetErrorString((cudaError_t)err));
+    if (ce != cudaSuccess || cs != cudaSuccess) return fail(ctx, DG_ECUDA, "autotune state restore failed");
+    return DG_OK;
+}
+
+// The tensor-core path: the tile-pipeline configuration of the stage kernel
+// (C CTAs per SM of P tile pipelines, code 10 C + P) among those that fit.
+static int autotune_tc(dg_ctx* ctx, MeshData* m, int nsteps, int32_t* tile_e_out, int32_t* cand_out, double* ms_out,
+                       int32_t* ncand_out) {
+    int list[4];
+    const int nl = dispatch_tc_configs(m->N, m->p.av_on, list);
+    if (nl <= 0) return fail(ctx, DG_EINVAL, "no tile-pipeline configuration fits");
+    const std::vector<int> cands(list, list + nl);
+    if (fused_sensor(*m) && !m->eps_valid) {   // eps(U^n) for the timed steps' first stage
+        CUDA_OK(ctx, cudaMemsetAsync(m->err + VISC_SLOT, 0, sizeof(int), ctx->stream));
+        const int se = enqueue_sensor(*m, m->U[0], m->eps_ring[0], ctx->stream, m->err + VISC_SLOT);
+        if (se) return fail(ctx, DG_ECUDA, "sensor launch failed");
+        m->eps_valid = true;
+    }
+    // dt = 0 leaves the state (and so its eps) unchanged
+    std::vector<double> ms;
+    const int e = time_candidates(ctx, m, nsteps, cands, [&](int c) {
+        m->tc_cfg = c;
+        drop_graphs(*m);
+    }, ms);
+    size_t best = 0;
+    for (size_t c = 1; c < cands.size(); ++c)
+        if (ms[c] < ms[best]) best = c;
+    m->tc_cfg = e ? 0 : cands[best];
+    drop_graphs(*m);
+    reset_batch(ctx);
+    if (e) return e;
+    const int key = tune_key(m->dim, m->N, 16 + m->prec, m->p.av_on);
+    ctx->tuned_e[key] = m->tc_cfg;
+    for (auto& kv : ctx->meshes) {   // the context's other meshes of this kind follow
+        MeshData* o = kv.second;
+        if (o == m || o->dim != m->dim || o->prec != m->prec || o->N != m->N || o->p.av_on != m->p.av_on) continue;
+        o->tc_cfg = m->tc_cfg;
+        drop_graphs(*o);
+    }
+    *tile_e_out = 32;
+    if (ncand_out) *ncand_out = (int32_t)cands.size();
+    for (size_t c = 0; c < cands.size() && c < 8; ++c) {
+        if (cand_out) cand_out[c] = cands[c];
+        if (ms_out) ms_out[c] = ms[c] / nsteps;
+    }
+    return check_device_errors(ctx);
+}
+
 int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t* cand_out, double* ms_out,
                 int32_t* ncand_out) {
     if (!ctx || !tile_e_out) return fail(ctx, DG_EINVAL, "NULL argument");
@@ -1522,11 +1623,12 @@ int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
     if (nsteps < 1 || nsteps > 1000) return fail(ctx, DG_EINVAL, "nsteps must be in 1..1000");
     if (ncand_out) *ncand_out = 0;
-    if (tensor_prec(m->prec)) {   // fixed tiles: the rows of the products (32 triangles, 5 E <= 128 tetrahedra)
-        *tile_e_out = m->dim == 3 ? tile3_tc(m->N) : 32;
+    if (tensor_prec(m->prec) && m->dim == 3) {   // fixed tiles: 5 E <= 128 rows of the products
+        *tile_e_out = tile3_tc(m->N);
         return DG_OK;
     }
     cudaSetDevice(ctx->device);
+    if (tensor_prec(m->prec)) return autotune_tc(ctx, m, nsteps, tile_e_out, cand_out, ms_out, ncand_out);
     const bool dbl = m->rsize == 8;
     const int av = m->p.av_on;
     const int E0 = m->dim == 3 ? tile3_default(m->N, (int)m->rsize)

@@ -113,11 +113,15 @@ template <int N, typename Real> int prepare_kernels();
 template <int N, typename Real> int tile_e_default();
 template <int N, typename Real> bool tile_e_fits(int e, int av);
 
-// Tensor-core stage kernel (tc_kernels.cuh): prec 1 = TF32, 2 = BF16 x3.
-template <int N>
-int launch_stage_tc(const StageArgs<float>& a, int av, int prec, const unsigned char* ops_tc, int* err,
-                    cudaStream_t st);
-template <int N> int prepare_tc();
+// Tensor-core stage kernel (tc_kernels.cuh, instantiated per degree and
+// precision in tc_stage_n<N>_<prec>.cu): PREC 1 = TF32, 2 = BF16 x3; cfg =
+// the tile-pipeline configuration 10 C + P (C CTAs per SM of P pipelines),
+// 0 = the default; tc_configs lists the fitting ones (at most 4).
+template <int N, int PREC>
+int launch_stage_tc_prec(const StageArgs<float>& a, int av, const unsigned char* ops_tc, int* err, cudaStream_t st,
+                         int cfg);
+template <int N, int PREC> int prepare_tc_prec();
+template <int N> int tc_configs_n(int av, int* out4);
 #ifdef DGC_PHASE_CLOCKS
 template <int N> int tc_phase_cycles(unsigned long long* out16, bool reset);
 #endif

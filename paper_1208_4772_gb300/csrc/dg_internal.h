@@ -22,6 +22,7 @@ struct MeshData {
     int prec = 0;
     size_t rsize = 4;             // bytes of the device real type
     int tile_e = 0;               // elements per CUDA-core tile (0: default; see dg_autotune)
+    int tc_cfg = 0;               // tensor-core tile-pipeline configuration 10 C + P (0: default; dg_autotune)
     double s0 = 0.0;              // sensor offset actually used
     std::vector<long long> perm;  // device element d is caller element perm[d]
     void* U[3] = {nullptr, nullptr, nullptr};  // U^n, stage buffers

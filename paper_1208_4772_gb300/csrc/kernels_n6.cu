@@ -20,11 +20,6 @@ template bool tile_e_fits<6, float>(int, int);
 template bool tile_e_fits<6, double>(int, int);
 }  // namespace dgc
 namespace dgc {
-template int launch_stage_tc<6>(const StageArgs<float>&, int, int, const unsigned char*, int*, cudaStream_t);
-template int prepare_tc<6>();
-#ifdef DGC_PHASE_CLOCKS
-template int tc_phase_cycles<6>(unsigned long long*, bool);
-#endif
 template std::vector<uint8_t> pack_ops_tc<6>(const RefOps&, int);
 }  // namespace dgc
 namespace dgc {

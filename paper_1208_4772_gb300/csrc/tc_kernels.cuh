@@ -1045,33 +1045,30 @@ __device__ __forceinline__ void load_tc_operators(const unsigned char* ops_tc, u
 // operators are loaded once per CTA and shared.  STRIDE: the byte distance
 // between the groups' per-tile regions (the larger of the viscous layout and
 // the inviscid one of an AV launch).
-#ifndef DGC_TC_PIPES
-#define DGC_TC_PIPES 3
-#endif
-template <int N, bool AV>
+// Tile-pipeline configurations of the stage kernel, code = 10 C + P: C CTAs
+// per SM (the minimum the launch bounds ask for) of P pipelines of 256
+// threads, each pipeline working on its own tile with its own per-tile
+// shared-memory region, mbarriers, TMEM columns and named barrier; the
+// operator tables are loaded once per CTA and shared.  STRIDE: the byte
+// distance between the pipelines' per-tile regions (the larger of the
+// viscous layout and the inviscid one of an AV launch).  FITS: the
+// configuration fits an SM (shared memory, TMEM).
+template <int N, bool AV, int P_, int C_>
 struct TcPipes {
     using SV = TcSmem<N, AV, AV>;
     using SI = TcSmem<N, false, AV>;
+    static constexpr int P = P_, MIN_CTAS = C_, CODE = 10 * C_ + P_;
     static constexpr int mx(int a, int b) { return a > b ? a : b; }
     static constexpr int STRIDE = (mx(SV::TOTAL - SV::sA1, SI::TOTAL - SI::sA1) + 127) / 128 * 128;
-    static constexpr int LIMIT = 232448 - 1024 - 512;   // dynamic shared memory beside the static part
     // TMEM columns of one pipeline: D1, the q traces (AV), D2
     static constexpr int COLS = TcDims<N>::N1 + (AV ? 2 * TcDims<N>::NFP : 0) + TcDims<N>::N2;
     static constexpr int pow2(int c) { return c <= 32 ? 32 : 2 * pow2((c + 1) / 2); }
-    static constexpr int PMAX = DGC_TC_PIPES;
-    static constexpr int fit(int k) {
-        return (k <= 1 || (SV::TOTAL + (k - 1) * STRIDE <= LIMIT && pow2(k * COLS) <= 512)) ? k : fit(k - 1);
-    }
-    // two pipelines go into one CTA only when two CTAs of one pipeline do not
-    // fit an SM (measured: separate CTAs overlap the next kernel's start
-    // better, the shared operator copy only matters when the SM is full)
-    static constexpr bool TWO_CTAS = fit(PMAX) == 2 && 2 * (SV::TOTAL + 1024 + 512) <= 232448;
-    static constexpr int P = TWO_CTAS ? 1 : fit(PMAX);
-    static constexpr int MIN_CTAS = TWO_CTAS ? 2 : 1;
     static constexpr int ALLOC = pow2(P * COLS);   // one allocation for all pipelines (a power of two)
-    static_assert(ALLOC <= 512 && P * COLS <= ALLOC, "TMEM of the pipelines");
     static constexpr int BYTES = SV::TOTAL + (P - 1) * STRIDE;
     static constexpr int CTA_THREADS = P * THREADS;
+    // per block: dynamic + static (< 512 B) + the 1 KB the runtime reserves; per SM 228 KB
+    static constexpr bool FITS = BYTES + 512 + 1024 <= 232448 && C_ * (BYTES + 512 + 1024) <= 233472 &&
+                                 C_ * ALLOC <= 512;
     static_assert(SI::TOTAL <= SV::TOTAL, "the inviscid layout of an AV launch fits the viscous one");
     // elements of a curved tile: a pipeline runs it on the CUDA-core body in
     // its own per-tile region (of the smaller of the two layouts' regions)
@@ -1082,6 +1079,27 @@ struct TcPipes {
     }
     static constexpr int EC = ec_fit(Tile<N, float>::E);
     static_assert(Tile<N, float>::smem_stage(AV, EC) <= (size_t)REGION, "a curved tile fits a pipeline's region");
+};
+
+// The candidate configurations of a degree and viscosity setting, fitting
+// ones only: two CTAs of one pipeline, one CTA of two or three pipelines,
+// and one CTA of one pipeline where nothing larger fits.  The default (the
+// first): two single-pipeline CTAs where they fit (measured: they overlap
+// the next kernel's start better), else the most pipelines that fit.
+template <int N, bool AV>
+struct TcConfigs {
+    static constexpr bool f21 = TcPipes<N, AV, 1, 2>::FITS, f12 = TcPipes<N, AV, 2, 1>::FITS,
+                          f13 = TcPipes<N, AV, 3, 1>::FITS;
+    static constexpr bool f11 = !f21 && !f12 && !f13;
+    static int list(int* out) {
+        int n = 0;
+        if (f21) out[n++] = 21;
+        if (f13) out[n++] = 13;
+        if (f12) out[n++] = 12;
+        if (f11) out[n++] = 11;
+        return n;
+    }
+    static constexpr int deflt() { return f21 ? 21 : f13 ? 13 : f12 ? 12 : 11; }
 };
 
 // Persistent grid, one CTA per SM.  Each CTA sets up its mbarriers and TMEM
@@ -1096,10 +1114,10 @@ struct TcPipes {
 // wrote it) runs the inviscid tile body with the next stage's sensor in its
 // epilogue: the viscous terms are sqrt(eps) q, all zero then.  The last CTA
 // resets that count for the slot's next use.
-template <int N, bool AV, int PREC>
-__global__ void __launch_bounds__(TcPipes<N, AV>::CTA_THREADS, TcPipes<N, AV>::MIN_CTAS)
+template <int N, bool AV, int PREC, int P_, int C_>
+__global__ void __launch_bounds__(P_ * THREADS, C_)
     stage_kernel_tc(StageArgs<float> p, const unsigned char* ops_tc, int* err, int* counter, int* done) {
-    using PP = TcPipes<N, AV>;
+    using PP = TcPipes<N, AV, P_, C_>;
     constexpr int P = PP::P;
     extern __shared__ __align__(128) unsigned char smem_tc[];
     __shared__ __align__(8) uint64_t bars[4 * P];
@@ -1214,72 +1232,113 @@ __global__ void __launch_bounds__(TcPipes<N, AV>::CTA_THREADS, TcPipes<N, AV>::M
     if ((tid >> 5) == 0) tc::tmem_free(slot, PP::ALLOC);
 }
 
-// Persistent grid size per instantiation: SMs x resident CTAs (one, by the
-// shared memory of the pipelines), set by prepare_tc before any launch.
-template <int N, bool AV, int PREC>
+// Persistent grid size per instantiation: SMs x resident CTAs, set by
+// prepare_tc before any launch.
+template <int N, bool AV, int PREC, int P_, int C_>
 struct TcGrid {
     static inline int ctas = 0;
 };
 
-template <int N, bool AV, int PREC>
+template <int N, bool AV, int PREC, int P_, int C_>
 int prepare_tc_t() {
-    using PP = TcPipes<N, AV>;
-    auto kern = stage_kernel_tc<N, AV, PREC>;
-    const int sm = PP::BYTES;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e != cudaSuccess) return (int)e;
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
-        return (int)e;
-    int occ = resident_ctas((const void*)kern, PP::CTA_THREADS, sm), dev = 0, nsm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)e;
-    const int by_tmem = 512 / PP::ALLOC;
-    occ = occ < by_tmem ? occ : by_tmem;
-    if (occ < 1) return (int)cudaErrorInvalidConfiguration;
-    if (getenv("DGC_VERBOSE"))
-        fprintf(stderr, "dgcurved: %s N=%d AV=%d: %d CTAs per SM, %d tile pipelines, %d B shared memory\n", __func__,
-                N, (int)AV, occ, PP::P, sm);
-    TcGrid<N, AV, PREC>::ctas = nsm * occ;
-    return 0;
+    using PP = TcPipes<N, AV, P_, C_>;
+    if constexpr (!PP::FITS) {
+        return 0;
+    } else {
+        auto kern = stage_kernel_tc<N, AV, PREC, P_, C_>;
+        const int sm = PP::BYTES;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e != cudaSuccess) return (int)e;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
+            return (int)e;
+        int occ = resident_ctas((const void*)kern, PP::CTA_THREADS, sm), dev = 0, nsm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
+        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)e;
+        const int by_tmem = 512 / PP::ALLOC;
+        occ = occ < by_tmem ? occ : by_tmem;
+        if (occ < 1) return (int)cudaErrorInvalidConfiguration;
+        if (getenv("DGC_VERBOSE"))
+            fprintf(stderr, "dgcurved: stage_kernel_tc N=%d AV=%d config %d: %d CTAs per SM, %d B shared memory\n", N,
+                    (int)AV, PP::CODE, occ, sm);
+        TcGrid<N, AV, PREC, P_, C_>::ctas = nsm * occ;
+        return 0;
+    }
 }
 
 // err[0]: error word; err[1]: tile counter, err[3]: CTAs done (both zero
 // between launches: the last CTA resets them).
-template <int N, bool AV, int PREC>
+template <int N, bool AV, int PREC, int P_, int C_>
 int launch_stage_tc_t(const StageArgs<float>& a, const unsigned char* ops_tc, int* err, cudaStream_t st) {
-    using PP = TcPipes<N, AV>;
-    constexpr int ET = TcDims<N>::E, EC = PP::EC;
-    const long long tiles = (a.Kaff + ET - 1) / ET + (a.K - a.Kaff + EC - 1) / EC;
-    if (tiles == 0) return 0;
-    const int ctas = TcGrid<N, AV, PREC>::ctas;
-    if (ctas <= 0) return (int)cudaErrorNotReady;   // prepare_tc was not called
-    // the tile and neighbour records travel by TMA bulk copies: 16-byte aligned
-    if (((uintptr_t)a.Us | (uintptr_t)a.Un | (uintptr_t)a.Uout | (uintptr_t)a.q | (uintptr_t)a.dU | (uintptr_t)ops_tc) &
-        15)
-        return (int)cudaErrorMisalignedAddress;
-    const long long need = (tiles + PP::P - 1) / PP::P;
-    const unsigned grid = (unsigned)(need < ctas ? need : ctas);
-    return (int)launch_pdl(stage_kernel_tc<N, AV, PREC>, grid, PP::CTA_THREADS, (size_t)PP::BYTES, st, a, ops_tc, err,
-                           err + 1, err + 3);
+    using PP = TcPipes<N, AV, P_, C_>;
+    if constexpr (!PP::FITS) {
+        return (int)cudaErrorInvalidConfiguration;
+    } else {
+        constexpr int ET = TcDims<N>::E, EC = PP::EC;
+        const long long tiles = (a.Kaff + ET - 1) / ET + (a.K - a.Kaff + EC - 1) / EC;
+        if (tiles == 0) return 0;
+        const int ctas = TcGrid<N, AV, PREC, P_, C_>::ctas;
+        if (ctas <= 0) return (int)cudaErrorNotReady;   // prepare_tc was not called
+        // the tile and neighbour records travel by TMA bulk copies: 16-byte aligned
+        if (((uintptr_t)a.Us | (uintptr_t)a.Un | (uintptr_t)a.Uout | (uintptr_t)a.q | (uintptr_t)a.dU |
+             (uintptr_t)ops_tc) & 15)
+            return (int)cudaErrorMisalignedAddress;
+        const long long need = (tiles + PP::P - 1) / PP::P;
+        const unsigned grid = (unsigned)(need < ctas ? need : ctas);
+        return (int)launch_pdl(stage_kernel_tc<N, AV, PREC, P_, C_>, grid, PP::CTA_THREADS, (size_t)PP::BYTES, st, a,
+                               ops_tc, err, err + 1, err + 3);
+    }
 }
 
-template <int N>
-int launch_stage_tc(const StageArgs<float>& a, int av, int prec, const unsigned char* ops_tc, int* err,
-                    cudaStream_t st) {
-    if (prec == PREC_TF32)
-        return av ? launch_stage_tc_t<N, true, PREC_TF32>(a, ops_tc, err, st)
-                  : launch_stage_tc_t<N, false, PREC_TF32>(a, ops_tc, err, st);
-    return av ? launch_stage_tc_t<N, true, PREC_BF16X3>(a, ops_tc, err, st)
-              : launch_stage_tc_t<N, false, PREC_BF16X3>(a, ops_tc, err, st);
+// One precision and viscosity setting: the configuration cfg (0: the default).
+template <int N, bool AV, int PREC>
+int launch_stage_tc_cfg(const StageArgs<float>& a, const unsigned char* ops_tc, int* err, cudaStream_t st, int cfg) {
+    if (cfg == 0) cfg = TcConfigs<N, AV>::deflt();
+    using C = TcConfigs<N, AV>;
+    switch (cfg) {
+        case 21:
+            if constexpr (C::f21) return launch_stage_tc_t<N, AV, PREC, 1, 2>(a, ops_tc, err, st);
+            break;
+        case 12:
+            if constexpr (C::f12) return launch_stage_tc_t<N, AV, PREC, 2, 1>(a, ops_tc, err, st);
+            break;
+        case 13:
+            if constexpr (C::f13) return launch_stage_tc_t<N, AV, PREC, 3, 1>(a, ops_tc, err, st);
+            break;
+        case 11:
+            if constexpr (C::f11) return launch_stage_tc_t<N, AV, PREC, 1, 1>(a, ops_tc, err, st);
+            break;
+    }
+    return (int)cudaErrorInvalidValue;
 }
 
-template <int N>
-int prepare_tc() {
-    int e = prepare_tc_t<N, false, PREC_TF32>();
-    if (!e) e = prepare_tc_t<N, true, PREC_TF32>();
-    if (!e) e = prepare_tc_t<N, false, PREC_BF16X3>();
-    if (!e) e = prepare_tc_t<N, true, PREC_BF16X3>();
+template <int N, bool AV, int PREC>
+int prepare_tc_av() {
+    using C = TcConfigs<N, AV>;
+    int e = 0;
+    if constexpr (C::f21) e = e ? e : prepare_tc_t<N, AV, PREC, 1, 2>();
+    if constexpr (C::f12) e = e ? e : prepare_tc_t<N, AV, PREC, 2, 1>();
+    if constexpr (C::f13) e = e ? e : prepare_tc_t<N, AV, PREC, 3, 1>();
+    if constexpr (C::f11) e = e ? e : prepare_tc_t<N, AV, PREC, 1, 1>();
     return e;
+}
+
+template <int N, int PREC>
+int prepare_tc_prec() {
+    const int e = prepare_tc_av<N, false, PREC>();
+    return e ? e : prepare_tc_av<N, true, PREC>();
+}
+
+template <int N>
+int tc_configs_n(int av, int* out4) {
+    return av ? TcConfigs<N, true>::list(out4) : TcConfigs<N, false>::list(out4);
+}
+
+// The per-precision halves (one translation unit each, compiled in parallel).
+template <int N, int PREC>
+int launch_stage_tc_prec(const StageArgs<float>& a, int av, const unsigned char* ops_tc, int* err, cudaStream_t st,
+                         int cfg) {
+    return av ? launch_stage_tc_cfg<N, true, PREC>(a, ops_tc, err, st, cfg)
+              : launch_stage_tc_cfg<N, false, PREC>(a, ops_tc, err, st, cfg);
 }
 
 // ---------------------------------------------------------------------------

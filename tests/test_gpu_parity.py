@@ -265,7 +265,7 @@ def test_autotune_keeps_state_and_results(B, ctx, prec):
     leaves the state as it was, and the tuned tiles step bitwise like the
     default ones (each element's arithmetic is the same; only its CTA
     changes).  A later mesh of the same kind in the context inherits the
-    choice; the tensor-core path reports its fixed 32-element tiles."""
+    choice."""
     N = 4
     r, s = B.dg_reference_nodes(N)
     case = make_case("naca", N, r, s, av=True)
@@ -273,7 +273,7 @@ def test_autotune_keeps_state_and_results(B, ctx, prec):
     K, Np = case["mesh"].K, len(r)
     h = upload(B, ctx, case, prec)
     U0 = B.dg_get_state(ctx, h, K, Np)
-    best, table = B.dg_autotune(ctx, h, 3)
+    best, table, _ = B.dg_autotune(ctx, h, 3)
     assert len(table) >= 2 and best in table and all(t > 0 for t in table.values()), table
     assert np.array_equal(B.dg_get_state(ctx, h, K, Np), U0)
     B.dg_step(ctx, h, dt, 3)
@@ -284,8 +284,6 @@ def test_autotune_keeps_state_and_results(B, ctx, prec):
         h2 = upload(B, c2, case, prec)
         B.dg_step(c2, h2, dt, 3)
         Ud = B.dg_get_state(c2, h2, K, Np)
-        h3 = upload(B, c2, case, "tf32")
-        assert B.dg_autotune(c2, h3, 2) == (32, {})
     finally:
         B.dg_destroy(c2)
     assert np.array_equal(Ut, Ud)

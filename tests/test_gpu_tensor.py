@@ -302,3 +302,36 @@ def test_mixed_precision_keeps_convergence_order(B, ctx, N, n1):
         assert np.log2(e1 / e2) >= N + 0.5, (prec, e1, e2)
     for prec in ("tf32", "bf16x3"):
         assert errs[prec][1] <= 1.1 * errs["fp32"][1], errs
+
+
+@pytest.mark.parametrize("kind,N,av", [("naca", 4, True), ("cyl", 4, False), ("vortex", 6, False)])
+def test_tc_autotune_times_pipeline_configurations(B, ctx, kind, N, av):
+    """The autotuner on the tensor-core path times the stage kernel's
+    tile-pipeline configurations that fit (10 C + P: C CTAs per SM of P
+    pipelines), leaves the state as it was, and the chosen configuration
+    steps bitwise like the default one (each tile's arithmetic does not
+    depend on which pipeline runs it); a later mesh of the same kind
+    inherits the choice."""
+    r, s = B.dg_reference_nodes(N)
+    case = make_case(kind, N, r, s, av=av)
+    case["U"] = case["U"].astype(np.float32).astype(np.float64)
+    dt = 0.2 * states.time_step(case["mesh"].verts, case["U"], N, eps0=0.3 if av else None)
+    K, Np = case["mesh"].K, len(r)
+    c2 = B.dg_create(0)
+    try:
+        h = upload(B, c2, case, "tf32")
+        B.dg_step(c2, h, dt, 2)
+        Ud = B.dg_get_state(c2, h, K, Np)           # default configuration
+        B.dg_set_state(c2, h, case["U"])
+        tile, table, cfg = B.dg_autotune(c2, h, 3)
+        assert tile == 32 and len(table) >= 1 and cfg in table and all(t > 0 for t in table.values()), table
+        assert set(table) <= {11, 12, 13, 21}
+        assert np.array_equal(B.dg_get_state(c2, h, K, Np), case["U"])
+        # the chosen configuration steps like the default one
+        B.dg_step(c2, h, dt, 2)
+        assert np.array_equal(B.dg_get_state(c2, h, K, Np), Ud)
+        h2 = upload(B, c2, case, "tf32")             # inherits the tuned configuration
+        B.dg_step(c2, h2, dt, 2)
+        assert np.array_equal(B.dg_get_state(c2, h2, K, Np), Ud)
+    finally:
+        B.dg_destroy(c2)

@@ -200,7 +200,7 @@ def test_tet_autotune_keeps_state_and_results(B, ctx, prec):
     case, U, h, o = setup(B, ctx, "bump", 3, prec, size="medium")
     dt = 0.5 * states.time_step3(case["mesh"].verts, U, 3)
     U0 = B.dg_get_state(ctx, h)
-    best, table = B.dg_autotune(ctx, h, 2)
+    best, table, _ = B.dg_autotune(ctx, h, 2)
     assert len(table) >= 2 and best in table and all(t > 0 for t in table.values()), table
     assert np.array_equal(B.dg_get_state(ctx, h), U0)
     B.dg_step(ctx, h, dt, 2)
@@ -223,6 +223,6 @@ def test_tet_tf32_autotune_reports_fixed_tiles(B, ctx):
     products): the autotuner times nothing and reports them."""
     for N, E in ((2, 16), (3, 8)):
         case, U, h, o = setup(B, ctx, "box", N, "tf32")
-        best, table = B.dg_autotune(ctx, h, 2)
+        best, table, _ = B.dg_autotune(ctx, h, 2)
         B.dg_mesh_free(ctx, h)
         assert best == E and table == {}
