@@ -1007,6 +1007,10 @@ static int upload_prepared(dg_ctx* ctx, dg_prepared* pr, dg_mesh* out) {
         auto tit = ctx->ops.find(tkey);
         if (tit == ctx->ops.end()) {
             const std::vector<uint8_t> packed = dispatch_pack_tc(N, *R, p->prec == DG_TF32 ? 1 : 2);
+            if (packed.empty()) {
+                free_mesh(m);
+                return fail(ctx, DG_EINVAL, "face traces do not reduce to the face nodes");
+            }
             void* d = nullptr;
             if (cudaMalloc(&d, packed.size()) != cudaSuccess) {
                 cudaGetLastError();

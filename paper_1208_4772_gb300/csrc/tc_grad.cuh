@@ -172,18 +172,21 @@ __device__ __forceinline__ bool grad_tile_tc(const StageArgs<float>& p, float* q
                 const int4 nbw = sNb[ee];
                 const int fn = code_face(nbw.w, f);
                 const float* rec = sTr + fi * S::REC;
-                float un[NP];
+                // the neighbour's values at the nodes of its face fn
+                constexpr int NE = TcDims<N>::NE;
+                const int* fmask = reinterpret_cast<const int*>(sIgF + 3 * NG * NE) + fn * NE;
+                float un[NE];
 #pragma unroll
-                for (int j = 0; j < NP; ++j) un[j] = rec[w * NP + j];
+                for (int k = 0; k < NE; ++k) un[k] = rec[w * NP + fmask[k]];
                 const float sen = sqrtf(rec[4 * NP]);
                 const int g1 = hp ? NG : GH;
 #pragma unroll 1
                 for (int gg = hp * GH; gg < g1; ++gg) {
-                    const float* ig = sIgF + (fn * NG + (NG - 1 - gg)) * NP;
+                    const float* eg = sIgF + (fn * NG + (NG - 1 - gg)) * NE;
                     float* dst = sNbv + (ee * NF + f * NG + gg) * S::NBV_C;
                     float a = 0.f;
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) a += ig[j] * un[j];
+                    for (int k = 0; k < NE; ++k) a += eg[k] * un[k];
                     dst[w] = a;
                     if (w == 0) dst[4] = sen;
                 }

@@ -43,6 +43,8 @@ constexpr int PREC_TF32 = 1, PREC_BF16X3 = 2;
 template <int N>
 struct TcDims {
     static constexpr int NP = np_of(N), NQ = nq_of(N), NG = ng_of(N), NF = nf_of(N);
+    static constexpr int NE = N + 1;                       // nodes on a face
+    static_assert(3 * NG * NE + 3 * NE <= NF * NP, "the compact face tables fit the trace table's slot");
     static constexpr int NPK = (NP + 15) / 16 * 16;        // K of G1
     static constexpr int FOFF = (NQ + 15) / 16 * 16;       // first face column of D1
     static constexpr int N1 = (FOFF + NF + 15) / 16 * 16;  // columns of D1
@@ -86,7 +88,9 @@ struct TcLayout {
     static constexpr int B1Q_BYTES = D::NFP * D::NPK * 4;
     static constexpr int B2 = B1Q + B1Q_BYTES;                     // NCH x [N2 rows][32]
     static constexpr int B2_CHUNK = D::N2 * 32 * 4;
-    static constexpr int IGF = B2 + D::NCH * B2_CHUNK;             // I_g fp32 [NF][NP]
+    // face traces from the face nodes, fp32 [3][NG][NE], then the face nodes int [3][NE]
+    // (in a slot of NF x NP floats)
+    static constexpr int IGF = B2 + D::NCH * B2_CHUNK;
     static constexpr int BQ = (IGF + D::NF * D::NP * 4 + 15) / 16 * 16;  // [2 N2 rows][NPK]: Q_r; Q_s
     static constexpr int BQ_BYTES = 2 * D::N2 * D::NPK * 4;
     static constexpr int VINV = BQ + BQ_BYTES;                      // V^-1 transposed, fp32 [NP][NP] (sensor)
@@ -585,15 +589,18 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 const int4 nbw = sNb[ee];
                 const int fn = code_face(nbw.w, f);
                 const float* rec = sTr + fi * S::REC;
-                float un[NP], qx[AV ? NP : 1], qy[AV ? NP : 1];
+                // the neighbour's values at the nodes of its face fn
+                constexpr int NE = D::NE;
+                const int* fmask = reinterpret_cast<const int*>(sIgF + 3 * NG * NE) + fn * NE;
+                float un[NE], qx[AV ? NE : 1], qy[AV ? NE : 1];
 #pragma unroll
-                for (int j = 0; j < NP; ++j) un[j] = rec[w * NP + j];
+                for (int k = 0; k < NE; ++k) un[k] = rec[w * NP + fmask[k]];
                 float sen = 0.f, nx = 0.f, ny = 0.f;
                 if constexpr (AV) {
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) {
-                        qx[j] = rec[(4 + w) * NP + j];
-                        qy[j] = rec[(8 + w) * NP + j];
+                    for (int k = 0; k < NE; ++k) {
+                        qx[k] = rec[(4 + w) * NP + fmask[k]];
+                        qy[k] = rec[(8 + w) * NP + fmask[k]];
                     }
                     sen = sqrtf(rec[12 * NP]);
                     nx = sGeo[ee * 16 + 5 + 3 * f];
@@ -603,16 +610,16 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
 #pragma unroll 1
                 for (int gg = hp * GH; gg < g1; ++gg) {
                     const int fg = f * NG + gg;
-                    const float* ig = sIgF + (fn * NG + (NG - 1 - gg)) * NP;
+                    const float* eg = sIgF + (fn * NG + (NG - 1 - gg)) * NE;
                     float* dst = sNbv + (ee * NF + fg) * S::NBV_C;
                     float a = 0.f, ax = 0.f, ay = 0.f;
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) {
-                        const float g = ig[j];
-                        a += g * un[j];
+                    for (int k = 0; k < NE; ++k) {
+                        const float g = eg[k];
+                        a += g * un[k];
                         if constexpr (AV) {
-                            ax += g * qx[j];
-                            ay += g * qy[j];
+                            ax += g * qx[k];
+                            ay += g * qy[k];
                         }
                     }
                     dst[w] = a;
@@ -1426,11 +1433,34 @@ std::vector<uint8_t> pack_ops_tc(const RefOps& R, int prec) {
             return s < 16 ? -R.Qr[(size_t)i * NP + j] : -R.Qs[(size_t)i * NP + j];
         });
     }
-    for (int fg = 0; fg < NF; ++fg)
-        for (int j = 0; j < NP; ++j) {
-            const float f = (float)Ig(fg, j);
-            std::memcpy(&out[L::IGF + ((size_t)fg * NP + j) * 4], &f, 4);
+    // the traces as 1D interpolation from each face's N + 1 nodes (the
+    // nodes on a face carry the restriction of the degree-N polynomial):
+    // E[f][g][k] = I_g[f][g][fmask[f][k]], all other entries of I_g vanish
+    {
+        constexpr int NG = D::NG, NE = TcDims<N>::NE;
+        std::vector<int> fm(3 * NE, -1);
+        for (int f = 0; f < 3; ++f) {
+            int k = 0;
+            for (int j = 0; j < NP; ++j) {
+                double mxv = 0.0;
+                for (int g = 0; g < NG; ++g) mxv = std::max(mxv, std::fabs(Ig(f * NG + g, j)));
+                if (mxv > 1e-9) {
+                    if (k >= NE) return {};   // more nodes on a face than a degree-N trace needs
+                    fm[f * NE + k++] = j;
+                } else if (mxv > 1e-12) {
+                    return {};
+                }
+            }
+            if (k != NE) return {};
         }
+        for (int f = 0; f < 3; ++f)
+            for (int g = 0; g < NG; ++g)
+                for (int k = 0; k < NE; ++k) {
+                    const float v = (float)Ig(f * NG + g, fm[f * NE + k]);
+                    std::memcpy(&out[L::IGF + ((size_t)(f * NG + g) * NE + k) * 4], &v, 4);
+                }
+        std::memcpy(&out[L::IGF + (size_t)3 * NG * NE * 4], fm.data(), 3 * NE * sizeof(int));
+    }
     for (int j = 0; j < NP; ++j)
         for (int m = 0; m < NP; ++m) {
             const float f = (float)R.Vinv[(size_t)m * NP + j];
