@@ -150,7 +150,15 @@ struct TcSmem {
     static constexpr int sFL = sLIST + 100 * 4;                              // faces owned by the tile: n, then (e,f)
     static constexpr int sND = sFL + 100 * 4;                                // [32][2] sensor sums of the new state
     static constexpr int sFC = sND + 64 * 4;                                 // [32][8] contravariant mean flux
-    static constexpr int TOTAL = sFC + 32 * 8 * 4;
+    static constexpr int sFBN = sFC + 32 * 8 * 4;                            // [32][3][4] (F(Ubar).n) sJ per face
+    // [96] face records, 3 int4 each: in the second A2 buffer, free from the
+    // previous tile's end to the face chunk unless viscous chunks occupy both
+    // buffers at tile start (then a region of their own)
+    static constexpr bool REC_OWN = AV && D::CA >= 2;
+    static constexpr int REC_BYTES = 96 * 48;
+    static constexpr int sREC = REC_OWN ? sFBN + 32 * 3 * 4 * 4 : sA2 + A2_BYTES;
+    static constexpr int TOTAL = sFBN + 32 * 3 * 4 * 4 + (REC_OWN ? REC_BYTES : 0);
+    static_assert(REC_BYTES <= A2_BYTES, "face records fit an A2 buffer");
     static_assert(TOTAL + 256 <= 232448, "tensor-core tile exceeds the shared-memory limit");
     static_assert(D::CA <= NBUF, "viscous chunks are written at tile start, one per A2 buffer");
     static_assert(NBB >= 32 && (REC * 4) % 16 == 0 && (32 * 4 * D::NP * 4) % 16 == 0, "bulk-copy staging layout");
@@ -241,7 +249,7 @@ __device__ __forceinline__ void issue_mma(uint32_t d_tmem, const unsigned char* 
     }
 }
 
-// Per-element data of a tensor-core tile, by warp 0, from the staged copies
+// Per-element data of a tensor-core tile, by one warp (tid: its lane), from the staged copies
 // of x_r, x_s, y_r, y_s, the connectivity words and eps: affine geometry,
 // connectivity word, sqrt(eps) (when av), and two compact face lists (count
 // first, then element * 3 + face): sList the faces whose neighbour lies
@@ -411,6 +419,8 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     int* sFL = reinterpret_cast<int*>(smem + g.toff + S::sFL);
     float* sND = reinterpret_cast<float*>(smem + g.toff + S::sND);
     float* sFC = reinterpret_cast<float*>(smem + g.toff + S::sFC);
+    float* sFbnJ = reinterpret_cast<float*>(smem + g.toff + S::sFBN);
+    int4* sRec = reinterpret_cast<int4*>(smem + g.toff + S::sREC);
 
     // G2 runs as a sequence of K chunks; chunk number s uses A2 buffer s % 2.
     auto a2_buf = [&](int s) { return smem + g.toff + S::sA2 + (s & 1) * S::A2_BYTES; };
@@ -430,16 +440,16 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     DGC_PHASE_BEGIN();
 
     // ---------------- tile inputs: the U (and q) rows of the tile by TMA bulk
-    // copies into the trace region; per-element data and face lists by warp 0
+    // copies into the trace region; per-element data and face lists by warp 4
     if (tid == 32 && !rows_ready) issue_tile_rows<N, AV, AV>(p, e0, ne, sTr, &bars[3]);
     const long long k = e0 + e;
     const bool live = e < ne;
     using TS = TileStage<N, AV>;
     if (!tc::mbar_wait(&bars[3], ph.ld & 1)) atomicOr(err, 8);
     ph.ld++;
-    if (tid < 32)
-        tile_info(tid, e0, ne, AV, sTr + TS::G, reinterpret_cast<const int4*>(sTr + TS::C), sTr + TS::E, sGeo, sNb, sSe,
-                  sList, sFL);
+    if (warp == 4)   // per-element data by a warp of the half that does not build the G1 operand
+        tile_info(tid - 128, e0, ne, AV, sTr + TS::G, reinterpret_cast<const int4*>(sTr + TS::C), sTr + TS::E, sGeo,
+                  sNb, sSe, sList, sFL);
     if (half == 0) {
         float u[NP];
         float mean = 0.f;
@@ -563,10 +573,14 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         euler_flux(Ub, p.gamma, Fb, Gb);
         sFb[e * 8 + v] = Fb[v];
         sFb[e * 8 + 4 + v] = Gb[v];
-        // and its contravariant forms with the element's metric
+        // and its contravariant forms with the element's metric, and its
+        // normal flux times sJ on each face
         const float* ge = sGeo + e * 16;
         sFC[e * 8 + v] = ge[0] * Fb[v] + ge[1] * Gb[v];
         sFC[e * 8 + 4 + v] = ge[2] * Fb[v] + ge[3] * Gb[v];
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+            sFbnJ[(e * 3 + f) * 4 + v] = (Fb[v] * ge[5 + 3 * f] + Gb[v] * ge[6 + 3 * f]) * ge[7 + 3 * f];
     }
     if (!tc::mbar_wait(&bars[2], ph.g1 & 1)) atomicOr(err, 1);
     ph.g1++;
@@ -668,6 +682,38 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             }
         }
     }
+    // face records, one thread per face the tile computes: where each side's
+    // values are, the normal, sJ of both sides and their mean-flux indices
+    {
+        const int rt = AV ? tid : tid - 128;
+        if (rt >= 0 && rt < sFL[0]) {
+            const int entry = sFL[1 + rt];
+            const int ee = entry / 3, f = entry - ee * 3;
+            const int4 nbw = sNb[ee];
+            const int bc = code_bc(nbw.w, f);
+            const int nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
+            const int fn = code_face(nbw.w, f);
+            const long long nbll = (long long)nb - e0;
+            const bool in_tile = (bc == 0) && nbll >= 0 && nbll < ne;
+            const int nbl = in_tile ? (int)nbll : 0;
+            const int own = ee * 4 * NFS + f * NG;
+            int up = own, step = 0, vstr = NFS;
+            if (in_tile) {
+                up = nbl * 4 * NFS + fn * NG + (NG - 1);
+                step = -1;
+            } else if (bc == 0) {
+                up = (ee * NF + f * NG) * S::NBV_C;
+                step = S::NBV_C;
+                vstr = 1;
+            }
+            const float* ge = sGeo + ee * 16;
+            const float sJn = in_tile ? sGeo[nbl * 16 + 7 + 3 * fn] : 0.f;
+            sRec[3 * rt] = make_int4(own, up, (bc | (in_tile ? 4 : 0)) | ((step + 128) << 8) | (vstr << 16),
+                                     (ee * 3 + f) | ((in_tile ? nbl * 3 + fn : 0) << 16));
+            sRec[3 * rt + 1] = make_int4(__float_as_int(ge[5 + 3 * f]), __float_as_int(ge[6 + 3 * f]),
+                                         __float_as_int(ge[7 + 3 * f]), __float_as_int(sJn));
+        }
+    }
     g.sync();
     DGC_PHASE_MARK(3);
 
@@ -695,28 +741,24 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 }
                 continue;
             }
-            const int entry = sFL[1 + it / NG], gg = it % NG;
-            const int ee = entry / 3, f = entry - ee * 3, fg = f * NG + gg;
-            const int4 nbw = sNb[ee];
-            const int bc = code_bc(nbw.w, f);
-            const int nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
-            const int fn = code_face(nbw.w, f), fgn = fn * NG + (NG - 1 - gg);
-            const float* ge = sGeo + ee * 16;
-            const float nx = ge[5 + 3 * f], ny = ge[6 + 3 * f], sJ = ge[7 + 3 * f];
-            const long long nbll = (long long)nb - e0;
-            const bool in_tile = (bc == 0) && nbll >= 0 && nbll < ne;
-            const int nbl = in_tile ? (int)nbll : 0;
+            const int fi = it / NG, gg = it - fi * NG;
+            const int4 r0 = sRec[3 * fi], r1 = sRec[3 * fi + 1];
+            const int bc = r0.z & 3;
+            const bool in_tile = (r0.z & 4) != 0;
+            const int step = ((r0.z >> 8) & 255) - 128, vstr = r0.z >> 16;
+            const float nx = __int_as_float(r1.x), ny = __int_as_float(r1.y), sJ = __int_as_float(r1.z);
+            const int om = r0.x + gg, op = r0.y + step * gg;
             float Um[4], Up[4];
 #pragma unroll
-            for (int w = 0; w < 4; ++w) Um[w] = sTr[(ee * 4 + w) * NFS + fg];
+            for (int w = 0; w < 4; ++w) Um[w] = sTr[om + w * NFS];
             if (bc != 0) {
                 ghost_state(Um, bc, nx, ny, p.uinf, Up);
-            } else if (in_tile) {
-#pragma unroll
-                for (int w = 0; w < 4; ++w) Up[w] = sTr[(nbl * 4 + w) * NFS + fgn];
             } else {
+                // the neighbour's trace: in the tile's own rows (reversed
+                // along the face) or among the out-of-tile neighbour traces
+                const float* src = in_tile ? sTr : sNbv;
 #pragma unroll
-                for (int w = 0; w < 4; ++w) Up[w] = sNbv[(ee * NF + fg) * S::NBV_C + w];
+                for (int w = 0; w < 4; ++w) Up[w] = src[op + w * vstr];
             }
             float Fn[4];
             if constexpr (FLUX == 1)
@@ -726,28 +768,30 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             if constexpr (AV) {
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
-                    const float own = sQn[(ee * 4 + w) * NFS + fg];
+                    const float own = sQn[om + w * NFS];
                     float other;   // the neighbour's sqrt(eps) q.n' with n' = -n, negated
                     if (bc != 0) {
                         other = own;
                     } else if (in_tile) {
-                        other = -sQn[(nbl * 4 + w) * NFS + fgn];
+                        other = -sQn[op + w * NFS];
                     } else {
-                        other = sNbv[(ee * NF + fg) * S::NBV_C + 4 + w];
+                        other = sNbv[op + 4 + w];
                     }
                     Fn[w] -= 0.5f * (own + other);
                 }
             }
-#pragma unroll
-            for (int w = 0; w < 4; ++w)
-                sTr[(ee * 4 + w) * NFS + fg] = (Fn[w] - (sFb[ee * 8 + w] * nx + sFb[ee * 8 + 4 + w] * ny)) * sJ;
+            const float4 fo = *reinterpret_cast<const float4*>(sFbnJ + 4 * (r0.w & 0xffff));
+            sTr[om] = fmaf(Fn[0], sJ, -fo.x);
+            sTr[om + NFS] = fmaf(Fn[1], sJ, -fo.y);
+            sTr[om + 2 * NFS] = fmaf(Fn[2], sJ, -fo.z);
+            sTr[om + 3 * NFS] = fmaf(Fn[3], sJ, -fo.w);
             if (in_tile) {
-                const float* gn = sGeo + nbl * 16;
-                const float mx = gn[5 + 3 * fn], my = gn[6 + 3 * fn], sJn = gn[7 + 3 * fn];
-#pragma unroll
-                for (int w = 0; w < 4; ++w)
-                    sTr[(nbl * 4 + w) * NFS + fgn] =
-                        (-Fn[w] - (sFb[nbl * 8 + w] * mx + sFb[nbl * 8 + 4 + w] * my)) * sJn;
+                const float sJn = __int_as_float(r1.w);
+                const float4 fm = *reinterpret_cast<const float4*>(sFbnJ + 4 * (r0.w >> 16));
+                sTr[op] = fmaf(-Fn[0], sJn, -fm.x);
+                sTr[op + NFS] = fmaf(-Fn[1], sJn, -fm.y);
+                sTr[op + 2 * NFS] = fmaf(-Fn[2], sJn, -fm.z);
+                sTr[op + 3 * NFS] = fmaf(-Fn[3], sJn, -fm.w);
             }
         }
     };
