@@ -298,7 +298,9 @@ int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to);
  *     the candidates are the stage kernel's tile-pipeline configurations
  *     10 C + P that fit an SM: C CTAs per SM of P groups of 256 threads, each
  *     group working on its own tile and sharing the CTA's operator tables
- *     (21, 13, 12, or 11 where nothing larger fits).
+ *     (21, 13, 12, or 11 where nothing larger fits), and 113: three groups
+ *     with a lean per-tile layout (one operand buffer for the flux
+ *     products), offered for inviscid meshes where 13 does not fit.
  *   - Tensor-core path on tetrahedra: fixed tiles (8 tetrahedra at N = 3,
  *     16 at N = 2), nothing timed.
  * Optional outputs cand_out[8], ms_out[8] (candidates and milliseconds per
@@ -308,6 +310,16 @@ int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to);
  * the tuned quantity. */
 int dg_autotune(dg_ctx* ctx, dg_mesh m, int nsteps, int32_t* tile_e_out, int32_t* cand_out, double* ms_out,
                 int32_t* ncand_out);
+
+/* Set the stage kernel's tile-pipeline configuration of one tensor-core
+ * mesh of triangles (DG_TF32, DG_BF16X3) by hand: cfg one of the codes that
+ * fit its kernel (see dg_autotune), or 0 for the built-in default.  The
+ * other meshes of its kind keep theirs.  Optional outputs cands_out[4] (the
+ * codes that fit) and *ncand_out (their number).  Every configuration gives
+ * the same state bit for bit: a tile's arithmetic does not depend on which
+ * pipeline runs it.  Returns DG_EINVAL for another precision, a tetrahedral
+ * mesh or a code that does not fit, with nothing changed. */
+int dg_set_tc_config(dg_ctx* ctx, dg_mesh m, int32_t cfg, int32_t* cands_out, int32_t* ncand_out);
 
 /* Kernel timing for profiling (paper Sec. 4 reports run times of the time
  * loop).  dg_set_profiling(ctx, m, 1) puts CUDA event-record nodes around

@@ -90,6 +90,7 @@ def load():
         "dg_step_lserk": (I, [P, C.c_int32, D, I]),
         "dg_autotune": (I, [P, C.c_int32, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32), dp,
                             C.POINTER(C.c_int32)]),
+        "dg_set_tc_config": (I, [P, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "dg_tet_reference_nodes": (I, [I, dp]),
         "dg_tet_sizes": (I, [I, C.POINTER(C.c_int32)]),
         "dg_tet_mesh_upload": (I, [P, I, I64, P, P, dp, C.POINTER(dg_params), C.POINTER(C.c_int32)]),
@@ -331,6 +332,15 @@ def dg_autotune(ctx, m, nsteps=5):
     _check(load().dg_autotune(ctx, m, int(nsteps), C.byref(best), cand, _dptr(ms), C.byref(n)), ctx)
     table = {int(cand[i]): float(ms[i]) for i in range(n.value)}
     return int(best.value), table, (min(table, key=table.get) if table else int(best.value))
+
+
+def dg_set_tc_config(ctx, m, cfg=0):
+    """Set a tensor-core mesh's tile-pipeline configuration (0: the default);
+    returns the codes that fit its kernel."""
+    cand = (C.c_int32 * 4)()
+    n = C.c_int32(0)
+    _check(load().dg_set_tc_config(ctx, m, int(cfg), cand, C.byref(n)), ctx)
+    return [int(cand[i]) for i in range(n.value)]
 
 
 def dg_kernel_times(ctx, m):

@@ -1620,6 +1620,26 @@ static int autotune_tc(dg_ctx* ctx, MeshData* m, int nsteps, int32_t* tile_e_out
     return check_device_errors(ctx);
 }
 
+int dg_set_tc_config(dg_ctx* ctx, dg_mesh h, int32_t cfg, int32_t* cands_out, int32_t* ncand_out) {
+    if (!ctx) return fail(ctx, DG_EINVAL, "NULL argument");
+    MeshData* m = find(ctx, h);
+    if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
+    if (ncand_out) *ncand_out = 0;
+    if (!tensor_prec(m->prec) || m->dim != 2) return fail(ctx, DG_EINVAL, "not a tensor-core mesh of triangles");
+    int list[4];
+    const int nl = dispatch_tc_configs(m->N, m->p.av_on, list);
+    if (nl <= 0) return fail(ctx, DG_EINVAL, "no tile-pipeline configuration fits");
+    if (cfg != 0 && std::find(list, list + nl, (int)cfg) == list + nl)
+        return fail(ctx, DG_EINVAL, "configuration does not fit this mesh's kernel");
+    for (int c = 0; c < nl; ++c)
+        if (cands_out) cands_out[c] = list[c];
+    if (ncand_out) *ncand_out = nl;
+    m->tc_cfg = cfg;
+    drop_graphs(*m);
+    reset_batch(ctx);
+    return DG_OK;
+}
+
 int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t* cand_out, double* ms_out,
                 int32_t* ncand_out) {
     if (!ctx || !tile_e_out) return fail(ctx, DG_EINVAL, "NULL argument");

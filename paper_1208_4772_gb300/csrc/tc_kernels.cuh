@@ -107,8 +107,10 @@ struct TcLayout {
 // the own traces, then the face fluxes (in place), then the warp-private
 // transposes of the cubature chunks, then the epilogue rows.  Two A2
 // buffers, so that the tensor core works on one chunk while the next is
-// written.
-template <int N, bool AV, bool SENSE = AV>   // SENSE: the epilogue computes the next stage's eps
+// written; the lean layout (inviscid only) has one, so that three tile
+// pipelines fit an SM at the high degrees, where the other pipelines fill
+// the wait for each chunk's products.
+template <int N, bool AV, bool SENSE = AV, bool LEAN = false>   // SENSE: the epilogue computes the next stage's eps
 struct TcSmem {
     using D = TcDims<N>;
     using L = TcLayout<N>;
@@ -132,7 +134,8 @@ struct TcSmem {
     static constexpr int sA1 = al(OPS_END);                                  // G1 operands, then neighbour traces
     static constexpr int A1_REGION = al(mx(A1_BYTES * (AV ? 3 : 1), NBV_BYTES));
     static constexpr int A2_BYTES = 128 * 32 * 4;
-    static constexpr int NBUF = 2;
+    static constexpr int NBUF = LEAN ? 1 : 2;
+    static_assert(!(LEAN && AV), "the lean layout is inviscid");
     static constexpr int TR_FLOATS = 128 * D::NFS;
     static constexpr int WST = 32 * 18;                                      // floats per warp: cubature transpose
     static constexpr int REC = (AV ? 12 : 4) * D::NP + (AV ? 4 : 0);        // one element's U (and q, eps) record
@@ -143,30 +146,30 @@ struct TcSmem {
     static constexpr int sTR = sA2 + NBUF * A2_BYTES;
     static constexpr int sMEAN = sTR + TR_REGION;                            // [128]
     static constexpr int sGEO = sMEAN + 128 * 4;                             // [32][16]
-    static constexpr int sFB = sGEO + 32 * 16 * 4;                           // [32][8] mean flux
-    static constexpr int sSE = sFB + 32 * 8 * 4;                             // [32] sqrt(eps)
+    static constexpr int sSE = sGEO + 32 * 16 * 4;                           // [32] sqrt(eps)
     static constexpr int sNB = sSE + 32 * 4;                                 // [32] int4
     static constexpr int sLIST = sNB + 32 * 16;                              // out-of-tile faces: n, then (e,f)
     static constexpr int sFL = sLIST + 100 * 4;                              // faces owned by the tile: n, then (e,f)
     static constexpr int sND = sFL + 100 * 4;                                // [32][2] sensor sums of the new state
     static constexpr int sFC = sND + 64 * 4;                                 // [32][8] contravariant mean flux
     static constexpr int sFBN = sFC + 32 * 8 * 4;                            // [32][3][4] (F(Ubar).n) sJ per face
-    // [96] face records, 3 int4 each: in the second A2 buffer, free from the
+    // [96] face records, 3 int4 each: in the last A2 buffer, free from the
     // previous tile's end to the face chunk unless viscous chunks occupy both
     // buffers at tile start (then a region of their own)
     static constexpr bool REC_OWN = AV && D::CA >= 2;
     static constexpr int REC_BYTES = 96 * 48;
-    static constexpr int sREC = REC_OWN ? sFBN + 32 * 3 * 4 * 4 : sA2 + A2_BYTES;
+    static constexpr int sREC = REC_OWN ? sFBN + 32 * 3 * 4 * 4 : sA2 + (NBUF - 1) * A2_BYTES;
     static constexpr int TOTAL = sFBN + 32 * 3 * 4 * 4 + (REC_OWN ? REC_BYTES : 0);
     static_assert(REC_BYTES <= A2_BYTES, "face records fit an A2 buffer");
     static_assert(TOTAL + 256 <= 232448, "tensor-core tile exceeds the shared-memory limit");
-    static_assert(D::CA <= NBUF, "viscous chunks are written at tile start, one per A2 buffer");
+    static_assert(!AV || D::CA <= NBUF, "viscous chunks are written at tile start, one per A2 buffer");
     static_assert(NBB >= 32 && (REC * 4) % 16 == 0 && (32 * 4 * D::NP * 4) % 16 == 0, "bulk-copy staging layout");
     static_assert(A1_REGION >= 32 * 4 * D::NP * 4, "epilogue rows live in the G1 operand region");
     // a curved tile (CUDA-core body, with viscosity in either kind of
     // launch) overwrites the dynamic region; the mbarriers and the TMEM slot
     // live in static shared memory and the operators are reloaded after it
-    static_assert(Tile<N, float>::smem_stage(AV) <= (size_t)TOTAL, "curved tile exceeds the tile's region");
+    // (the lean layout: a curved tile of fewer elements, set by the launch)
+    static_assert(LEAN || Tile<N, float>::smem_stage(AV) <= (size_t)TOTAL, "curved tile exceeds the tile's region");
 };
 
 template <int N, bool AV>
@@ -389,13 +392,13 @@ __device__ __forceinline__ void issue_tile_rows(const StageArgs<float>& p, long 
 // done (its latency is long hidden by then) and read after the cubature
 // chunks.  bars: the CTA's four mbarriers (A2 buffers 0 and 1, G1, bulk
 // copies).  Returns true if the next tile's rows were requested here.
-template <int N, bool AV, int PREC, bool SENSE = AV>
+template <int N, bool AV, int PREC, bool SENSE = AV, bool LEAN = false>
 __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long long e0, int ne, unsigned char* smem,
                                               uint32_t tmem, TcPhase& ph, int* err, bool rows_ready,
                                               int claim, int* next_tile, long long nCur, long long nAff,
                                               uint64_t* bars, const TcGroup& g) {
     using D = TcDims<N>;
-    using S = TcSmem<N, AV, SENSE>;
+    using S = TcSmem<N, AV, SENSE, LEAN>;
     constexpr int NP = D::NP, NQ = D::NQ, NG = D::NG, NF = D::NF, NPK = D::NPK, FOFF = D::FOFF;
     constexpr int N1 = D::N1, NFP = D::NFP, N2 = D::N2, NFS = D::NFS, CF = D::CF, CQ = D::CQ, CA = D::CA;
     constexpr int B2C = TcLayout<N>::B2_CHUNK;
@@ -404,11 +407,13 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     const int half = warp >> 2;                 // which half of the columns this thread loads
     const int e = row >> 2, v = row & 3;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    const uint32_t tD1 = tmem, tD1q = tmem + N1, tD2 = tmem + N1 + (AV ? 2 * NFP : 0);
+    // lean layout: D2 over D1's face columns, which are read before the
+    // first G2 product (the cubature columns lie below FOFF)
+    static_assert(!LEAN || FOFF + N2 <= N1, "D2 fits over D1's face columns");
+    const uint32_t tD1 = tmem, tD1q = tmem + N1, tD2 = LEAN ? tmem + FOFF : tmem + N1 + (AV ? 2 * NFP : 0);
 
     float* sMean = reinterpret_cast<float*>(smem + g.toff + S::sMEAN);
     float* sGeo = reinterpret_cast<float*>(smem + g.toff + S::sGEO);
-    float* sFb = reinterpret_cast<float*>(smem + g.toff + S::sFB);
     float* sSe = reinterpret_cast<float*>(smem + g.toff + S::sSE);
     int4* sNb = reinterpret_cast<int4*>(smem + g.toff + S::sNB);
     float* sTr = reinterpret_cast<float*>(smem + g.toff + S::sTR);
@@ -422,8 +427,9 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     float* sFbnJ = reinterpret_cast<float*>(smem + g.toff + S::sFBN);
     int4* sRec = reinterpret_cast<int4*>(smem + g.toff + S::sREC);
 
-    // G2 runs as a sequence of K chunks; chunk number s uses A2 buffer s % 2.
-    auto a2_buf = [&](int s) { return smem + g.toff + S::sA2 + (s & 1) * S::A2_BYTES; };
+    // G2 runs as a sequence of K chunks; chunk number s uses A2 buffer s % NBUF.
+    auto buf_of = [](int s) { return S::NBUF == 1 ? 0 : (s & 1); };
+    auto a2_buf = [&](int s) { return smem + g.toff + S::sA2 + buf_of(s) * S::A2_BYTES; };
     auto wait_buf = [&](int b) {   // every product issued from buffer b has completed
         uint32_t& w = b ? ph.w1 : ph.w0;
         const uint32_t c = b ? ph.c1 : ph.c0;
@@ -434,7 +440,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     };
     auto issue_chunk = [&](int s, int op_chunk) {   // thread 0, after the operand is visible
         issue_mma<PREC>(tD2, a2_buf(s), smem + S::sB2 + op_chunk * B2C, N2, 32, s > 0);
-        tc::mma_commit(&bars[s & 1]);
+        tc::mma_commit(&bars[buf_of(s)]);
     };
     int seq = 0;
     DGC_PHASE_BEGIN();
@@ -536,7 +542,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             for (int ca = 0; ca < CA; ++ca) issue_chunk(ca, CF + CQ + ca);
     }
     if constexpr (AV) {
-        for (int ca = 0; ca < CA; ++ca) ph.commit(ca & 1);
+        for (int ca = 0; ca < CA; ++ca) ph.commit(buf_of(ca));
         seq = CA;
     }
 
@@ -571,8 +577,6 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
 #pragma unroll
         for (int w = 0; w < 4; ++w) Ub[w] = sMean[e * 4 + w];
         euler_flux(Ub, p.gamma, Fb, Gb);
-        sFb[e * 8 + v] = Fb[v];
-        sFb[e * 8 + 4 + v] = Gb[v];
         // and its contravariant forms with the element's metric, and its
         // normal flux times sJ on each face
         const float* ge = sGeo + e * 16;
@@ -714,6 +718,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                                          __float_as_int(ge[7 + 3 * f]), __float_as_int(sJn));
         }
     }
+    if constexpr (LEAN) tc::fence_before_sync();   // D1's face columns are read: D2 may overwrite them
     g.sync();
     DGC_PHASE_MARK(3);
 
@@ -806,7 +811,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     // ---------------- face chunk: the rows of the flux region, 16 slots per half
     static_assert(CF == 1, "one face chunk");
     {
-        wait_buf(seq & 1);
+        wait_buf(buf_of(seq));
         unsigned char* A2 = a2_buf(seq);
 #pragma unroll
         for (int s0 = 0; s0 < 16; s0 += 8) {
@@ -825,7 +830,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             tc::fence_after_sync();
             issue_chunk(seq, 0);
         }
-        ph.commit(seq & 1);
+        ph.commit(buf_of(seq));
         ++seq;
     }
 
@@ -881,7 +886,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 }
             }
             __syncwarp();
-            wait_buf(seq & 1);
+            wait_buf(buf_of(seq));
             unsigned char* A2 = a2_buf(seq);
             {
                 const float2* rw = reinterpret_cast<const float2*>(wst + lane * 18);
@@ -903,7 +908,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 tc::fence_after_sync();
                 issue_chunk(seq, CF + cq);
             }
-            ph.commit(seq & 1);
+            ph.commit(buf_of(seq));
         }
     }
 
@@ -945,7 +950,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         }
     }
     wait_buf(0);
-    wait_buf(1);
+    if constexpr (S::NBUF > 1) wait_buf(1);
     tc::fence_after_sync();
     {
         float* sOut = reinterpret_cast<float*>(smem + g.toff + S::sA1);
@@ -1103,16 +1108,18 @@ __device__ __forceinline__ void load_tc_operators(const unsigned char* ops_tc, u
 // operator tables are loaded once per CTA and shared.  STRIDE: the byte
 // distance between the pipelines' per-tile regions (the larger of the
 // viscous layout and the inviscid one of an AV launch).  FITS: the
-// configuration fits an SM (shared memory, TMEM).
-template <int N, bool AV, int P_, int C_>
+// configuration fits an SM (shared memory, TMEM).  LEAN_: the lean
+// per-tile layout (one A2 buffer, D2 over D1's face columns; inviscid).
+template <int N, bool AV, int P_, int C_, bool LEAN_ = false>
 struct TcPipes {
-    using SV = TcSmem<N, AV, AV>;
-    using SI = TcSmem<N, false, AV>;
-    static constexpr int P = P_, MIN_CTAS = C_, CODE = 10 * C_ + P_;
+    static_assert(!(LEAN_ && AV), "the lean layout is inviscid");
+    using SV = TcSmem<N, AV, AV, LEAN_>;
+    using SI = TcSmem<N, false, AV, LEAN_>;
+    static constexpr int P = P_, MIN_CTAS = C_, CODE = 100 * LEAN_ + 10 * C_ + P_;
     static constexpr int mx(int a, int b) { return a > b ? a : b; }
     static constexpr int STRIDE = (mx(SV::TOTAL - SV::sA1, SI::TOTAL - SI::sA1) + 127) / 128 * 128;
-    // TMEM columns of one pipeline: D1, the q traces (AV), D2
-    static constexpr int COLS = TcDims<N>::N1 + (AV ? 2 * TcDims<N>::NFP : 0) + TcDims<N>::N2;
+    // TMEM columns of one pipeline: D1, the q traces (AV), D2 (lean: in D1)
+    static constexpr int COLS = TcDims<N>::N1 + (LEAN_ ? 0 : (AV ? 2 * TcDims<N>::NFP : 0) + TcDims<N>::N2);
     static constexpr int pow2(int c) { return c <= 32 ? 32 : 2 * pow2((c + 1) / 2); }
     static constexpr int ALLOC = pow2(P * COLS);   // one allocation for all pipelines (a power of two)
     static constexpr int BYTES = SV::TOTAL + (P - 1) * STRIDE;
@@ -1134,23 +1141,31 @@ struct TcPipes {
 
 // The candidate configurations of a degree and viscosity setting, fitting
 // ones only: two CTAs of one pipeline, one CTA of two or three pipelines,
+// three lean pipelines (113) where three full ones do not fit (inviscid),
 // and one CTA of one pipeline where nothing larger fits.  The default (the
 // first): two single-pipeline CTAs where they fit (measured: they overlap
-// the next kernel's start better), else the most pipelines that fit.
+// the next kernel's start better), else the most pipelines that fit (the
+// lean three before two full ones: measured 11% faster at N = 6).
 template <int N, bool AV>
 struct TcConfigs {
     static constexpr bool f21 = TcPipes<N, AV, 1, 2>::FITS, f12 = TcPipes<N, AV, 2, 1>::FITS,
                           f13 = TcPipes<N, AV, 3, 1>::FITS;
-    static constexpr bool f11 = !f21 && !f12 && !f13;
+    static constexpr bool lean3() {
+        if constexpr (AV) return false;
+        else return !f13 && TcPipes<N, false, 3, 1, true>::FITS;
+    }
+    static constexpr bool f113 = lean3();
+    static constexpr bool f11 = !f21 && !f12 && !f13 && !f113;
     static int list(int* out) {
         int n = 0;
         if (f21) out[n++] = 21;
         if (f13) out[n++] = 13;
+        if (f113) out[n++] = 113;
         if (f12) out[n++] = 12;
         if (f11) out[n++] = 11;
         return n;
     }
-    static constexpr int deflt() { return f21 ? 21 : f13 ? 13 : f12 ? 12 : 11; }
+    static constexpr int deflt() { return f21 ? 21 : f13 ? 13 : f113 ? 113 : f12 ? 12 : 11; }
 };
 
 // Persistent grid, one CTA per SM.  Each CTA sets up its mbarriers and TMEM
@@ -1165,10 +1180,10 @@ struct TcConfigs {
 // wrote it) runs the inviscid tile body with the next stage's sensor in its
 // epilogue: the viscous terms are sqrt(eps) q, all zero then.  The last CTA
 // resets that count for the slot's next use.
-template <int N, bool AV, int PREC, int P_, int C_>
+template <int N, bool AV, int PREC, int P_, int C_, bool LEAN_ = false>
 __global__ void __launch_bounds__(P_ * THREADS, C_)
     stage_kernel_tc(StageArgs<float> p, const unsigned char* ops_tc, int* err, int* counter, int* done) {
-    using PP = TcPipes<N, AV, P_, C_>;
+    using PP = TcPipes<N, AV, P_, C_, LEAN_>;
     constexpr int P = PP::P;
     extern __shared__ __align__(128) unsigned char smem_tc[];
     __shared__ __align__(8) uint64_t bars[4 * P];
@@ -1258,8 +1273,9 @@ __global__ void __launch_bounds__(P_ * THREADS, C_)
                     rows_ready = stage_tile_tc<N, false, PREC, true>(p, e0, ne, smem_tc, tmem, ph, err, rows_ready,
                                                                      claim, &s_tile[pipe], nCur, nAff, pb, g);
             } else {
-                rows_ready = stage_tile_tc<N, false, PREC>(p, e0, ne, smem_tc, tmem, ph, err, rows_ready, claim,
-                                                           &s_tile[pipe], nCur, nAff, pb, g);
+                rows_ready = stage_tile_tc<N, false, PREC, false, LEAN_>(p, e0, ne, smem_tc, tmem, ph, err,
+                                                                         rows_ready, claim, &s_tile[pipe], nCur,
+                                                                         nAff, pb, g);
             }
         }
         t = s_tile[pipe];
@@ -1285,18 +1301,18 @@ __global__ void __launch_bounds__(P_ * THREADS, C_)
 
 // Persistent grid size per instantiation: SMs x resident CTAs, set by
 // prepare_tc before any launch.
-template <int N, bool AV, int PREC, int P_, int C_>
+template <int N, bool AV, int PREC, int P_, int C_, bool LEAN_ = false>
 struct TcGrid {
     static inline int ctas = 0;
 };
 
-template <int N, bool AV, int PREC, int P_, int C_>
+template <int N, bool AV, int PREC, int P_, int C_, bool LEAN_ = false>
 int prepare_tc_t() {
-    using PP = TcPipes<N, AV, P_, C_>;
+    using PP = TcPipes<N, AV, P_, C_, LEAN_>;
     if constexpr (!PP::FITS) {
         return 0;
     } else {
-        auto kern = stage_kernel_tc<N, AV, PREC, P_, C_>;
+        auto kern = stage_kernel_tc<N, AV, PREC, P_, C_, LEAN_>;
         const int sm = PP::BYTES;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
         if (e != cudaSuccess) return (int)e;
@@ -1311,23 +1327,23 @@ int prepare_tc_t() {
         if (getenv("DGC_VERBOSE"))
             fprintf(stderr, "dgcurved: stage_kernel_tc N=%d AV=%d config %d: %d CTAs per SM, %d B shared memory\n", N,
                     (int)AV, PP::CODE, occ, sm);
-        TcGrid<N, AV, PREC, P_, C_>::ctas = nsm * occ;
+        TcGrid<N, AV, PREC, P_, C_, LEAN_>::ctas = nsm * occ;
         return 0;
     }
 }
 
 // err[0]: error word; err[1]: tile counter, err[3]: CTAs done (both zero
 // between launches: the last CTA resets them).
-template <int N, bool AV, int PREC, int P_, int C_>
+template <int N, bool AV, int PREC, int P_, int C_, bool LEAN_ = false>
 int launch_stage_tc_t(const StageArgs<float>& a, const unsigned char* ops_tc, int* err, cudaStream_t st) {
-    using PP = TcPipes<N, AV, P_, C_>;
+    using PP = TcPipes<N, AV, P_, C_, LEAN_>;
     if constexpr (!PP::FITS) {
         return (int)cudaErrorInvalidConfiguration;
     } else {
         constexpr int ET = TcDims<N>::E, EC = PP::EC;
         const long long tiles = (a.Kaff + ET - 1) / ET + (a.K - a.Kaff + EC - 1) / EC;
         if (tiles == 0) return 0;
-        const int ctas = TcGrid<N, AV, PREC, P_, C_>::ctas;
+        const int ctas = TcGrid<N, AV, PREC, P_, C_, LEAN_>::ctas;
         if (ctas <= 0) return (int)cudaErrorNotReady;   // prepare_tc was not called
         // the tile and neighbour records travel by TMA bulk copies: 16-byte aligned
         if (((uintptr_t)a.Us | (uintptr_t)a.Un | (uintptr_t)a.Uout | (uintptr_t)a.q | (uintptr_t)a.dU |
@@ -1335,7 +1351,7 @@ int launch_stage_tc_t(const StageArgs<float>& a, const unsigned char* ops_tc, in
             return (int)cudaErrorMisalignedAddress;
         const long long need = (tiles + PP::P - 1) / PP::P;
         const unsigned grid = (unsigned)(need < ctas ? need : ctas);
-        return (int)launch_pdl(stage_kernel_tc<N, AV, PREC, P_, C_>, grid, PP::CTA_THREADS, (size_t)PP::BYTES, st, a,
+        return (int)launch_pdl(stage_kernel_tc<N, AV, PREC, P_, C_, LEAN_>, grid, PP::CTA_THREADS, (size_t)PP::BYTES, st, a,
                                ops_tc, err, err + 1, err + 3);
     }
 }
@@ -1355,6 +1371,9 @@ int launch_stage_tc_cfg(const StageArgs<float>& a, const unsigned char* ops_tc, 
         case 13:
             if constexpr (C::f13) return launch_stage_tc_t<N, AV, PREC, 3, 1>(a, ops_tc, err, st);
             break;
+        case 113:
+            if constexpr (C::f113) return launch_stage_tc_t<N, AV, PREC, 3, 1, true>(a, ops_tc, err, st);
+            break;
         case 11:
             if constexpr (C::f11) return launch_stage_tc_t<N, AV, PREC, 1, 1>(a, ops_tc, err, st);
             break;
@@ -1369,6 +1388,7 @@ int prepare_tc_av() {
     if constexpr (C::f21) e = e ? e : prepare_tc_t<N, AV, PREC, 1, 2>();
     if constexpr (C::f12) e = e ? e : prepare_tc_t<N, AV, PREC, 2, 1>();
     if constexpr (C::f13) e = e ? e : prepare_tc_t<N, AV, PREC, 3, 1>();
+    if constexpr (C::f113) e = e ? e : prepare_tc_t<N, AV, PREC, 3, 1, true>();
     if constexpr (C::f11) e = e ? e : prepare_tc_t<N, AV, PREC, 1, 1>();
     return e;
 }

@@ -325,7 +325,7 @@ def test_tc_autotune_times_pipeline_configurations(B, ctx, kind, N, av):
         B.dg_set_state(c2, h, case["U"])
         tile, table, cfg = B.dg_autotune(c2, h, 3)
         assert tile == 32 and len(table) >= 1 and cfg in table and all(t > 0 for t in table.values()), table
-        assert set(table) <= {11, 12, 13, 21}
+        assert set(table) <= {11, 12, 13, 21, 113}
         assert np.array_equal(B.dg_get_state(c2, h, K, Np), case["U"])
         # the chosen configuration steps like the default one
         B.dg_step(c2, h, dt, 2)
@@ -333,5 +333,37 @@ def test_tc_autotune_times_pipeline_configurations(B, ctx, kind, N, av):
         h2 = upload(B, c2, case, "tf32")             # inherits the tuned configuration
         B.dg_step(c2, h2, dt, 2)
         assert np.array_equal(B.dg_get_state(c2, h2, K, Np), Ud)
+    finally:
+        B.dg_destroy(c2)
+
+
+@pytest.mark.parametrize("kind,N,av", [("cyl", 6, False), ("naca", 5, False), ("cyl", 4, False),
+                                       ("naca", 4, True), ("vortex", 3, False)])
+def test_tc_every_pipeline_configuration_steps_alike(B, ctx, kind, N, av):
+    """Every tile-pipeline configuration that fits (set by hand), the lean
+    three-pipeline layout (113: one operand buffer for the flux products,
+    D2 in D1's face columns) among them, steps bitwise like the default
+    one; a code that does not fit is refused."""
+    r, s = B.dg_reference_nodes(N)
+    case = make_case(kind, N, r, s, av=av)
+    case["U"] = case["U"].astype(np.float32).astype(np.float64)
+    dt = 0.2 * states.time_step(case["mesh"].verts, case["U"], N, eps0=0.3 if av else None)
+    K, Np = case["mesh"].K, len(r)
+    c2 = B.dg_create(0)
+    try:
+        h = upload(B, c2, case, "tf32")
+        cands = B.dg_set_tc_config(c2, h, 0)
+        B.dg_step(c2, h, dt, 2)
+        Ud = B.dg_get_state(c2, h, K, Np)
+        assert np.all(np.isfinite(Ud))
+        if N >= 5 and not av:
+            assert 113 in cands, cands
+        for cfg in cands:
+            B.dg_set_tc_config(c2, h, cfg)
+            B.dg_set_state(c2, h, case["U"])
+            B.dg_step(c2, h, dt, 2)
+            assert np.array_equal(B.dg_get_state(c2, h, K, Np), Ud), cfg
+        with pytest.raises(B.DgError):
+            B.dg_set_tc_config(c2, h, 99)
     finally:
         B.dg_destroy(c2)

@@ -80,6 +80,7 @@ def test_autotune_argument_errors(B):
     lib = B.load()
     out = ctypes.c_int32(0)
     assert lib.dg_autotune(None, 1, 5, ctypes.byref(out), None, None, None) == B.DG_EINVAL
+    assert lib.dg_set_tc_config(None, 1, 12, None, None) == B.DG_EINVAL
 
 
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
