@@ -108,8 +108,9 @@ struct TcLayout {
 // transposes of the cubature chunks, then the epilogue rows.  Two A2
 // buffers, so that the tensor core works on one chunk while the next is
 // written; the lean layout (inviscid only) has one, so that three tile
-// pipelines fit an SM at the high degrees, where the other pipelines fill
-// the wait for each chunk's products.
+// pipelines fit an SM at the high degrees, and borrows the G1 operand
+// region as the second: free from the face phase to the epilogue, when the
+// chunks after the first (which uses the first buffer) are written.
 template <int N, bool AV, bool SENSE = AV, bool LEAN = false>   // SENSE: the epilogue computes the next stage's eps
 struct TcSmem {
     using D = TcDims<N>;
@@ -143,6 +144,8 @@ struct TcSmem {
         al(mx(mx(TR_FLOATS * 4 * (AV ? 2 : 1), 8 * WST * 4), mx(TileStage<N, AV>::FLOATS * 4, 32 * REC * 4)));
     static constexpr int NBB = TR_REGION / (REC * 4);                        // neighbour records per batch
     static constexpr int sA2 = sA1 + A1_REGION;
+    static constexpr int sBUF1 = LEAN ? sA1 : sA2 + A2_BYTES;                // the second A2 buffer
+    static constexpr bool LEAN_OK = A1_REGION >= A2_BYTES;                   // (the lean layout needs it)
     static constexpr int sTR = sA2 + NBUF * A2_BYTES;
     static constexpr int sMEAN = sTR + TR_REGION;                            // [128]
     static constexpr int sGEO = sMEAN + 128 * 4;                             // [32][16]
@@ -222,6 +225,23 @@ __device__ __forceinline__ void store8(unsigned char* A, int row, int k0, int ro
         }
         *reinterpret_cast<uint4*>(A + tc::cm_offset(row, k0 * 2, rb)) = *reinterpret_cast<const uint4*>(h);
         *reinterpret_cast<uint4*>(A + half + tc::cm_offset(row, k0 * 2, rb)) = *reinterpret_cast<const uint4*>(l);
+    }
+}
+
+// Writes 2 consecutive K values (k0 even) of one row of an A operand, as
+// store8 does.
+template <int PREC>
+__device__ __forceinline__ void store2(unsigned char* A, int row, int k0, int row_k, float x0, float x1) {
+    if constexpr (PREC == PREC_TF32) {
+        *reinterpret_cast<float2*>(A + tc::cm_offset(row, k0 * 4, row_k * 4)) =
+            make_float2(tc::to_tf32(x0), tc::to_tf32(x1));
+    } else {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+        const uint32_t o = tc::cm_offset(row, k0 * 2, row_k * 2);
+        *reinterpret_cast<__nv_bfloat162*>(A + o) = __halves2bfloat162(h0, h1);
+        *reinterpret_cast<__nv_bfloat162*>(A + 128 * row_k * 2 + o) = __halves2bfloat162(l0, l1);
     }
 }
 
@@ -403,13 +423,17 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     constexpr int N1 = D::N1, NFP = D::NFP, N2 = D::N2, NFS = D::NFS, CF = D::CF, CQ = D::CQ, CA = D::CA;
     constexpr int B2C = TcLayout<N>::B2_CHUNK;
     const int tid = g.tid, warp = tid >> 5, lane = tid & 31;
-    const int row = (warp & 3) * 32 + lane;     // TMEM lane = (element, variable) row
+    // TMEM lane / operand row: within each warp's 32 lanes, variable-major
+    // (row = 32 q + 8 v + element % 8 for the element 8 q + element % 8);
+    // shared-memory arrays keep the element-major order lrow = 4 e + v
+    const int row = (warp & 3) * 32 + lane;
     const int half = warp >> 2;                 // which half of the columns this thread loads
-    const int e = row >> 2, v = row & 3;
+    const int e = (warp & 3) * 8 + (lane & 7), v = lane >> 3, lrow = e * 4 + v;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     // lean layout: D2 over D1's face columns, which are read before the
     // first G2 product (the cubature columns lie below FOFF)
     static_assert(!LEAN || FOFF + N2 <= N1, "D2 fits over D1's face columns");
+    static_assert(!LEAN || S::LEAN_OK, "the G1 operand region holds an A2 buffer");
     const uint32_t tD1 = tmem, tD1q = tmem + N1, tD2 = LEAN ? tmem + FOFF : tmem + N1 + (AV ? 2 * NFP : 0);
 
     float* sMean = reinterpret_cast<float*>(smem + g.toff + S::sMEAN);
@@ -427,9 +451,9 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     float* sFbnJ = reinterpret_cast<float*>(smem + g.toff + S::sFBN);
     int4* sRec = reinterpret_cast<int4*>(smem + g.toff + S::sREC);
 
-    // G2 runs as a sequence of K chunks; chunk number s uses A2 buffer s % NBUF.
-    auto buf_of = [](int s) { return S::NBUF == 1 ? 0 : (s & 1); };
-    auto a2_buf = [&](int s) { return smem + g.toff + S::sA2 + buf_of(s) * S::A2_BYTES; };
+    // G2 runs as a sequence of K chunks; chunk number s uses A2 buffer s % 2.
+    auto buf_of = [](int s) { return s & 1; };
+    auto a2_buf = [&](int s) { return smem + g.toff + ((s & 1) ? S::sBUF1 : S::sA2); };
     auto wait_buf = [&](int b) {   // every product issued from buffer b has completed
         uint32_t& w = b ? ph.w1 : ph.w0;
         const uint32_t c = b ? ph.c1 : ph.c0;
@@ -460,7 +484,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         float u[NP];
         float mean = 0.f;
         if (live) {
-            const float* src = sTr + TS::U + row * NP;
+            const float* src = sTr + TS::U + lrow * NP;
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
                 u[j] = src[j];
@@ -472,7 +496,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
 #pragma unroll
             for (int j = 0; j < NP; ++j) u[j] = mean;
         }
-        sMean[row] = mean;
+        sMean[lrow] = mean;
 #pragma unroll
         for (int j0 = 0; j0 < NPK; j0 += 8) {
             float x[8];
@@ -650,7 +674,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     DGC_PHASE_MARK(2);
 
     // ---------------- own traces (and sqrt(eps) q.n) to shared memory
-    const float mean_v = sMean[row];
+    const float mean_v = sMean[lrow];
     if (half == 0) {
 #pragma unroll
         for (int c0 = 0; c0 < NF; c0 += 8) {
@@ -659,14 +683,14 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             tc::tmem_ld_wait(x);
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-                if (c0 + i < NF) sTr[row * NFS + c0 + i] = x[i] + mean_v;
+                if (c0 + i < NF) sTr[lrow * NFS + c0 + i] = x[i] + mean_v;
         }
         if constexpr (D::NQF > 0) {   // the folded cubature points' values
             float x[8];
             tc::tmem_ld8(tD1 + lane_base + CQ * 16, x);
             tc::tmem_ld_wait(x);
 #pragma unroll
-            for (int m = 0; m < D::NQF; ++m) sTr[row * NFS + NF + 2 * m] = x[m] + mean_v;
+            for (int m = 0; m < D::NQF; ++m) sTr[lrow * NFS + NF + 2 * m] = x[m] + mean_v;
         }
     } else if constexpr (AV) {
         const float se = sSe[e];
@@ -681,7 +705,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 const int fg = c0 + i;
                 if (fg < NF) {
                     const int f = fg / NG;
-                    sQn[row * NFS + fg] = se * (qx[i] * sGeo[e * 16 + 5 + 3 * f] + qy[i] * sGeo[e * 16 + 6 + 3 * f]);
+                    sQn[lrow * NFS + fg] = se * (qx[i] * sGeo[e * 16 + 5 + 3 * f] + qy[i] * sGeo[e * 16 + 6 + 3 * f]);
                 }
             }
         }
@@ -819,7 +843,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int c = half * 16 + s0 + i;
-                x[i] = (c < NF + 2 * D::NQF) ? sTr[row * NFS + c] : 0.f;
+                x[i] = (c < NF + 2 * D::NQF) ? sTr[lrow * NFS + c] : 0.f;
             }
             store8<PREC>(A2, row, half * 16 + s0, 32, x);
         }
@@ -835,72 +859,46 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     }
 
     // ---------------- cubature chunks: contravariant flux deviations.  Each
-    // warp owns 8 elements (its 32 rows) and 8 of the 16 points of the chunk;
-    // the (variable x point) block is transposed through the warp's own slice
-    // of the trace region, one flux per (element, point).
+    // warp owns 8 elements (its 32 rows) and 8 of the 16 points of the
+    // chunk.  With the rows ordered (variable, element) within each warp's
+    // 32 lanes, a 16-lane TMEM load hands each thread the 4 variables of one
+    // element at 2 points: the fluxes are formed in registers and written
+    // straight into the operand, 2 K values per row.
     {
-        float* wst = sTr + warp * S::WST;
-        const int eb = (warp & 3) * 8;             // first element of this warp
-        // the lane's two (element, point) pairs keep their elements across
-        // chunks: metric and contravariant mean flux in registers
-        float cg[2][4], cfr[2][4], cfs[2][4];
+        const int el = lane >> 2, kp = 2 * (lane & 3);   // element within the warp, first point of the pair
+        const int ec = (warp & 3) * 8 + el;               // element in the tile
+        const uint32_t tq = tD1 + ((uint32_t)((warp & 3) * 32) << 16) + half * 8;
+        // the element's mean state, metric and contravariant mean flux, in
+        // registers for all chunks
+        float mu[4], cg[4], cfr[4], cfs[4];
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int el = (lane >> 3) + 4 * r;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                cg[r][i] = sGeo[(eb + el) * 16 + i];
-                cfr[r][i] = sFC[(eb + el) * 8 + i];
-                cfs[r][i] = sFC[(eb + el) * 8 + 4 + i];
-            }
+        for (int i = 0; i < 4; ++i) {
+            mu[i] = sMean[ec * 4 + i];
+            cg[i] = sGeo[ec * 16 + i];
+            cfr[i] = sFC[ec * 8 + i];
+            cfs[i] = sFC[ec * 8 + 4 + i];
         }
+        const int r0 = (warp & 3) * 32 + el;              // the element's row of variable 0
 #pragma unroll 1
         for (int cq = 0; cq < CQ; ++cq, ++seq) {
-            float x[8];
-            tc::tmem_ld8(tD1 + lane_base + cq * 16 + half * 8, x);
-            tc::tmem_ld_wait(x);
-            // [element][point][variable], element stride 36: conflict-free
+            float a[4], b[4];   // a: variables 0, 1; b: variables 2, 3 (2 points each)
+            tc::tmem_ld16x256(tq + cq * 16, a);
+            tc::tmem_ld16x256(tq + (16u << 16) + cq * 16, b);
+            tc::tmem_ld_wait4(a, b);
+            float Fr[2][4], Fs[2][4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) wst[(lane >> 2) * 36 + i * 4 + v] = x[i] + mean_v;
-            __syncwarp();
-            float4 U4[2];
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int pp = lane + 32 * r;
-                U4[r] = *reinterpret_cast<const float4*>(wst + (pp >> 3) * 36 + (pp & 7) * 4);
-            }
-            __syncwarp();
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int j = 0; j < 2; ++j) {
                 // padded points (beyond NQ) carry the element mean, a finite
                 // value, and meet zero operator columns
-                const int pp = lane + 32 * r, el = pp >> 3, ip = pp & 7;
-                const float Uc[4] = {U4[r].x, U4[r].y, U4[r].z, U4[r].w};
-                float Fr[4], Fs[4];
-                contra_flux_dev(Uc, p.gamma, cg[r], cfr[r], cfs[r], Fr, Fs);
-#pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    // rows (element, variable) with stride 18: conflict-free
-                    wst[(el * 4 + w) * 18 + ip] = Fr[w];
-                    wst[(el * 4 + w) * 18 + 8 + ip] = Fs[w];
-                }
+                const float Uc[4] = {a[j] + mu[0], a[2 + j] + mu[1], b[j] + mu[2], b[2 + j] + mu[3]};
+                contra_flux_dev(Uc, p.gamma, cg, cfr, cfs, Fr[j], Fs[j]);
             }
-            __syncwarp();
             wait_buf(buf_of(seq));
             unsigned char* A2 = a2_buf(seq);
-            {
-                const float2* rw = reinterpret_cast<const float2*>(wst + lane * 18);
-                float ar[8], as[8];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float2 a = rw[i], b = rw[4 + i];
-                    ar[2 * i] = a.x;
-                    ar[2 * i + 1] = a.y;
-                    as[2 * i] = b.x;
-                    as[2 * i + 1] = b.y;
-                }
-                store8<PREC>(A2, row, half * 8, 32, ar);
-                store8<PREC>(A2, row, 16 + half * 8, 32, as);
+            for (int w = 0; w < 4; ++w) {
+                store2<PREC>(A2, r0 + 8 * w, half * 8 + kp, 32, Fr[0][w], Fr[1][w]);
+                store2<PREC>(A2, r0 + 8 * w, 16 + half * 8 + kp, 32, Fs[0][w], Fs[1][w]);
             }
             tc::fence_async_smem();
             g.sync();
@@ -950,7 +948,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         }
     }
     wait_buf(0);
-    if constexpr (S::NBUF > 1) wait_buf(1);
+    wait_buf(1);
     tc::fence_after_sync();
     {
         float* sOut = reinterpret_cast<float*>(smem + g.toff + S::sA1);
@@ -964,7 +962,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             tc::tmem_ld_wait(x);
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-                if (i0 + i < NP) sOut[row * NP + i0 + i] = x[i] * invJ;
+                if (i0 + i < NP) sOut[lrow * NP + i0 + i] = x[i] * invJ;
         }
         tc::fence_before_sync();
         g.sync();
@@ -1126,7 +1124,7 @@ struct TcPipes {
     static constexpr int CTA_THREADS = P * THREADS;
     // per block: dynamic + static (< 512 B) + the 1 KB the runtime reserves; per SM 228 KB
     static constexpr bool FITS = BYTES + 512 + 1024 <= 232448 && C_ * (BYTES + 512 + 1024) <= 233472 &&
-                                 C_ * ALLOC <= 512;
+                                 C_ * ALLOC <= 512 && (!LEAN_ || SV::LEAN_OK);
     static_assert(SI::TOTAL <= SV::TOTAL, "the inviscid layout of an AV launch fits the viscous one");
     // elements of a curved tile: a pipeline runs it on the CUDA-core body in
     // its own per-tile region (of the smaller of the two layouts' regions)

@@ -135,6 +135,22 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
+// 16 lanes x 8 columns (warp-wide, aligned; taddr's lane field is the first
+// of the 16 lanes): thread t gets lane t/4 in v[0], v[1] and lane 8 + t/4 in
+// v[2], v[3], columns 2 (t % 4) and 2 (t % 4) + 1 of each.
+__device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, float v[4]) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait4(float a[4], float b[4]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    asm volatile("" : "+f"(a[0]), "+f"(a[1]), "+f"(a[2]), "+f"(a[3]), "+f"(b[0]), "+f"(b[1]), "+f"(b[2]), "+f"(b[3])
+                 :: "memory");
+}
 // Wait for this thread's TMEM loads; the loaded registers pass through the
 // statements below, so that no use of them is scheduled before the wait.
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
