@@ -485,11 +485,21 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         float mean = 0.f;
         if (live) {
             const float* src = sTr + TS::U + lrow * NP;
+            if constexpr (NP % 4 == 0) {   // rows on 16-byte boundaries
 #pragma unroll
-            for (int j = 0; j < NP; ++j) {
-                u[j] = src[j];
-                mean += u[j];
+                for (int j = 0; j < NP; j += 4) {
+                    const float4 q4 = *reinterpret_cast<const float4*>(src + j);
+                    u[j] = q4.x;
+                    u[j + 1] = q4.y;
+                    u[j + 2] = q4.z;
+                    u[j + 3] = q4.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < NP; ++j) u[j] = src[j];
             }
+#pragma unroll
+            for (int j = 0; j < NP; ++j) mean += u[j];
             mean *= (1.0f / NP);
         } else {
             mean = (v == 0) ? 1.f : (v == 3) ? 2.5f : 0.f;
@@ -960,9 +970,17 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             const int i0 = half * per_half + c0;
             tc::tmem_ld8(tD2 + lane_base + i0, x);
             tc::tmem_ld_wait(x);
+            if constexpr (NP % 4 == 0) {   // rows on 16-byte boundaries
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-                if (i0 + i < NP) sOut[lrow * NP + i0 + i] = x[i] * invJ;
+                for (int i = 0; i < 8; i += 4)
+                    if (i0 + i < NP)
+                        *reinterpret_cast<float4*>(sOut + lrow * NP + i0 + i) =
+                            make_float4(x[i] * invJ, x[i + 1] * invJ, x[i + 2] * invJ, x[i + 3] * invJ);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (i0 + i < NP) sOut[lrow * NP + i0 + i] = x[i] * invJ;
+            }
         }
         tc::fence_before_sync();
         g.sync();

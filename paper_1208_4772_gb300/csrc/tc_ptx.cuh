@@ -71,13 +71,33 @@ __device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier
 
 // Bounded wait for the given phase parity.  Returns false if the limit ran
 // out (the caller records an error and skips the dependent work).
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(a), "r"(parity) : "memory");
+    return done != 0;
+}
+// Bounded wait for the phase with the given parity: at most `limit` waits,
+// each suspending the thread until the phase completes or for up to about
+// 1 ms (the suspend-time hint), and at most 2 s in all.  False if the limit
+// ran out (the caller records an error and carries on).
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit = 1u << 26) {
-    uint32_t done = 0;
+    const uint32_t a = smem_addr(mbar);
+    if (mbar_try(a, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
     for (uint32_t it = 0; it < limit; ++it) {
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
                      " selp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(done) : "r"(smem_addr(mbar)), "r"(parity) : "memory");
+                     : "=r"(done) : "r"(a), "r"(parity), "r"(1000000u) : "memory");
         if (done) return true;
+        if (globaltimer_ns() - t0 > 2000000000ull) return false;
     }
     return false;
 }
