@@ -210,18 +210,24 @@ template <int PREC>
 __device__ __forceinline__ void store8(unsigned char* A, int row, int k0, int row_k, const float x[8]) {
     if constexpr (PREC == PREC_TF32) {
         const uint32_t rb = row_k * 4;
-        float4 lo = make_float4(tc::to_tf32(x[0]), tc::to_tf32(x[1]), tc::to_tf32(x[2]), tc::to_tf32(x[3]));
-        float4 hi = make_float4(tc::to_tf32(x[4]), tc::to_tf32(x[5]), tc::to_tf32(x[6]), tc::to_tf32(x[7]));
-        *reinterpret_cast<float4*>(A + tc::cm_offset(row, k0 * 4, rb)) = lo;
-        *reinterpret_cast<float4*>(A + tc::cm_offset(row, k0 * 4 + 16, rb)) = hi;
+        float y[8];
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+            y[i] = x[i];
+            y[i + 1] = x[i + 1];
+            tc::to_tf32x2(y[i], y[i + 1]);
+        }
+        *reinterpret_cast<float4*>(A + tc::cm_offset(row, k0 * 4, rb)) = make_float4(y[0], y[1], y[2], y[3]);
+        *reinterpret_cast<float4*>(A + tc::cm_offset(row, k0 * 4 + 16, rb)) = make_float4(y[4], y[5], y[6], y[7]);
     } else {
         const uint32_t rb = row_k * 2;
         const int half = 128 * row_k * 2;
-        __align__(16) __nv_bfloat16 h[8], l[8];
+        __align__(16) __nv_bfloat162 h[4], l[4];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            h[i] = __float2bfloat16_rn(x[i]);
-            l[i] = __float2bfloat16_rn(x[i] - __bfloat162float(h[i]));
+        for (int i = 0; i < 4; ++i) {
+            h[i] = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+            const float2 hf = __bfloat1622float2(h[i]);
+            l[i] = __floats2bfloat162_rn(x[2 * i] - hf.x, x[2 * i + 1] - hf.y);
         }
         *reinterpret_cast<uint4*>(A + tc::cm_offset(row, k0 * 2, rb)) = *reinterpret_cast<const uint4*>(h);
         *reinterpret_cast<uint4*>(A + half + tc::cm_offset(row, k0 * 2, rb)) = *reinterpret_cast<const uint4*>(l);
@@ -233,15 +239,14 @@ __device__ __forceinline__ void store8(unsigned char* A, int row, int k0, int ro
 template <int PREC>
 __device__ __forceinline__ void store2(unsigned char* A, int row, int k0, int row_k, float x0, float x1) {
     if constexpr (PREC == PREC_TF32) {
-        *reinterpret_cast<float2*>(A + tc::cm_offset(row, k0 * 4, row_k * 4)) =
-            make_float2(tc::to_tf32(x0), tc::to_tf32(x1));
+        tc::to_tf32x2(x0, x1);
+        *reinterpret_cast<float2*>(A + tc::cm_offset(row, k0 * 4, row_k * 4)) = make_float2(x0, x1);
     } else {
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+        const float2 hf = __bfloat1622float2(h);
         const uint32_t o = tc::cm_offset(row, k0 * 2, row_k * 2);
-        *reinterpret_cast<__nv_bfloat162*>(A + o) = __halves2bfloat162(h0, h1);
-        *reinterpret_cast<__nv_bfloat162*>(A + 128 * row_k * 2 + o) = __halves2bfloat162(l0, l1);
+        *reinterpret_cast<__nv_bfloat162*>(A + o) = h;
+        *reinterpret_cast<__nv_bfloat162*>(A + 128 * row_k * 2 + o) = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
     }
 }
 

@@ -195,6 +195,18 @@ __device__ __forceinline__ void tmem_ld_wait(float a[8], float b[8], float c[8],
     reg_fence8(d);
 }
 
+// Two values rounded to nearest TF32 (11 significant bits) by Veltkamp's
+// splitting, s = 8193 x, x' = s - (s - x), in packed FP32 arithmetic: the
+// low 13 bits of each result are zero, so that the tensor cores' truncation
+// of the operand is exact.  Equal to cvt.rna.tf32.f32 except at exact ties
+// (even here, away from zero there); NaN stays NaN, +-inf becomes NaN.
+__device__ __forceinline__ void to_tf32x2(float& a, float& b) {
+    asm("{\n .reg .b64 x, s, t, c;\n mov.b64 x, {%0, %1};\n mov.b64 c, {%2, %2};\n"
+        " fma.rn.f32x2 s, x, c, x;\n sub.rn.f32x2 t, s, x;\n sub.rn.f32x2 s, s, t;\n mov.b64 {%0, %1}, s;\n}"
+        : "+f"(a), "+f"(b)
+        : "f"(8192.0f));
+}
+
 __device__ __forceinline__ float to_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
