@@ -19,7 +19,7 @@ constexpr size_t batch_tc_smem() {
     if (n >= NLO && n <= NHI && tc_smem_bytes<n, false>() > m) m = tc_smem_bytes<n, false>();
     DGC_BT_MAX(2) DGC_BT_MAX(3) DGC_BT_MAX(4) DGC_BT_MAX(5) DGC_BT_MAX(6)
 #undef DGC_BT_MAX
-    return m;
+    return m + 1024;   // + up to 1 KB to align the layout to 1024 bytes
 }
 
 template <int NLO, int NHI>
@@ -36,7 +36,9 @@ template <int PREC, int NLO, int NHI>
 __global__ void __launch_bounds__(THREADS, 2)
     batch_stage_kernel_tc(const StageArgs<float>* args, const BatchItem* items, int nitems,
                           const unsigned char* const* ops_by_n, int* err, int* counter) {
-    extern __shared__ __align__(128) unsigned char smem_bt[];
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    // the tile layout starts on a 1024-byte boundary (128-byte swizzled operands)
+    unsigned char* smem_bt = smem_dyn + ((1024u - (tc::smem_addr(smem_dyn) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t bars[4];
     __shared__ uint32_t s_tmem;
     __shared__ int s_tile;
@@ -51,7 +53,7 @@ __global__ void __launch_bounds__(THREADS, 2)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
-    const TcGroup grp{tid, 0u, 0u};   // one tile at a time, the whole CTA
+    const TcGroup grp{tid, 0u, 0u, 1u};   // one tile at a time, the whole CTA
     TcPhase ph;
     int loaded = 0;   // degree whose operators are in shared memory (0: none)
     if (tid == 0) s_tile = atomicAdd(counter, 1);

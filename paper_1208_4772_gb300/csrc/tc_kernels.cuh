@@ -117,6 +117,7 @@ struct TcSmem {
     using L = TcLayout<N>;
     static constexpr int NCHU = D::CF + D::CQ + (AV ? D::CA : 0);  // chunks used
     static constexpr int al(int x) { return (x + 127) / 128 * 128; }
+    static constexpr int al1k(int x) { return (x + 1023) / 1024 * 1024; }
     static constexpr int mx(int a, int b) { return a > b ? a : b; }
     // constant region: operators, loaded once per CTA.  The viscous layout
     // extends the inviscid one with the sensor (SENSE) at its end: the
@@ -132,16 +133,18 @@ struct TcSmem {
     static constexpr int A1_BYTES = 128 * D::NPK * 4;
     static constexpr int NBV_C = AV ? 8 : 4;                                  // values per face point
     static constexpr int NBV_BYTES = 32 * D::NF * NBV_C * 4;
-    static constexpr int sA1 = al(OPS_END);                                  // G1 operands, then neighbour traces
-    static constexpr int A1_REGION = al(mx(A1_BYTES * (AV ? 3 : 1), NBV_BYTES));
-    static constexpr int A2_BYTES = 128 * 32 * 4;
+    // the A2 buffers (128-byte-swizzled operands) start on 1024-byte
+    // boundaries: the per-tile region and the G1 operand region are
+    // multiples of 1024 bytes
+    static constexpr int sA1 = al1k(OPS_END);                                // G1 operands, then neighbour traces
+    static constexpr int A1_REGION = al1k(mx(A1_BYTES * (AV ? 3 : 1), NBV_BYTES));
+    static constexpr int A2_BYTES = 128 * 128;                               // 128 rows of 128 bytes
     static constexpr int NBUF = LEAN ? 1 : 2;
     static_assert(!(LEAN && AV), "the lean layout is inviscid");
     static constexpr int TR_FLOATS = 128 * D::NFS;
-    static constexpr int WST = 32 * 18;                                      // floats per warp: cubature transpose
     static constexpr int REC = (AV ? 12 : 4) * D::NP + (AV ? 4 : 0);        // one element's U (and q, eps) record
     static constexpr int TR_REGION =
-        al(mx(mx(TR_FLOATS * 4 * (AV ? 2 : 1), 8 * WST * 4), mx(TileStage<N, AV>::FLOATS * 4, 32 * REC * 4)));
+        al(mx(TR_FLOATS * 4 * (AV ? 2 : 1), mx(TileStage<N, AV>::FLOATS * 4, 32 * REC * 4)));
     static constexpr int NBB = TR_REGION / (REC * 4);                        // neighbour records per batch
     static constexpr int sA2 = sA1 + A1_REGION;
     static constexpr int sBUF1 = LEAN ? sA1 : sA2 + A2_BYTES;                // the second A2 buffer
@@ -167,7 +170,11 @@ struct TcSmem {
     static_assert(TOTAL + 256 <= 232448, "tensor-core tile exceeds the shared-memory limit");
     static_assert(!AV || D::CA <= NBUF, "viscous chunks are written at tile start, one per A2 buffer");
     static_assert(NBB >= 32 && (REC * 4) % 16 == 0 && (32 * 4 * D::NP * 4) % 16 == 0, "bulk-copy staging layout");
-    static_assert(A1_REGION >= 32 * 4 * D::NP * 4, "epilogue rows live in the G1 operand region");
+    // epilogue rows: element e at floats [ES e, ES e + 4 NP); with rows on
+    // 16-byte boundaries a padding of 4 floats per element spreads the
+    // 16-byte stores of one quarter-warp over all banks
+    static constexpr int ES = (D::NP % 4 == 0) ? 4 * D::NP + 4 : 4 * D::NP;
+    static_assert(A1_REGION >= 32 * ES * 4, "epilogue rows live in the G1 operand region");
     // a curved tile (CUDA-core body, with viscosity in either kind of
     // launch) overwrites the dynamic region; the mbarriers and the TMEM slot
     // live in static shared memory and the operators are reloaded after it
@@ -247,6 +254,85 @@ __device__ __forceinline__ void store2(unsigned char* A, int row, int k0, int ro
         const uint32_t o = tc::cm_offset(row, k0 * 2, row_k * 2);
         *reinterpret_cast<__nv_bfloat162*>(A + o) = h;
         *reinterpret_cast<__nv_bfloat162*>(A + 128 * row_k * 2 + o) = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+    }
+}
+
+// Writes 8 consecutive K values (k0 multiple of 8, k0 < 32) of one row of a
+// G2 operand chunk (an A2 buffer): 128 rows of 128 bytes in the 128-byte
+// swizzled layout.  TF32: the 32 values of a row, rounded; BF16X3: the high
+// parts of the 32 values in bytes 0..63 and the low parts in bytes 64..127.
+// Two 16-byte stores either way.
+template <int PREC>
+__device__ __forceinline__ void store8_a2(unsigned char* A, int row, int k0, const float x[8]) {
+    if constexpr (PREC == PREC_TF32) {
+        float y[8];
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+            y[i] = x[i];
+            y[i + 1] = x[i + 1];
+            tc::to_tf32x2(y[i], y[i + 1]);
+        }
+        *reinterpret_cast<float4*>(A + tc::sw128_offset(row, k0 * 4)) = make_float4(y[0], y[1], y[2], y[3]);
+        *reinterpret_cast<float4*>(A + tc::sw128_offset(row, k0 * 4 + 16)) = make_float4(y[4], y[5], y[6], y[7]);
+    } else {
+        __align__(16) __nv_bfloat162 h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            h[i] = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+            const float2 hf = __bfloat1622float2(h[i]);
+            l[i] = __floats2bfloat162_rn(x[2 * i] - hf.x, x[2 * i + 1] - hf.y);
+        }
+        *reinterpret_cast<uint4*>(A + tc::sw128_offset(row, k0 * 2)) = *reinterpret_cast<const uint4*>(h);
+        *reinterpret_cast<uint4*>(A + tc::sw128_offset(row, 64 + k0 * 2)) = *reinterpret_cast<const uint4*>(l);
+    }
+}
+
+// Writes 4 consecutive K values (k0 multiple of 4, k0 < 32) of one row of
+// an A2 buffer, as store8_a2 does: one 16-byte store (TF32) or two 8-byte
+// stores (BF16X3: high and low parts).
+template <int PREC>
+__device__ __forceinline__ void store4_a2(unsigned char* A, int row, int k0, const float x[4]) {
+    if constexpr (PREC == PREC_TF32) {
+        float y0 = x[0], y1 = x[1], y2 = x[2], y3 = x[3];
+        tc::to_tf32x2(y0, y1);
+        tc::to_tf32x2(y2, y3);
+        *reinterpret_cast<float4*>(A + tc::sw128_offset(row, k0 * 4)) = make_float4(y0, y1, y2, y3);
+    } else {
+        __align__(8) __nv_bfloat162 h[2], l[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            h[i] = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+            const float2 hf = __bfloat1622float2(h[i]);
+            l[i] = __floats2bfloat162_rn(x[2 * i] - hf.x, x[2 * i + 1] - hf.y);
+        }
+        *reinterpret_cast<uint2*>(A + tc::sw128_offset(row, k0 * 2)) = *reinterpret_cast<const uint2*>(h);
+        *reinterpret_cast<uint2*>(A + tc::sw128_offset(row, 64 + k0 * 2)) = *reinterpret_cast<const uint2*>(l);
+    }
+}
+
+// Issue the products D += A2 x B^T of one G2 chunk (K = 32): A2 an A2
+// buffer (128-byte swizzled, see store8_a2), B n rows of 32 values in the
+// core-matrix layout.
+template <int PREC>
+__device__ __forceinline__ void issue_mma_a2(uint32_t d_tmem, const unsigned char* A, const unsigned char* B, int n,
+                                             bool accumulate) {
+    const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(B);
+    if constexpr (PREC == PREC_TF32) {
+        const uint32_t idesc = tc::instr_desc(2, 128, n);
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+            tc::mma_tf32(d_tmem, tc::smem_desc_sw128(a0 + ks * 32), tc::smem_desc(b0 + ks * 256, 128u), idesc,
+                         (accumulate || ks > 0) ? 1u : 0u);
+    } else {
+        const uint32_t idesc = tc::instr_desc(1, 128, n);
+        const uint32_t bh = b0, bl = b0 + n * 64;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t ah = tc::smem_desc_sw128(a0 + ks * 32), al = tc::smem_desc_sw128(a0 + 64 + ks * 32);
+            tc::mma_bf16(d_tmem, ah, tc::smem_desc(bh + ks * 256, 64u), idesc, (accumulate || ks > 0) ? 1u : 0u);
+            tc::mma_bf16(d_tmem, ah, tc::smem_desc(bl + ks * 256, 64u), idesc, 1u);
+            tc::mma_bf16(d_tmem, al, tc::smem_desc(bh + ks * 256, 64u), idesc, 1u);
+        }
     }
 }
 
@@ -332,12 +418,18 @@ __device__ __forceinline__ void tile_info(int tid, long long e0, int ne, bool av
 // the tile pipelines of a larger CTA that share its operator tables.  tid:
 // index within the group; bar: the group's named barrier (0 in a CTA of 256
 // threads); toff: byte offset of the group's per-tile shared-memory regions.
+// hbar: the first of the two named barriers of the group's halves (threads
+// 0..127 and 128..255), which work on alternate G2 chunks.
 struct TcGroup {
     int tid;
     uint32_t bar;
     uint32_t toff;
+    uint32_t hbar;
     __device__ __forceinline__ void sync() const {
         asm volatile("bar.sync %0, %1;" :: "r"(bar), "n"(THREADS) : "memory");
+    }
+    __device__ __forceinline__ void half_sync(int h) const {
+        asm volatile("bar.sync %0, %1;" :: "r"(hbar + (uint32_t)h), "n"(THREADS / 2) : "memory");
     }
 };
 
@@ -411,6 +503,19 @@ __device__ __forceinline__ void issue_tile_rows(const StageArgs<float>& p, long 
     if constexpr (EPS) tc::bulk_g2s(dst + T::E, p.eps + e0, 128u, bar);
 }
 
+// The 16 D1 columns of one cubature chunk from the 16-lane halves of a
+// warp's 32 TMEM lanes (t: the warp's lane base and the chunk's first
+// column): a, b the columns 2 (lane % 4) and + 1 of lanes 0..15 and 16..31,
+// c, d the same 8 columns further.
+__device__ __forceinline__ void tmem_ld_chunk(uint32_t t, float a[4], float b[4], float c[4], float d[4]) {
+    tc::tmem_ld16x256(t, a);
+    tc::tmem_ld16x256(t + (16u << 16), b);
+    tc::tmem_ld16x256(t + 8, c);
+    tc::tmem_ld16x256(t + (16u << 16) + 8, d);
+    tc::tmem_ld_wait4(a, b);
+    tc::tmem_ld_wait4(c, d);
+}
+
 // Tile body.  rows_ready: this tile's rows were requested by the previous
 // tile.  claim: in the last thread, the index of this CTA's next tile from
 // the atomic counter; it is stored to *next_tile once the face phase is
@@ -440,6 +545,16 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     static_assert(!LEAN || FOFF + N2 <= N1, "D2 fits over D1's face columns");
     static_assert(!LEAN || S::LEAN_OK, "the G1 operand region holds an A2 buffer");
     const uint32_t tD1 = tmem, tD1q = tmem + N1, tD2 = LEAN ? tmem + FOFF : tmem + N1 + (AV ? 2 * NFP : 0);
+    // the cubature chunks of the second half accumulate into D2b over D1's
+    // first N2 columns (those of cubature chunks 0 and 1), once both halves
+    // have read their first chunk
+    static_assert(N2 <= 32 && (CQ < 2 || N2 <= 32), "D2b lies over the columns of cubature chunks 0 and 1");
+    // with an odd number of cubature chunks the last one is shared by the
+    // halves (each thread 2 of its points) so that both halves finish together
+    constexpr bool JOINT = CQ % 2 == 1;
+    constexpr int CP = JOINT ? CQ - 1 : CQ;   // the chunks the halves take in turn
+    constexpr bool D2B = CP >= 2;
+    const uint32_t tD2b = tmem;
 
     float* sMean = reinterpret_cast<float*>(smem + g.toff + S::sMEAN);
     float* sGeo = reinterpret_cast<float*>(smem + g.toff + S::sGEO);
@@ -468,7 +583,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         }
     };
     auto issue_chunk = [&](int s, int op_chunk) {   // thread 0, after the operand is visible
-        issue_mma<PREC>(tD2, a2_buf(s), smem + S::sB2 + op_chunk * B2C, N2, 32, s > 0);
+        issue_mma_a2<PREC>(tD2, a2_buf(s), smem + S::sB2 + op_chunk * B2C, N2, s > 0);
         tc::mma_commit(&bars[buf_of(s)]);
     };
     int seq = 0;
@@ -485,7 +600,33 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     if (warp == 4)   // per-element data by a warp of the half that does not build the G1 operand
         tile_info(tid - 128, e0, ne, AV, sTr + TS::G, reinterpret_cast<const int4*>(sTr + TS::C), sTr + TS::E, sGeo,
                   sNb, sSe, sList, sFL);
-    if (half == 0) {
+    // out-of-tile neighbours: their U (and q) records by 16-byte asynchronous
+    // copies into the trace region, in batches of NBB faces (the first batch
+    // overlaps G1), then their traces at the reversed face points into the G1
+    // operand region, one item per (face, variable, half of the face points)
+    float* sRecs = sTr;
+    constexpr int NBB = S::NBB;
+    auto issue_batch = [&](int b0, int t0, int nt) {
+        // 16-byte pieces: U rows, then q rows; with AV one more item per face
+        // copies its eps (4 bytes) to the last word of the record
+        constexpr int CU = NP, CH = (AV ? 12 : 4) * NP / 4 + (AV ? 1 : 0);
+        const int nc = min(NBB, sList[0] - b0) * CH;
+        for (int c = t0; c < nc; c += nt) {
+            const int i = c / CH, j = c - i * CH;
+            const int entry = sList[1 + b0 + i];
+            const int ee = entry / 3, f = entry - ee * 3;
+            const int4 nbw = sNb[ee];
+            const long long nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
+            if (AV && j == CH - 1) {
+                tc::cp_async4(sRecs + i * S::REC + 12 * NP, p.eps + nb);
+                continue;
+            }
+            const float* src = (j < CU) ? p.Us + nb * 4 * NP + j * 4 : p.q + nb * 8 * NP + (j - CU) * 4;
+            tc::cp_async16(sRecs + i * S::REC + j * 4, src);
+        }
+    };
+
+    if (half == 0) {   // the G1 operand
         float u[NP];
         float mean = 0.f;
         if (live) {
@@ -557,8 +698,8 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                     ar[i] = se * (g[0] * a + g[1] * b);
                     as[i] = se * (g[2] * a + g[3] * b);
                 }
-                store8<PREC>(a2_buf(ca), row, k0, 32, ar);
-                store8<PREC>(a2_buf(ca), row, 16 + k0, 32, as);
+                store8_a2<PREC>(a2_buf(ca), row, k0, ar);
+                store8_a2<PREC>(a2_buf(ca), row, 16 + k0, as);
             }
         }
     }
@@ -585,32 +726,9 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         seq = CA;
     }
 
-    // out-of-tile neighbours: their U (and q) records by 16-byte asynchronous
-    // copies into the trace region, in batches of NBB faces (the first batch
-    // overlaps G1), then their traces at the reversed face points into the G1
-    // operand region, one item per (face, variable, half of the face points)
     float* sNbv = reinterpret_cast<float*>(smem + g.toff + S::sA1);
     const int nlist = sList[0];
-    auto issue_batch = [&](int b0) {
-        // 16-byte pieces: U rows, then q rows; with AV one more item per face
-        // copies its eps (4 bytes) to the last word of the record
-        constexpr int CU = NP, CH = (AV ? 12 : 4) * NP / 4 + (AV ? 1 : 0);
-        const int nc = min(S::NBB, nlist - b0) * CH;
-        for (int c = tid; c < nc; c += THREADS) {
-            const int i = c / CH, j = c - i * CH;
-            const int entry = sList[1 + b0 + i];
-            const int ee = entry / 3, f = entry - ee * 3;
-            const int4 nbw = sNb[ee];
-            const long long nb = (f == 0) ? nbw.x : (f == 1) ? nbw.y : nbw.z;
-            if (AV && j == CH - 1) {
-                tc::cp_async4(sTr + i * S::REC + 12 * NP, p.eps + nb);
-                continue;
-            }
-            const float* src = (j < CU) ? p.Us + nb * 4 * NP + j * 4 : p.q + nb * 8 * NP + (j - CU) * 4;
-            tc::cp_async16(sTr + i * S::REC + j * 4, src);
-        }
-    };
-    if (nlist > 0) issue_batch(0);
+    if (nlist > 0) issue_batch(0, tid, THREADS);
     if (tid < 128) {   // flux of the element-mean state, one (element, variable) per thread
         float Ub[4], Fb[4], Gb[4];
 #pragma unroll
@@ -631,21 +749,21 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     DGC_PHASE_MARK(1);
     {
         constexpr int GH = (NG + 1) / 2;
-        for (int b0 = 0; b0 < nlist; b0 += S::NBB) {
+        for (int b0 = 0; b0 < nlist; b0 += NBB) {
             if (b0 > 0) {
                 g.sync();   // the previous batch is consumed
-                issue_batch(b0);
+                issue_batch(b0, tid, THREADS);
             }
             tc::cp_async_wait_all();
             g.sync();
-            const int nitems = min(S::NBB, nlist - b0) * 8;
+            const int nitems = min(NBB, nlist - b0) * 8;
             for (int it = tid; it < nitems; it += THREADS) {
                 const int fi = it >> 3, w = it & 3, hp = (it >> 2) & 1;
                 const int entry = sList[1 + b0 + fi];
                 const int ee = entry / 3, f = entry - ee * 3;
                 const int4 nbw = sNb[ee];
                 const int fn = code_face(nbw.w, f);
-                const float* rec = sTr + fi * S::REC;
+                const float* rec = sRecs + fi * S::REC;
                 // the neighbour's values at the nodes of its face fn
                 constexpr int NE = D::NE;
                 const int* fmask = reinterpret_cast<const int*>(sIgF + 3 * NG * NE) + fn * NE;
@@ -860,7 +978,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 const int c = half * 16 + s0 + i;
                 x[i] = (c < NF + 2 * D::NQF) ? sTr[lrow * NFS + c] : 0.f;
             }
-            store8<PREC>(A2, row, half * 16 + s0, 32, x);
+            store8_a2<PREC>(A2, row, half * 16 + s0, x);
         }
         tc::fence_async_smem();
         g.sync();
@@ -873,60 +991,8 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         ++seq;
     }
 
-    // ---------------- cubature chunks: contravariant flux deviations.  Each
-    // warp owns 8 elements (its 32 rows) and 8 of the 16 points of the
-    // chunk.  With the rows ordered (variable, element) within each warp's
-    // 32 lanes, a 16-lane TMEM load hands each thread the 4 variables of one
-    // element at 2 points: the fluxes are formed in registers and written
-    // straight into the operand, 2 K values per row.
-    {
-        const int el = lane >> 2, kp = 2 * (lane & 3);   // element within the warp, first point of the pair
-        const int ec = (warp & 3) * 8 + el;               // element in the tile
-        const uint32_t tq = tD1 + ((uint32_t)((warp & 3) * 32) << 16) + half * 8;
-        // the element's mean state, metric and contravariant mean flux, in
-        // registers for all chunks
-        float mu[4], cg[4], cfr[4], cfs[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            mu[i] = sMean[ec * 4 + i];
-            cg[i] = sGeo[ec * 16 + i];
-            cfr[i] = sFC[ec * 8 + i];
-            cfs[i] = sFC[ec * 8 + 4 + i];
-        }
-        const int r0 = (warp & 3) * 32 + el;              // the element's row of variable 0
-#pragma unroll 1
-        for (int cq = 0; cq < CQ; ++cq, ++seq) {
-            float a[4], b[4];   // a: variables 0, 1; b: variables 2, 3 (2 points each)
-            tc::tmem_ld16x256(tq + cq * 16, a);
-            tc::tmem_ld16x256(tq + (16u << 16) + cq * 16, b);
-            tc::tmem_ld_wait4(a, b);
-            float Fr[2][4], Fs[2][4];
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                // padded points (beyond NQ) carry the element mean, a finite
-                // value, and meet zero operator columns
-                const float Uc[4] = {a[j] + mu[0], a[2 + j] + mu[1], b[j] + mu[2], b[2 + j] + mu[3]};
-                contra_flux_dev(Uc, p.gamma, cg, cfr, cfs, Fr[j], Fs[j]);
-            }
-            wait_buf(buf_of(seq));
-            unsigned char* A2 = a2_buf(seq);
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                store2<PREC>(A2, r0 + 8 * w, half * 8 + kp, 32, Fr[0][w], Fr[1][w]);
-                store2<PREC>(A2, r0 + 8 * w, 16 + half * 8 + kp, 32, Fs[0][w], Fs[1][w]);
-            }
-            tc::fence_async_smem();
-            g.sync();
-            if (tid == 0) {
-                tc::fence_after_sync();
-                issue_chunk(seq, CF + cq);
-            }
-            ph.commit(buf_of(seq));
-        }
-    }
-
-    DGC_PHASE_MARK(6);
-    // ---------------- the next tile's rows into the (now free) trace region
+    // ---------------- the next tile's rows into the trace region, free now
+    // that the face chunk's operand is written
     bool pre = false;
     {
         const long long tn = *next_tile;
@@ -939,12 +1005,204 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         }
     }
 
+    // ---------------- cubature chunks: contravariant flux deviations.  The
+    // two halves of the group work on alternate chunks (half h: chunks h,
+    // h + 2, ...), each with its own A2 buffer (h), named barrier and MMA
+    // issuer (its thread 0); half 0 accumulates into D2 after the face
+    // chunk, half 1 into D2b.  Each warp of a half owns 8 elements (its 32
+    // rows); with the rows ordered (variable, element) within the warp's 32
+    // lanes, 16-lane TMEM loads hand each thread the 4 variables of one
+    // element at 4 points of the chunk (2g, 2g + 1, 2g + 8, 2g + 9 with g =
+    // lane % 4).  The chunk's K slots are ordered so that each pair of these
+    // points has its r and s parts in 4 consecutive slots (the operator
+    // table is packed to match): each row's values of a pair go out in one
+    // 16-byte store, which the swizzled layout spreads over all banks.
+    {
+        const int el = lane >> 2, gq = lane & 3;          // element within the warp, point group
+        const int ec = (warp & 3) * 8 + el;               // element in the tile
+        const uint32_t tq = tD1 + ((uint32_t)((warp & 3) * 32) << 16);
+        // the element's mean state, metric and contravariant mean flux, in
+        // registers for all chunks
+        float mu[4], cg[4], cfr[4], cfs[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            mu[i] = sMean[ec * 4 + i];
+            cg[i] = sGeo[ec * 16 + i];
+            cfr[i] = sFC[ec * 8 + i];
+            cfs[i] = sFC[ec * 8 + 4 + i];
+        }
+        const int r0 = (warp & 3) * 32 + el;              // the element's row of variable 0
+        unsigned char* A2 = smem + g.toff + (half ? S::sBUF1 : S::sA2);
+        const uint32_t tDh = half ? tD2b : tD2;
+        // a: variables 0, 1 at points 2g, 2g + 1; b: variables 2, 3 at
+        // them; c, d: the same at points 2g + 8, 2g + 9
+        float a[4], b[4], c[4], d[4];
+        if constexpr (JOINT) {
+            // the shared last chunk: half h forms the pair h of every
+            // thread's points, into the buffer after the face chunk's
+            tc::tmem_ld16x256(tq + (CQ - 1) * 16 + 8 * half, a);
+            tc::tmem_ld16x256(tq + (16u << 16) + (CQ - 1) * 16 + 8 * half, b);
+            tc::tmem_ld_wait4(a, b);
+            float Fr[2][4], Fs[2][4];
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const float Uc[4] = {a[o] + mu[0], a[2 + o] + mu[1], b[o] + mu[2], b[2 + o] + mu[3]};
+                contra_flux_dev(Uc, p.gamma, cg, cfr, cfs, Fr[o], Fs[o]);
+            }
+            wait_buf(buf_of(seq));
+            unsigned char* AJ = a2_buf(seq);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const float x[4] = {Fr[0][w], Fr[1][w], Fs[0][w], Fs[1][w]};
+                store4_a2<PREC>(AJ, r0 + 8 * w, 8 * gq + 4 * half, x);
+            }
+            tc::fence_async_smem();
+        }
+        if (half < CP) tmem_ld_chunk(tq + half * 16, a, b, c, d);
+        if constexpr (D2B || JOINT) {
+            // the shared chunk's operand is complete, and D2b (over the
+            // columns of chunks 0 and 1) is read before half 1's first product
+            tc::fence_before_sync();
+            g.sync();
+            tc::fence_after_sync();
+        }
+        if constexpr (JOINT) {
+            if (tid == 0) issue_chunk(seq, CF + CQ - 1);
+            ph.commit(buf_of(seq));
+            ++seq;
+        }
+        bool first = true;
+#pragma unroll 1
+        for (int cq = half; cq < CP; cq += 2) {
+            if (!first) tmem_ld_chunk(tq + cq * 16, a, b, c, d);
+            // the points in two pairs, each pair's fluxes stored as soon as
+            // they are formed: (2g, 2g + 1) from a, b into slots 8g..8g+3,
+            // (2g + 8, 2g + 9) from c, d into slots 8g+4..8g+7.  Padded
+            // points (beyond NQ) carry the element mean, a finite value, and
+            // meet zero operator columns.
+#pragma unroll
+            for (int pr = 0; pr < 2; ++pr) {
+                float Fr[2][4], Fs[2][4];   // [point][variable]
+#pragma unroll
+                for (int o = 0; o < 2; ++o) {
+                    const float Uc[4] = {(pr ? c : a)[o] + mu[0], (pr ? c : a)[2 + o] + mu[1],
+                                         (pr ? d : b)[o] + mu[2], (pr ? d : b)[2 + o] + mu[3]};
+                    contra_flux_dev(Uc, p.gamma, cg, cfr, cfs, Fr[o], Fs[o]);
+                }
+                if (pr == 0) wait_buf(half);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const float x[4] = {Fr[0][w], Fr[1][w], Fs[0][w], Fs[1][w]};
+                    store4_a2<PREC>(A2, r0 + 8 * w, 8 * gq + 4 * pr, x);
+                }
+            }
+            tc::fence_async_smem();
+            g.half_sync(half);
+            if ((tid & 127) == 0) {
+                tc::fence_after_sync();
+                // half 0 accumulates onto the face (and viscous) chunks
+                issue_mma_a2<PREC>(tDh, A2, smem + S::sB2 + (CF + cq) * B2C, N2, half == 0 || !first);
+                tc::mma_commit(&bars[half]);
+            }
+            ph.commit(half);
+            first = false;
+        }
+    }
+    DGC_PHASE_MARK(6);
+
     // ---------------- epilogue: L = D2 / J into shared memory (the G1
     // operand region), then a coalesced pass over the tile for the stage
     // combination, whose inputs from global memory (U_s, and U^n or the
     // low-storage register) are loaded here, while the last products run
     const long long base = e0 * 4 * NP;
     const int n4 = ne * NP;   // float4 groups: ne * 4 * NP / 4
+    // the stage combination of 4 values: U_out = a U^n + b (U_s + dt L), or
+    // the low-storage form dU <- a dU + dt L (stored to *du), U = U_s + b dU
+    auto combine = [&](const float4 L4, const float4 s4, const float4 n4v, float4* du) -> float4 {
+        if (p.rhs_only) return L4;
+        if (p.dU) {
+            const float4 d = make_float4(p.a * n4v.x + p.dt * L4.x, p.a * n4v.y + p.dt * L4.y,
+                                         p.a * n4v.z + p.dt * L4.z, p.a * n4v.w + p.dt * L4.w);
+            *du = d;
+            return make_float4(s4.x + p.b * d.x, s4.y + p.b * d.y, s4.z + p.b * d.z, s4.w + p.b * d.w);
+        }
+        float4 r = make_float4(p.b * (s4.x + p.dt * L4.x), p.b * (s4.y + p.dt * L4.y), p.b * (s4.z + p.dt * L4.z),
+                               p.b * (s4.w + p.dt * L4.w));
+        if (p.a != 0.f) {
+            r.x += p.a * n4v.x;
+            r.y += p.a * n4v.y;
+            r.z += p.a * n4v.z;
+            r.w += p.a * n4v.w;
+        }
+        return r;
+    };
+    // rows on 16-byte boundaries and no sensor in the epilogue: each thread
+    // combines its own row's values straight from TMEM (no pass through
+    // shared memory); its U_s and U^n values are loaded here
+    constexpr bool DIRECT = (NP % 4 == 0) && !SENSE;
+    constexpr int per_half = N2 / 2;
+    static_assert(!DIRECT || per_half % 8 == 0, "whole 8-column TMEM loads per half row");
+    constexpr int NV4 = DIRECT ? per_half / 4 : 1;
+    const long long rbase = base + (long long)(e * 4 + v) * NP + half * per_half;   // this thread's first value
+    if constexpr (DIRECT) {
+        float4 rs[NV4], rn[NV4];
+        {
+            const float4* us = reinterpret_cast<const float4*>(p.Us + rbase);
+            const float4* un = reinterpret_cast<const float4*>((p.dU ? p.dU : p.Un) + rbase);
+            const bool need = !p.rhs_only && p.a != 0.f;
+#pragma unroll
+            for (int k = 0; k < NV4; ++k) {
+                const bool ok = live && half * per_half + 4 * k < NP;
+                rs[k] = (ok && !p.rhs_only) ? us[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                rn[k] = (ok && need) ? un[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        wait_buf(half);
+        {
+            constexpr uint32_t n0 = (CP + 1) / 2, n1 = CP / 2;
+            if (half) {
+                ph.c0 += n0;
+            } else {
+                ph.c1 += n1;
+            }
+        }
+        tc::fence_before_sync();
+        g.sync();
+        tc::fence_after_sync();
+        ph.w0 = ph.c0;
+        ph.w1 = ph.c1;
+        const float invJ = sGeo[e * 16 + 4];
+        float4* uo = reinterpret_cast<float4*>(p.Uout + rbase);
+        float4* du = reinterpret_cast<float4*>(p.dU ? p.dU + rbase : p.Uout + rbase);
+#pragma unroll
+        for (int c0 = 0; c0 < per_half; c0 += 8) {
+            float x[8], y[8];
+            const int i0 = half * per_half + c0;
+            tc::tmem_ld8(tD2 + lane_base + i0, x);
+            if constexpr (D2B) {
+                tc::tmem_ld8(tD2b + lane_base + i0, y);
+                tc::tmem_ld_wait(x, y);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) x[i] += y[i];
+            } else {
+                tc::tmem_ld_wait(x);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; i += 4) {
+                const int k = (c0 + i) / 4;
+                if (live && i0 + i < NP) {
+                    const float4 L4 = make_float4(x[i] * invJ, x[i + 1] * invJ, x[i + 2] * invJ, x[i + 3] * invJ);
+                    float4 dv;
+                    const float4 r = combine(L4, rs[k], rn[k], &dv);
+                    if (p.dU && !p.rhs_only) du[k] = dv;
+                    uo[k] = r;
+                }
+            }
+        }
+        g.sync();   // staging and per-element data are reused by the next tile
+        DGC_PHASE_MARK(7);
+        return pre;
+    }
     constexpr int NI = (32 * NP + THREADS - 1) / THREADS;
     float4 pre_s[NI], pre_n[NI];
     {
@@ -962,65 +1220,74 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             }
         }
     }
-    wait_buf(0);
-    wait_buf(1);
+    // every product of this half has completed; those of the other half
+    // after the barrier below (their commits are counted here without
+    // waiting for them, all of them complete then)
+    wait_buf(half);
+    {
+        constexpr uint32_t n0 = (CP + 1) / 2, n1 = CP / 2;   // cubature chunks of halves 0 and 1
+        if (half) {
+            ph.c0 += n0;
+        } else {
+            ph.c1 += n1;
+        }
+    }
+    tc::fence_before_sync();
+    g.sync();
     tc::fence_after_sync();
+    ph.w0 = ph.c0;
+    ph.w1 = ph.c1;
     {
         float* sOut = reinterpret_cast<float*>(smem + g.toff + S::sA1);
         const float invJ = sGeo[e * 16 + 4];
         constexpr int per_half = N2 / 2;
+        constexpr int ES = S::ES;
 #pragma unroll
         for (int c0 = 0; c0 < per_half; c0 += 8) {
-            float x[8];
+            float x[8], y[8];
             const int i0 = half * per_half + c0;
             tc::tmem_ld8(tD2 + lane_base + i0, x);
-            tc::tmem_ld_wait(x);
+            if constexpr (D2B) {
+                tc::tmem_ld8(tD2b + lane_base + i0, y);
+                tc::tmem_ld_wait(x, y);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) x[i] += y[i];
+            } else {
+                tc::tmem_ld_wait(x);
+            }
+            float* orow = sOut + e * ES + v * NP;
             if constexpr (NP % 4 == 0) {   // rows on 16-byte boundaries
 #pragma unroll
                 for (int i = 0; i < 8; i += 4)
                     if (i0 + i < NP)
-                        *reinterpret_cast<float4*>(sOut + lrow * NP + i0 + i) =
+                        *reinterpret_cast<float4*>(orow + i0 + i) =
                             make_float4(x[i] * invJ, x[i + 1] * invJ, x[i + 2] * invJ, x[i + 3] * invJ);
             } else {
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    if (i0 + i < NP) sOut[lrow * NP + i0 + i] = x[i] * invJ;
+                    if (i0 + i < NP) orow[i0 + i] = x[i] * invJ;
             }
         }
         tc::fence_before_sync();
         g.sync();
         float4* uo = reinterpret_cast<float4*>(p.Uout + base);
         float4* lo = reinterpret_cast<float4*>(sOut);
+        // float4 group i of the tile in the padded rows of sOut
+        auto lo_at = [&](int i) -> int {
+            if constexpr (ES == 4 * NP) return i;
+            else return i + i / NP;
+        };
         const bool sense = SENSE && p.eps_next != nullptr && !p.rhs_only;
 #pragma unroll
         for (int k = 0; k < NI; ++k) {
             const int i = tid + k * THREADS;
             if (i >= n4) break;
-            const float4 L4 = lo[i];
-            const float4 s4 = pre_s[k];
-            float4 r;
-            if (p.rhs_only) {
-                r = L4;
-            } else if (p.dU) {   // low-storage RK: dU <- a dU + dt L, U = Us + b dU
-                float4* du = reinterpret_cast<float4*>(p.dU + base);
-                const float4 d0 = pre_n[k];   // zero when a = 0
-                const float4 d = make_float4(p.a * d0.x + p.dt * L4.x, p.a * d0.y + p.dt * L4.y,
-                                             p.a * d0.z + p.dt * L4.z, p.a * d0.w + p.dt * L4.w);
-                du[i] = d;
-                r = make_float4(s4.x + p.b * d.x, s4.y + p.b * d.y, s4.z + p.b * d.z, s4.w + p.b * d.w);
-            } else {
-                r = make_float4(p.b * (s4.x + p.dt * L4.x), p.b * (s4.y + p.dt * L4.y), p.b * (s4.z + p.dt * L4.z),
-                                p.b * (s4.w + p.dt * L4.w));
-                if (p.a != 0.f) {
-                    const float4 n4v = pre_n[k];
-                    r.x += p.a * n4v.x;
-                    r.y += p.a * n4v.y;
-                    r.z += p.a * n4v.z;
-                    r.w += p.a * n4v.w;
-                }
-            }
+            const float4 L4 = lo[lo_at(i)];
+            float4 dv;   // low-storage RK: pre_n holds dU (zero when a = 0)
+            const float4 r = combine(L4, pre_s[k], pre_n[k], &dv);
+            if (p.dU && !p.rhs_only) reinterpret_cast<float4*>(p.dU + base)[i] = dv;
             uo[i] = r;
-            if (sense) lo[i] = r;
+            if (sense) lo[lo_at(i)] = r;
         }
         if constexpr (SENSE) {
             // the next stage's eps: the sensor of the new state, 4 threads per
@@ -1032,7 +1299,7 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                     constexpr int MT = (NP + 7) / 8;   // modes per thread, 8 threads per element
                     const float* sVinvT = reinterpret_cast<const float*>(smem + S::sVI);
                     const int ee = tid >> 3, sub = tid & 7;
-                    const float* rho = sOut + ee * 4 * NP;
+                    const float* rho = sOut + ee * ES;
                     float um[MT];
 #pragma unroll
                     for (int t = 0; t < MT; ++t) um[t] = 0.f;
@@ -1138,12 +1405,14 @@ struct TcPipes {
     using SI = TcSmem<N, false, AV, LEAN_>;
     static constexpr int P = P_, MIN_CTAS = C_, CODE = 100 * LEAN_ + 10 * C_ + P_;
     static constexpr int mx(int a, int b) { return a > b ? a : b; }
-    static constexpr int STRIDE = (mx(SV::TOTAL - SV::sA1, SI::TOTAL - SI::sA1) + 127) / 128 * 128;
+    static constexpr int STRIDE = (mx(SV::TOTAL - SV::sA1, SI::TOTAL - SI::sA1) + 1023) / 1024 * 1024;
     // TMEM columns of one pipeline: D1, the q traces (AV), D2 (lean: in D1)
     static constexpr int COLS = TcDims<N>::N1 + (LEAN_ ? 0 : (AV ? 2 * TcDims<N>::NFP : 0) + TcDims<N>::N2);
     static constexpr int pow2(int c) { return c <= 32 ? 32 : 2 * pow2((c + 1) / 2); }
     static constexpr int ALLOC = pow2(P * COLS);   // one allocation for all pipelines (a power of two)
-    static constexpr int BYTES = SV::TOTAL + (P - 1) * STRIDE;
+    static_assert(STRIDE % 1024 == 0 || P == 1, "pipelines' regions on 1024-byte boundaries");
+    // + up to 1 KB to align the dynamic shared memory to 1024 bytes
+    static constexpr int BYTES = SV::TOTAL + (P - 1) * STRIDE + 1024;
     static constexpr int CTA_THREADS = P * THREADS;
     // per block: dynamic + static (< 512 B) + the 1 KB the runtime reserves; per SM 228 KB
     static constexpr bool FITS = BYTES + 512 + 1024 <= 232448 && C_ * (BYTES + 512 + 1024) <= 233472 &&
@@ -1206,14 +1475,18 @@ __global__ void __launch_bounds__(P_ * THREADS, C_)
     stage_kernel_tc(StageArgs<float> p, const unsigned char* ops_tc, int* err, int* counter, int* done) {
     using PP = TcPipes<N, AV, P_, C_, LEAN_>;
     constexpr int P = PP::P;
-    extern __shared__ __align__(128) unsigned char smem_tc[];
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    // the A2 buffers' 128-byte swizzle works on address bits: the layout
+    // starts on a 1024-byte boundary (the launch adds 1 KB for this)
+    unsigned char* smem_tc = smem_dyn + ((1024u - (tc::smem_addr(smem_dyn) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t bars[4 * P];
     __shared__ uint32_t slot;
     __shared__ int s_tile[P];
     __shared__ int s_visc;
     constexpr int ET = TcDims<N>::E, EC = PP::EC, COLS = PP::COLS;
     const int tid = threadIdx.x, pipe = tid / THREADS;
-    const TcGroup g{tid - pipe * THREADS, (uint32_t)(1 + pipe), (uint32_t)(pipe * PP::STRIDE)};
+    const TcGroup g{tid - pipe * THREADS, (uint32_t)(1 + pipe), (uint32_t)(pipe * PP::STRIDE),
+                    (uint32_t)(1 + P + 2 * pipe)};
     const long long nAff = (p.Kaff + ET - 1) / ET;
     const long long nCur = (p.K - p.Kaff + EC - 1) / EC;
 #ifdef DGC_PHASE_CLOCKS
@@ -1509,9 +1782,14 @@ std::vector<uint8_t> pack_ops_tc(const RefOps& R, int prec) {
                 return 0.0;
             }
             if (c < D::CF + D::CQ) {
-                const int q = (c - D::CF) * 16 + (s & 15);
+                // slots 8 g .. 8 g + 7 hold the points one thread of the
+                // tile body forms, in two pairs: the r parts of points 2 g,
+                // 2 g + 1, their s parts, then the same of 2 g + 8, 2 g + 9
+                const int gq = s >> 3, pair = (s >> 2) & 1, part = (s >> 1) & 1, j = s & 1;
+                const int pt = 2 * gq + j + 8 * pair;
+                const int q = (c - D::CF) * 16 + pt;
                 if (q >= NQ) return 0.0;
-                return s < 16 ? R.MrW[(size_t)i * NQ + q] : R.MsW[(size_t)i * NQ + q];
+                return part == 0 ? R.MrW[(size_t)i * NQ + q] : R.MsW[(size_t)i * NQ + q];
             }
             const int j = (c - D::CF - D::CQ) * 16 + (s & 15);
             if (j >= NP) return 0.0;

@@ -41,6 +41,29 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
+// The 128-byte-swizzled K-major layout of an operand whose rows hold
+// exactly 128 bytes of K: eight rows form a 1024-byte atom (rows 128 bytes
+// apart, atoms 1024 bytes apart), and the 16-byte piece c of row r sits at
+// piece position c XOR (r mod 8) of its row.  The swizzle is applied to
+// shared-memory address bits, so an operand in this layout must start on a
+// 1024-byte boundary.  Byte offset of byte `kbyte` (0..127) of row `row`:
+__host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t kbyte) {
+    return (row >> 3) * 1024 + (row & 7) * 128 + ((((kbyte >> 4) ^ row) & 7) << 4) + (kbyte & 15);
+}
+
+// Shared-memory matrix descriptor of that layout (layout type 2 =
+// 128-byte swizzle; the stride between 8-row atoms 1024 bytes; the leading
+// offset is not used by a K-major swizzled operand and is set to 16 bytes).
+// A product over K bytes [32 k, 32 k + 32) of each row starts at saddr + 32 k.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 // Instruction descriptor: FP32 accumulate, K-major A and B, M x N.
 // fmt: 2 = TF32 (kind::tf32), 1 = BF16 (kind::f16).
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, uint32_t M, uint32_t N) {
