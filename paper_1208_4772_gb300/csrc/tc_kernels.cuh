@@ -705,13 +705,25 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
+    if constexpr (!AV) {
+        // G1 as soon as half 0 has written its operand, while warp 4 may
+        // still be forming the per-element data
+        if (half == 0) {
+            g.half_sync(0);
+            if (tid == 0) {
+                tc::fence_after_sync();
+                issue_mma<PREC>(tD1, A1, smem + S::sB1, N1, NPK, false);
+                tc::mma_commit(&bars[2]);
+            }
+        }
+    }
     g.sync();
     DGC_PHASE_MARK(0);
     tc::fence_after_sync();
 
-    // ---------------- G1: state deviations to cubature and face points; the
-    // viscous chunks of G2 start at once
-    if (tid == 0) {
+    // ---------------- G1: state deviations to cubature and face points (AV:
+    // here, after the q operands; the viscous chunks of G2 start at once)
+    if (AV && tid == 0) {
         issue_mma<PREC>(tD1, A1, smem + S::sB1, N1, NPK, false);
         if constexpr (AV) {
             issue_mma<PREC>(tD1q, A1 + S::A1_BYTES, smem + S::sB1Q, NFP, NPK, false);
@@ -991,6 +1003,14 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         ++seq;
     }
 
+    // the epilogue's inputs from global memory (U_s, and U^n or the
+    // low-storage register) into L2 while the cubature chunks run
+    if (tid == 64 && !p.rhs_only) {
+        const uint32_t nb = (uint32_t)ne * 4 * NP * 4;
+        tc::prefetch_l2(p.Us + e0 * 4 * NP, nb);
+        if (p.a != 0.f) tc::prefetch_l2((p.dU ? p.dU : p.Un) + e0 * 4 * NP, nb);
+    }
+
     // ---------------- the next tile's rows into the trace region, free now
     // that the face chunk's operand is written
     bool pre = false;
@@ -1199,7 +1219,8 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 }
             }
         }
-        g.sync();   // staging and per-element data are reused by the next tile
+        tc::fence_before_sync();   // this tile's TMEM reads precede the next tile's products
+        g.sync();                  // staging and per-element data are reused by the next tile
         DGC_PHASE_MARK(7);
         return pre;
     }
@@ -1344,7 +1365,8 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
                 }
             }
         }
-        g.sync();   // staging and per-element data are reused by the next tile
+        tc::fence_before_sync();   // this tile's TMEM reads precede the next tile's products
+        g.sync();                  // staging and per-element data are reused by the next tile
     DGC_PHASE_MARK(7);
     }
     return pre;

@@ -139,6 +139,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(mbar)) : "memory");
 }
 
+// Bulk prefetch of global memory into L2 (no completion to wait for): both
+// the address and the size multiples of 16 bytes.
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(src), "r"(bytes) : "memory");
+}
+
 // Per-thread asynchronous copies global -> shared (16 bytes through L2 only;
 // 4 bytes), and the wait for all of this thread's outstanding copies.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {

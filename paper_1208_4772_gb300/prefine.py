@@ -5,8 +5,8 @@ low-degree field instead of the freestream.
 
 run_levels(ctx, mesh, levels, ...) uploads the mesh at each degree in turn
 (curved nodes for that degree; a triangle mesh through dg_mesh_upload, a
-tetrahedral one -- a mesh with EToV -- through dg_tet_mesh_upload with its
-map applied to the nodes), starts the first level from the freestream,
+tetrahedral one -- four vertices per element -- through dg_tet_mesh_upload
+with its map applied to the nodes), starts the first level from the freestream,
 advances each level with dg_step in blocks of check_every steps and stops it
 when the largest per-variable L2 residual norm has dropped by `drop` from the
 level's first check, or reaches `target` (absolute), or max_steps.  The step
@@ -21,10 +21,16 @@ from . import binding as B
 from .inputs import curving, meshes3d, states
 
 
+def _is_tet(mesh):
+    """A tetrahedral mesh: four vertices per element (triangle meshes
+    carry EToV too, with three)."""
+    return mesh.EToV.shape[1] == 4
+
+
 def _upload(ctx, mesh, N, u_inf, prec, av_on):
     """Upload the mesh at degree N; returns (handle, nodes, variables)."""
     p = B.make_params(u_inf=u_inf, prec=prec, av_on=av_on)
-    if hasattr(mesh, "EToV"):      # tetrahedra
+    if _is_tet(mesh):
         r, s, t = B.dg_tet_reference_nodes(N)
         X = meshes3d.node_coords(mesh, r, s, t)
         return B.dg_tet_mesh_upload(ctx, N, mesh.EToV, mesh.bc, X, p), len(r), 5
@@ -39,7 +45,7 @@ def run_levels(ctx, mesh, levels, u_inf, prec="tf32", drop=1e-2, target=None, ch
     below the last stop at `drop` or max_steps_low (default max_steps); the
     last at `target` when given, else at `drop`, or max_steps."""
     prev, prevN, report = None, None, []
-    tet = hasattr(mesh, "EToV")
+    tet = _is_tet(mesh)
     for N in levels:
         h, Np, nvar = _upload(ctx, mesh, N, u_inf, prec, av_on)
         if prev is None:

@@ -153,3 +153,32 @@ def test_prefine_driver_on_tetrahedra(B, ctx):
         B.dg_mesh_free(ctx, x)
     assert U.shape == (m.K, 5, 20)
     assert np.array_equal(U, Uh)
+
+
+def test_prefine_driver_on_triangles(B, ctx):
+    """The level driver on a curved triangle mesh (the workloads' setting):
+    its final state equals the same sequence done by hand -- freestream at
+    N = 2, the level's steps, dg_prolong to N = 3, its steps -- bitwise."""
+    from paper_1208_4772_gb300 import prefine
+    from paper_1208_4772_gb300.inputs import curving, meshes
+    m = meshes.cylinder_channel(n_t=24, n_r=6, seed=1002)
+    ui = states.freestream(0.38, 0.0)
+    h, rep = prefine.run_levels(ctx, m, [2, 3], ui, prec="fp32", drop=1e-3, check_every=25, max_steps=50)
+    assert [r["N"] for r in rep] == [2, 3] and all(r["steps"] == 50 for r in rep)
+    assert all(np.isfinite(r["r_last"]) for r in rep)
+    U = B.dg_get_state(ctx, h, m.K, 10)
+    B.dg_mesh_free(ctx, h)
+    hs = []
+    for N in (2, 3):
+        r, s = B.dg_reference_nodes(N)
+        xy, _ = curving.curve_mesh(m, N, r, s)
+        hs.append(B.dg_mesh_upload(ctx, N, m.EToE, m.EToF, m.bc, xy, B.make_params(u_inf=ui, prec="fp32")))
+    B.dg_set_state(ctx, hs[0], states.uniform_state(m.K, 6, ui))
+    B.dg_step(ctx, hs[0], rep[0]["dt"], 50)
+    B.dg_prolong(ctx, hs[0], hs[1])
+    B.dg_step(ctx, hs[1], rep[1]["dt"], 50)
+    Uh = B.dg_get_state(ctx, hs[1], m.K, 10)
+    for x in hs:
+        B.dg_mesh_free(ctx, x)
+    assert U.shape == (m.K, 4, 10)
+    assert np.array_equal(U, Uh)
