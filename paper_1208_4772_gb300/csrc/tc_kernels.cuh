@@ -1094,7 +1094,21 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         bool first = true;
 #pragma unroll 1
         for (int cq = half; cq < CP; cq += 2) {
-            if (!first) tmem_ld_chunk(tq + cq * 16, a, b, c, d);
+            if (LEAN && !first) tmem_ld_chunk(tq + cq * 16, a, b, c, d);
+            // the next chunk's TMEM loads are issued now and waited for after
+            // this chunk's products are issued: their latency overlaps the
+            // flux arithmetic (the registers are read only after the wait).
+            // Not in the lean layout's kernels, whose 80 registers a thread
+            // (three pipelines per SM) leave no room for the 16 values.
+            float na[4], nb[4], nc[4], nd[4];
+            const bool more = !LEAN && cq + 2 < CP;
+            if (more) {
+                const uint32_t tn = tq + (cq + 2) * 16;
+                tc::tmem_ld16x256(tn, na);
+                tc::tmem_ld16x256(tn + (16u << 16), nb);
+                tc::tmem_ld16x256(tn + 8, nc);
+                tc::tmem_ld16x256(tn + (16u << 16) + 8, nd);
+            }
             // the points in two pairs, each pair's fluxes stored as soon as
             // they are formed: (2g, 2g + 1) from a, b into slots 8g..8g+3,
             // (2g + 8, 2g + 9) from c, d into slots 8g+4..8g+7.  Padded
@@ -1126,6 +1140,17 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             }
             ph.commit(half);
             first = false;
+            if (more) {
+                tc::tmem_ld_wait4(na, nb);
+                tc::tmem_ld_wait4(nc, nd);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    a[i] = na[i];
+                    b[i] = nb[i];
+                    c[i] = nc[i];
+                    d[i] = nd[i];
+                }
+            }
         }
     }
     DGC_PHASE_MARK(6);
