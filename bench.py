@@ -51,7 +51,13 @@ DTYPE = {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3", "fp64": "f64"}
 # products, flux, launch kind), SSP-RK3 stages only.  Each entry carries the
 # hash of the kernel sources it was taken on; a line whose sources differ
 # reports traffic null.
-TRAFFIC = {}
+TRAFFIC = {
+    # cylinder N = 6, 250k elements, inviscid launch (stage 1 of a timed step, after the L2 flush)
+    ("cylinder_m0.38_n6", "tf32", "llf", "stage"): (129.611264e6 + 72.476160e6, "f8f332a1192c"),
+    # NACA 0012 N = 4, 60k elements: a viscous launch (troubled cells) and an inviscid one
+    ("naca0012_m0.8_n4_av", "tf32", "llf", "stage_viscous"): (46.184704e6 + 0.424960e6, "f8f332a1192c"),
+    ("naca0012_m0.8_n4_av", "tf32", "llf", "stage"): (17.487872e6 + 0.000512e6, "f8f332a1192c"),
+}
 
 # the sources of each stage kernel, hashed into the traffic key above
 KERNEL_SOURCES = {"tri": ("tc_kernels.cuh", "tc_ptx.cuh", "kernels.cuh", "dg_device.h"),
@@ -239,7 +245,11 @@ def stage_kernel_bytes(K, Kc, N, av, viscous=True):
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """nvidia-smi clock / throttle sampling during the timed region: the
+    sampler runs every 20 ms from before the region (start() returns once
+    the first sample has arrived, so that the region is covered from its
+    beginning) and stop() keeps the samples read between mark() and stop()
+    (all of them if none fell inside a very short region)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -249,25 +259,35 @@ class ClockSampler:
         self.device = device
         self.lines = []
         self.proc = None
+        self.t_mark = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                                          "-i", str(self.device), "-lms", "200"],
+                                          "-i", str(self.device), "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.005)
+        self.t_mark = time.perf_counter()
+
+    def mark(self):
+        """The timed region begins now."""
+        self.t_mark = time.perf_counter()
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def stop(self):
         if self.proc is None:
             return None
+        t_end = time.perf_counter()
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -276,7 +296,8 @@ class ClockSampler:
         self.thread.join(timeout=5)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        inside = [ln for t, ln in self.lines if self.t_mark is not None and self.t_mark <= t <= t_end + 0.03]
+        for ln in (inside or [ln for _, ln in self.lines]):
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -766,6 +787,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    clocks.mark()
     times, _, _ = timed_steps(B, ctx, h, wl["dt"], args.steps, stream, flush, torch, step=step)
     torch.cuda.synchronize()
     if dist:
@@ -932,6 +954,7 @@ def run_tet(args):
     clocks = ClockSampler(0)
     clocks.start()
     torch.cuda.synchronize()
+    clocks.mark()
     times, _, _ = timed_steps(B, ctx, h, wl["dt"], args.steps, stream, flush, torch, step=step)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -1041,6 +1064,21 @@ def make_batch(n, seed0=2000):
     return reqs
 
 
+def batch_launches_per_step(reqs, prec):
+    """Kernels of one batched SSP-RK3 step: per stage one persistent launch
+    for the meshes without viscosity (a second one when a degree-6 mesh is
+    among them), and on each viscous mesh's branch its gradient and stage
+    launches (the sensor is fused into the tensor-core stage kernel; the
+    CUDA-core path launches it separately)."""
+    plain = [r for r in reqs if not r.av]
+    n = 0
+    if plain:
+        n += 3 * (2 if any(r.N == 6 for r in plain) else 1)
+    per_stage = 2 if prec in ("tf32", "bf16x3") else 3
+    n += 3 * per_stage * sum(1 for r in reqs if r.av)
+    return n
+
+
 def run_batch(args):
     """All meshes of the batch advanced together by dg_batch_step; one
     timed step = one SSP-RK3 step of every mesh.  The batch's device
@@ -1129,7 +1167,7 @@ def run_batch(args):
             "roofline": {"kernel": "batched stage kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
                          "bytes_per_step": bytes_step},
-            "cpu_baseline": None, "e2e": e2e, "gpu_launches": 3 * args.steps * (2 if any(r.N == 6 for r in reqs) else 1),
+            "cpu_baseline": None, "e2e": e2e, "gpu_launches": args.steps * batch_launches_per_step(reqs, args.prec),
             "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0

@@ -11,11 +11,12 @@ active set changes), checks each request's FP64 residual every
 is measured from arrival to retirement.
 
 Host set-up of a request (mesh generation, wall curving) happens before its
-arrival time.  The library's host half of the upload (dg_mesh_prepare:
-classification, device order, FP64 geometric factors) runs on a worker
-thread as soon as a request is known, overlapping the device's work on the
-active requests; admission is the device half (dg_mesh_upload_prepared) and
-the state upload.  The residuals of all active requests are read with one
+arrival time (the client brings its mesh).  The library's host half of the
+upload (dg_mesh_prepare: classification, device order, FP64 geometric
+factors) starts on a worker thread when the request arrives and runs while
+the device steps the active requests; the request is admitted once it is
+done and memory allows: admission is the device half
+(dg_mesh_upload_prepared) and the state upload.  The residuals of all active requests are read with one
 synchronisation per check (dg_batch_residual).
 
 Transonic requests (Mach >= av_mach) run with the Persson-Peraire
@@ -227,13 +228,20 @@ class ServeLoop:
         self._t0 = t0 = self.clock()
         pool = cf.ThreadPoolExecutor(max_workers=self.workers) if self.workers > 0 else None
         try:
-            if pool is not None:
-                for r in pending:          # host halves of the uploads, in arrival order
-                    r.prepared = pool.submit(self._prepare_host, r)
             while pending or active:
                 now = self.clock() - t0
+                if pool is not None:
+                    # the host half of each arrived request's upload starts on
+                    # a worker thread while the device steps the active ones
+                    for r in pending:
+                        if r.arrival > now:
+                            break
+                        if r.prepared is None:
+                            r.prepared = pool.submit(self._prepare_host, r)
                 while pending and pending[0].arrival <= now:
                     nxt = pending[0]
+                    if nxt.prepared is not None and not nxt.prepared.done():
+                        break                            # its host half is still running
                     curved = int(np.any(nxt.mesh.bc == 1, axis=1).sum()) if nxt.mesh is not None else 0
                     est = estimate_bytes(nxt.K, nxt.N, curved=curved, av=nxt.av,
                                          tensor=self.prec in ("tf32", "bf16x3"))
@@ -246,7 +254,7 @@ class ServeLoop:
                     active.append(req)
                 if not active:
                     if pending:
-                        time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
+                        time.sleep(max(0.001, min(0.01, pending[0].arrival - now)))
                     continue
                 self.peak_active = max(self.peak_active, len(active))
                 n = min(self.check_every, min(self.max_steps - r.steps for r in active))

@@ -196,3 +196,41 @@ def test_nonfinite_requests_restart_with_more_viscosity(monkeypatch):
                            max_retries=5)
     done = loop.run([r2])
     assert done[0].reason == "nonfinite" and done[0].eps0 == 0.3
+
+
+class SlowFakeLib(FakeLib):
+    """Host half of an upload and each chunk of steps take real time (the
+    residual read is where the loop waits for the device)."""
+
+    def dg_mesh_prepare(self, N, EToE, EToF, bc, xy, p):
+        import time
+        time.sleep(0.05)
+        return super().dg_mesh_prepare(N, EToE, EToF, bc, xy, p)
+
+    def dg_batch_residual(self, ctx, hs, allow_nonfinite=False):
+        import time
+        time.sleep(0.01)
+        return super().dg_batch_residual(ctx, hs, allow_nonfinite)
+
+
+def test_host_preparation_overlaps_device_steps(monkeypatch):
+    """A request that arrives while another is being stepped gets the host
+    half of its upload on a worker thread at its arrival, and that work
+    runs while the loop keeps stepping the active request (the event trace
+    shows preparation inside stepping intervals); it is admitted once its
+    host half is done."""
+    import time
+    fake = SlowFakeLib(decay=0.97)
+    monkeypatch.setattr(serve, "B", fake)
+    reqs = [fake_request(0, 0.0, 400), fake_request(1, 0.15, 400)]
+    loop = serve.ServeLoop(ctx=None, budget_bytes=1e12, check_every=10, max_steps=1000, clock=time.perf_counter,
+                           workers=2)
+    done = loop.run(reqs)
+    assert sorted(r.rid for r in done) == [0, 1]
+    ov = loop.overlap()
+    assert ov["prepare_s"] > 0.08 and ov["prepare_during_steps_s"] > 0.02, ov
+    starts = {rid: t for t, ev, rid in loop.trace if ev == "prepare_start"}
+    assert starts[1] >= 0.15                      # not before the request arrived
+    r1 = [r for r in done if r.rid == 1][0]
+    assert r1.admitted >= starts[1] + 0.05        # after its host half
+    assert max(len(b) for b in fake.batches) == 2
