@@ -142,6 +142,12 @@ int dg_sizes(int N, int cub_q, int32_t* out4);
  * mass matrix with its Cholesky-based inverse for curved elements, paper
  * Sec. 2 eqs. stiffness, mass, face_mass), classifies each element as affine
  * or curved, and copies everything to the device.  The state is set to 0.
+ * There is no argument for caller-computed geometric factors: on
+ * isoparametric elements they are a function of the node coordinates
+ * (paper Sec. 2, the mapping of the reference element by the collocation
+ * nodes), and the library always derives them from node_xy, so that the
+ * factors and the nodes cannot disagree (free-stream preservation rests on
+ * their consistency).
  * Errors: DG_EINVAL (bad sizes or connectivity, J <= 0 at a cubature node,
  * unsupported N or prec), DG_ENOMEM, DG_ECUDA. */
 int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int8_t* EToF,
