@@ -503,6 +503,13 @@ int dg_tet_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const
         auto it = ctx->tuned_e.find(3000 + N * 32 + (int)rs * 2);
         if (it != ctx->tuned_e.end()) m->tile_e = it->second;
     }
+    // the copies and memsets above ran on the legacy default stream, which
+    // the context's non-blocking stream does not wait for: complete them
+    // before any work of the context can touch the mesh
+    if (cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) {
+        api_free_mesh(m);
+        return api_fail(ctx, DG_ECUDA, "mesh upload synchronisation failed");
+    }
     const dg_mesh h = ctx->next_id++;
     ctx->meshes[h] = m;
     *out = h;

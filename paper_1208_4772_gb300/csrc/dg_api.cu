@@ -545,6 +545,7 @@ static int build_batch(dg_ctx* ctx, const std::vector<MeshData*>& ms, const doub
     ctx->batch_bufs = {dargs, ditems, dcnt};
     CUDA_OK(ctx, cudaMemcpy(dargs, args.data(), args.size() * sizeof(StageArgs<Real>), cudaMemcpyHostToDevice));
     CUDA_OK(ctx, cudaMemcpy(ditems, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
+    CUDA_OK(ctx, cudaStreamSynchronize(cudaStreamLegacy));   // before the context's stream reads them
     const size_t smem = batch_smem_bytes<Real>(e_by_n);
     const int grid = batch_grid<Real>(ctx->device, 0, smem);
     if (grid <= 0) return fail(ctx, DG_ECUDA, "batch kernel occupancy query failed");
@@ -556,7 +557,9 @@ static int build_batch(dg_ctx* ctx, const std::vector<MeshData*>& ms, const doub
     for (int st = 0; st < 3 && !e; ++st)
         e = launch_batch_stage<Real>((const char*)dargs + (size_t)st * n * as, (const BatchItem*)ditems,
                                      (int)items.size(), (int*)dcnt + st, grid, smem, ctx->stream);
-    return e ? fail(ctx, DG_ECUDA, "batched stage launch failed") : DG_OK;
+    return e ? fail(ctx, DG_ECUDA, std::string("batched stage launch failed: ") +
+                                       cudaGetErrorString((cudaError_t)e))
+             : DG_OK;
 }
 
 // Tensor-core batch: affine tiles of 32 elements and curved tiles of the
@@ -608,6 +611,7 @@ static int build_batch_tc(dg_ctx* ctx, const std::vector<MeshData*>& ms, const d
     CUDA_OK(ctx, cudaMemcpy(dargs, args.data(), args.size() * sizeof(StageArgs<float>), cudaMemcpyHostToDevice));
     CUDA_OK(ctx, cudaMemcpy(ditems, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
     CUDA_OK(ctx, cudaMemcpy(dops, ops.data(), ops.size() * sizeof(void*), cudaMemcpyHostToDevice));
+    CUDA_OK(ctx, cudaStreamSynchronize(cudaStreamLegacy));   // before the context's stream reads them
     const int glo = lo.empty() ? 0 : batch_tc_grid(ctx->device, prec, false);
     const int ghi = hi.empty() ? 0 : batch_tc_grid(ctx->device, prec, true);
     if ((!lo.empty() && glo <= 0) || (!hi.empty() && ghi <= 0))
@@ -627,7 +631,9 @@ static int build_batch_tc(dg_ctx* ctx, const std::vector<MeshData*>& ms, const d
                                       (const unsigned char* const*)dops, ms[0]->err, (int*)dcnt + 2 * st + 1, ghi,
                                       ctx->stream);
     }
-    return e ? fail(ctx, DG_ECUDA, "batched stage launch failed") : DG_OK;
+    return e ? fail(ctx, DG_ECUDA, std::string("batched stage launch failed: ") +
+                                       cudaGetErrorString((cudaError_t)e))
+             : DG_OK;
 }
 
 // Meshes with artificial viscosity in a batch: each runs its own stage
@@ -1107,6 +1113,13 @@ static int upload_prepared(dg_ctx* ctx, dg_prepared* pr, dg_mesh* out) {
         auto it = ctx->tuned_e.find(tune_key(m->dim, m->N, 16 + m->prec, m->p.av_on));
         if (it != ctx->tuned_e.end()) m->tc_cfg = it->second;
     }
+    // the copies and memsets above ran on the legacy default stream, which
+    // the context's non-blocking stream does not wait for: complete them
+    // before any work of the context can touch the mesh
+    if (cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) {
+        free_mesh(m);
+        return fail(ctx, DG_ECUDA, "mesh upload synchronisation failed");
+    }
     const dg_mesh h = ctx->next_id++;
     ctx->meshes[h] = m;
     *out = h;
@@ -1310,7 +1323,7 @@ int dg_residual(dg_ctx* ctx, dg_mesh h, double* out_linf, double* out_l2) {
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
     cudaSetDevice(ctx->device);
     int e = enqueue_stage(*m, m->U[0], nullptr, m->rhs, 0.0, 0.0, 0.0, 1, ctx->stream);
-    if (e) return fail(ctx, DG_ECUDA, "stage launch failed");
+    if (e) return fail(ctx, DG_ECUDA, std::string("stage launch failed: ") + cudaGetErrorString((cudaError_t)e));
     const int nv = m->nvar;
     double* out = m->red + residual_blocks() * 10;
     if (m->rsize == 8)
@@ -1348,7 +1361,7 @@ int dg_batch_residual(dg_ctx* ctx, int n, const dg_mesh* hs, double* out10) {
     for (int i = 0; i < n; ++i) {
         MeshData* m = ms[i];
         int e = enqueue_stage(*m, m->U[0], nullptr, m->rhs, 0.0, 0.0, 0.0, 1, ctx->stream);
-        if (e) return fail(ctx, DG_ECUDA, "stage launch failed");
+        if (e) return fail(ctx, DG_ECUDA, std::string("stage launch failed: ") + cudaGetErrorString((cudaError_t)e));
         double* dout = m->red + residual_blocks() * 10;
         if (m->rsize == 8)
             e = launch_residual<double>((const double*)m->rhs, m->nvar, m->K, m->Np, m->red, dout, ctx->stream);
@@ -1526,6 +1539,7 @@ int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to) {
         if (ce == cudaSuccess)
             ce = cudaMemcpy(dsrc, src.data(), src.size() * sizeof(long long), cudaMemcpyHostToDevice);
     }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(cudaStreamLegacy);   // copies complete before the kernel
     int e = (int)ce;
     if (!e)
         e = rs == 8 ? launch_prolong<double>((const double*)a->U[0], (double*)b->U[0], (const double*)dP, a->K,
