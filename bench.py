@@ -969,9 +969,11 @@ def run_tet(args):
         B.dg_set_profiling(ctx, h, 0)
         launch_ms = kt[2] / (3 * n_prof)
         launches = launches * args.steps // n_prof
+        if args.tet_av:   # each stage: the sensor, three gradient passes and the stage kernel (events wrap the last)
+            launches = args.steps * 3 * 5
     else:
         launch_ms = total_ms / args.steps / 5
-        launches = args.steps * 5
+        launches = args.steps * 5 * (5 if args.tet_av else 1)
     flops = tet_stage_flops(N) * m.K
     bytes_launch = tet_stage_bytes(m.K, info["curved"], N)
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
