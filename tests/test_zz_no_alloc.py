@@ -46,6 +46,14 @@ def test_noalloc_norms_match_dg_residual():
             got = out.cpu().numpy()
             assert np.allclose(got[:4], linf, rtol=1e-12, atol=0), (got[:4], linf)
             assert np.allclose(got[4:], l2, rtol=1e-12, atol=0), (got[4:], l2)
+            # the same on a stream of the caller's (ordered after the values
+            # are written on it; the result read after that stream finishes)
+            side = torch.cuda.Stream()
+            out2 = torch.full((8,), float("nan"), dtype=torch.float64, device="cuda")
+            side.wait_stream(torch.cuda.current_stream())
+            B.dg_residual_norms_noalloc(vals.data_ptr(), m.K, len(r), out2.data_ptr(), side.cuda_stream)
+            side.synchronize()
+            assert np.array_equal(out2.cpu().numpy(), got)
         # beyond the static scratch limit, and bad arguments: refused, nothing launched
         with pytest.raises(B.DgError) as e:
             B.dg_residual_norms_noalloc(vals.data_ptr(), 1 << 26, 28, out.data_ptr(), None)
