@@ -1188,19 +1188,48 @@ int dg_mesh_bytes(dg_ctx* ctx, dg_mesh h, int64_t* out) {
     return DG_OK;
 }
 
-// host FP64 canonical <-> device order in the mesh precision
+// host FP64 canonical <-> device order in the mesh precision.  The rows
+// are converted and reordered by up to 16 host threads (about a million
+// values or more each) in a host buffer, which is copied to or from the
+// device in one transfer.
+static void parallel_rows(long long K, size_t row, const std::function<void(long long, long long)>& body) {
+    const size_t n = (size_t)K * row;
+    unsigned T = std::thread::hardware_concurrency();
+    T = std::max(1u, std::min(std::min(T, 16u), (unsigned)std::min<size_t>(n >> 20, 1u << 20) + 1u));
+    if (T <= 1) {
+        body(0LL, K);
+        return;
+    }
+    const long long per = (K + T - 1) / T;
+    std::vector<std::thread> th;
+    th.reserve(T);
+    for (unsigned t = 0; t < T; ++t) {
+        const long long d0 = (long long)t * per, d1 = std::min<long long>(K, d0 + per);
+        if (d0 >= d1) break;
+        th.emplace_back([&body, d0, d1] { body(d0, d1); });
+    }
+    for (auto& x : th) x.join();
+}
+
 static int put_host(dg_ctx* ctx, MeshData* m, const double* U, void* dst) {
     const size_t row = (size_t)m->nvar * m->Np, n = (size_t)m->K * row;
+    const long long* perm = m->perm.data();
     cudaError_t ce;
     if (m->rsize == 8) {
         std::vector<double> buf(n);
-        for (long long d = 0; d < m->K; ++d) std::memcpy(&buf[d * row], U + m->perm[d] * row, row * 8);
+        double* b = buf.data();
+        parallel_rows(m->K, row, [&](long long d0, long long d1) {
+            for (long long d = d0; d < d1; ++d) std::memcpy(&b[d * row], U + perm[d] * row, row * 8);
+        });
         ce = cudaMemcpyAsync(dst, buf.data(), n * 8, cudaMemcpyHostToDevice, ctx->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
     } else {
         std::vector<float> buf(n);
-        for (long long d = 0; d < m->K; ++d)
-            for (size_t i = 0; i < row; ++i) buf[d * row + i] = (float)U[m->perm[d] * row + i];
+        float* b = buf.data();
+        parallel_rows(m->K, row, [&](long long d0, long long d1) {
+            for (long long d = d0; d < d1; ++d)
+                for (size_t i = 0; i < row; ++i) b[d * row + i] = (float)U[perm[d] * row + i];
+        });
         ce = cudaMemcpyAsync(dst, buf.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
     }
@@ -1210,20 +1239,29 @@ static int put_host(dg_ctx* ctx, MeshData* m, const double* U, void* dst) {
 
 static int get_host(dg_ctx* ctx, MeshData* m, const void* src, double* U) {
     const size_t row = (size_t)m->nvar * m->Np, n = (size_t)m->K * row;
+    const long long* perm = m->perm.data();
     cudaError_t ce;
     if (m->rsize == 8) {
         std::vector<double> buf(n);
         ce = cudaMemcpyAsync(buf.data(), src, n * 8, cudaMemcpyDeviceToHost, ctx->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
-        if (ce == cudaSuccess)
-            for (long long d = 0; d < m->K; ++d) std::memcpy(U + m->perm[d] * row, &buf[d * row], row * 8);
+        if (ce == cudaSuccess) {
+            const double* b = buf.data();
+            parallel_rows(m->K, row, [&](long long d0, long long d1) {
+                for (long long d = d0; d < d1; ++d) std::memcpy(U + perm[d] * row, &b[d * row], row * 8);
+            });
+        }
     } else {
         std::vector<float> buf(n);
         ce = cudaMemcpyAsync(buf.data(), src, n * 4, cudaMemcpyDeviceToHost, ctx->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
-        if (ce == cudaSuccess)
-            for (long long d = 0; d < m->K; ++d)
-                for (size_t i = 0; i < row; ++i) U[m->perm[d] * row + i] = buf[d * row + i];
+        if (ce == cudaSuccess) {
+            const float* b = buf.data();
+            parallel_rows(m->K, row, [&](long long d0, long long d1) {
+                for (long long d = d0; d < d1; ++d)
+                    for (size_t i = 0; i < row; ++i) U[perm[d] * row + i] = b[d * row + i];
+            });
+        }
     }
     if (ce != cudaSuccess) return fail(ctx, DG_ECUDA, std::string("state download: ") + cudaGetErrorString(ce));
     return DG_OK;
