@@ -53,10 +53,10 @@ DTYPE = {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3", "fp64": "f64"}
 # reports traffic null.
 TRAFFIC = {
     # cylinder N = 6, 250k elements, inviscid launch (stage 1 of a timed step, after the L2 flush)
-    ("cylinder_m0.38_n6", "tf32", "llf", "stage"): (129.611264e6 + 72.476160e6, "f8f332a1192c"),
+    ("cylinder_m0.38_n6", "tf32", "llf", "stage"): (129.754112e6 + 72.465920e6, "2342ba159b1e"),
     # NACA 0012 N = 4, 60k elements: a viscous launch (troubled cells) and an inviscid one
-    ("naca0012_m0.8_n4_av", "tf32", "llf", "stage_viscous"): (46.184704e6 + 0.424960e6, "f8f332a1192c"),
-    ("naca0012_m0.8_n4_av", "tf32", "llf", "stage"): (17.487872e6 + 0.000512e6, "f8f332a1192c"),
+    ("naca0012_m0.8_n4_av", "tf32", "llf", "stage_viscous"): (46.189824e6 + 0.414720e6, "2342ba159b1e"),
+    ("naca0012_m0.8_n4_av", "tf32", "llf", "stage"): (17.494272e6 + 0.000256e6, "2342ba159b1e"),
 }
 
 # the sources of each stage kernel, hashed into the traffic key above

@@ -210,6 +210,33 @@ __device__ __forceinline__ void contra_flux_dev(const float U[4], float gamma, c
     Fs[3] = fmaf(H, us, -fs[3]);
 }
 
+// contra_flux_dev for two points at once on packed FP32 pairs (one FMA2,
+// FADD2 or FMUL2 instruction for both points): U[w] holds variable w at the
+// two points; g, nfr, nfs are the element's metric and the negated mean
+// contravariant fluxes -fr, -fs, each value in both halves of its pair;
+// gm1 = (gamma - 1) in both halves.  Each component is rounded as the
+// scalar form's, up to the order of the two products in m_r and m_s.
+__device__ __forceinline__ void contra_flux2_dev(const float2 U[4], float2 gm1, const float2 g[4],
+                                                 const float2 nfr[4], const float2 nfs[4], float2 Fr[4],
+                                                 float2 Fs[4]) {
+    const float2 ir = make_float2(recip(U[0].x), recip(U[0].y));
+    const float2 mr = __ffma2_rn(g[1], U[2], __fmul2_rn(g[0], U[1]));
+    const float2 ms = __ffma2_rn(g[3], U[2], __fmul2_rn(g[2], U[1]));
+    const float2 ur = __fmul2_rn(mr, ir), us = __fmul2_rn(ms, ir);
+    // p = (gamma - 1) (E - |m|^2 / (2 rho))
+    const float2 m2 = __ffma2_rn(U[2], U[2], __fmul2_rn(U[1], U[1]));
+    const float2 p = __fmul2_rn(gm1, __ffma2_rn(__fmul2_rn(m2, ir), make_float2(-0.5f, -0.5f), U[3]));
+    const float2 H = __fadd2_rn(U[3], p);
+    Fr[0] = __fadd2_rn(mr, nfr[0]);
+    Fr[1] = __ffma2_rn(U[1], ur, __ffma2_rn(g[0], p, nfr[1]));
+    Fr[2] = __ffma2_rn(U[2], ur, __ffma2_rn(g[1], p, nfr[2]));
+    Fr[3] = __ffma2_rn(H, ur, nfr[3]);
+    Fs[0] = __fadd2_rn(ms, nfs[0]);
+    Fs[1] = __ffma2_rn(U[1], us, __ffma2_rn(g[2], p, nfs[1]));
+    Fs[2] = __ffma2_rn(U[2], us, __ffma2_rn(g[3], p, nfs[2]));
+    Fs[3] = __ffma2_rn(H, us, nfs[3]);
+}
+
 // Writes 8 consecutive K values (k0 multiple of 8) of one row of an A
 // operand with row_k K values.  TF32: rounded fp32; BF16X3: high part in the
 // first half of the buffer, low part (x - high) in the second half.
@@ -1041,16 +1068,30 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
         const int el = lane >> 2, gq = lane & 3;          // element within the warp, point group
         const int ec = (warp & 3) * 8 + el;               // element in the tile
         const uint32_t tq = tD1 + ((uint32_t)((warp & 3) * 32) << 16);
-        // the element's mean state, metric and contravariant mean flux, in
-        // registers for all chunks
-        float mu[4], cg[4], cfr[4], cfs[4];
+        // the element's mean state, metric and negated contravariant mean
+        // flux, each value in both halves of a pair (the flux of two points
+        // is formed with packed pair instructions), in registers for all chunks
+        float2 mu[4], cg[4], nfr[4], nfs[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            mu[i] = sMean[ec * 4 + i];
-            cg[i] = sGeo[ec * 16 + i];
-            cfr[i] = sFC[ec * 8 + i];
-            cfs[i] = sFC[ec * 8 + 4 + i];
+            const float m = sMean[ec * 4 + i], gi = sGeo[ec * 16 + i];
+            const float fr = -sFC[ec * 8 + i], fs = -sFC[ec * 8 + 4 + i];
+            mu[i] = make_float2(m, m);
+            cg[i] = make_float2(gi, gi);
+            nfr[i] = make_float2(fr, fr);
+            nfs[i] = make_float2(fs, fs);
         }
+        const float2 gm1 = make_float2(p.gamma - 1.f, p.gamma - 1.f);
+        // the fluxes of a pair of points (o = 0, 1) from its TMEM values:
+        // lo = (v0 at o = 0, v0 at o = 1, v1 at 0, v1 at 1), hi the same for
+        // variables 2 and 3
+        auto pair_flux = [&](const float lo[4], const float hi[4], float2 Fr[4], float2 Fs[4]) {
+            const float2 Uc[4] = {__fadd2_rn(make_float2(lo[0], lo[1]), mu[0]),
+                                  __fadd2_rn(make_float2(lo[2], lo[3]), mu[1]),
+                                  __fadd2_rn(make_float2(hi[0], hi[1]), mu[2]),
+                                  __fadd2_rn(make_float2(hi[2], hi[3]), mu[3])};
+            contra_flux2_dev(Uc, gm1, cg, nfr, nfs, Fr, Fs);
+        };
         const int r0 = (warp & 3) * 32 + el;              // the element's row of variable 0
         unsigned char* A2 = smem + g.toff + (half ? S::sBUF1 : S::sA2);
         const uint32_t tDh = half ? tD2b : tD2;
@@ -1063,17 +1104,13 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             tc::tmem_ld16x256(tq + (CQ - 1) * 16 + 8 * half, a);
             tc::tmem_ld16x256(tq + (16u << 16) + (CQ - 1) * 16 + 8 * half, b);
             tc::tmem_ld_wait4(a, b);
-            float Fr[2][4], Fs[2][4];
-#pragma unroll
-            for (int o = 0; o < 2; ++o) {
-                const float Uc[4] = {a[o] + mu[0], a[2 + o] + mu[1], b[o] + mu[2], b[2 + o] + mu[3]};
-                contra_flux_dev(Uc, p.gamma, cg, cfr, cfs, Fr[o], Fs[o]);
-            }
+            float2 Fr[4], Fs[4];   // [variable], the two points in .x, .y
+            pair_flux(a, b, Fr, Fs);
             wait_buf(buf_of(seq));
             unsigned char* AJ = a2_buf(seq);
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
-                const float x[4] = {Fr[0][w], Fr[1][w], Fs[0][w], Fs[1][w]};
+                const float x[4] = {Fr[w].x, Fr[w].y, Fs[w].x, Fs[w].y};
                 store4_a2<PREC>(AJ, r0 + 8 * w, 8 * gq + 4 * half, x);
             }
             tc::fence_async_smem();
@@ -1116,17 +1153,12 @@ __device__ __forceinline__ bool stage_tile_tc(const StageArgs<float>& p, long lo
             // meet zero operator columns.
 #pragma unroll
             for (int pr = 0; pr < 2; ++pr) {
-                float Fr[2][4], Fs[2][4];   // [point][variable]
-#pragma unroll
-                for (int o = 0; o < 2; ++o) {
-                    const float Uc[4] = {(pr ? c : a)[o] + mu[0], (pr ? c : a)[2 + o] + mu[1],
-                                         (pr ? d : b)[o] + mu[2], (pr ? d : b)[2 + o] + mu[3]};
-                    contra_flux_dev(Uc, p.gamma, cg, cfr, cfs, Fr[o], Fs[o]);
-                }
+                float2 Fr[4], Fs[4];   // [variable], the two points in .x, .y
+                pair_flux(pr ? c : a, pr ? d : b, Fr, Fs);
                 if (pr == 0) wait_buf(half);
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
-                    const float x[4] = {Fr[0][w], Fr[1][w], Fs[0][w], Fs[1][w]};
+                    const float x[4] = {Fr[w].x, Fr[w].y, Fs[w].x, Fs[w].y};
                     store4_a2<PREC>(A2, r0 + 8 * w, 8 * gq + 4 * pr, x);
                 }
             }
