@@ -850,14 +850,28 @@ def run_ours(args):
         step(ctx, h, wl["dt"], 1)     # capture the plain graph outside the timing
         torch.cuda.synchronize()
         U_host = np.ascontiguousarray(wl["U0"])
-        t0 = time.perf_counter()
-        B.dg_set_state(ctx, h, U_host)
-        step(ctx, h, wl["dt"], args.steps)
-        U_out = B.dg_get_state(ctx, h, m.K, Np)
-        el = time.perf_counter() - t0
+        auto = B.dg_host_io(ctx)
+
+        def e2e_run():
+            t0 = time.perf_counter()
+            B.dg_set_state(ctx, h, U_host)
+            step(ctx, h, wl["dt"], args.steps)
+            U_out = B.dg_get_state(ctx, h, m.K, Np)
+            return time.perf_counter() - t0, U_out.nbytes
+
+        # every host I/O mode the device offers, the context's own (auto) last
+        by_mode = {}
+        for mode in [x for x in ("staged", "device") if x != auto] + [auto]:
+            try:
+                B.dg_set_host_io(ctx, mode)
+            except B.DgError:
+                continue
+            el, out_bytes = e2e_run()
+            by_mode[mode] = dof_stage * nstage * args.steps / el
         nbytes = U_host.nbytes
-        e2e = {"value": dof_stage * nstage * args.steps / el, "unit": UNIT,
-               "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": U_out.nbytes / args.steps,
+        e2e = {"value": by_mode[auto], "unit": UNIT,
+               "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": out_bytes / args.steps,
+               "host_io": auto, "by_host_io": by_mode,
                "how": "dg_set_state(host FP64) + %s(%d) + dg_get_state(host FP64), wall clock"
                       % ("dg_step_lserk" if args.integrator == "lserk" else "dg_step", args.steps)}
     B.dg_mesh_free(ctx, h)
@@ -1016,7 +1030,7 @@ def run_tet(args):
         U_out = B.dg_get_state(ctx, h)
         el = time.perf_counter() - t0
         e2e = {"value": dof_stage * nstage * n_e2e / el, "unit": UNIT, "h2d_bytes_per_step": U_host.nbytes / n_e2e,
-               "d2h_bytes_per_step": U_out.nbytes / n_e2e,
+               "d2h_bytes_per_step": U_out.nbytes / n_e2e, "host_io": B.dg_host_io(ctx),
                "how": "dg_set_state(host FP64) + %s(%d) + dg_get_state(host FP64), wall clock"
                       % ("dg_step_lserk" if args.integrator == "lserk" else "dg_step", n_e2e)}
     B.dg_destroy(ctx)
@@ -1149,7 +1163,7 @@ def run_batch(args):
         el = time.perf_counter() - t0
         e2e = {"value": dof_step * args.steps / el, "unit": UNIT,
                "h2d_bytes_per_step": sum(r.U0.nbytes for r in reqs) / args.steps,
-               "d2h_bytes_per_step": out_bytes / args.steps,
+               "d2h_bytes_per_step": out_bytes / args.steps, "host_io": B.dg_host_io(ctx),
                "how": "dg_set_state x%d (host FP64) + dg_batch_step(%d) + dg_get_state x%d, wall clock"
                       % (len(reqs), args.steps, len(reqs))}
     B.dg_destroy(ctx)

@@ -119,6 +119,30 @@ int dg_create(dg_ctx** out, int device, void* cuda_stream);
 /* Free every mesh, graph and buffer of ctx, then ctx itself.  NULL is a no-op. */
 int dg_destroy(dg_ctx* ctx);
 
+/* How dg_set_state, dg_get_state and dg_eval_rhs move the host FP64 state
+ * (the conversion to and from the mesh precision and the reordering
+ * between the canonical and the device element order):
+ *   DG_HOST_IO_STAGED  up to 16 host threads convert and reorder the rows
+ *                      in a host buffer, copied in one transfer;
+ *   DG_HOST_IO_DEVICE  one kernel reads (writes) the caller's rows in
+ *                      place and converts and reorders them on the device.
+ *                      Needs coherent device access to pageable host memory
+ *                      through the host's page tables (as on Grace systems
+ *                      over NVLink-C2C): the device attributes
+ *                      PageableMemoryAccess and
+ *                      PageableMemoryAccessUsesHostPageTables both 1.
+ *   DG_HOST_IO_AUTO    STAGED (the mode a new context starts in): the
+ *                      faster of the two on GB300 with the caller's
+ *                      buffers in pageable memory.
+ * Either way the call returns when the data has arrived, so the caller's
+ * buffer may be reused at once; the results are the same bit for bit.
+ * dg_set_host_io errors: DG_EINVAL (ctx NULL, unknown mode, DEVICE without
+ * that access).  dg_host_io writes the mode in effect (STAGED or DEVICE)
+ * to *out; DG_EINVAL for NULL arguments. */
+enum dg_host_io_mode { DG_HOST_IO_AUTO = 0, DG_HOST_IO_STAGED = 1, DG_HOST_IO_DEVICE = 2 };
+int dg_set_host_io(dg_ctx* ctx, int mode);
+int dg_host_io(dg_ctx* ctx, int32_t* out);
+
 /* Collocation nodes of degree N on T (paper Sec. 2: nodes after Warburton
  * 2006, the warp & blend construction, blending parameter 0), written as
  * rs_out[N_p][2] (caller-owned).  The order is j (the s index) outer, i

@@ -64,6 +64,8 @@ def load():
     sig = {
         "dg_create": (I, [C.POINTER(P), I, P]),
         "dg_destroy": (I, [P]),
+        "dg_set_host_io": (I, [P, I]),
+        "dg_host_io": (I, [P, C.POINTER(C.c_int32)]),
         "dg_reference_nodes": (I, [I, dp]),
         "dg_sizes": (I, [I, I, C.POINTER(C.c_int32)]),
         "dg_mesh_upload": (I, [P, I, I64, P, P, P, dp, C.POINTER(dg_params), C.POINTER(C.c_int32)]),
@@ -125,6 +127,23 @@ def dg_create(device=0, stream=None):
 
 def dg_destroy(ctx):
     return _check(load().dg_destroy(ctx), None)
+
+
+HOST_IO = {"auto": 0, "staged": 1, "device": 2}
+
+
+def dg_set_host_io(ctx, mode):
+    """How dg_set_state / dg_get_state / dg_eval_rhs move host FP64 state:
+    "staged" (host threads and one copy; also "auto"), or "device" (a kernel
+    on the caller's rows through coherent host-memory access)."""
+    return _check(load().dg_set_host_io(ctx, HOST_IO[mode] if isinstance(mode, str) else int(mode)), ctx)
+
+
+def dg_host_io(ctx):
+    """The host I/O mode in effect: "staged" or "device"."""
+    out = C.c_int32()
+    _check(load().dg_host_io(ctx, C.byref(out)), ctx)
+    return {v: k for k, v in HOST_IO.items()}[out.value]
 
 
 def dg_reference_nodes(N):

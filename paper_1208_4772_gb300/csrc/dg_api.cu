@@ -764,7 +764,35 @@ int dg_create(dg_ctx** out, int device, void* cuda_stream) {
         }
         c->own_stream = true;
     }
+    int pageable = 0, host_tables = 0;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, device) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        pageable = host_tables = 0;
+    }
+    c->host_coherent = pageable == 1 && host_tables == 1;
+    c->host_io = DG_HOST_IO_STAGED;
     *out = c;
+    return DG_OK;
+}
+
+int dg_set_host_io(dg_ctx* ctx, int mode) {
+    if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    // the staged path is the faster of the two on GB300 (the device path's
+    // kernel runs at well under the link's bandwidth on pageable memory)
+    if (mode == DG_HOST_IO_AUTO) mode = DG_HOST_IO_STAGED;
+    if (mode != DG_HOST_IO_STAGED && mode != DG_HOST_IO_DEVICE)
+        return fail(ctx, DG_EINVAL, "unknown host I/O mode " + std::to_string(mode));
+    if (mode == DG_HOST_IO_DEVICE && !ctx->host_coherent)
+        return fail(ctx, DG_EINVAL, "the device has no coherent access to pageable host memory");
+    ctx->host_io = mode;
+    return DG_OK;
+}
+
+int dg_host_io(dg_ctx* ctx, int32_t* out) {
+    if (!ctx || !out) return fail(ctx, DG_EINVAL, "NULL argument");
+    *out = ctx->host_io;
     return DG_OK;
 }
 
@@ -1188,10 +1216,14 @@ int dg_mesh_bytes(dg_ctx* ctx, dg_mesh h, int64_t* out) {
     return DG_OK;
 }
 
-// host FP64 canonical <-> device order in the mesh precision.  The rows
-// are converted and reordered by up to 16 host threads (about a million
-// values or more each) in a host buffer, which is copied to or from the
-// device in one transfer.
+// host FP64 canonical <-> device order in the mesh precision.  Staged
+// (DG_HOST_IO_STAGED): the rows are converted and reordered by up to 16
+// host threads (about a million values or more each) in a host buffer,
+// which is copied to or from the device in one transfer.  Device
+// (DG_HOST_IO_DEVICE, where the device reaches pageable host memory
+// coherently): one kernel reads (writes) the caller's FP64 rows in place,
+// converting and reordering them on the device; the call returns when it
+// has completed.
 static void parallel_rows(long long K, size_t row, const std::function<void(long long, long long)>& body) {
     const size_t n = (size_t)K * row;
     unsigned T = std::thread::hardware_concurrency();
@@ -1215,7 +1247,12 @@ static int put_host(dg_ctx* ctx, MeshData* m, const double* U, void* dst) {
     const size_t row = (size_t)m->nvar * m->Np, n = (size_t)m->K * row;
     const long long* perm = m->perm.data();
     cudaError_t ce;
-    if (m->rsize == 8) {
+    if (ctx->host_io == DG_HOST_IO_DEVICE) {   // device row d <- canonical row perm[d]
+        const int e = m->rsize == 8
+                          ? launch_gather_convert<double, double>(U, (double*)dst, m->dperm, m->K, (int)row, ctx->stream)
+                          : launch_gather_convert<double, float>(U, (float*)dst, m->dperm, m->K, (int)row, ctx->stream);
+        ce = e ? (cudaError_t)e : cudaStreamSynchronize(ctx->stream);
+    } else if (m->rsize == 8) {
         std::vector<double> buf(n);
         double* b = buf.data();
         parallel_rows(m->K, row, [&](long long d0, long long d1) {
@@ -1241,7 +1278,14 @@ static int get_host(dg_ctx* ctx, MeshData* m, const void* src, double* U) {
     const size_t row = (size_t)m->nvar * m->Np, n = (size_t)m->K * row;
     const long long* perm = m->perm.data();
     cudaError_t ce;
-    if (m->rsize == 8) {
+    if (ctx->host_io == DG_HOST_IO_DEVICE) {   // canonical row k <- device row iperm[k]
+        const int e = m->rsize == 8
+                          ? launch_gather_convert<double, double>((const double*)src, U, m->diperm, m->K, (int)row,
+                                                                  ctx->stream)
+                          : launch_gather_convert<float, double>((const float*)src, U, m->diperm, m->K, (int)row,
+                                                                 ctx->stream);
+        ce = e ? (cudaError_t)e : cudaStreamSynchronize(ctx->stream);
+    } else if (m->rsize == 8) {
         std::vector<double> buf(n);
         ce = cudaMemcpyAsync(buf.data(), src, n * 8, cudaMemcpyDeviceToHost, ctx->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);

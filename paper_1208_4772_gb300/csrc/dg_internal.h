@@ -10,6 +10,12 @@
 
 namespace dgc {
 
+// dst row r <- src row map[r] (rows of rowlen values), converted from S to
+// D, on the device; either side may be host memory that the device reaches
+// coherently (kernels_common.cu)
+template <typename S, typename D>
+int launch_gather_convert(const S* src, D* dst, const long long* map, long long K, int rowlen, cudaStream_t st);
+
 struct MeshData {
     int dim = 2;                  // 2: triangles, 4 variables; 3: tetrahedra, 5 variables
     int nvar = 4;
@@ -117,5 +123,10 @@ struct dg_ctx {
     std::vector<cudaEvent_t> side_events;
     double* res_host = nullptr;       // pinned slots of dg_batch_residual
     int res_host_n = 0;
+    // host state I/O: the device reaches pageable host memory coherently
+    // through the host's page tables (host_coherent), and the mode in
+    // effect (DG_HOST_IO_STAGED or DG_HOST_IO_DEVICE)
+    bool host_coherent = false;
+    int host_io = 1;
     std::string err;
 };

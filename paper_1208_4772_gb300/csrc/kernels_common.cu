@@ -91,6 +91,22 @@ __global__ void permute_rows(const Real* src, Real* dst, const long long* map, l
     }
 }
 
+// dst row r <- src row map[r], converted from S to D; one warp per row at a
+// time, its lanes along the row.  Either side may be host memory that the
+// device reaches coherently (pageable memory through the host's page
+// tables): each row is one contiguous read and one contiguous write.
+template <typename S, typename D>
+__global__ void __launch_bounds__(256) gather_rows_convert(const S* src, D* dst, const long long* map, long long K,
+                                                           int rowlen) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < K; r += nw) {
+        const S* s = src + map[r] * rowlen;
+        D* d = dst + r * rowlen;
+        for (int c = lane; c < rowlen; c += 32) d[c] = (D)s[c];
+    }
+}
+
 // Prolongation of a state between degrees: out[k][v][i] = sum_j P[i][j]
 // in[src[k]][v][j] (nvar variables; src null: src[k] = k), one thread per
 // output value.
@@ -142,6 +158,14 @@ int launch_permute(const Real* src, Real* dst, const long long* map, long long K
     return (int)cudaGetLastError();
 }
 
+template <typename S, typename D>
+int launch_gather_convert(const S* src, D* dst, const long long* map, long long K, int rowlen, cudaStream_t st) {
+    if (K == 0) return 0;
+    const long long warps = K < 152LL * 64 ? K : 152LL * 64;   // 8 warps a block, up to 8 blocks an SM
+    gather_rows_convert<S, D><<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(src, dst, map, K, rowlen);
+    return (int)cudaGetLastError();
+}
+
 template int launch_residual<float>(const float*, int, long long, int, double*, double*, cudaStream_t);
 template int launch_residual<double>(const double*, int, long long, int, double*, double*, cudaStream_t);
 template int launch_permute<float>(const float*, float*, const long long*, long long, int, cudaStream_t);
@@ -172,5 +196,12 @@ int launch_bounded_wait(uint32_t limit, int arrive, int* status, cudaStream_t st
     bounded_wait_kernel<<<1, 32, 0, st>>>(limit, arrive, status);
     return (int)cudaGetLastError();
 }
+
+template int launch_gather_convert<double, float>(const double*, float*, const long long*, long long, int,
+                                                  cudaStream_t);
+template int launch_gather_convert<float, double>(const float*, double*, const long long*, long long, int,
+                                                  cudaStream_t);
+template int launch_gather_convert<double, double>(const double*, double*, const long long*, long long, int,
+                                                   cudaStream_t);
 
 }  // namespace dgc
