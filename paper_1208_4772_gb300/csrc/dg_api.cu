@@ -1253,21 +1253,21 @@ static int put_host(dg_ctx* ctx, MeshData* m, const double* U, void* dst) {
                           : launch_gather_convert<double, float>(U, (float*)dst, m->dperm, m->K, (int)row, ctx->stream);
         ce = e ? (cudaError_t)e : cudaStreamSynchronize(ctx->stream);
     } else if (m->rsize == 8) {
-        std::vector<double> buf(n);
-        double* b = buf.data();
+        std::unique_ptr<double[]> buf(new double[n]);   // not zero-filled: every value is written
+        double* b = buf.get();
         parallel_rows(m->K, row, [&](long long d0, long long d1) {
             for (long long d = d0; d < d1; ++d) std::memcpy(&b[d * row], U + perm[d] * row, row * 8);
         });
-        ce = cudaMemcpyAsync(dst, buf.data(), n * 8, cudaMemcpyHostToDevice, ctx->stream);
+        ce = cudaMemcpyAsync(dst, buf.get(), n * 8, cudaMemcpyHostToDevice, ctx->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
     } else {
-        std::vector<float> buf(n);
-        float* b = buf.data();
+        std::unique_ptr<float[]> buf(new float[n]);   // not zero-filled: every value is written
+        float* b = buf.get();
         parallel_rows(m->K, row, [&](long long d0, long long d1) {
             for (long long d = d0; d < d1; ++d)
                 for (size_t i = 0; i < row; ++i) b[d * row + i] = (float)U[perm[d] * row + i];
         });
-        ce = cudaMemcpyAsync(dst, buf.data(), n * 4, cudaMemcpyHostToDevice, ctx->stream);
+        ce = cudaMemcpyAsync(dst, buf.get(), n * 4, cudaMemcpyHostToDevice, ctx->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
     }
     if (ce != cudaSuccess) return fail(ctx, DG_ECUDA, std::string("state upload: ") + cudaGetErrorString(ce));
@@ -1286,21 +1286,21 @@ static int get_host(dg_ctx* ctx, MeshData* m, const void* src, double* U) {
                                                                  ctx->stream);
         ce = e ? (cudaError_t)e : cudaStreamSynchronize(ctx->stream);
     } else if (m->rsize == 8) {
-        std::vector<double> buf(n);
-        ce = cudaMemcpyAsync(buf.data(), src, n * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        std::unique_ptr<double[]> buf(new double[n]);   // not zero-filled: every value is written
+        ce = cudaMemcpyAsync(buf.get(), src, n * 8, cudaMemcpyDeviceToHost, ctx->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
         if (ce == cudaSuccess) {
-            const double* b = buf.data();
+            const double* b = buf.get();
             parallel_rows(m->K, row, [&](long long d0, long long d1) {
                 for (long long d = d0; d < d1; ++d) std::memcpy(U + perm[d] * row, &b[d * row], row * 8);
             });
         }
     } else {
-        std::vector<float> buf(n);
-        ce = cudaMemcpyAsync(buf.data(), src, n * 4, cudaMemcpyDeviceToHost, ctx->stream);
+        std::unique_ptr<float[]> buf(new float[n]);   // not zero-filled: every value is written
+        ce = cudaMemcpyAsync(buf.get(), src, n * 4, cudaMemcpyDeviceToHost, ctx->stream);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
         if (ce == cudaSuccess) {
-            const float* b = buf.data();
+            const float* b = buf.get();
             parallel_rows(m->K, row, [&](long long d0, long long d1) {
                 for (long long d = d0; d < d1; ++d)
                     for (size_t i = 0; i < row; ++i) U[perm[d] * row + i] = b[d * row + i];
