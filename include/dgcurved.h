@@ -10,7 +10,8 @@
  *
  * Conventions (all calls)
  *   - Every function returns an int status: DG_OK (0) or a negative DG_E*
- *     code.  No C++ exception crosses the ABI.  dg_last_error(ctx) returns a
+ *     code.  No C++ exception crosses the ABI: a host allocation or thread
+ *     that cannot be had inside a call returns DG_ENOMEM.  dg_last_error(ctx) returns a
  *     NUL-terminated description of the last failure on that context (valid
  *     until the next call on the same context; ctx may be NULL for calls
  *     that take none).

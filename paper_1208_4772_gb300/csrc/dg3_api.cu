@@ -183,7 +183,7 @@ int dg_tet_sizes(int N, int32_t* out4) {
     return DG_OK;
 }
 
-int dg_tet_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const int8_t* bc, const double* node_xyz,
+static int dg_tet_mesh_upload_body(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const int8_t* bc, const double* node_xyz,
                     const dg_params* p, dg_mesh* out) {
     if (!ctx) return api_fail(nullptr, DG_EINVAL, "ctx is NULL");
     if (!EToV || !bc || !node_xyz || !p || !out) return api_fail(ctx, DG_EINVAL, "NULL argument");
@@ -514,6 +514,15 @@ int dg_tet_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const
     ctx->meshes[h] = m;
     *out = h;
     return DG_OK;
+}
+
+int dg_tet_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const int8_t* bc, const double* node_xyz,
+                    const dg_params* p, dg_mesh* out) {
+    try {
+        return dg_tet_mesh_upload_body(ctx, N, K, EToV, bc, node_xyz, p, out);
+    } catch (...) {
+        return exception_status(ctx);
+    }
 }
 
 int dg_mesh_info(dg_ctx* ctx, dg_mesh h, int64_t* out6) {

@@ -12,10 +12,12 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <map>
 #include <memory>
 #include <functional>
 #include <mutex>
+#include <new>
 #include <string>
 #include <thread>
 #include <vector>
@@ -436,6 +438,17 @@ namespace dgc {
 void set_global_error(const std::string& msg) { g_err = msg; }
 
 int api_fail(dg_ctx* ctx, int code, const std::string& msg) { return fail(ctx, code, msg); }
+int exception_status(dg_ctx* ctx) {
+    try {
+        throw;
+    } catch (const std::bad_alloc&) {
+        return fail(ctx, DG_ENOMEM, "host allocation failed");
+    } catch (const std::exception& e) {
+        return fail(ctx, DG_ENOMEM, std::string("host resources exhausted: ") + e.what());
+    } catch (...) {
+        return fail(ctx, DG_ENOMEM, "host resources exhausted");
+    }
+}
 int api_alloc(dg_ctx* ctx, MeshData& m, void** p, size_t bytes) { return alloc(ctx, m, p, bytes); }
 void api_free_mesh(MeshData* m) { free_mesh(m); }
 
@@ -669,7 +682,7 @@ static int enqueue_av_branches(dg_ctx* ctx, const std::vector<MeshData*>& av, co
     return DG_OK;
 }
 
-extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* hs, const double* dts, int nsteps) {
+static int dg_batch_step_body(dg_ctx* ctx, int n, const dg_mesh* hs, const double* dts, int nsteps) {
     if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
     if (n <= 0 || !hs || !dts || nsteps < 0) return fail(ctx, DG_EINVAL, "bad argument");
     std::vector<MeshData*> ms(n);
@@ -736,6 +749,14 @@ extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* hs, const double
     }
     for (int s = 0; s < nsteps; ++s) CUDA_OK(ctx, cudaGraphLaunch(ctx->batch_gexec, ctx->stream));
     return DG_OK;
+}
+
+extern "C" extern "C" int dg_batch_step(dg_ctx* ctx, int n, const dg_mesh* hs, const double* dts, int nsteps) {
+    try {
+        return dg_batch_step_body(ctx, n, hs, dts, nsteps);
+    } catch (...) {
+        return exception_status(ctx);
+    }
 }
 
 // ===========================================================================
@@ -1154,7 +1175,7 @@ static int upload_prepared(dg_ctx* ctx, dg_prepared* pr, dg_mesh* out) {
     return DG_OK;
 }
 
-int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int8_t* EToF, const int8_t* bc,
+static int dg_mesh_upload_body(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int8_t* EToF, const int8_t* bc,
                    const double* node_xy, const dg_params* p, dg_mesh* out) {
     if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
     if (!out) return fail(ctx, DG_EINVAL, "NULL argument");
@@ -1164,7 +1185,16 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
     return upload_prepared(ctx, &pr, out);
 }
 
-int dg_mesh_prepare(int N, int64_t K, const int32_t* EToE, const int8_t* EToF, const int8_t* bc,
+int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int8_t* EToF, const int8_t* bc,
+                   const double* node_xy, const dg_params* p, dg_mesh* out) {
+    try {
+        return dg_mesh_upload_body(ctx, N, K, EToE, EToF, bc, node_xy, p, out);
+    } catch (...) {
+        return exception_status(ctx);
+    }
+}
+
+static int dg_mesh_prepare_body(int N, int64_t K, const int32_t* EToE, const int8_t* EToF, const int8_t* bc,
                     const double* node_xy, const dg_params* p, dg_prepared** out) {
     if (!out) return fail(nullptr, DG_EINVAL, "NULL argument");
     *out = nullptr;
@@ -1178,7 +1208,16 @@ int dg_mesh_prepare(int N, int64_t K, const int32_t* EToE, const int8_t* EToF, c
     return DG_OK;
 }
 
-int dg_mesh_upload_prepared(dg_ctx* ctx, dg_prepared* prep, dg_mesh* out) {
+int dg_mesh_prepare(int N, int64_t K, const int32_t* EToE, const int8_t* EToF, const int8_t* bc,
+                    const double* node_xy, const dg_params* p, dg_prepared** out) {
+    try {
+        return dg_mesh_prepare_body(N, K, EToE, EToF, bc, node_xy, p, out);
+    } catch (...) {
+        return exception_status(nullptr);
+    }
+}
+
+static int dg_mesh_upload_prepared_body(dg_ctx* ctx, dg_prepared* prep, dg_mesh* out) {
     if (!prep) return fail(ctx, DG_EINVAL, "NULL prepared mesh");
     if (!ctx || !out || !prep->m) {
         dg_prepared_free(prep);
@@ -1187,6 +1226,14 @@ int dg_mesh_upload_prepared(dg_ctx* ctx, dg_prepared* prep, dg_mesh* out) {
     const int e = upload_prepared(ctx, prep, out);
     delete prep;
     return e;
+}
+
+int dg_mesh_upload_prepared(dg_ctx* ctx, dg_prepared* prep, dg_mesh* out) {
+    try {
+        return dg_mesh_upload_prepared_body(ctx, prep, out);
+    } catch (...) {
+        return exception_status(ctx);
+    }
 }
 
 int dg_prepared_free(dg_prepared* prep) {
@@ -1238,7 +1285,12 @@ static void parallel_rows(long long K, size_t row, const std::function<void(long
     for (unsigned t = 0; t < T; ++t) {
         const long long d0 = (long long)t * per, d1 = std::min<long long>(K, d0 + per);
         if (d0 >= d1) break;
-        th.emplace_back([&body, d0, d1] { body(d0, d1); });
+        try {
+            th.emplace_back([&body, d0, d1] { body(d0, d1); });
+        } catch (...) {   // no thread to be had: the remaining rows on this one
+            body(d0, K);
+            break;
+        }
     }
     for (auto& x : th) x.join();
 }
@@ -1311,7 +1363,7 @@ static int get_host(dg_ctx* ctx, MeshData* m, const void* src, double* U) {
     return DG_OK;
 }
 
-int dg_set_state(dg_ctx* ctx, dg_mesh h, const double* U) {
+static int dg_set_state_body(dg_ctx* ctx, dg_mesh h, const double* U) {
     if (!ctx || !U) return fail(ctx, DG_EINVAL, "NULL argument");
     MeshData* m = find(ctx, h);
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
@@ -1320,12 +1372,28 @@ int dg_set_state(dg_ctx* ctx, dg_mesh h, const double* U) {
     return put_host(ctx, m, U, m->U[0]);
 }
 
-int dg_get_state(dg_ctx* ctx, dg_mesh h, double* U_out) {
+int dg_set_state(dg_ctx* ctx, dg_mesh h, const double* U) {
+    try {
+        return dg_set_state_body(ctx, h, U);
+    } catch (...) {
+        return exception_status(ctx);
+    }
+}
+
+static int dg_get_state_body(dg_ctx* ctx, dg_mesh h, double* U_out) {
     if (!ctx || !U_out) return fail(ctx, DG_EINVAL, "NULL argument");
     MeshData* m = find(ctx, h);
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
     cudaSetDevice(ctx->device);
     return get_host(ctx, m, m->U[0], U_out);
+}
+
+int dg_get_state(dg_ctx* ctx, dg_mesh h, double* U_out) {
+    try {
+        return dg_get_state_body(ctx, h, U_out);
+    } catch (...) {
+        return exception_status(ctx);
+    }
 }
 
 int dg_set_state_device(dg_ctx* ctx, dg_mesh h, const float* U_dev) {
@@ -1353,7 +1421,7 @@ int dg_get_state_device(dg_ctx* ctx, dg_mesh h, float* U_dev_out) {
     return DG_OK;
 }
 
-int dg_eval_rhs(dg_ctx* ctx, dg_mesh h, double* rhs_out) {
+static int dg_eval_rhs_body(dg_ctx* ctx, dg_mesh h, double* rhs_out) {
     if (!ctx || !rhs_out) return fail(ctx, DG_EINVAL, "NULL argument");
     MeshData* m = find(ctx, h);
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
@@ -1363,7 +1431,15 @@ int dg_eval_rhs(dg_ctx* ctx, dg_mesh h, double* rhs_out) {
     return get_host(ctx, m, m->rhs, rhs_out);
 }
 
-int dg_step(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
+int dg_eval_rhs(dg_ctx* ctx, dg_mesh h, double* rhs_out) {
+    try {
+        return dg_eval_rhs_body(ctx, h, rhs_out);
+    } catch (...) {
+        return exception_status(ctx);
+    }
+}
+
+static int dg_step_body(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
     if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
     MeshData* m = find(ctx, h);
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
@@ -1399,6 +1475,14 @@ int dg_step(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
     return DG_OK;
 }
 
+int dg_step(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
+    try {
+        return dg_step_body(ctx, h, dt, nsteps);
+    } catch (...) {
+        return exception_status(ctx);
+    }
+}
+
 int dg_residual(dg_ctx* ctx, dg_mesh h, double* out_linf, double* out_l2) {
     if (!ctx || !out_linf || !out_l2) return fail(ctx, DG_EINVAL, "NULL argument");
     MeshData* m = find(ctx, h);
@@ -1425,7 +1509,7 @@ int dg_residual(dg_ctx* ctx, dg_mesh h, double* out_linf, double* out_l2) {
     return finite ? DG_OK : fail(ctx, DG_ENONFINITE, "non-finite residual norm");
 }
 
-int dg_batch_residual(dg_ctx* ctx, int n, const dg_mesh* hs, double* out10) {
+static int dg_batch_residual_body(dg_ctx* ctx, int n, const dg_mesh* hs, double* out10) {
     if (!ctx || n <= 0 || !hs || !out10) return fail(ctx, DG_EINVAL, "bad argument");
     std::vector<MeshData*> ms(n);
     for (int i = 0; i < n; ++i) {
@@ -1466,6 +1550,14 @@ int dg_batch_residual(dg_ctx* ctx, int n, const dg_mesh* hs, double* out10) {
         }
     }
     return finite ? DG_OK : fail(ctx, DG_ENONFINITE, "non-finite residual norm");
+}
+
+int dg_batch_residual(dg_ctx* ctx, int n, const dg_mesh* hs, double* out10) {
+    try {
+        return dg_batch_residual_body(ctx, n, hs, out10);
+    } catch (...) {
+        return exception_status(ctx);
+    }
 }
 
 int dg_av_count(dg_ctx* ctx, dg_mesh h, int64_t* out) {
@@ -1546,7 +1638,7 @@ int dg_selftest_bounded_wait(dg_ctx* ctx, uint32_t limit, int arrive, int32_t* o
     return DG_OK;
 }
 
-int dg_step_lserk(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
+static int dg_step_lserk_body(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
     if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
     MeshData* m = find(ctx, h);
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
@@ -1579,7 +1671,15 @@ int dg_step_lserk(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
     return DG_OK;
 }
 
-int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to) {
+int dg_step_lserk(dg_ctx* ctx, dg_mesh h, double dt, int nsteps) {
+    try {
+        return dg_step_lserk_body(ctx, h, dt, nsteps);
+    } catch (...) {
+        return exception_status(ctx);
+    }
+}
+
+static int dg_prolong_body(dg_ctx* ctx, dg_mesh from, dg_mesh to) {
     if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
     MeshData* a = find(ctx, from);
     MeshData* b = find(ctx, to);
@@ -1634,6 +1734,14 @@ int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to) {
     if (e) return fail(ctx, DG_ECUDA, std::string("prolongation failed: ") + cudaGetErrorString((cudaError_t)e));
     b->eps_valid = false;
     return DG_OK;
+}
+
+int dg_prolong(dg_ctx* ctx, dg_mesh from, dg_mesh to) {
+    try {
+        return dg_prolong_body(ctx, from, to);
+    } catch (...) {
+        return exception_status(ctx);
+    }
 }
 
 // Time nsteps SSP-RK3 steps of m (dt = 0: the full work, the state
@@ -1736,7 +1844,7 @@ int dg_set_tc_config(dg_ctx* ctx, dg_mesh h, int32_t cfg, int32_t* cands_out, in
     return DG_OK;
 }
 
-int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t* cand_out, double* ms_out,
+static int dg_autotune_body(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t* cand_out, double* ms_out,
                 int32_t* ncand_out) {
     if (!ctx || !tile_e_out) return fail(ctx, DG_EINVAL, "NULL argument");
     MeshData* m = find(ctx, h);
@@ -1815,6 +1923,15 @@ int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t
         if (ms_out) ms_out[c] = ms[c] / nsteps;
     }
     return check_device_errors(ctx);
+}
+
+int dg_autotune(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t* cand_out, double* ms_out,
+                int32_t* ncand_out) {
+    try {
+        return dg_autotune_body(ctx, h, nsteps, tile_e_out, cand_out, ms_out, ncand_out);
+    } catch (...) {
+        return exception_status(ctx);
+    }
 }
 
 int dg_set_profiling(dg_ctx* ctx, dg_mesh h, int on) {

@@ -74,6 +74,9 @@ int enqueue_stage3(const MeshData& m, const void* Us, const void* Un, void* out,
                    int rhs_only, cudaStream_t st, void* dU);
 // helpers of the C ABI shared by dg_api.cu and dg3_api.cu
 int api_fail(dg_ctx* ctx, int code, const std::string& msg);
+// the status of an exception caught around an entry point's body (called
+// inside the catch handler): none may cross the C ABI
+int exception_status(dg_ctx* ctx);
 int api_alloc(dg_ctx* ctx, MeshData& m, void** p, size_t bytes);
 void api_free_mesh(MeshData* m);
 bool fused_sensor(const MeshData& m);
