@@ -184,7 +184,7 @@ int dg_tet_sizes(int N, int32_t* out4) {
 }
 
 static int dg_tet_mesh_upload_body(dg_ctx* ctx, int N, int64_t K, const int64_t* EToV, const int8_t* bc, const double* node_xyz,
-                    const dg_params* p, dg_mesh* out) {
+                                   const dg_params* p, dg_mesh* out) {
     if (!ctx) return api_fail(nullptr, DG_EINVAL, "ctx is NULL");
     if (!EToV || !bc || !node_xyz || !p || !out) return api_fail(ctx, DG_EINVAL, "NULL argument");
     if (!supported_degree3(N)) return api_fail(ctx, DG_EINVAL, "tetrahedral device path supports 2 <= N <= 4");

@@ -1176,7 +1176,7 @@ static int upload_prepared(dg_ctx* ctx, dg_prepared* pr, dg_mesh* out) {
 }
 
 static int dg_mesh_upload_body(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int8_t* EToF, const int8_t* bc,
-                   const double* node_xy, const dg_params* p, dg_mesh* out) {
+                               const double* node_xy, const dg_params* p, dg_mesh* out) {
     if (!ctx) return fail(nullptr, DG_EINVAL, "ctx is NULL");
     if (!out) return fail(ctx, DG_EINVAL, "NULL argument");
     dg_prepared pr;
@@ -1195,7 +1195,7 @@ int dg_mesh_upload(dg_ctx* ctx, int N, int64_t K, const int32_t* EToE, const int
 }
 
 static int dg_mesh_prepare_body(int N, int64_t K, const int32_t* EToE, const int8_t* EToF, const int8_t* bc,
-                    const double* node_xy, const dg_params* p, dg_prepared** out) {
+                                const double* node_xy, const dg_params* p, dg_prepared** out) {
     if (!out) return fail(nullptr, DG_EINVAL, "NULL argument");
     *out = nullptr;
     auto* pr = new dg_prepared();
@@ -1845,7 +1845,7 @@ int dg_set_tc_config(dg_ctx* ctx, dg_mesh h, int32_t cfg, int32_t* cands_out, in
 }
 
 static int dg_autotune_body(dg_ctx* ctx, dg_mesh h, int nsteps, int32_t* tile_e_out, int32_t* cand_out, double* ms_out,
-                int32_t* ncand_out) {
+                            int32_t* ncand_out) {
     if (!ctx || !tile_e_out) return fail(ctx, DG_EINVAL, "NULL argument");
     MeshData* m = find(ctx, h);
     if (!m) return fail(ctx, DG_ENOTFOUND, "unknown mesh handle");
